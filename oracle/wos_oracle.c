@@ -1,0 +1,557 @@
+/*
+ * Walk on Spheres for the screened Poisson equation -- plain FP64 CPU oracle.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test suite, the package's smoke check and
+ * the benchmark's CPU-baseline / reference legs may load this library. It shares
+ * no code, header, table or constant generator with the CUDA path, and it never
+ * calls it. It is deliberately slow and written for reading against the paper:
+ *
+ *   PDE (Sec. III, Eq. screened_poisson_wos with c = sigma):  Laplace(u) = sigma u in Omega,
+ *       u = g on the boundary.  f = 0 (no source term).
+ *   One-point estimator (Sec. IV-A, recursive estimator):     u^(x_k) = g(xbar_k)  if x_k is within
+ *       eps of the boundary, else C(x_k) u^(x_{k+1}), x_{k+1} uniform on the largest empty sphere.
+ *   Normaliser C (Sec. IV-A, "depends on dimension and radius"):
+ *       C_nu(z) = (z/2)^nu / (Gamma(nu+1) I_nu(z)),  z = R sqrt(sigma),  nu = d/2 - 1.
+ *   First-sphere gradient (Sec. IV-A, gradient estimator):   grad^ = alpha(R0) u^(x_1) v(x_1).
+ *       The paper prints the Laplace factor n/R; for sigma > 0 the unbiased factor is
+ *       alpha = (d/R0) C_{nu+1}(z0) (it reduces to d/R0 at sigma = 0). The literal factor is
+ *       available through or_options.laplace_factor.
+ *   Closest boundary point xbar (Fig. 2): g is read at the projection of x_k on the nearest
+ *       boundary component.
+ *   Planner (Sec. III screened-harmonic paths; Sec. VII adaptive step):
+ *       x <- x + s grad/|grad|,  s = min(s_ub, 0.5 d_bound).
+ *   Distance functions (Sec. VI, Eq. for d(x, dOmega); Sec. VII-A point-set distance):
+ *       balls: |x - c| - r;  outer ball: r_o - |x - c_o|;  points: |x - p|;  box faces.
+ *
+ * Readings where the paper is silent (random stream, ties, caps) follow the build's
+ * documented contract:
+ *   - sphere directions: Philox4x32-10 (Salmon et al., SC'11), key = seed, counter =
+ *     (walk_lo, walk_hi, step, block); Box-Muller on consecutive output pairs;
+ *   - strict eps test (R < eps); ties between components go to the lowest component id in
+ *     the order [goal, balls, points, outer ball, box faces lo_0, hi_0, lo_1, ...];
+ *   - a walk that reaches max_steps jumps without entering the eps shell contributes 0.
+ *
+ * Log-Bessel: S_mu(z) = Gamma(mu+1) (z/2)^-mu I_mu(z) = sum_k (z^2/4)^k / (k! (mu+1)_k)
+ * (DLMF 10.25.2), summed directly; log C_nu(z) = -log S_nu(z).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXD 16
+#define OR_MAXEXP 16
+#define OR_CHUNK 256 /* walks per partial sum; fixed so results do not depend on threads */
+
+#define OR_KIND_GOAL 0
+#define OR_KIND_BALL 1
+#define OR_KIND_POINT 2
+#define OR_KIND_OUTER 3
+#define OR_KIND_FACE 4
+
+typedef struct {
+    int32_t d;
+    int32_t has_box;
+    double box_lo[OR_MAXD];
+    double box_hi[OR_MAXD];
+    int32_t has_outer;
+    double outer_c[OR_MAXD];
+    double outer_r;
+    int32_t has_goal;
+    double goal_c[OR_MAXD];
+    double goal_r;
+    int32_t n_balls;
+    const double *ball_c; /* n_balls x d, row major */
+    const double *ball_r; /* n_balls */
+    int64_t n_points;
+    const double *points; /* n_points x d */
+    int32_t n_exp;        /* >0: g(x) = sum_k w_k exp(a_k . x) on the whole boundary */
+    const double *exp_w;  /* n_exp */
+    const double *exp_a;  /* n_exp x d */
+} or_domain;
+
+typedef struct {
+    uint64_t seed;
+    int64_t max_steps;
+    int32_t grad;           /* 1: gradient walks (the first sphere is always taken) */
+    int32_t laplace_factor; /* 1: the paper's printed factor d/R0 instead of alpha(R0) */
+} or_options;
+
+typedef struct {
+    double term;   /* u^ for this walk */
+    int64_t jumps; /* sphere jumps k; distance evaluations = k + 1 */
+    int32_t capped;
+    int32_t outside;
+    int32_t comp_kind;
+    int64_t comp_index;
+    double grad[OR_MAXD];
+    double dsigma;
+    double dw[OR_MAXEXP];
+} or_walk_out;
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10, from the definition in Salmon, Moraes, Dror, Shaw (SC'11):  */
+/* 10 rounds of two 32x32->64 multiplies, Weyl key schedule.                  */
+/* ------------------------------------------------------------------------- */
+void or_philox4x32_10(const uint32_t key[2], const uint32_t ctr[4], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u; /* round multipliers */
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u; /* key increments    */
+    uint32_t k0 = key[0], k1 = key[1];
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+/* d standard normals for (walk, step): block b uses counter (walk_lo, walk_hi, step, b);
+ * outputs (r0, r1) and (r2, r3) feed Box-Muller with u1 = (r + 1) 2^-32 in (0, 1] and
+ * u2 = r 2^-32 in [0, 1). */
+void or_normals(uint64_t seed, uint64_t walk, uint32_t step, int d, double *n)
+{
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    const double two_m32 = 1.0 / 4294967296.0;
+    const double two_pi = 6.283185307179586476925286766559;
+    int nblocks = (d + 3) / 4;
+    for (int b = 0; b < nblocks; ++b) {
+        uint32_t ctr[4] = {(uint32_t)walk, (uint32_t)(walk >> 32), step, (uint32_t)b};
+        uint32_t r[4];
+        or_philox4x32_10(key, ctr, r);
+        for (int pair = 0; pair < 2; ++pair) {
+            double u1 = ((double)r[2 * pair] + 1.0) * two_m32;
+            double u2 = (double)r[2 * pair + 1] * two_m32;
+            double rad = sqrt(-2.0 * log(u1));
+            int i0 = 4 * b + 2 * pair;
+            if (i0 < d) n[i0] = rad * cos(two_pi * u2);
+            if (i0 + 1 < d) n[i0 + 1] = rad * sin(two_pi * u2);
+        }
+    }
+}
+
+/* Uniform direction on the unit sphere: v = n / |n| (e_0 if |n| = 0). */
+void or_direction(uint64_t seed, uint64_t walk, uint32_t step, int d, double *v)
+{
+    double n[OR_MAXD + 4];
+    or_normals(seed, walk, step, d, n);
+    double ss = 0.0;
+    for (int j = 0; j < d; ++j) ss += n[j] * n[j];
+    if (ss > 0.0) {
+        double norm = sqrt(ss);
+        for (int j = 0; j < d; ++j) v[j] = n[j] / norm;
+    } else {
+        for (int j = 0; j < d; ++j) v[j] = 0.0;
+        v[0] = 1.0;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Normaliser: S_mu(z) = sum_k (z^2/4)^k / (k! (mu+1)_k)   (DLMF 10.25.2)     */
+/* ------------------------------------------------------------------------- */
+double or_series_S(double mu, double z)
+{
+    double q = 0.25 * z * z;
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 5000; ++k) {
+        term *= q / ((double)k * (mu + (double)k));
+        sum += term;
+        if (term <= 1e-17 * sum) break;
+    }
+    return sum;
+}
+
+/* log C_nu(z), C_nu(z) = (z/2)^nu / (Gamma(nu+1) I_nu(z)) = 1 / S_nu(z). Valid for z < ~700. */
+double or_log_C(double nu, double z) { return -log(or_series_S(nu, z)); }
+
+/* d/dsigma log C_nu(R sqrt(sigma)) = -(R^2 / (2d)) S_{nu+1}(z) / S_nu(z), d = 2 nu + 2. */
+double or_dsigma_log_C(double nu, double R, double sigma)
+{
+    double z = R * sqrt(sigma);
+    double d = 2.0 * nu + 2.0;
+    return -(R * R / (2.0 * d)) * or_series_S(nu + 1.0, z) / or_series_S(nu, z);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Distance to the boundary and closest boundary point (Sec. VI, VII-A).      */
+/* ------------------------------------------------------------------------- */
+static double norm_diff(int d, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) {
+        double t = a[j] - b[j];
+        s += t * t;
+    }
+    return sqrt(s);
+}
+
+double or_distance(const or_domain *D, const double *x, int32_t *kind, int64_t *index,
+                   double *xbar)
+{
+    const int d = D->d;
+    double best = INFINITY;
+    int32_t bk = -1;
+    int64_t bi = -1;
+    if (D->has_goal) {
+        double r = norm_diff(d, x, D->goal_c) - D->goal_r;
+        if (r < best) { best = r; bk = OR_KIND_GOAL; bi = 0; }
+    }
+    for (int32_t i = 0; i < D->n_balls; ++i) {
+        double r = norm_diff(d, x, D->ball_c + (int64_t)i * d) - D->ball_r[i];
+        if (r < best) { best = r; bk = OR_KIND_BALL; bi = i; }
+    }
+    for (int64_t i = 0; i < D->n_points; ++i) {
+        double r = norm_diff(d, x, D->points + i * d);
+        if (r < best) { best = r; bk = OR_KIND_POINT; bi = i; }
+    }
+    if (D->has_outer) {
+        double r = D->outer_r - norm_diff(d, x, D->outer_c);
+        if (r < best) { best = r; bk = OR_KIND_OUTER; bi = 0; }
+    }
+    if (D->has_box) {
+        for (int j = 0; j < d; ++j) {
+            double rlo = x[j] - D->box_lo[j];
+            if (rlo < best) { best = rlo; bk = OR_KIND_FACE; bi = 2 * j; }
+            double rhi = D->box_hi[j] - x[j];
+            if (rhi < best) { best = rhi; bk = OR_KIND_FACE; bi = 2 * j + 1; }
+        }
+    }
+    if (kind) *kind = bk;
+    if (index) *index = bi;
+    if (xbar) {
+        /* projection of x on the nearest component */
+        const double *c = NULL;
+        double rad = 0.0;
+        if (bk == OR_KIND_GOAL) { c = D->goal_c; rad = D->goal_r; }
+        if (bk == OR_KIND_BALL) { c = D->ball_c + bi * d; rad = D->ball_r[bi]; }
+        if (bk == OR_KIND_OUTER) { c = D->outer_c; rad = D->outer_r; }
+        if (c) {
+            double len = norm_diff(d, x, c);
+            for (int j = 0; j < d; ++j)
+                xbar[j] = len > 0.0 ? c[j] + rad * (x[j] - c[j]) / len : c[j] + (j == 0 ? rad : 0.0);
+        } else if (bk == OR_KIND_POINT) {
+            for (int j = 0; j < d; ++j) xbar[j] = D->points[bi * d + j];
+        } else if (bk == OR_KIND_FACE) {
+            for (int j = 0; j < d; ++j) xbar[j] = x[j];
+            int j = (int)(bi / 2);
+            xbar[j] = (bi % 2 == 0) ? D->box_lo[j] : D->box_hi[j];
+        } else {
+            for (int j = 0; j < d; ++j) xbar[j] = x[j];
+        }
+    }
+    return best;
+}
+
+/* Boundary data: sum_k w_k exp(a_k . xbar) if exp data is set, else 1 on the goal, 0 elsewhere. */
+static double boundary_g(const or_domain *D, int32_t kind, const double *xbar, double *dw)
+{
+    if (D->n_exp > 0) {
+        double g = 0.0;
+        for (int k = 0; k < D->n_exp; ++k) {
+            double dot = 0.0;
+            for (int j = 0; j < D->d; ++j) dot += D->exp_a[k * D->d + j] * xbar[j];
+            double e = exp(dot);
+            if (dw) dw[k] = e;
+            g += D->exp_w[k] * e;
+        }
+        return g;
+    }
+    return kind == OR_KIND_GOAL ? 1.0 : 0.0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* One walk (Sec. IV-A).                                                      */
+/* ------------------------------------------------------------------------- */
+void or_walk(const or_domain *D, const double *x0, uint64_t walk, double eps, double sigma,
+             const or_options *opt, or_walk_out *out)
+{
+    const int d = D->d;
+    const double nu = 0.5 * d - 1.0;
+    const double sq = sqrt(sigma);
+    double x[OR_MAXD], xbar[OR_MAXD], v[OR_MAXD], v0[OR_MAXD];
+    double logw = 0.0, dsig = 0.0, R0 = 0.0, z0 = 0.0, logC0 = 0.0;
+    int64_t k = 0;
+    int32_t kind = -1;
+    int64_t index = -1;
+    memset(out, 0, sizeof(*out));
+    for (int j = 0; j < d; ++j) x[j] = x0[j];
+    for (;;) {
+        double R = or_distance(D, x, &kind, &index, xbar);
+        if (k == 0 && !(R > 0.0)) { /* query not in the open domain */
+            out->outside = 1;
+            out->term = NAN;
+            out->dsigma = NAN;
+            for (int j = 0; j < d; ++j) out->grad[j] = NAN;
+            for (int q = 0; q < D->n_exp; ++q) out->dw[q] = NAN;
+            return;
+        }
+        int in_shell = R < eps;
+        if (in_shell && !(opt->grad && k == 0)) {
+            double dw[OR_MAXEXP];
+            double g = boundary_g(D, kind, xbar, dw);
+            double w = exp(logw);
+            out->term = g * w;
+            for (int q = 0; q < D->n_exp; ++q) out->dw[q] = w * dw[q];
+            break;
+        }
+        if (k == opt->max_steps) {
+            out->capped = 1;
+            out->term = 0.0;
+            break;
+        }
+        or_direction(opt->seed, walk, (uint32_t)k, d, v);
+        double z = R * sq;
+        double Snu = or_series_S(nu, z);
+        double Snu1 = or_series_S(nu + 1.0, z);
+        double logC = -log(Snu);
+        if (k == 0) {
+            R0 = R;
+            z0 = z;
+            logC0 = logC;
+            for (int j = 0; j < d; ++j) v0[j] = v[j];
+        }
+        logw += logC;
+        dsig += -(R * R / (2.0 * d)) * Snu1 / Snu;
+        for (int j = 0; j < d; ++j) x[j] = x[j] + R * v[j];
+        ++k;
+    }
+    out->jumps = k;
+    out->comp_kind = kind;
+    out->comp_index = index;
+    out->dsigma = out->term * dsig;
+    if (k > 0 && !out->capped) {
+        /* u^(x_1) = term / C(R0);  alpha(R0) = (d/R0) C_{nu+1}(z0) */
+        double u1 = out->term * exp(-logC0);
+        double factor = opt->laplace_factor ? (double)d / R0
+                                            : ((double)d / R0) / or_series_S(nu + 1.0, z0);
+        for (int j = 0; j < d; ++j) out->grad[j] = factor * u1 * v0[j];
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Per-query estimates over N walks, threaded over fixed chunks of walks.     */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    const or_domain *D;
+    const double *X;
+    int64_t Q, N, walk_offset;
+    double eps, sigma;
+    const or_options *opt;
+    int64_t nchunks;   /* per query */
+    int nfields;       /* doubles per chunk partial */
+    double *partial;   /* Q x nchunks x nfields */
+    int64_t *ipartial; /* Q x nchunks x 3: steps, capped, outside */
+    double *walk_term;
+    int64_t *walk_jumps;
+    double *walk_grad;
+    double *walk_dsigma;
+    int64_t next; /* work cursor */
+    pthread_mutex_t lock;
+} solve_job;
+
+static void run_unit(solve_job *J, int64_t unit)
+{
+    const int d = J->D->d;
+    const int K = J->D->n_exp;
+    int64_t q = unit / J->nchunks, c = unit % J->nchunks;
+    int64_t w0 = c * OR_CHUNK, w1 = w0 + OR_CHUNK < J->N ? w0 + OR_CHUNK : J->N;
+    double *P = J->partial + unit * J->nfields;
+    int64_t *I = J->ipartial + unit * 3;
+    memset(P, 0, sizeof(double) * J->nfields);
+    I[0] = I[1] = I[2] = 0;
+    or_walk_out o;
+    for (int64_t w = w0; w < w1; ++w) {
+        uint64_t walk = (uint64_t)(J->walk_offset + q * J->N + w);
+        or_walk(J->D, J->X + q * d, walk, J->eps, J->sigma, J->opt, &o);
+        int64_t flat = q * J->N + w;
+        if (J->walk_term) J->walk_term[flat] = o.term;
+        if (J->walk_jumps) J->walk_jumps[flat] = o.jumps;
+        if (J->walk_dsigma) J->walk_dsigma[flat] = o.dsigma;
+        if (J->walk_grad)
+            for (int j = 0; j < d; ++j) J->walk_grad[flat * d + j] = o.grad[j];
+        /* fields: [sum u, sum u^2, sum dsigma, grad[d], grad^2[d], dw[K]] */
+        P[0] += o.term;
+        P[1] += o.term * o.term;
+        P[2] += o.dsigma;
+        for (int j = 0; j < d; ++j) {
+            P[3 + j] += o.grad[j];
+            P[3 + d + j] += o.grad[j] * o.grad[j];
+        }
+        for (int k = 0; k < K; ++k) P[3 + 2 * d + k] += o.dw[k];
+        I[0] += o.jumps + 1;
+        I[1] += o.capped;
+        I[2] += o.outside;
+    }
+}
+
+static void *solve_worker(void *arg)
+{
+    solve_job *J = (solve_job *)arg;
+    const int64_t total = J->Q * J->nchunks;
+    for (;;) {
+        pthread_mutex_lock(&J->lock);
+        int64_t unit = J->next++;
+        pthread_mutex_unlock(&J->lock);
+        if (unit >= total) break;
+        run_unit(J, unit);
+    }
+    return NULL;
+}
+
+static double se_of(double s, double s2, int64_t n)
+{
+    if (n < 2) return 0.0;
+    double var = (s2 - s * s / (double)n) / (double)(n - 1);
+    return var > 0.0 ? sqrt(var / (double)n) : 0.0;
+}
+
+/*
+ * Estimates at Q query points (X: Q x d), N walks each. Walk w of query q uses the global
+ * walk index walk_offset + q N + w. Every output pointer may be NULL.
+ *   u, u_se, du_dsigma, walk_steps, capped, outside: Q;  grad, grad_se: Q x d;  du_dw: Q x n_exp;
+ *   walk_term, walk_jumps, walk_dsigma: Q x N;  walk_grad: Q x N x d.
+ * Returns 0, or -1 on bad arguments / allocation failure.
+ */
+int or_solve(const or_domain *D, const double *X, int64_t Q, int64_t N, int64_t walk_offset,
+             double eps, double sigma, const or_options *opt, int nthreads, double *u,
+             double *u_se, double *grad, double *grad_se, double *du_dsigma, double *du_dw,
+             int64_t *walk_steps, int64_t *capped, int64_t *outside, double *walk_term,
+             int64_t *walk_jumps, double *walk_grad, double *walk_dsigma)
+{
+    if (!D || !X || !opt || D->d < 1 || D->d > OR_MAXD || D->n_exp < 0 || D->n_exp > OR_MAXEXP ||
+        Q < 0 || N < 1 || sigma < 0.0)
+        return -1;
+    const int d = D->d, K = D->n_exp;
+    solve_job J;
+    memset(&J, 0, sizeof(J));
+    J.D = D;
+    J.X = X;
+    J.Q = Q;
+    J.N = N;
+    J.walk_offset = walk_offset;
+    J.eps = eps;
+    J.sigma = sigma;
+    J.opt = opt;
+    J.nchunks = (N + OR_CHUNK - 1) / OR_CHUNK;
+    J.nfields = 3 + 2 * d + K;
+    J.walk_term = walk_term;
+    J.walk_jumps = walk_jumps;
+    J.walk_grad = walk_grad;
+    J.walk_dsigma = walk_dsigma;
+    int64_t units = Q * J.nchunks;
+    J.partial = (double *)malloc(sizeof(double) * (size_t)(units * J.nfields + 1));
+    J.ipartial = (int64_t *)malloc(sizeof(int64_t) * (size_t)(units * 3 + 1));
+    if (!J.partial || !J.ipartial) {
+        free(J.partial);
+        free(J.ipartial);
+        return -1;
+    }
+    pthread_mutex_init(&J.lock, NULL);
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    pthread_t th[256];
+    int started = 0;
+    for (int t = 1; t < nthreads; ++t)
+        if (pthread_create(&th[started], NULL, solve_worker, &J) == 0) ++started;
+    solve_worker(&J);
+    for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+    pthread_mutex_destroy(&J.lock);
+
+    for (int64_t q = 0; q < Q; ++q) {
+        double S[3 + 2 * OR_MAXD + OR_MAXEXP];
+        int64_t I[3] = {0, 0, 0};
+        memset(S, 0, sizeof(S));
+        for (int64_t c = 0; c < J.nchunks; ++c) {
+            const double *P = J.partial + (q * J.nchunks + c) * J.nfields;
+            const int64_t *IP = J.ipartial + (q * J.nchunks + c) * 3;
+            for (int f = 0; f < J.nfields; ++f) S[f] += P[f];
+            for (int f = 0; f < 3; ++f) I[f] += IP[f];
+        }
+        double inv = 1.0 / (double)N;
+        if (u) u[q] = S[0] * inv;
+        if (u_se) u_se[q] = I[2] ? NAN : se_of(S[0], S[1], N);
+        if (du_dsigma) du_dsigma[q] = S[2] * inv;
+        for (int j = 0; j < d; ++j) {
+            if (grad) grad[q * d + j] = S[3 + j] * inv;
+            if (grad_se) grad_se[q * d + j] = I[2] ? NAN : se_of(S[3 + j], S[3 + d + j], N);
+        }
+        for (int k = 0; k < K; ++k)
+            if (du_dw) du_dw[q * K + k] = S[3 + 2 * d + k] * inv;
+        if (walk_steps) walk_steps[q] = I[0];
+        if (capped) capped[q] = I[1];
+        if (outside) outside[q] = I[2];
+    }
+    free(J.partial);
+    free(J.ipartial);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Screened-harmonic path (Sec. III; Sec. VII adaptive step s = min(s_ub, d/2)). */
+/* Step i estimates grad u at x_i with N gradient walks, walk offset i N.      */
+/* flags[i]: 1 goal reached before step i (no move), 2 no signal (|grad| = 0,   */
+/* no move), 4 outside the domain (no move).                                  */
+/* Returns the number of points written (the path stops at the goal).         */
+/* ------------------------------------------------------------------------- */
+int64_t or_plan_path(const or_domain *D, const double *x0, int64_t n_steps, int64_t N, double eps,
+                     double sigma, double s_ub, const or_options *opt_in, int nthreads,
+                     double *path, int32_t *flags, double *grads)
+{
+    const int d = D->d;
+    or_options opt = *opt_in;
+    opt.grad = 1;
+    double x[OR_MAXD], g[OR_MAXD], xbar[OR_MAXD];
+    for (int64_t i = 0; i < n_steps; ++i) flags[i] = 0;
+    for (int j = 0; j < d; ++j) x[j] = path[j] = x0[j];
+    int64_t written = 1;
+    for (int64_t i = 0; i < n_steps; ++i) {
+        flags[i] = 0;
+        if (D->has_goal) {
+            double rg = norm_diff(d, x, D->goal_c) - D->goal_r;
+            if (rg < eps) {
+                flags[i] = 1;
+                break;
+            }
+        }
+        int32_t kind;
+        int64_t index;
+        double R = or_distance(D, x, &kind, &index, xbar);
+        int64_t out = 0;
+        if (or_solve(D, x, 1, N, i * N, eps, sigma, &opt, nthreads, NULL, NULL, g, NULL, NULL, NULL,
+                     NULL, NULL, &out, NULL, NULL, NULL, NULL) != 0 ||
+            out > 0 || !(R > 0.0)) {
+            flags[i] = 4;
+            break;
+        }
+        if (grads)
+            for (int j = 0; j < d; ++j) grads[i * d + j] = g[j];
+        double gg = 0.0;
+        for (int j = 0; j < d; ++j) gg += g[j] * g[j];
+        if (gg > 0.0) {
+            double gn = sqrt(gg);
+            double s = 0.5 * R < s_ub ? 0.5 * R : s_ub;
+            for (int j = 0; j < d; ++j) x[j] = x[j] + s * (g[j] / gn);
+        } else {
+            flags[i] = 2;
+        }
+        for (int j = 0; j < d; ++j) path[written * d + j] = x[j];
+        ++written;
+    }
+    return written;
+}

@@ -1,0 +1,1 @@
+"""Placeholder; the binding is added with the CUDA library."""

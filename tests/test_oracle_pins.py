@@ -1,0 +1,354 @@
+"""Pins for the FP64 CPU oracle: checks against what the paper and the mathematics fix,
+never against the oracle itself.
+
+  * Philox4x32-10 known-answer vectors (Salmon et al., SC'11)           -> RNG contract
+  * Box-Muller normals / sphere directions: moments, KS test              -> sphere sampling
+  * log C_nu against scipy's exponentially scaled Bessel I and the odd-d
+    closed forms (d = 3: z / sinh z; d = 5: z^3 / (3 (z cosh z - sinh z)))  -> normaliser C
+  * ball centre (P1): one jump, u^ = C_nu(R sqrt(sigma)) exactly, |grad^| = (d/R) C_{nu+1}
+  * ball off-centre (P2): u = rho(r)/rho(R), grad u radial (scipy), within 4.5 SE
+  * exp boundary data with |a|^2 = sigma (P3): u = g, grad u = a g, du/dw = exp(a.x)
+  * annulus with g = 1 on the inner sphere: closed forms with I_nu, K_nu (sigma > 0) and
+    log / power laws (sigma = 0)
+  * derivative in sigma: closed form at the ball centre, common-random-number FD (P8)
+  * derivative in w: linear, FD exact (P9); max principle (P6); SE ~ N^-1/2 (P7)
+  * planner: adaptive step s = min(s_ub, d/2) and radial descent in the annulus
+and one planted mistake (the paper's literal d/R gradient factor at sigma > 0), which the
+off-centre ball pin must reject.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import special, stats
+
+from paper_2406_01713_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def log_C_scipy(nu, z):
+    """log[(z/2)^nu / (Gamma(nu+1) I_nu(z))] from scipy's ive (I_nu(z) = ive(nu, z) e^z)."""
+    z = np.asarray(z, float)
+    return nu * np.log(z / 2.0) - special.gammaln(nu + 1.0) - (np.log(special.ive(nu, z)) + z)
+
+
+# --------------------------------------------------------------------------- RNG
+def test_philox_known_answers(oracle_mod):
+    n = 0
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        v = [int(t, 16) for t in line.split()]
+        assert oracle_mod.philox4x32_10(v[4:6], v[0:4]) == v[6:10]
+        n += 1
+    assert n == 3
+
+
+def test_normals_are_standard_gaussian(oracle_mod):
+    d = 4
+    samples = np.array([oracle_mod.normals(2406, w, 3, d) for w in range(20000)]).ravel()
+    assert abs(samples.mean()) < 5 / math.sqrt(samples.size)
+    assert abs(samples.var() - 1.0) < 5 * math.sqrt(2.0 / samples.size)
+    assert stats.kstest(samples, "norm").pvalue > 1e-3
+
+
+@pytest.mark.parametrize("d", [2, 3, 7])
+def test_directions_uniform_on_sphere(oracle_mod, d):
+    n = 20000
+    v = np.array([oracle_mod.direction(7, w, 0, d) for w in range(n)])
+    assert np.allclose(np.linalg.norm(v, axis=1), 1.0, atol=1e-14)
+    assert np.all(np.abs(v.mean(axis=0)) < 5 / math.sqrt(n))
+    cov = v.T @ v / n
+    assert np.all(np.abs(cov - np.eye(d) / d) < 6 * math.sqrt(2.0 / n) / d + 1e-3)
+
+
+def test_counter_layout_distinguishes_walk_step_block(oracle_mod):
+    base = oracle_mod.normals(1, 5, 2, 8)
+    assert not np.allclose(base, oracle_mod.normals(1, 6, 2, 8))
+    assert not np.allclose(base, oracle_mod.normals(1, 5, 3, 8))
+    assert not np.allclose(base, oracle_mod.normals(2, 5, 2, 8))
+    # walk index high word is part of the counter
+    assert not np.allclose(oracle_mod.normals(1, 5, 2, 4), oracle_mod.normals(1, 5 + (1 << 32), 2, 4))
+    # blocks: normals 4..7 come from block 1, not a repeat of block 0
+    assert not np.allclose(base[:4], base[4:])
+
+
+# --------------------------------------------------------------------------- normaliser
+@pytest.mark.parametrize("nu", [0.0, 0.5, 1.0, 1.5, 2.0, 2.5, 3.5, 5.0, 6.0])
+def test_log_C_matches_scipy(oracle_mod, nu):
+    for z in np.concatenate([np.logspace(-4, 1.9, 60), [0.0]]):
+        got = oracle_mod.log_C(nu, z)
+        if z == 0.0:
+            assert got == 0.0
+            continue
+        want = log_C_scipy(nu, z)
+        assert abs(got - want) <= 1e-13 * max(1.0, abs(want)), (nu, z, got, want)
+
+
+def test_log_C_odd_dimension_closed_forms(oracle_mod):
+    for z in [1e-3, 0.1, 0.7, 1.0, 3.3, 9.0, 25.0]:
+        # d = 3 (nu = 1/2): C = z / sinh z
+        assert abs(oracle_mod.log_C(0.5, z) - math.log(z / math.sinh(z))) < 1e-13 * max(1, z)
+        # d = 5 (nu = 3/2): C = z^3 / (3 (z cosh z - sinh z)); series for tiny z avoids cancellation
+        if z > 0.05:
+            c5 = z ** 3 / (3.0 * (z * math.cosh(z) - math.sinh(z)))
+            assert abs(oracle_mod.log_C(1.5, z) - math.log(c5)) < 1e-12 * max(1, z)
+
+
+def test_dsigma_log_C(oracle_mod):
+    for nu in [0.0, 0.5, 2.0, 4.0]:
+        d = 2 * nu + 2
+        for R, sigma in [(0.3, 4.0), (1.0, 25.0), (0.05, 0.5), (2.0, 10.0)]:
+            z = R * math.sqrt(sigma)
+            # d/dsigma log C = -(R / (2 sqrt(sigma))) I_{nu+1}(z) / I_nu(z)
+            want = -(R / (2 * math.sqrt(sigma))) * special.ive(nu + 1, z) / special.ive(nu, z)
+            got = oracle_mod.dsigma_log_C(nu, R, sigma)
+            assert abs(got - want) < 1e-12 * abs(want)
+        # sigma -> 0 limit: -R^2 / (2d)
+        assert abs(oracle_mod.dsigma_log_C(nu, 0.7, 0.0) + 0.49 / (2 * d)) < 1e-15
+
+
+# --------------------------------------------------------------------------- distance
+def test_distance_invariants(oracle_mod):
+    w = synth.c1()
+    dom = w["domain"]
+    rng = np.random.default_rng(0)
+    for x in rng.uniform(0, 1, size=(200, 2)):
+        R, kind, idx, xbar = oracle_mod.distance(dom, x)
+        if R <= 0:
+            continue  # not in the open domain (inside a disc)
+        # closest point is at distance |R| and lies on the boundary
+        assert abs(np.linalg.norm(x - xbar) - abs(R)) < 1e-12
+        R2, _, _, _ = oracle_mod.distance(dom, xbar)
+        assert abs(R2) < 1e-12
+        # no boundary point of any component is closer: sample each component densely
+        for c, r in zip(dom["ball_c"], dom["ball_r"]):
+            t = np.linspace(0, 2 * math.pi, 721)
+            ring = c[None, :] + r * np.stack([np.cos(t), np.sin(t)], 1)
+            assert np.min(np.linalg.norm(ring - x[None, :], axis=1)) >= R - 1e-12
+        for j in range(2):
+            assert x[j] - 0.0 >= R - 1e-15 and 1.0 - x[j] >= R - 1e-15
+
+
+# --------------------------------------------------------------------------- P1, P2
+@pytest.mark.parametrize("d", [2, 3, 4, 7, 12, 14])
+def test_ball_centre_is_deterministic(oracle_mod, d):
+    R, sigma = 1.3, 9.0
+    dom = synth.ball_domain(d, R)
+    res = oracle_mod.solve(dom, np.zeros((1, d)), 64, 1e-6, sigma, seed=11, grad=True, per_walk=True)
+    nu = d / 2 - 1
+    z = R * math.sqrt(sigma)
+    C = math.exp(log_C_scipy(nu, z))
+    assert np.all(res["walk_jumps"] == 1)
+    assert np.max(np.abs(res["walk_term"] - C)) < 1e-13 * C
+    # |grad^| per walk = (d/R) C_{nu+1}(z): pins the first-sphere factor alpha
+    gn = np.linalg.norm(res["walk_grad"][0], axis=1)
+    alpha = (d / R) * math.exp(log_C_scipy(nu + 1, z))
+    assert np.max(np.abs(gn - alpha)) < 1e-12 * alpha
+    # d/dsigma of C at the centre, against a central difference of the scipy closed form
+    h = 1e-5
+    dC = (math.exp(log_C_scipy(nu, R * math.sqrt(sigma + h))) -
+          math.exp(log_C_scipy(nu, R * math.sqrt(sigma - h)))) / (2 * h)
+    assert np.max(np.abs(res["walk_dsigma"] - dC)) < 1e-7 * abs(dC)
+
+
+def ball_solution(d, R, sigma, x):
+    """u = rho(|x|)/rho(R), rho(r) = r^-nu I_nu(k r); grad u = k r^-nu I_{nu+1}(k r)/rho(R) x/r."""
+    if sigma == 0.0:
+        return 1.0, np.zeros(d)  # g = 1 is harmonic: u = 1
+    nu = d / 2 - 1
+    k = math.sqrt(sigma)
+    r = np.linalg.norm(x)
+    rho = lambda s: s ** (-nu) * special.iv(nu, k * s)
+    u = rho(r) / rho(R)
+    du = k * r ** (-nu) * special.iv(nu + 1, k * r) / rho(R)
+    return u, du * x / r
+
+
+def _ball_case(oracle_mod, d, sigma, laplace_factor=False, n=40000):
+    R = 1.0
+    dom = synth.ball_domain(d, R)
+    rng = np.random.default_rng(d)
+    X = []
+    for rad in [0.25, 0.5, 0.7]:
+        v = rng.standard_normal(d)
+        X.append(rad * v / np.linalg.norm(v))
+    X = np.array(X)
+    res = oracle_mod.solve(dom, X, n, 1e-6, sigma, seed=99 + d, grad=True,
+                           laplace_factor=laplace_factor)
+    ok_u, ok_g = True, True
+    for q in range(len(X)):
+        u, g = ball_solution(d, R, sigma, X[q])
+        ok_u &= abs(res["u"][q] - u) < 4.5 * res["u_se"][q] + 1e-5
+        ok_g &= bool(np.all(np.abs(res["grad"][q] - g) < 4.5 * res["grad_se"][q] + 1e-4))
+    return ok_u, ok_g
+
+
+@pytest.mark.parametrize("d,sigma", [(2, 4.0), (3, 16.0), (6, 9.0), (3, 0.0)])
+def test_ball_off_centre(oracle_mod, d, sigma):
+    ok_u, ok_g = _ball_case(oracle_mod, d, sigma)
+    assert ok_u and ok_g
+
+
+def test_planted_laplace_factor_is_rejected(oracle_mod):
+    # The paper's printed factor n/R is the Laplace one; at sigma > 0 it overestimates |grad u|.
+    ok_u, ok_g = _ball_case(oracle_mod, 3, 16.0, laplace_factor=True)
+    assert ok_u and not ok_g
+
+
+# --------------------------------------------------------------------------- P3
+def test_exp_data_exact_solution_c1(oracle_mod):
+    w = synth.c1(n_queries=16)
+    dom = w["domain"]
+    res = oracle_mod.solve(dom, w["X"], 20000, 1e-4, w["sigma"], w["seed"], grad=True)
+    a = dom["exp_a"][0]
+    g = np.exp(w["X"] @ a)
+    bias = 3e-4 * np.abs(g) * np.linalg.norm(a)  # O(eps) shell bias
+    assert np.all(np.abs(res["u"] - g) < 4.5 * res["u_se"] + bias)
+    gg = a[None, :] * g[:, None]
+    assert np.all(np.abs(res["grad"] - gg) < 4.5 * res["grad_se"] + 10 * bias[:, None])
+    assert np.all(res["capped"] == 0)
+
+
+def test_du_dw_is_exp_and_fd_exact(oracle_mod):
+    w = synth.c5(n_queries=4, n_walks=2000, n_balls=8, n_terms=3)
+    dom = w["domain"]
+    base = oracle_mod.solve(dom, w["X"], w["n_walks"], w["eps"], w["sigma"], w["seed"])
+    h = 1e-3
+    for k in range(3):
+        dp = dict(dom)
+        dm = dict(dom)
+        dp["exp_w"] = dom["exp_w"].copy()
+        dm["exp_w"] = dom["exp_w"].copy()
+        dp["exp_w"][k] += h
+        dm["exp_w"][k] -= h
+        up = oracle_mod.solve(dp, w["X"], w["n_walks"], w["eps"], w["sigma"], w["seed"])["u"]
+        um = oracle_mod.solve(dm, w["X"], w["n_walks"], w["eps"], w["sigma"], w["seed"])["u"]
+        fd = (up - um) / (2 * h)
+        assert np.allclose(fd, base["du_dw"][:, k], rtol=1e-9, atol=1e-12)
+        # and du/dw_k estimates exp(a_k . x) (the exact solution's derivative)
+        e = np.exp(w["X"] @ dom["exp_a"][k])
+        assert np.all(np.abs(base["du_dw"][:, k] - e) < 0.1 * e)
+
+
+def test_dsigma_crn_finite_difference(oracle_mod):
+    w = synth.c5(n_queries=4, n_walks=2000, n_balls=8, n_terms=2)
+    dom = w["domain"]
+    s, h = w["sigma"], 1e-3
+    base = oracle_mod.solve(dom, w["X"], w["n_walks"], w["eps"], s, w["seed"])
+    up = oracle_mod.solve(dom, w["X"], w["n_walks"], w["eps"], s + h, w["seed"])["u"]
+    um = oracle_mod.solve(dom, w["X"], w["n_walks"], w["eps"], s - h, w["seed"])["u"]
+    fd = (up - um) / (2 * h)
+    assert np.allclose(fd, base["du_dsigma"], rtol=1e-5, atol=1e-9)
+    assert np.all(base["du_dsigma"] < 0)  # more screening, smaller u for positive data
+
+
+# --------------------------------------------------------------------------- annulus
+def annulus_solution(d, r1, r2, sigma, x):
+    r = np.linalg.norm(x)
+    if sigma == 0.0:
+        if d == 2:
+            u = math.log(r2 / r) / math.log(r2 / r1)
+            du = -1.0 / (r * math.log(r2 / r1))
+        else:
+            p = 2 - d
+            u = (r ** p - r2 ** p) / (r1 ** p - r2 ** p)
+            du = p * r ** (p - 1) / (r1 ** p - r2 ** p)
+    else:
+        nu, k = d / 2 - 1, math.sqrt(sigma)
+        f = lambda s: s ** (-nu) * (special.iv(nu, k * s) * special.kv(nu, k * r2) -
+                                    special.kv(nu, k * s) * special.iv(nu, k * r2))
+        fp = lambda s: k * s ** (-nu) * (special.iv(nu + 1, k * s) * special.kv(nu, k * r2) +
+                                         special.kv(nu + 1, k * s) * special.iv(nu, k * r2))
+        u = f(r) / f(r1)
+        du = fp(r) / f(r1)
+    return u, du * x / r
+
+
+@pytest.mark.parametrize("d,sigma", [(2, 0.0), (2, 4.0), (3, 0.0), (3, 9.0), (5, 2.0)])
+def test_annulus_goal_indicator(oracle_mod, d, sigma):
+    r1, r2 = 0.3, 1.0
+    dom = synth.annulus_domain(d, r1, r2)
+    rng = np.random.default_rng(5)
+    X = []
+    for rad in [0.4, 0.6, 0.85]:
+        v = rng.standard_normal(d)
+        X.append(rad * v / np.linalg.norm(v))
+    X = np.array(X)
+    eps = 1e-5
+    res = oracle_mod.solve(dom, X, 40000, eps, sigma, seed=3 + d, grad=True, per_walk=True)
+    assert np.all((res["walk_term"] >= 0) & (res["walk_term"] <= 1))  # max principle, P6
+    for q in range(len(X)):
+        u, g = annulus_solution(d, r1, r2, sigma, X[q])
+        assert abs(res["u"][q] - u) < 4.5 * res["u_se"][q] + 1e-4
+        assert np.all(np.abs(res["grad"][q] - g) < 4.5 * res["grad_se"][q] + 1e-3)
+
+
+# --------------------------------------------------------------------------- statistics
+def test_standard_error_scaling(oracle_mod):
+    w = synth.c1(n_queries=6)
+    dom, X = w["domain"], w["X"]
+    s1 = oracle_mod.solve(dom, X, 4000, w["eps"], w["sigma"], 1)["u_se"]
+    s4 = oracle_mod.solve(dom, X, 16000, w["eps"], w["sigma"], 1)["u_se"]
+    ratio = s1 / s4
+    assert np.all((ratio > 1.8) & (ratio < 2.2)), ratio
+    # spread of independent estimates matches the reported standard error
+    us = np.array([oracle_mod.solve(dom, X[:2], 1000, w["eps"], w["sigma"], seed)["u"]
+                   for seed in range(24)])
+    se = oracle_mod.solve(dom, X[:2], 1000, w["eps"], w["sigma"], 100)["u_se"]
+    emp = us.std(axis=0, ddof=1)
+    assert np.all((emp / se > 0.6) & (emp / se < 1.5))
+
+
+def test_max_principle_indicator_c2(oracle_mod):
+    w = synth.c2()
+    X = synth._free_points(np.random.default_rng(1), 8, w["domain"]["box_lo"], w["domain"]["box_hi"],
+                           w["domain"]["ball_c"], w["domain"]["ball_r"], 0.05)
+    res = oracle_mod.solve(w["domain"], X, 500, w["eps"], w["sigma"], w["seed"], per_walk=True)
+    t = res["walk_term"]
+    assert np.all((t >= 0) & (t <= 1))
+    assert np.all((res["u"] >= 0) & (res["u"] <= 1))
+
+
+def test_thread_count_does_not_change_results(oracle_mod):
+    w = synth.c1(n_queries=5)
+    a = oracle_mod.solve(w["domain"], w["X"], 3000, w["eps"], w["sigma"], 5, grad=True, threads=1)
+    b = oracle_mod.solve(w["domain"], w["X"], 3000, w["eps"], w["sigma"], 5, grad=True, threads=7)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_cap_and_outside(oracle_mod):
+    w = synth.c1(n_queries=3)
+    res = oracle_mod.solve(w["domain"], w["X"], 500, 1e-9, w["sigma"], 1, max_steps=2, per_walk=True)
+    # exp data is positive, so a zero terminal marks a capped walk; caps happen only at 2 jumps
+    capped = res["walk_term"] == 0.0
+    assert res["capped"].sum() == capped.sum() > 0
+    assert np.all(res["walk_jumps"][capped] == 2)
+    assert np.all(res["walk_steps"] == res["walk_jumps"].sum(axis=1) + 500)
+    inside_disc = w["domain"]["ball_c"][:1]
+    out = oracle_mod.solve(w["domain"], inside_disc, 10, 1e-3, 4.0, 1)
+    assert out["outside"][0] == 10 and np.isnan(out["u"][0])
+
+
+# --------------------------------------------------------------------------- planner
+def test_planner_annulus_descends_radially(oracle_mod):
+    d = 2
+    dom = synth.annulus_domain(d, 0.2, 2.0)
+    x0 = np.array([1.2, 0.3])
+    s_ub = 0.1
+    path, flags, grads = oracle_mod.plan_path(dom, x0, 60, 4000, 1e-4, 1.0, s_ub, seed=8)
+    assert flags[len(path) - 1] == 1  # reached the goal
+    r = np.linalg.norm(path, axis=1)
+    for i in range(len(path) - 1):
+        R = min(r[i] - 0.2, 2.0 - r[i])
+        s = min(s_ub, 0.5 * R)
+        assert abs(np.linalg.norm(path[i + 1] - path[i]) - s) < 1e-12
+        if R > 0.05:
+            # far from the goal the estimate is accurate: the step points at the centre.
+            # (Close to the boundary the first-sphere estimator's variance grows like 1/R0^2.)
+            radial = -path[i] / r[i]
+            assert (path[i + 1] - path[i]) @ radial / s > math.cos(math.radians(25))
+            assert r[i + 1] < r[i]
