@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Benchmark of the batched Walk-on-Spheres hot path on one GB300 (or N replicas).
+
+Workload (one "step"): the batched uneven configuration -- 256 independent problems with
+d in {3..12}, 16-4096 ball obstacles (radii log-uniform 0.01-0.2) in [-1,1]^d, sigma in [0,50],
+256-16384 walks per query and 64 queries per problem; u and grad u at every query; one
+persistent launch replayed from a CUDA graph with autotuned launch shape; FP32 walkers, FP64
+per-query sums. Inputs are resident in HBM before timing; L2 (129 MB) is flushed between steps.
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on a bounded sample
+of the same workload instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("WoS walk-steps/s and ∇u queries/s at stated RMSE vs FP64 oracle; "
+          "mixed vs plain FP32")
+WORKLOAD = ("batched uneven: 256 problems, d U{3..12}, 16-4096 balls (r log-U[0.01,0.2]) in [-1,1]^d, "
+            "sigma U[0,50], 256-16384 walks/query, 64 queries/problem, eps 1e-3, u + grad u")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-secondary", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0,
+                   help="target CPU-baseline sample time (0 skips it: profiling runs only)")
+    p.add_argument("--problems", type=int, default=256,
+                   help="leading problems of the workload (fewer: the small profiling case)")
+    p.add_argument("--scale-walks", type=float, default=1.0,
+                   help="scale of the walk counts (below 1: the small profiling case)")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def alg_flops_per_step(d, n_balls):
+    """Algorithmic FP32 flops of one walk step (one distance evaluation): the ball screen
+    costs 2d+3 flops per ball (d FMAs of x.m, the b-term FMA and the threshold add), the
+    box faces and sampling about 4d."""
+    return n_balls * (2 * d + 3) + 4 * d
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [t.strip() for t in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        power = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [s for s, p in zip(sm, power) if p is not None and power and p > 0.3 * max(power)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------------------ oracle sample
+def oracle_sample(problems, seed, target_seconds):
+    """The FP64 oracle on a bounded sample of the batched workload: the first `nq` queries of
+    each problem (problems in a seeded shuffled order), min(N, 64) gradient walks per query,
+    until about target_seconds. The oracle threads over queries, so nq = host cores keeps every
+    core busy. Returns (walk_steps, seconds, threads used, description)."""
+    import oracle
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    nq = min(threads, 64)
+    order = np.random.default_rng(7).permutation(len(problems))
+    steps = 0
+    used = 0
+    t0 = time.perf_counter()
+    for i in order:
+        p = problems[i]
+        n = min(p["n_walks"], 64)
+        r = oracle.solve(p["domain"], p["X"][:nq], n, p["eps"], p["sigma"], seed, grad=True, threads=threads)
+        steps += int(r["walk_steps"].sum())
+        used += 1
+        if time.perf_counter() - t0 > target_seconds:
+            break
+    dt = time.perf_counter() - t0
+    desc = ("FP64 oracle (plain C, pthreads over queries), %d queries x min(N,64) gradient walks of each of %d "
+            "of the 256 problems (seeded order)" % (nq, used))
+    return steps, dt, min(threads, nq), desc
+
+
+def run_reference(args, rank, world):
+    from paper_2406_01713_gb300 import synth
+
+    if rank != 0:
+        return
+    w = synth.c4()
+    per_step = max(2.0, args.cpu_seconds / 3.0)
+    for _ in range(args.warmup):
+        oracle_sample(w["problems"], w["seed"], per_step / 4)
+    tot_steps, tot_t, threads, desc = 0, 0.0, 1, ""
+    for _ in range(args.steps):
+        s, t, threads, desc = oracle_sample(w["problems"], w["seed"], per_step)
+        tot_steps += s
+        tot_t += t
+    v = tot_steps / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "walk-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": v, "unit": "walk-steps/s", "cores": threads, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": v, "unit": "walk-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ ours
+def log(*a):
+    print("[bench %.1fs]" % (time.perf_counter() - T0), *a, file=sys.stderr, flush=True)
+
+
+T0 = time.perf_counter()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+
+    import paper_2406_01713_gb300 as pkg
+    from paper_2406_01713_gb300 import synth
+    from paper_2406_01713_gb300 import wos as W
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    pkg.build()
+    dev = torch.cuda.current_device()
+    props = torch.cuda.get_device_properties(dev)
+    w = synth.c4(n_problems=args.problems, scale_walks=args.scale_walks)
+    probs = w["problems"]
+    doms = [W.Domain(p["domain"]) for p in probs]
+    workload = WORKLOAD if (args.problems == 256 and args.scale_walks == 1.0) else (
+        "SMALL CASE (profiling): first %d problems of [%s], walks x %g" % (args.problems, WORKLOAD, args.scale_walks))
+    batch = W.Batch([{"domain": d, "x": p["X"], "n_walks": p["n_walks"], "eps": p["eps"], "sigma": p["sigma"],
+                      "grad": True} for d, p in zip(doms, probs)], seed=w["seed"] + 1000003 * rank)
+    cache = os.environ.get("WOS_AUTOTUNE_CACHE",
+                           os.path.join(ROOT, "paper_2406_01713_gb300", "csrc", "_build", "autotune_cache.txt"))
+    log("workload ready: %d problems" % len(probs))
+    tuned = batch.autotune(cache) if not args.no_autotune else batch.config()
+    log("launch shape", tuned)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        batch.run()
+    torch.cuda.synchronize()
+    # per-problem algorithmic flops per launch (walk steps are deterministic for a seed)
+    steps_pq = [int(o["walk_steps"].sum()) for o in batch.out]
+    total_steps = int(W.stats_dict(batch.stats)["walk_steps"])
+    assert total_steps == sum(steps_pq)
+    flops = sum(s * alg_flops_per_step(p["domain"]["d"], p["domain"]["ball_r"].size) for s, p in zip(steps_pq, probs))
+    total_q = sum(p["X"].shape[0] for p in probs)
+
+    sampler = ClockSampler(dev)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()  # L2 flush between steps (512 MB > 129 MB L2)
+        ev[i][0].record(stream)
+        batch.run()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    log("timed steps (ms)", [round(x, 2) for x in step_ms])
+    dev_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dev_s = float(t[0])
+    value = total_steps * args.steps * world / dev_s
+    ms_per_step = 1e3 * dev_s / args.steps
+
+    # accuracy: exact solution u = exp(a.x), grad u = a u on the exponential-data problems
+    rel_u, rel_g = [], []
+    for i, (p, o) in enumerate(zip(probs, batch.out)):
+        if "exp_a" in p["domain"]:
+            a = p["domain"]["exp_a"][0]
+            us = np.exp(p["X"] @ a)
+            u = o["u"].cpu().numpy()
+            g = o["grad"].cpu().numpy()
+            rel_u.append((u - us) / us)
+            rel_g.append(np.linalg.norm(g - a[None, :] * us[:, None], axis=1) / (np.linalg.norm(a) * us + 1e-300))
+    rmse_u = float(np.sqrt(np.mean(np.concatenate(rel_u) ** 2))) if rel_u else None
+    rmse_g = float(np.sqrt(np.mean(np.concatenate(rel_g) ** 2))) if rel_g else None
+
+    # end to end through the public API: pinned host queries in, u and grad u out, each step
+    x_host = batch.x_buf.cpu().pin_memory()
+    u_host = torch.empty(batch.u_buf.numel(), dtype=torch.float64).pin_memory()
+    g_host = torch.empty(batch.grad_buf.numel(), dtype=torch.float64).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        batch.x_buf.copy_(x_host, non_blocking=True)
+        batch.run()
+        u_host.copy_(batch.u_buf, non_blocking=True)
+        g_host.copy_(batch.grad_buf, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    e2e = {"value": total_steps * args.steps * world / e2e_s, "unit": "walk-steps/s",
+           "h2d_bytes_per_step": int(x_host.numel() * 8),
+           "d2h_bytes_per_step": int((u_host.numel() + g_host.numel()) * 8)}
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    peak_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (ms_per_step / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "kernel": "walk_mixed_kernel<true> (persistent batched walker)",
+                "peak_note": "FP32 FMA pipe: %d SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % (
+                    props.multi_processor_count, sm_max),
+                "flops_per_launch": flops}
+
+    line = {"metric": METRIC, "value": value, "unit": "walk-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload, "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "l2": "flushed between steps (512 MB write)", "launch": tuned,
+                       "walk_steps_per_step": total_steps, "queries_per_step": total_q},
+            "queries_per_s": total_q * args.steps * world / dev_s,
+            "grad_evals_per_s": total_q * args.steps * world / dev_s,
+            "rmse": {"u_rel": rmse_u, "grad_rel": rmse_g,
+                     "against": "exact solution exp(a.x) on the 128 exponential-data problems"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clocks,
+            "wall_s": wall}
+
+    log("e2e done")
+    if rank == 0 and not args.no_secondary:
+        line["vs_plain_fp32"] = plain_comparison(W, doms, probs, w["seed"], total_steps, dev_s / args.steps,
+                                                 rmse_u)
+        line["secondary"] = secondary(W, synth)
+    if rank == 0:
+        if args.cpu_seconds > 0:
+            steps_cpu, t_cpu, cores, desc = oracle_sample(probs, w["seed"], args.cpu_seconds)
+            line["cpu_baseline"] = {"value": steps_cpu / t_cpu, "unit": "walk-steps/s", "cores": cores,
+                                    "kind": "oracle", "sample": desc}
+        else:
+            line["cpu_baseline"] = None
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def plain_comparison(W, doms, probs, seed, mixed_steps, mixed_s, mixed_rmse):
+    """The plain FP32 walker (one thread per walk, global-memory obstacles, FP32 Bessel series,
+    FP32 sums) on the same 256 problems, same seeds and walk counts (equal N: both estimators
+    are unbiased, so their RMSE agree up to noise, which is reported)."""
+    import torch
+
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    outs = []
+    e0.record()
+    base = 0
+    steps = torch.zeros(6, dtype=torch.int64, device="cuda")
+    total = 0
+    for d, p in zip(doms, probs):
+        r = d.grad(p["X"], p["n_walks"], p["eps"], p["sigma"], precision="fp32", seed=seed, walk_offset=base,
+                   with_stats=True)
+        base += p["X"].shape[0] * p["n_walks"]
+        outs.append((r["u"], r["stats"]))
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    total = sum(int(s[1]) for _, s in outs)
+    rel = []
+    for (u, _), p in zip(outs, probs):
+        if "exp_a" in p["domain"]:
+            us = np.exp(p["X"] @ p["domain"]["exp_a"][0])
+            rel.append((u.cpu().numpy() - us) / us)
+    rmse = float(np.sqrt(np.mean(np.concatenate(rel) ** 2)))
+    plain_rate = total / t
+    mixed_rate = mixed_steps / mixed_s
+    return {"plain_walk_steps_per_s": plain_rate, "mixed_walk_steps_per_s": mixed_rate,
+            "speedup": mixed_rate / plain_rate, "plain_rmse_u_rel": rmse, "mixed_rmse_u_rel": mixed_rmse,
+            "note": "same walk counts; plain launched per problem (256 launches)"}
+
+
+def secondary(W, synth):
+    """Quick measurements of the other workloads (not the headline)."""
+    import torch
+
+    out = {}
+    # 2D planning field: 200-step graph-replayed path, 1024 walks per grad u
+    w = synth.c2()
+    dom = W.Domain(w["domain"])
+    dom.plan_path(w["start"], 5, w["n_walks"], w["eps"], w["sigma"], w["s_ub"], seed=w["seed"])
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    path, flags, _ = dom.plan_path(w["start"], w["n_steps"], w["n_walks"], w["eps"], w["sigma"], w["s_ub"],
+                                   seed=w["seed"])
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    f = flags.cpu().numpy()
+    out["planning_2d"] = {"path_ms": 1e3 * dt, "ms_per_planner_step": 1e3 * dt / w["n_steps"],
+                          "reached_goal_at_step": int(np.argmax(f == 1)) if (f == 1).any() else None}
+    # differentiable d=6: forward + backward, 4096 queries x 2048 walks
+    w = synth.c5()
+    dom = W.Domain(w["domain"])
+    X = torch.tensor(w["X"], dtype=torch.float64, device="cuda", requires_grad=True)
+    wt = torch.tensor(w["domain"]["exp_w"], dtype=torch.float64, device="cuda", requires_grad=True)
+    sig = torch.tensor(w["sigma"], dtype=torch.float64, requires_grad=True)
+    u = W.WoSFunction.apply(X, sig, wt, dom, w["n_walks"], w["eps"], w["seed"])
+    u.sum().backward()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    r = dom.grad(X.detach(), w["n_walks"], w["eps"], w["sigma"], seed=w["seed"], with_stats=True)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    u = W.WoSFunction.apply(X, sig, wt, dom, w["n_walks"], w["eps"], w["seed"])
+    u.sum().backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    out["differentiable_6d"] = {"forward_ms": 1e3 * (t1 - t), "forward_backward_ms": 1e3 * (t2 - t1),
+                                "walk_steps_per_s": int(r["stats"][1]) / (t1 - t)}
+    # plain FP64 d=2 check workload
+    w = synth.c1()
+    dom = W.Domain(w["domain"])
+    for prec in ["fp64", "mixed"]:
+        dom.grad(w["X"], w["n_walks"], w["eps"], w["sigma"], precision=prec, seed=w["seed"])
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = dom.grad(w["X"], w["n_walks"], w["eps"], w["sigma"], precision=prec, seed=w["seed"], with_stats=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        out["fp64_check_2d_" + prec] = {"ms": 1e3 * dt, "walk_steps_per_s": int(r["stats"][1]) / dt}
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,280 @@
+/*
+ * wos.h -- C ABI of the GB300 Walk-on-Spheres library (libwos.so).
+ *
+ * Walk on Spheres (WoS) estimates, at batches of query points x in a d-dimensional
+ * configuration space, the solution u of the screened Poisson problem
+ *
+ *     Laplace(u) = sigma u   in Omega,        u = g   on the boundary of Omega
+ *
+ * (Sec. III, Eq. screened_poisson_wos, with the paper's c written sigma and f = 0) and its
+ * spatial gradient grad u, which the gradient-following planner consumes at every step
+ * (Sec. III, screened-harmonic paths; Sec. VII adaptive step).
+ *
+ * Estimators (Sec. IV-A):
+ *   one walk:   u^(x_k) = g(xbar_k) once x_k is closer than eps to the boundary (xbar_k is the
+ *               closest boundary point, Fig. 2), else C(R_k) u^(x_{k+1}) with x_{k+1} uniform on
+ *               the largest empty sphere of radius R_k around x_k;
+ *   normaliser: C(R) = (z/2)^nu / (Gamma(nu+1) I_nu(z)),  z = R sqrt(sigma),  nu = d/2 - 1;
+ *   gradient:   grad^ = alpha(R_0) u^(x_1) v_0 with v_0 the first direction. The paper prints
+ *               the Laplace factor d/R_0; for sigma > 0 the unbiased factor is
+ *               alpha(R_0) = (d/R_0) C_{nu+1}(z_0), which this library uses unless
+ *               WOS_FLAG_LAPLACE_FACTOR is set.
+ * The walk geometry does not depend on sigma, so d u^/d sigma = u^ sum_k d log C(R_k)/d sigma
+ * per walk is exact; for g = sum_k w_k exp(a_k . x), d u^/d w_k = prod C * exp(a_k . xbar).
+ *
+ * Conventions for every call:
+ *   - Pointers named "device" are device pointers owned by the caller; "host" pointers are read
+ *     during the call only. The library owns only what wos_domain_create / wos_batch_create
+ *     allocate, and frees it in the matching destroy call.
+ *   - Every call that takes a stream is asynchronous on that stream (a cudaStream_t passed as
+ *     void*; NULL is the legacy default stream). Outputs are valid when the stream reaches the
+ *     point of the call.
+ *   - Every call returns a wos_status; the library never aborts or exits. wos_last_error()
+ *     gives a thread-local one-line detail of the last failure.
+ *   - A query point with no positive distance to the boundary (not in the open domain) gets
+ *     NaN outputs and is counted in wos_stats.outside; the other queries still complete, and
+ *     the call returns WOS_OK.
+ *   - Random directions: Philox4x32-10 (Salmon et al., SC'11) with key = seed and counter =
+ *     (walk_lo, walk_hi, step, block). Walk w of query q has the global index
+ *     walk_offset + q * n_walks + w, so results are a pure function of (seed, index, step).
+ */
+#ifndef WOS_H
+#define WOS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WOS_OK = 0,
+    WOS_ERR_INVALID_ARG = 1,   /* a size, pointer or value is out of range; nothing was launched */
+    WOS_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement (e.g. d > 12) */
+    WOS_ERR_OOM = 3,           /* a device or host allocation failed */
+    WOS_ERR_CUDA = 4,          /* a CUDA runtime call failed; see wos_last_error() */
+    WOS_ERR_TIMEOUT = 5,       /* a device-side iteration budget ran out (status word set) */
+    WOS_ERR_OUTSIDE_DOMAIN = 6 /* reserved for callers that treat outside queries as errors */
+} wos_status;
+
+typedef enum {
+    WOS_FP64 = 0,       /* FP64 walkers, direct FP64 log-Bessel series per step (parity mode) */
+    WOS_FP32_PLAIN = 1, /* one thread per walk, FP32 direct Bessel series, FP32 per-query sums */
+    WOS_MIXED = 2       /* FP32 persistent walkers, FP64-built weight tables, FP64 per-query sums */
+} wos_precision;
+
+#define WOS_FLAG_LAPLACE_FACTOR 1 /* use the paper's printed gradient factor d/R0 */
+
+#define WOS_MAX_D 12    /* dimensions 2..12 are supported */
+#define WOS_MAX_EXP 8   /* at most 8 exponential boundary-data terms */
+
+typedef struct wos_domain_s *wos_domain_t;
+typedef struct wos_batch_s *wos_batch_t;
+
+/*
+ * Domain description (all host pointers, FP64, read during wos_domain_create only).
+ * Omega = {inside the box, if any} and {inside the outer ball, if any}, minus the closed ball
+ * obstacles, minus the goal ball, minus the point set. At least one of box / outer ball is
+ * required so that every walk can terminate.
+ * Distance to the boundary (Sec. VI, Eq. for d(x, dOmega); Sec. VII-A point-set distance):
+ *   balls |x - c| - r, goal |x - c_g| - r_g, outer r_o - |x - c_o|, points |x - p|,
+ *   box faces x_j - lo_j and hi_j - x_j; the minimum over all components.
+ * Boundary data g: if n_exp > 0, g(x) = sum_k exp_w[k] exp(exp_a[k] . x) on the whole boundary;
+ * otherwise g = 1 on the goal sphere and 0 on every other component (the planning field).
+ */
+typedef struct {
+    int32_t d;                  /* dimension, 2..WOS_MAX_D */
+    const double *box_lo;       /* d values, or NULL for no box */
+    const double *box_hi;       /* d values, or NULL */
+    const double *outer_c;      /* d values, or NULL for no outer ball */
+    double outer_r;             /* > 0 when outer_c is given */
+    const double *goal_c;       /* d values, or NULL for no goal */
+    double goal_r;              /* > 0 when goal_c is given */
+    int32_t n_balls;            /* >= 0 ball obstacles */
+    const double *ball_c;       /* n_balls x d, row major */
+    const double *ball_r;       /* n_balls radii, > 0 */
+    int64_t n_points;           /* >= 0 obstacle points (point-cloud C-space, Sec. VII-A) */
+    const double *points;       /* n_points x d, row major */
+    int32_t n_exp;              /* 0..WOS_MAX_EXP exponential data terms */
+    const double *exp_w;        /* n_exp weights */
+    const double *exp_a;        /* n_exp x d exponents */
+} wos_domain_desc;
+
+/* Per-call options. A NULL options pointer means {WOS_MIXED, 0, seed 0, offset 0, 10000}. */
+typedef struct {
+    int32_t precision;   /* wos_precision */
+    int32_t flags;       /* WOS_FLAG_* */
+    uint64_t seed;       /* Philox key */
+    int64_t walk_offset; /* first global walk index of this call */
+    int64_t max_steps;   /* jumps per walk before it is capped (contributes 0); <= 0: 10000 */
+} wos_options;
+
+/* Counters of one call, written to DEVICE memory when the stream completes (int64, exact). */
+typedef struct {
+    int64_t walks;           /* walks run (= Q * n_walks) */
+    int64_t walk_steps;      /* distance evaluations (a walk with k jumps counts k + 1) */
+    int64_t capped;          /* walks that hit max_steps */
+    int64_t outside;         /* walks whose query was not in the open domain */
+    int64_t shrinks;         /* point-cloud steps whose radius was set by the error bound */
+    int64_t refine_overflow; /* point-cloud steps whose candidate list overflowed (bound used) */
+} wos_stats;
+
+/* ---- domain ------------------------------------------------------------------------- */
+
+/* Copies the description to the device (FP64 and FP32 copies; BF16 split copies of the point
+ * set). Synchronous. Errors: INVALID_ARG (bad sizes, radii <= 0, no box or outer ball),
+ * UNSUPPORTED (d outside 2..12, n_exp > 8), OOM, CUDA. *out is NULL on failure. */
+wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out);
+
+/* Frees everything the domain owns. Synchronises the device first. NULL is accepted. */
+wos_status wos_domain_destroy(wos_domain_t dom);
+
+/* Replaces the boundary-data weights exp_w (n_exp device doubles) on the stream, for the
+ * autograd path where w is a learnable tensor. Errors: INVALID_ARG if n differs from n_exp. */
+wos_status wos_domain_set_exp_w(wos_domain_t dom, const double *w_device, int32_t n, void *stream);
+
+/* ---- estimators (Sec. IV-A) --------------------------------------------------------- */
+
+/*
+ * u at Q query points: x is Q x d device doubles (row major); u and u_se (standard error of the
+ * mean, may be NULL) are Q device doubles. stats: one device wos_stats or NULL.
+ * Errors: INVALID_ARG (NULL x/u with Q > 0, n_walks < 1, eps <= 0, sigma < 0), CUDA, OOM.
+ */
+wos_status wos_solve(wos_domain_t dom, const wos_options *opt, const double *x, int64_t Q,
+                     int64_t n_walks, double eps, double sigma, double *u, double *u_se,
+                     wos_stats *stats, void *stream);
+
+/*
+ * u and grad u at Q query points with gradient walks (the first sphere is always taken).
+ * Device outputs, any of which may be NULL except grad: u, u_se (Q); grad, grad_se (Q x d);
+ * du_dsigma (Q); du_dw (Q x n_exp). Errors as wos_solve.
+ */
+wos_status wos_grad(wos_domain_t dom, const wos_options *opt, const double *x, int64_t Q,
+                    int64_t n_walks, double eps, double sigma, double *u, double *u_se,
+                    double *grad, double *grad_se, double *du_dsigma, double *du_dw,
+                    wos_stats *stats, void *stream);
+
+/*
+ * Per-walk instrumentation for parity checks: runs Q x n_walks walks (value walks if
+ * grad_mode == 0, gradient walks otherwise) and writes, per walk j = q * n_walks + w, the
+ * terminal estimate term[j], the number of jumps jumps[j] (int64), grad[j*d + i] and
+ * dsigma[j] (device; any pointer may be NULL). Errors as wos_solve.
+ */
+wos_status wos_walks(wos_domain_t dom, const wos_options *opt, const double *x, int64_t Q,
+                     int64_t n_walks, double eps, double sigma, int32_t grad_mode, double *term,
+                     int64_t *jumps, double *grad, double *dsigma, void *stream);
+
+/* ---- planner (Sec. III screened-harmonic path; Sec. VII s = min(s_ub, d_bound / 2)) ---- */
+
+/*
+ * One planner step on the device point x (d device doubles, updated in place): if x is within
+ * eps of the goal, flag = 1 and x is kept; otherwise grad u is estimated with n_walks gradient
+ * walks (walk offset opt->walk_offset + step_idx * n_walks) and x <- x + s grad/|grad| with
+ * s = min(s_ub, d_bound(x) / 2); flag = 2 if |grad| = 0 (x kept), 4 if x is outside.
+ * flag: one device int32; grad_out: d device doubles or NULL. Errors as wos_solve.
+ */
+wos_status wos_plan_step(wos_domain_t dom, const wos_options *opt, double *x, int64_t n_walks,
+                         double eps, double sigma, double s_ub, int64_t step_idx, int32_t *flag,
+                         double *grad_out, void *stream);
+
+/*
+ * n_steps planner steps from x0 (d device doubles), recorded and replayed as one CUDA graph.
+ * path: (n_steps + 1) x d device doubles (row 0 = x0; rows after the goal repeat the last
+ * point); flags: n_steps device int32 (as wos_plan_step; 8 marks steps after the goal);
+ * grads: n_steps x d device doubles or NULL. Errors as wos_solve.
+ */
+wos_status wos_plan_path(wos_domain_t dom, const wos_options *opt, const double *x0,
+                         int64_t n_steps, int64_t n_walks, double eps, double sigma, double s_ub,
+                         double *path, int32_t *flags, double *grads, void *stream);
+
+/* ---- backward of u(x; sigma, w) (autograd) --------------------------------------------- */
+
+/*
+ * Given the upstream gradient gout (Q device doubles) and the saved forward estimates grad
+ * (Q x d), du_dsigma (Q, or NULL) and du_dw (Q x K, or NULL): gx[q*d+i] = gout[q] grad[q*d+i];
+ * gsigma[0] = sum_q gout[q] du_dsigma[q]; gw[k] = sum_q gout[q] du_dw[q*K+k]. FP64 sums in a
+ * fixed order (deterministic). All device pointers; gx/gsigma/gw may be NULL.
+ */
+wos_status wos_backward(const double *gout, const double *grad, const double *du_dsigma,
+                        const double *du_dw, int64_t Q, int32_t d, int32_t K, double *gx,
+                        double *gsigma, double *gw, void *stream);
+
+/* ---- batched uneven problems in one persistent launch --------------------------------- */
+
+typedef struct {
+    wos_domain_t domain;
+    const double *x;  /* n_queries x d device doubles */
+    int64_t n_queries;
+    int64_t n_walks;  /* walks per query */
+    double eps;
+    double sigma;
+    double *u;        /* n_queries device doubles */
+    double *u_se;     /* n_queries device doubles or NULL */
+    double *grad;     /* n_queries x d device doubles or NULL (NULL: value walks) */
+    double *grad_se;  /* n_queries x d device doubles or NULL */
+    int64_t *walk_steps; /* n_queries device int64 or NULL: distance evaluations per query */
+} wos_problem;
+
+/* Launch shape of the persistent kernel. A NULL config means "autotuned": the cached best for
+ * this device and problem mix if any, else the built-in default. */
+typedef struct {
+    int32_t threads;         /* threads per CTA: 128..1024, multiple of 32 */
+    int32_t ctas_per_sm;     /* resident CTAs per SM requested (1..8) */
+    int64_t item_work;       /* target work per queue item, in ball-dimension units */
+} wos_batch_config;
+
+/*
+ * Builds a batch: uploads the problem table and the longest-first work queue, sizes the
+ * persistent grid to a multiple of the SM count, and records [reset, persistent walk kernel,
+ * finalize] as one CUDA graph. Problems may differ in d, obstacle count, walk budget, sigma and
+ * eps. Precision is WOS_MIXED. The problems' domains and buffers must outlive the batch.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
+ */
+wos_status wos_batch_create(const wos_problem *probs, int32_t n_problems, const wos_options *opt,
+                            const wos_batch_config *cfg, wos_batch_t *out);
+
+/* Replays the batch graph on the stream; stats (device) may be NULL. */
+wos_status wos_batch_run(wos_batch_t batch, wos_stats *stats, void *stream);
+
+/* Reads back the launch shape in use (host struct). */
+wos_status wos_batch_get_config(wos_batch_t batch, wos_batch_config *cfg);
+
+/* Frees the batch (synchronises the device). NULL is accepted. */
+wos_status wos_batch_destroy(wos_batch_t batch);
+
+/* One-shot convenience: create, run, destroy. */
+wos_status wos_solve_batch(const wos_problem *probs, int32_t n_problems, const wos_options *opt,
+                           wos_stats *stats, void *stream);
+
+/*
+ * Autotuner: times each candidate launch shape on this batch (CUDA events, after a warm-up
+ * run), keeps the fastest in the batch, and appends it to the text cache file cache_path (may
+ * be NULL) keyed by device name and problem-mix signature, so later wos_batch_create calls with
+ * a NULL config reuse it. best (host) may be NULL. Synchronous.
+ */
+wos_status wos_batch_autotune(wos_batch_t batch, const char *cache_path, wos_batch_config *best);
+
+/* Sets the cache file consulted by wos_batch_create when cfg is NULL (NULL: no cache). */
+wos_status wos_set_autotune_cache(const char *cache_path);
+
+/* ---- diagnostics ------------------------------------------------------------------------ */
+
+const char *wos_status_string(wos_status s);
+const char *wos_last_error(void);
+
+/* Writes the library's log C_nu(z) and S_{nu+1}/S_nu tables as seen by the FP32 walkers for
+ * dimension d over z in [0, z_max] (n nodes each, host doubles), for table-accuracy tests. */
+wos_status wos_debug_weight_table(int32_t d, double z_max, int32_t n, double *log_c,
+                                  double *ratio);
+
+/* Writes the Philox4x32-10 blocks the walkers draw for walks walk0 .. walk0 + n - 1 at the given
+ * step and block: out[4 i + c] (device uint32, n x 4), key = seed, counter =
+ * (walk_lo, walk_hi, step, block). For bitwise checks of the random-stream contract. */
+wos_status wos_debug_philox(uint64_t seed, uint64_t walk0, int64_t n, uint32_t step,
+                            uint32_t block, uint32_t *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WOS_H */

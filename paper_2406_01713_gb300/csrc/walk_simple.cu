@@ -1,0 +1,217 @@
+// One-thread-per-walk Walk-on-Spheres walkers (Sec. IV-A):
+//   T = double : FP64 parity mode. Same component order, same Philox counters and the same
+//                direct normaliser series as the definition, so every walk can be compared
+//                with an FP64 reference walk by walk.
+//   T = float  : the plain FP32 walker used as the speed baseline: obstacles read from global
+//                memory, FP32 normaliser series evaluated every step, FP32 per-query sums.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "wos_geom.cuh"
+#include "wos_launch.h"
+
+namespace wos {
+namespace {
+
+template <typename T, int D>
+struct WalkResult {
+    T term, dsig;
+    T grad[D];
+    T dw[kMaxExp];
+    int64_t jumps;
+    int capped, outside;
+};
+
+template <int D>
+__device__ __forceinline__ void direction(uint64_t seed, uint64_t walk, uint32_t step,
+                                          double (&v)[D]) {
+    direction_f64<D>(seed, walk, step, v);
+}
+template <int D>
+__device__ __forceinline__ void direction(uint64_t seed, uint64_t walk, uint32_t step,
+                                          float (&v)[D]) {
+    direction_f32<D, false>(seed, walk, step, v);
+}
+
+template <typename T, int D>
+__device__ void run_walk(const SimpleParams<T> &p, const double *xq, uint64_t walk,
+                         WalkResult<T, D> &res) {
+    const DomainView<T> &dm = p.dom;
+    const T nu = T(0.5) * T(D) - T(1);
+    T x[D], v[D], v0[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        x[j] = (T)xq[j];
+        v0[j] = T(0);
+    }
+    T logw = T(0), dsig = T(0), R0 = T(0), logC0 = T(0), S1_0 = T(1);
+    int64_t k = 0;
+    int kind = -1;
+    int64_t idx = -1;
+    res.term = T(0);
+    res.dsig = T(0);
+    res.capped = 0;
+    res.outside = 0;
+#pragma unroll
+    for (int i = 0; i < kMaxExp; ++i) res.dw[i] = T(0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) res.grad[j] = T(0);
+    for (;;) {
+        const T R = distance<T, D>(dm, x, kind, idx) - p.shrink;
+        if (k == 0 && !(R > T(0))) {
+            res.outside = 1;
+            res.jumps = 0;
+            return;
+        }
+        if (R < p.eps && !(p.grad_mode && k == 0)) {
+            T e[kMaxExp];
+            const T g = boundary_value<T, D>(dm, x, kind, idx, e);
+            const T w = exp(logw);
+            res.term = g * w;
+#pragma unroll
+            for (int i = 0; i < kMaxExp; ++i)
+                if (i < dm.n_exp) res.dw[i] = w * e[i];
+            break;
+        }
+        if (k == p.max_steps) {
+            res.capped = 1;
+            res.term = T(0);
+            break;
+        }
+        direction<D>(p.seed, walk, (uint32_t)k, v);
+        const T z = R * p.sqrt_sigma;
+        const T S0 = bessel_S<T>(nu, z);
+        const T S1 = bessel_S<T>(nu + T(1), z);
+        const T logC = -log(S0);
+        if (k == 0) {
+            R0 = R;
+            logC0 = logC;
+            S1_0 = S1;
+#pragma unroll
+            for (int j = 0; j < D; ++j) v0[j] = v[j];
+        }
+        logw += logC;
+        dsig += -(R * R / (T(2) * T(D))) * S1 / S0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) x[j] = x[j] + R * v[j];
+        ++k;
+    }
+    res.jumps = k;
+    res.dsig = res.term * dsig;
+    if (k > 0 && !res.capped) {
+        const T u1 = res.term * exp(-logC0);
+        const T factor = p.laplace ? T(D) / R0 : (T(D) / R0) / S1_0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) res.grad[j] = factor * u1 * v0[j];
+    }
+}
+
+// Sum of v over the lanes of this lane's segment that follow it (segments = runs of equal
+// query index in consecutive lanes); the first lane of a segment gets the segment total.
+template <typename V>
+__device__ __forceinline__ V segment_sum(V v, int lane, int seg_end) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const V o = __shfl_down_sync(0xffffffffu, v, off);
+        if (lane + off <= seg_end) v += o;
+    }
+    return v;
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(128) walk_simple_kernel(const SimpleParams<T> p) {
+    if (p.skip != nullptr && *p.skip != 0) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t total = p.Q * p.N;
+    const int K = p.dom.n_exp;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = base + threadIdx.x;
+        const bool active = j < total;
+        const int64_t q = active ? j / p.N : -1;
+        WalkResult<T, D> r;
+        r.jumps = 0;
+        r.term = T(0);
+        if (active) {
+            run_walk<T, D>(p, p.x + q * D, (uint64_t)(p.walk_offset + j), r);
+            if (p.w_term) p.w_term[j] = r.outside ? (double)CUDART_NAN : (double)r.term;
+            if (p.w_jumps) p.w_jumps[j] = r.jumps;
+            if (p.w_dsigma) p.w_dsigma[j] = (double)r.dsig;
+            if (p.w_grad)
+                for (int i = 0; i < D; ++i) p.w_grad[j * D + i] = (double)r.grad[i];
+        } else {
+            r.outside = 0;
+            r.capped = 0;
+        }
+        __syncwarp();
+        // Per-query reduction: consecutive walks share a query, so reduce runs of equal q.
+        const unsigned peers = __match_any_sync(0xffffffffu, (long long)q);
+        const int seg_end = 31 - __clz(peers);
+        const bool leader = (lane == __ffs(peers) - 1) && q >= 0;
+        const bool ok = active && !r.outside;
+        T vals[3] = {ok ? r.term : T(0), ok ? r.term * r.term : T(0), ok ? r.dsig : T(0)};
+        T *acc = p.acc + (q >= 0 ? q : 0) * p.nf;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            const T s = segment_sum(vals[f], lane, seg_end);
+            if (leader) atomicAdd(acc + f, s);
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const T g = ok ? r.grad[i] : T(0);
+            const T s1 = segment_sum(g, lane, seg_end);
+            const T s2 = segment_sum(g * g, lane, seg_end);
+            if (leader) {
+                atomicAdd(acc + 3 + i, s1);
+                atomicAdd(acc + 3 + D + i, s2);
+            }
+        }
+        for (int k = 0; k < K; ++k) {
+            const T s = segment_sum(ok ? r.dw[k] : T(0), lane, seg_end);
+            if (leader) atomicAdd(acc + 3 + 2 * D + k, s);
+        }
+        const unsigned long long c[4] = {active ? 1ull : 0ull,
+                                         active ? (unsigned long long)(r.jumps + 1) : 0ull,
+                                         (unsigned long long)(active && r.capped),
+                                         (unsigned long long)(active && r.outside)};
+        unsigned long long *cnt = p.counts + (q >= 0 ? q : 0) * kCounters;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const unsigned long long s = segment_sum(c[f], lane, seg_end);
+            if (leader) atomicAdd(cnt + f, s);
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_simple(const SimpleParams<T> &p, cudaStream_t s) {
+    const int threads = 128;
+    const int64_t total = p.Q * p.N;
+    if (total <= 0) return cudaSuccess;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t blocks = (total + threads - 1) / threads;
+    const int64_t cap = (int64_t)sms * 16;
+    if (blocks > cap) blocks = cap;
+    switch (p.dom.d) {
+#define WOS_CASE(DD) \
+    case DD: walk_simple_kernel<T, DD><<<(unsigned)blocks, threads, 0, s>>>(p); break;
+        WOS_CASE(2) WOS_CASE(3) WOS_CASE(4) WOS_CASE(5) WOS_CASE(6) WOS_CASE(7)
+        WOS_CASE(8) WOS_CASE(9) WOS_CASE(10) WOS_CASE(11) WOS_CASE(12)
+#undef WOS_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_walk_simple_f64(const SimpleParams<double> &p, cudaStream_t s) {
+    return launch_simple<double>(p, s);
+}
+cudaError_t launch_walk_simple_f32(const SimpleParams<float> &p, cudaStream_t s) {
+    return launch_simple<float>(p, s);
+}
+
+}  // namespace wos

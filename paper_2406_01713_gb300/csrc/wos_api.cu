@@ -1,0 +1,1485 @@
+// Host side of the C ABI declared in include/wos.h: domain objects, weight tables,
+// walker launches, per-query finalisation, planner, backward and the batched persistent
+// launch with its CUDA graph and autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "wos_geom.cuh"
+#include "wos_launch.h"
+
+using namespace wos;
+
+// =====================================================================================
+// errors
+// =====================================================================================
+namespace {
+
+thread_local std::string g_err;
+
+wos_status fail(wos_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define WOS_CUDA(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(WOS_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                              \
+    } while (0)
+
+#define WOS_TRY(expr)                     \
+    do {                                  \
+        wos_status s_ = (expr);           \
+        if (s_ != WOS_OK) return s_;      \
+    } while (0)
+
+const double kU32 = 5.9604644775390625e-08;  // FP32 unit roundoff 2^-24
+
+int device_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return sms > 0 ? sms : 1;
+}
+
+}  // namespace
+
+// =====================================================================================
+// domain
+// =====================================================================================
+struct wos_domain_s {
+    int d = 0, has_box = 0, has_outer = 0, has_goal = 0, n_balls = 0, n_exp = 0;
+    int64_t n_points = 0;
+    double outer_r = 0, goal_r = 0;
+    std::vector<double> box_lo, box_hi, outer_c, goal_c, exp_w, exp_a, ball_r, ball_c, points;
+    double R_max = 0;     // upper bound of any distance to the boundary
+    double shrink32 = 0;  // FP32 distance + jump error bound
+    double slack32 = 0;   // FP32 ball-screen rounding bound
+    double *f64 = nullptr;
+    float *f32 = nullptr;
+    DomainView<double> v64{};
+    DomainView<float> v32{};
+    float *balls_mixed = nullptr;  // 4-ball blocks for shared-memory staging
+    float *geom_mixed = nullptr;   // box lo/hi, goal c, outer c, exp w (padded), exp a (padded)
+    int nblk = 0;
+    std::mutex mu;
+    std::vector<float2 *> tables;
+    float2 *table = nullptr;
+    double table_zmax = 0;
+};
+
+namespace {
+
+template <typename T>
+void layout_view(DomainView<T> &v, T *base, const wos_domain_s &D) {
+    const int d = D.d, K = D.n_exp;
+    const int64_t B = D.n_balls, M = D.n_points;
+    T *p = base;
+    v.d = d;
+    v.n_balls = D.n_balls;
+    v.n_exp = K;
+    v.has_box = D.has_box;
+    v.has_outer = D.has_outer;
+    v.has_goal = D.has_goal;
+    v.n_points = M;
+    v.outer_r = (T)D.outer_r;
+    v.goal_r = (T)D.goal_r;
+    v.box_lo = p; p += d;
+    v.box_hi = p; p += d;
+    v.outer_c = p; p += d;
+    v.goal_c = p; p += d;
+    v.exp_w = p; p += K;
+    v.exp_a = p; p += (int64_t)K * d;
+    v.ball_r = p; p += B;
+    v.ball_c = p; p += B * d;
+    v.points = p; p += M * d;
+}
+
+int64_t view_size(const wos_domain_s &D) {
+    return 4LL * D.d + D.n_exp + (int64_t)D.n_exp * D.d + D.n_balls + (int64_t)D.n_balls * D.d +
+           D.n_points * D.d;
+}
+
+template <typename T>
+std::vector<T> pack_view(const wos_domain_s &D) {
+    std::vector<T> h((size_t)view_size(D), T(0));
+    size_t o = 0;
+    auto put = [&](const std::vector<double> &v, size_t n) {
+        for (size_t i = 0; i < n; ++i) h[o + i] = (T)(i < v.size() ? v[i] : 0.0);
+        o += n;
+    };
+    const size_t d = D.d;
+    put(D.box_lo, d);
+    put(D.box_hi, d);
+    put(D.outer_c, d);
+    put(D.goal_c, d);
+    put(D.exp_w, D.n_exp);
+    put(D.exp_a, (size_t)D.n_exp * d);
+    put(D.ball_r, D.n_balls);
+    put(D.ball_c, (size_t)D.n_balls * d);
+    put(D.points, (size_t)D.n_points * d);
+    return h;
+}
+
+int geom_floats(int d) { return 4 * d + kMaxExp + kMaxExp * d; }
+
+// Error bounds of the FP32 walkers (rounding unit u = 2^-24):
+//  * shrink: distance |x-c| - r evaluated in FP32 is within u((d+4)/2 (|x|+|c|) + R + |c| + r)
+//    of the exact distance at the FP32 point; the jump x + R v moves by at most
+//    R (1 + (d+5) u) + u |x|. Twice the sum keeps every sphere inside the FP64 domain.
+//  * slack: the screen L = e0 + e1 b + x.m and the threshold b^2 - |x|^2 are FMA chains whose
+//    partial sums are bounded by P = |c|^2 + r^2 + 2 r b + 2 |x||c| and b^2 + |x|^2.
+void error_bounds(wos_domain_s &D) {
+    const int d = D.d;
+    double xabs = 0.0;  // bound of |x_j| inside the domain
+    double xa_box = 0.0, xa_out = 0.0;
+    if (D.has_box)
+        for (int j = 0; j < d; ++j) xa_box = std::max({xa_box, std::fabs(D.box_lo[j]), std::fabs(D.box_hi[j])});
+    if (D.has_outer)
+        for (int j = 0; j < d; ++j) xa_out = std::max(xa_out, std::fabs(D.outer_c[j]) + D.outer_r);
+    if (D.has_box && D.has_outer) xabs = std::min(xa_box, xa_out);
+    else xabs = D.has_box ? xa_box : xa_out;
+    const double L = std::sqrt((double)d) * xabs;
+    double cmax = 0.0, rmax = 0.0, ccmax = 0.0;
+    for (int i = 0; i < D.n_balls; ++i) {
+        double cc = 0.0;
+        for (int j = 0; j < d; ++j) cc += D.ball_c[(size_t)i * d + j] * D.ball_c[(size_t)i * d + j];
+        ccmax = std::max(ccmax, cc);
+        rmax = std::max(rmax, D.ball_r[i]);
+    }
+    cmax = std::sqrt(ccmax);
+    double cgo = 0.0;
+    if (D.has_goal) {
+        double cc = 0.0;
+        for (int j = 0; j < d; ++j) cc += D.goal_c[j] * D.goal_c[j];
+        cgo = std::sqrt(cc) + D.goal_r;
+    }
+    if (D.has_outer) {
+        double cc = 0.0;
+        for (int j = 0; j < d; ++j) cc += D.outer_c[j] * D.outer_c[j];
+        cgo = std::max(cgo, std::sqrt(cc) + D.outer_r);
+    }
+    const double C = std::max(cmax, cgo);
+    const double R = D.R_max;
+    const double dist_err = ((d + 4) / 2.0) * (L + C) + R + C + rmax + xabs;
+    const double jump_err = (d + 5) * R + L;
+    D.shrink32 = 2.0 * kU32 * (dist_err + jump_err);
+    const double P = ccmax + rmax * rmax + 2.0 * rmax * R + 2.0 * L * cmax;
+    D.slack32 = 2.0 * (d + 4) * kU32 * (P + R * R + 2.0 * L * L);
+}
+
+// Table of log C_nu(z) and S_{nu+1}(z)/S_nu(z), built in FP64 on the device.
+__global__ void build_table_kernel(int d, double h, int n, float2 *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double z = h * i;
+    const double nu = 0.5 * d - 1.0;
+    const double S0 = bessel_S<double>(nu, z);
+    const double S1 = bessel_S<double>(nu + 1.0, z);
+    out[i] = make_float2((float)(-log(S0)), (float)(S1 / S0));
+}
+
+// Copies device FP64 weights w[K] into the FP64, FP32 and mixed copies of the domain.
+__global__ void set_exp_w_kernel(const double *w, int K, double *w64, float *w32, float *wg) {
+    const int k = threadIdx.x;
+    if (k < K) {
+        w64[k] = w[k];
+        w32[k] = (float)w[k];
+        wg[k] = (float)w[k];
+    }
+}
+
+wos_status ensure_table(wos_domain_t dom, double sigma, WeightTable *out) {
+    const double need = dom->R_max * std::sqrt(sigma) * 1.0001 + 1e-9;
+    std::lock_guard<std::mutex> lk(dom->mu);
+    if (dom->table == nullptr || dom->table_zmax < need) {
+        const double zmax = std::max(1.0, need * 1.25);
+        float2 *t = nullptr;
+        WOS_CUDA(cudaMalloc(&t, sizeof(float2) * kTableNodes));
+        cudaStream_t s;
+        WOS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        const double h = zmax / (kTableNodes - 1);
+        build_table_kernel<<<(kTableNodes + 255) / 256, 256, 0, s>>>(dom->d, h, kTableNodes, t);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+        if (e != cudaSuccess) {
+            cudaFree(t);
+            return fail(WOS_ERR_CUDA, "weight table build failed: %s", cudaGetErrorString(e));
+        }
+        dom->tables.push_back(t);
+        dom->table = t;
+        dom->table_zmax = zmax;
+    }
+    out->nodes = dom->table;
+    out->n = kTableNodes;
+    out->inv_h = (float)((kTableNodes - 1) / dom->table_zmax);
+    return WOS_OK;
+}
+
+// =====================================================================================
+// per-query finalisation (u = mean, SE of the mean, grad, derivatives)
+// =====================================================================================
+struct FinalizeRec {
+    int d, K, acc_f32;
+    int64_t Q, N, q_begin;
+    const void *acc;
+    const unsigned long long *counts;
+    double *u, *u_se, *grad, *grad_se, *du_dsigma, *du_dw;
+    int64_t *walk_steps;
+};
+
+struct FinalizeArgs {
+    const FinalizeRec *recs;  // device, or nullptr to use `single`
+    int n;
+    int64_t total_q;
+    FinalizeRec single;
+    wos_stats *stats;
+};
+
+__device__ __forceinline__ double se_mean(double s, double s2, double n) {
+    if (n < 2.0) return 0.0;
+    const double var = (s2 - s * s / n) / (n - 1.0);
+    return var > 0.0 ? sqrt(var / n) : 0.0;
+}
+
+__global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.total_q;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const FinalizeRec *R = &a.single;
+        if (a.recs != nullptr) {
+            int lo = 0, hi = a.n - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.recs[mid].q_begin <= t) lo = mid;
+                else hi = mid - 1;
+            }
+            R = a.recs + lo;
+        }
+        const int64_t q = t - R->q_begin;
+        const int d = R->d, K = R->K, nf = acc_fields(d, K);
+        auto S = [&](int f) -> double {
+            return R->acc_f32 ? (double)((const float *)R->acc)[q * nf + f]
+                              : ((const double *)R->acc)[q * nf + f];
+        };
+        const unsigned long long *c = R->counts + q * kCounters;
+        const double n = (double)R->N;
+        const double inv = 1.0 / n;
+        const bool out = c[3] > 0;
+        const double nan = CUDART_NAN;
+        if (R->u) R->u[q] = out ? nan : S(0) * inv;
+        if (R->u_se) R->u_se[q] = out ? nan : se_mean(S(0), S(1), n);
+        if (R->du_dsigma) R->du_dsigma[q] = out ? nan : S(2) * inv;
+        for (int i = 0; i < d; ++i) {
+            if (R->grad) R->grad[q * d + i] = out ? nan : S(3 + i) * inv;
+            if (R->grad_se) R->grad_se[q * d + i] = out ? nan : se_mean(S(3 + i), S(3 + d + i), n);
+        }
+        for (int k = 0; k < K; ++k)
+            if (R->du_dw) R->du_dw[q * K + k] = out ? nan : S(3 + 2 * d + k) * inv;
+        if (R->walk_steps) R->walk_steps[q] = (int64_t)c[1];
+        if (a.stats != nullptr) {
+            unsigned long long *st = reinterpret_cast<unsigned long long *>(a.stats);
+            atomicAdd(st + 0, c[0]);
+            atomicAdd(st + 1, c[1]);
+            if (c[2]) atomicAdd(st + 2, c[2]);
+            if (c[3]) atomicAdd(st + 3, c[3]);
+        }
+    }
+}
+
+wos_status launch_finalize(const FinalizeArgs &a, cudaStream_t s) {
+    if (a.total_q <= 0) return WOS_OK;
+    const int threads = 128;
+    const int64_t blocks = std::min<int64_t>((a.total_q + threads - 1) / threads, 4096);
+    finalize_kernel<<<(unsigned)blocks, threads, 0, s>>>(a);
+    WOS_CUDA(cudaGetLastError());
+    return WOS_OK;
+}
+
+// =====================================================================================
+// walker launches
+// =====================================================================================
+struct Opts {
+    int precision, laplace;
+    uint64_t seed;
+    int64_t walk_offset, max_steps;
+};
+
+Opts read_opts(const wos_options *o) {
+    Opts r{WOS_MIXED, 0, 0ull, 0, 10000};
+    if (o != nullptr) {
+        r.precision = o->precision;
+        r.laplace = (o->flags & WOS_FLAG_LAPLACE_FACTOR) ? 1 : 0;
+        r.seed = o->seed;
+        r.walk_offset = o->walk_offset;
+        r.max_steps = o->max_steps > 0 ? o->max_steps : 10000;
+    }
+    return r;
+}
+
+struct PerWalk {
+    double *term = nullptr;
+    int64_t *jumps = nullptr;
+    double *grad = nullptr;
+    double *dsigma = nullptr;
+};
+
+struct Scratch {
+    void *acc = nullptr;                    // Q x nf (double, or float for the plain walker)
+    unsigned long long *counts = nullptr;   // Q x kCounters
+    unsigned long long *cursor = nullptr;   // work-queue cursor (mixed walker)
+};
+
+size_t scratch_bytes(int precision, int64_t Q, int nf) {
+    const size_t es = precision == WOS_FP32_PLAIN ? sizeof(float) : sizeof(double);
+    size_t acc = ((size_t)Q * nf * es + 255) & ~(size_t)255;
+    size_t cnt = ((size_t)Q * kCounters * 8 + 255) & ~(size_t)255;
+    return acc + cnt + 256;
+}
+
+Scratch carve_scratch(void *base, int precision, int64_t Q, int nf) {
+    const size_t es = precision == WOS_FP32_PLAIN ? sizeof(float) : sizeof(double);
+    size_t acc = ((size_t)Q * nf * es + 255) & ~(size_t)255;
+    size_t cnt = ((size_t)Q * kCounters * 8 + 255) & ~(size_t)255;
+    Scratch s;
+    s.acc = base;
+    s.counts = reinterpret_cast<unsigned long long *>((char *)base + acc);
+    s.cursor = reinterpret_cast<unsigned long long *>((char *)base + acc + cnt);
+    return s;
+}
+
+size_t g_mixed_smem_configured = 0;
+std::mutex g_mixed_mu;
+
+wos_status ensure_mixed_smem(size_t bytes) {
+    std::lock_guard<std::mutex> lk(g_mixed_mu);
+    if (bytes > g_mixed_smem_configured) {
+        WOS_CUDA(configure_walk_mixed(bytes));
+        g_mixed_smem_configured = bytes;
+    }
+    return WOS_OK;
+}
+
+MixedProblem make_mixed_problem(wos_domain_t dom, const double *x, int64_t Q, int64_t N,
+                                double eps, double sigma, int grad_mode, int laplace,
+                                int64_t walk_base, const WeightTable &tab, double *acc,
+                                unsigned long long *counts, const PerWalk &pw) {
+    MixedProblem P{};
+    P.d = dom->d;
+    P.n_balls = dom->n_balls;
+    P.n_exp = dom->n_exp;
+    P.has_box = dom->has_box;
+    P.has_outer = dom->has_outer;
+    P.has_goal = dom->has_goal;
+    P.grad_mode = grad_mode;
+    P.laplace = laplace;
+    P.eps = (float)eps;
+    P.sqrt_sigma = (float)std::sqrt(sigma);
+    P.shrink = (float)dom->shrink32;
+    P.slack = (float)dom->slack32;
+    P.goal_r = (float)dom->goal_r;
+    P.outer_r = (float)dom->outer_r;
+    P.Q = Q;
+    P.N = N;
+    P.walk_base = walk_base;
+    P.balls = dom->balls_mixed;
+    P.geom = dom->geom_mixed;
+    P.x = x;
+    P.table = tab;
+    P.acc = acc;
+    P.counts = counts;
+    P.w_term = pw.term;
+    P.w_jumps = pw.jumps;
+    P.w_grad = pw.grad;
+    P.w_dsigma = pw.dsigma;
+    return P;
+}
+
+size_t mixed_smem_bytes(const wos_domain_s &D) {
+    return (size_t)((D.n_balls + 3) / 4) * (D.d + 2) * 16;
+}
+
+// Launches the walk kernel of the chosen precision for Q x N walks on zeroed scratch.
+wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int64_t Q, int64_t N,
+                          double eps, double sigma, int grad_mode, const Scratch &sc,
+                          const PerWalk &pw, const int *skip, cudaStream_t s) {
+    const int nf = acc_fields(dom->d, dom->n_exp);
+    if (o.precision == WOS_FP64) {
+        SimpleParams<double> p{};
+        p.dom = dom->v64;
+        p.x = x;
+        p.Q = Q;
+        p.N = N;
+        p.seed = o.seed;
+        p.walk_offset = o.walk_offset;
+        p.max_steps = o.max_steps;
+        p.eps = eps;
+        p.sqrt_sigma = std::sqrt(sigma);
+        p.shrink = 0.0;
+        p.grad_mode = grad_mode;
+        p.laplace = o.laplace;
+        p.acc = (double *)sc.acc;
+        p.counts = sc.counts;
+        p.nf = nf;
+        p.w_term = pw.term;
+        p.w_jumps = pw.jumps;
+        p.w_grad = pw.grad;
+        p.w_dsigma = pw.dsigma;
+        p.skip = skip;
+        WOS_CUDA(launch_walk_simple_f64(p, s));
+        return WOS_OK;
+    }
+    if (o.precision == WOS_FP32_PLAIN) {
+        SimpleParams<float> p{};
+        p.dom = dom->v32;
+        p.x = x;
+        p.Q = Q;
+        p.N = N;
+        p.seed = o.seed;
+        p.walk_offset = o.walk_offset;
+        p.max_steps = o.max_steps;
+        p.eps = (float)eps;
+        p.sqrt_sigma = (float)std::sqrt(sigma);
+        p.shrink = (float)dom->shrink32;
+        p.grad_mode = grad_mode;
+        p.laplace = o.laplace;
+        p.acc = (float *)sc.acc;
+        p.counts = sc.counts;
+        p.nf = nf;
+        p.w_term = pw.term;
+        p.w_jumps = pw.jumps;
+        p.w_grad = pw.grad;
+        p.w_dsigma = pw.dsigma;
+        p.skip = skip;
+        WOS_CUDA(launch_walk_simple_f32(p, s));
+        return WOS_OK;
+    }
+    if (o.precision != WOS_MIXED) return fail(WOS_ERR_INVALID_ARG, "unknown precision %d", o.precision);
+    if (dom->n_points > 0)
+        return fail(WOS_ERR_UNSUPPORTED, "point-cloud domains use the point-cloud walker");
+    WeightTable tab;
+    WOS_TRY(ensure_table(dom, sigma, &tab));
+    const int64_t total = Q * N;
+    if (total > (int64_t)0x7fffffff) return fail(WOS_ERR_UNSUPPORTED, "Q * n_walks must be < 2^31");
+    const size_t smem = mixed_smem_bytes(*dom);
+    WOS_TRY(ensure_mixed_smem(smem));
+    const int sms = device_sms();
+    int threads = (int)std::min<int64_t>(256, std::max<int64_t>(32, ((total / sms) + 31) / 32 * 32));
+    int occ = max_active_mixed(threads, smem, grad_mode);
+    if (occ < 1) return fail(WOS_ERR_UNSUPPORTED, "mixed walker does not fit (%zu B smem)", smem);
+    const int64_t grid_full = (int64_t)sms * occ;
+    int64_t wpi = (total + 4 * grid_full - 1) / (4 * grid_full);
+    wpi = std::max<int64_t>(threads, std::min<int64_t>(1 << 20, (wpi + 31) / 32 * 32));
+    const int64_t n_items = (total + wpi - 1) / wpi;
+    const int grid = (int)std::min<int64_t>(grid_full, n_items);
+    MixedLaunch L{};
+    L.problems = nullptr;
+    L.items = nullptr;
+    L.n_items = n_items;
+    L.walks_per_item = wpi;
+    L.total_walks = total;
+    L.cursor = sc.cursor;
+    L.seed = o.seed;
+    L.max_steps = o.max_steps;
+    L.skip = skip;
+    L.single = make_mixed_problem(dom, x, Q, N, eps, sigma, grad_mode, o.laplace, o.walk_offset,
+                                  tab, (double *)sc.acc, sc.counts, pw);
+    WOS_CUDA(launch_walk_mixed(L, grad_mode, grid, threads, smem, s));
+    return WOS_OK;
+}
+
+wos_status check_common(wos_domain_t dom, const double *x, int64_t Q, int64_t N, double eps,
+                        double sigma) {
+    if (dom == nullptr) return fail(WOS_ERR_INVALID_ARG, "domain is NULL");
+    if (Q < 0 || N < 1) return fail(WOS_ERR_INVALID_ARG, "Q must be >= 0 and n_walks >= 1");
+    if (Q > 0 && x == nullptr) return fail(WOS_ERR_INVALID_ARG, "x is NULL");
+    if (!(eps > 0.0) || !(sigma >= 0.0) || !std::isfinite(sigma))
+        return fail(WOS_ERR_INVALID_ARG, "eps must be > 0 and sigma >= 0");
+    if (Q > ((int64_t)1 << 40) / N) return fail(WOS_ERR_INVALID_ARG, "Q * n_walks too large");
+    return WOS_OK;
+}
+
+struct Outputs {
+    double *u = nullptr, *u_se = nullptr, *grad = nullptr, *grad_se = nullptr;
+    double *du_dsigma = nullptr, *du_dw = nullptr;
+};
+
+wos_status run_estimator(wos_domain_t dom, const wos_options *opt, const double *x, int64_t Q,
+                         int64_t N, double eps, double sigma, int grad_mode, const Outputs &out,
+                         const PerWalk &pw, wos_stats *stats, cudaStream_t s) {
+    WOS_TRY(check_common(dom, x, Q, N, eps, sigma));
+    const Opts o = read_opts(opt);
+    if (o.precision < WOS_FP64 || o.precision > WOS_MIXED)
+        return fail(WOS_ERR_INVALID_ARG, "unknown precision %d", o.precision);
+    if (stats != nullptr) WOS_CUDA(cudaMemsetAsync(stats, 0, sizeof(wos_stats), s));
+    if (Q == 0) return WOS_OK;
+    const int nf = acc_fields(dom->d, dom->n_exp);
+    const size_t bytes = scratch_bytes(o.precision, Q, nf);
+    void *base = nullptr;
+    WOS_CUDA(cudaMallocAsync(&base, bytes, s));
+    Scratch sc = carve_scratch(base, o.precision, Q, nf);
+    wos_status st = WOS_OK;
+    if (cudaMemsetAsync(base, 0, bytes, s) != cudaSuccess)
+        st = fail(WOS_ERR_CUDA, "scratch memset failed");
+    if (st == WOS_OK) st = launch_walkers(dom, o, x, Q, N, eps, sigma, grad_mode, sc, pw, nullptr, s);
+    if (st == WOS_OK) {
+        FinalizeArgs a{};
+        a.recs = nullptr;
+        a.n = 1;
+        a.total_q = Q;
+        a.stats = stats;
+        FinalizeRec &r = a.single;
+        r.d = dom->d;
+        r.K = dom->n_exp;
+        r.acc_f32 = o.precision == WOS_FP32_PLAIN;
+        r.Q = Q;
+        r.N = N;
+        r.q_begin = 0;
+        r.acc = sc.acc;
+        r.counts = sc.counts;
+        r.u = out.u;
+        r.u_se = out.u_se;
+        r.grad = out.grad;
+        r.grad_se = out.grad_se;
+        r.du_dsigma = out.du_dsigma;
+        r.du_dw = out.du_dw;
+        r.walk_steps = nullptr;
+        st = launch_finalize(a, s);
+    }
+    cudaFreeAsync(base, s);
+    return st;
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI: domain
+// =====================================================================================
+extern "C" {
+
+const char *wos_status_string(wos_status s) {
+    switch (s) {
+        case WOS_OK: return "ok";
+        case WOS_ERR_INVALID_ARG: return "invalid argument";
+        case WOS_ERR_UNSUPPORTED: return "unsupported";
+        case WOS_ERR_OOM: return "out of memory";
+        case WOS_ERR_CUDA: return "CUDA error";
+        case WOS_ERR_TIMEOUT: return "device iteration budget exhausted";
+        case WOS_ERR_OUTSIDE_DOMAIN: return "query outside the domain";
+    }
+    return "unknown status";
+}
+
+const char *wos_last_error(void) { return g_err.c_str(); }
+
+wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
+    if (out == nullptr) return fail(WOS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (desc == nullptr) return fail(WOS_ERR_INVALID_ARG, "desc is NULL");
+    const int d = desc->d;
+    if (d < 2 || d > WOS_MAX_D) return fail(WOS_ERR_UNSUPPORTED, "d = %d outside 2..%d", d, WOS_MAX_D);
+    if (desc->n_balls < 0 || desc->n_points < 0 || desc->n_exp < 0)
+        return fail(WOS_ERR_INVALID_ARG, "negative count");
+    if (desc->n_exp > WOS_MAX_EXP) return fail(WOS_ERR_UNSUPPORTED, "n_exp > %d", WOS_MAX_EXP);
+    if ((desc->box_lo == nullptr) != (desc->box_hi == nullptr))
+        return fail(WOS_ERR_INVALID_ARG, "box_lo and box_hi must both be given");
+    if (desc->box_lo == nullptr && desc->outer_c == nullptr)
+        return fail(WOS_ERR_INVALID_ARG, "a box or an outer ball is required");
+    if (desc->n_balls > 0 && (desc->ball_c == nullptr || desc->ball_r == nullptr))
+        return fail(WOS_ERR_INVALID_ARG, "ball arrays missing");
+    if (desc->n_points > 0 && desc->points == nullptr) return fail(WOS_ERR_INVALID_ARG, "points missing");
+    if (desc->n_exp > 0 && (desc->exp_w == nullptr || desc->exp_a == nullptr))
+        return fail(WOS_ERR_INVALID_ARG, "exp arrays missing");
+    if (desc->outer_c != nullptr && !(desc->outer_r > 0)) return fail(WOS_ERR_INVALID_ARG, "outer_r <= 0");
+    if (desc->goal_c != nullptr && !(desc->goal_r > 0)) return fail(WOS_ERR_INVALID_ARG, "goal_r <= 0");
+    for (int i = 0; i < desc->n_balls; ++i)
+        if (!(desc->ball_r[i] > 0) || !std::isfinite(desc->ball_r[i]))
+            return fail(WOS_ERR_INVALID_ARG, "ball %d radius <= 0", i);
+    if (desc->box_lo != nullptr)
+        for (int j = 0; j < d; ++j)
+            if (!(desc->box_hi[j] > desc->box_lo[j])) return fail(WOS_ERR_INVALID_ARG, "empty box");
+
+    wos_domain_s *D = new (std::nothrow) wos_domain_s();
+    if (D == nullptr) return fail(WOS_ERR_OOM, "host allocation failed");
+    D->d = d;
+    D->has_box = desc->box_lo != nullptr;
+    D->has_outer = desc->outer_c != nullptr;
+    D->has_goal = desc->goal_c != nullptr;
+    D->n_balls = desc->n_balls;
+    D->n_points = desc->n_points;
+    D->n_exp = desc->n_exp;
+    D->outer_r = D->has_outer ? desc->outer_r : 0.0;
+    D->goal_r = D->has_goal ? desc->goal_r : 0.0;
+    auto copy = [](std::vector<double> &v, const double *p, size_t n) {
+        v.assign(n, 0.0);
+        if (p) std::copy(p, p + n, v.begin());
+    };
+    copy(D->box_lo, desc->box_lo, d);
+    copy(D->box_hi, desc->box_hi, d);
+    copy(D->outer_c, desc->outer_c, d);
+    copy(D->goal_c, desc->goal_c, d);
+    copy(D->exp_w, desc->exp_w, desc->n_exp);
+    copy(D->exp_a, desc->exp_a, (size_t)desc->n_exp * d);
+    copy(D->ball_r, desc->ball_r, desc->n_balls);
+    copy(D->ball_c, desc->ball_c, (size_t)desc->n_balls * d);
+    copy(D->points, desc->points, (size_t)desc->n_points * d);
+    double rmax = INFINITY;
+    if (D->has_box)
+        for (int j = 0; j < d; ++j) rmax = std::min(rmax, 0.5 * (D->box_hi[j] - D->box_lo[j]));
+    if (D->has_outer) rmax = std::min(rmax, D->outer_r);
+    D->R_max = rmax;
+    error_bounds(*D);
+
+    // device copies
+    const int64_t nv = view_size(*D);
+    std::vector<double> h64 = pack_view<double>(*D);
+    std::vector<float> h32 = pack_view<float>(*D);
+    const int nblk = (D->n_balls + 3) / 4;
+    D->nblk = nblk;
+    std::vector<float> hb((size_t)std::max(1, nblk) * (d + 2) * 4, 0.0f);
+    for (int i = 0; i < nblk * 4; ++i) {
+        const int blk = i / 4, t = i % 4;
+        float *B = hb.data() + (size_t)blk * (d + 2) * 4;
+        if (i < D->n_balls) {
+            double cc = 0.0;
+            for (int j = 0; j < d; ++j) {
+                const float c = (float)D->ball_c[(size_t)i * d + j];
+                B[4 * j + t] = -2.0f * c;
+                cc += (double)c * (double)c;
+            }
+            const float r = (float)D->ball_r[i];
+            B[4 * d + t] = (float)(cc - (double)r * (double)r);
+            B[4 * (d + 1) + t] = -2.0f * r;
+        } else {
+            // padding ball: far away (never passes the screen), radius 0
+            for (int j = 0; j < d; ++j) B[4 * j + t] = 0.0f;
+            B[4 * d + t] = 3.0e38f;
+            B[4 * (d + 1) + t] = 0.0f;
+        }
+    }
+    std::vector<float> hg((size_t)geom_floats(d), 0.0f);
+    for (int j = 0; j < d; ++j) {
+        hg[j] = (float)D->box_lo[j];
+        hg[d + j] = (float)D->box_hi[j];
+        hg[2 * d + j] = (float)D->goal_c[j];
+        hg[3 * d + j] = (float)D->outer_c[j];
+    }
+    for (int k = 0; k < D->n_exp; ++k) {
+        hg[4 * d + k] = (float)D->exp_w[k];
+        for (int j = 0; j < d; ++j) hg[4 * d + kMaxExp + k * d + j] = (float)D->exp_a[(size_t)k * d + j];
+    }
+    cudaError_t e = cudaMalloc(&D->f64, sizeof(double) * (size_t)nv);
+    if (e == cudaSuccess) e = cudaMalloc(&D->f32, sizeof(float) * (size_t)nv);
+    if (e == cudaSuccess) e = cudaMalloc(&D->balls_mixed, sizeof(float) * hb.size());
+    if (e == cudaSuccess) e = cudaMalloc(&D->geom_mixed, sizeof(float) * hg.size());
+    if (e == cudaSuccess) e = cudaMemcpy(D->f64, h64.data(), sizeof(double) * nv, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(D->f32, h32.data(), sizeof(float) * nv, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(D->balls_mixed, hb.data(), sizeof(float) * hb.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(D->geom_mixed, hg.data(), sizeof(float) * hg.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        const wos_status st = fail(e == cudaErrorMemoryAllocation ? WOS_ERR_OOM : WOS_ERR_CUDA,
+                                   "domain upload failed: %s", cudaGetErrorString(e));
+        wos_domain_destroy(D);
+        return st;
+    }
+    layout_view<double>(D->v64, D->f64, *D);
+    layout_view<float>(D->v32, D->f32, *D);
+    *out = D;
+    return WOS_OK;
+}
+
+wos_status wos_domain_destroy(wos_domain_t dom) {
+    if (dom == nullptr) return WOS_OK;
+    cudaDeviceSynchronize();
+    cudaFree(dom->f64);
+    cudaFree(dom->f32);
+    cudaFree(dom->balls_mixed);
+    cudaFree(dom->geom_mixed);
+    for (float2 *t : dom->tables) cudaFree(t);
+    delete dom;
+    return WOS_OK;
+}
+
+wos_status wos_domain_set_exp_w(wos_domain_t dom, const double *w_device, int32_t n, void *stream) {
+    if (dom == nullptr || w_device == nullptr) return fail(WOS_ERR_INVALID_ARG, "NULL argument");
+    if (n != dom->n_exp) return fail(WOS_ERR_INVALID_ARG, "n = %d but the domain has %d terms", n, dom->n_exp);
+    if (n == 0) return WOS_OK;
+    set_exp_w_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(
+        w_device, n, const_cast<double *>(dom->v64.exp_w), const_cast<float *>(dom->v32.exp_w),
+        dom->geom_mixed + 4 * dom->d);
+    WOS_CUDA(cudaGetLastError());
+    return WOS_OK;
+}
+
+// =====================================================================================
+// C ABI: estimators
+// =====================================================================================
+wos_status wos_solve(wos_domain_t dom, const wos_options *opt, const double *x, int64_t Q,
+                     int64_t n_walks, double eps, double sigma, double *u, double *u_se,
+                     wos_stats *stats, void *stream) {
+    if (Q > 0 && u == nullptr) return fail(WOS_ERR_INVALID_ARG, "u is NULL");
+    Outputs o;
+    o.u = u;
+    o.u_se = u_se;
+    return run_estimator(dom, opt, x, Q, n_walks, eps, sigma, 0, o, PerWalk{}, stats,
+                         (cudaStream_t)stream);
+}
+
+wos_status wos_grad(wos_domain_t dom, const wos_options *opt, const double *x, int64_t Q,
+                    int64_t n_walks, double eps, double sigma, double *u, double *u_se,
+                    double *grad, double *grad_se, double *du_dsigma, double *du_dw,
+                    wos_stats *stats, void *stream) {
+    if (Q > 0 && grad == nullptr) return fail(WOS_ERR_INVALID_ARG, "grad is NULL");
+    Outputs o;
+    o.u = u;
+    o.u_se = u_se;
+    o.grad = grad;
+    o.grad_se = grad_se;
+    o.du_dsigma = du_dsigma;
+    o.du_dw = du_dw;
+    return run_estimator(dom, opt, x, Q, n_walks, eps, sigma, 1, o, PerWalk{}, stats,
+                         (cudaStream_t)stream);
+}
+
+wos_status wos_walks(wos_domain_t dom, const wos_options *opt, const double *x, int64_t Q,
+                     int64_t n_walks, double eps, double sigma, int32_t grad_mode, double *term,
+                     int64_t *jumps, double *grad, double *dsigma, void *stream) {
+    PerWalk pw;
+    pw.term = term;
+    pw.jumps = jumps;
+    pw.grad = grad;
+    pw.dsigma = dsigma;
+    return run_estimator(dom, opt, x, Q, n_walks, eps, sigma, grad_mode ? 1 : 0, Outputs{}, pw,
+                         nullptr, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// =====================================================================================
+// planner
+// =====================================================================================
+namespace {
+
+struct PlanArgs {
+    DomainView<double> dom;
+    double *x;
+    double eps, s_ub;
+    int64_t N;
+    int *done;
+    int *skip;
+    int32_t *flag;
+    void *acc;
+    int acc_bytes;
+    int acc_f32;
+    unsigned long long *counts;
+    unsigned long long *cursor;
+    double *grad_row;
+    double *path_row;
+};
+
+__global__ void plan_pre_kernel(const __grid_constant__ PlanArgs a) {
+    if (threadIdx.x == 0) {
+        int skip = 0;
+        int32_t f = 0;
+        if (*a.done) {
+            skip = 1;
+            f = 8;
+        } else if (a.dom.has_goal) {
+            double s = 0.0;
+            for (int j = 0; j < a.dom.d; ++j) {
+                const double t = a.x[j] - a.dom.goal_c[j];
+                s += t * t;
+            }
+            if (sqrt(s) - a.dom.goal_r < a.eps) {
+                skip = 1;
+                f = 1;
+                *a.done = 1;
+            }
+        }
+        *a.skip = skip;
+        *a.flag = f;
+        *a.cursor = 0ull;
+    }
+    __syncthreads();
+    unsigned char *acc = (unsigned char *)a.acc;
+    for (int i = threadIdx.x; i < a.acc_bytes; i += blockDim.x) acc[i] = 0;
+    for (int i = threadIdx.x; i < kCounters; i += blockDim.x) a.counts[i] = 0ull;
+}
+
+template <int D>
+__device__ void plan_post_d(const PlanArgs &a) {
+    double x[D];
+    for (int j = 0; j < D; ++j) x[j] = a.x[j];
+    if (!*a.skip) {
+        int kind;
+        int64_t idx;
+        const double R = distance<double, D>(a.dom, x, kind, idx);
+        const bool outside = a.counts[3] > 0;
+        if (outside || !(R > 0.0)) {
+            *a.flag = 4;
+            *a.done = 1;
+        } else {
+            const double inv = 1.0 / (double)a.N;
+            double g[D];
+            double gg = 0.0;
+            for (int j = 0; j < D; ++j) {
+                g[j] = (a.acc_f32 ? (double)((const float *)a.acc)[3 + j] : ((const double *)a.acc)[3 + j]) * inv;
+                gg += g[j] * g[j];
+            }
+            if (a.grad_row)
+                for (int j = 0; j < D; ++j) a.grad_row[j] = g[j];
+            if (gg > 0.0) {
+                const double gn = sqrt(gg);
+                const double s = 0.5 * R < a.s_ub ? 0.5 * R : a.s_ub;
+                for (int j = 0; j < D; ++j) x[j] = x[j] + s * (g[j] / gn);
+                for (int j = 0; j < D; ++j) a.x[j] = x[j];
+            } else {
+                *a.flag = 2;
+            }
+        }
+    }
+    if (a.path_row)
+        for (int j = 0; j < D; ++j) a.path_row[j] = x[j];
+}
+
+__global__ void plan_post_kernel(const __grid_constant__ PlanArgs a) {
+    if (threadIdx.x != 0) return;
+    switch (a.dom.d) {
+#define WOS_CASE(DD) \
+    case DD: plan_post_d<DD>(a); break;
+        WOS_CASE(2) WOS_CASE(3) WOS_CASE(4) WOS_CASE(5) WOS_CASE(6) WOS_CASE(7)
+        WOS_CASE(8) WOS_CASE(9) WOS_CASE(10) WOS_CASE(11) WOS_CASE(12)
+#undef WOS_CASE
+        default: break;
+    }
+}
+
+// One planner step: [pre: goal test, zero scratch] [gradient walkers] [post: step].
+wos_status enqueue_plan_step(wos_domain_t dom, const Opts &o, double *x, int64_t N, double eps,
+                             double sigma, double s_ub, int64_t step_idx, int *done, int *skip,
+                             int32_t *flag, const Scratch &sc, double *grad_row, double *path_row,
+                             cudaStream_t s) {
+    const int nf = acc_fields(dom->d, dom->n_exp);
+    PlanArgs a{};
+    a.dom = dom->v64;
+    a.x = x;
+    a.eps = eps;
+    a.s_ub = s_ub;
+    a.N = N;
+    a.done = done;
+    a.skip = skip;
+    a.flag = flag;
+    a.acc = sc.acc;
+    a.acc_f32 = o.precision == WOS_FP32_PLAIN;
+    a.acc_bytes = nf * (a.acc_f32 ? 4 : 8);
+    a.counts = sc.counts;
+    a.cursor = sc.cursor;
+    a.grad_row = grad_row;
+    a.path_row = path_row;
+    plan_pre_kernel<<<1, 128, 0, s>>>(a);
+    WOS_CUDA(cudaGetLastError());
+    Opts os = o;
+    os.walk_offset = o.walk_offset + step_idx * N;
+    WOS_TRY(launch_walkers(dom, os, x, 1, N, eps, sigma, 1, sc, PerWalk{}, skip, s));
+    plan_post_kernel<<<1, 32, 0, s>>>(a);
+    WOS_CUDA(cudaGetLastError());
+    return WOS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+wos_status wos_plan_step(wos_domain_t dom, const wos_options *opt, double *x, int64_t n_walks,
+                         double eps, double sigma, double s_ub, int64_t step_idx, int32_t *flag,
+                         double *grad_out, void *stream) {
+    WOS_TRY(check_common(dom, x, 1, n_walks, eps, sigma));
+    if (flag == nullptr || !(s_ub > 0)) return fail(WOS_ERR_INVALID_ARG, "flag NULL or s_ub <= 0");
+    const Opts o = read_opts(opt);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (o.precision == WOS_MIXED) {
+        WeightTable t;
+        WOS_TRY(ensure_table(dom, sigma, &t));
+    }
+    const int nf = acc_fields(dom->d, dom->n_exp);
+    const size_t bytes = scratch_bytes(o.precision, 1, nf) + 256;
+    void *base = nullptr;
+    WOS_CUDA(cudaMallocAsync(&base, bytes, s));
+    Scratch sc = carve_scratch(base, o.precision, 1, nf);
+    int *ints = reinterpret_cast<int *>((char *)base + bytes - 256);
+    wos_status st = WOS_OK;
+    if (cudaMemsetAsync(ints, 0, 2 * sizeof(int), s) != cudaSuccess) st = fail(WOS_ERR_CUDA, "memset");
+    if (st == WOS_OK)
+        st = enqueue_plan_step(dom, o, x, n_walks, eps, sigma, s_ub, step_idx, ints, ints + 1, flag,
+                               sc, grad_out, nullptr, s);
+    cudaFreeAsync(base, s);
+    return st;
+}
+
+wos_status wos_plan_path(wos_domain_t dom, const wos_options *opt, const double *x0,
+                         int64_t n_steps, int64_t n_walks, double eps, double sigma, double s_ub,
+                         double *path, int32_t *flags, double *grads, void *stream) {
+    WOS_TRY(check_common(dom, x0, 1, n_walks, eps, sigma));
+    if (path == nullptr || flags == nullptr || n_steps < 0 || !(s_ub > 0))
+        return fail(WOS_ERR_INVALID_ARG, "bad planner arguments");
+    const Opts o = read_opts(opt);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int d = dom->d;
+    WOS_CUDA(cudaMemcpyAsync(path, x0, sizeof(double) * d, cudaMemcpyDeviceToDevice, s));
+    if (n_steps == 0) return WOS_OK;
+    if (o.precision == WOS_MIXED) {
+        WeightTable t;
+        WOS_TRY(ensure_table(dom, sigma, &t));
+        WOS_TRY(ensure_mixed_smem(mixed_smem_bytes(*dom)));
+    }
+    const int nf = acc_fields(d, dom->n_exp);
+    const size_t bytes = scratch_bytes(o.precision, 1, nf) + 256 + sizeof(double) * d;
+    void *base = nullptr;
+    WOS_CUDA(cudaMalloc(&base, bytes));
+    Scratch sc = carve_scratch(base, o.precision, 1, nf);
+    int *ints = reinterpret_cast<int *>((char *)base + scratch_bytes(o.precision, 1, nf));
+    double *x = reinterpret_cast<double *>((char *)ints + 256);
+    wos_status st = WOS_OK;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    do {
+        if (cudaMemsetAsync(ints, 0, 2 * sizeof(int), s) != cudaSuccess ||
+            cudaMemcpyAsync(x, x0, sizeof(double) * d, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+            st = fail(WOS_ERR_CUDA, "planner setup failed");
+            break;
+        }
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+            st = fail(WOS_ERR_CUDA, "stream create failed");
+            break;
+        }
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            st = fail(WOS_ERR_CUDA, "graph capture failed to start");
+            break;
+        }
+        for (int64_t i = 0; i < n_steps && st == WOS_OK; ++i)
+            st = enqueue_plan_step(dom, o, x, n_walks, eps, sigma, s_ub, i, ints, ints + 1,
+                                   flags + i, sc, grads ? grads + i * d : nullptr,
+                                   path + (i + 1) * d, cap);
+        cudaError_t e = cudaStreamEndCapture(cap, &graph);
+        if (st != WOS_OK) break;
+        if (e != cudaSuccess) {
+            st = fail(WOS_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+            break;
+        }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) {
+            st = fail(WOS_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+            break;
+        }
+        e = cudaGraphLaunch(exec, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = fail(WOS_ERR_CUDA, "planner graph failed: %s", cudaGetErrorString(e));
+    } while (0);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    cudaStreamSynchronize(s);
+    cudaFree(base);
+    return st;
+}
+
+}  // extern "C"
+
+// =====================================================================================
+// backward
+// =====================================================================================
+namespace {
+
+__global__ void backward_kernel(const double *gout, const double *grad, const double *dsig,
+                                const double *dw, int64_t Q, int d, int K, double *gx,
+                                double *gsigma, double *gw) {
+    __shared__ double red[256];
+    if (gx != nullptr)
+        for (int64_t i = threadIdx.x; i < Q * d; i += blockDim.x) gx[i] = gout[i / d] * grad[i];
+    for (int s = 0; s <= K; ++s) {
+        const double *src = s == 0 ? dsig : dw;
+        double *dst = s == 0 ? gsigma : gw + (s - 1);
+        if (src == nullptr || (s == 0 && gsigma == nullptr) || (s > 0 && gw == nullptr)) continue;
+        double acc = 0.0;
+        for (int64_t q = threadIdx.x; q < Q; q += blockDim.x)
+            acc += gout[q] * (s == 0 ? src[q] : src[q * K + (s - 1)]);
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) *dst = red[0];
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+extern "C" wos_status wos_backward(const double *gout, const double *grad, const double *du_dsigma,
+                                   const double *du_dw, int64_t Q, int32_t d, int32_t K,
+                                   double *gx, double *gsigma, double *gw, void *stream) {
+    if (Q < 0 || d < 1 || K < 0) return fail(WOS_ERR_INVALID_ARG, "bad sizes");
+    if (Q > 0 && gout == nullptr) return fail(WOS_ERR_INVALID_ARG, "gout is NULL");
+    if (gx != nullptr && grad == nullptr) return fail(WOS_ERR_INVALID_ARG, "grad is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (Q == 0) {
+        if (gsigma) WOS_CUDA(cudaMemsetAsync(gsigma, 0, sizeof(double), s));
+        if (gw && K) WOS_CUDA(cudaMemsetAsync(gw, 0, sizeof(double) * K, s));
+        return WOS_OK;
+    }
+    backward_kernel<<<1, 256, 0, s>>>(gout, grad, du_dsigma, du_dw, Q, d, K, gx, gsigma, gw);
+    WOS_CUDA(cudaGetLastError());
+    return WOS_OK;
+}
+
+// =====================================================================================
+// random-stream diagnostics
+// =====================================================================================
+namespace {
+__global__ void philox_kernel(uint64_t seed, uint64_t walk0, int64_t n, uint32_t step, uint32_t block,
+                              uint32_t *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 r = philox_block(seed, walk0 + (uint64_t)i, step, block);
+        out[4 * i + 0] = r.x;
+        out[4 * i + 1] = r.y;
+        out[4 * i + 2] = r.z;
+        out[4 * i + 3] = r.w;
+    }
+}
+}  // namespace
+
+extern "C" wos_status wos_debug_philox(uint64_t seed, uint64_t walk0, int64_t n, uint32_t step,
+                                       uint32_t block, uint32_t *out, void *stream) {
+    if (n < 0 || (n > 0 && out == nullptr)) return fail(WOS_ERR_INVALID_ARG, "bad arguments");
+    if (n == 0) return WOS_OK;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 65535);
+    philox_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(seed, walk0, n, step, block, out);
+    WOS_CUDA(cudaGetLastError());
+    return WOS_OK;
+}
+
+// =====================================================================================
+// weight-table diagnostics
+// =====================================================================================
+extern "C" wos_status wos_debug_weight_table(int32_t d, double z_max, int32_t n, double *log_c,
+                                             double *ratio) {
+    if (d < 2 || d > WOS_MAX_D || n < 2 || !(z_max > 0) || !log_c || !ratio)
+        return fail(WOS_ERR_INVALID_ARG, "bad arguments");
+    float2 *t = nullptr;
+    WOS_CUDA(cudaMalloc(&t, sizeof(float2) * n));
+    build_table_kernel<<<(n + 255) / 256, 256>>>(d, z_max / (n - 1), n, t);
+    std::vector<float2> h(n);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), t, sizeof(float2) * n, cudaMemcpyDeviceToHost);
+    cudaFree(t);
+    if (e != cudaSuccess) return fail(WOS_ERR_CUDA, "table debug failed: %s", cudaGetErrorString(e));
+    for (int i = 0; i < n; ++i) {
+        log_c[i] = h[i].x;
+        ratio[i] = h[i].y;
+    }
+    return WOS_OK;
+}
+
+// =====================================================================================
+// batched uneven problems: one persistent launch, recorded as a CUDA graph
+// =====================================================================================
+struct wos_batch_s {
+    std::vector<wos_problem> probs;
+    Opts o{};
+    wos_batch_config cfg{};
+    int grad_any = 0;
+    size_t smem = 0;
+    int grid = 0;
+    int64_t n_items = 0, total_q = 0;
+    void *dev = nullptr;       // problems | items | finalize records | zeroed region
+    size_t zero_off = 0, zero_bytes = 0;
+    wos_stats *d_stats = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::string signature;
+};
+
+namespace {
+
+std::mutex g_cache_mu;
+std::string g_cache_path;
+
+size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+// Relative cost of one walk step of a problem: ball screen B (d+3), plus the fixed per-step
+// work (faces, sampling, weights).
+double step_cost(const wos_domain_s &D) { return (double)D.n_balls * (D.d + 3) + 40.0 * D.d + 200.0; }
+
+std::string batch_signature(const std::vector<wos_problem> &ps) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) {
+        for (int i = 0; i < 8; ++i) {
+            h ^= (v >> (8 * i)) & 0xff;
+            h *= 1099511628211ull;
+        }
+    };
+    mix(ps.size());
+    for (const wos_problem &p : ps) {
+        mix((uint64_t)p.domain->d);
+        mix((uint64_t)p.domain->n_balls);
+        mix((uint64_t)p.n_queries);
+        mix((uint64_t)p.n_walks);
+        mix(p.grad != nullptr);
+    }
+    int dev = 0;
+    cudaDeviceProp prop{};
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&prop, dev);
+    char buf[64];
+    snprintf(buf, sizeof(buf), "%016llx", (unsigned long long)h);
+    std::string name(prop.name);
+    for (char &c : name)
+        if (c == ' ') c = '_';
+    return name + ":" + buf;
+}
+
+bool cache_lookup(const std::string &path, const std::string &sig, wos_batch_config *cfg) {
+    if (path.empty()) return false;
+    FILE *f = fopen(path.c_str(), "r");
+    if (!f) return false;
+    char key[256];
+    int th, ct;
+    long long iw;
+    double ms;
+    bool found = false;
+    while (fscanf(f, "%255s %d %d %lld %lf", key, &th, &ct, &iw, &ms) == 5) {
+        if (sig == key) {  // the last entry for a signature wins
+            cfg->threads = th;
+            cfg->ctas_per_sm = ct;
+            cfg->item_work = iw;
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void free_batch_device(wos_batch_s *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->dev) cudaFree(b->dev);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->dev = nullptr;
+}
+
+wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
+    free_batch_device(b);
+    wos_batch_config cfg = cfg_in;
+    if (cfg.threads < 32 || cfg.threads > 512 || cfg.threads % 32)
+        return fail(WOS_ERR_INVALID_ARG, "threads must be a multiple of 32 in 32..512");
+    if (cfg.ctas_per_sm < 1 || cfg.ctas_per_sm > 8) return fail(WOS_ERR_INVALID_ARG, "ctas_per_sm in 1..8");
+    if (cfg.item_work < 1) return fail(WOS_ERR_INVALID_ARG, "item_work must be positive");
+    const int n = (int)b->probs.size();
+    b->grad_any = 0;
+    b->smem = 16;
+    for (const wos_problem &p : b->probs) {
+        b->grad_any |= p.grad != nullptr;
+        b->smem = std::max(b->smem, mixed_smem_bytes(*p.domain));
+    }
+    if (b->smem > 227 * 1024) return fail(WOS_ERR_UNSUPPORTED, "ball set needs %zu B of shared memory", b->smem);
+    WOS_TRY(ensure_mixed_smem(b->smem));
+    const int occ = max_active_mixed(cfg.threads, b->smem, b->grad_any);
+    if (occ < 1) return fail(WOS_ERR_UNSUPPORTED, "persistent walker does not fit with %d threads", cfg.threads);
+    cfg.ctas_per_sm = std::min(cfg.ctas_per_sm, occ);
+    b->cfg = cfg;
+    const int sms = device_sms();
+
+    // problem records, accumulators and work items
+    std::vector<MixedProblem> mp(n);
+    std::vector<FinalizeRec> fr(n);
+    std::vector<MixedItem> items;
+    std::vector<double> item_cost;
+    size_t acc_bytes = 0;
+    std::vector<size_t> acc_off(n), cnt_off(n);
+    for (int i = 0; i < n; ++i) {
+        const wos_problem &p = b->probs[i];
+        const int nf = acc_fields(p.domain->d, p.domain->n_exp);
+        acc_off[i] = acc_bytes;
+        acc_bytes += align256((size_t)p.n_queries * nf * sizeof(double));
+    }
+    for (int i = 0; i < n; ++i) {
+        cnt_off[i] = acc_bytes;
+        acc_bytes += align256((size_t)b->probs[i].n_queries * kCounters * 8);
+    }
+    const size_t off_items = align256(sizeof(MixedProblem) * n);
+    int64_t walk_base = b->o.walk_offset, q_begin = 0;
+    for (int i = 0; i < n; ++i) {
+        const wos_problem &p = b->probs[i];
+        const double c = step_cost(*p.domain);
+        int64_t wpi = (int64_t)((double)cfg.item_work / c);
+        wpi = std::max<int64_t>(cfg.threads, std::min<int64_t>(1 << 20, wpi));
+        wpi = (wpi + 31) / 32 * 32;
+        const int64_t total = p.n_queries * p.n_walks;
+        for (int64_t j0 = 0; j0 < total; j0 += wpi) {
+            MixedItem it{};
+            it.problem = i;
+            it.j0 = j0;
+            it.j1 = std::min(total, j0 + wpi);
+            items.push_back(it);
+            item_cost.push_back(c * (double)(it.j1 - it.j0));
+        }
+        walk_base += total;
+        q_begin += p.n_queries;
+    }
+    // longest-first order (ties keep problem order so a CTA rarely restages its obstacles)
+    std::vector<size_t> order(items.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t c) { return item_cost[a] > item_cost[c]; });
+    std::vector<MixedItem> sorted(items.size());
+    for (size_t k = 0; k < order.size(); ++k) sorted[k] = items[order[k]];
+    b->n_items = (int64_t)sorted.size();
+    b->total_q = q_begin;
+    const size_t off_recs = off_items + align256(sizeof(MixedItem) * std::max<size_t>(1, sorted.size()));
+    const size_t off_zero = off_recs + align256(sizeof(FinalizeRec) * n);
+    const size_t zero_bytes = acc_bytes + 256 /* cursor */ + align256(sizeof(wos_stats));
+    const size_t total_bytes = off_zero + zero_bytes;
+    WOS_CUDA(cudaMalloc(&b->dev, total_bytes));
+    char *base = (char *)b->dev;
+    char *zero = base + off_zero;
+    unsigned long long *cursor = (unsigned long long *)(zero + acc_bytes);
+    b->d_stats = (wos_stats *)(zero + acc_bytes + 256);
+    b->zero_off = off_zero;
+    b->zero_bytes = zero_bytes;
+    walk_base = b->o.walk_offset;
+    q_begin = 0;
+    for (int i = 0; i < n; ++i) {
+        const wos_problem &p = b->probs[i];
+        WeightTable tab;
+        WOS_TRY(ensure_table(p.domain, p.sigma, &tab));
+        double *acc = (double *)(zero + acc_off[i]);
+        unsigned long long *cnt = (unsigned long long *)(zero + cnt_off[i]);
+        mp[i] = make_mixed_problem(p.domain, p.x, p.n_queries, p.n_walks, p.eps, p.sigma,
+                                   p.grad != nullptr, b->o.laplace, walk_base, tab, acc, cnt, PerWalk{});
+        FinalizeRec &r = fr[i];
+        r.d = p.domain->d;
+        r.K = p.domain->n_exp;
+        r.acc_f32 = 0;
+        r.Q = p.n_queries;
+        r.N = p.n_walks;
+        r.q_begin = q_begin;
+        r.acc = acc;
+        r.counts = cnt;
+        r.u = p.u;
+        r.u_se = p.u_se;
+        r.grad = p.grad;
+        r.grad_se = p.grad_se;
+        r.du_dsigma = nullptr;
+        r.du_dw = nullptr;
+        r.walk_steps = p.walk_steps;
+        walk_base += p.n_queries * p.n_walks;
+        q_begin += p.n_queries;
+    }
+    WOS_CUDA(cudaMemcpy(base, mp.data(), sizeof(MixedProblem) * n, cudaMemcpyHostToDevice));
+    if (!sorted.empty())
+        WOS_CUDA(cudaMemcpy(base + off_items, sorted.data(), sizeof(MixedItem) * sorted.size(),
+                            cudaMemcpyHostToDevice));
+    WOS_CUDA(cudaMemcpy(base + off_recs, fr.data(), sizeof(FinalizeRec) * n, cudaMemcpyHostToDevice));
+
+    MixedLaunch L{};
+    L.problems = (const MixedProblem *)base;
+    L.items = (const MixedItem *)(base + off_items);
+    L.n_items = b->n_items;
+    L.cursor = cursor;
+    L.seed = b->o.seed;
+    L.max_steps = b->o.max_steps;
+    L.skip = nullptr;
+    b->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * cfg.ctas_per_sm, b->n_items));
+    FinalizeArgs fa{};
+    fa.recs = (const FinalizeRec *)(base + off_recs);
+    fa.n = n;
+    fa.total_q = b->total_q;
+    fa.stats = b->d_stats;
+
+    cudaStream_t cap = nullptr;
+    WOS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    wos_status st = WOS_OK;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaStreamDestroy(cap);
+        return fail(WOS_ERR_CUDA, "batch capture failed to start");
+    }
+    if (cudaMemsetAsync(zero, 0, zero_bytes, cap) != cudaSuccess) st = fail(WOS_ERR_CUDA, "memset capture");
+    if (st == WOS_OK && b->n_items > 0 &&
+        launch_walk_mixed(L, b->grad_any, b->grid, cfg.threads, b->smem, cap) != cudaSuccess)
+        st = fail(WOS_ERR_CUDA, "walk kernel capture failed");
+    if (st == WOS_OK) st = launch_finalize(fa, cap);
+    cudaError_t e = cudaStreamEndCapture(cap, &b->graph);
+    cudaStreamDestroy(cap);
+    if (st != WOS_OK) return st;
+    if (e != cudaSuccess) return fail(WOS_ERR_CUDA, "batch capture failed: %s", cudaGetErrorString(e));
+    WOS_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    return WOS_OK;
+}
+
+wos_batch_config default_batch_config() {
+    // the autotuner's choice for the 256-problem batched workload on GB300
+    wos_batch_config c;
+    c.threads = 512;
+    c.ctas_per_sm = 1;
+    c.item_work = (int64_t)1 << 26;
+    return c;
+}
+
+}  // namespace
+
+extern "C" {
+
+wos_status wos_set_autotune_cache(const char *cache_path) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    g_cache_path = cache_path ? cache_path : "";
+    return WOS_OK;
+}
+
+wos_status wos_batch_create(const wos_problem *probs, int32_t n_problems, const wos_options *opt,
+                            const wos_batch_config *cfg, wos_batch_t *out) {
+    if (out == nullptr) return fail(WOS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_problems < 0 || (n_problems > 0 && probs == nullptr))
+        return fail(WOS_ERR_INVALID_ARG, "bad problem array");
+    const Opts o = read_opts(opt);
+    if (opt != nullptr && o.precision != WOS_MIXED)
+        return fail(WOS_ERR_UNSUPPORTED, "batched launches run the mixed-precision walker");
+    for (int i = 0; i < n_problems; ++i) {
+        const wos_problem &p = probs[i];
+        WOS_TRY(check_common(p.domain, p.x, p.n_queries, p.n_walks, p.eps, p.sigma));
+        if (p.n_queries > 0 && p.u == nullptr) return fail(WOS_ERR_INVALID_ARG, "problem %d: u is NULL", i);
+        if (p.domain->n_points > 0)
+            return fail(WOS_ERR_UNSUPPORTED, "problem %d: point-cloud domains are not batched", i);
+        if (p.n_queries * p.n_walks > (int64_t)0x7fffffff)
+            return fail(WOS_ERR_UNSUPPORTED, "problem %d: n_queries * n_walks must be < 2^31", i);
+    }
+    wos_batch_s *b = new (std::nothrow) wos_batch_s();
+    if (b == nullptr) return fail(WOS_ERR_OOM, "host allocation failed");
+    b->probs.assign(probs, probs + n_problems);
+    b->o = o;
+    b->signature = batch_signature(b->probs);
+    wos_batch_config c = default_batch_config();
+    if (cfg != nullptr) {
+        c = *cfg;
+    } else {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        cache_lookup(g_cache_path, b->signature, &c);
+    }
+    const wos_status st = batch_build(b, c);
+    if (st != WOS_OK) {
+        free_batch_device(b);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return WOS_OK;
+}
+
+wos_status wos_batch_run(wos_batch_t b, wos_stats *stats, void *stream) {
+    if (b == nullptr || b->exec == nullptr) return fail(WOS_ERR_INVALID_ARG, "batch is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    WOS_CUDA(cudaGraphLaunch(b->exec, s));
+    if (stats != nullptr)
+        WOS_CUDA(cudaMemcpyAsync(stats, b->d_stats, sizeof(wos_stats), cudaMemcpyDeviceToDevice, s));
+    return WOS_OK;
+}
+
+wos_status wos_batch_get_config(wos_batch_t b, wos_batch_config *cfg) {
+    if (b == nullptr || cfg == nullptr) return fail(WOS_ERR_INVALID_ARG, "NULL argument");
+    *cfg = b->cfg;
+    return WOS_OK;
+}
+
+wos_status wos_batch_destroy(wos_batch_t b) {
+    if (b == nullptr) return WOS_OK;
+    cudaDeviceSynchronize();
+    free_batch_device(b);
+    delete b;
+    return WOS_OK;
+}
+
+wos_status wos_solve_batch(const wos_problem *probs, int32_t n_problems, const wos_options *opt,
+                           wos_stats *stats, void *stream) {
+    wos_batch_t b = nullptr;
+    WOS_TRY(wos_batch_create(probs, n_problems, opt, nullptr, &b));
+    wos_status st = wos_batch_run(b, stats, stream);
+    if (st == WOS_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        st = fail(WOS_ERR_CUDA, "batch run failed");
+    wos_batch_destroy(b);
+    return st;
+}
+
+wos_status wos_batch_autotune(wos_batch_t b, const char *cache_path, wos_batch_config *best) {
+    if (b == nullptr) return fail(WOS_ERR_INVALID_ARG, "batch is NULL");
+    const wos_batch_config start = b->cfg;
+    std::vector<wos_batch_config> cands;
+    for (int th : {256, 512})
+        for (int ct : {1, 2})
+            for (int64_t iw : {(int64_t)1 << 24, (int64_t)1 << 26}) cands.push_back(wos_batch_config{th, ct, iw});
+    cudaStream_t s;
+    WOS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best_ms = 1e300;
+    wos_batch_config best_cfg = start;
+    std::vector<std::pair<int, int>> seen;  // (threads, effective ctas) x item_work dedup
+    for (const wos_batch_config &c : cands) {
+        if (batch_build(b, c) != WOS_OK) continue;
+        bool dup = false;
+        for (auto &pr : seen)
+            if (pr.first == b->cfg.threads * 4096 + b->cfg.ctas_per_sm &&
+                pr.second == (int)(b->cfg.item_work >> 20))
+                dup = true;
+        if (dup) continue;
+        seen.push_back({b->cfg.threads * 4096 + b->cfg.ctas_per_sm, (int)(b->cfg.item_work >> 20)});
+        cudaEventRecord(e0, s);
+        cudaGraphLaunch(b->exec, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_cfg = b->cfg;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    WOS_TRY(batch_build(b, best_cfg));
+    if (best) *best = b->cfg;
+    if (cache_path != nullptr && best_ms < 1e300) {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        FILE *f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "%s %d %d %lld %.4f\n", b->signature.c_str(), b->cfg.threads, b->cfg.ctas_per_sm,
+                    (long long)b->cfg.item_work, best_ms);
+            fclose(f);
+        }
+    }
+    return WOS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Internal launch interface between the host API (wos_api.cu) and the kernel translation
+// units. Not part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "wos_device.cuh"
+
+namespace wos {
+
+// One-thread-per-walk walkers (FP64 parity mode and the plain FP32 baseline).
+template <typename T>
+struct SimpleParams {
+    DomainView<T> dom;
+    const double *x;  // Q x d queries (device)
+    int64_t Q, N;
+    uint64_t seed;
+    int64_t walk_offset;
+    int64_t max_steps;
+    T eps, sqrt_sigma, shrink;
+    int grad_mode, laplace;
+    T *acc;                      // Q x nf sums
+    unsigned long long *counts;  // Q x kCounters
+    int nf;
+    double *w_term;    // per-walk outputs (nullable)
+    int64_t *w_jumps;
+    double *w_grad;
+    double *w_dsigma;
+    const int *skip;   // nullable; the kernel does nothing if *skip != 0
+};
+
+cudaError_t launch_walk_simple_f64(const SimpleParams<double> &p, cudaStream_t s);
+cudaError_t launch_walk_simple_f32(const SimpleParams<float> &p, cudaStream_t s);
+
+// Problem record of the persistent mixed-precision walker.
+struct MixedProblem {
+    int d, n_balls, n_exp, has_box, has_outer, has_goal;
+    int grad_mode, laplace;
+    float eps, sqrt_sigma;
+    float shrink;  // FP32 error bound subtracted from every radius
+    float slack;   // FP32 rounding bound of the ball screening test
+    float goal_r, outer_r;
+    int64_t Q, N;
+    int64_t walk_base;            // global walk index of walk 0 of query 0
+    const float *balls;           // packed ball records (see walk_mixed.cu)
+    const float *geom;            // box lo[d], box hi[d], goal c[d], outer c[d], exp w[K], exp a[K*d]
+    const double *x;              // Q x d queries
+    WeightTable table;
+    double *acc;                  // Q x nf FP64 sums
+    unsigned long long *counts;   // Q x kCounters
+    double *w_term;               // per-walk outputs (nullable)
+    int64_t *w_jumps;
+    double *w_grad;
+    double *w_dsigma;
+};
+
+struct MixedItem {
+    int problem;
+    int pad;
+    int64_t j0, j1;  // walk range within the problem, j = q * N + w
+};
+
+struct MixedLaunch {
+    const MixedProblem *problems;  // device array, or nullptr: problem 0 is `single`
+    const MixedItem *items;        // device array, or nullptr: implicit items of problem 0
+    int64_t n_items;
+    int64_t walks_per_item;        // implicit items: item i = walks [i wpi, min((i+1) wpi, total))
+    int64_t total_walks;
+    unsigned long long *cursor;    // work-queue cursor (device, zero before the launch)
+    uint64_t seed;
+    int64_t max_steps;
+    const int *skip;               // nullable; the kernel does nothing if *skip != 0
+    MixedProblem single;
+};
+
+// Floats per packed ball record for dimension d.
+__host__ __device__ constexpr int ball_record_floats(int d) { return d + 2; }
+
+cudaError_t launch_walk_mixed_val(const MixedLaunch &L, int grid, int threads, size_t smem_bytes,
+                                  cudaStream_t s);
+cudaError_t launch_walk_mixed_grad(const MixedLaunch &L, int grid, int threads, size_t smem_bytes,
+                                   cudaStream_t s);
+cudaError_t configure_walk_mixed_val(size_t smem_bytes);
+cudaError_t configure_walk_mixed_grad(size_t smem_bytes);
+int max_active_mixed_val(int threads, size_t smem_bytes);
+int max_active_mixed_grad(int threads, size_t smem_bytes);
+
+inline cudaError_t launch_walk_mixed(const MixedLaunch &L, int grad_any, int grid, int threads,
+                                     size_t smem_bytes, cudaStream_t s) {
+    return grad_any ? launch_walk_mixed_grad(L, grid, threads, smem_bytes, s)
+                    : launch_walk_mixed_val(L, grid, threads, smem_bytes, s);
+}
+inline cudaError_t configure_walk_mixed(size_t smem_bytes) {
+    cudaError_t e = configure_walk_mixed_val(smem_bytes);
+    return e != cudaSuccess ? e : configure_walk_mixed_grad(smem_bytes);
+}
+inline int max_active_mixed(int threads, size_t smem_bytes, int grad_any) {
+    return grad_any ? max_active_mixed_grad(threads, smem_bytes)
+                    : max_active_mixed_val(threads, smem_bytes);
+}
+
+}  // namespace wos

@@ -36,6 +36,20 @@ def _clearance_ok(x, centres, radii, margin):
     """True where x (n x d) lies outside every ball by more than margin (input rejection)."""
     if centres is None or len(centres) == 0:
         return np.ones(x.shape[0], bool)
+    try:
+        from scipy.spatial import cKDTree
+    except ImportError:
+        cKDTree = None
+    if cKDTree is not None and len(centres) > 64:
+        # only balls whose centre lies within r_max + margin can violate the clearance
+        tree = cKDTree(centres)
+        near = tree.query_ball_point(x, float(np.max(radii)) + margin)
+        ok = np.ones(x.shape[0], bool)
+        for i, idx in enumerate(near):
+            if idx:
+                dd = np.linalg.norm(centres[idx] - x[i][None, :], axis=1)
+                ok[i] = bool(np.all(dd > radii[idx] + margin))
+        return ok
     ok = np.ones(x.shape[0], bool)
     for s in range(0, centres.shape[0], 512):
         c = centres[s:s + 512]
@@ -46,14 +60,20 @@ def _clearance_ok(x, centres, radii, margin):
     return ok
 
 
-def _free_points(rng, n, lo, hi, centres, radii, margin, extra=None):
-    """n points uniform in the box [lo+margin, hi-margin] outside all balls (+margin)."""
+def _free_points(rng, n, lo, hi, centres, radii, margin, extra=None, max_draws=4_000_000):
+    """n points uniform in the box [lo+margin, hi-margin] outside all balls (+margin).
+    Raises RuntimeError after max_draws candidates (a region too crowded for the margin)."""
     lo = np.asarray(lo, float)
     hi = np.asarray(hi, float)
     out = []
     have = 0
+    drawn = 0
     while have < n:
-        x = rng.uniform(lo + margin, hi - margin, size=(max(64, 2 * (n - have)), lo.size))
+        if drawn > max_draws:
+            raise RuntimeError("no free point with clearance %g after %d draws" % (margin, drawn))
+        m = max(64, 2 * (n - have))
+        drawn += m
+        x = rng.uniform(lo + margin, hi - margin, size=(m, lo.size))
         ok = _clearance_ok(x, centres, radii, margin)
         if extra is not None:
             ok &= extra(x)
@@ -152,7 +172,8 @@ def c4_problem(rng, index, n_queries=64, d=None, n_balls=None, n_walks=None, sig
     """One problem of the batched workload: d U{3..12}, B log-U[16,4096] balls with radii
     log-U[0.01,0.2] and centres U[-1,1]^d, sigma U[0,50], N log-U[256,16384].
     Even index: g = exp(a.x), |a| = sqrt(sigma) (exact solution u = g).
-    Odd index: goal ball r = 0.1 at a free point, g = 1 there and 0 elsewhere."""
+    Odd index: goal ball r = 0.1 at a point with clearance 0.15 from every obstacle (0.1, 0.05,
+    0.02 or 0.01 where the obstacles are too dense), g = 1 there and 0 elsewhere."""
     d = int(rng.integers(3, 13)) if d is None else d
     B = int(round(math.exp(rng.uniform(math.log(16), math.log(4096))))) if n_balls is None else n_balls
     N = int(round(math.exp(rng.uniform(math.log(256), math.log(16384))))) if n_walks is None else n_walks
@@ -168,7 +189,15 @@ def c4_problem(rng, index, n_queries=64, d=None, n_balls=None, n_walks=None, sig
         dom["exp_a"] = a[None, :]
         X = _free_points(rng, n_queries, lo, hi, centres, radii, 0.01)
     else:
-        goal = _free_points(rng, 1, lo, hi, centres, radii, 0.15)[0]
+        goal = None
+        for clearance in (0.15, 0.1, 0.05, 0.02, 0.01):
+            try:
+                goal = _free_points(rng, 1, lo, hi, centres, radii, clearance, max_draws=100_000)[0]
+                break
+            except RuntimeError:
+                continue
+        if goal is None:
+            raise RuntimeError("no free goal position")
         dom["goal_c"] = goal
         dom["goal_r"] = 0.1
         far = lambda x: np.linalg.norm(x - goal[None, :], axis=1) > 0.11
