@@ -257,6 +257,36 @@ wos_status wos_batch_autotune(wos_batch_t batch, const char *cache_path, wos_bat
 /* Sets the cache file consulted by wos_batch_create when cfg is NULL (NULL: no cache). */
 wos_status wos_set_autotune_cache(const char *cache_path);
 
+/* ---- allocation-free estimate ------------------------------------------------------------- */
+
+#define WOS_NOALLOC_SCRATCH_BYTES (1u << 20) /* static device scratch of wos_solve_noalloc */
+
+/*
+ * wos_solve_noalloc: the estimate of wos_solve (u and its standard error per query) for
+ * callers that cannot allocate device memory inside a call -- a control loop with a hard
+ * deadline, where cudaMalloc/cudaFree can block on the driver's device-wide allocator and
+ * synchronise the GPU, or a host application that has handed the device memory to its own
+ * pool and forbids allocations from libraries. The paper has no counterpart: this is a
+ * property of the library interface, not of the method.
+ * It allocates nothing: the caller passes x, u, u_se and stats as for wos_solve, and the
+ * per-query FP64 sums and counters live in one static device array of
+ * WOS_NOALLOC_SCRATCH_BYTES (1 MiB) that every GPU which loads the library holds until the
+ * process exits. Each query needs e (3 + 2d + n_exp) + 32 bytes of it, e = 8 for WOS_FP64 and
+ * 4 for WOS_FP32_PLAIN: about 10900 queries for d = 2 with one exponential term in FP64, 3360
+ * for d = 12 with eight.
+ * Precision: WOS_FP64 or WOS_FP32_PLAIN (the one-thread-per-walk walker); WOS_MIXED needs its
+ * weight table, which is allocated, and is rejected.
+ * The first call on a device looks up the device address of the array (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture. Each call clears
+ * the array on its stream and then reuses it, and the array keeps the last call's contents:
+ * calls whose work overlaps on the GPU (other streams, other host threads) race on it and
+ * must be serialised by the caller.
+ * Errors: as wos_solve; INVALID_ARG if Q exceeds the limit; UNSUPPORTED for WOS_MIXED.
+ */
+wos_status wos_solve_noalloc(wos_domain_t dom, const wos_options *opt, const double *x, int64_t Q,
+                             int64_t n_walks, double eps, double sigma, double *u, double *u_se,
+                             wos_stats *stats, void *stream);
+
 /* ---- diagnostics ------------------------------------------------------------------------ */
 
 const char *wos_status_string(wos_status s);

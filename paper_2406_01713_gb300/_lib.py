@@ -95,6 +95,8 @@ SIGNATURES = {
                                        _VP, _VP]),
     "wos_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_char_p, ctypes.POINTER(BatchConfig)]),
     "wos_set_autotune_cache": (ctypes.c_int, [ctypes.c_char_p]),
+    "wos_solve_noalloc": (ctypes.c_int, [_VP, ctypes.POINTER(Options), _VP, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP]),
     "wos_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "wos_last_error": (ctypes.c_char_p, []),
     "wos_debug_weight_table": (ctypes.c_int, [ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _PD, _PD]),

@@ -1483,3 +1483,80 @@ wos_status wos_batch_autotune(wos_batch_t b, const char *cache_path, wos_batch_c
 }
 
 }  // extern "C"
+
+// =====================================================================================
+// allocation-free estimate: scratch in a static device array
+// =====================================================================================
+namespace {
+
+// Per-query FP64 (or FP32) sums and int64 counters of wos_solve_noalloc. Every GPU that loads
+// the library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[WOS_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the array for the current device, looked up once per device with that
+// device current (host code cannot use the symbol itself as a device address).
+wos_status noalloc_scratch(void **out) {
+    int dev = 0;
+    WOS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(WOS_ERR_UNSUPPORTED, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_addr[dev] == nullptr) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr)
+            return fail(WOS_ERR_CUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return WOS_OK;
+}
+
+}  // namespace
+
+extern "C" wos_status wos_solve_noalloc(wos_domain_t dom, const wos_options *opt, const double *x,
+                                        int64_t Q, int64_t n_walks, double eps, double sigma,
+                                        double *u, double *u_se, wos_stats *stats, void *stream) {
+    WOS_TRY(check_common(dom, x, Q, n_walks, eps, sigma));
+    if (Q > 0 && u == nullptr) return fail(WOS_ERR_INVALID_ARG, "u is NULL");
+    const Opts o = read_opts(opt);
+    if (o.precision != WOS_FP64 && o.precision != WOS_FP32_PLAIN)
+        return fail(WOS_ERR_UNSUPPORTED,
+                    "wos_solve_noalloc runs WOS_FP64 or WOS_FP32_PLAIN (mixed precision allocates tables)");
+    const int nf = acc_fields(dom->d, dom->n_exp);
+    const size_t need = scratch_bytes(o.precision, Q, nf);
+    if (need > (size_t)WOS_NOALLOC_SCRATCH_BYTES)
+        return fail(WOS_ERR_INVALID_ARG,
+                    "Q = %lld needs %zu bytes of scratch; the static array holds %u (at most %lld queries)",
+                    (long long)Q, need, (unsigned)WOS_NOALLOC_SCRATCH_BYTES,
+                    (long long)(((size_t)WOS_NOALLOC_SCRATCH_BYTES - 768) /
+                                ((o.precision == WOS_FP32_PLAIN ? 4 : 8) * (size_t)nf + 8 * kCounters)));
+    cudaStream_t s = (cudaStream_t)stream;
+    void *base = nullptr;
+    WOS_TRY(noalloc_scratch(&base));
+    if (stats != nullptr) WOS_CUDA(cudaMemsetAsync(stats, 0, sizeof(wos_stats), s));
+    if (Q == 0) return WOS_OK;
+    WOS_CUDA(cudaMemsetAsync(base, 0, need, s));  // the array keeps the previous call's sums
+    const Scratch sc = carve_scratch(base, o.precision, Q, nf);
+    WOS_TRY(launch_walkers(dom, o, x, Q, n_walks, eps, sigma, 0, sc, PerWalk{}, nullptr, s));
+    FinalizeArgs a{};
+    a.recs = nullptr;
+    a.n = 1;
+    a.total_q = Q;
+    a.stats = stats;
+    FinalizeRec &r = a.single;
+    r.d = dom->d;
+    r.K = dom->n_exp;
+    r.acc_f32 = o.precision == WOS_FP32_PLAIN;
+    r.Q = Q;
+    r.N = n_walks;
+    r.q_begin = 0;
+    r.acc = sc.acc;
+    r.counts = sc.counts;
+    r.u = u;
+    r.u_se = u_se;
+    return launch_finalize(a, s);
+}
