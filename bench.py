@@ -46,6 +46,8 @@ def parse():
                    help="leading problems of the workload (fewer: the small profiling case)")
     p.add_argument("--scale-walks", type=float, default=1.0,
                    help="scale of the walk counts (below 1: the small profiling case)")
+    p.add_argument("--launch", default=None,
+                   help="explicit launch shape threads,ctas_per_sm,item_work (skips the autotuner)")
     return p.parse_args()
 
 
@@ -204,13 +206,20 @@ def main():
     doms = [W.Domain(p["domain"]) for p in probs]
     workload = WORKLOAD if (args.problems == 256 and args.scale_walks == 1.0) else (
         "SMALL CASE (profiling): first %d problems of [%s], walks x %g" % (args.problems, WORKLOAD, args.scale_walks))
+    launch = None
+    if args.launch:
+        th, ct, iw = (int(v) for v in args.launch.split(","))
+        launch = {"threads": th, "ctas_per_sm": ct, "item_work": iw}
+        args.no_autotune = True
     batch = W.Batch([{"domain": d, "x": p["X"], "n_walks": p["n_walks"], "eps": p["eps"], "sigma": p["sigma"],
-                      "grad": True} for d, p in zip(doms, probs)], seed=w["seed"] + 1000003 * rank)
+                      "grad": True} for d, p in zip(doms, probs)], seed=w["seed"] + 1000003 * rank, config=launch)
     cache = os.environ.get("WOS_AUTOTUNE_CACHE",
                            os.path.join(ROOT, "paper_2406_01713_gb300", "csrc", "_build", "autotune_cache.txt"))
     log("workload ready: %d problems" % len(probs))
     tuned = batch.autotune(cache) if not args.no_autotune else batch.config()
     log("launch shape", tuned)
+    if not args.no_autotune and os.path.exists(cache):
+        log("autotune candidates:\n" + "".join(l for l in open(cache) if l.startswith("#"))[-2000:])
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):

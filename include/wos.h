@@ -218,7 +218,7 @@ typedef struct {
 /* Launch shape of the persistent kernel. A NULL config means "autotuned": the cached best for
  * this device and problem mix if any, else the built-in default. */
 typedef struct {
-    int32_t threads;         /* threads per CTA: 128..1024, multiple of 32 */
+    int32_t threads;         /* threads per CTA: 32..768, multiple of 32 */
     int32_t ctas_per_sm;     /* resident CTAs per SM requested (1..8) */
     int64_t item_work;       /* target work per queue item, in ball-dimension units */
 } wos_batch_config;
@@ -302,6 +302,14 @@ wos_status wos_debug_weight_table(int32_t d, double z_max, int32_t n, double *lo
  * (walk_lo, walk_hi, step, block). For bitwise checks of the random-stream contract. */
 wos_status wos_debug_philox(uint64_t seed, uint64_t walk0, int64_t n, uint32_t step,
                             uint32_t block, uint32_t *out, void *stream);
+
+/* Writes, for each point x[q] (Q x d device doubles), the distance bound the tensor-core
+ * point-cloud walker uses there -- min over the FP32 refinement of its best 32-point candidate
+ * chunk, the second-best chunk minus the BF16 error bound, and the other components -- to
+ * radius[q] (device doubles). Sec. VII-A point-set distance; for checks that the bound never
+ * exceeds the exact distance. Errors: UNSUPPORTED without a mixed-precision point set. */
+wos_status wos_debug_pointcloud_radius(wos_domain_t dom, const double *x, int64_t Q, double *radius,
+                                       void *stream);
 
 #ifdef __cplusplus
 }

@@ -100,6 +100,7 @@ SIGNATURES = {
     "wos_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "wos_last_error": (ctypes.c_char_p, []),
     "wos_debug_weight_table": (ctypes.c_int, [ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _PD, _PD]),
+    "wos_debug_pointcloud_radius": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP]),
     "wos_debug_philox": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32,
                                         ctypes.c_uint32, _VP, _VP]),
 }

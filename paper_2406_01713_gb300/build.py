@@ -15,8 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(CSRC, "_build")
 LIB = os.path.join(HERE, "libwos.so")
-SOURCES = ["wos_api.cu", "walk_simple.cu", "walk_mixed_val.cu", "walk_mixed_grad.cu",
-           "pointcloud.cu"]
+SOURCES = ["wos_api.cu", "walk_simple.cu", "walk_mixed_val512.cu", "walk_mixed_val768.cu",
+           "walk_mixed_grad512.cu", "walk_mixed_grad768.cu", "pointcloud.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

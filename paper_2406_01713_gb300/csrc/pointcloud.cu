@@ -1,0 +1,697 @@
+// Point-cloud Walk-on-Spheres walker on the 5th-generation tensor cores (sm_103a).
+//
+// Distance to an obstacle point set (Sec. VII-A, d(q) = min_i |q - p_i|) for 128 walkers at a
+// time: the contraction D_wi = |p_i|^2 - 2 x_w . p_i runs as tcgen05.mma (BF16 inputs, FP32
+// accumulation in tensor memory) over point tiles that TMA streams into shared memory; the
+// walker warps read their rows back with tcgen05.ld and keep, per walker, the best and the
+// second-best 32-point chunk. The best chunk is then recomputed exactly in FP32 and the other
+// points are bounded from below by the second-best chunk minus a proven error bound, so the
+// radius never exceeds the true distance (no sphere leaves the domain).
+//
+// BF16 split: x = x_h + x_l and -2p = q_h + q_l (each a BF16), |p|^2 = n_h + n_l; the walker
+// row [x_h, x_h, x_l, 1, 1] times the point row [q_h, q_l, q_h, n_h, n_l] gives
+// |p|^2 - 2 x.p up to the dropped x_l q_l term and FP32 accumulation (3d + 2 <= 32 = K).
+//
+// CTA: warps 0-3 own one walker per thread (TMEM lanes 0..127); warp 4, lane 0, issues the
+// TMA loads and the MMAs. Every wait on an mbarrier is bounded by a clock budget; a timeout
+// sets the launch's status word and every thread leaves through the same teardown, which
+// waits for the issued MMAs and frees the tensor memory.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "walk_mixed.cuh"
+
+namespace wos {
+namespace pc {
+
+constexpr int kRows = 128;       // walkers per CTA = MMA M = TMEM lanes
+constexpr int kTileN = 128;      // points per tile = MMA N
+constexpr int kK = 32;           // padded contraction length (3d + 2 <= 32)
+constexpr int kStages = 6;       // point-tile ring in shared memory
+constexpr int kAhead = 4;        // tiles loaded ahead of the MMA issue point
+constexpr int kChunk = 32;       // candidate chunk (columns)
+constexpr int kWalkerThreads = 128;
+constexpr int kThreads = kWalkerThreads + 32;
+constexpr uint32_t kTileBytes = kTileN * kK * 2;
+constexpr uint32_t kABytes = kRows * kK * 2;
+constexpr uint32_t kTmemCols = 2 * kTileN;
+constexpr long long kWaitBudget = 4000000000ll;  // clock cycles (~2 s) before a wait gives up
+
+// Core-matrix layout (8 rows x 16 bytes), K-major, no swizzle: element (r, k) of a
+// rows x kK BF16 operand sits at byte (r/8) SBO + (k/8) LBO + (r%8) 16 + (k%8) 2.
+constexpr uint32_t kLBO = 128;               // to the next core matrix along K
+constexpr uint32_t kSBO = (kK / 8) * 128;    // to the next group of 8 rows
+
+// tcgen05 instruction descriptor, kind::f16: D = F32 (bits 4-5), A = B = BF16 (7-9, 10-12),
+// both K-major (15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
+                            ((uint32_t)(kRows >> 4) << 24);
+
+struct Launch {
+    CUtensorMap tmap;             // point tiles: 2D, 64 BF16 wide, 64 rows per tile
+    MixedProblem P;
+    const float *pts32;           // padded FP32 points, n_tiles * 128 x d
+    int n_tiles;
+    float delta;                  // bound of |D~ - D| (squared-distance units)
+    unsigned long long *cursor;   // global walk counter
+    int *status;                  // nonzero: a wait timed out
+    unsigned long long *shrinks;  // steps whose radius came from the bound
+    uint64_t seed;
+    int64_t max_steps;
+    int64_t total_walks;
+    double *radius_out;  // nullable: distance bound at each walk's start (diagnostics)
+};
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((kLBO >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((kSBO >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of tcgen05; base offset 0, no swizzle
+    return d;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+struct Shared {
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    uint64_t a_ready;
+    uint64_t drain;
+    uint32_t tmem_base;
+    volatile int abort_flag;
+    volatile int stop;
+};
+
+// Bounded wait: false if the budget ran out or another thread aborted.
+__device__ __forceinline__ bool wait_bar(Shared &S, uint64_t *b, uint32_t parity, int *status) {
+    if (mbar_test(b, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_test(b, parity)) return true;
+        if (S.abort_flag) return false;
+        if (clock64() - t0 > kWaitBudget) {
+            S.abort_flag = 1;
+            atomicOr(status, 1);
+            return false;
+        }
+    }
+}
+
+// Warp-uniform bounded wait for the walker warps: lane 0 polls, every lane gets the result.
+__device__ __forceinline__ bool warp_wait_bar(Shared &S, uint64_t *b, uint32_t parity, int *status) {
+    int ok = 0;
+    if ((threadIdx.x & 31) == 0) ok = wait_bar(S, b, parity, status) ? 1 : 0;
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap *map, int tile, uint64_t *bar) {
+    const int c0 = 0, c1 = tile * (kTileBytes / 128);
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(su32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+// 128 accumulator columns of this thread's TMEM lane, loaded and waited for in one step.
+__device__ __forceinline__ void tmem_row128(uint32_t taddr, float (&v)[kTileN]) {
+    uint32_t r[kTileN];
+#define R8(i) "=r"(r[i]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), "=r"(r[i + 4]), "=r"(r[i + 5]), "=r"(r[i + 6]), "=r"(r[i + 7])
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x128.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%"
+        "28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,"
+        "%55,%56,%57,%58,%59,%60,%61,%62,%63,%64,%65,%66,%67,%68,%69,%70,%71,%72,%73,%74,%75,%76,%77,%78,%79,%80,%81,"
+        "%82,%83,%84,%85,%86,%87,%88,%89,%90,%91,%92,%93,%94,%95,%96,%97,%98,%99,%100,%101,%102,%103,%104,%105,%106,"
+        "%107,%108,%109,%110,%111,%112,%113,%114,%115,%116,%117,%118,%119,%120,%121,%122,%123,%124,%125,%126,%127}, "
+        "[%128];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : R8(0), R8(8), R8(16), R8(24), R8(32), R8(40), R8(48), R8(56), R8(64), R8(72), R8(80), R8(88), R8(96),
+          R8(104), R8(112), R8(120)
+        : "r"(taddr)
+        : "memory");
+#undef R8
+#pragma unroll
+    for (int i = 0; i < kTileN; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float min32(const float *v) {
+    float m[11];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) m[i] = fmin3(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+    m[10] = fminf(v[30], v[31]);
+    const float a = fmin3(m[0], m[1], m[2]), b = fmin3(m[3], m[4], m[5]), c = fmin3(m[6], m[7], m[8]);
+    return fmin3(fmin3(a, b, c), m[9], m[10]);
+}
+
+// Writes this walker's A row (BF16 split of x; zeros for an idle lane).
+template <int D>
+__device__ __forceinline__ void write_row(unsigned char *A, int r, const float (&x)[D], bool active) {
+    __nv_bfloat16 row[kK];
+#pragma unroll
+    for (int k = 0; k < kK; ++k) row[k] = __float2bfloat16_rn(0.f);
+    if (active) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(x[j]);
+            const __nv_bfloat16 l = __float2bfloat16_rn(x[j] - __bfloat162float(h));
+            row[j] = h;
+            row[D + j] = h;
+            row[2 * D + j] = l;
+        }
+        row[3 * D] = __float2bfloat16_rn(1.f);
+        row[3 * D + 1] = __float2bfloat16_rn(1.f);
+    }
+#pragma unroll
+    for (int kc = 0; kc < kK / 8; ++kc) {
+        const uint32_t off = (r / 8) * kSBO + kc * kLBO + (r % 8) * 16;
+        *reinterpret_cast<uint4 *>(A + off) = *reinterpret_cast<const uint4 *>(row + 8 * kc);
+    }
+}
+
+template <int D, bool GRAD>
+__global__ void __launch_bounds__(kThreads, 2) pointcloud_kernel(const __grid_constant__ Launch L) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ Shared S;
+    __shared__ float geom_s[4 * kMaxD + kMaxExp + kMaxExp * kMaxD];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char *A = base;
+    unsigned char *Bst = base + kABytes;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const MixedProblem &P = L.P;
+
+    for (int i = threadIdx.x; i < 4 * D + kMaxExp + kMaxExp * D; i += blockDim.x) geom_s[i] = P.geom[i];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&S.full[s], 1);
+            mbar_init(&S.empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&S.tfull[b], 1);
+            mbar_init(&S.tempty[b], 4);
+        }
+        mbar_init(&S.a_ready, 4);
+        mbar_init(&S.drain, 1);
+        S.abort_flag = 0;
+        S.stop = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&S.tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = S.tmem_base;
+    const int T = L.n_tiles;
+
+    if (warp == 4) {
+        // ------------------------------------------------------------------ producer
+        if (lane == 0) {
+            long long g_load = 0, g_mma = 0;
+            const uint32_t a_addr = su32(A);
+            bool ok = true;
+            for (int step = 0; ok; ++step) {
+                if (!wait_bar(S, &S.a_ready, step & 1, L.status)) break;
+                if (S.stop) break;
+                int t_load = 0;
+                auto issue_load = [&]() -> bool {
+                    const int s = (int)(g_load % kStages);
+                    if (g_load >= kStages &&
+                        !wait_bar(S, &S.empty[s], (uint32_t)((g_load / kStages - 1) & 1), L.status))
+                        return false;
+                    mbar_expect_tx(&S.full[s], kTileBytes);
+                    tma_load_tile(su32(Bst + s * kTileBytes), &L.tmap, t_load, &S.full[s]);
+                    ++g_load;
+                    ++t_load;
+                    return true;
+                };
+                while (ok && t_load < T && g_load < g_mma + kAhead) ok = issue_load();
+                for (int t = 0; ok && t < T; ++t) {
+                    const int s = (int)(g_mma % kStages);
+                    const int b = (int)(g_mma & 1);
+                    if (!wait_bar(S, &S.full[s], (uint32_t)((g_mma / kStages) & 1), L.status)) { ok = false; break; }
+                    if (g_mma >= 2 && !wait_bar(S, &S.tempty[b], (uint32_t)(((g_mma >> 1) - 1) & 1), L.status)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t b_addr = su32(Bst + s * kTileBytes);
+#pragma unroll
+                    for (int kk = 0; kk < kK / 16; ++kk)
+                        mma_bf16(tmem + b * kTileN, smem_desc(a_addr + kk * 2 * kLBO), smem_desc(b_addr + kk * 2 * kLBO),
+                                 kk > 0);
+                    mma_commit(&S.tfull[b]);
+                    mma_commit(&S.empty[s]);
+                    ++g_mma;
+                    while (ok && t_load < T && g_load < g_mma + kAhead) ok = issue_load();
+                }
+            }
+            // drain: every issued MMA completes before the tensor memory is freed; every issued
+            // load was consumed by an MMA, except after an abort
+            mma_commit(&S.drain);
+            wait_bar(S, &S.drain, 0, L.status);
+            for (long long g = g_mma; g < g_load; ++g)
+                wait_bar(S, &S.full[g % kStages], (uint32_t)((g / kStages) & 1), L.status);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------------ walkers
+        const int r = threadIdx.x;  // TMEM lane / A row
+        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+        const float inv2d = 1.0f / (2.0f * (float)D);
+        float x[D];
+        float logw = 0.f, dsig = 0.f, gfac0 = 0.f;
+        int k = 0;
+        long long j = -1, q = 0;
+        bool active = false;
+        long long g_epi = 0;
+        const unsigned long long total = (unsigned long long)L.total_walks;
+        for (int step = 0;; ++step) {
+            // refill idle lanes (warp-aggregated claim on the global walk counter)
+            {
+                const bool need = !active;
+                const unsigned m = __ballot_sync(0xffffffffu, need);
+                unsigned long long basej = 0;
+                if (m != 0) {
+                    if (lane == __ffs(m) - 1) basej = atomicAdd(L.cursor, (unsigned long long)__popc(m));
+                    basej = __shfl_sync(0xffffffffu, basej, __ffs(m) - 1);
+                }
+                if (need) {
+                    const unsigned long long jj = basej + __popc(m & ((1u << lane) - 1u));
+                    if (jj < total) {
+                        active = true;
+                        j = (long long)jj;
+                        q = j / P.N;
+#pragma unroll
+                        for (int i = 0; i < D; ++i) x[i] = (float)__ldg(P.x + q * D + i);
+                        logw = dsig = gfac0 = 0.f;
+                        k = 0;
+                    }
+                }
+            }
+            // the only exit: a barrier reduction every walker thread reaches (an abort makes
+            // every thread vote 'no more work' at the next one)
+            const unsigned want = (active && !S.abort_flag) ? 1u : 0u;
+            int any;
+            asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.cta.red.or.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+                         : "=r"(any)
+                         : "r"(want)
+                         : "memory");
+            if (!any) {
+                if (lane == 0) {
+                    S.stop = 1;
+                    mbar_arrive(&S.a_ready);
+                }
+                break;
+            }
+            write_row<D>(A, r, x, active);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.a_ready);
+
+            // ---- epilogue: best and second-best 32-point chunk of D~ = |p|^2 - 2 x.p
+            float m1 = CUDART_INF_F, m2 = CUDART_INF_F;
+            int c1 = 0;
+            bool ok = true;
+            for (int t = 0; t < T; ++t, ++g_epi) {
+                const int b = (int)(g_epi & 1);
+                if (!warp_wait_bar(S, &S.tfull[b], (uint32_t)((g_epi >> 1) & 1), L.status)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                float v[kTileN];
+                tmem_row128(trow + b * kTileN, v);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.tempty[b]);
+#pragma unroll
+                for (int c = 0; c < kTileN / kChunk; ++c) {
+                    const float cm = min32(v + kChunk * c);
+                    const int id = t * (kTileN / kChunk) + c;
+                    m2 = fminf(m2, fmaxf(m1, cm));
+                    if (cm < m1) {
+                        m1 = cm;
+                        c1 = id;
+                    }
+                }
+            }
+            if (!ok) {
+                active = false;  // abandon the walk; the next barrier reduction ends the loop
+                continue;
+            }
+            if (!active) continue;
+
+            // ---- exact FP32 distances of the best chunk; the rest is bounded by m2 - delta
+            float xx = 0.f;
+#pragma unroll
+            for (int i = 0; i < D; ++i) xx = fmaf(x[i], x[i], xx);
+            float dbest = CUDART_INF_F;
+            int pbest = c1 * kChunk;
+            const float *pc = L.pts32 + (long long)c1 * kChunk * D;
+#pragma unroll 4
+            for (int i = 0; i < kChunk; ++i) {
+                float s2 = 0.f;
+#pragma unroll
+                for (int jj = 0; jj < D; ++jj) {
+                    const float t0 = x[jj] - __ldg(pc + i * D + jj);
+                    s2 = fmaf(t0, t0, s2);
+                }
+                if (s2 < dbest) {
+                    dbest = s2;
+                    pbest = c1 * kChunk + i;
+                }
+            }
+            float Rp = sqrtf(dbest);
+            const float lb2 = m2 + xx - L.delta;
+            const float lb = lb2 > 0.f ? sqrtf(lb2) : 0.f;
+            if (lb < Rp) {
+                Rp = lb;
+                atomicAdd(L.shrinks, 1ull);
+            }
+            // other components: goal, outer ball, box faces (FP32 direct form)
+            float best = Rp;
+            int kind = kPoint, idx = pbest;
+            if (P.has_goal) {
+                float s = 0.f;
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    const float t0 = x[i] - geom_s[2 * D + i];
+                    s = fmaf(t0, t0, s);
+                }
+                const float rg = sqrtf(s) - P.goal_r;
+                if (rg <= best) { best = rg; kind = kGoal; idx = 0; }
+            }
+            if (P.has_outer) {
+                float s = 0.f;
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    const float t0 = x[i] - geom_s[3 * D + i];
+                    s = fmaf(t0, t0, s);
+                }
+                const float ro = P.outer_r - sqrtf(s);
+                if (ro < best) { best = ro; kind = kOuter; idx = 0; }
+            }
+            if (P.has_box) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    const float rlo = x[i] - geom_s[i];
+                    if (rlo < best) { best = rlo; kind = kFace; idx = 2 * i; }
+                    const float rhi = geom_s[D + i] - x[i];
+                    if (rhi < best) { best = rhi; kind = kFace; idx = 2 * i + 1; }
+                }
+            }
+            if (L.radius_out != nullptr && k == 0) L.radius_out[j] = (double)best;
+            const float R = best - P.shrink;
+            int outcome = 0;
+            if (k == 0 && !(R > 0.f))
+                outcome = 3;
+            else if (R < P.eps && !(GRAD && P.grad_mode && k == 0))
+                outcome = 1;
+            else if (k >= L.max_steps)
+                outcome = 2;
+            if (outcome == 0) {
+                float v[D];
+                direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + j), (uint32_t)k, v);
+                const float2 tb = table_lookup(P.table, R * P.sqrt_sigma);
+                if (GRAD && k == 0)
+                    gfac0 = P.laplace ? ((float)D / R) * __expf(-tb.x) : ((float)D / R) / tb.y;
+                logw += tb.x;
+                dsig = fmaf(-(R * R) * inv2d, tb.y, dsig);
+#pragma unroll
+                for (int i = 0; i < D; ++i) x[i] = fmaf(R, v[i], x[i]);
+                ++k;
+                continue;
+            }
+            // ---- the walk ended
+            float term = 0.f;
+            float e[kMaxExp];
+#pragma unroll
+            for (int kk = 0; kk < kMaxExp; ++kk) e[kk] = 0.f;
+            if (outcome == 1) {
+                float xb[D];
+#pragma unroll
+                for (int i = 0; i < D; ++i) xb[i] = x[i];
+                if (kind == kPoint) {
+#pragma unroll
+                    for (int i = 0; i < D; ++i) xb[i] = __ldg(L.pts32 + (long long)idx * D + i);
+                } else if (kind == kFace) {
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+                        if (i == (idx >> 1)) xb[i] = (idx & 1) ? geom_s[D + i] : geom_s[i];
+                } else {
+                    const float *c = geom_s + (kind == kGoal ? 2 * D : 3 * D);
+                    const float rad = kind == kGoal ? P.goal_r : P.outer_r;
+                    float s = 0.f;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) s = fmaf(x[i] - c[i], x[i] - c[i], s);
+                    const float len = sqrtf(s);
+#pragma unroll
+                    for (int i = 0; i < D; ++i) xb[i] = len > 0.f ? fmaf(rad / len, x[i] - c[i], c[i]) : c[i];
+                }
+                if (P.n_exp > 0) {
+                    const float *wv = geom_s + 4 * D;
+                    const float *av = geom_s + 4 * D + kMaxExp;
+#pragma unroll
+                    for (int kk = 0; kk < kMaxExp; ++kk) {
+                        if (kk < P.n_exp) {
+                            float dot = logw;
+#pragma unroll
+                            for (int i = 0; i < D; ++i) dot = fmaf(av[kk * D + i], xb[i], dot);
+                            e[kk] = expf(dot);
+                            term = fmaf(wv[kk], e[kk], term);
+                        }
+                    }
+                } else {
+                    term = kind == kGoal ? expf(logw) : 0.f;
+                }
+            }
+            const bool has_grad = GRAD && outcome == 1 && k > 0;
+            float v0[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) v0[i] = 0.f;
+            if (has_grad) direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + j), 0u, v0);
+            const float gt = has_grad ? gfac0 * term : 0.f;
+            add_walk<D, GRAD>(P, q, outcome, k, term, dsig, gt, v0, e);
+            if (P.w_term != nullptr) P.w_term[j] = outcome == 3 ? (double)CUDART_NAN : (double)term;
+            if (P.w_jumps != nullptr) P.w_jumps[j] = k;
+            if (P.w_dsigma != nullptr) P.w_dsigma[j] = (double)(term * dsig);
+            if (P.w_grad != nullptr)
+#pragma unroll
+                for (int i = 0; i < D; ++i) P.w_grad[j * D + i] = (double)(gt * v0[i]);
+            active = false;
+        }
+    }
+    // ---------------------------------------------------------------------- teardown
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+size_t smem_bytes() { return 1024 + kABytes + (size_t)kStages * kTileBytes; }
+
+}  // namespace pc
+
+// ---------------------------------------------------------------------------------------
+// host side: operand preparation, tensor map, launch
+// ---------------------------------------------------------------------------------------
+static inline uint16_t bf16_bits(float f) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(f);
+    return *reinterpret_cast<const uint16_t *>(&h);
+}
+static inline float bf16_value(uint16_t b) {
+    __nv_bfloat16 h;
+    *reinterpret_cast<uint16_t *>(&h) = b;
+    return __bfloat162float(h);
+}
+
+cudaError_t pointcloud_prepare(const double *pts, int64_t M, int d, PointCloudDev *out) {
+    if (d < 2 || 3 * d + 2 > pc::kK) return cudaErrorInvalidValue;
+    const int64_t n_tiles = (M + pc::kTileN - 1) / pc::kTileN;
+    const int64_t Mp = n_tiles * pc::kTileN;
+    std::vector<uint16_t> hb((size_t)n_tiles * pc::kTileBytes / 2, 0);
+    std::vector<float> h32((size_t)Mp * d, 0.f);
+    double pmax = 0.0;
+    for (int64_t i = 0; i < Mp; ++i) {
+        const bool real = i < M;
+        float p[WOS_MAX_D];
+        double nn = 0.0;
+        for (int j = 0; j < d; ++j) {
+            // padding points sit far outside any domain: they never win the minimum
+            p[j] = real ? (float)pts[i * d + j] : 1.0e3f;
+            h32[(size_t)i * d + j] = p[j];
+            nn += (double)p[j] * (double)p[j];
+            if (real) pmax = std::max(pmax, std::fabs((double)p[j]));
+        }
+        uint16_t row[pc::kK] = {0};
+        for (int j = 0; j < d; ++j) {
+            const float qv = -2.0f * p[j];
+            const uint16_t qh = bf16_bits(qv);
+            const uint16_t ql = bf16_bits(qv - bf16_value(qh));
+            row[j] = qh;
+            row[d + j] = ql;
+            row[2 * d + j] = qh;
+        }
+        const float n32 = (float)nn;
+        const uint16_t nh = bf16_bits(n32);
+        row[3 * d] = nh;
+        row[3 * d + 1] = bf16_bits(n32 - bf16_value(nh));
+        const int64_t t = i / pc::kTileN;
+        const int r = (int)(i % pc::kTileN);
+        uint16_t *tile = hb.data() + (size_t)t * pc::kTileBytes / 2;
+        for (int k = 0; k < pc::kK; ++k) {
+            const uint32_t off = (r / 8) * pc::kSBO + (k / 8) * pc::kLBO + (r % 8) * 16 + (k % 8) * 2;
+            tile[off / 2] = row[k];
+        }
+    }
+    out->n_tiles = (int)n_tiles;
+    out->pmax = pmax;
+    cudaError_t e = cudaMalloc(&out->tiles, hb.size() * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&out->pts32, h32.size() * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(out->tiles, hb.data(), hb.size() * 2, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(out->pts32, h32.data(), h32.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    // tensor map over the tiles: 2D, 64 BF16 (128 B) wide, 64 rows per 8 KB tile
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr);
+    if (e != cudaSuccess || fn == nullptr || qr != cudaDriverEntryPointSuccess) return cudaErrorNotSupported;
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const cuuint64_t dims[2] = {64, (cuuint64_t)n_tiles * (pc::kTileBytes / 128)};
+    const cuuint64_t strides[1] = {128};
+    const cuuint32_t box[2] = {64, pc::kTileBytes / 128};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult cr = encode(&out->tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, out->tiles, dims, strides, box,
+                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return cr == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+void pointcloud_release(PointCloudDev *pcd) {
+    cudaFree(pcd->tiles);
+    cudaFree(pcd->pts32);
+    pcd->tiles = nullptr;
+    pcd->pts32 = nullptr;
+}
+
+// Bound of |D~ - D| for the BF16-split contraction: representation of x and -2p (2^-18
+// relative each), the dropped x_l q_l term (2^-18), |p|^2 in two BF16 (2^-16 relative), and
+// FP32 accumulation of 3d + 2 terms (2^-23 relative per addition, covering truncation).
+float pointcloud_delta(int d, double xabs, double pmax) {
+    const double dot = 2.0 * d * xabs * pmax;  // sum_j |x_j| |2 p_j|
+    const double nn = d * pmax * pmax;
+    const double terms = 2.0 * dot + nn;
+    const double u18 = 3.814697265625e-06, u16 = 1.52587890625e-05, u23 = 1.1920928955078125e-07;
+    const double bound = 3.0 * u18 * dot + u16 * nn + (3 * d + 2) * u23 * terms;
+    return (float)(2.0 * bound + 1e-6);
+}
+
+static cudaError_t configure_pc(size_t smem) {
+    cudaError_t e = cudaSuccess;
+#define WOS_CFG(DD)                                                                                             \
+    if (e == cudaSuccess)                                                                                       \
+        e = cudaFuncSetAttribute(pc::pointcloud_kernel<DD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)smem);                                                                    \
+    if (e == cudaSuccess)                                                                                       \
+        e = cudaFuncSetAttribute(pc::pointcloud_kernel<DD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                 (int)smem);
+    WOS_CFG(2) WOS_CFG(3) WOS_CFG(4) WOS_CFG(5) WOS_CFG(6) WOS_CFG(7) WOS_CFG(8) WOS_CFG(9) WOS_CFG(10)
+#undef WOS_CFG
+    return e;
+}
+
+cudaError_t launch_pointcloud(const PointCloudDev &pcd, const MixedProblem &P, float delta,
+                              unsigned long long *cursor, int *status, unsigned long long *shrinks,
+                              uint64_t seed, int64_t max_steps, int grad, cudaStream_t s,
+                              double *radius_out) {
+    static bool configured = false;
+    const size_t smem = pc::smem_bytes();
+    if (!configured) {
+        const cudaError_t e = configure_pc(smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    pc::Launch L;
+    memset(&L, 0, sizeof(L));
+    L.tmap = pcd.tmap;
+    L.P = P;
+    L.pts32 = pcd.pts32;
+    L.n_tiles = pcd.n_tiles;
+    L.delta = delta;
+    L.cursor = cursor;
+    L.status = status;
+    L.shrinks = shrinks;
+    L.seed = seed;
+    L.max_steps = max_steps;
+    L.total_walks = P.Q * P.N;
+    L.radius_out = radius_out;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t ctas_needed = (L.total_walks + pc::kRows - 1) / pc::kRows;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(2LL * sms, ctas_needed));
+    switch (P.d) {
+#define WOS_CASE(DD)                                                                         \
+    case DD:                                                                                 \
+        if (grad)                                                                            \
+            pc::pointcloud_kernel<DD, true><<<grid, pc::kThreads, smem, s>>>(L);            \
+        else                                                                                 \
+            pc::pointcloud_kernel<DD, false><<<grid, pc::kThreads, smem, s>>>(L);           \
+        break;
+        WOS_CASE(2) WOS_CASE(3) WOS_CASE(4) WOS_CASE(5) WOS_CASE(6) WOS_CASE(7) WOS_CASE(8) WOS_CASE(9)
+        WOS_CASE(10)
+#undef WOS_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace wos

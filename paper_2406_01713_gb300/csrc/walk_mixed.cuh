@@ -3,13 +3,15 @@
 // One launch serves many problems of uneven dimension, obstacle count and walk budget:
 //   * a global work queue of items (problem, walk range) in longest-first order, pulled by
 //     CTAs through an atomic cursor;
-//   * the current problem's balls are staged in shared memory as 4-ball blocks
-//     [m_0 x4][m_1 x4]...[m_{d-1} x4][e0 x4][e1 x4] with m = -2c, e0 = |c|^2 - r^2, e1 = -2r,
-//     so one 128-bit shared load fetches one field of four balls;
+//   * the current problem's balls are staged in shared memory as 8-ball blocks
+//     [m_0 x8][m_1 x8]...[m_{d-1} x8][e0 x8][e1 x8] with m = -2c, e0 = |c|^2 - r^2, e1 = -2r,
+//     so two 128-bit shared loads fetch one field of eight balls, and the screen runs as
+//     packed FP32x2 FMAs (two balls per instruction);
 //   * every lane runs walks back to back, refilling from the item's walk counter the moment
 //     its walk ends (walk lengths vary, so lanes never wait for the slowest walk of a batch);
-//   * per-lane FP32 partial sums over the walks of one query, flushed to FP64 per-query
-//     sums in global memory (warp-reduced when the whole warp holds the same query).
+//   * each finished walk adds its contribution (u, u^2, du/dsigma, grad, grad^2, du/dw,
+//     counters) straight into the FP64 per-query sums in global memory, so no per-lane
+//     accumulator occupies registers between walks.
 //
 // Distance to the balls (Sec. VI, |x - c| - r): a ball can only beat the current best
 // distance b if |x-c|^2 < (r+b)^2, i.e. if
@@ -49,6 +51,32 @@ struct MixedWalker {
     bool active;
 };
 
+// ---- packed FP32x2 helpers (sm_100+: fma.rn.f32x2, three-input min.f32) -----------------
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pack2(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 unpack2(f32x2 v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ f32x2 ffma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+constexpr int kBallBlock = 8;  // balls per shared-memory block
+
 // geom layout in shared memory: [0,d) box lo, [d,2d) box hi, [2d,3d) goal c, [3d,4d) outer c,
 // [4d, 4d+K) exp w, then K x d exp a.
 template <int D>
@@ -69,7 +97,7 @@ __device__ __forceinline__ float distance_mixed(const MixedProblem &P, const flo
         const float r = sqrtf(s) - P.goal_r;
         if (r < best) { best = r; kind = kGoal; idx = 0; }
     }
-    // Balls are searched below; the other components go first so that `best` starts small.
+    // Balls are searched below; the other components go first so that the bound starts small.
     float other = CUDART_INF_F;
     int okind = -1, oidx = -1;
     if (P.has_outer) {
@@ -91,53 +119,60 @@ __device__ __forceinline__ float distance_mixed(const MixedProblem &P, const flo
             if (rhi < other) { other = rhi; okind = kFace; oidx = 2 * j + 1; }
         }
     }
-    // Running upper bound used by the ball screen (ties and ordering are resolved below).
+    // Running upper bound b of the distance used by the ball screen.
     float b = fminf(best, other);
-    float xx = 0.f;
-#pragma unroll
-    for (int j = 0; j < D; ++j) xx = fmaf(x[j], x[j], xx);
-    float thr = fmaf(b, b, slack - xx);
     float bball = CUDART_INF_F;
     int bidx = -1;
+    float xx = 0.f;
+    f32x2 x2[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        xx = fmaf(x[j], x[j], xx);
+        x2[j] = pack2(x[j], x[j]);
+    }
+    float thr = fmaf(b, b, slack - xx);
+    f32x2 b2 = pack2(b, b);
+    const ulonglong2 *B2 = reinterpret_cast<const ulonglong2 *>(balls);
 #pragma unroll 1
     for (int blk = 0; blk < nblk; ++blk) {
-        const float4 *B = balls + blk * (D + 2);
-        const float4 e0 = B[D];
-        const float4 e1 = B[D + 1];
-        float4 L;
-        L.x = fmaf(e1.x, b, e0.x);
-        L.y = fmaf(e1.y, b, e0.y);
-        L.z = fmaf(e1.z, b, e0.z);
-        L.w = fmaf(e1.w, b, e0.w);
+        const ulonglong2 *F = B2 + blk * 2 * (D + 2);
+        const ulonglong2 e0a = F[2 * D], e0b = F[2 * D + 1];
+        const ulonglong2 e1a = F[2 * D + 2], e1b = F[2 * D + 3];
+        f32x2 L0 = ffma2(e1a.x, b2, e0a.x);
+        f32x2 L1 = ffma2(e1a.y, b2, e0a.y);
+        f32x2 L2 = ffma2(e1b.x, b2, e0b.x);
+        f32x2 L3 = ffma2(e1b.y, b2, e0b.y);
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            const float4 m = B[j];
-            L.x = fmaf(x[j], m.x, L.x);
-            L.y = fmaf(x[j], m.y, L.y);
-            L.z = fmaf(x[j], m.z, L.z);
-            L.w = fmaf(x[j], m.w, L.w);
+            const ulonglong2 ma = F[2 * j], mb = F[2 * j + 1];
+            L0 = ffma2(x2[j], ma.x, L0);
+            L1 = ffma2(x2[j], ma.y, L1);
+            L2 = ffma2(x2[j], mb.x, L2);
+            L3 = ffma2(x2[j], mb.y, L3);
         }
-        const bool c0 = L.x < thr, c1 = L.y < thr, c2 = L.z < thr, c3 = L.w < thr;
-        if (c0 | c1 | c2 | c3) {
-            const float *Bf = reinterpret_cast<const float *>(B);
+        const float2 l0 = unpack2(L0), l1 = unpack2(L1), l2 = unpack2(L2), l3 = unpack2(L3);
+        const float lmin = fminf(fmin3(l0.x, l0.y, l1.x), fmin3(fmin3(l1.y, l2.x, l2.y), l3.x, l3.y));
+        if (lmin < thr) {
+            const float Lt[8] = {l0.x, l0.y, l1.x, l1.y, l2.x, l2.y, l3.x, l3.y};
+            const float *Bf = reinterpret_cast<const float *>(F);
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const bool ct = t == 0 ? c0 : (t == 1 ? c1 : (t == 2 ? c2 : c3));
-                if (ct) {
+            for (int t = 0; t < kBallBlock; ++t) {
+                if (Lt[t] < thr) {
                     float s = 0.f;
 #pragma unroll
                     for (int j = 0; j < D; ++j) {
-                        const float dj = fmaf(0.5f, Bf[4 * j + t], x[j]);  // x_j - c_j
+                        const float dj = fmaf(0.5f, Bf[kBallBlock * j + t], x[j]);  // x_j - c_j
                         s = fmaf(dj, dj, s);
                     }
-                    const float r = -0.5f * Bf[4 * (D + 1) + t];
+                    const float r = -0.5f * Bf[kBallBlock * (D + 1) + t];
                     const float dist = sqrtf(s) - r;
                     if (dist < bball) {
                         bball = dist;
-                        bidx = 4 * blk + t;
+                        bidx = kBallBlock * blk + t;
                         if (dist < b) {
                             b = dist;
                             thr = fmaf(b, b, slack - xx);
+                            b2 = pack2(b, b);
                         }
                     }
                 }
@@ -168,11 +203,11 @@ __device__ __forceinline__ float terminal_value(const MixedProblem &P, const flo
         rad = kind == kGoal ? P.goal_r : P.outer_r;
         sphere = true;
     } else if (kind == kBall) {
-        const float *Bf = reinterpret_cast<const float *>(balls + (idx >> 2) * (D + 2));
-        const int t = idx & 3;
+        const float *Bf = reinterpret_cast<const float *>(balls + (idx / kBallBlock) * 2 * (D + 2));
+        const int t = idx % kBallBlock;
 #pragma unroll
-        for (int j = 0; j < D; ++j) cc[j] = -0.5f * Bf[4 * j + t];
-        rad = -0.5f * Bf[4 * (D + 1) + t];
+        for (int j = 0; j < D; ++j) cc[j] = -0.5f * Bf[kBallBlock * j + t];
+        rad = -0.5f * Bf[kBallBlock * (D + 1) + t];
         sphere = true;
     }
     if (sphere) {
@@ -216,72 +251,40 @@ __device__ __forceinline__ float terminal_value(const MixedProblem &P, const flo
     return kind == kGoal ? expf(logw) : 0.f;
 }
 
-// Per-lane FP32 partial sums of one query: [u, u^2, du/dsigma, (grad[D], grad^2[D]), dw_0].
-// Boundary-data derivatives dw_k for k >= 1 go straight to the FP64 sums at walk end.
+// Adds one finished walk to the FP64 per-query sums: fields [u, u^2, du/dsigma, grad (D),
+// grad^2 (D), du/dw (K)] and counters [walks, walk-steps, capped, outside].
 template <int D, bool GRAD>
-struct LaneAcc {
-    static constexpr int kG = GRAD ? 2 * D : 0;  // gradient fields present
-    static constexpr int kN = 3 + kG + 1;
-    float s[kN];
-    unsigned c[kCounters];
-    long long q;
-};
-
-template <int D, bool GRAD>
-__device__ __forceinline__ void lane_acc_clear(LaneAcc<D, GRAD> &A) {
-#pragma unroll
-    for (int f = 0; f < LaneAcc<D, GRAD>::kN; ++f) A.s[f] = 0.f;
-#pragma unroll
-    for (int f = 0; f < kCounters; ++f) A.c[f] = 0u;
-}
-
-// Global FP64 field index of lane-accumulator field f.
-template <int D, bool GRAD>
-__device__ __forceinline__ int acc_global_field(int f) {
-    return f < 3 + LaneAcc<D, GRAD>::kG ? f : f - (3 + LaneAcc<D, GRAD>::kG) + 3 + 2 * D;
-}
-
-template <int D, bool GRAD>
-__device__ __forceinline__ void lane_acc_flush(const MixedProblem &P, const LaneAcc<D, GRAD> &A) {
+__device__ __forceinline__ void add_walk(const MixedProblem &P, long long q, int outcome, int k,
+                                         float term, float dsig, float gt, const float (&v0)[D],
+                                         const float (&e)[kMaxExp]) {
     const int nf = acc_fields(D, P.n_exp);
-    double *acc = P.acc + A.q * nf;
-    constexpr int kE = 3 + LaneAcc<D, GRAD>::kG;
-#pragma unroll
-    for (int f = 0; f < kE; ++f) atomicAdd(acc + f, (double)A.s[f]);
-    if (P.n_exp > 0) atomicAdd(acc + 3 + 2 * D, (double)A.s[kE]);
-    unsigned long long *cnt = P.counts + A.q * kCounters;
-#pragma unroll
-    for (int f = 0; f < kCounters; ++f)
-        if (A.c[f]) atomicAdd(cnt + f, (unsigned long long)A.c[f]);
-}
-
-// End of an item: warp-reduce when all lanes hold the same query, else flush lane by lane.
-template <int D, bool GRAD>
-__device__ __forceinline__ void lane_acc_final(const MixedProblem &P, LaneAcc<D, GRAD> &A) {
-    const unsigned peers = __match_any_sync(0xffffffffu, A.q);
-    if (peers == 0xffffffffu) {
-        if (A.q < 0) return;
-        constexpr int kE = 3 + LaneAcc<D, GRAD>::kG;
-        const int nf = acc_fields(D, P.n_exp);
-#pragma unroll
-        for (int f = 0; f < LaneAcc<D, GRAD>::kN; ++f) {
-            if (f >= kE && f - kE >= P.n_exp) continue;  // warp-uniform
-            double dv = (double)A.s[f];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) dv += __shfl_xor_sync(0xffffffffu, dv, off);
-            if ((threadIdx.x & 31) == 0) atomicAdd(P.acc + A.q * nf + acc_global_field<D, GRAD>(f), dv);
-        }
-#pragma unroll
-        for (int f = 0; f < kCounters; ++f) {
-            unsigned long long v = A.c[f];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if ((threadIdx.x & 31) == 0 && v) atomicAdd(P.counts + A.q * kCounters + f, v);
-        }
-    } else if (A.q >= 0) {
-        lane_acc_flush<D, GRAD>(P, A);
+    double *acc = P.acc + q * nf;
+    unsigned long long *cnt = P.counts + q * kCounters;
+    atomicAdd(cnt + 0, 1ull);
+    atomicAdd(cnt + 1, (unsigned long long)(k + 1));
+    if (outcome == 2) atomicAdd(cnt + 2, 1ull);
+    if (outcome == 3) {
+        atomicAdd(cnt + 3, 1ull);
+        return;
     }
-    A.q = -1;
+    if (term != 0.f) {
+        atomicAdd(acc + 0, (double)term);
+        atomicAdd(acc + 1, (double)term * (double)term);
+        atomicAdd(acc + 2, (double)term * (double)dsig);
+        if constexpr (GRAD) {
+            if (gt != 0.f) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    const double g = (double)gt * (double)v0[i];
+                    atomicAdd(acc + 3 + i, g);
+                    atomicAdd(acc + 3 + D + i, g * g);
+                }
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < kMaxExp; ++kk)
+            if (kk < P.n_exp) atomicAdd(acc + 3 + 2 * D + kk, (double)e[kk]);
+    }
 }
 
 // Warp-aggregated grab of one walk index per calling lane from the item's shared counter.
@@ -312,14 +315,11 @@ __device__ __forceinline__ void start_walk(const MixedProblem &P, MixedWalker<D>
 template <int D, bool GRAD>
 __device__ void run_item(const MixedLaunch &L, const MixedProblem &P, MixedSmem &S,
                          const float4 *balls) {
-    const int nblk = (P.n_balls + 3) >> 2;
+    const int nblk = (P.n_balls + kBallBlock - 1) / kBallBlock;
     const float *geom = S.geom;
     const unsigned end = S.end_walk;
     const float inv2d = 1.0f / (2.0f * (float)D);
     MixedWalker<D> W;
-    LaneAcc<D, GRAD> A;
-    lane_acc_clear<D, GRAD>(A);
-    A.q = -1;
     {
         const unsigned j = grab_walk(S);
         W.active = j < end;
@@ -359,64 +359,33 @@ __device__ void run_item(const MixedLaunch &L, const MixedProblem &P, MixedSmem 
 #pragma unroll
         for (int k = 0; k < kMaxExp; ++k) e[k] = 0.f;
         if (outcome == 1) term = terminal_value<D>(P, geom, balls, W.x, kind, idx, W.logw, e);
-        if (A.q != W.q) {
-            if (A.q >= 0) lane_acc_flush<D, GRAD>(P, A);
-            lane_acc_clear<D, GRAD>(A);
-            A.q = W.q;
-        }
         const bool has_grad = GRAD && outcome == 1 && W.k > 0;
         float v0[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) v0[i] = 0.f;
         if constexpr (GRAD) {
-            if (has_grad) {
+            if (has_grad)
                 direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + (long long)W.j), 0u, v0);
-            } else {
-#pragma unroll
-                for (int i = 0; i < D; ++i) v0[i] = 0.f;
-            }
         }
-        if (outcome != 3) {
-            A.s[0] += term;
-            A.s[1] = fmaf(term, term, A.s[1]);
-            A.s[2] = fmaf(term, W.dsig, A.s[2]);
-            if constexpr (GRAD) {
-                const float gt = W.gfac0 * term;
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    const float g = gt * v0[i];
-                    A.s[3 + i] += g;
-                    A.s[3 + D + i] = fmaf(g, g, A.s[3 + D + i]);
-                }
-            }
-            A.s[3 + LaneAcc<D, GRAD>::kG] += e[0];
-            if (P.n_exp > 1) {
-                double *accq = P.acc + W.q * acc_fields(D, P.n_exp) + 3 + 2 * D;
-#pragma unroll
-                for (int k = 1; k < kMaxExp; ++k)
-                    if (k < P.n_exp) atomicAdd(accq + k, (double)e[k]);
-            }
-        }
-        A.c[0] += 1u;
-        A.c[1] += (unsigned)(W.k + 1);
-        A.c[2] += outcome == 2 ? 1u : 0u;
-        A.c[3] += outcome == 3 ? 1u : 0u;
+        const float gt = has_grad ? W.gfac0 * term : 0.f;
+        add_walk<D, GRAD>(P, W.q, outcome, W.k, term, W.dsig, gt, v0, e);
         if (P.w_term != nullptr) P.w_term[W.j] = outcome == 3 ? (double)CUDART_NAN : (double)term;
         if (P.w_jumps != nullptr) P.w_jumps[W.j] = W.k;
         if (P.w_dsigma != nullptr) P.w_dsigma[W.j] = (double)(term * W.dsig);
         if (P.w_grad != nullptr) {
-            const float gt = has_grad ? W.gfac0 * term : 0.f;
 #pragma unroll
-            for (int i = 0; i < D; ++i)
-                P.w_grad[(long long)W.j * D + i] = GRAD ? (double)(gt * v0[i]) : 0.0;
+            for (int i = 0; i < D; ++i) P.w_grad[(long long)W.j * D + i] = (double)(gt * v0[i]);
         }
         const unsigned nj = grab_walk(S);
         W.active = nj < end;
         if (W.active) start_walk<D, GRAD>(P, W, nj);
     }
-    lane_acc_final<D, GRAD>(P, A);
 }
 
-template <bool GRAD>
-__global__ void __launch_bounds__(512, 1) walk_mixed_kernel(const __grid_constant__ MixedLaunch L) {
+// MAXT: the largest CTA this instantiation is launched with (one CTA per SM); it sets the
+// register budget (65536 / MAXT per thread).
+template <bool GRAD, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) walk_mixed_kernel(const __grid_constant__ MixedLaunch L) {
     extern __shared__ float4 smem_balls[];
     __shared__ MixedSmem S;
     __shared__ MixedProblem SP;
@@ -449,7 +418,7 @@ __global__ void __launch_bounds__(512, 1) walk_mixed_kernel(const __grid_constan
             const MixedProblem *src = L.problems != nullptr ? L.problems + pi : &L.single;
             if (threadIdx.x == 0) SP = *src;
             const int d = src->d;
-            const int nfl = ((src->n_balls + 3) >> 2) * (d + 2);
+            const int nfl = ((src->n_balls + kBallBlock - 1) / kBallBlock) * 2 * (d + 2);
             const float4 *bsrc = reinterpret_cast<const float4 *>(src->balls);
             for (int i = threadIdx.x; i < nfl; i += blockDim.x) smem_balls[i] = __ldg(bsrc + i);
             const int ng = 4 * d + kMaxExp + kMaxExp * d;

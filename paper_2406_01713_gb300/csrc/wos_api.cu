@@ -81,6 +81,9 @@ struct wos_domain_s {
     std::vector<float2 *> tables;
     float2 *table = nullptr;
     double table_zmax = 0;
+    PointCloudDev pcd{};  // tensor-core operands of the point set (mixed precision, d <= 10)
+    bool has_pcd = false;
+    float pc_delta = 0.f;
 };
 
 namespace {
@@ -161,6 +164,11 @@ void error_bounds(wos_domain_s &D) {
         for (int j = 0; j < d; ++j) cc += D.ball_c[(size_t)i * d + j] * D.ball_c[(size_t)i * d + j];
         ccmax = std::max(ccmax, cc);
         rmax = std::max(rmax, D.ball_r[i]);
+    }
+    for (int64_t i = 0; i < D.n_points; ++i) {
+        double cc = 0.0;
+        for (int j = 0; j < d; ++j) cc += D.points[(size_t)i * d + j] * D.points[(size_t)i * d + j];
+        ccmax = std::max(ccmax, cc);
     }
     cmax = std::sqrt(ccmax);
     double cgo = 0.0;
@@ -250,6 +258,8 @@ struct FinalizeArgs {
     int64_t total_q;
     FinalizeRec single;
     wos_stats *stats;
+    const int *status;                   // nonzero: the walker gave up (timeout); NaN outputs
+    const unsigned long long *shrinks;   // point-cloud radius-bound events (nullable)
 };
 
 __device__ __forceinline__ double se_mean(double s, double s2, double n) {
@@ -280,7 +290,9 @@ __global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
         const unsigned long long *c = R->counts + q * kCounters;
         const double n = (double)R->N;
         const double inv = 1.0 / n;
-        const bool out = c[3] > 0;
+        const bool out = c[3] > 0 || (a.status != nullptr && *a.status != 0);
+        if (t == 0 && a.stats != nullptr && a.shrinks != nullptr)
+            atomicAdd(reinterpret_cast<unsigned long long *>(a.stats) + 4, *a.shrinks);
         const double nan = CUDART_NAN;
         if (R->u) R->u[q] = out ? nan : S(0) * inv;
         if (R->u_se) R->u_se[q] = out ? nan : se_mean(S(0), S(1), n);
@@ -411,7 +423,7 @@ MixedProblem make_mixed_problem(wos_domain_t dom, const double *x, int64_t Q, in
 }
 
 size_t mixed_smem_bytes(const wos_domain_s &D) {
-    return (size_t)((D.n_balls + 3) / 4) * (D.d + 2) * 16;
+    return (size_t)((D.n_balls + 7) / 8) * (D.d + 2) * 32;
 }
 
 // Launches the walk kernel of the chosen precision for Q x N walks on zeroed scratch.
@@ -470,10 +482,21 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
         return WOS_OK;
     }
     if (o.precision != WOS_MIXED) return fail(WOS_ERR_INVALID_ARG, "unknown precision %d", o.precision);
-    if (dom->n_points > 0)
-        return fail(WOS_ERR_UNSUPPORTED, "point-cloud domains use the point-cloud walker");
     WeightTable tab;
     WOS_TRY(ensure_table(dom, sigma, &tab));
+    if (dom->n_points > 0) {
+        if (!dom->has_pcd)
+            return fail(WOS_ERR_UNSUPPORTED, "mixed-precision point clouds need d <= %d", kPointCloudMaxD);
+        if (dom->n_balls > 0)
+            return fail(WOS_ERR_UNSUPPORTED, "a domain with both balls and points runs in FP64 or plain FP32");
+        MixedProblem P = make_mixed_problem(dom, x, Q, N, eps, sigma, grad_mode, o.laplace, o.walk_offset, tab,
+                                            (double *)sc.acc, sc.counts, pw);
+        unsigned long long *shrinks = sc.cursor + 1;
+        int *status = reinterpret_cast<int *>(sc.cursor + 2);
+        WOS_CUDA(launch_pointcloud(dom->pcd, P, dom->pc_delta, sc.cursor, status, shrinks, o.seed, o.max_steps,
+                                   grad_mode, s));
+        return WOS_OK;
+    }
     const int64_t total = Q * N;
     if (total > (int64_t)0x7fffffff) return fail(WOS_ERR_UNSUPPORTED, "Q * n_walks must be < 2^31");
     const size_t smem = mixed_smem_bytes(*dom);
@@ -543,6 +566,8 @@ wos_status run_estimator(wos_domain_t dom, const wos_options *opt, const double 
         a.n = 1;
         a.total_q = Q;
         a.stats = stats;
+        a.status = reinterpret_cast<const int *>(sc.cursor + 2);
+        a.shrinks = sc.cursor + 1;
         FinalizeRec &r = a.single;
         r.d = dom->d;
         r.K = dom->n_exp;
@@ -649,27 +674,29 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
     const int64_t nv = view_size(*D);
     std::vector<double> h64 = pack_view<double>(*D);
     std::vector<float> h32 = pack_view<float>(*D);
-    const int nblk = (D->n_balls + 3) / 4;
+    // 8-ball blocks [m_0 x8]...[m_{d-1} x8][e0 x8][e1 x8], m = -2c, e0 = |c|^2 - r^2, e1 = -2r
+    const int kB = 8;
+    const int nblk = (D->n_balls + kB - 1) / kB;
     D->nblk = nblk;
-    std::vector<float> hb((size_t)std::max(1, nblk) * (d + 2) * 4, 0.0f);
-    for (int i = 0; i < nblk * 4; ++i) {
-        const int blk = i / 4, t = i % 4;
-        float *B = hb.data() + (size_t)blk * (d + 2) * 4;
+    std::vector<float> hb((size_t)std::max(1, nblk) * (d + 2) * kB, 0.0f);
+    for (int i = 0; i < nblk * kB; ++i) {
+        const int blk = i / kB, t = i % kB;
+        float *B = hb.data() + (size_t)blk * (d + 2) * kB;
         if (i < D->n_balls) {
             double cc = 0.0;
             for (int j = 0; j < d; ++j) {
                 const float c = (float)D->ball_c[(size_t)i * d + j];
-                B[4 * j + t] = -2.0f * c;
+                B[kB * j + t] = -2.0f * c;
                 cc += (double)c * (double)c;
             }
             const float r = (float)D->ball_r[i];
-            B[4 * d + t] = (float)(cc - (double)r * (double)r);
-            B[4 * (d + 1) + t] = -2.0f * r;
+            B[kB * d + t] = (float)(cc - (double)r * (double)r);
+            B[kB * (d + 1) + t] = -2.0f * r;
         } else {
             // padding ball: far away (never passes the screen), radius 0
-            for (int j = 0; j < d; ++j) B[4 * j + t] = 0.0f;
-            B[4 * d + t] = 3.0e38f;
-            B[4 * (d + 1) + t] = 0.0f;
+            for (int j = 0; j < d; ++j) B[kB * j + t] = 0.0f;
+            B[kB * d + t] = 3.0e38f;
+            B[kB * (d + 1) + t] = 0.0f;
         }
     }
     std::vector<float> hg((size_t)geom_floats(d), 0.0f);
@@ -701,6 +728,21 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
     }
     layout_view<double>(D->v64, D->f64, *D);
     layout_view<float>(D->v32, D->f32, *D);
+    if (D->n_points > 0 && d <= kPointCloudMaxD) {
+        e = pointcloud_prepare(D->points.data(), D->n_points, d, &D->pcd);
+        if (e != cudaSuccess) {
+            const wos_status st = fail(e == cudaErrorMemoryAllocation ? WOS_ERR_OOM : WOS_ERR_CUDA,
+                                       "point-cloud operand setup failed: %s", cudaGetErrorString(e));
+            wos_domain_destroy(D);
+            return st;
+        }
+        D->has_pcd = true;
+        double xabs = 0.0;
+        for (int j = 0; j < d; ++j)
+            xabs = std::max({xabs, std::fabs(D->box_lo[j]), std::fabs(D->box_hi[j]),
+                             std::fabs(D->outer_c[j]) + D->outer_r});
+        D->pc_delta = pointcloud_delta(d, xabs, D->pcd.pmax);
+    }
     *out = D;
     return WOS_OK;
 }
@@ -713,6 +755,7 @@ wos_status wos_domain_destroy(wos_domain_t dom) {
     cudaFree(dom->balls_mixed);
     cudaFree(dom->geom_mixed);
     for (float2 *t : dom->tables) cudaFree(t);
+    if (dom->has_pcd) pointcloud_release(&dom->pcd);
     delete dom;
     return WOS_OK;
 }
@@ -1162,14 +1205,15 @@ bool cache_lookup(const std::string &path, const std::string &sig, wos_batch_con
     if (path.empty()) return false;
     FILE *f = fopen(path.c_str(), "r");
     if (!f) return false;
-    char key[256];
+    char line[512], key[256];
     int th, ct;
     long long iw;
     double ms;
     bool found = false;
-    while (fscanf(f, "%255s %d %d %lld %lf", key, &th, &ct, &iw, &ms) == 5) {
-        if (sig == key) {  // the last entry for a signature wins
-            cfg->threads = th;
+    while (fgets(line, sizeof(line), f) != nullptr) {
+        if (line[0] == '#') continue;  // candidate timings
+        if (sscanf(line, "%255s %d %d %lld %lf", key, &th, &ct, &iw, &ms) == 5 && sig == key) {
+            cfg->threads = th;  // the last entry for a signature wins
             cfg->ctas_per_sm = ct;
             cfg->item_work = iw;
             found = true;
@@ -1191,8 +1235,8 @@ void free_batch_device(wos_batch_s *b) {
 wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     free_batch_device(b);
     wos_batch_config cfg = cfg_in;
-    if (cfg.threads < 32 || cfg.threads > 512 || cfg.threads % 32)
-        return fail(WOS_ERR_INVALID_ARG, "threads must be a multiple of 32 in 32..512");
+    if (cfg.threads < 32 || cfg.threads > 768 || cfg.threads % 32)
+        return fail(WOS_ERR_INVALID_ARG, "threads must be a multiple of 32 in 32..768");
     if (cfg.ctas_per_sm < 1 || cfg.ctas_per_sm > 8) return fail(WOS_ERR_INVALID_ARG, "ctas_per_sm in 1..8");
     if (cfg.item_work < 1) return fail(WOS_ERR_INVALID_ARG, "item_work must be positive");
     const int n = (int)b->probs.size();
@@ -1213,8 +1257,6 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     // problem records, accumulators and work items
     std::vector<MixedProblem> mp(n);
     std::vector<FinalizeRec> fr(n);
-    std::vector<MixedItem> items;
-    std::vector<double> item_cost;
     size_t acc_bytes = 0;
     std::vector<size_t> acc_off(n), cnt_off(n);
     for (int i = 0; i < n; ++i) {
@@ -1229,31 +1271,39 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     }
     const size_t off_items = align256(sizeof(MixedProblem) * n);
     int64_t walk_base = b->o.walk_offset, q_begin = 0;
+    // Items: at least 8 walks per lane (so the walk-length spread averages out before an item
+    // ends), about item_work units of work otherwise. Problems in decreasing order of total
+    // work, each problem's items consecutive: the long items go first, a CTA usually pulls its
+    // next item from the problem it has staged, and the tail of the launch is made of short
+    // items.
+    std::vector<double> prob_cost(n);
+    std::vector<int64_t> prob_wpi(n);
     for (int i = 0; i < n; ++i) {
         const wos_problem &p = b->probs[i];
         const double c = step_cost(*p.domain);
         int64_t wpi = (int64_t)((double)cfg.item_work / c);
-        wpi = std::max<int64_t>(cfg.threads, std::min<int64_t>(1 << 20, wpi));
-        wpi = (wpi + 31) / 32 * 32;
+        wpi = std::max<int64_t>(8 * (int64_t)cfg.threads, std::min<int64_t>(1 << 20, wpi));
+        prob_wpi[i] = (wpi + 31) / 32 * 32;
+        prob_cost[i] = c * (double)(p.n_queries * p.n_walks);
+        walk_base += p.n_queries * p.n_walks;
+        q_begin += p.n_queries;
+    }
+    std::vector<int> porder(n);
+    for (int i = 0; i < n; ++i) porder[i] = i;
+    std::stable_sort(porder.begin(), porder.end(),
+                     [&](int a, int c) { return prob_cost[a] > prob_cost[c]; });
+    std::vector<MixedItem> sorted;
+    for (int i : porder) {
+        const wos_problem &p = b->probs[i];
         const int64_t total = p.n_queries * p.n_walks;
-        for (int64_t j0 = 0; j0 < total; j0 += wpi) {
+        for (int64_t j0 = 0; j0 < total; j0 += prob_wpi[i]) {
             MixedItem it{};
             it.problem = i;
             it.j0 = j0;
-            it.j1 = std::min(total, j0 + wpi);
-            items.push_back(it);
-            item_cost.push_back(c * (double)(it.j1 - it.j0));
+            it.j1 = std::min(total, j0 + prob_wpi[i]);
+            sorted.push_back(it);
         }
-        walk_base += total;
-        q_begin += p.n_queries;
     }
-    // longest-first order (ties keep problem order so a CTA rarely restages its obstacles)
-    std::vector<size_t> order(items.size());
-    for (size_t k = 0; k < order.size(); ++k) order[k] = k;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](size_t a, size_t c) { return item_cost[a] > item_cost[c]; });
-    std::vector<MixedItem> sorted(items.size());
-    for (size_t k = 0; k < order.size(); ++k) sorted[k] = items[order[k]];
     b->n_items = (int64_t)sorted.size();
     b->total_q = q_begin;
     const size_t off_recs = off_items + align256(sizeof(MixedItem) * std::max<size_t>(1, sorted.size()));
@@ -1434,9 +1484,9 @@ wos_status wos_batch_autotune(wos_batch_t b, const char *cache_path, wos_batch_c
     if (b == nullptr) return fail(WOS_ERR_INVALID_ARG, "batch is NULL");
     const wos_batch_config start = b->cfg;
     std::vector<wos_batch_config> cands;
-    for (int th : {256, 512})
-        for (int ct : {1, 2})
-            for (int64_t iw : {(int64_t)1 << 24, (int64_t)1 << 26}) cands.push_back(wos_batch_config{th, ct, iw});
+    for (int th : {512, 768})
+        for (int64_t iw : {(int64_t)1 << 24, (int64_t)1 << 26}) cands.push_back(wos_batch_config{th, 1, iw});
+    cands.push_back(wos_batch_config{256, 2, (int64_t)1 << 26});
     cudaStream_t s;
     WOS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     cudaEvent_t e0, e1;
@@ -1444,6 +1494,7 @@ wos_status wos_batch_autotune(wos_batch_t b, const char *cache_path, wos_batch_c
     cudaEventCreate(&e1);
     double best_ms = 1e300;
     wos_batch_config best_cfg = start;
+    std::vector<std::pair<wos_batch_config, float>> timed;
     std::vector<std::pair<int, int>> seen;  // (threads, effective ctas) x item_work dedup
     for (const wos_batch_config &c : cands) {
         if (batch_build(b, c) != WOS_OK) continue;
@@ -1460,6 +1511,7 @@ wos_status wos_batch_autotune(wos_batch_t b, const char *cache_path, wos_batch_c
         if (cudaEventSynchronize(e1) != cudaSuccess) break;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
+        timed.push_back({b->cfg, ms});
         if (ms < best_ms) {
             best_ms = ms;
             best_cfg = b->cfg;
@@ -1474,6 +1526,9 @@ wos_status wos_batch_autotune(wos_batch_t b, const char *cache_path, wos_batch_c
         std::lock_guard<std::mutex> lk(g_cache_mu);
         FILE *f = fopen(cache_path, "a");
         if (f) {
+            for (const auto &t : timed)
+                fprintf(f, "# %s %d %d %lld %.4f\n", b->signature.c_str(), t.first.threads,
+                        t.first.ctas_per_sm, (long long)t.first.item_work, t.second);
             fprintf(f, "%s %d %d %lld %.4f\n", b->signature.c_str(), b->cfg.threads, b->cfg.ctas_per_sm,
                     (long long)b->cfg.item_work, best_ms);
             fclose(f);
@@ -1559,4 +1614,37 @@ extern "C" wos_status wos_solve_noalloc(wos_domain_t dom, const wos_options *opt
     r.u = u;
     r.u_se = u_se;
     return launch_finalize(a, s);
+}
+
+// =====================================================================================
+// point-cloud distance diagnostics
+// =====================================================================================
+extern "C" wos_status wos_debug_pointcloud_radius(wos_domain_t dom, const double *x, int64_t Q,
+                                                  double *radius, void *stream) {
+    WOS_TRY(check_common(dom, x, Q, 1, 1e-30, 0.0));
+    if (Q > 0 && radius == nullptr) return fail(WOS_ERR_INVALID_ARG, "radius is NULL");
+    if (!dom->has_pcd) return fail(WOS_ERR_UNSUPPORTED, "the domain has no tensor-core point set");
+    if (dom->n_balls > 0) return fail(WOS_ERR_UNSUPPORTED, "a domain with both balls and points");
+    if (Q == 0) return WOS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    WeightTable tab;
+    WOS_TRY(ensure_table(dom, 0.0, &tab));
+    const int nf = acc_fields(dom->d, dom->n_exp);
+    const size_t bytes = scratch_bytes(WOS_MIXED, Q, nf);
+    void *base = nullptr;
+    WOS_CUDA(cudaMallocAsync(&base, bytes, s));
+    const Scratch sc = carve_scratch(base, WOS_MIXED, Q, nf);
+    wos_status st = WOS_OK;
+    if (cudaMemsetAsync(base, 0, bytes, s) != cudaSuccess) st = fail(WOS_ERR_CUDA, "memset");
+    if (st == WOS_OK) {
+        // one distance evaluation per query: a walk capped at zero jumps
+        MixedProblem P = make_mixed_problem(dom, x, Q, 1, 1e-30, 0.0, 0, 0, 0, tab, (double *)sc.acc, sc.counts,
+                                            PerWalk{});
+        const cudaError_t e = launch_pointcloud(dom->pcd, P, dom->pc_delta, sc.cursor,
+                                                reinterpret_cast<int *>(sc.cursor + 2), sc.cursor + 1, 0, 0, 0, s,
+                                                radius);
+        if (e != cudaSuccess) st = fail(WOS_ERR_CUDA, "point-cloud probe failed: %s", cudaGetErrorString(e));
+    }
+    cudaFreeAsync(base, s);
+    return st;
 }

@@ -2,6 +2,7 @@
 // units. Not part of the public C ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -77,27 +78,60 @@ struct MixedLaunch {
 // Floats per packed ball record for dimension d.
 __host__ __device__ constexpr int ball_record_floats(int d) { return d + 2; }
 
-cudaError_t launch_walk_mixed_val(const MixedLaunch &L, int grid, int threads, size_t smem_bytes,
-                                  cudaStream_t s);
-cudaError_t launch_walk_mixed_grad(const MixedLaunch &L, int grid, int threads, size_t smem_bytes,
-                                   cudaStream_t s);
-cudaError_t configure_walk_mixed_val(size_t smem_bytes);
-cudaError_t configure_walk_mixed_grad(size_t smem_bytes);
-int max_active_mixed_val(int threads, size_t smem_bytes);
-int max_active_mixed_grad(int threads, size_t smem_bytes);
+cudaError_t configure_walk_mixed_val512(size_t smem_bytes);
+int max_active_walk_mixed_val512(int threads, size_t smem_bytes);
+cudaError_t launch_walk_mixed_val512(const MixedLaunch &L, int grid, int threads, size_t smem_bytes, cudaStream_t s);
+cudaError_t configure_walk_mixed_val768(size_t smem_bytes);
+int max_active_walk_mixed_val768(int threads, size_t smem_bytes);
+cudaError_t launch_walk_mixed_val768(const MixedLaunch &L, int grid, int threads, size_t smem_bytes, cudaStream_t s);
+cudaError_t configure_walk_mixed_grad512(size_t smem_bytes);
+int max_active_walk_mixed_grad512(int threads, size_t smem_bytes);
+cudaError_t launch_walk_mixed_grad512(const MixedLaunch &L, int grid, int threads, size_t smem_bytes, cudaStream_t s);
+cudaError_t configure_walk_mixed_grad768(size_t smem_bytes);
+int max_active_walk_mixed_grad768(int threads, size_t smem_bytes);
+cudaError_t launch_walk_mixed_grad768(const MixedLaunch &L, int grid, int threads, size_t smem_bytes, cudaStream_t s);
 
+// The persistent walker instantiations: value or gradient walks, CTAs of up to 512 or 768
+// threads (the 768 variant trades registers for resident warps).
 inline cudaError_t launch_walk_mixed(const MixedLaunch &L, int grad_any, int grid, int threads,
                                      size_t smem_bytes, cudaStream_t s) {
-    return grad_any ? launch_walk_mixed_grad(L, grid, threads, smem_bytes, s)
-                    : launch_walk_mixed_val(L, grid, threads, smem_bytes, s);
+    if (threads <= 512)
+        return grad_any ? launch_walk_mixed_grad512(L, grid, threads, smem_bytes, s)
+                        : launch_walk_mixed_val512(L, grid, threads, smem_bytes, s);
+    return grad_any ? launch_walk_mixed_grad768(L, grid, threads, smem_bytes, s)
+                    : launch_walk_mixed_val768(L, grid, threads, smem_bytes, s);
 }
 inline cudaError_t configure_walk_mixed(size_t smem_bytes) {
-    cudaError_t e = configure_walk_mixed_val(smem_bytes);
-    return e != cudaSuccess ? e : configure_walk_mixed_grad(smem_bytes);
+    cudaError_t e = configure_walk_mixed_val512(smem_bytes);
+    if (e == cudaSuccess) e = configure_walk_mixed_val768(smem_bytes);
+    if (e == cudaSuccess) e = configure_walk_mixed_grad512(smem_bytes);
+    if (e == cudaSuccess) e = configure_walk_mixed_grad768(smem_bytes);
+    return e;
 }
 inline int max_active_mixed(int threads, size_t smem_bytes, int grad_any) {
-    return grad_any ? max_active_mixed_grad(threads, smem_bytes)
-                    : max_active_mixed_val(threads, smem_bytes);
+    if (threads <= 512)
+        return grad_any ? max_active_walk_mixed_grad512(threads, smem_bytes)
+                        : max_active_walk_mixed_val512(threads, smem_bytes);
+    return grad_any ? max_active_walk_mixed_grad768(threads, smem_bytes)
+                    : max_active_walk_mixed_val768(threads, smem_bytes);
 }
+
+// Point-cloud obstacles for the tensor-core walker (pointcloud.cu): BF16-split point tiles in
+// the MMA's core-matrix layout, their TMA tensor map, and padded FP32 copies for refinement.
+struct PointCloudDev {
+    CUtensorMap tmap;
+    void *tiles = nullptr;
+    float *pts32 = nullptr;
+    int n_tiles = 0;
+    double pmax = 0.0;  // largest |coordinate| of a point
+};
+cudaError_t pointcloud_prepare(const double *pts, int64_t M, int d, PointCloudDev *out);
+void pointcloud_release(PointCloudDev *pcd);
+float pointcloud_delta(int d, double xabs, double pmax);
+cudaError_t launch_pointcloud(const PointCloudDev &pcd, const MixedProblem &P, float delta,
+                              unsigned long long *cursor, int *status, unsigned long long *shrinks,
+                              uint64_t seed, int64_t max_steps, int grad, cudaStream_t s,
+                              double *radius_out = nullptr);
+constexpr int kPointCloudMaxD = 10;  // 3d + 2 BF16 columns fit the 32-wide contraction
 
 }  // namespace wos
