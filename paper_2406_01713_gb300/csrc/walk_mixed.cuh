@@ -121,8 +121,6 @@ __device__ __forceinline__ float distance_mixed(const MixedProblem &P, const flo
     }
     // Running upper bound b of the distance used by the ball screen.
     float b = fminf(best, other);
-    float bball = CUDART_INF_F;
-    int bidx = -1;
     float xx = 0.f;
     f32x2 x2[D];
 #pragma unroll
@@ -132,6 +130,12 @@ __device__ __forceinline__ float distance_mixed(const MixedProblem &P, const flo
     }
     float thr = fmaf(b, b, slack - xx);
     f32x2 b2 = pack2(b, b);
+    // Passing balls are bounded, not recomputed: with L = |x-c|^2 - |x|^2 - r^2 - 2 r b_used,
+    // s = L + |x|^2 + r (r + 2 b_used) is |x-c|^2 up to the slack E, so
+    // lb = sqrt(s - E) - r <= d_i <= sqrt(s + E) - r = ub. The ball with the smallest lb is
+    // evaluated exactly after the scan; every other passing ball is bounded by its lb.
+    float lb1 = CUDART_INF_F, lb2 = CUDART_INF_F;
+    int bidx = -1;
     const ulonglong2 *B2 = reinterpret_cast<const ulonglong2 *>(balls);
 #pragma unroll 1
     for (int blk = 0; blk < nblk; ++blk) {
@@ -154,30 +158,44 @@ __device__ __forceinline__ float distance_mixed(const MixedProblem &P, const flo
         const float lmin = fminf(fmin3(l0.x, l0.y, l1.x), fmin3(fmin3(l1.y, l2.x, l2.y), l3.x, l3.y));
         if (lmin < thr) {
             const float Lt[8] = {l0.x, l0.y, l1.x, l1.y, l2.x, l2.y, l3.x, l3.y};
-            const float *Bf = reinterpret_cast<const float *>(F);
+            const float2 ea = unpack2(e1a.x), eb = unpack2(e1a.y), ec = unpack2(e1b.x), ed = unpack2(e1b.y);
+            const float Rt[8] = {-0.5f * ea.x, -0.5f * ea.y, -0.5f * eb.x, -0.5f * eb.y,
+                                 -0.5f * ec.x, -0.5f * ec.y, -0.5f * ed.x, -0.5f * ed.y};
+            const float bu = b;  // the bound these L values were computed with
 #pragma unroll
             for (int t = 0; t < kBallBlock; ++t) {
                 if (Lt[t] < thr) {
-                    float s = 0.f;
-#pragma unroll
-                    for (int j = 0; j < D; ++j) {
-                        const float dj = fmaf(0.5f, Bf[kBallBlock * j + t], x[j]);  // x_j - c_j
-                        s = fmaf(dj, dj, s);
-                    }
-                    const float r = -0.5f * Bf[kBallBlock * (D + 1) + t];
-                    const float dist = sqrtf(s) - r;
-                    if (dist < bball) {
-                        bball = dist;
+                    const float st = fmaf(Rt[t], fmaf(2.f, bu, Rt[t]), Lt[t] + xx);
+                    const float lb = sqrtf(fmaxf(st - slack, 0.f)) - Rt[t];
+                    const float ub = sqrtf(st + slack) - Rt[t];
+                    if (lb < lb1) {
+                        lb2 = lb1;
+                        lb1 = lb;
                         bidx = kBallBlock * blk + t;
-                        if (dist < b) {
-                            b = dist;
-                            thr = fmaf(b, b, slack - xx);
-                            b2 = pack2(b, b);
-                        }
+                    } else {
+                        lb2 = fminf(lb2, lb);
+                    }
+                    if (ub < b) {
+                        b = ub;
+                        thr = fmaf(b, b, slack - xx);
+                        b2 = pack2(b, b);
                     }
                 }
             }
         }
+    }
+    float bball = CUDART_INF_F;
+    if (bidx >= 0) {
+        // exact FP32 direct form for the best candidate; the others are bounded by lb2
+        const float *Bf = reinterpret_cast<const float *>(B2 + (bidx / kBallBlock) * 2 * (D + 2));
+        const int t = bidx % kBallBlock;
+        float s2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const float dj = fmaf(0.5f, Bf[kBallBlock * j + t], x[j]);  // x_j - c_j
+            s2 = fmaf(dj, dj, s2);
+        }
+        bball = fminf(sqrtf(s2) + 0.5f * Bf[kBallBlock * (D + 1) + t], lb2);
     }
     // Combine in the component order goal, balls, outer, faces (strict '<').
     if (bball < best) { best = bball; kind = kBall; idx = bidx; }
@@ -312,8 +330,10 @@ __device__ __forceinline__ void start_walk(const MixedProblem &P, MixedWalker<D>
     W.k = 0;
 }
 
+// Not inlined: each dimension gets its own register allocation instead of the maximum over
+// all eleven specialisations of the kernel.
 template <int D, bool GRAD>
-__device__ void run_item(const MixedLaunch &L, const MixedProblem &P, MixedSmem &S,
+__device__ __noinline__ void run_item(const MixedLaunch &L, const MixedProblem &P, MixedSmem &S,
                          const float4 *balls) {
     const int nblk = (P.n_balls + kBallBlock - 1) / kBallBlock;
     const float *geom = S.geom;

@@ -502,7 +502,7 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
     const size_t smem = mixed_smem_bytes(*dom);
     WOS_TRY(ensure_mixed_smem(smem));
     const int sms = device_sms();
-    int threads = (int)std::min<int64_t>(256, std::max<int64_t>(32, ((total / sms) + 31) / 32 * 32));
+    int threads = (int)std::min<int64_t>(512, std::max<int64_t>(32, ((total / sms) + 31) / 32 * 32));
     int occ = max_active_mixed(threads, smem, grad_mode);
     if (occ < 1) return fail(WOS_ERR_UNSUPPORTED, "mixed walker does not fit (%zu B smem)", smem);
     const int64_t grid_full = (int64_t)sms * occ;
