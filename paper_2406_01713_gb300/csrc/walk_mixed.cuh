@@ -142,18 +142,38 @@ __device__ __forceinline__ float distance_mixed(const MixedProblem &P, const flo
         const ulonglong2 *F = B2 + blk * 2 * (D + 2);
         const ulonglong2 e0a = F[2 * D], e0b = F[2 * D + 1];
         const ulonglong2 e1a = F[2 * D + 2], e1b = F[2 * D + 3];
+        // two half-sums over the coordinates: eight independent packed FMA chains per block
+        constexpr int H = D / 2;
         f32x2 L0 = ffma2(e1a.x, b2, e0a.x);
         f32x2 L1 = ffma2(e1a.y, b2, e0a.y);
         f32x2 L2 = ffma2(e1b.x, b2, e0b.x);
         f32x2 L3 = ffma2(e1b.y, b2, e0b.y);
+        f32x2 M0 = 0ull, M1 = 0ull, M2 = 0ull, M3 = 0ull;
 #pragma unroll
-        for (int j = 0; j < D; ++j) {
+        for (int j = 0; j < H; ++j) {
             const ulonglong2 ma = F[2 * j], mb = F[2 * j + 1];
+            const ulonglong2 na = F[2 * (j + H)], nb = F[2 * (j + H) + 1];
             L0 = ffma2(x2[j], ma.x, L0);
             L1 = ffma2(x2[j], ma.y, L1);
             L2 = ffma2(x2[j], mb.x, L2);
             L3 = ffma2(x2[j], mb.y, L3);
+            M0 = ffma2(x2[j + H], na.x, M0);
+            M1 = ffma2(x2[j + H], na.y, M1);
+            M2 = ffma2(x2[j + H], nb.x, M2);
+            M3 = ffma2(x2[j + H], nb.y, M3);
         }
+        if constexpr (D % 2 == 1) {
+            const ulonglong2 ma = F[2 * (D - 1)], mb = F[2 * (D - 1) + 1];
+            L0 = ffma2(x2[D - 1], ma.x, L0);
+            L1 = ffma2(x2[D - 1], ma.y, L1);
+            L2 = ffma2(x2[D - 1], mb.x, L2);
+            L3 = ffma2(x2[D - 1], mb.y, L3);
+        }
+        const f32x2 one2 = pack2(1.f, 1.f);
+        L0 = ffma2(one2, M0, L0);
+        L1 = ffma2(one2, M1, L1);
+        L2 = ffma2(one2, M2, L2);
+        L3 = ffma2(one2, M3, L3);
         const float2 l0 = unpack2(L0), l1 = unpack2(L1), l2 = unpack2(L2), l3 = unpack2(L3);
         const float lmin = fminf(fmin3(l0.x, l0.y, l1.x), fmin3(fmin3(l1.y, l2.x, l2.y), l3.x, l3.y));
         if (lmin < thr) {

@@ -501,15 +501,30 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
     if (total > (int64_t)0x7fffffff) return fail(WOS_ERR_UNSUPPORTED, "Q * n_walks must be < 2^31");
     const size_t smem = mixed_smem_bytes(*dom);
     WOS_TRY(ensure_mixed_smem(smem));
+    // Launch shape. Few walks (a planner step): one walk per lane, as many lanes as walks, for
+    // latency. Many walks: at least 8 walks per lane per item, so that the spread of walk
+    // lengths averages out before an item ends, and at least as many items as CTAs.
     const int sms = device_sms();
-    int threads = (int)std::min<int64_t>(512, std::max<int64_t>(32, ((total / sms) + 31) / 32 * 32));
-    int occ = max_active_mixed(threads, smem, grad_mode);
-    if (occ < 1) return fail(WOS_ERR_UNSUPPORTED, "mixed walker does not fit (%zu B smem)", smem);
-    const int64_t grid_full = (int64_t)sms * occ;
-    int64_t wpi = (total + 4 * grid_full - 1) / (4 * grid_full);
-    wpi = std::max<int64_t>(threads, std::min<int64_t>(1 << 20, (wpi + 31) / 32 * 32));
+    int threads;
+    int64_t wpi;
+    int grid;
+    if (total <= (int64_t)sms * 512) {
+        threads = (int)std::min<int64_t>(512, std::max<int64_t>(32, (total / sms + 31) / 32 * 32));
+        if (max_active_mixed(threads, smem, grad_mode) < 1)
+            return fail(WOS_ERR_UNSUPPORTED, "mixed walker does not fit (%zu B smem)", smem);
+        wpi = threads;
+        grid = (int)((total + wpi - 1) / wpi);
+    } else {
+        threads = (int)std::min<int64_t>(512, std::max<int64_t>(32, (total / (8LL * sms) + 31) / 32 * 32));
+        const int occ = max_active_mixed(threads, smem, grad_mode);
+        if (occ < 1) return fail(WOS_ERR_UNSUPPORTED, "mixed walker does not fit (%zu B smem)", smem);
+        const int64_t grid_full = (int64_t)sms * occ;
+        wpi = std::max<int64_t>(8LL * threads, (total + 4 * grid_full - 1) / (4 * grid_full));
+        wpi = std::min<int64_t>(wpi, 1 << 22);
+        wpi = (wpi + 31) / 32 * 32;
+        grid = (int)std::min<int64_t>(grid_full, (total + wpi - 1) / wpi);
+    }
     const int64_t n_items = (total + wpi - 1) / wpi;
-    const int grid = (int)std::min<int64_t>(grid_full, n_items);
     MixedLaunch L{};
     L.problems = nullptr;
     L.items = nullptr;
