@@ -56,6 +56,54 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def replica_seed(base_seed, rank):
+    """Walk seed of a replica: ranks draw disjoint random streams (independent estimates)."""
+    return base_seed + 1000003 * rank
+
+
+def aggregate_over_ranks(seconds, units, world, device="cpu"):
+    """Replica aggregation: the job takes as long as its slowest rank and processes the units of
+    all ranks. Returns (max seconds over ranks, total units, value = total units / max seconds).
+    With world == 1 no process group is used."""
+    if world <= 1:
+        return seconds, units, units / seconds
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0]), float(u[0]) / float(t[0])
+
+
+KERNEL_SOURCES = ["paper_2406_01713_gb300/csrc/walk_mixed.cuh", "paper_2406_01713_gb300/csrc/wos_device.cuh",
+                  "paper_2406_01713_gb300/csrc/wos_launch.h"]
+TRAFFIC_PROFILE = "profiles/walk_mixed_batched_traffic.txt"
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the batched walker from the committed ncu summary, or None when
+    the kernel sources changed since that capture."""
+    import hashlib
+
+    try:
+        h = hashlib.sha256()
+        for f in KERNEL_SOURCES:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        vals = {}
+        for line in open(os.path.join(ROOT, TRAFFIC_PROFILE)):
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v = line.split()
+            vals[k] = v
+        if vals.get("kernel_sources_sha256") != h.hexdigest():
+            return None
+        return int(vals["dram_bytes_read"]) + int(vals["dram_bytes_write"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def alg_flops_per_step(d, n_balls):
     """Algorithmic FP32 flops of one walk step (one distance evaluation): the ball screen
     costs 2d+3 flops per ball (d FMAs of x.m, the b-term FMA and the threshold add), the
@@ -212,7 +260,8 @@ def main():
         launch = {"threads": th, "ctas_per_sm": ct, "item_work": iw}
         args.no_autotune = True
     batch = W.Batch([{"domain": d, "x": p["X"], "n_walks": p["n_walks"], "eps": p["eps"], "sigma": p["sigma"],
-                      "grad": True} for d, p in zip(doms, probs)], seed=w["seed"] + 1000003 * rank, config=launch)
+                      "grad": True} for d, p in zip(doms, probs)], seed=replica_seed(w["seed"], rank),
+                    config=launch)
     cache = os.environ.get("WOS_AUTOTUNE_CACHE",
                            os.path.join(ROOT, "paper_2406_01713_gb300", "csrc", "_build", "autotune_cache.txt"))
     log("workload ready: %d problems" % len(probs))
@@ -251,12 +300,7 @@ def main():
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     log("timed steps (ms)", [round(x, 2) for x in step_ms])
-    dev_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dev_s = float(t[0])
-    value = total_steps * args.steps * world / dev_s
+    dev_s, _, value = aggregate_over_ranks(sum(step_ms) / 1e3, total_steps * args.steps, world, device="cuda")
     ms_per_step = 1e3 * dev_s / args.steps
 
     # accuracy: exact solution u = exp(a.x), grad u = a u on the exponential-data problems
@@ -300,7 +344,9 @@ def main():
     peak_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     achieved = flops / (ms_per_step / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None,
+                "frac": achieved / peak_tflops, "traffic": measured_traffic(),
+                "traffic_note": "ncu dram__bytes_read+write per launch (profiles/walk_mixed_batched_traffic.txt); "
+                                "algorithmic bytes are not the bound: balls, queries and sums are L2-resident",
                 "kernel": "walk_mixed_kernel<true> (persistent batched walker)",
                 "peak_note": "FP32 FMA pipe: %d SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % (
                     props.multi_processor_count, sm_max),
@@ -408,6 +454,21 @@ def secondary(W, synth):
     t2 = time.perf_counter()
     out["differentiable_6d"] = {"forward_ms": 1e3 * (t1 - t), "forward_backward_ms": 1e3 * (t2 - t1),
                                 "walk_steps_per_s": int(r["stats"][1]) / (t1 - t)}
+    # point-cloud C-space, d = 7: 65536 points, tensor-core distance; 2048 of the 8192 queries
+    w = synth.c3()
+    dom = W.Domain(w["domain"])
+    Xs = w["X"][:2048]
+    dom.solve(Xs[:128], 256, w["eps"], w["sigma"], seed=w["seed"])
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    r = dom.solve(Xs, w["n_walks"], w["eps"], w["sigma"], seed=w["seed"], with_stats=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    st = W.stats_dict(r["stats"])
+    out["pointcloud_7d"] = {"queries": 2048, "walks_per_query": w["n_walks"], "ms": 1e3 * dt,
+                            "walk_steps_per_s": st["walk_steps"] / dt,
+                            "point_distance_evals_per_s": st["walk_steps"] * w["domain"]["points"].shape[0] / dt,
+                            "bound_shrinks": st["shrinks"]}
     # plain FP64 d=2 check workload
     w = synth.c1()
     dom = W.Domain(w["domain"])
