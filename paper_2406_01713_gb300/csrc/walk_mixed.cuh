@@ -17,8 +17,13 @@
 // distance b if |x-c|^2 < (r+b)^2, i.e. if
 //     L = e0 + e1 b + x.m  <  b^2 - |x|^2.
 // L is evaluated in FP32 for every ball (d+1 FMAs) and compared against the threshold plus a
-// slack E that bounds the FP32 rounding of both sides, so no true candidate is ever missed;
-// candidates are then refined with the direct form sqrt(sum (x_j - c_j)^2) - r.
+// slack E that bounds the FP32 rounding of both sides, so no true candidate is ever missed.
+// Passing balls get distance bounds rebuilt from L; after the scan the best candidate is
+// evaluated exactly with the direct form sqrt(sum (x_j - c_j)^2) - r.
+//
+// Walker positions are held as packed pairs (x_j, x_j), the operand the packed FMAs need. Each
+// walker's coordinate sum is split into two halves, so one 8-ball block gives eight
+// independent FMA chains.
 // The radius used for the jump is the computed distance minus `shrink`, a bound on the FP32
 // error of the distance evaluation and of the position update, so every sphere lies inside
 // the FP64 domain.
@@ -39,16 +44,6 @@ struct MixedSmem {
     unsigned end_walk;
     unsigned begin_walk;
     long long item;
-};
-
-template <int D>
-struct MixedWalker {
-    float x[D];
-    float logw, dsig, gfac0;  // gfac0 = alpha(R0) / C(R0); v0 is regenerated from its counter
-    int k;
-    unsigned j;      // walk index within the problem
-    long long q;     // query
-    bool active;
 };
 
 // ---- packed FP32x2 helpers (sm_100+: fma.rn.f32x2, three-input min.f32) -----------------
@@ -75,36 +70,46 @@ __device__ __forceinline__ float fmin3(float a, float b, float c) {
     return r;
 }
 
+
 constexpr int kBallBlock = 8;  // balls per shared-memory block
 
-// geom layout in shared memory: [0,d) box lo, [d,2d) box hi, [2d,3d) goal c, [3d,4d) outer c,
-// [4d, 4d+K) exp w, then K x d exp a.
 template <int D>
-__device__ __forceinline__ float distance_mixed(const MixedProblem &P, const float *geom,
-                                                const float4 *balls, int nblk,
-                                                const float (&x)[D], float slack, int &kind,
-                                                int &idx) {
-    float best = CUDART_INF_F;
-    kind = -1;
-    idx = -1;
+struct MixedWalker {
+    f32x2 x2[D];              // position as packed pairs (x_j, x_j)
+    float logw, dsig, gfac0;  // gfac0 = alpha(R0) / C(R0); v0 is regenerated from its counter
+    int k;
+    unsigned j;      // walk index within the problem
+    long long q;     // query
+    bool active;
+};
+
+template <int D>
+__device__ __forceinline__ float xj(const f32x2 (&x2)[D], int j) { return unpack2(x2[j]).x; }
+
+// Distance to the components other than the balls. geom layout in shared memory: [0,d) box lo,
+// [d,2d) box hi, [2d,3d) goal c, [3d,4d) outer c, [4d, 4d+K) exp w, then K x d exp a.
+template <int D>
+__device__ __forceinline__ void other_components(const MixedProblem &P, const float *geom,
+                                                 const f32x2 (&x2)[D], float &goal, float &other,
+                                                 int &okind, int &oidx) {
+    goal = CUDART_INF_F;
+    other = CUDART_INF_F;
+    okind = -1;
+    oidx = -1;
     if (P.has_goal) {
         float s = 0.f;
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            const float t = x[j] - geom[2 * D + j];
+            const float t = xj(x2, j) - geom[2 * D + j];
             s = fmaf(t, t, s);
         }
-        const float r = sqrtf(s) - P.goal_r;
-        if (r < best) { best = r; kind = kGoal; idx = 0; }
+        goal = sqrtf(s) - P.goal_r;
     }
-    // Balls are searched below; the other components go first so that the bound starts small.
-    float other = CUDART_INF_F;
-    int okind = -1, oidx = -1;
     if (P.has_outer) {
         float s = 0.f;
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            const float t = x[j] - geom[3 * D + j];
+            const float t = xj(x2, j) - geom[3 * D + j];
             s = fmaf(t, t, s);
         }
         const float r = P.outer_r - sqrtf(s);
@@ -113,41 +118,128 @@ __device__ __forceinline__ float distance_mixed(const MixedProblem &P, const flo
     if (P.has_box) {
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            const float rlo = x[j] - geom[j];
+            const float rlo = xj(x2, j) - geom[j];
             if (rlo < other) { other = rlo; okind = kFace; oidx = 2 * j; }
-            const float rhi = geom[D + j] - x[j];
+            const float rhi = geom[D + j] - xj(x2, j);
             if (rhi < other) { other = rhi; okind = kFace; oidx = 2 * j + 1; }
         }
     }
-    // Running upper bound b of the distance used by the ball screen.
-    float b = fminf(best, other);
+}
+
+// Per-walker state of the ball screen. b: running upper bound of the distance (starts at the
+// nearest other component); thr = b^2 - |x|^2 + E; lb1/lb2/bidx: the smallest and second
+// smallest lower bound among the balls that passed, and the ball of the smallest.
+struct ScreenState {
+    float b, thr, xx, lb1, lb2;
+    f32x2 b2;
+    int bidx;
+};
+
+template <int D>
+__device__ __forceinline__ void screen_init(ScreenState &S, const f32x2 (&x2)[D], float b0, float slack) {
     float xx = 0.f;
-    f32x2 x2[D];
 #pragma unroll
-    for (int j = 0; j < D; ++j) {
-        xx = fmaf(x[j], x[j], xx);
-        x2[j] = pack2(x[j], x[j]);
+    for (int j = 0; j < D; ++j) xx = fmaf(xj(x2, j), xj(x2, j), xx);
+    S.xx = xx;
+    S.b = b0;
+    S.thr = fmaf(b0, b0, slack - xx);
+    S.b2 = pack2(b0, b0);
+    S.lb1 = CUDART_INF_F;
+    S.lb2 = CUDART_INF_F;
+    S.bidx = -1;
+}
+
+// Balls of one block that passed the screen: with L = |x-c|^2 - |x|^2 - r^2 - 2 r b_used,
+// s = L + |x|^2 + r (r + 2 b_used) is |x-c|^2 up to the slack E, so
+// lb = sqrt(s - E) - r <= d_i <= sqrt(s + E) - r = ub.
+__device__ __forceinline__ void screen_passing(ScreenState &S, const float (&Lt)[kBallBlock],
+                                               const float (&Rt)[kBallBlock], float slack, int blk) {
+    const float bu = S.b;  // the bound these L values were computed with
+#pragma unroll
+    for (int t = 0; t < kBallBlock; ++t) {
+        if (Lt[t] < S.thr) {
+            const float st = fmaf(Rt[t], fmaf(2.f, bu, Rt[t]), Lt[t] + S.xx);
+            const float lb = sqrtf(fmaxf(st - slack, 0.f)) - Rt[t];
+            const float ub = sqrtf(st + slack) - Rt[t];
+            if (lb < S.lb1) {
+                S.lb2 = S.lb1;
+                S.lb1 = lb;
+                S.bidx = kBallBlock * blk + t;
+            } else {
+                S.lb2 = fminf(S.lb2, lb);
+            }
+            if (ub < S.b) {
+                S.b = ub;
+                S.thr = fmaf(ub, ub, slack - S.xx);
+                S.b2 = pack2(ub, ub);
+            }
+        }
     }
-    float thr = fmaf(b, b, slack - xx);
-    f32x2 b2 = pack2(b, b);
-    // Passing balls are bounded, not recomputed: with L = |x-c|^2 - |x|^2 - r^2 - 2 r b_used,
-    // s = L + |x|^2 + r (r + 2 b_used) is |x-c|^2 up to the slack E, so
-    // lb = sqrt(s - E) - r <= d_i <= sqrt(s + E) - r = ub. The ball with the smallest lb is
-    // evaluated exactly after the scan; every other passing ball is bounded by its lb.
-    float lb1 = CUDART_INF_F, lb2 = CUDART_INF_F;
-    int bidx = -1;
+}
+
+__device__ __forceinline__ void block_radii(const ulonglong2 &e1a, const ulonglong2 &e1b,
+                                            float (&Rt)[kBallBlock]) {
+    const float2 ea = unpack2(e1a.x), eb = unpack2(e1a.y), ec = unpack2(e1b.x), ed = unpack2(e1b.y);
+    Rt[0] = -0.5f * ea.x; Rt[1] = -0.5f * ea.y; Rt[2] = -0.5f * eb.x; Rt[3] = -0.5f * eb.y;
+    Rt[4] = -0.5f * ec.x; Rt[5] = -0.5f * ec.y; Rt[6] = -0.5f * ed.x; Rt[7] = -0.5f * ed.y;
+}
+
+__device__ __forceinline__ float block_min(const f32x2 &L0, const f32x2 &L1, const f32x2 &L2, const f32x2 &L3,
+                                           float (&Lt)[kBallBlock]) {
+    const float2 l0 = unpack2(L0), l1 = unpack2(L1), l2 = unpack2(L2), l3 = unpack2(L3);
+    Lt[0] = l0.x; Lt[1] = l0.y; Lt[2] = l1.x; Lt[3] = l1.y;
+    Lt[4] = l2.x; Lt[5] = l2.y; Lt[6] = l3.x; Lt[7] = l3.y;
+    return fminf(fmin3(l0.x, l0.y, l1.x), fmin3(fmin3(l1.y, l2.x, l2.y), l3.x, l3.y));
+}
+
+// After the scan: exact FP32 direct form for the best candidate (others bounded by lb2), then
+// the component order goal, balls, outer, faces (strict '<').
+template <int D>
+__device__ __forceinline__ float screen_finish(const ScreenState &S, const ulonglong2 *B2,
+                                               const f32x2 (&x2)[D], float goal, float other,
+                                               int okind, int oidx, int &kind, int &idx) {
+    float best = CUDART_INF_F;
+    kind = -1;
+    idx = -1;
+    if (goal < best) { best = goal; kind = kGoal; idx = 0; }
+    float bball = CUDART_INF_F;
+    if (S.bidx >= 0) {
+        const float *Bf = reinterpret_cast<const float *>(B2 + (S.bidx / kBallBlock) * 2 * (D + 2));
+        const int t = S.bidx % kBallBlock;
+        float s2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const float dj = fmaf(0.5f, Bf[kBallBlock * j + t], xj(x2, j));  // x_j - c_j
+            s2 = fmaf(dj, dj, s2);
+        }
+        bball = fminf(sqrtf(s2) + 0.5f * Bf[kBallBlock * (D + 1) + t], S.lb2);
+    }
+    if (bball < best) { best = bball; kind = kBall; idx = S.bidx; }
+    if (other < best) { best = other; kind = okind; idx = oidx; }
+    return best;
+}
+
+template <int D>
+__device__ __forceinline__ float distance_mixed(const MixedProblem &P, const float *geom,
+                                                const float4 *balls, int nblk,
+                                                const f32x2 (&x2)[D], float slack, int &kind,
+                                                int &idx) {
+    float goal, other;
+    int okind, oidx;
+    other_components<D>(P, geom, x2, goal, other, okind, oidx);
+    ScreenState S;
+    screen_init<D>(S, x2, fminf(goal, other), slack);
     const ulonglong2 *B2 = reinterpret_cast<const ulonglong2 *>(balls);
+    constexpr int H = D / 2;
 #pragma unroll 1
     for (int blk = 0; blk < nblk; ++blk) {
         const ulonglong2 *F = B2 + blk * 2 * (D + 2);
         const ulonglong2 e0a = F[2 * D], e0b = F[2 * D + 1];
         const ulonglong2 e1a = F[2 * D + 2], e1b = F[2 * D + 3];
-        // two half-sums over the coordinates: eight independent packed FMA chains per block
-        constexpr int H = D / 2;
-        f32x2 L0 = ffma2(e1a.x, b2, e0a.x);
-        f32x2 L1 = ffma2(e1a.y, b2, e0a.y);
-        f32x2 L2 = ffma2(e1b.x, b2, e0b.x);
-        f32x2 L3 = ffma2(e1b.y, b2, e0b.y);
+        f32x2 L0 = ffma2(e1a.x, S.b2, e0a.x);
+        f32x2 L1 = ffma2(e1a.y, S.b2, e0a.y);
+        f32x2 L2 = ffma2(e1b.x, S.b2, e0b.x);
+        f32x2 L3 = ffma2(e1b.y, S.b2, e0b.y);
         f32x2 M0 = 0ull, M1 = 0ull, M2 = 0ull, M3 = 0ull;
 #pragma unroll
         for (int j = 0; j < H; ++j) {
@@ -174,60 +266,21 @@ __device__ __forceinline__ float distance_mixed(const MixedProblem &P, const flo
         L1 = ffma2(one2, M1, L1);
         L2 = ffma2(one2, M2, L2);
         L3 = ffma2(one2, M3, L3);
-        const float2 l0 = unpack2(L0), l1 = unpack2(L1), l2 = unpack2(L2), l3 = unpack2(L3);
-        const float lmin = fminf(fmin3(l0.x, l0.y, l1.x), fmin3(fmin3(l1.y, l2.x, l2.y), l3.x, l3.y));
-        if (lmin < thr) {
-            const float Lt[8] = {l0.x, l0.y, l1.x, l1.y, l2.x, l2.y, l3.x, l3.y};
-            const float2 ea = unpack2(e1a.x), eb = unpack2(e1a.y), ec = unpack2(e1b.x), ed = unpack2(e1b.y);
-            const float Rt[8] = {-0.5f * ea.x, -0.5f * ea.y, -0.5f * eb.x, -0.5f * eb.y,
-                                 -0.5f * ec.x, -0.5f * ec.y, -0.5f * ed.x, -0.5f * ed.y};
-            const float bu = b;  // the bound these L values were computed with
-#pragma unroll
-            for (int t = 0; t < kBallBlock; ++t) {
-                if (Lt[t] < thr) {
-                    const float st = fmaf(Rt[t], fmaf(2.f, bu, Rt[t]), Lt[t] + xx);
-                    const float lb = sqrtf(fmaxf(st - slack, 0.f)) - Rt[t];
-                    const float ub = sqrtf(st + slack) - Rt[t];
-                    if (lb < lb1) {
-                        lb2 = lb1;
-                        lb1 = lb;
-                        bidx = kBallBlock * blk + t;
-                    } else {
-                        lb2 = fminf(lb2, lb);
-                    }
-                    if (ub < b) {
-                        b = ub;
-                        thr = fmaf(b, b, slack - xx);
-                        b2 = pack2(b, b);
-                    }
-                }
-            }
+        float Lt[kBallBlock];
+        if (block_min(L0, L1, L2, L3, Lt) < S.thr) {
+            float Rt[kBallBlock];
+            block_radii(e1a, e1b, Rt);
+            screen_passing(S, Lt, Rt, slack, blk);
         }
     }
-    float bball = CUDART_INF_F;
-    if (bidx >= 0) {
-        // exact FP32 direct form for the best candidate; the others are bounded by lb2
-        const float *Bf = reinterpret_cast<const float *>(B2 + (bidx / kBallBlock) * 2 * (D + 2));
-        const int t = bidx % kBallBlock;
-        float s2 = 0.f;
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            const float dj = fmaf(0.5f, Bf[kBallBlock * j + t], x[j]);  // x_j - c_j
-            s2 = fmaf(dj, dj, s2);
-        }
-        bball = fminf(sqrtf(s2) + 0.5f * Bf[kBallBlock * (D + 1) + t], lb2);
-    }
-    // Combine in the component order goal, balls, outer, faces (strict '<').
-    if (bball < best) { best = bball; kind = kBall; idx = bidx; }
-    if (other < best) { best = other; kind = okind; idx = oidx; }
-    return best;
+    return screen_finish<D>(S, B2, x2, goal, other, okind, oidx, kind, idx);
 }
 
-// Closest boundary point and g there, in log space: returns log(g) + logw contributions as
-// t = g * exp(logw) and e[k] = exp(a_k . xbar + logw).
+// Closest boundary point and g there, in log space: returns g(xbar) exp(logw) and
+// e[k] = exp(a_k . xbar + logw).
 template <int D>
 __device__ __forceinline__ float terminal_value(const MixedProblem &P, const float *geom,
-                                                const float4 *balls, const float (&x)[D],
+                                                const float4 *balls, const f32x2 (&x2)[D],
                                                 int kind, int idx, float logw,
                                                 float (&e)[kMaxExp]) {
     float xb[D];
@@ -252,17 +305,17 @@ __device__ __forceinline__ float terminal_value(const MixedProblem &P, const flo
         float s = 0.f;
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            const float t = x[j] - cc[j];
+            const float t = xj(x2, j) - cc[j];
             s = fmaf(t, t, s);
         }
         const float len = sqrtf(s);
         const float f = len > 0.f ? rad / len : 0.f;
 #pragma unroll
         for (int j = 0; j < D; ++j)
-            xb[j] = len > 0.f ? fmaf(f, x[j] - cc[j], cc[j]) : cc[j] + (j == 0 ? rad : 0.f);
+            xb[j] = len > 0.f ? fmaf(f, xj(x2, j) - cc[j], cc[j]) : cc[j] + (j == 0 ? rad : 0.f);
     } else {
 #pragma unroll
-        for (int j = 0; j < D; ++j) xb[j] = x[j];
+        for (int j = 0; j < D; ++j) xb[j] = xj(x2, j);
         if (kind == kFace) {
             const int jf = idx >> 1;
 #pragma unroll
@@ -343,82 +396,100 @@ __device__ __forceinline__ void start_walk(const MixedProblem &P, MixedWalker<D>
     W.q = (long long)(j / (unsigned long long)P.N);
     const double *xq = P.x + W.q * D;
 #pragma unroll
-    for (int i = 0; i < D; ++i) W.x[i] = (float)__ldg(xq + i);
+    for (int i = 0; i < D; ++i) {
+        const float v = (float)__ldg(xq + i);
+        W.x2[i] = pack2(v, v);
+    }
     W.logw = 0.f;
     W.dsig = 0.f;
     W.gfac0 = 0.f;
     W.k = 0;
 }
 
+template <int D, bool GRAD>
+__device__ __forceinline__ void first_walk(const MixedProblem &P, MixedSmem &S, MixedWalker<D> &W,
+                                           unsigned end) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) W.x2[i] = 0ull;
+    const unsigned j = grab_walk(S);
+    W.active = j < end;
+    if (W.active) start_walk<D, GRAD>(P, W, j);
+}
+
+// Everything after the distance of one step: the eps test, the cap, the jump (sphere sample,
+// screened weight, first-sphere gradient factor) or the end of the walk (boundary value,
+// contribution, per-walk record) and the refill.
+template <int D, bool GRAD>
+__device__ __forceinline__ void step_walker(const MixedLaunch &L, const MixedProblem &P, MixedSmem &S,
+                                            const float4 *balls, const float *geom, MixedWalker<D> &W,
+                                            float R, int kind, int idx, unsigned end) {
+    int outcome = 0;  // 0 jump, 1 boundary reached, 2 capped, 3 query outside
+    if (W.k == 0 && !(R > 0.f))
+        outcome = 3;
+    else if (R < P.eps && !(GRAD && P.grad_mode && W.k == 0))
+        outcome = 1;
+    else if (W.k >= L.max_steps)
+        outcome = 2;
+    if (outcome == 0) {
+        float v[D];
+        direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + (long long)W.j), (uint32_t)W.k, v);
+        const float2 t = table_lookup(P.table, R * P.sqrt_sigma);
+        if (GRAD && W.k == 0) {
+            // alpha(R0) u^(x_1) = (d/R0) C_{nu+1}(z0) term / C_nu(z0) = (d/R0) term / ratio(z0)
+            W.gfac0 = P.laplace ? ((float)D / R) * __expf(-t.x) : ((float)D / R) / t.y;
+        }
+        W.logw += t.x;
+        W.dsig = fmaf(-(R * R) * (1.0f / (2.0f * (float)D)), t.y, W.dsig);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const float xn = fmaf(R, v[i], xj(W.x2, i));
+            W.x2[i] = pack2(xn, xn);
+        }
+        ++W.k;
+        return;
+    }
+    // ---- the walk ended: contribution, per-walk record, refill
+    float term = 0.f;
+    float e[kMaxExp];
+#pragma unroll
+    for (int k = 0; k < kMaxExp; ++k) e[k] = 0.f;
+    if (outcome == 1) term = terminal_value<D>(P, geom, balls, W.x2, kind, idx, W.logw, e);
+    const bool has_grad = GRAD && outcome == 1 && W.k > 0;
+    float v0[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) v0[i] = 0.f;
+    if constexpr (GRAD) {
+        if (has_grad) direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + (long long)W.j), 0u, v0);
+    }
+    const float gt = has_grad ? W.gfac0 * term : 0.f;
+    add_walk<D, GRAD>(P, W.q, outcome, W.k, term, W.dsig, gt, v0, e);
+    if (P.w_term != nullptr) P.w_term[W.j] = outcome == 3 ? (double)CUDART_NAN : (double)term;
+    if (P.w_jumps != nullptr) P.w_jumps[W.j] = W.k;
+    if (P.w_dsigma != nullptr) P.w_dsigma[W.j] = (double)(term * W.dsig);
+    if (P.w_grad != nullptr) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) P.w_grad[(long long)W.j * D + i] = (double)(gt * v0[i]);
+    }
+    const unsigned nj = grab_walk(S);
+    W.active = nj < end;
+    if (W.active) start_walk<D, GRAD>(P, W, nj);
+}
+
 // Not inlined: each dimension gets its own register allocation instead of the maximum over
-// all eleven specialisations of the kernel.
+// all eleven specialisations of the kernel. One walker per thread.
 template <int D, bool GRAD>
 __device__ __noinline__ void run_item(const MixedLaunch &L, const MixedProblem &P, MixedSmem &S,
-                         const float4 *balls) {
+                                      const float4 *balls) {
     const int nblk = (P.n_balls + kBallBlock - 1) / kBallBlock;
     const float *geom = S.geom;
     const unsigned end = S.end_walk;
-    const float inv2d = 1.0f / (2.0f * (float)D);
     MixedWalker<D> W;
-    {
-        const unsigned j = grab_walk(S);
-        W.active = j < end;
-        if (W.active) start_walk<D, GRAD>(P, W, j);
-    }
+    first_walk<D, GRAD>(P, S, W, end);
     while (__any_sync(0xffffffffu, W.active)) {
         if (!W.active) continue;
         int kind, idx;
-        const float R =
-            distance_mixed<D>(P, geom, balls, nblk, W.x, P.slack, kind, idx) - P.shrink;
-        int outcome = 0;  // 0 jump, 1 boundary reached, 2 capped, 3 query outside
-        if (W.k == 0 && !(R > 0.f))
-            outcome = 3;
-        else if (R < P.eps && !(GRAD && P.grad_mode && W.k == 0))
-            outcome = 1;
-        else if (W.k >= L.max_steps)
-            outcome = 2;
-        if (outcome == 0) {
-            float v[D];
-            direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + (long long)W.j),
-                                   (uint32_t)W.k, v);
-            const float2 t = table_lookup(P.table, R * P.sqrt_sigma);
-            if (GRAD && W.k == 0) {
-                // alpha(R0) u^(x_1) = (d/R0) C_{nu+1}(z0) term / C_nu(z0) = (d/R0) term / ratio(z0)
-                W.gfac0 = P.laplace ? ((float)D / R) * __expf(-t.x) : ((float)D / R) / t.y;
-            }
-            W.logw += t.x;
-            W.dsig = fmaf(-(R * R) * inv2d, t.y, W.dsig);
-#pragma unroll
-            for (int i = 0; i < D; ++i) W.x[i] = fmaf(R, v[i], W.x[i]);
-            ++W.k;
-            continue;
-        }
-        // ---- the walk ended: contribution, per-walk record, refill
-        float term = 0.f;
-        float e[kMaxExp];
-#pragma unroll
-        for (int k = 0; k < kMaxExp; ++k) e[k] = 0.f;
-        if (outcome == 1) term = terminal_value<D>(P, geom, balls, W.x, kind, idx, W.logw, e);
-        const bool has_grad = GRAD && outcome == 1 && W.k > 0;
-        float v0[D];
-#pragma unroll
-        for (int i = 0; i < D; ++i) v0[i] = 0.f;
-        if constexpr (GRAD) {
-            if (has_grad)
-                direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + (long long)W.j), 0u, v0);
-        }
-        const float gt = has_grad ? W.gfac0 * term : 0.f;
-        add_walk<D, GRAD>(P, W.q, outcome, W.k, term, W.dsig, gt, v0, e);
-        if (P.w_term != nullptr) P.w_term[W.j] = outcome == 3 ? (double)CUDART_NAN : (double)term;
-        if (P.w_jumps != nullptr) P.w_jumps[W.j] = W.k;
-        if (P.w_dsigma != nullptr) P.w_dsigma[W.j] = (double)(term * W.dsig);
-        if (P.w_grad != nullptr) {
-#pragma unroll
-            for (int i = 0; i < D; ++i) P.w_grad[(long long)W.j * D + i] = (double)(gt * v0[i]);
-        }
-        const unsigned nj = grab_walk(S);
-        W.active = nj < end;
-        if (W.active) start_walk<D, GRAD>(P, W, nj);
+        const float R = distance_mixed<D>(P, geom, balls, nblk, W.x2, P.slack, kind, idx) - P.shrink;
+        step_walker<D, GRAD>(L, P, S, balls, geom, W, R, kind, idx, end);
     }
 }
 
