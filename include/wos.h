@@ -65,6 +65,25 @@ typedef enum {
 
 #define WOS_FLAG_LAPLACE_FACTOR 1 /* use the paper's printed gradient factor d/R0 */
 
+/*
+ * Control variate for the first-sphere gradient (gradient calls only: wos_grad, the planner,
+ * gradient batches). The paper's estimator averages y_w = G t_w v_w over the N walks of a
+ * query, with t_w the walk's value estimate, v_w its first direction and G = alpha(R0)/C(R0)
+ * (R0 = distance at the query, so G is one number per query). Because E[v_w] = 0, subtracting
+ * the sample mean tbar of the t_w changes nothing in expectation but removes the part of the
+ * noise that the level of u contributes:
+ *
+ *     grad^ = G / (N - 1) * sum_w (t_w - tbar) v_w     (unbiased for N >= 2: it is G times the
+ *                                                       sample covariance of t and v)
+ *     grad_se = N/(N-1) * sqrt(var_w(G (t_w - tbar) v_w) / N)
+ *
+ * Walks capped at max_steps (t_w = 0) take part with their first direction. This is a
+ * variance reduction in the spirit of the paper's closing discussion (Sec. IX), not an
+ * estimator the paper prints. Cost: 3d more FP64 sums per query and up to 3d more atomic
+ * adds per walk. With N = 1 the plain estimate is returned. Value-only calls ignore the flag.
+ */
+#define WOS_FLAG_GRAD_CONTROL_VARIATE 2
+
 #define WOS_MAX_D 12    /* dimensions 2..12 are supported */
 #define WOS_MAX_EXP 8   /* at most 8 exponential boundary-data terms */
 

@@ -68,6 +68,7 @@ class _Options(ctypes.Structure):
         ("max_steps", ctypes.c_int64),
         ("grad", ctypes.c_int32),
         ("laplace_factor", ctypes.c_int32),
+        ("control_variate", ctypes.c_int32),
     ]
 
 
@@ -82,6 +83,7 @@ class _WalkOut(ctypes.Structure):
         ("grad", ctypes.c_double * MAXD),
         ("dsigma", ctypes.c_double),
         ("dw", ctypes.c_double * MAXEXP),
+        ("gv0", ctypes.c_double * MAXD),
     ]
 
 
@@ -181,12 +183,13 @@ class Domain:
         self.s = s
 
 
-def _opts(seed, max_steps, grad, laplace_factor):
+def _opts(seed, max_steps, grad, laplace_factor, control_variate=False):
     o = _Options()
     o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     o.max_steps = int(max_steps)
     o.grad = int(bool(grad))
     o.laplace_factor = int(bool(laplace_factor))
+    o.control_variate = int(bool(control_variate))
     return o
 
 
@@ -243,14 +246,16 @@ def walk(dom, x0, walk_index, eps, sigma, seed, max_steps=10000, grad=False, lap
         "term": o.term, "jumps": o.jumps, "capped": o.capped, "outside": o.outside,
         "comp_kind": o.comp_kind, "comp_index": o.comp_index,
         "grad": np.array(o.grad[:D.d]), "dsigma": o.dsigma, "dw": np.array(o.dw[:D.n_exp]),
+        "gv0": np.array(o.gv0[:D.d]),
     }
 
 
 def solve(dom, X, n_walks, eps, sigma, seed, walk_offset=0, max_steps=10000, grad=False,
-          laplace_factor=False, threads=None, per_walk=False):
+          laplace_factor=False, threads=None, per_walk=False, control_variate=False):
     """Per-query estimates. Returns a dict of numpy arrays (u, u_se, grad, grad_se,
     du_dsigma, du_dw, walk_steps, capped, outside; with per_walk also walk_term,
-    walk_jumps, walk_grad, walk_dsigma)."""
+    walk_jumps, walk_grad, walk_dsigma). control_variate (with grad): grad and grad_se are
+    the control-variate estimate G/(N-1) sum_w (t_w - tbar) v_w and its standard error."""
     D = dom if isinstance(dom, Domain) else Domain(dom)
     d, K = D.d, D.n_exp
     X = np.ascontiguousarray(np.asarray(X, float).reshape(-1, d))
@@ -267,7 +272,7 @@ def solve(dom, X, n_walks, eps, sigma, seed, walk_offset=0, max_steps=10000, gra
     if per_walk:
         pw = {"walk_term": np.zeros((Q, N)), "walk_jumps": np.zeros((Q, N), np.int64),
               "walk_grad": np.zeros((Q, N, d)), "walk_dsigma": np.zeros((Q, N))}
-    opt = _opts(seed, max_steps, grad, laplace_factor)
+    opt = _opts(seed, max_steps, grad, laplace_factor, control_variate)
     rc = lib().or_solve(
         ctypes.byref(D.s), _ptr(X), Q, N, int(walk_offset), float(eps), float(sigma), ctypes.byref(opt),
         int(threads), _ptr(out["u"]), _ptr(out["u_se"]), _ptr(out["grad"]), _ptr(out["grad_se"]),
@@ -284,7 +289,7 @@ def solve(dom, X, n_walks, eps, sigma, seed, walk_offset=0, max_steps=10000, gra
 
 
 def plan_path(dom, x0, n_steps, n_walks, eps, sigma, s_ub, seed, max_steps=10000, threads=None,
-              laplace_factor=False):
+              laplace_factor=False, control_variate=False):
     """Screened-harmonic path; returns (path[n_points, d], flags[n_steps], grads[n_steps, d])."""
     D = dom if isinstance(dom, Domain) else Domain(dom)
     d = D.d
@@ -294,7 +299,7 @@ def plan_path(dom, x0, n_steps, n_walks, eps, sigma, s_ub, seed, max_steps=10000
     path = np.zeros((n_steps + 1, d))
     flags = np.zeros(n_steps, np.int32)
     grads = np.zeros((n_steps, d))
-    opt = _opts(seed, max_steps, True, laplace_factor)
+    opt = _opts(seed, max_steps, True, laplace_factor, control_variate)
     n = lib().or_plan_path(ctypes.byref(D.s), _ptr(x0), int(n_steps), int(n_walks), float(eps),
                            float(sigma), float(s_ub), ctypes.byref(opt), int(threads), _ptr(path),
                            _ptr(flags, ctypes.c_int32), _ptr(grads))

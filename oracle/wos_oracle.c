@@ -16,6 +16,12 @@
  *       The paper prints the Laplace factor n/R; for sigma > 0 the unbiased factor is
  *       alpha = (d/R0) C_{nu+1}(z0) (it reduces to d/R0 at sigma = 0). The literal factor is
  *       available through or_options.laplace_factor.
+ *   Control variate for the gradient (optional; a variance reduction in the spirit of Sec. IX,
+ *       not an estimator the paper prints): with t_w the value estimate of walk w, v_w its first
+ *       direction and G = alpha(R0)/C(R0), grad^ = G/(N-1) sum_w (t_w - tbar) v_w, tbar the
+ *       sample mean of the t_w. E[v] = 0 makes it unbiased for every N >= 2 (G times the sample
+ *       covariance of t and v). Computed here by its definition, in two passes over stored
+ *       per-walk values.
  *   Closest boundary point xbar (Fig. 2): g is read at the projection of x_k on the nearest
  *       boundary component.
  *   Planner (Sec. III screened-harmonic paths; Sec. VII adaptive step):
@@ -76,6 +82,7 @@ typedef struct {
     int64_t max_steps;
     int32_t grad;           /* 1: gradient walks (the first sphere is always taken) */
     int32_t laplace_factor; /* 1: the paper's printed factor d/R0 instead of alpha(R0) */
+    int32_t control_variate; /* 1 (with grad): the control-variate gradient of or_solve */
 } or_options;
 
 typedef struct {
@@ -88,6 +95,7 @@ typedef struct {
     double grad[OR_MAXD];
     double dsigma;
     double dw[OR_MAXEXP];
+    double gv0[OR_MAXD]; /* G v0 = alpha(R0)/C(R0) times the first direction, if k > 0; else 0 */
 } or_walk_out;
 
 /* ------------------------------------------------------------------------- */
@@ -335,12 +343,16 @@ void or_walk(const or_domain *D, const double *x0, uint64_t walk, double eps, do
     out->comp_kind = kind;
     out->comp_index = index;
     out->dsigma = out->term * dsig;
-    if (k > 0 && !out->capped) {
-        /* u^(x_1) = term / C(R0);  alpha(R0) = (d/R0) C_{nu+1}(z0) */
-        double u1 = out->term * exp(-logC0);
+    if (k > 0) {
+        /* u^(x_1) = term / C(R0);  alpha(R0) = (d/R0) C_{nu+1}(z0);  G = alpha(R0) / C(R0) */
         double factor = opt->laplace_factor ? (double)d / R0
                                             : ((double)d / R0) / or_series_S(nu + 1.0, z0);
-        for (int j = 0; j < d; ++j) out->grad[j] = factor * u1 * v0[j];
+        double G = factor * exp(-logC0);
+        for (int j = 0; j < d; ++j) out->gv0[j] = G * v0[j];
+        if (!out->capped) {
+            double u1 = out->term * exp(-logC0);
+            for (int j = 0; j < d; ++j) out->grad[j] = factor * u1 * v0[j];
+        }
     }
 }
 
@@ -361,6 +373,8 @@ typedef struct {
     int64_t *walk_jumps;
     double *walk_grad;
     double *walk_dsigma;
+    double *cv_t;   /* control variate: Q x N walk values and Q x N x d values of G v0 */
+    double *cv_gv0;
     int64_t next; /* work cursor */
     pthread_mutex_t lock;
 } solve_job;
@@ -385,6 +399,10 @@ static void run_unit(solve_job *J, int64_t unit)
         if (J->walk_dsigma) J->walk_dsigma[flat] = o.dsigma;
         if (J->walk_grad)
             for (int j = 0; j < d; ++j) J->walk_grad[flat * d + j] = o.grad[j];
+        if (J->cv_t) {
+            J->cv_t[flat] = o.term;
+            for (int j = 0; j < d; ++j) J->cv_gv0[flat * d + j] = o.gv0[j];
+        }
         /* fields: [sum u, sum u^2, sum dsigma, grad[d], grad^2[d], dw[K]] */
         P[0] += o.term;
         P[1] += o.term * o.term;
@@ -455,11 +473,18 @@ int or_solve(const or_domain *D, const double *X, int64_t Q, int64_t N, int64_t 
     J.walk_grad = walk_grad;
     J.walk_dsigma = walk_dsigma;
     int64_t units = Q * J.nchunks;
+    const int cv = opt->grad && opt->control_variate && N >= 2;
     J.partial = (double *)malloc(sizeof(double) * (size_t)(units * J.nfields + 1));
     J.ipartial = (int64_t *)malloc(sizeof(int64_t) * (size_t)(units * 3 + 1));
-    if (!J.partial || !J.ipartial) {
+    if (cv) {
+        J.cv_t = (double *)malloc(sizeof(double) * (size_t)(Q * N + 1));
+        J.cv_gv0 = (double *)malloc(sizeof(double) * (size_t)(Q * N * d + 1));
+    }
+    if (!J.partial || !J.ipartial || (cv && (!J.cv_t || !J.cv_gv0))) {
         free(J.partial);
         free(J.ipartial);
+        free(J.cv_t);
+        free(J.cv_gv0);
         return -1;
     }
     pthread_mutex_init(&J.lock, NULL);
@@ -491,6 +516,28 @@ int or_solve(const or_domain *D, const double *X, int64_t Q, int64_t N, int64_t 
             if (grad) grad[q * d + j] = S[3 + j] * inv;
             if (grad_se) grad_se[q * d + j] = I[2] ? NAN : se_of(S[3 + j], S[3 + d + j], N);
         }
+        if (cv) {
+            /* first pass: tbar; second pass: y_w = G (t_w - tbar) v_w, its sum and spread */
+            const double *t = J.cv_t + q * N;
+            const double *gv = J.cv_gv0 + q * N * d;
+            double tbar = 0.0;
+            for (int64_t w = 0; w < N; ++w) tbar += t[w];
+            tbar /= (double)N;
+            for (int j = 0; j < d; ++j) {
+                double sy = 0.0;
+                for (int64_t w = 0; w < N; ++w) sy += (t[w] - tbar) * gv[w * d + j];
+                const double ybar = sy / (double)N;
+                double ss = 0.0;
+                for (int64_t w = 0; w < N; ++w) {
+                    const double e = (t[w] - tbar) * gv[w * d + j] - ybar;
+                    ss += e * e;
+                }
+                const double var = ss / (double)(N - 1);
+                if (grad) grad[q * d + j] = I[2] ? NAN : sy / (double)(N - 1);
+                if (grad_se)
+                    grad_se[q * d + j] = I[2] ? NAN : ((double)N / (double)(N - 1)) * sqrt(var / (double)N);
+            }
+        }
         for (int k = 0; k < K; ++k)
             if (du_dw) du_dw[q * K + k] = S[3 + 2 * d + k] * inv;
         if (walk_steps) walk_steps[q] = I[0];
@@ -499,6 +546,8 @@ int or_solve(const or_domain *D, const double *X, int64_t Q, int64_t N, int64_t 
     }
     free(J.partial);
     free(J.ipartial);
+    free(J.cv_t);
+    free(J.cv_gv0);
     return 0;
 }
 

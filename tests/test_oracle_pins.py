@@ -352,3 +352,63 @@ def test_planner_annulus_descends_radially(oracle_mod):
             radial = -path[i] / r[i]
             assert (path[i + 1] - path[i]) @ radial / s > math.cos(math.radians(25))
             assert r[i + 1] < r[i]
+
+
+# --------------------------------------------------------------------------- control variate
+# grad^ = G/(N-1) sum_w (t_w - tbar) v_w: G times the sample covariance of the walk values and
+# the first directions; E[v] = 0 makes it unbiased for every N >= 2.
+def test_control_variate_vanishes_for_constant_data(oracle_mod):
+    # sigma = 0 and g = 1 on the whole boundary: every walk returns exactly 1 (C = 1), so the
+    # deviations t_w - tbar are rounding-sized and so are the estimate and its standard error,
+    # while the plain first-sphere estimate carries the full sampling noise of v.
+    d = 3
+    dom = synth.ball_domain(d, 1.0)
+    X = np.array([[0.3, -0.2, 0.1], [0.0, 0.6, 0.0]])
+    cv = oracle_mod.solve(dom, X, 2000, 1e-4, 0.0, 5, grad=True, control_variate=True, per_walk=True)
+    plain = oracle_mod.solve(dom, X, 2000, 1e-4, 0.0, 5, grad=True)
+    assert np.all(cv["walk_term"] == 1.0)
+    G = d / (1.0 - np.linalg.norm(X, axis=1, keepdims=True))  # alpha(R0) / C(R0) = d / R0 at sigma = 0
+    assert np.all(np.abs(cv["grad"]) <= 1e-12 * G)
+    assert np.all(cv["grad_se"] <= 1e-12 * G)
+    assert np.all(np.abs(plain["grad"]).max(axis=1) > 1e-3)
+    # the per-query value outputs do not depend on the option
+    assert np.array_equal(cv["u"], plain["u"]) and np.array_equal(cv["u_se"], plain["u_se"])
+
+
+def _two_walk_replicas(oracle_mod, scale=1.0):
+    # 20000 independent two-walk estimates at one point of the disc, sigma = 4: the mean of
+    # the control-variate estimates must be the exact gradient (off-centre ball closed form)
+    d, R, sigma = 2, 1.0, 4.0
+    dom = synth.ball_domain(d, R)
+    x = np.array([0.3, 0.4])
+    Q = 20000
+    res = oracle_mod.solve(dom, np.tile(x, (Q, 1)), 2, 1e-6, sigma, 17, grad=True, control_variate=True)
+    g = scale * res["grad"]
+    mean, se = g.mean(axis=0), g.std(axis=0, ddof=1) / math.sqrt(Q)
+    _, exact = ball_solution(d, R, sigma, x)
+    return np.abs(mean - exact) < 4.0 * se, se, exact
+
+
+def test_control_variate_unbiased_with_two_walks(oracle_mod):
+    ok, se, exact = _two_walk_replicas(oracle_mod)
+    assert np.all(ok)
+    assert np.all(se < 0.05 * np.linalg.norm(exact))  # the check has the power to see a bias
+
+
+def test_planted_control_variate_normalisation_is_rejected(oracle_mod):
+    # dividing by N instead of N - 1 (a plausible slip) halves the two-walk estimate
+    ok, _, _ = _two_walk_replicas(oracle_mod, scale=0.5)
+    assert not np.any(ok)
+
+
+def test_control_variate_exp_data_exact_and_lower_variance(oracle_mod):
+    w = synth.c1(n_queries=16)
+    dom = w["domain"]
+    cv = oracle_mod.solve(dom, w["X"], 20000, 1e-4, w["sigma"], w["seed"], grad=True, control_variate=True)
+    plain = oracle_mod.solve(dom, w["X"], 20000, 1e-4, w["sigma"], w["seed"], grad=True)
+    a = dom["exp_a"][0]
+    g = np.exp(w["X"] @ a)
+    bias = 3e-4 * np.abs(g) * np.linalg.norm(a)  # O(eps) shell bias
+    gg = a[None, :] * g[:, None]
+    assert np.all(np.abs(cv["grad"] - gg) < 4.5 * cv["grad_se"] + 10 * bias[:, None])
+    assert np.mean(cv["grad_se"]) < 0.5 * np.mean(plain["grad_se"])
