@@ -9,6 +9,7 @@ LIB_PATH = os.path.join(HERE, "libwos.so")
 WOS_OK = 0
 WOS_FP64, WOS_FP32_PLAIN, WOS_MIXED = 0, 1, 2
 WOS_FLAG_LAPLACE_FACTOR = 1
+WOS_FLAG_GRAD_CONTROL_VARIATE = 2
 WOS_MAX_D = 12
 WOS_MAX_EXP = 8
 

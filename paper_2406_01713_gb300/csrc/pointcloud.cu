@@ -513,12 +513,13 @@ __global__ void __launch_bounds__(kThreads, 2) pointcloud_kernel(const __grid_co
                 }
             }
             const bool has_grad = GRAD && outcome == 1 && k > 0;
+            const bool cv_walk = GRAD && P.cv && k > 0 && outcome != 3;  // capped walks count too
             float v0[D];
 #pragma unroll
             for (int i = 0; i < D; ++i) v0[i] = 0.f;
-            if (has_grad) direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + j), 0u, v0);
+            if (has_grad || cv_walk) direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + j), 0u, v0);
             const float gt = has_grad ? gfac0 * term : 0.f;
-            add_walk<D, GRAD>(P, q, outcome, k, term, dsig, gt, v0, e);
+            add_walk<D, GRAD>(P, q, outcome, k, term, dsig, gt, v0, e, cv_walk ? gfac0 : 0.f);
             if (P.w_term != nullptr) P.w_term[j] = outcome == 3 ? (double)CUDART_NAN : (double)term;
             if (P.w_jumps != nullptr) P.w_jumps[j] = k;
             if (P.w_dsigma != nullptr) P.w_dsigma[j] = (double)(term * dsig);

@@ -347,8 +347,8 @@ __device__ __forceinline__ float terminal_value(const MixedProblem &P, const flo
 template <int D, bool GRAD>
 __device__ __forceinline__ void add_walk(const MixedProblem &P, long long q, int outcome, int k,
                                          float term, float dsig, float gt, const float (&v0)[D],
-                                         const float (&e)[kMaxExp]) {
-    const int nf = acc_fields(D, P.n_exp);
+                                         const float (&e)[kMaxExp], float gf) {
+    const int nf = acc_fields(D, P.n_exp, P.cv);
     double *acc = P.acc + q * nf;
     unsigned long long *cnt = P.counts + q * kCounters;
     atomicAdd(cnt + 0, 1ull);
@@ -375,6 +375,19 @@ __device__ __forceinline__ void add_walk(const MixedProblem &P, long long q, int
 #pragma unroll
         for (int kk = 0; kk < kMaxExp; ++kk)
             if (kk < P.n_exp) atomicAdd(acc + 3 + 2 * D + kk, (double)e[kk]);
+    }
+    if constexpr (GRAD) {
+        // control variate: gf = G = alpha(R0)/C(R0) for every walk that took its first sphere
+        if (gf != 0.f) {
+            double *cvp = acc + cv_field(D, P.n_exp);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const double gv = (double)gf * (double)v0[i];
+                atomicAdd(cvp + i, gv);
+                if (term != 0.f) atomicAdd(cvp + D + i, (double)term * gv * gv);
+                atomicAdd(cvp + 2 * D + i, gv * gv);
+            }
+        }
     }
 }
 
@@ -455,14 +468,16 @@ __device__ __forceinline__ void step_walker(const MixedLaunch &L, const MixedPro
     for (int k = 0; k < kMaxExp; ++k) e[k] = 0.f;
     if (outcome == 1) term = terminal_value<D>(P, geom, balls, W.x2, kind, idx, W.logw, e);
     const bool has_grad = GRAD && outcome == 1 && W.k > 0;
+    const bool cv_walk = GRAD && P.cv && W.k > 0 && outcome != 3;  // capped walks count too
     float v0[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) v0[i] = 0.f;
     if constexpr (GRAD) {
-        if (has_grad) direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + (long long)W.j), 0u, v0);
+        if (has_grad || cv_walk)
+            direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + (long long)W.j), 0u, v0);
     }
     const float gt = has_grad ? W.gfac0 * term : 0.f;
-    add_walk<D, GRAD>(P, W.q, outcome, W.k, term, W.dsig, gt, v0, e);
+    add_walk<D, GRAD>(P, W.q, outcome, W.k, term, W.dsig, gt, v0, e, cv_walk ? W.gfac0 : 0.f);
     if (P.w_term != nullptr) P.w_term[W.j] = outcome == 3 ? (double)CUDART_NAN : (double)term;
     if (P.w_jumps != nullptr) P.w_jumps[W.j] = W.k;
     if (P.w_dsigma != nullptr) P.w_dsigma[W.j] = (double)(term * W.dsig);

@@ -245,6 +245,7 @@ wos_status ensure_table(wos_domain_t dom, double sigma, WeightTable *out) {
 // =====================================================================================
 struct FinalizeRec {
     int d, K, acc_f32;
+    int cv;  // gradient control variate sums present
     int64_t Q, N, q_begin;
     const void *acc;
     const unsigned long long *counts;
@@ -282,7 +283,7 @@ __global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
             R = a.recs + lo;
         }
         const int64_t q = t - R->q_begin;
-        const int d = R->d, K = R->K, nf = acc_fields(d, K);
+        const int d = R->d, K = R->K, nf = acc_fields(d, K, R->cv);
         auto S = [&](int f) -> double {
             return R->acc_f32 ? (double)((const float *)R->acc)[q * nf + f]
                               : ((const double *)R->acc)[q * nf + f];
@@ -297,9 +298,13 @@ __global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
         if (R->u) R->u[q] = out ? nan : S(0) * inv;
         if (R->u_se) R->u_se[q] = out ? nan : se_mean(S(0), S(1), n);
         if (R->du_dsigma) R->du_dsigma[q] = out ? nan : S(2) * inv;
+        const bool cv = R->cv && n >= 2.0;
+        const int cf = cv_field(d, K);
         for (int i = 0; i < d; ++i) {
-            if (R->grad) R->grad[q * d + i] = out ? nan : S(3 + i) * inv;
-            if (R->grad_se) R->grad_se[q * d + i] = out ? nan : se_mean(S(3 + i), S(3 + d + i), n);
+            double g = S(3 + i) * inv, se = se_mean(S(3 + i), S(3 + d + i), n);
+            if (cv) cv_estimate(S(3 + i), S(3 + d + i), S(cf + i), S(cf + d + i), S(cf + 2 * d + i), S(0), n, g, se);
+            if (R->grad) R->grad[q * d + i] = out ? nan : g;
+            if (R->grad_se) R->grad_se[q * d + i] = out ? nan : se;
         }
         for (int k = 0; k < K; ++k)
             if (R->du_dw) R->du_dw[q * K + k] = out ? nan : S(3 + 2 * d + k) * inv;
@@ -328,15 +333,17 @@ wos_status launch_finalize(const FinalizeArgs &a, cudaStream_t s) {
 // =====================================================================================
 struct Opts {
     int precision, laplace;
+    int cv;  // gradient control variate (gradient calls only)
     uint64_t seed;
     int64_t walk_offset, max_steps;
 };
 
 Opts read_opts(const wos_options *o) {
-    Opts r{WOS_MIXED, 0, 0ull, 0, 10000};
+    Opts r{WOS_MIXED, 0, 0, 0ull, 0, 10000};
     if (o != nullptr) {
         r.precision = o->precision;
         r.laplace = (o->flags & WOS_FLAG_LAPLACE_FACTOR) ? 1 : 0;
+        r.cv = (o->flags & WOS_FLAG_GRAD_CONTROL_VARIATE) ? 1 : 0;
         r.seed = o->seed;
         r.walk_offset = o->walk_offset;
         r.max_steps = o->max_steps > 0 ? o->max_steps : 10000;
@@ -388,7 +395,7 @@ wos_status ensure_mixed_smem(size_t bytes) {
 }
 
 MixedProblem make_mixed_problem(wos_domain_t dom, const double *x, int64_t Q, int64_t N,
-                                double eps, double sigma, int grad_mode, int laplace,
+                                double eps, double sigma, int grad_mode, int laplace, int cv,
                                 int64_t walk_base, const WeightTable &tab, double *acc,
                                 unsigned long long *counts, const PerWalk &pw) {
     MixedProblem P{};
@@ -400,6 +407,7 @@ MixedProblem make_mixed_problem(wos_domain_t dom, const double *x, int64_t Q, in
     P.has_goal = dom->has_goal;
     P.grad_mode = grad_mode;
     P.laplace = laplace;
+    P.cv = grad_mode && cv;
     P.eps = (float)eps;
     P.sqrt_sigma = (float)std::sqrt(sigma);
     P.shrink = (float)dom->shrink32;
@@ -430,7 +438,8 @@ size_t mixed_smem_bytes(const wos_domain_s &D) {
 wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int64_t Q, int64_t N,
                           double eps, double sigma, int grad_mode, const Scratch &sc,
                           const PerWalk &pw, const int *skip, cudaStream_t s) {
-    const int nf = acc_fields(dom->d, dom->n_exp);
+    const int cv = grad_mode && o.cv;
+    const int nf = acc_fields(dom->d, dom->n_exp, cv);
     if (o.precision == WOS_FP64) {
         SimpleParams<double> p{};
         p.dom = dom->v64;
@@ -445,6 +454,7 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
         p.shrink = 0.0;
         p.grad_mode = grad_mode;
         p.laplace = o.laplace;
+        p.cv = cv;
         p.acc = (double *)sc.acc;
         p.counts = sc.counts;
         p.nf = nf;
@@ -470,6 +480,7 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
         p.shrink = (float)dom->shrink32;
         p.grad_mode = grad_mode;
         p.laplace = o.laplace;
+        p.cv = cv;
         p.acc = (float *)sc.acc;
         p.counts = sc.counts;
         p.nf = nf;
@@ -489,7 +500,7 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
             return fail(WOS_ERR_UNSUPPORTED, "mixed-precision point clouds need d <= %d", kPointCloudMaxD);
         if (dom->n_balls > 0)
             return fail(WOS_ERR_UNSUPPORTED, "a domain with both balls and points runs in FP64 or plain FP32");
-        MixedProblem P = make_mixed_problem(dom, x, Q, N, eps, sigma, grad_mode, o.laplace, o.walk_offset, tab,
+        MixedProblem P = make_mixed_problem(dom, x, Q, N, eps, sigma, grad_mode, o.laplace, cv, o.walk_offset, tab,
                                             (double *)sc.acc, sc.counts, pw);
         unsigned long long *shrinks = sc.cursor + 1;
         int *status = reinterpret_cast<int *>(sc.cursor + 2);
@@ -535,7 +546,7 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
     L.seed = o.seed;
     L.max_steps = o.max_steps;
     L.skip = skip;
-    L.single = make_mixed_problem(dom, x, Q, N, eps, sigma, grad_mode, o.laplace, o.walk_offset,
+    L.single = make_mixed_problem(dom, x, Q, N, eps, sigma, grad_mode, o.laplace, cv, o.walk_offset,
                                   tab, (double *)sc.acc, sc.counts, pw);
     WOS_CUDA(launch_walk_mixed(L, grad_mode, grid, threads, smem, s));
     return WOS_OK;
@@ -566,7 +577,8 @@ wos_status run_estimator(wos_domain_t dom, const wos_options *opt, const double 
         return fail(WOS_ERR_INVALID_ARG, "unknown precision %d", o.precision);
     if (stats != nullptr) WOS_CUDA(cudaMemsetAsync(stats, 0, sizeof(wos_stats), s));
     if (Q == 0) return WOS_OK;
-    const int nf = acc_fields(dom->d, dom->n_exp);
+    const int cv = grad_mode && o.cv;
+    const int nf = acc_fields(dom->d, dom->n_exp, cv);
     const size_t bytes = scratch_bytes(o.precision, Q, nf);
     void *base = nullptr;
     WOS_CUDA(cudaMallocAsync(&base, bytes, s));
@@ -587,6 +599,7 @@ wos_status run_estimator(wos_domain_t dom, const wos_options *opt, const double 
         r.d = dom->d;
         r.K = dom->n_exp;
         r.acc_f32 = o.precision == WOS_FP32_PLAIN;
+        r.cv = cv;
         r.Q = Q;
         r.N = N;
         r.q_begin = 0;
@@ -846,6 +859,7 @@ struct PlanArgs {
     void *acc;
     int acc_bytes;
     int acc_f32;
+    int cv;  // control-variate gradient (sums after the du/dw fields)
     unsigned long long *counts;
     unsigned long long *cursor;
     double *grad_row;
@@ -895,10 +909,19 @@ __device__ void plan_post_d(const PlanArgs &a) {
             *a.done = 1;
         } else {
             const double inv = 1.0 / (double)a.N;
+            auto S = [&](int f) -> double {
+                return a.acc_f32 ? (double)((const float *)a.acc)[f] : ((const double *)a.acc)[f];
+            };
+            const int cf = cv_field(D, a.dom.n_exp);
             double g[D];
             double gg = 0.0;
             for (int j = 0; j < D; ++j) {
-                g[j] = (a.acc_f32 ? (double)((const float *)a.acc)[3 + j] : ((const double *)a.acc)[3 + j]) * inv;
+                g[j] = S(3 + j) * inv;
+                if (a.cv && a.N >= 2) {
+                    double se;
+                    cv_estimate(S(3 + j), S(3 + D + j), S(cf + j), S(cf + D + j), S(cf + 2 * D + j), S(0),
+                                (double)a.N, g[j], se);
+                }
                 gg += g[j] * g[j];
             }
             if (a.grad_row)
@@ -934,7 +957,7 @@ wos_status enqueue_plan_step(wos_domain_t dom, const Opts &o, double *x, int64_t
                              double sigma, double s_ub, int64_t step_idx, int *done, int *skip,
                              int32_t *flag, const Scratch &sc, double *grad_row, double *path_row,
                              cudaStream_t s) {
-    const int nf = acc_fields(dom->d, dom->n_exp);
+    const int nf = acc_fields(dom->d, dom->n_exp, o.cv);
     PlanArgs a{};
     a.dom = dom->v64;
     a.x = x;
@@ -946,6 +969,7 @@ wos_status enqueue_plan_step(wos_domain_t dom, const Opts &o, double *x, int64_t
     a.flag = flag;
     a.acc = sc.acc;
     a.acc_f32 = o.precision == WOS_FP32_PLAIN;
+    a.cv = o.cv;
     a.acc_bytes = nf * (a.acc_f32 ? 4 : 8);
     a.counts = sc.counts;
     a.cursor = sc.cursor;
@@ -976,7 +1000,7 @@ wos_status wos_plan_step(wos_domain_t dom, const wos_options *opt, double *x, in
         WeightTable t;
         WOS_TRY(ensure_table(dom, sigma, &t));
     }
-    const int nf = acc_fields(dom->d, dom->n_exp);
+    const int nf = acc_fields(dom->d, dom->n_exp, o.cv);
     const size_t bytes = scratch_bytes(o.precision, 1, nf) + 256;
     void *base = nullptr;
     WOS_CUDA(cudaMallocAsync(&base, bytes, s));
@@ -1007,7 +1031,7 @@ wos_status wos_plan_path(wos_domain_t dom, const wos_options *opt, const double 
         WOS_TRY(ensure_table(dom, sigma, &t));
         WOS_TRY(ensure_mixed_smem(mixed_smem_bytes(*dom)));
     }
-    const int nf = acc_fields(d, dom->n_exp);
+    const int nf = acc_fields(d, dom->n_exp, o.cv);
     const size_t bytes = scratch_bytes(o.precision, 1, nf) + 256 + sizeof(double) * d;
     void *base = nullptr;
     WOS_CUDA(cudaMalloc(&base, bytes));
@@ -1276,7 +1300,7 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     std::vector<size_t> acc_off(n), cnt_off(n);
     for (int i = 0; i < n; ++i) {
         const wos_problem &p = b->probs[i];
-        const int nf = acc_fields(p.domain->d, p.domain->n_exp);
+        const int nf = acc_fields(p.domain->d, p.domain->n_exp, p.grad != nullptr && b->o.cv);
         acc_off[i] = acc_bytes;
         acc_bytes += align256((size_t)p.n_queries * nf * sizeof(double));
     }
@@ -1341,11 +1365,13 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         double *acc = (double *)(zero + acc_off[i]);
         unsigned long long *cnt = (unsigned long long *)(zero + cnt_off[i]);
         mp[i] = make_mixed_problem(p.domain, p.x, p.n_queries, p.n_walks, p.eps, p.sigma,
-                                   p.grad != nullptr, b->o.laplace, walk_base, tab, acc, cnt, PerWalk{});
+                                   p.grad != nullptr, b->o.laplace, b->o.cv, walk_base, tab, acc, cnt,
+                                   PerWalk{});
         FinalizeRec &r = fr[i];
         r.d = p.domain->d;
         r.K = p.domain->n_exp;
         r.acc_f32 = 0;
+        r.cv = mp[i].cv;
         r.Q = p.n_queries;
         r.N = p.n_walks;
         r.q_begin = q_begin;
@@ -1653,7 +1679,7 @@ extern "C" wos_status wos_debug_pointcloud_radius(wos_domain_t dom, const double
     if (cudaMemsetAsync(base, 0, bytes, s) != cudaSuccess) st = fail(WOS_ERR_CUDA, "memset");
     if (st == WOS_OK) {
         // one distance evaluation per query: a walk capped at zero jumps
-        MixedProblem P = make_mixed_problem(dom, x, Q, 1, 1e-30, 0.0, 0, 0, 0, tab, (double *)sc.acc, sc.counts,
+        MixedProblem P = make_mixed_problem(dom, x, Q, 1, 1e-30, 0.0, 0, 0, 0, 0, tab, (double *)sc.acc, sc.counts,
                                             PerWalk{});
         const cudaError_t e = launch_pointcloud(dom->pcd, P, dom->pc_delta, sc.cursor,
                                                 reinterpret_cast<int *>(sc.cursor + 2), sc.cursor + 1, 0, 0, 0, s,

@@ -21,6 +21,7 @@ struct SimpleParams {
     int64_t max_steps;
     T eps, sqrt_sigma, shrink;
     int grad_mode, laplace;
+    int cv;                      // gradient control variate: accumulate the 3d extra sums
     T *acc;                      // Q x nf sums
     unsigned long long *counts;  // Q x kCounters
     int nf;
@@ -38,6 +39,7 @@ cudaError_t launch_walk_simple_f32(const SimpleParams<float> &p, cudaStream_t s)
 struct MixedProblem {
     int d, n_balls, n_exp, has_box, has_outer, has_goal;
     int grad_mode, laplace;
+    int cv;        // gradient control variate: accumulate the 3d extra sums
     float eps, sqrt_sigma;
     float shrink;  // FP32 error bound subtracted from every radius
     float slack;   // FP32 rounding bound of the ball screening test

@@ -26,10 +26,11 @@ def _stream():
     return _VP(torch.cuda.current_stream().cuda_stream)
 
 
-def _opts(precision="mixed", seed=0, walk_offset=0, max_steps=10000, laplace=False):
+def _opts(precision="mixed", seed=0, walk_offset=0, max_steps=10000, laplace=False, control_variate=False):
     o = _lib.Options()
     o.precision = _lib.PRECISION[precision] if isinstance(precision, str) else int(precision)
-    o.flags = _lib.WOS_FLAG_LAPLACE_FACTOR if laplace else 0
+    o.flags = ((_lib.WOS_FLAG_LAPLACE_FACTOR if laplace else 0) |
+               (_lib.WOS_FLAG_GRAD_CONTROL_VARIATE if control_variate else 0))
     o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     o.walk_offset = int(walk_offset)
     o.max_steps = int(max_steps)
@@ -134,7 +135,9 @@ class Domain:
         return out
 
     def grad(self, x, n_walks, eps, sigma, precision="mixed", seed=0, walk_offset=0,
-             max_steps=10000, laplace=False, with_stats=False):
+             max_steps=10000, laplace=False, with_stats=False, control_variate=False):
+        """u, grad u (first-sphere estimator; control_variate=True subtracts the walks' mean
+        value, WOS_FLAG_GRAD_CONTROL_VARIATE), their SEs, du/dsigma and du/dw per query."""
         L = _lib.load()
         x = _dev_f64(x, self.d)
         Q, d = x.shape[0], self.d
@@ -143,7 +146,7 @@ class Domain:
                "grad_se": torch.empty(Q, d, **f), "du_dsigma": torch.empty(Q, **f),
                "du_dw": torch.empty(Q, self.n_exp, **f) if self.n_exp else None}
         st = torch.zeros(6, dtype=torch.int64, device=x.device) if with_stats else None
-        o = _opts(precision, seed, walk_offset, max_steps, laplace)
+        o = _opts(precision, seed, walk_offset, max_steps, laplace, control_variate)
         _lib.check(L.wos_grad(self.h, ctypes.byref(o), _ptr(x), Q, int(n_walks), float(eps), float(sigma),
                               _ptr(out["u"]), _ptr(out["u_se"]), _ptr(out["grad"]), _ptr(out["grad_se"]),
                               _ptr(out["du_dsigma"]), _ptr(out["du_dw"]), _ptr(st), _stream()),
@@ -169,20 +172,20 @@ class Domain:
 
     # ----------------------------------------------------------------- planner
     def plan_step(self, x, n_walks, eps, sigma, s_ub, step_idx, precision="mixed", seed=0,
-                  walk_offset=0, max_steps=10000):
+                  walk_offset=0, max_steps=10000, control_variate=False):
         """One step in place on the device tensor x (d doubles); returns (flag, grad)."""
         L = _lib.load()
         assert x.dtype == torch.float64 and x.is_cuda and x.numel() == self.d and x.is_contiguous()
         flag = torch.zeros(1, dtype=torch.int32, device=x.device)
         g = torch.empty(self.d, dtype=torch.float64, device=x.device)
-        o = _opts(precision, seed, walk_offset, max_steps)
+        o = _opts(precision, seed, walk_offset, max_steps, control_variate=control_variate)
         _lib.check(L.wos_plan_step(self.h, ctypes.byref(o), _ptr(x), int(n_walks), float(eps), float(sigma),
                                    float(s_ub), int(step_idx), _ptr(flag), _ptr(g), _stream()),
                    "wos_plan_step")
         return flag, g
 
     def plan_path(self, x0, n_steps, n_walks, eps, sigma, s_ub, precision="mixed", seed=0,
-                  walk_offset=0, max_steps=10000):
+                  walk_offset=0, max_steps=10000, control_variate=False):
         """n_steps planner steps replayed as one CUDA graph: (path, flags, grads) on the device."""
         L = _lib.load()
         x0 = _dev_f64(x0).reshape(-1)
@@ -191,7 +194,7 @@ class Domain:
         path = torch.empty(n_steps + 1, d, **f)
         flags = torch.zeros(n_steps, dtype=torch.int32, device=x0.device)
         grads = torch.zeros(n_steps, d, **f)
-        o = _opts(precision, seed, walk_offset, max_steps)
+        o = _opts(precision, seed, walk_offset, max_steps, control_variate=control_variate)
         _lib.check(L.wos_plan_path(self.h, ctypes.byref(o), _ptr(x0), int(n_steps), int(n_walks), float(eps),
                                    float(sigma), float(s_ub), _ptr(path), _ptr(flags), _ptr(grads),
                                    _stream()), "wos_plan_path")
@@ -230,10 +233,11 @@ class WoSFunction(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx, x, sigma, w, domain, n_walks, eps, seed=0, precision="mixed"):
+    def forward(ctx, x, sigma, w, domain, n_walks, eps, seed=0, precision="mixed", control_variate=False):
         if w is not None:
             domain.set_exp_w(w.detach())
-        r = domain.grad(x.detach(), n_walks, eps, float(sigma), precision=precision, seed=seed)
+        r = domain.grad(x.detach(), n_walks, eps, float(sigma), precision=precision, seed=seed,
+                        control_variate=control_variate)
         ctx.save_for_backward(r["grad"], r["du_dsigma"],
                               r["du_dw"] if r["du_dw"] is not None else torch.zeros(0, device=x.device))
         ctx.has_w = w is not None
@@ -245,7 +249,7 @@ class WoSFunction(torch.autograd.Function):
         grad, dsig, dw = ctx.saved_tensors
         gx, gs, gw = backward(gout, grad, dsig, dw if dw.numel() else None)
         return (gx, gs if ctx.sigma_is_tensor else None, gw if ctx.has_w else None,
-                None, None, None, None, None)
+                None, None, None, None, None, None)
 
 
 class Batch:
@@ -257,7 +261,7 @@ class Batch:
     self.out[i] = {u, u_se, grad, grad_se, walk_steps} are views of them.
     """
 
-    def __init__(self, problems, seed=0, max_steps=10000, config=None):
+    def __init__(self, problems, seed=0, max_steps=10000, config=None, control_variate=False):
         L = _lib.load()
         self.problems = problems
         f = dict(dtype=torch.float64, device="cuda")
@@ -302,7 +306,7 @@ class Batch:
             a.walk_steps = o["walk_steps"].data_ptr()
         self.n_x, self.n_q, self.n_g = ox, oq, og
         self._arr = arr
-        opts = _opts("mixed", seed, 0, max_steps)
+        opts = _opts("mixed", seed, 0, max_steps, control_variate=control_variate)
         cfg = None
         if config is not None:
             cfg = _lib.BatchConfig(int(config["threads"]), int(config["ctas_per_sm"]), int(config["item_work"]))
