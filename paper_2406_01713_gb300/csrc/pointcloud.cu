@@ -517,7 +517,8 @@ __global__ void __launch_bounds__(kThreads, 2) pointcloud_kernel(const __grid_co
             float v0[D];
 #pragma unroll
             for (int i = 0; i < D; ++i) v0[i] = 0.f;
-            if (has_grad || cv_walk) direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + j), 0u, v0);
+            if (has_grad && term != 0.f)
+                direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + j), 0u, v0);
             const float gt = has_grad ? gfac0 * term : 0.f;
             add_walk<D, GRAD>(P, q, outcome, k, term, dsig, gt, v0, e, cv_walk ? gfac0 : 0.f);
             if (P.w_term != nullptr) P.w_term[j] = outcome == 3 ? (double)CUDART_NAN : (double)term;

@@ -378,15 +378,15 @@ __device__ __forceinline__ void add_walk(const MixedProblem &P, long long q, int
     }
     if constexpr (GRAD) {
         // control variate: gf = G = alpha(R0)/C(R0) for every walk that took its first sphere
+        // (the same value for all walks of the query). sum v0 and sum v0^2 do not depend on the
+        // walk's outcome; cv_prepass_kernel forms them from the Philox stream.
         if (gf != 0.f) {
             double *cvp = acc + cv_field(D, P.n_exp);
+            if (term != 0.f) {
 #pragma unroll
-            for (int i = 0; i < D; ++i) {
-                const double gv = (double)gf * (double)v0[i];
-                atomicAdd(cvp + i, gv);
-                if (term != 0.f) atomicAdd(cvp + D + i, (double)term * gv * gv);
-                atomicAdd(cvp + 2 * D + i, gv * gv);
+                for (int i = 0; i < D; ++i) atomicAdd(cvp + D + i, (double)term * (double)v0[i] * (double)v0[i]);
             }
+            cvp[3 * D] = (double)gf;
         }
     }
 }
@@ -473,7 +473,7 @@ __device__ __forceinline__ void step_walker(const MixedLaunch &L, const MixedPro
 #pragma unroll
     for (int i = 0; i < D; ++i) v0[i] = 0.f;
     if constexpr (GRAD) {
-        if (has_grad || cv_walk)
+        if (has_grad && term != 0.f)
             direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + (long long)W.j), 0u, v0);
     }
     const float gt = has_grad ? W.gfac0 * term : 0.f;

@@ -17,7 +17,8 @@ template <typename T, int D>
 struct WalkResult {
     T term, dsig;
     T grad[D];
-    T gv0[D];  // G v0 = alpha(R0)/C(R0) times the first direction (control variate), 0 if k = 0
+    T v0[D];   // first direction if the walk took its first sphere (control variate), else 0
+    T G;       // alpha(R0)/C(R0) if the walk took its first sphere, else 0
     T dw[kMaxExp];
     int64_t jumps;
     int capped, outside;
@@ -56,7 +57,8 @@ __device__ void run_walk(const SimpleParams<T> &p, const double *xq, uint64_t wa
 #pragma unroll
     for (int i = 0; i < kMaxExp; ++i) res.dw[i] = T(0);
 #pragma unroll
-    for (int j = 0; j < D; ++j) res.grad[j] = res.gv0[j] = T(0);
+    for (int j = 0; j < D; ++j) res.grad[j] = res.v0[j] = T(0);
+    res.G = T(0);
     for (;;) {
         const T R = distance<T, D>(dm, x, kind, idx) - p.shrink;
         if (k == 0 && !(R > T(0))) {
@@ -102,9 +104,9 @@ __device__ void run_walk(const SimpleParams<T> &p, const double *xq, uint64_t wa
     if (k > 0) {
         const T factor = p.laplace ? T(D) / R0 : (T(D) / R0) / S1_0;
         if (p.cv) {
-            const T G = factor * exp(-logC0);
+            res.G = factor * exp(-logC0);
 #pragma unroll
-            for (int j = 0; j < D; ++j) res.gv0[j] = G * v0[j];
+            for (int j = 0; j < D; ++j) res.v0[j] = v0[j];
         }
         if (!res.capped) {
             const T u1 = res.term * exp(-logC0);
@@ -179,20 +181,22 @@ __global__ void __launch_bounds__(128) walk_simple_kernel(const SimpleParams<T> 
             if (leader) atomicAdd(acc + 3 + 2 * D + k, s);
         }
         if (p.cv) {
+            // [sum v0, sum t v0^2, sum v0^2, G]; G is the same for every walk of the query
             T *cvp = acc + cv_field(D, K);
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                const T gv = ok ? r.gv0[i] : T(0);
+                const T v = ok ? r.v0[i] : T(0);
                 const T tt = ok ? r.term : T(0);
-                const T s1 = segment_sum(gv, lane, seg_end);
-                const T s2 = segment_sum(tt * gv * gv, lane, seg_end);
-                const T s3 = segment_sum(gv * gv, lane, seg_end);
+                const T s1 = segment_sum(v, lane, seg_end);
+                const T s2 = segment_sum(tt * v * v, lane, seg_end);
+                const T s3 = segment_sum(v * v, lane, seg_end);
                 if (leader) {
                     atomicAdd(cvp + i, s1);
                     atomicAdd(cvp + D + i, s2);
                     atomicAdd(cvp + 2 * D + i, s3);
                 }
             }
+            if (ok && r.G != T(0)) cvp[3 * D] = r.G;
         }
         const unsigned long long c[4] = {active ? 1ull : 0ull,
                                          active ? (unsigned long long)(r.jumps + 1) : 0ull,

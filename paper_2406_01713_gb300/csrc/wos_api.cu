@@ -302,7 +302,9 @@ __global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
         const int cf = cv_field(d, K);
         for (int i = 0; i < d; ++i) {
             double g = S(3 + i) * inv, se = se_mean(S(3 + i), S(3 + d + i), n);
-            if (cv) cv_estimate(S(3 + i), S(3 + d + i), S(cf + i), S(cf + d + i), S(cf + 2 * d + i), S(0), n, g, se);
+            if (cv)
+                cv_estimate(S(3 + i), S(3 + d + i), S(cf + i), S(cf + d + i), S(cf + 2 * d + i), S(cf + 3 * d), S(0),
+                            n, g, se);
             if (R->grad) R->grad[q * d + i] = out ? nan : g;
             if (R->grad_se) R->grad_se[q * d + i] = out ? nan : se;
         }
@@ -317,6 +319,88 @@ __global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
             if (c[3]) atomicAdd(st + 3, c[3]);
         }
     }
+}
+
+// Control variate, outcome-independent sums: the first direction of every walk of a query,
+// regenerated from its Philox counter with the walkers' own sampler and arguments (so the
+// values are the walkers' v0 bit for bit), summed per component and squared into the query's
+// [sum v0] and [sum v0^2] fields. One warp per query; plain stores (a warp owns its query).
+struct CvPrepassArgs {
+    const MixedProblem *problems;  // device array, or nullptr: problem 0 is `single`
+    const FinalizeRec *recs;       // device array (q_begin per problem), or nullptr
+    int n;
+    int64_t total_q;
+    MixedProblem single;
+    uint64_t seed;
+};
+
+template <int D>
+__device__ void cv_prepass_query(const MixedProblem &P, int64_t q, uint64_t seed, int lane) {
+    double s1[D], s2[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) s1[i] = s2[i] = 0.0;
+    for (int64_t w = lane; w < P.N; w += 32) {
+        float v[D];
+        direction_f32<D, true>(seed, (uint64_t)(P.walk_base + q * P.N + w), 0u, v);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            s1[i] += (double)v[i];
+            s2[i] += (double)v[i] * (double)v[i];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            s1[i] += __shfl_xor_sync(0xffffffffu, s1[i], off);
+            s2[i] += __shfl_xor_sync(0xffffffffu, s2[i], off);
+        }
+    }
+    if (lane == 0) {
+        double *cvp = P.acc + q * acc_fields(D, P.n_exp, 1) + cv_field(D, P.n_exp);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            cvp[i] = s1[i];
+            cvp[2 * D + i] = s2[i];
+        }
+    }
+}
+
+__global__ void cv_prepass_kernel(const __grid_constant__ CvPrepassArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.total_q; t += nwarps) {
+        const MixedProblem *P = &a.single;
+        int64_t q = t;
+        if (a.recs != nullptr) {
+            int lo = 0, hi = a.n - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.recs[mid].q_begin <= t) lo = mid;
+                else hi = mid - 1;
+            }
+            P = a.problems + lo;
+            q = t - a.recs[lo].q_begin;
+        }
+        if (!P->cv) continue;
+        switch (P->d) {
+#define WOS_CASE(DD) \
+    case DD: cv_prepass_query<DD>(*P, q, a.seed, lane); break;
+            WOS_CASE(2) WOS_CASE(3) WOS_CASE(4) WOS_CASE(5) WOS_CASE(6) WOS_CASE(7)
+            WOS_CASE(8) WOS_CASE(9) WOS_CASE(10) WOS_CASE(11) WOS_CASE(12)
+#undef WOS_CASE
+            default: break;
+        }
+    }
+}
+
+wos_status launch_cv_prepass(const CvPrepassArgs &a, cudaStream_t s) {
+    if (a.total_q <= 0) return WOS_OK;
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>((a.total_q * 32 + threads - 1) / threads, 8192);
+    cv_prepass_kernel<<<(unsigned)blocks, threads, 0, s>>>(a);
+    WOS_CUDA(cudaGetLastError());
+    return WOS_OK;
 }
 
 wos_status launch_finalize(const FinalizeArgs &a, cudaStream_t s) {
@@ -502,6 +586,13 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
             return fail(WOS_ERR_UNSUPPORTED, "a domain with both balls and points runs in FP64 or plain FP32");
         MixedProblem P = make_mixed_problem(dom, x, Q, N, eps, sigma, grad_mode, o.laplace, cv, o.walk_offset, tab,
                                             (double *)sc.acc, sc.counts, pw);
+        if (cv) {
+            CvPrepassArgs pa{};
+            pa.total_q = Q;
+            pa.single = P;
+            pa.seed = o.seed;
+            WOS_TRY(launch_cv_prepass(pa, s));
+        }
         unsigned long long *shrinks = sc.cursor + 1;
         int *status = reinterpret_cast<int *>(sc.cursor + 2);
         WOS_CUDA(launch_pointcloud(dom->pcd, P, dom->pc_delta, sc.cursor, status, shrinks, o.seed, o.max_steps,
@@ -548,6 +639,13 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
     L.skip = skip;
     L.single = make_mixed_problem(dom, x, Q, N, eps, sigma, grad_mode, o.laplace, cv, o.walk_offset,
                                   tab, (double *)sc.acc, sc.counts, pw);
+    if (cv) {
+        CvPrepassArgs pa{};
+        pa.total_q = Q;
+        pa.single = L.single;
+        pa.seed = o.seed;
+        WOS_TRY(launch_cv_prepass(pa, s));
+    }
     WOS_CUDA(launch_walk_mixed(L, grad_mode, grid, threads, smem, s));
     return WOS_OK;
 }
@@ -919,8 +1017,8 @@ __device__ void plan_post_d(const PlanArgs &a) {
                 g[j] = S(3 + j) * inv;
                 if (a.cv && a.N >= 2) {
                     double se;
-                    cv_estimate(S(3 + j), S(3 + D + j), S(cf + j), S(cf + D + j), S(cf + 2 * D + j), S(0),
-                                (double)a.N, g[j], se);
+                    cv_estimate(S(3 + j), S(3 + D + j), S(cf + j), S(cf + D + j), S(cf + 2 * D + j), S(cf + 3 * D),
+                                S(0), (double)a.N, g[j], se);
                 }
                 gg += g[j] * g[j];
             }
@@ -1416,6 +1514,15 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         return fail(WOS_ERR_CUDA, "batch capture failed to start");
     }
     if (cudaMemsetAsync(zero, 0, zero_bytes, cap) != cudaSuccess) st = fail(WOS_ERR_CUDA, "memset capture");
+    if (st == WOS_OK && b->o.cv && b->grad_any) {
+        CvPrepassArgs pa{};
+        pa.problems = (const MixedProblem *)base;
+        pa.recs = fa.recs;
+        pa.n = n;
+        pa.total_q = b->total_q;
+        pa.seed = b->o.seed;
+        st = launch_cv_prepass(pa, cap);
+    }
     if (st == WOS_OK && b->n_items > 0 &&
         launch_walk_mixed(L, b->grad_any, b->grid, cfg.threads, b->smem, cap) != cudaSuccess)
         st = fail(WOS_ERR_CUDA, "walk kernel capture failed");

@@ -170,24 +170,26 @@ struct DomainView {
 };
 
 // Per-query accumulator fields: [sum u, sum u^2, sum du/dsigma, sum grad (d), sum grad^2 (d),
-// sum du/dw (K)] and, with the gradient control variate, [sum G v0 (d), sum G^2 t v0^2 (d),
-// sum G^2 v0^2 (d)]; int64 counters [walks, walk_steps, capped, outside] live apart.
+// sum du/dw (K)] and, with the gradient control variate, [sum v0 (d), sum t v0^2 (d),
+// sum v0^2 (d), G] (v0 the first direction, t the walk's value, G = alpha(R0)/C(R0), one number
+// per query because R0 is the distance at the query); int64 counters [walks, walk_steps,
+// capped, outside] live apart.
 __host__ __device__ __forceinline__ int acc_fields(int d, int K, int cv = 0) {
-    return 3 + 2 * d + K + (cv ? 3 * d : 0);
+    return 3 + 2 * d + K + (cv ? 3 * d + 1 : 0);
 }
 __host__ __device__ __forceinline__ int cv_field(int d, int K) { return 3 + 2 * d + K; }
 constexpr int kCounters = 4;
 
 // Control-variate gradient of one component from the one-pass sums of a query:
-//   A = sum G t v, A2 = sum (G t v)^2, B = sum G v, C1 = sum G^2 t v^2, C2 = sum G^2 v^2,
-//   St = sum t, n walks. With y_w = G (t_w - tbar) v_w:
-//   sum y = A - tbar B,  sum y^2 = A2 - 2 tbar C1 + tbar^2 C2,
+//   A = sum G t v, A2 = sum (G t v)^2, Sv = sum v, Stv2 = sum t v^2, Sv2 = sum v^2, St = sum t,
+//   n walks. With y_w = G (t_w - tbar) v_w:
+//   sum y = A - tbar G Sv,  sum y^2 = A2 - 2 tbar G^2 Stv2 + tbar^2 G^2 Sv2,
 //   grad = sum y / (n - 1),  se = n/(n-1) sqrt(var(y) / n).
-__host__ __device__ __forceinline__ void cv_estimate(double A, double A2, double B, double C1, double C2,
-                                                     double St, double n, double &g, double &se) {
+__host__ __device__ __forceinline__ void cv_estimate(double A, double A2, double Sv, double Stv2, double Sv2,
+                                                     double G, double St, double n, double &g, double &se) {
     const double tbar = St / n;
-    const double sy = A - tbar * B;
-    const double sy2 = A2 - 2.0 * tbar * C1 + tbar * tbar * C2;
+    const double sy = A - tbar * G * Sv;
+    const double sy2 = A2 + G * G * (tbar * tbar * Sv2 - 2.0 * tbar * Stv2);
     g = sy / (n - 1.0);
     const double var = (sy2 - sy * sy / n) / (n - 1.0);
     se = var > 0.0 ? (n / (n - 1.0)) * sqrt(var / n) : 0.0;
