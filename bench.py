@@ -334,29 +334,28 @@ def main():
     except Exception:
         pass
     sm_max = peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0
-    peak_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
-    achieved = flops / (ms_per_step / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": measured_traffic(),
-                "traffic_note": "ncu dram__bytes_read+write per launch (profiles/walk_mixed_batched_traffic.txt); "
-                                "algorithmic bytes are not the bound: balls, queries and sums are L2-resident",
-                "kernel": "walk_mixed_kernel<true> (persistent batched walker)",
-                "peak_note": "FP32 FMA pipe: %d SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % (
-                    props.multi_processor_count, sm_max),
-                "flops_per_launch": flops}
+    kernels = kernel_rooflines(W, doms, probs, replica_seed(w["seed"], rank), tuned, not args.no_cv, peaks,
+                               props.multi_processor_count, sm_max, flush)
+    roofline = dict(max(kernels.values(), key=lambda r: r["ms"]))
+    roofline["all_kernels"] = {k: {kk: v for kk, v in r.items() if kk in ("bound", "achieved", "peak", "unit",
+                                                                           "frac", "ms", "share", "kernel")}
+                               for k, r in kernels.items()}
+    n_sphere_dims = len({p["domain"]["d"] for d, p in zip(doms, probs) if d.info()["tensor_sphere_set"]})
+    launches_per_step = 1 + (0 if args.no_cv else 1) + n_sphere_dims + (1 if "cuda_core" in kernels else 0)
 
     line = {"metric": METRIC, "value": value, "unit": "walk-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload, "parallelism": "replicas" if world > 1 else "1 GPU",
                        "l2": "flushed between steps (512 MB write)", "launch": tuned,
-                       "walk_steps_per_step": total_steps, "queries_per_step": total_q},
+                       "walk_steps_per_step": total_steps, "queries_per_step": total_q,
+                       "algorithmic_flops_per_step": flops},
             "queries_per_s": total_q * args.steps * world / dev_s,
             "grad_evals_per_s": total_q * args.steps * world / dev_s,
             "rmse": {"u_rel": rmse_u, "grad_rel": rmse_g, "grad_rel_aggregate": rmse_gn,
                      "against": "exact solution exp(a.x) on the 128 exponential-data problems",
                      "grad_estimator": "first sphere" + ("" if args.no_cv else " with control variate")},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clocks,
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
             "wall_s": wall}
 
     log("e2e done")
@@ -377,6 +376,69 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def kernel_rooflines(W, doms, probs, seed, config, cv, peaks, sms, sm_max, flush):
+    """Roofline of each walker family, each timed alone with CUDA events (two launches after a
+    warm-up, L2 flushed before each) on the problems the batch gives it:
+      * CUDA-core persistent walker: FP32 ALU bound, algorithmic flops per walk-step
+        B(2d+3) + 4d, against 152 SMs x 128 lanes x 2 flops x the maximum SM clock;
+      * tensor-core sphere-set walker: bound by the tensor pipe, algorithmic flops per walk-step
+        B x 2(3d+2) (the BF16-split contraction |c|^2 - 2x.c over every sphere), against the
+        measured sustained dense BF16 peak (the launch runs for a second or more)."""
+    import torch
+
+    tens = [i for i, d in enumerate(doms) if d.info()["tensor_sphere_set"]]
+    groups = {"cuda_core": [i for i in range(len(doms)) if i not in set(tens)], "tensor": tens}
+    out = {}
+    for name, idx in groups.items():
+        if not idx:
+            continue
+        b = W.Batch([{"domain": doms[i], "x": probs[i]["X"], "n_walks": probs[i]["n_walks"], "eps": probs[i]["eps"],
+                      "sigma": probs[i]["sigma"], "grad": True} for i in idx], seed=seed, config=config,
+                    control_variate=cv)
+        b.run()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.run()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        steps = [int(o["walk_steps"].sum()) for o in b.out]
+        b.close()
+        ms = min(times)
+        if name == "cuda_core":
+            fl = sum(s_ * alg_flops_per_step(probs[i]["domain"]["d"], probs[i]["domain"]["ball_r"].size)
+                     for s_, i in zip(steps, idx))
+            peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
+            r = {"bound": "alu", "peak": peak, "peak_note": "FP32 FMA pipe: %d SMs x 128 lanes x 2 flop x %.0f MHz "
+                 "(max SM clock)" % (sms, sm_max), "kernel": "walk_mixed_kernel<true> (CUDA-core persistent walker)",
+                 "traffic": measured_traffic(),
+                 "traffic_note": "ncu dram__bytes_read+write per launch (profiles/walk_mixed_batched_traffic.txt); "
+                                 "balls, queries and sums are L2-resident"}
+        else:
+            fl = 0
+            for s_, i in zip(steps, idx):
+                dd = probs[i]["domain"]
+                m = dd["ball_r"].size if "ball_r" in dd else dd["points"].shape[0]
+                fl += s_ * m * 2 * (3 * dd["d"] + 2)
+            peak = peaks.get("bf16_tflops_sustained") or 1700.0
+            r = {"bound": "tensor", "peak": peak, "peak_note": "measured sustained dense BF16 (cuBLAS), "
+                 "MEASURED_PEAKS.json", "kernel": "sphere_kernel<d, true> (tensor-core sphere-set walker, one "
+                 "launch per dimension)", "traffic": None,
+                 "traffic_note": "not captured for this kernel; its tiles and sums are L2-resident"}
+        achieved = fl / (ms / 1e3) / 1e12
+        r.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / r["peak"], "ms": ms,
+                  "flops_per_launch": fl, "problems": len(idx)})
+        out[name] = r
+    tot = sum(r["ms"] for r in out.values())
+    for r in out.values():
+        r["share"] = r["ms"] / tot
+    return out
 
 
 def exact_rmse(probs, outs):

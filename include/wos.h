@@ -84,6 +84,14 @@ typedef enum {
  */
 #define WOS_FLAG_GRAD_CONTROL_VARIATE 2
 
+/*
+ * Ball sets of at least 512 balls in d <= 10 run, in WOS_MIXED, on the tensor-core sphere-set
+ * walker (the same walker as point sets: |c|^2 - 2 x.c by tcgen05.mma, exact FP32 refinement of
+ * the best 32-ball chunk, a proven lower bound for the rest). This flag keeps them on the
+ * CUDA-core ball screen instead (for comparisons; both are exact up to their error bounds).
+ */
+#define WOS_FLAG_CUDA_CORE_BALLS 4
+
 #define WOS_MAX_D 12    /* dimensions 2..12 are supported */
 #define WOS_MAX_EXP 8   /* at most 8 exponential boundary-data terms */
 
@@ -151,6 +159,15 @@ wos_status wos_domain_destroy(wos_domain_t dom);
 /* Replaces the boundary-data weights exp_w (n_exp device doubles) on the stream, for the
  * autograd path where w is a learnable tensor. Errors: INVALID_ARG if n differs from n_exp. */
 wos_status wos_domain_set_exp_w(wos_domain_t dom, const double *w_device, int32_t n, void *stream);
+
+/*
+ * Which walker the domain's obstacles run on in WOS_MIXED: *tensor_sphere_set = 1 if they form a
+ * tensor-core sphere set (a point set, or at least 512 balls, in d <= 10), with *sphere_tiles
+ * 64-sphere tiles; 0 (and 0 tiles) for the CUDA-core walker. Host outputs; either may be NULL.
+ * No counterpart in the paper (introspection for schedulers and benchmarks).
+ * Errors: INVALID_ARG (NULL domain).
+ */
+wos_status wos_domain_info(wos_domain_t dom, int32_t *tensor_sphere_set, int32_t *sphere_tiles);
 
 /* ---- estimators (Sec. IV-A) --------------------------------------------------------- */
 
@@ -243,11 +260,15 @@ typedef struct {
 } wos_batch_config;
 
 /*
- * Builds a batch: uploads the problem table and the longest-first work queue, sizes the
- * persistent grid to a multiple of the SM count, and records [reset, persistent walk kernel,
- * finalize] as one CUDA graph. Problems may differ in d, obstacle count, walk budget, sigma and
- * eps. Precision is WOS_MIXED. The problems' domains and buffers must outlive the batch.
- * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
+ * Builds a batch: uploads the problem table and the longest-first work queues, sizes the
+ * persistent grids to a multiple of the SM count, and records one CUDA graph: [reset,
+ * control-variate prepass (with WOS_FLAG_GRAD_CONTROL_VARIATE), the CUDA-core persistent walker
+ * for the problems with small ball sets or d > 10, in parallel one tensor-core sphere-set walker
+ * launch per dimension for the problems with tensor-core sphere sets (>= 512 balls or a point
+ * set, d <= 10; WOS_FLAG_CUDA_CORE_BALLS keeps ball sets off it), finalize]. Problems may differ
+ * in d, obstacle count, walk budget, sigma and eps. Precision is WOS_MIXED. The problems'
+ * domains and buffers must outlive the batch. Errors: INVALID_ARG, UNSUPPORTED (a point set
+ * with d > 10, a domain with both balls and points), OOM, CUDA.
  */
 wos_status wos_batch_create(const wos_problem *probs, int32_t n_problems, const wos_options *opt,
                             const wos_batch_config *cfg, wos_batch_t *out);
@@ -325,8 +346,9 @@ wos_status wos_debug_philox(uint64_t seed, uint64_t walk0, int64_t n, uint32_t s
 /* Writes, for each point x[q] (Q x d device doubles), the distance bound the tensor-core
  * point-cloud walker uses there -- min over the FP32 refinement of its best 32-point candidate
  * chunk, the second-best chunk minus the BF16 error bound, and the other components -- to
- * radius[q] (device doubles). Sec. VII-A point-set distance; for checks that the bound never
- * exceeds the exact distance. Errors: UNSUPPORTED without a mixed-precision point set. */
+ * radius[q] (device doubles). Sec. VII-A point-set distance (and Sec. VI ball distance for a
+ * tensor-core ball set); for checks that the bound never exceeds the exact distance.
+ * Errors: UNSUPPORTED without a tensor-core sphere set. */
 wos_status wos_debug_pointcloud_radius(wos_domain_t dom, const double *x, int64_t Q, double *radius,
                                        void *stream);
 

@@ -10,6 +10,7 @@ WOS_OK = 0
 WOS_FP64, WOS_FP32_PLAIN, WOS_MIXED = 0, 1, 2
 WOS_FLAG_LAPLACE_FACTOR = 1
 WOS_FLAG_GRAD_CONTROL_VARIATE = 2
+WOS_FLAG_CUDA_CORE_BALLS = 4
 WOS_MAX_D = 12
 WOS_MAX_EXP = 8
 
@@ -72,6 +73,7 @@ SIGNATURES = {
     "wos_domain_create": (ctypes.c_int, [ctypes.POINTER(DomainDesc), ctypes.POINTER(_VP)]),
     "wos_domain_destroy": (ctypes.c_int, [_VP]),
     "wos_domain_set_exp_w": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, _VP]),
+    "wos_domain_info": (ctypes.c_int, [_VP, _VP, _VP]),
     "wos_solve": (ctypes.c_int, [_VP, ctypes.POINTER(Options), _VP, ctypes.c_int64, ctypes.c_int64,
                                  ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP]),
     "wos_grad": (ctypes.c_int, [_VP, ctypes.POINTER(Options), _VP, ctypes.c_int64, ctypes.c_int64,

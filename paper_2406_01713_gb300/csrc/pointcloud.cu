@@ -1,29 +1,35 @@
-// Point-cloud Walk-on-Spheres walker on the 5th-generation tensor cores (sm_103a).
+// Sphere-set Walk-on-Spheres walker on the 5th-generation tensor cores (sm_103a).
 //
-// Distance to an obstacle point set (Sec. VII-A, d(q) = min_i |q - p_i|) for 128 walkers at a
-// time: the contraction D_wi = |p_i|^2 - 2 x_w . p_i runs as tcgen05.mma (BF16 inputs, FP32
-// accumulation in tensor memory) over point tiles that TMA streams into shared memory; the
-// walker warps read their rows back with tcgen05.ld and keep, per walker, the best and the
-// second-best 32-point chunk. The best chunk is then recomputed exactly in FP32 and the other
-// points are bounded from below by the second-best chunk minus a proven error bound, so the
-// radius never exceeds the true distance (no sphere leaves the domain).
+// Distance to a set of obstacle spheres: points (Sec. VII-A, d(q) = min_i |q - p_i|) or balls
+// (Sec. VI, |q - c_i| - r_i), for 128 walkers at a time. The contraction
+// D_wi = |c_i|^2 - 2 x_w . c_i runs as tcgen05.mma (BF16 inputs, FP32 accumulation in tensor
+// memory) over centre tiles that TMA streams into shared memory; the walker warps read their
+// rows back with tcgen05.ld. Per 32-column chunk, min D gives a lower bound of the chunk's
+// distances, sqrt(min D + |x|^2 - delta) - r_hi (balls are sorted by radius, so r_hi, the
+// chunk's largest radius, is close to every radius in it); each walker keeps the best and the
+// second-best chunk. The best chunk is then recomputed exactly in FP32 and every other sphere
+// is bounded from below by the second-best chunk's bound, so the radius never exceeds the true
+// distance (no sphere leaves the domain).
 //
 // BF16 split: x = x_h + x_l and -2p = q_h + q_l (each a BF16), |p|^2 = n_h + n_l; the walker
 // row [x_h, x_h, x_l, 1, 1] times the point row [q_h, q_l, q_h, n_h, n_l] gives
 // |p|^2 - 2 x.p up to the dropped x_l q_l term and FP32 accumulation (3d + 2 <= 32 = K).
 //
 // CTA: warps 0-3 own one walker per thread (TMEM lanes 0..127); warp 4, lane 0, issues the
-// TMA loads and the MMAs. Every wait on an mbarrier is bounded by a clock budget; a timeout
-// sets the launch's status word and every thread leaves through the same teardown, which
-// waits for the issued MMAs and frees the tensor memory.
-#include <cuda.h>
+// bulk copies of the centre tiles and the MMAs. The launch is persistent over a queue of items
+// (problem, walk range) of problems with the same dimension: the walkers of a CTA draw walks
+// from their item, take the next item when it runs out (continuing seamlessly if it belongs to
+// the same problem), and switch problems once their last walks have ended. Every wait on an
+// mbarrier is bounded by a clock budget; a timeout sets the launch's status word and every
+// thread leaves through the same teardown, which waits for the issued MMAs and frees the
+// tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
-#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "walk_mixed.cuh"
@@ -32,16 +38,18 @@ namespace wos {
 namespace pc {
 
 constexpr int kRows = 128;       // walkers per CTA = MMA M = TMEM lanes
-constexpr int kTileN = 128;      // points per tile = MMA N
+constexpr int kTileN = 64;       // centres per tile = MMA N
 constexpr int kK = 32;           // padded contraction length (3d + 2 <= 32)
-constexpr int kStages = 6;       // point-tile ring in shared memory
+constexpr int kStages = 6;       // centre-tile ring in shared memory
 constexpr int kAhead = 4;        // tiles loaded ahead of the MMA issue point
+constexpr int kCtasPerSm = 4;    // 4 x 128 TMEM columns; registers <= 102 per thread
 constexpr int kChunk = 32;       // candidate chunk (columns)
 constexpr int kWalkerThreads = 128;
 constexpr int kThreads = kWalkerThreads + 32;
 constexpr uint32_t kTileBytes = kTileN * kK * 2;
 constexpr uint32_t kABytes = kRows * kK * 2;
 constexpr uint32_t kTmemCols = 2 * kTileN;
+constexpr uint32_t kTransposeBytes = 4 * 32 * 33 * 4;  // per walker warp: 32 walkers x 32 spheres (+1 pad)
 constexpr long long kWaitBudget = 4000000000ll;  // clock cycles (~2 s) before a wait gives up
 
 // Core-matrix layout (8 rows x 16 bytes), K-major, no swizzle: element (r, k) of a
@@ -53,21 +61,6 @@ constexpr uint32_t kSBO = (kK / 8) * 128;    // to the next group of 8 rows
 // both K-major (15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
                             ((uint32_t)(kRows >> 4) << 24);
-
-struct Launch {
-    CUtensorMap tmap;             // point tiles: 2D, 64 BF16 wide, 64 rows per tile
-    MixedProblem P;
-    const float *pts32;           // padded FP32 points, n_tiles * 128 x d
-    int n_tiles;
-    float delta;                  // bound of |D~ - D| (squared-distance units)
-    unsigned long long *cursor;   // global walk counter
-    int *status;                  // nonzero: a wait timed out
-    unsigned long long *shrinks;  // steps whose radius came from the bound
-    uint64_t seed;
-    int64_t max_steps;
-    int64_t total_walks;
-    double *radius_out;  // nullable: distance bound at each walk's start (diagnostics)
-};
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -88,12 +81,14 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *b) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
 }
+// try_wait with a suspend-time hint (ns): a waiting thread is parked until the phase completes
+// or the hint runs out, instead of spinning on the issue slots the MMA-issuing thread needs.
 __device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(su32(b)), "r"(parity)
+        : "r"(su32(b)), "r"(parity), "r"(20000u)
         : "memory");
     return ok != 0;
 }
@@ -108,6 +103,10 @@ struct Shared {
     uint32_t tmem_base;
     volatile int abort_flag;
     volatile int stop;
+    // work control: written by walker thread 0 between the two barriers of a step
+    int cur, has_pend, queue_empty, skip, switched;
+    unsigned long long j_next, j_end;  // walk range of the current item; j_next is the shared counter
+    SphereItem pend;
 };
 
 // Bounded wait: false if the budget ran out or another thread aborted.
@@ -132,14 +131,39 @@ __device__ __forceinline__ bool warp_wait_bar(Shared &S, uint64_t *b, uint32_t p
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-__device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap *map, int tile, uint64_t *bar) {
-    const int c0 = 0, c1 = tile * (kTileBytes / 128);
+// One centre tile (kTileBytes, already in the core-matrix layout) by a bulk copy; both
+// addresses are 16-byte aligned (tile offsets are multiples of 4 KB).
+__device__ __forceinline__ void bulk_load_tile(uint32_t dst, const void *src, uint64_t *bar) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-            "r"(dst),
-        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(su32(bar))
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"((uint64_t)src), "r"(kTileBytes), "r"(su32(bar))
         : "memory");
 }
+
+// Next item of the launch's queue; false when the queue is empty.
+__device__ __forceinline__ bool next_item(const SphereLaunch &L, SphereItem &it) {
+    const unsigned long long i = atomicAdd(L.item_cursor, 1ull);
+    if (i >= (unsigned long long)L.n_items) return false;
+    if (L.items != nullptr) {
+        it = L.items[i];
+    } else {
+        const int64_t total = L.single.P.Q * L.single.P.N;
+        it.problem = 0;
+        it.j0 = (int64_t)i * L.walks_per_item;
+        it.j1 = it.j0 + L.walks_per_item < total ? it.j0 + L.walks_per_item : total;
+    }
+    return true;
+}
+
+// Copies problem p into shared memory (threads tid, tid + nt, ...).
+__device__ __forceinline__ void load_problem(const SphereLaunch &L, int p, SphereProblem &SP, int tid, int nt) {
+    const SphereProblem *src = L.problems != nullptr ? L.problems + p : &L.single;
+    const int *s = reinterpret_cast<const int *>(src);
+    int *d = reinterpret_cast<int *>(&SP);
+    for (int i = tid; i < (int)(sizeof(SphereProblem) / 4); i += nt) d[i] = s[i];
+}
+
+__device__ __forceinline__ void walker_barrier() { asm volatile("barrier.cta.sync 2, 128;" ::: "memory"); }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
     asm volatile(
@@ -154,27 +178,24 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-// 128 accumulator columns of this thread's TMEM lane, loaded and waited for in one step.
-__device__ __forceinline__ void tmem_row128(uint32_t taddr, float (&v)[kTileN]) {
-    uint32_t r[kTileN];
+// The 64 accumulator columns of this thread's TMEM lane, loaded and waited for in one step.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+    uint32_t r[64];
 #define R8(i) "=r"(r[i]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), "=r"(r[i + 4]), "=r"(r[i + 5]), "=r"(r[i + 6]), "=r"(r[i + 7])
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x128.b32 "
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%"
         "28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,"
-        "%55,%56,%57,%58,%59,%60,%61,%62,%63,%64,%65,%66,%67,%68,%69,%70,%71,%72,%73,%74,%75,%76,%77,%78,%79,%80,%81,"
-        "%82,%83,%84,%85,%86,%87,%88,%89,%90,%91,%92,%93,%94,%95,%96,%97,%98,%99,%100,%101,%102,%103,%104,%105,%106,"
-        "%107,%108,%109,%110,%111,%112,%113,%114,%115,%116,%117,%118,%119,%120,%121,%122,%123,%124,%125,%126,%127}, "
-        "[%128];\n"
+        "%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n"
         "tcgen05.wait::ld.sync.aligned;\n"
-        : R8(0), R8(8), R8(16), R8(24), R8(32), R8(40), R8(48), R8(56), R8(64), R8(72), R8(80), R8(88), R8(96),
-          R8(104), R8(112), R8(120)
+        : R8(0), R8(8), R8(16), R8(24), R8(32), R8(40), R8(48), R8(56)
         : "r"(taddr)
         : "memory");
 #undef R8
 #pragma unroll
-    for (int i = 0; i < kTileN; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
 }
+static_assert(kTileN == 64, "the epilogue reads a 64-column tile with one tcgen05.ld");
 
 __device__ __forceinline__ float min32(const float *v) {
     float m[11];
@@ -211,18 +232,19 @@ __device__ __forceinline__ void write_row(unsigned char *A, int r, const float (
 }
 
 template <int D, bool GRAD>
-__global__ void __launch_bounds__(kThreads, 2) pointcloud_kernel(const __grid_constant__ Launch L) {
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __grid_constant__ SphereLaunch L) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ Shared S;
+    __shared__ SphereProblem SP;  // the problem the CTA's walkers are on
     __shared__ float geom_s[4 * kMaxD + kMaxExp + kMaxExp * kMaxD];
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char *A = base;
     unsigned char *Bst = base + kABytes;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const MixedProblem &P = L.P;
+    const MixedProblem &P = SP.P;
+    constexpr int kGeom = 4 * D + kMaxExp + kMaxExp * D;
 
-    for (int i = threadIdx.x; i < 4 * D + kMaxExp + kMaxExp * D; i += blockDim.x) geom_s[i] = P.geom[i];
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&S.full[s], 1);
@@ -236,8 +258,26 @@ __global__ void __launch_bounds__(kThreads, 2) pointcloud_kernel(const __grid_co
         mbar_init(&S.drain, 1);
         S.abort_flag = 0;
         S.stop = 0;
+        S.has_pend = 0;
+        S.queue_empty = 0;
+        S.skip = 0;
+        S.switched = 0;
+        SphereItem it;
+        if (next_item(L, it)) {
+            S.cur = it.problem;
+            S.j_next = (unsigned long long)it.j0;
+            S.j_end = (unsigned long long)it.j1;
+        } else {
+            S.cur = 0;
+            S.j_next = S.j_end = 0ull;
+            S.queue_empty = 1;
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    __syncthreads();
+    load_problem(L, S.cur, SP, threadIdx.x, blockDim.x);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kGeom; i += blockDim.x) geom_s[i] = SP.P.geom[i];
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&S.tmem_base)),
                      "r"(kTmemCols)
@@ -248,7 +288,6 @@ __global__ void __launch_bounds__(kThreads, 2) pointcloud_kernel(const __grid_co
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = S.tmem_base;
-    const int T = L.n_tiles;
 
     if (warp == 4) {
         // ------------------------------------------------------------------ producer
@@ -259,6 +298,9 @@ __global__ void __launch_bounds__(kThreads, 2) pointcloud_kernel(const __grid_co
             for (int step = 0; ok; ++step) {
                 if (!wait_bar(S, &S.a_ready, step & 1, L.status)) break;
                 if (S.stop) break;
+                // the problem of this step (the walkers change it only between steps)
+                const int T = SP.n_tiles;
+                const unsigned char *tiles = reinterpret_cast<const unsigned char *>(SP.tiles);
                 int t_load = 0;
                 auto issue_load = [&]() -> bool {
                     const int s = (int)(g_load % kStages);
@@ -266,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 2) pointcloud_kernel(const __grid_co
                         !wait_bar(S, &S.empty[s], (uint32_t)((g_load / kStages - 1) & 1), L.status))
                         return false;
                     mbar_expect_tx(&S.full[s], kTileBytes);
-                    tma_load_tile(su32(Bst + s * kTileBytes), &L.tmap, t_load, &S.full[s]);
+                    bulk_load_tile(su32(Bst + s * kTileBytes), tiles + (size_t)t_load * kTileBytes, &S.full[s]);
                     ++g_load;
                     ++t_load;
                     return true;
@@ -306,25 +348,26 @@ __global__ void __launch_bounds__(kThreads, 2) pointcloud_kernel(const __grid_co
         const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
         const float inv2d = 1.0f / (2.0f * (float)D);
         float x[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) x[i] = 0.f;
         float logw = 0.f, dsig = 0.f, gfac0 = 0.f;
         int k = 0;
         long long j = -1, q = 0;
         bool active = false;
         long long g_epi = 0;
-        const unsigned long long total = (unsigned long long)L.total_walks;
         for (int step = 0;; ++step) {
-            // refill idle lanes (warp-aggregated claim on the global walk counter)
+            // refill idle lanes from the CTA's item (warp-aggregated claim on its counter)
             {
                 const bool need = !active;
                 const unsigned m = __ballot_sync(0xffffffffu, need);
                 unsigned long long basej = 0;
                 if (m != 0) {
-                    if (lane == __ffs(m) - 1) basej = atomicAdd(L.cursor, (unsigned long long)__popc(m));
+                    if (lane == __ffs(m) - 1) basej = atomicAdd(&S.j_next, (unsigned long long)__popc(m));
                     basej = __shfl_sync(0xffffffffu, basej, __ffs(m) - 1);
                 }
                 if (need) {
                     const unsigned long long jj = basej + __popc(m & ((1u << lane) - 1u));
-                    if (jj < total) {
+                    if (jj < S.j_end) {
                         active = true;
                         j = (long long)jj;
                         q = j / P.N;
@@ -335,50 +378,115 @@ __global__ void __launch_bounds__(kThreads, 2) pointcloud_kernel(const __grid_co
                     }
                 }
             }
-            // the only exit: a barrier reduction every walker thread reaches (an abort makes
-            // every thread vote 'no more work' at the next one)
-            const unsigned want = (active && !S.abort_flag) ? 1u : 0u;
+            // every walker thread reaches this reduction each step; then thread 0 manages the
+            // item queue and the others learn its decision after the second barrier
             int any;
             asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.cta.red.or.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}\n"
                          : "=r"(any)
-                         : "r"(want)
+                         : "r"(active ? 1u : 0u)
                          : "memory");
-            if (!any) {
-                if (lane == 0) {
+            if (threadIdx.x == 0) {
+                S.skip = 0;
+                if (S.abort_flag) {
                     S.stop = 1;
-                    mbar_arrive(&S.a_ready);
+                } else {
+                    if (S.j_next >= S.j_end && !S.has_pend && !S.queue_empty) {
+                        SphereItem it;
+                        if (!next_item(L, it)) {
+                            S.queue_empty = 1;
+                        } else if (it.problem == S.cur) {  // same problem: walks continue without a pause
+                            S.j_next = (unsigned long long)it.j0;
+                            S.j_end = (unsigned long long)it.j1;
+                        } else {
+                            S.pend = it;
+                            S.has_pend = 1;
+                        }
+                    }
+                    if (!any) {
+                        if (S.has_pend) {  // every walk of the old problem has ended: switch
+                            S.cur = S.pend.problem;
+                            S.j_next = (unsigned long long)S.pend.j0;
+                            S.j_end = (unsigned long long)S.pend.j1;
+                            S.has_pend = 0;
+                            S.switched = 1;
+                            S.skip = 1;
+                        } else if (S.queue_empty) {
+                            S.stop = 1;
+                        } else {
+                            S.skip = 1;  // the item was extended: refill first
+                        }
+                    }
                 }
+            }
+            walker_barrier();
+            if (S.stop) {
+                if (lane == 0) mbar_arrive(&S.a_ready);
                 break;
             }
+            if (S.skip) {
+                if (S.switched) {
+                    load_problem(L, S.cur, SP, threadIdx.x, kWalkerThreads);
+                    walker_barrier();
+                    for (int i = threadIdx.x; i < kGeom; i += kWalkerThreads) geom_s[i] = SP.P.geom[i];
+                    walker_barrier();
+                    if (threadIdx.x == 0) S.switched = 0;
+                }
+                continue;
+            }
+            const int T = SP.n_tiles;
             write_row<D>(A, r, x, active);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&S.a_ready);
 
-            // ---- epilogue: best and second-best 32-point chunk of D~ = |p|^2 - 2 x.p
-            float m1 = CUDART_INF_F, m2 = CUDART_INF_F;
-            int c1 = 0;
+            // ---- epilogue: best and second-best 32-column chunk by the lower bound
+            //      sqrt(min D~ + |x|^2 - delta) - r_hi, D~ = |c|^2 - 2 x.c
+            float xx = 0.f;
+#pragma unroll
+            for (int i = 0; i < D; ++i) xx = fmaf(x[i], x[i], xx);
+            const float xxd = xx - SP.delta;
+            float m1 = CUDART_INF_F, m2 = CUDART_INF_F, m3 = CUDART_INF_F;
+            int c1 = 0, c2 = 0;
             bool ok = true;
             for (int t = 0; t < T; ++t, ++g_epi) {
                 const int b = (int)(g_epi & 1);
+                // the chunk radius bounds of this tile, fetched while the MMA result is awaited
+                float rhi[kTileN / kChunk];
+#pragma unroll
+                for (int c = 0; c < kTileN / kChunk; ++c) rhi[c] = __ldg(SP.chunk_rhi + t * (kTileN / kChunk) + c);
                 if (!warp_wait_bar(S, &S.tfull[b], (uint32_t)((g_epi >> 1) & 1), L.status)) {
                     ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                float v[kTileN];
-                tmem_row128(trow + b * kTileN, v);
+                float cmin[kTileN / kChunk];
+                {
+                    float v[kTileN];
+                    tmem_ld64(trow + b * kTileN, v);
+#pragma unroll
+                    for (int c = 0; c < kTileN / kChunk; ++c) cmin[c] = min32(v + kChunk * c);
+                }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&S.tempty[b]);
 #pragma unroll
                 for (int c = 0; c < kTileN / kChunk; ++c) {
-                    const float cm = min32(v + kChunk * c);
                     const int id = t * (kTileN / kChunk) + c;
-                    m2 = fminf(m2, fmaxf(m1, cm));
-                    if (cm < m1) {
-                        m1 = cm;
-                        c1 = id;
+                    const float cs = cmin[c] + xxd;
+                    const float cm = (cs > 0.f ? sqrtf(cs) : 0.f) - rhi[c];
+                    if (cm < m2) {
+                        m3 = m2;
+                        if (cm < m1) {
+                            m2 = m1;
+                            c2 = c1;
+                            m1 = cm;
+                            c1 = id;
+                        } else {
+                            m2 = cm;
+                            c2 = id;
+                        }
+                    } else {
+                        m3 = fminf(m3, cm);
                     }
                 }
             }
@@ -386,33 +494,54 @@ __global__ void __launch_bounds__(kThreads, 2) pointcloud_kernel(const __grid_co
                 active = false;  // abandon the walk; the next barrier reduction ends the loop
                 continue;
             }
-            if (!active) continue;
 
-            // ---- exact FP32 distances of the best chunk; the rest is bounded by m2 - delta
-            float xx = 0.f;
-#pragma unroll
-            for (int i = 0; i < D; ++i) xx = fmaf(x[i], x[i], xx);
-            float dbest = CUDART_INF_F;
+            // ---- exact FP32 distances |x - c| - r of the best chunk (and of the second-best
+            //      one when its bound is below that); every other sphere is bounded below by the
+            //      next chunk's bound. The warp refines one walker at a time, one sphere per lane:
+            //      a chunk is stored coordinate-major, so every load is one coalesced row.
+            float Rp = CUDART_INF_F;
             int pbest = c1 * kChunk;
-            const float *pc = L.pts32 + (long long)c1 * kChunk * D;
+            float *tr = reinterpret_cast<float *>(Bst + kStages * kTileBytes) + warp * 32 * 33;
+            auto refine = [&](int cc, bool want) {
+                const unsigned todo = __ballot_sync(0xffffffffu, want);
+                if (todo == 0u) return;
+                // lane i: sphere i of walker w's chunk, for every walker w that asks
 #pragma unroll 4
-            for (int i = 0; i < kChunk; ++i) {
-                float s2 = 0.f;
+                for (int w = 0; w < 32; ++w) {
+                    if (!((todo >> w) & 1u)) continue;
+                    const int cw = __shfl_sync(0xffffffffu, cc, w);
+                    const float *ch = SP.soa + (long long)cw * (D + 1) * kChunk;
+                    float s2 = 0.f;
 #pragma unroll
-                for (int jj = 0; jj < D; ++jj) {
-                    const float t0 = x[jj] - __ldg(pc + i * D + jj);
-                    s2 = fmaf(t0, t0, s2);
+                    for (int jj = 0; jj < D; ++jj) {
+                        const float t0 = __shfl_sync(0xffffffffu, x[jj], w) - __ldg(ch + jj * kChunk + lane);
+                        s2 = fmaf(t0, t0, s2);
+                    }
+                    tr[w * 33 + lane] = sqrtf(s2) - __ldg(ch + D * kChunk + lane);
                 }
-                if (s2 < dbest) {
-                    dbest = s2;
-                    pbest = c1 * kChunk + i;
+                __syncwarp();
+                // walker w scans its own row (lowest index on ties)
+                if (want) {
+                    const float *row = tr + lane * 33;
+#pragma unroll 8
+                    for (int i = 0; i < kChunk; ++i) {
+                        const float di = row[i];
+                        if (di < Rp) {
+                            Rp = di;
+                            pbest = cc * kChunk + i;
+                        }
+                    }
                 }
-            }
-            float Rp = sqrtf(dbest);
-            const float lb2 = m2 + xx - L.delta;
-            const float lb = lb2 > 0.f ? sqrtf(lb2) : 0.f;
-            if (lb < Rp) {
-                Rp = lb;
+                __syncwarp();
+            };
+            refine(c1, active);
+            float mrest = m2;
+            const bool second = active && m2 < Rp;
+            refine(c2, second);
+            if (second) mrest = m3;
+            if (!active) continue;
+            if (mrest < Rp) {
+                Rp = mrest;
                 atomicAdd(L.shrinks, 1ull);
             }
             // other components: goal, outer ball, box faces (FP32 direct form)
@@ -479,8 +608,16 @@ __global__ void __launch_bounds__(kThreads, 2) pointcloud_kernel(const __grid_co
 #pragma unroll
                 for (int i = 0; i < D; ++i) xb[i] = x[i];
                 if (kind == kPoint) {
+                    // closest point of the sphere (c, r): c + r (x - c)/|x - c|; c itself for a point
+                    const float *c = SP.soa + (long long)(idx / kChunk) * (D + 1) * kChunk + (idx % kChunk);
+                    const float rad = __ldg(c + D * kChunk);
+                    float s = 0.f;
 #pragma unroll
-                    for (int i = 0; i < D; ++i) xb[i] = __ldg(L.pts32 + (long long)idx * D + i);
+                    for (int i = 0; i < D; ++i) s = fmaf(x[i] - __ldg(c + i * kChunk), x[i] - __ldg(c + i * kChunk), s);
+                    const float len = sqrtf(s);
+                    const float f = len > 0.f ? rad / len : 0.f;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) xb[i] = fmaf(f, x[i] - __ldg(c + i * kChunk), __ldg(c + i * kChunk));
                 } else if (kind == kFace) {
 #pragma unroll
                     for (int i = 0; i < D; ++i)
@@ -538,7 +675,11 @@ __global__ void __launch_bounds__(kThreads, 2) pointcloud_kernel(const __grid_co
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-size_t smem_bytes() { return 1024 + kABytes + (size_t)kStages * kTileBytes; }
+// At least 48 KB: shared memory then also caps the residency at kCtasPerSm CTAs per SM, so the
+// CTAs of an SM never ask for more than the 512 TMEM columns it has.
+size_t smem_bytes() {
+    return std::max<size_t>(48 * 1024, 1024 + kABytes + (size_t)kStages * kTileBytes + kTransposeBytes);
+}
 
 }  // namespace pc
 
@@ -555,21 +696,37 @@ static inline float bf16_value(uint16_t b) {
     return __bfloat162float(h);
 }
 
-cudaError_t pointcloud_prepare(const double *pts, int64_t M, int d, PointCloudDev *out) {
+cudaError_t pointcloud_prepare(const double *pts, const double *radii, int64_t M, int d, PointCloudDev *out) {
     if (d < 2 || 3 * d + 2 > pc::kK) return cudaErrorInvalidValue;
     const int64_t n_tiles = (M + pc::kTileN - 1) / pc::kTileN;
     const int64_t Mp = n_tiles * pc::kTileN;
     std::vector<uint16_t> hb((size_t)n_tiles * pc::kTileBytes / 2, 0);
-    std::vector<float> h32((size_t)Mp * d, 0.f);
+    std::vector<float> hsoa((size_t)(Mp / pc::kChunk) * (d + 1) * pc::kChunk, 0.f);
+    std::vector<float> hrhi((size_t)(Mp / pc::kChunk), 0.f);
+    // balls in increasing radius (ties by index), points in input order
+    std::vector<int64_t> order((size_t)M);
+    for (int64_t i = 0; i < M; ++i) order[(size_t)i] = i;
+    if (radii != nullptr)
+        std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return radii[a] < radii[b]; });
     double pmax = 0.0;
     for (int64_t i = 0; i < Mp; ++i) {
         const bool real = i < M;
+        const int64_t src = real ? order[(size_t)i] : 0;
         float p[WOS_MAX_D];
         double nn = 0.0;
+        float *chunk = hsoa.data() + (size_t)(i / pc::kChunk) * (d + 1) * pc::kChunk + (size_t)(i % pc::kChunk);
+        if (real && radii != nullptr) {
+            const float r32 = (float)radii[src];
+            chunk[(size_t)d * pc::kChunk] = r32;
+            // chunk bound rounded up: never below the FP64 radius
+            float up = r32 < radii[src] ? std::nextafter(r32, 3.0e38f) : r32;
+            float &cb = hrhi[(size_t)(i / pc::kChunk)];
+            cb = std::max(cb, up);
+        }
         for (int j = 0; j < d; ++j) {
-            // padding points sit far outside any domain: they never win the minimum
-            p[j] = real ? (float)pts[i * d + j] : 1.0e3f;
-            h32[(size_t)i * d + j] = p[j];
+            // padding centres sit far outside any domain: they never win the minimum
+            p[j] = real ? (float)pts[src * d + j] : 1.0e3f;
+            chunk[(size_t)j * pc::kChunk] = p[j];
             nn += (double)p[j] * (double)p[j];
             if (real) pmax = std::max(pmax, std::fabs((double)p[j]));
         }
@@ -596,32 +753,24 @@ cudaError_t pointcloud_prepare(const double *pts, int64_t M, int d, PointCloudDe
     }
     out->n_tiles = (int)n_tiles;
     out->pmax = pmax;
+    out->spheres = radii != nullptr ? 1 : 0;
     cudaError_t e = cudaMalloc(&out->tiles, hb.size() * 2);
-    if (e == cudaSuccess) e = cudaMalloc(&out->pts32, h32.size() * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&out->soa, hsoa.size() * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&out->chunk_rhi, hrhi.size() * 4);
     if (e == cudaSuccess) e = cudaMemcpy(out->tiles, hb.data(), hb.size() * 2, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(out->pts32, h32.data(), h32.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(out->soa, hsoa.data(), hsoa.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(out->chunk_rhi, hrhi.data(), hrhi.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
-    // tensor map over the tiles: 2D, 64 BF16 (128 B) wide, 64 rows per 8 KB tile
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult qr;
-    e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr);
-    if (e != cudaSuccess || fn == nullptr || qr != cudaDriverEntryPointSuccess) return cudaErrorNotSupported;
-    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    const cuuint64_t dims[2] = {64, (cuuint64_t)n_tiles * (pc::kTileBytes / 128)};
-    const cuuint64_t strides[1] = {128};
-    const cuuint32_t box[2] = {64, pc::kTileBytes / 128};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult cr = encode(&out->tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, out->tiles, dims, strides, box,
-                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return cr == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+    return cudaSuccess;
 }
 
 void pointcloud_release(PointCloudDev *pcd) {
     cudaFree(pcd->tiles);
-    cudaFree(pcd->pts32);
+    cudaFree(pcd->soa);
+    cudaFree(pcd->chunk_rhi);
     pcd->tiles = nullptr;
-    pcd->pts32 = nullptr;
+    pcd->soa = nullptr;
+    pcd->chunk_rhi = nullptr;
 }
 
 // Bound of |D~ - D| for the BF16-split contraction: representation of x and -2p (2^-18
@@ -636,57 +785,46 @@ float pointcloud_delta(int d, double xabs, double pmax) {
     return (float)(2.0 * bound + 1e-6);
 }
 
-static cudaError_t configure_pc(size_t smem) {
+static cudaError_t configure_spheres(size_t smem) {
     cudaError_t e = cudaSuccess;
-#define WOS_CFG(DD)                                                                                             \
-    if (e == cudaSuccess)                                                                                       \
-        e = cudaFuncSetAttribute(pc::pointcloud_kernel<DD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)smem);                                                                    \
-    if (e == cudaSuccess)                                                                                       \
-        e = cudaFuncSetAttribute(pc::pointcloud_kernel<DD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+#define WOS_CFG(DD)                                                                                          \
+    if (e == cudaSuccess)                                                                                    \
+        e = cudaFuncSetAttribute(pc::sphere_kernel<DD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)smem);                                                                 \
+    if (e == cudaSuccess)                                                                                    \
+        e = cudaFuncSetAttribute(pc::sphere_kernel<DD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                                  (int)smem);
     WOS_CFG(2) WOS_CFG(3) WOS_CFG(4) WOS_CFG(5) WOS_CFG(6) WOS_CFG(7) WOS_CFG(8) WOS_CFG(9) WOS_CFG(10)
 #undef WOS_CFG
     return e;
 }
 
-cudaError_t launch_pointcloud(const PointCloudDev &pcd, const MixedProblem &P, float delta,
-                              unsigned long long *cursor, int *status, unsigned long long *shrinks,
-                              uint64_t seed, int64_t max_steps, int grad, cudaStream_t s,
-                              double *radius_out) {
-    static bool configured = false;
+int sphere_ctas_per_sm() { return pc::kCtasPerSm; }
+
+cudaError_t launch_spheres(const SphereLaunch &L, int d, int grad, int grid, cudaStream_t s) {
+    // the attribute is per device: remember which devices are configured
+    static std::mutex mu;
+    static std::vector<int> configured;
     const size_t smem = pc::smem_bytes();
-    if (!configured) {
-        const cudaError_t e = configure_pc(smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        if (std::find(configured.begin(), configured.end(), dev) == configured.end()) {
+            e = configure_spheres(smem);
+            if (e != cudaSuccess) return e;
+            configured.push_back(dev);
+        }
     }
-    pc::Launch L;
-    memset(&L, 0, sizeof(L));
-    L.tmap = pcd.tmap;
-    L.P = P;
-    L.pts32 = pcd.pts32;
-    L.n_tiles = pcd.n_tiles;
-    L.delta = delta;
-    L.cursor = cursor;
-    L.status = status;
-    L.shrinks = shrinks;
-    L.seed = seed;
-    L.max_steps = max_steps;
-    L.total_walks = P.Q * P.N;
-    L.radius_out = radius_out;
-    int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t ctas_needed = (L.total_walks + pc::kRows - 1) / pc::kRows;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(2LL * sms, ctas_needed));
-    switch (P.d) {
-#define WOS_CASE(DD)                                                                         \
-    case DD:                                                                                 \
-        if (grad)                                                                            \
-            pc::pointcloud_kernel<DD, true><<<grid, pc::kThreads, smem, s>>>(L);            \
-        else                                                                                 \
-            pc::pointcloud_kernel<DD, false><<<grid, pc::kThreads, smem, s>>>(L);           \
+    if (grid < 1) return cudaSuccess;
+    switch (d) {
+#define WOS_CASE(DD)                                                               \
+    case DD:                                                                       \
+        if (grad)                                                                  \
+            pc::sphere_kernel<DD, true><<<grid, pc::kThreads, smem, s>>>(L);       \
+        else                                                                       \
+            pc::sphere_kernel<DD, false><<<grid, pc::kThreads, smem, s>>>(L);      \
         break;
         WOS_CASE(2) WOS_CASE(3) WOS_CASE(4) WOS_CASE(5) WOS_CASE(6) WOS_CASE(7) WOS_CASE(8) WOS_CASE(9)
         WOS_CASE(10)
@@ -694,6 +832,40 @@ cudaError_t launch_pointcloud(const PointCloudDev &pcd, const MixedProblem &P, f
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+// One problem: implicit items of about 64 walks per walker (at least 4 items per CTA slot
+// when there is that much work), so that the item tails stay short against the item.
+cudaError_t launch_pointcloud(const PointCloudDev &pcd, const MixedProblem &P, float delta,
+                              unsigned long long *cursor, int *status, unsigned long long *shrinks,
+                              uint64_t seed, int64_t max_steps, int grad, cudaStream_t s,
+                              double *radius_out) {
+    SphereLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.single.P = P;
+    L.single.tiles = pcd.tiles;
+    L.single.soa = pcd.soa;
+    L.single.chunk_rhi = pcd.chunk_rhi;
+    L.single.n_tiles = pcd.n_tiles;
+    L.single.delta = delta;
+    L.item_cursor = cursor;
+    L.status = status;
+    L.shrinks = shrinks;
+    L.seed = seed;
+    L.max_steps = max_steps;
+    L.radius_out = radius_out;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t total = P.Q * P.N;
+    if (total <= 0) return cudaSuccess;
+    const int64_t slots = (int64_t)pc::kCtasPerSm * sms;
+    int64_t wpi = (total + 4 * slots - 1) / (4 * slots);
+    wpi = std::max<int64_t>(pc::kRows, std::min<int64_t>(wpi, (int64_t)pc::kRows * 64));
+    L.walks_per_item = wpi;
+    L.n_items = (total + wpi - 1) / wpi;
+    const int grid = (int)std::min<int64_t>(slots, L.n_items);
+    return launch_spheres(L, P.d, grad, grid, s);
 }
 
 }  // namespace wos

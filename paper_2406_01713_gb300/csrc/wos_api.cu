@@ -418,16 +418,18 @@ wos_status launch_finalize(const FinalizeArgs &a, cudaStream_t s) {
 struct Opts {
     int precision, laplace;
     int cv;  // gradient control variate (gradient calls only)
+    int cuda_core_balls;  // keep tensor-core ball sets on the CUDA-core screen
     uint64_t seed;
     int64_t walk_offset, max_steps;
 };
 
 Opts read_opts(const wos_options *o) {
-    Opts r{WOS_MIXED, 0, 0, 0ull, 0, 10000};
+    Opts r{WOS_MIXED, 0, 0, 0, 0ull, 0, 10000};
     if (o != nullptr) {
         r.precision = o->precision;
         r.laplace = (o->flags & WOS_FLAG_LAPLACE_FACTOR) ? 1 : 0;
         r.cv = (o->flags & WOS_FLAG_GRAD_CONTROL_VARIATE) ? 1 : 0;
+        r.cuda_core_balls = (o->flags & WOS_FLAG_CUDA_CORE_BALLS) ? 1 : 0;
         r.seed = o->seed;
         r.walk_offset = o->walk_offset;
         r.max_steps = o->max_steps > 0 ? o->max_steps : 10000;
@@ -579,10 +581,10 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
     if (o.precision != WOS_MIXED) return fail(WOS_ERR_INVALID_ARG, "unknown precision %d", o.precision);
     WeightTable tab;
     WOS_TRY(ensure_table(dom, sigma, &tab));
-    if (dom->n_points > 0) {
+    if (dom->n_points > 0 || (dom->has_pcd && !o.cuda_core_balls)) {
         if (!dom->has_pcd)
             return fail(WOS_ERR_UNSUPPORTED, "mixed-precision point clouds need d <= %d", kPointCloudMaxD);
-        if (dom->n_balls > 0)
+        if (dom->n_balls > 0 && dom->n_points > 0)
             return fail(WOS_ERR_UNSUPPORTED, "a domain with both balls and points runs in FP64 or plain FP32");
         MixedProblem P = make_mixed_problem(dom, x, Q, N, eps, sigma, grad_mode, o.laplace, cv, o.walk_offset, tab,
                                             (double *)sc.acc, sc.counts, pw);
@@ -854,8 +856,10 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
     }
     layout_view<double>(D->v64, D->f64, *D);
     layout_view<float>(D->v32, D->f32, *D);
-    if (D->n_points > 0 && d <= kPointCloudMaxD) {
-        e = pointcloud_prepare(D->points.data(), D->n_points, d, &D->pcd);
+    const bool sphere_balls = D->n_points == 0 && D->n_balls >= kSphereMinBalls && d <= kPointCloudMaxD;
+    if ((D->n_points > 0 && d <= kPointCloudMaxD) || sphere_balls) {
+        e = sphere_balls ? pointcloud_prepare(D->ball_c.data(), D->ball_r.data(), D->n_balls, d, &D->pcd)
+                         : pointcloud_prepare(D->points.data(), nullptr, D->n_points, d, &D->pcd);
         if (e != cudaSuccess) {
             const wos_status st = fail(e == cudaErrorMemoryAllocation ? WOS_ERR_OOM : WOS_ERR_CUDA,
                                        "point-cloud operand setup failed: %s", cudaGetErrorString(e));
@@ -883,6 +887,13 @@ wos_status wos_domain_destroy(wos_domain_t dom) {
     for (float2 *t : dom->tables) cudaFree(t);
     if (dom->has_pcd) pointcloud_release(&dom->pcd);
     delete dom;
+    return WOS_OK;
+}
+
+wos_status wos_domain_info(wos_domain_t dom, int32_t *tensor_sphere_set, int32_t *sphere_tiles) {
+    if (dom == nullptr) return fail(WOS_ERR_INVALID_ARG, "domain is NULL");
+    if (tensor_sphere_set != nullptr) *tensor_sphere_set = dom->has_pcd ? 1 : 0;
+    if (sphere_tiles != nullptr) *sphere_tiles = dom->has_pcd ? dom->pcd.n_tiles : 0;
     return WOS_OK;
 }
 
@@ -1291,6 +1302,7 @@ struct wos_batch_s {
     size_t smem = 0;
     int grid = 0;
     int64_t n_items = 0, total_q = 0;
+    int64_t n_sphere_items = 0;  // items of the tensor-core sphere-set launches
     void *dev = nullptr;       // problems | items | finalize records | zeroed region
     size_t zero_off = 0, zero_bytes = 0;
     wos_stats *d_stats = nullptr;
@@ -1379,9 +1391,18 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     const int n = (int)b->probs.size();
     b->grad_any = 0;
     b->smem = 16;
-    for (const wos_problem &p : b->probs) {
+    // problems whose obstacles are a tensor-core sphere set (large ball sets, point sets) run on
+    // the sphere-set walker, the others on the CUDA-core persistent walker
+    std::vector<char> tensor(n, 0);
+    for (int i = 0; i < n; ++i) {
+        const wos_problem &p = b->probs[i];
         b->grad_any |= p.grad != nullptr;
-        b->smem = std::max(b->smem, mixed_smem_bytes(*p.domain));
+        if (p.domain->n_points > 0 && !p.domain->has_pcd)
+            return fail(WOS_ERR_UNSUPPORTED, "problem %d: mixed-precision point sets need d <= %d", i, kPointCloudMaxD);
+        if (p.domain->n_points > 0 && p.domain->n_balls > 0)
+            return fail(WOS_ERR_UNSUPPORTED, "problem %d: a domain with both balls and points", i);
+        tensor[i] = p.domain->has_pcd && (p.domain->n_points > 0 || !b->o.cuda_core_balls);
+        if (!tensor[i]) b->smem = std::max(b->smem, mixed_smem_bytes(*p.domain));
     }
     if (b->smem > 227 * 1024) return fail(WOS_ERR_UNSUPPORTED, "ball set needs %zu B of shared memory", b->smem);
     WOS_TRY(ensure_mixed_smem(b->smem));
@@ -1431,6 +1452,7 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
                      [&](int a, int c) { return prob_cost[a] > prob_cost[c]; });
     std::vector<MixedItem> sorted;
     for (int i : porder) {
+        if (tensor[i]) continue;
         const wos_problem &p = b->probs[i];
         const int64_t total = p.n_queries * p.n_walks;
         for (int64_t j0 = 0; j0 < total; j0 += prob_wpi[i]) {
@@ -1443,15 +1465,53 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     }
     b->n_items = (int64_t)sorted.size();
     b->total_q = q_begin;
+    // sphere-set items: one queue per dimension, problems by decreasing cost, 32 walks per
+    // walker slot per item (a CTA continues into the next item of the same problem without a
+    // pause, so items only matter for the balance at the end)
+    const int64_t kSphereItemWalks = 128 * 32;
+    std::vector<int> sph_index(n, -1);
+    std::vector<int> sph_problem;  // sphere problem -> batch problem
+    std::vector<std::vector<SphereItem>> sph_items(kPointCloudMaxD + 1);
+    for (int i : porder) {
+        if (!tensor[i]) continue;
+        sph_index[i] = (int)sph_problem.size();
+        sph_problem.push_back(i);
+        const wos_problem &p = b->probs[i];
+        const int64_t total = p.n_queries * p.n_walks;
+        for (int64_t j0 = 0; j0 < total; j0 += kSphereItemWalks) {
+            SphereItem it{};
+            it.problem = sph_index[i];
+            it.j0 = j0;
+            it.j1 = std::min(total, j0 + kSphereItemWalks);
+            sph_items[p.domain->d].push_back(it);
+        }
+    }
+    std::vector<SphereItem> sph_all;
+    std::vector<size_t> sph_off(kPointCloudMaxD + 2, 0);
+    for (int dd = 0; dd <= kPointCloudMaxD; ++dd) {
+        sph_off[dd] = sph_all.size();
+        sph_all.insert(sph_all.end(), sph_items[dd].begin(), sph_items[dd].end());
+    }
+    sph_off[kPointCloudMaxD + 1] = sph_all.size();
+    b->n_sphere_items = (int64_t)sph_all.size();
+    const int n_sph = (int)sph_problem.size();
     const size_t off_recs = off_items + align256(sizeof(MixedItem) * std::max<size_t>(1, sorted.size()));
-    const size_t off_zero = off_recs + align256(sizeof(FinalizeRec) * n);
-    const size_t zero_bytes = acc_bytes + 256 /* cursor */ + align256(sizeof(wos_stats));
+    const size_t off_sph = off_recs + align256(sizeof(FinalizeRec) * n);
+    const size_t off_sph_items = off_sph + align256(sizeof(SphereProblem) * std::max(1, n_sph));
+    const size_t off_zero = off_sph_items + align256(sizeof(SphereItem) * std::max<size_t>(1, sph_all.size()));
+    // zeroed: accumulators | mixed cursor (8) + sphere status (8) + shrinks (8) + one cursor per
+    // dimension | stats
+    const size_t ctl_bytes = align256(8 * (3 + kPointCloudMaxD + 1));
+    const size_t zero_bytes = acc_bytes + ctl_bytes + align256(sizeof(wos_stats));
     const size_t total_bytes = off_zero + zero_bytes;
     WOS_CUDA(cudaMalloc(&b->dev, total_bytes));
     char *base = (char *)b->dev;
     char *zero = base + off_zero;
     unsigned long long *cursor = (unsigned long long *)(zero + acc_bytes);
-    b->d_stats = (wos_stats *)(zero + acc_bytes + 256);
+    int *sph_status = reinterpret_cast<int *>(cursor + 1);
+    unsigned long long *sph_shrinks = cursor + 2;
+    unsigned long long *sph_cursors = cursor + 3;  // [d]
+    b->d_stats = (wos_stats *)(zero + acc_bytes + ctl_bytes);
     b->zero_off = off_zero;
     b->zero_bytes = zero_bytes;
     walk_base = b->o.walk_offset;
@@ -1490,6 +1550,22 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         WOS_CUDA(cudaMemcpy(base + off_items, sorted.data(), sizeof(MixedItem) * sorted.size(),
                             cudaMemcpyHostToDevice));
     WOS_CUDA(cudaMemcpy(base + off_recs, fr.data(), sizeof(FinalizeRec) * n, cudaMemcpyHostToDevice));
+    if (n_sph > 0) {
+        std::vector<SphereProblem> sp(n_sph);
+        for (int k = 0; k < n_sph; ++k) {
+            const int i = sph_problem[k];
+            const wos_domain_s &D = *b->probs[i].domain;
+            sp[k].P = mp[i];
+            sp[k].tiles = D.pcd.tiles;
+            sp[k].soa = D.pcd.soa;
+            sp[k].chunk_rhi = D.pcd.chunk_rhi;
+            sp[k].n_tiles = D.pcd.n_tiles;
+            sp[k].delta = D.pc_delta;
+        }
+        WOS_CUDA(cudaMemcpy(base + off_sph, sp.data(), sizeof(SphereProblem) * n_sph, cudaMemcpyHostToDevice));
+        WOS_CUDA(cudaMemcpy(base + off_sph_items, sph_all.data(), sizeof(SphereItem) * sph_all.size(),
+                            cudaMemcpyHostToDevice));
+    }
 
     MixedLaunch L{};
     L.problems = (const MixedProblem *)base;
@@ -1505,12 +1581,39 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     fa.n = n;
     fa.total_q = b->total_q;
     fa.stats = b->d_stats;
+    fa.status = n_sph > 0 ? sph_status : nullptr;
+    fa.shrinks = n_sph > 0 ? sph_shrinks : nullptr;
+
+    // one sphere-set launch per dimension, each on its own stream so that their CTAs and the
+    // CUDA-core walker's share the GPU as each queue drains
+    std::vector<int> sph_dims;
+    for (int dd = 0; dd <= kPointCloudMaxD; ++dd)
+        if (sph_off[dd + 1] > sph_off[dd]) sph_dims.push_back(dd);
+    std::vector<cudaStream_t> side(sph_dims.size(), nullptr);
+    std::vector<cudaEvent_t> ev(sph_dims.size() + 1, nullptr);
+    auto cleanup = [&]() {
+        for (cudaStream_t x : side)
+            if (x) cudaStreamDestroy(x);
+        for (cudaEvent_t x : ev)
+            if (x) cudaEventDestroy(x);
+    };
+    for (size_t k = 0; k < side.size(); ++k)
+        if (cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking) != cudaSuccess) {
+            cleanup();
+            return fail(WOS_ERR_CUDA, "stream creation failed");
+        }
+    for (size_t k = 0; k < ev.size(); ++k)
+        if (cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) != cudaSuccess) {
+            cleanup();
+            return fail(WOS_ERR_CUDA, "event creation failed");
+        }
 
     cudaStream_t cap = nullptr;
     WOS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     wos_status st = WOS_OK;
     if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaStreamDestroy(cap);
+        cleanup();
         return fail(WOS_ERR_CUDA, "batch capture failed to start");
     }
     if (cudaMemsetAsync(zero, 0, zero_bytes, cap) != cudaSuccess) st = fail(WOS_ERR_CUDA, "memset capture");
@@ -1523,12 +1626,35 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         pa.seed = b->o.seed;
         st = launch_cv_prepass(pa, cap);
     }
+    if (st == WOS_OK && !sph_dims.empty() && cudaEventRecord(ev.back(), cap) != cudaSuccess)
+        st = fail(WOS_ERR_CUDA, "fork event capture failed");
+    for (size_t k = 0; st == WOS_OK && k < sph_dims.size(); ++k) {
+        const int dd = sph_dims[k];
+        SphereLaunch SL;
+        memset(&SL, 0, sizeof(SL));
+        SL.problems = (const SphereProblem *)(base + off_sph);
+        SL.items = (const SphereItem *)(base + off_sph_items) + sph_off[dd];
+        SL.n_items = (int64_t)(sph_off[dd + 1] - sph_off[dd]);
+        SL.item_cursor = sph_cursors + dd;
+        SL.status = sph_status;
+        SL.shrinks = sph_shrinks;
+        SL.seed = b->o.seed;
+        SL.max_steps = b->o.max_steps;
+        const int grid = (int)std::min<int64_t>((int64_t)sphere_ctas_per_sm() * sms, SL.n_items);
+        if (cudaStreamWaitEvent(side[k], ev.back(), 0) != cudaSuccess ||
+            launch_spheres(SL, dd, b->grad_any, grid, side[k]) != cudaSuccess ||
+            cudaEventRecord(ev[k], side[k]) != cudaSuccess)
+            st = fail(WOS_ERR_CUDA, "sphere-set kernel capture failed");
+    }
     if (st == WOS_OK && b->n_items > 0 &&
         launch_walk_mixed(L, b->grad_any, b->grid, cfg.threads, b->smem, cap) != cudaSuccess)
         st = fail(WOS_ERR_CUDA, "walk kernel capture failed");
+    for (size_t k = 0; st == WOS_OK && k < sph_dims.size(); ++k)
+        if (cudaStreamWaitEvent(cap, ev[k], 0) != cudaSuccess) st = fail(WOS_ERR_CUDA, "join capture failed");
     if (st == WOS_OK) st = launch_finalize(fa, cap);
     cudaError_t e = cudaStreamEndCapture(cap, &b->graph);
     cudaStreamDestroy(cap);
+    cleanup();
     if (st != WOS_OK) return st;
     if (e != cudaSuccess) return fail(WOS_ERR_CUDA, "batch capture failed: %s", cudaGetErrorString(e));
     WOS_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
@@ -1567,8 +1693,9 @@ wos_status wos_batch_create(const wos_problem *probs, int32_t n_problems, const 
         const wos_problem &p = probs[i];
         WOS_TRY(check_common(p.domain, p.x, p.n_queries, p.n_walks, p.eps, p.sigma));
         if (p.n_queries > 0 && p.u == nullptr) return fail(WOS_ERR_INVALID_ARG, "problem %d: u is NULL", i);
-        if (p.domain->n_points > 0)
-            return fail(WOS_ERR_UNSUPPORTED, "problem %d: point-cloud domains are not batched", i);
+        if (p.domain->n_points > 0 && !p.domain->has_pcd)
+            return fail(WOS_ERR_UNSUPPORTED, "problem %d: mixed-precision point sets need d <= %d", i,
+                        kPointCloudMaxD);
         if (p.n_queries * p.n_walks > (int64_t)0x7fffffff)
             return fail(WOS_ERR_UNSUPPORTED, "problem %d: n_queries * n_walks must be < 2^31", i);
     }
@@ -1771,8 +1898,7 @@ extern "C" wos_status wos_debug_pointcloud_radius(wos_domain_t dom, const double
                                                   double *radius, void *stream) {
     WOS_TRY(check_common(dom, x, Q, 1, 1e-30, 0.0));
     if (Q > 0 && radius == nullptr) return fail(WOS_ERR_INVALID_ARG, "radius is NULL");
-    if (!dom->has_pcd) return fail(WOS_ERR_UNSUPPORTED, "the domain has no tensor-core point set");
-    if (dom->n_balls > 0) return fail(WOS_ERR_UNSUPPORTED, "a domain with both balls and points");
+    if (!dom->has_pcd) return fail(WOS_ERR_UNSUPPORTED, "the domain has no tensor-core sphere set");
     if (Q == 0) return WOS_OK;
     cudaStream_t s = (cudaStream_t)stream;
     WeightTable tab;

@@ -120,20 +120,58 @@ inline int max_active_mixed(int threads, size_t smem_bytes, int grad_any) {
 
 // Point-cloud obstacles for the tensor-core walker (pointcloud.cu): BF16-split point tiles in
 // the MMA's core-matrix layout, their TMA tensor map, and padded FP32 copies for refinement.
+// Sphere set for the tensor-core walker: points (radius 0) or balls. Balls are sorted by radius
+// so that each 32-column chunk spans a narrow radius range; chunk_rhi bounds the radii of a
+// chunk from above.
 struct PointCloudDev {
-    CUtensorMap tmap;
-    void *tiles = nullptr;
-    float *pts32 = nullptr;
+    void *tiles = nullptr;      // n_tiles x 4 KB BF16 tiles, already in the shared-memory layout
+    float *soa = nullptr;       // per 32-sphere chunk: d rows of centre coordinates, then radii
+    float *chunk_rhi = nullptr; // largest radius of each 32-column chunk (rounded up)
     int n_tiles = 0;
-    double pmax = 0.0;  // largest |coordinate| of a point
+    int spheres = 0;            // 1: balls with radii; 0: points
+    double pmax = 0.0;  // largest |coordinate| of a centre
 };
-cudaError_t pointcloud_prepare(const double *pts, int64_t M, int d, PointCloudDev *out);
+// radii: NULL for a point set, else M ball radii (the set is reordered by radius).
+cudaError_t pointcloud_prepare(const double *pts, const double *radii, int64_t M, int d, PointCloudDev *out);
 void pointcloud_release(PointCloudDev *pcd);
 float pointcloud_delta(int d, double xabs, double pmax);
+
+// One problem of the tensor-core walker.
+struct SphereProblem {
+    MixedProblem P;
+    const void *tiles;
+    const float *soa;
+    const float *chunk_rhi;
+    int n_tiles;
+    float delta;  // bound of |D~ - D| of the BF16 contraction (squared-distance units)
+};
+struct SphereItem {
+    int problem;
+    int pad;
+    int64_t j0, j1;  // walk range within the problem
+};
+// A persistent launch over items (problem, walk range) of problems that share the dimension.
+struct SphereLaunch {
+    const SphereProblem *problems;    // device array, or nullptr: problem 0 is `single`
+    const SphereItem *items;          // device array, or nullptr: implicit items of `single`
+    int64_t n_items;
+    int64_t walks_per_item;           // implicit items: item i = walks [i wpi, min((i+1) wpi, Q N))
+    unsigned long long *item_cursor;  // zero before the launch
+    int *status;                      // nonzero: a wait timed out
+    unsigned long long *shrinks;      // steps whose radius came from a chunk bound
+    uint64_t seed;
+    int64_t max_steps;
+    double *radius_out;  // nullable: distance bound at each walk's start (single problem only)
+    SphereProblem single;
+};
+cudaError_t launch_spheres(const SphereLaunch &L, int d, int grad, int grid, cudaStream_t s);
+int sphere_ctas_per_sm();
+// Single problem: implicit items, grid sized to the work.
 cudaError_t launch_pointcloud(const PointCloudDev &pcd, const MixedProblem &P, float delta,
                               unsigned long long *cursor, int *status, unsigned long long *shrinks,
                               uint64_t seed, int64_t max_steps, int grad, cudaStream_t s,
                               double *radius_out = nullptr);
 constexpr int kPointCloudMaxD = 10;  // 3d + 2 BF16 columns fit the 32-wide contraction
+constexpr int kSphereMinBalls = 512; // ball sets at least this large run on the tensor cores
 
 }  // namespace wos

@@ -26,11 +26,13 @@ def _stream():
     return _VP(torch.cuda.current_stream().cuda_stream)
 
 
-def _opts(precision="mixed", seed=0, walk_offset=0, max_steps=10000, laplace=False, control_variate=False):
+def _opts(precision="mixed", seed=0, walk_offset=0, max_steps=10000, laplace=False, control_variate=False,
+          cuda_core_balls=False):
     o = _lib.Options()
     o.precision = _lib.PRECISION[precision] if isinstance(precision, str) else int(precision)
     o.flags = ((_lib.WOS_FLAG_LAPLACE_FACTOR if laplace else 0) |
-               (_lib.WOS_FLAG_GRAD_CONTROL_VARIATE if control_variate else 0))
+               (_lib.WOS_FLAG_GRAD_CONTROL_VARIATE if control_variate else 0) |
+               (_lib.WOS_FLAG_CUDA_CORE_BALLS if cuda_core_balls else 0))
     o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     o.walk_offset = int(walk_offset)
     o.max_steps = int(max_steps)
@@ -119,14 +121,14 @@ class Domain:
 
     # ----------------------------------------------------------------- estimators
     def solve(self, x, n_walks, eps, sigma, precision="mixed", seed=0, walk_offset=0,
-              max_steps=10000, laplace=False, with_stats=False):
+              max_steps=10000, laplace=False, with_stats=False, cuda_core_balls=False):
         L = _lib.load()
         x = _dev_f64(x, self.d)
         Q = x.shape[0]
         u = torch.empty(Q, dtype=torch.float64, device=x.device)
         se = torch.empty_like(u)
         st = torch.zeros(6, dtype=torch.int64, device=x.device) if with_stats else None
-        o = _opts(precision, seed, walk_offset, max_steps, laplace)
+        o = _opts(precision, seed, walk_offset, max_steps, laplace, cuda_core_balls=cuda_core_balls)
         _lib.check(L.wos_solve(self.h, ctypes.byref(o), _ptr(x), Q, int(n_walks), float(eps),
                                float(sigma), _ptr(u), _ptr(se), _ptr(st), _stream()), "wos_solve")
         out = {"u": u, "u_se": se}
@@ -135,7 +137,7 @@ class Domain:
         return out
 
     def grad(self, x, n_walks, eps, sigma, precision="mixed", seed=0, walk_offset=0,
-             max_steps=10000, laplace=False, with_stats=False, control_variate=False):
+             max_steps=10000, laplace=False, with_stats=False, control_variate=False, cuda_core_balls=False):
         """u, grad u (first-sphere estimator; control_variate=True subtracts the walks' mean
         value, WOS_FLAG_GRAD_CONTROL_VARIATE), their SEs, du/dsigma and du/dw per query."""
         L = _lib.load()
@@ -146,7 +148,7 @@ class Domain:
                "grad_se": torch.empty(Q, d, **f), "du_dsigma": torch.empty(Q, **f),
                "du_dw": torch.empty(Q, self.n_exp, **f) if self.n_exp else None}
         st = torch.zeros(6, dtype=torch.int64, device=x.device) if with_stats else None
-        o = _opts(precision, seed, walk_offset, max_steps, laplace, control_variate)
+        o = _opts(precision, seed, walk_offset, max_steps, laplace, control_variate, cuda_core_balls)
         _lib.check(L.wos_grad(self.h, ctypes.byref(o), _ptr(x), Q, int(n_walks), float(eps), float(sigma),
                               _ptr(out["u"]), _ptr(out["u_se"]), _ptr(out["grad"]), _ptr(out["grad_se"]),
                               _ptr(out["du_dsigma"]), _ptr(out["du_dw"]), _ptr(st), _stream()),
@@ -156,7 +158,7 @@ class Domain:
         return out
 
     def walks(self, x, n_walks, eps, sigma, grad_mode=False, precision="mixed", seed=0,
-              walk_offset=0, max_steps=10000, laplace=False):
+              walk_offset=0, max_steps=10000, laplace=False, cuda_core_balls=False):
         """Per-walk terminals, jump counts, gradient estimates and d/dsigma (parity checks)."""
         L = _lib.load()
         x = _dev_f64(x, self.d)
@@ -164,7 +166,7 @@ class Domain:
         f = dict(dtype=torch.float64, device=x.device)
         out = {"term": torch.empty(Q, N, **f), "jumps": torch.empty(Q, N, dtype=torch.int64, device=x.device),
                "grad": torch.empty(Q, N, d, **f), "dsigma": torch.empty(Q, N, **f)}
-        o = _opts(precision, seed, walk_offset, max_steps, laplace)
+        o = _opts(precision, seed, walk_offset, max_steps, laplace, cuda_core_balls=cuda_core_balls)
         _lib.check(L.wos_walks(self.h, ctypes.byref(o), _ptr(x), Q, N, float(eps), float(sigma),
                                int(bool(grad_mode)), _ptr(out["term"]), _ptr(out["jumps"]),
                                _ptr(out["grad"]), _ptr(out["dsigma"]), _stream()), "wos_walks")
@@ -199,6 +201,13 @@ class Domain:
                                    float(sigma), float(s_ub), _ptr(path), _ptr(flags), _ptr(grads),
                                    _stream()), "wos_plan_path")
         return path, flags, grads
+
+    def info(self):
+        """{'tensor_sphere_set': bool, 'sphere_tiles': int}: which mixed-precision walker runs it."""
+        L = _lib.load()
+        t, n = ctypes.c_int32(0), ctypes.c_int32(0)
+        _lib.check(L.wos_domain_info(self.h, ctypes.byref(t), ctypes.byref(n)), "wos_domain_info")
+        return {"tensor_sphere_set": bool(t.value), "sphere_tiles": int(n.value)}
 
     def set_exp_w(self, w):
         L = _lib.load()

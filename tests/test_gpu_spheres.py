@@ -1,0 +1,148 @@
+"""Ball sets on the tensor-core sphere-set walker (|c|^2 - 2 x.c by tcgen05.mma, balls sorted by
+radius into 32-ball chunks, exact FP32 refinement of the best chunk, lower bound for the rest).
+
+* the distance bound never exceeds the exact FP64 distance |x - c| - r (minus box) and is
+  tight for most points;
+* walks agree with the FP64 oracle and with the CUDA-core ball screen (same Philox streams),
+  within 4 combined standard errors;
+* with exponential boundary data the estimates match the exact solution u = exp(a.x).
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+from paper_2406_01713_gb300 import _lib, synth  # noqa: E402
+from paper_2406_01713_gb300 import wos as W  # noqa: E402
+
+
+def np_(t):
+    return t.detach().cpu().numpy()
+
+
+def within(a, se_a, b, se_b, k=4.0, atol=1e-4):
+    return np.abs(a - b) <= k * np.sqrt(se_a ** 2 + se_b ** 2) + atol
+
+
+def ball_problem(d, B, sigma, seed, n_queries):
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-1, 1, size=(B, d))
+    r = np.exp(rng.uniform(math.log(0.01), math.log(0.2), size=B))
+    a = rng.standard_normal(d)
+    a *= math.sqrt(sigma) / np.linalg.norm(a)
+    dom = {"d": d, "box_lo": -np.ones(d), "box_hi": np.ones(d), "ball_c": c, "ball_r": r,
+           "exp_w": np.ones(1), "exp_a": a[None, :]}
+    X = synth._free_points(rng, n_queries, -np.ones(d), np.ones(d), c, r, 0.01)
+    return dom, X, rng
+
+
+def exact_radius(dom, X):
+    c, r = dom["ball_c"], dom["ball_r"]
+    db = (np.sqrt(((X[:, None, :] - c[None, :, :]) ** 2).sum(-1)) - r[None, :]).min(1)
+    box = np.minimum(X - dom["box_lo"][None, :], dom["box_hi"][None, :] - X).min(1)
+    return np.minimum(db, box)
+
+
+def gpu_radius(D, X):
+    L = _lib.load()
+    x = torch.tensor(X, dtype=torch.float64, device="cuda")
+    out = torch.full((X.shape[0],), float("nan"), dtype=torch.float64, device="cuda")
+    _lib.check(L.wos_debug_pointcloud_radius(D.h, ctypes.c_void_p(x.data_ptr()), X.shape[0],
+                                             ctypes.c_void_p(out.data_ptr()), None), "radius")
+    torch.cuda.synchronize()
+    return np_(out)
+
+
+@pytest.mark.parametrize("d,B", [(3, 4096), (7, 1000), (10, 600)])
+def test_radius_bound_is_safe_and_tight(d, B):
+    dom, X, rng = ball_problem(d, B, 4.0, 11 + d, 2000)
+    D = W.Domain(dom)
+    # also points close to ball surfaces (outside them)
+    idx = rng.integers(0, B, size=2000)
+    v = rng.standard_normal((2000, d))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    near = dom["ball_c"][idx] + (dom["ball_r"][idx] + 10 ** rng.uniform(-4, -1.5, size=2000))[:, None] * v
+    near = near[np.all(np.abs(near) < 0.999, axis=1)]
+    want_near = exact_radius(dom, near)
+    Y = np.vstack([X, near[want_near > 0]])
+    want = exact_radius(dom, Y)
+    got = gpu_radius(D, Y)
+    assert np.all(np.isfinite(got))
+    assert np.all(got <= want * (1 + 1e-5) + 2e-6), np.max(got - want)
+    rel = (want - got) / np.maximum(want, 1e-12)
+    assert np.mean(rel < 1e-3) > 0.9, np.mean(rel < 1e-3)
+    assert np.mean(rel < 0.5) > 0.99
+
+
+@pytest.mark.parametrize("d,B", [(3, 2048), (6, 512)])
+def test_walks_match_oracle_and_cuda_core_screen(d, B):
+    dom, X, _ = ball_problem(d, B, 9.0, 5 + d, 12)
+    D = W.Domain(dom)
+    N, eps, sigma, seed = 4096, 1e-3, 9.0, 3
+    ref = oracle.solve(dom, X, N, eps, sigma, seed, grad=True, control_variate=True)
+    tc = D.grad(X, N, eps, sigma, seed=seed, with_stats=True, control_variate=True)
+    cc = D.grad(X, N, eps, sigma, seed=seed, with_stats=True, control_variate=True, cuda_core_balls=True)
+    for got in (tc, cc):
+        st = W.stats_dict(got["stats"])
+        assert st["walks"] == 12 * N and st["outside"] == 0
+        assert np.all(within(np_(got["u"]), np_(got["u_se"]), ref["u"], ref["u_se"]))
+        assert np.all(within(np_(got["grad"]), np_(got["grad_se"]), ref["grad"], ref["grad_se"], atol=1e-3))
+    # exact solution u = exp(a.x) (|a|^2 = sigma) on any domain
+    a = dom["exp_a"][0]
+    ex = np.exp(X @ a)
+    u, se = np_(tc["u"]), np_(tc["u_se"])
+    assert np.all(np.abs(u - ex) <= 4.5 * se + 3e-3 * ex)
+
+
+def test_large_problem_exact_solution():
+    dom, X, _ = ball_problem(8, 4096, 16.0, 99, 64)
+    D = W.Domain(dom)
+    r = D.grad(X, 8192, 1e-3, 16.0, seed=1, with_stats=True, control_variate=True)
+    st = W.stats_dict(r["stats"])
+    assert st["walks"] == 64 * 8192 and st["outside"] == 0 and st["capped"] == 0
+    a = dom["exp_a"][0]
+    ex = np.exp(X @ a)
+    u, se = np_(r["u"]), np_(r["u_se"])
+    assert np.mean(np.abs(u - ex) <= 4.5 * se + 3e-3 * ex) > 0.98
+    g, gse = np_(r["grad"]), np_(r["grad_se"])
+    gx = a[None, :] * ex[:, None]
+    assert np.mean(np.abs(g - gx) <= 4.5 * gse + 3e-2 * np.abs(gx).max(axis=1, keepdims=True)) > 0.97
+
+
+def test_batch_mixes_tensor_and_cuda_core_problems():
+    """A batch with large ball sets (tensor-core sphere walker, one launch per dimension), small
+    ones (CUDA-core walker) and a point set, in one graph: every problem matches the oracle."""
+    specs = [(3, 2048, 4.0), (5, 16, 9.0), (5, 700, 1.0), (7, 64, 0.0), (8, 1024, 16.0), (3, 600, 25.0)]
+    probs, refs, base, seed = [], [], 0, 11
+    for i, (d, B, sigma) in enumerate(specs):
+        dom, X, _ = ball_problem(d, B, sigma, 100 + i, 6)
+        N = 2048
+        probs.append({"domain": W.Domain(dom), "x": X, "n_walks": N, "eps": 1e-3, "sigma": sigma, "grad": True})
+        refs.append(oracle.solve(dom, X, N, 1e-3, sigma, seed, walk_offset=base, grad=True, control_variate=True))
+        base += X.shape[0] * N
+    rng = np.random.default_rng(3)
+    pts = synth.ellipsoid_cloud(rng, 6, 2, 300)
+    a = rng.standard_normal(6)
+    a *= 2.0 / np.linalg.norm(a)
+    pdom = {"d": 6, "box_lo": -np.ones(6), "box_hi": np.ones(6), "points": pts, "exp_w": np.ones(1),
+            "exp_a": a[None, :]}
+    Xp = rng.uniform(-0.8, 0.8, size=(6, 6))
+    probs.append({"domain": W.Domain(pdom), "x": Xp, "n_walks": 2048, "eps": 1e-3, "sigma": 4.0, "grad": True})
+    refs.append(oracle.solve(pdom, Xp, 2048, 1e-3, 4.0, seed, walk_offset=base, grad=True, control_variate=True))
+    B_ = W.Batch(probs, seed=seed, control_variate=True)
+    out = B_.run()
+    torch.cuda.synchronize()
+    st = W.stats_dict(B_.stats)
+    assert st["walks"] == sum(p["x"].shape[0] * p["n_walks"] for p in probs) and st["outside"] == 0
+    for o, ref in zip(out, refs):
+        assert np.all(within(np_(o["u"]), np_(o["u_se"]), ref["u"], ref["u_se"]))
+        assert np.all(within(np_(o["grad"]), np_(o["grad_se"]), ref["grad"], ref["grad_se"], atol=1e-3))
+    B_.close()
