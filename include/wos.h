@@ -85,7 +85,7 @@ typedef enum {
 #define WOS_FLAG_GRAD_CONTROL_VARIATE 2
 
 /*
- * Ball sets of at least 512 balls in d <= 10 run, in WOS_MIXED, on the tensor-core sphere-set
+ * Ball sets of at least 512 balls run, in WOS_MIXED, on the tensor-core sphere-set
  * walker (the same walker as point sets: |c|^2 - 2 x.c by tcgen05.mma, exact FP32 refinement of
  * the best 32-ball chunk, a proven lower bound for the rest). This flag keeps them on the
  * CUDA-core ball screen instead (for comparisons; both are exact up to their error bounds).
@@ -162,7 +162,7 @@ wos_status wos_domain_set_exp_w(wos_domain_t dom, const double *w_device, int32_
 
 /*
  * Which walker the domain's obstacles run on in WOS_MIXED: *tensor_sphere_set = 1 if they form a
- * tensor-core sphere set (a point set, or at least 512 balls, in d <= 10), with *sphere_tiles
+ * tensor-core sphere set (a point set, or at least 512 balls), with *sphere_tiles
  * 64-sphere tiles; 0 (and 0 tiles) for the CUDA-core walker. Host outputs; either may be NULL.
  * No counterpart in the paper (introspection for schedulers and benchmarks).
  * Errors: INVALID_ARG (NULL domain).
@@ -263,12 +263,12 @@ typedef struct {
  * Builds a batch: uploads the problem table and the longest-first work queues, sizes the
  * persistent grids to a multiple of the SM count, and records one CUDA graph: [reset,
  * control-variate prepass (with WOS_FLAG_GRAD_CONTROL_VARIATE), the CUDA-core persistent walker
- * for the problems with small ball sets or d > 10, in parallel one tensor-core sphere-set walker
- * launch per dimension for the problems with tensor-core sphere sets (>= 512 balls or a point
- * set, d <= 10; WOS_FLAG_CUDA_CORE_BALLS keeps ball sets off it), finalize]. Problems may differ
- * in d, obstacle count, walk budget, sigma and eps. Precision is WOS_MIXED. The problems'
- * domains and buffers must outlive the batch. Errors: INVALID_ARG, UNSUPPORTED (a point set
- * with d > 10, a domain with both balls and points), OOM, CUDA.
+ * for the problems with small ball sets, in parallel one tensor-core sphere-set walker launch
+ * per dimension for the problems with tensor-core sphere sets (>= 512 balls or a point set;
+ * WOS_FLAG_CUDA_CORE_BALLS keeps ball sets off it), finalize]. Problems may differ in d,
+ * obstacle count, walk budget, sigma and eps. Precision is WOS_MIXED. The problems' domains and
+ * buffers must outlive the batch. Errors: INVALID_ARG, UNSUPPORTED (a domain with both balls
+ * and points), OOM, CUDA.
  */
 wos_status wos_batch_create(const wos_problem *probs, int32_t n_problems, const wos_options *opt,
                             const wos_batch_config *cfg, wos_batch_t *out);

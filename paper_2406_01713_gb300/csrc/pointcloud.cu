@@ -13,7 +13,8 @@
 //
 // BF16 split: x = x_h + x_l and -2p = q_h + q_l (each a BF16), |p|^2 = n_h + n_l; the walker
 // row [x_h, x_h, x_l, 1, 1] times the point row [q_h, q_l, q_h, n_h, n_l] gives
-// |p|^2 - 2 x.p up to the dropped x_l q_l term and FP32 accumulation (3d + 2 <= 32 = K).
+// |p|^2 - 2 x.p up to the dropped x_l q_l term and FP32 accumulation (3d + 2 columns, padded
+// to K = 32 for d <= 10 and K = 48 for d = 11, 12).
 //
 // CTA: warps 0-3 own one walker per thread (TMEM lanes 0..127); warp 4, lane 0, issues the
 // bulk copies of the centre tiles and the MMAs. The launch is persistent over a queue of items
@@ -39,23 +40,31 @@ namespace pc {
 
 constexpr int kRows = 128;       // walkers per CTA = MMA M = TMEM lanes
 constexpr int kTileN = 64;       // centres per tile = MMA N
-constexpr int kK = 32;           // padded contraction length (3d + 2 <= 32)
-constexpr int kStages = 6;       // centre-tile ring in shared memory
-constexpr int kAhead = 4;        // tiles loaded ahead of the MMA issue point
+constexpr int kMaxStages = 6;
 constexpr int kCtasPerSm = 4;    // 4 x 128 TMEM columns; registers <= 102 per thread
 constexpr int kChunk = 32;       // candidate chunk (columns)
 constexpr int kWalkerThreads = 128;
 constexpr int kThreads = kWalkerThreads + 32;
-constexpr uint32_t kTileBytes = kTileN * kK * 2;
-constexpr uint32_t kABytes = kRows * kK * 2;
 constexpr uint32_t kTmemCols = 2 * kTileN;
+
+// Contraction length: 3d + 2 BF16 columns padded to 32 (d <= 10) or 48 (d = 11, 12); the
+// centre-tile ring is shorter for the wider tiles so that four CTAs still fit an SM.
+__host__ __device__ constexpr int contraction_k(int d) { return 3 * d + 2 <= 32 ? 32 : 48; }
+template <int K>
+struct Geo {
+    static constexpr int kK = K;
+    static constexpr uint32_t kTileBytes = kTileN * K * 2;
+    static constexpr uint32_t kABytes = kRows * K * 2;
+    static constexpr uint32_t kSBO = (K / 8) * 128;  // to the next group of 8 rows
+    static constexpr int kStages = K == 32 ? 6 : 4;  // centre-tile ring in shared memory
+    static constexpr int kAhead = kStages - 2;       // tiles loaded ahead of the MMA issue point
+};
 constexpr uint32_t kTransposeBytes = 4 * 32 * 33 * 4;  // per walker warp: 32 walkers x 32 spheres (+1 pad)
 constexpr long long kWaitBudget = 4000000000ll;  // clock cycles (~2 s) before a wait gives up
 
 // Core-matrix layout (8 rows x 16 bytes), K-major, no swizzle: element (r, k) of a
-// rows x kK BF16 operand sits at byte (r/8) SBO + (k/8) LBO + (r%8) 16 + (k%8) 2.
+// rows x K BF16 operand sits at byte (r/8) SBO + (k/8) LBO + (r%8) 16 + (k%8) 2, SBO = (K/8) 128.
 constexpr uint32_t kLBO = 128;               // to the next core matrix along K
-constexpr uint32_t kSBO = (kK / 8) * 128;    // to the next group of 8 rows
 
 // tcgen05 instruction descriptor, kind::f16: D = F32 (bits 4-5), A = B = BF16 (7-9, 10-12),
 // both K-major (15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
@@ -64,10 +73,10 @@ constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTi
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo) {
     uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)((kLBO >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((kSBO >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;  // descriptor version of tcgen05; base offset 0, no swizzle
     return d;
 }
@@ -94,8 +103,8 @@ __device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
 }
 
 struct Shared {
-    uint64_t full[kStages];
-    uint64_t empty[kStages];
+    uint64_t full[kMaxStages];
+    uint64_t empty[kMaxStages];
     uint64_t tfull[2];
     uint64_t tempty[2];
     uint64_t a_ready;
@@ -131,12 +140,12 @@ __device__ __forceinline__ bool warp_wait_bar(Shared &S, uint64_t *b, uint32_t p
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-// One centre tile (kTileBytes, already in the core-matrix layout) by a bulk copy; both
-// addresses are 16-byte aligned (tile offsets are multiples of 4 KB).
-__device__ __forceinline__ void bulk_load_tile(uint32_t dst, const void *src, uint64_t *bar) {
+// One centre tile (already in the core-matrix layout) by a bulk copy; both addresses are
+// 16-byte aligned (tile sizes are multiples of 2 KB).
+__device__ __forceinline__ void bulk_load_tile(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"((uint64_t)src), "r"(kTileBytes), "r"(su32(bar))
+        "l"((uint64_t)src), "r"(bytes), "r"(su32(bar))
         : "memory");
 }
 
@@ -209,6 +218,8 @@ __device__ __forceinline__ float min32(const float *v) {
 // Writes this walker's A row (BF16 split of x; zeros for an idle lane).
 template <int D>
 __device__ __forceinline__ void write_row(unsigned char *A, int r, const float (&x)[D], bool active) {
+    constexpr int kK = contraction_k(D);
+    constexpr uint32_t kSBO = Geo<kK>::kSBO;
     __nv_bfloat16 row[kK];
 #pragma unroll
     for (int k = 0; k < kK; ++k) row[k] = __float2bfloat16_rn(0.f);
@@ -233,6 +244,10 @@ __device__ __forceinline__ void write_row(unsigned char *A, int r, const float (
 
 template <int D, bool GRAD>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __grid_constant__ SphereLaunch L) {
+    using G = Geo<contraction_k(D)>;
+    constexpr int kK = G::kK;
+    constexpr uint32_t kTileBytes = G::kTileBytes, kABytes = G::kABytes, kSBO = G::kSBO;
+    constexpr int kStages = G::kStages, kAhead = G::kAhead;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ Shared S;
     __shared__ SphereProblem SP;  // the problem the CTA's walkers are on
@@ -308,7 +323,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                         !wait_bar(S, &S.empty[s], (uint32_t)((g_load / kStages - 1) & 1), L.status))
                         return false;
                     mbar_expect_tx(&S.full[s], kTileBytes);
-                    bulk_load_tile(su32(Bst + s * kTileBytes), tiles + (size_t)t_load * kTileBytes, &S.full[s]);
+                    bulk_load_tile(su32(Bst + s * kTileBytes), tiles + (size_t)t_load * kTileBytes, kTileBytes,
+                                   &S.full[s]);
                     ++g_load;
                     ++t_load;
                     return true;
@@ -326,8 +342,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                     const uint32_t b_addr = su32(Bst + s * kTileBytes);
 #pragma unroll
                     for (int kk = 0; kk < kK / 16; ++kk)
-                        mma_bf16(tmem + b * kTileN, smem_desc(a_addr + kk * 2 * kLBO), smem_desc(b_addr + kk * 2 * kLBO),
-                                 kk > 0);
+                        mma_bf16(tmem + b * kTileN, smem_desc(a_addr + kk * 2 * kLBO, kSBO),
+                                 smem_desc(b_addr + kk * 2 * kLBO, kSBO), kk > 0);
                     mma_commit(&S.tfull[b]);
                     mma_commit(&S.empty[s]);
                     ++g_mma;
@@ -677,9 +693,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
 
 // At least 48 KB: shared memory then also caps the residency at kCtasPerSm CTAs per SM, so the
 // CTAs of an SM never ask for more than the 512 TMEM columns it has.
-size_t smem_bytes() {
-    return std::max<size_t>(48 * 1024, 1024 + kABytes + (size_t)kStages * kTileBytes + kTransposeBytes);
+template <int K>
+size_t smem_bytes_k() {
+    using G = Geo<K>;
+    return std::max<size_t>(48 * 1024, 1024 + G::kABytes + (size_t)G::kStages * G::kTileBytes + kTransposeBytes);
 }
+size_t smem_bytes(int d) { return contraction_k(d) == 32 ? smem_bytes_k<32>() : smem_bytes_k<48>(); }
 
 }  // namespace pc
 
@@ -697,10 +716,12 @@ static inline float bf16_value(uint16_t b) {
 }
 
 cudaError_t pointcloud_prepare(const double *pts, const double *radii, int64_t M, int d, PointCloudDev *out) {
-    if (d < 2 || 3 * d + 2 > pc::kK) return cudaErrorInvalidValue;
+    if (d < 2 || d > kPointCloudMaxD) return cudaErrorInvalidValue;
+    const int K = pc::contraction_k(d);
+    const uint32_t tile_bytes = (uint32_t)pc::kTileN * K * 2, sbo = (uint32_t)(K / 8) * 128;
     const int64_t n_tiles = (M + pc::kTileN - 1) / pc::kTileN;
     const int64_t Mp = n_tiles * pc::kTileN;
-    std::vector<uint16_t> hb((size_t)n_tiles * pc::kTileBytes / 2, 0);
+    std::vector<uint16_t> hb((size_t)n_tiles * tile_bytes / 2, 0);
     std::vector<float> hsoa((size_t)(Mp / pc::kChunk) * (d + 1) * pc::kChunk, 0.f);
     std::vector<float> hrhi((size_t)(Mp / pc::kChunk), 0.f);
     // balls in increasing radius (ties by index), points in input order
@@ -730,7 +751,7 @@ cudaError_t pointcloud_prepare(const double *pts, const double *radii, int64_t M
             nn += (double)p[j] * (double)p[j];
             if (real) pmax = std::max(pmax, std::fabs((double)p[j]));
         }
-        uint16_t row[pc::kK] = {0};
+        uint16_t row[48] = {0};
         for (int j = 0; j < d; ++j) {
             const float qv = -2.0f * p[j];
             const uint16_t qh = bf16_bits(qv);
@@ -745,9 +766,9 @@ cudaError_t pointcloud_prepare(const double *pts, const double *radii, int64_t M
         row[3 * d + 1] = bf16_bits(n32 - bf16_value(nh));
         const int64_t t = i / pc::kTileN;
         const int r = (int)(i % pc::kTileN);
-        uint16_t *tile = hb.data() + (size_t)t * pc::kTileBytes / 2;
-        for (int k = 0; k < pc::kK; ++k) {
-            const uint32_t off = (r / 8) * pc::kSBO + (k / 8) * pc::kLBO + (r % 8) * 16 + (k % 8) * 2;
+        uint16_t *tile = hb.data() + (size_t)t * tile_bytes / 2;
+        for (int k = 0; k < K; ++k) {
+            const uint32_t off = (r / 8) * sbo + (k / 8) * pc::kLBO + (r % 8) * 16 + (k % 8) * 2;
             tile[off / 2] = row[k];
         }
     }
@@ -785,16 +806,17 @@ float pointcloud_delta(int d, double xabs, double pmax) {
     return (float)(2.0 * bound + 1e-6);
 }
 
-static cudaError_t configure_spheres(size_t smem) {
+static cudaError_t configure_spheres() {
     cudaError_t e = cudaSuccess;
 #define WOS_CFG(DD)                                                                                          \
     if (e == cudaSuccess)                                                                                    \
         e = cudaFuncSetAttribute(pc::sphere_kernel<DD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)smem);                                                                 \
+                                 (int)pc::smem_bytes(DD));                                                   \
     if (e == cudaSuccess)                                                                                    \
         e = cudaFuncSetAttribute(pc::sphere_kernel<DD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                 (int)smem);
+                                 (int)pc::smem_bytes(DD));
     WOS_CFG(2) WOS_CFG(3) WOS_CFG(4) WOS_CFG(5) WOS_CFG(6) WOS_CFG(7) WOS_CFG(8) WOS_CFG(9) WOS_CFG(10)
+    WOS_CFG(11) WOS_CFG(12)
 #undef WOS_CFG
     return e;
 }
@@ -805,14 +827,15 @@ cudaError_t launch_spheres(const SphereLaunch &L, int d, int grad, int grid, cud
     // the attribute is per device: remember which devices are configured
     static std::mutex mu;
     static std::vector<int> configured;
-    const size_t smem = pc::smem_bytes();
+    if (d < 2 || d > kPointCloudMaxD) return cudaErrorInvalidValue;
+    const size_t smem = pc::smem_bytes(d);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     {
         std::lock_guard<std::mutex> g(mu);
         if (std::find(configured.begin(), configured.end(), dev) == configured.end()) {
-            e = configure_spheres(smem);
+            e = configure_spheres();
             if (e != cudaSuccess) return e;
             configured.push_back(dev);
         }
@@ -827,7 +850,7 @@ cudaError_t launch_spheres(const SphereLaunch &L, int d, int grad, int grid, cud
             pc::sphere_kernel<DD, false><<<grid, pc::kThreads, smem, s>>>(L);      \
         break;
         WOS_CASE(2) WOS_CASE(3) WOS_CASE(4) WOS_CASE(5) WOS_CASE(6) WOS_CASE(7) WOS_CASE(8) WOS_CASE(9)
-        WOS_CASE(10)
+        WOS_CASE(10) WOS_CASE(11) WOS_CASE(12)
 #undef WOS_CASE
         default: return cudaErrorInvalidValue;
     }

@@ -81,7 +81,7 @@ struct wos_domain_s {
     std::vector<float2 *> tables;
     float2 *table = nullptr;
     double table_zmax = 0;
-    PointCloudDev pcd{};  // tensor-core operands of the point set (mixed precision, d <= 10)
+    PointCloudDev pcd{};  // tensor-core operands of the sphere set (point set or >= 512 balls)
     bool has_pcd = false;
     float pc_delta = 0.f;
 };

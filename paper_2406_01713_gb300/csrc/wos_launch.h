@@ -171,7 +171,7 @@ cudaError_t launch_pointcloud(const PointCloudDev &pcd, const MixedProblem &P, f
                               unsigned long long *cursor, int *status, unsigned long long *shrinks,
                               uint64_t seed, int64_t max_steps, int grad, cudaStream_t s,
                               double *radius_out = nullptr);
-constexpr int kPointCloudMaxD = 10;  // 3d + 2 BF16 columns fit the 32-wide contraction
+constexpr int kPointCloudMaxD = 12;  // 3d + 2 BF16 columns fit a 32- or 48-wide contraction
 constexpr int kSphereMinBalls = 512; // ball sets at least this large run on the tensor cores
 
 }  // namespace wos

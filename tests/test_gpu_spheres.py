@@ -61,7 +61,7 @@ def gpu_radius(D, X):
     return np_(out)
 
 
-@pytest.mark.parametrize("d,B", [(3, 4096), (7, 1000), (10, 600)])
+@pytest.mark.parametrize("d,B", [(3, 4096), (7, 1000), (10, 600), (12, 800)])
 def test_radius_bound_is_safe_and_tight(d, B):
     dom, X, rng = ball_problem(d, B, 4.0, 11 + d, 2000)
     D = W.Domain(dom)
@@ -82,7 +82,7 @@ def test_radius_bound_is_safe_and_tight(d, B):
     assert np.mean(rel < 0.5) > 0.99
 
 
-@pytest.mark.parametrize("d,B", [(3, 2048), (6, 512)])
+@pytest.mark.parametrize("d,B", [(3, 2048), (6, 512), (11, 600)])
 def test_walks_match_oracle_and_cuda_core_screen(d, B):
     dom, X, _ = ball_problem(d, B, 9.0, 5 + d, 12)
     D = W.Domain(dom)
@@ -120,7 +120,7 @@ def test_large_problem_exact_solution():
 def test_batch_mixes_tensor_and_cuda_core_problems():
     """A batch with large ball sets (tensor-core sphere walker, one launch per dimension), small
     ones (CUDA-core walker) and a point set, in one graph: every problem matches the oracle."""
-    specs = [(3, 2048, 4.0), (5, 16, 9.0), (5, 700, 1.0), (7, 64, 0.0), (8, 1024, 16.0), (3, 600, 25.0)]
+    specs = [(3, 2048, 4.0), (5, 16, 9.0), (5, 700, 1.0), (7, 64, 0.0), (8, 1024, 16.0), (3, 600, 25.0), (12, 900, 9.0)]
     probs, refs, base, seed = [], [], 0, 11
     for i, (d, B, sigma) in enumerate(specs):
         dom, X, _ = ball_problem(d, B, sigma, 100 + i, 6)
