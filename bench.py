@@ -82,19 +82,21 @@ def aggregate_over_ranks(seconds, units, world, device="cpu"):
 KERNEL_SOURCES = ["paper_2406_01713_gb300/csrc/walk_mixed.cuh", "paper_2406_01713_gb300/csrc/wos_device.cuh",
                   "paper_2406_01713_gb300/csrc/wos_launch.h"]
 TRAFFIC_PROFILE = "profiles/walk_mixed_batched_traffic.txt"
+SPHERE_SOURCES = ["paper_2406_01713_gb300/csrc/pointcloud.cu"] + KERNEL_SOURCES
+SPHERE_TRAFFIC_PROFILE = "profiles/sphere_kernel_batched_traffic.txt"
 
 
-def measured_traffic():
-    """DRAM bytes per launch of the batched walker from the committed ncu summary, or None when
-    the kernel sources changed since that capture."""
+def measured_traffic(profile=TRAFFIC_PROFILE, sources=KERNEL_SOURCES):
+    """DRAM bytes (read + write) from a committed ncu summary, or None when the kernel sources
+    changed since that capture."""
     import hashlib
 
     try:
         h = hashlib.sha256()
-        for f in KERNEL_SOURCES:
+        for f in sources:
             h.update(open(os.path.join(ROOT, f), "rb").read())
         vals = {}
-        for line in open(os.path.join(ROOT, TRAFFIC_PROFILE)):
+        for line in open(os.path.join(ROOT, profile)):
             if line.startswith("#") or not line.strip():
                 continue
             k, v = line.split()
@@ -429,8 +431,10 @@ def kernel_rooflines(W, doms, probs, seed, config, cv, peaks, sms, sm_max, flush
             peak = peaks.get("bf16_tflops_sustained") or 1700.0
             r = {"bound": "tensor", "peak": peak, "peak_note": "measured sustained dense BF16 (cuBLAS), "
                  "MEASURED_PEAKS.json", "kernel": "sphere_kernel<d, true> (tensor-core sphere-set walker, one "
-                 "launch per dimension)", "traffic": None,
-                 "traffic_note": "not captured for this kernel; its tiles and sums are L2-resident"}
+                 "launch per dimension)", "traffic": measured_traffic(SPHERE_TRAFFIC_PROFILE, SPHERE_SOURCES),
+                 "traffic_note": "ncu dram__bytes_read+write summed over the per-dimension launches of one "
+                                 "batch run (profiles/sphere_kernel_batched_traffic.txt); tiles and sums are "
+                                 "L2-resident"}
         achieved = fl / (ms / 1e3) / 1e12
         r.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / r["peak"], "ms": ms,
                   "flops_per_launch": fl, "problems": len(idx)})
