@@ -479,31 +479,25 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                 {
                     float v[kTileN];
                     tmem_ld64(trow + b * kTileN, v);
+                    // the accumulator buffer is free as soon as its columns are in registers
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&S.tempty[b]);
 #pragma unroll
                     for (int c = 0; c < kTileN / kChunk; ++c) cmin[c] = min32(v + kChunk * c);
                 }
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&S.tempty[b]);
 #pragma unroll
                 for (int c = 0; c < kTileN / kChunk; ++c) {
                     const int id = t * (kTileN / kChunk) + c;
                     const float cs = cmin[c] + xxd;
                     const float cm = (cs > 0.f ? sqrtf(cs) : 0.f) - rhi[c];
-                    if (cm < m2) {
-                        m3 = m2;
-                        if (cm < m1) {
-                            m2 = m1;
-                            c2 = c1;
-                            m1 = cm;
-                            c1 = id;
-                        } else {
-                            m2 = cm;
-                            c2 = id;
-                        }
-                    } else {
-                        m3 = fminf(m3, cm);
-                    }
+                    // best, second and third bound; select form, no divergent branches
+                    const bool lt1 = cm < m1, lt2 = cm < m2;
+                    m3 = lt2 ? m2 : fminf(m3, cm);
+                    m2 = lt1 ? m1 : (lt2 ? cm : m2);
+                    c2 = lt1 ? c1 : (lt2 ? id : c2);
+                    m1 = lt1 ? cm : m1;
+                    c1 = lt1 ? id : c1;
                 }
             }
             if (!ok) {
