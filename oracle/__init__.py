@@ -59,6 +59,9 @@ class _Domain(ctypes.Structure):
         ("n_exp", ctypes.c_int32),
         ("exp_w", ctypes.POINTER(ctypes.c_double)),
         ("exp_a", ctypes.POINTER(ctypes.c_double)),
+        ("has_source", ctypes.c_int32),
+        ("source_z", ctypes.c_double * MAXD),
+        ("source_q", ctypes.c_double),
     ]
 
 
@@ -69,6 +72,7 @@ class _Options(ctypes.Structure):
         ("grad", ctypes.c_int32),
         ("laplace_factor", ctypes.c_int32),
         ("control_variate", ctypes.c_int32),
+        ("plant_free_space_source_grad", ctypes.c_int32),
     ]
 
 
@@ -84,6 +88,7 @@ class _WalkOut(ctypes.Structure):
         ("dsigma", ctypes.c_double),
         ("dw", ctypes.c_double * MAXEXP),
         ("gv0", ctypes.c_double * MAXD),
+        ("gsrc", ctypes.c_double * MAXD),
     ]
 
 
@@ -108,6 +113,10 @@ def lib():
             L.or_log_C.restype = ctypes.c_double
             L.or_dsigma_log_C.argtypes = [ctypes.c_double] * 3
             L.or_dsigma_log_C.restype = ctypes.c_double
+            L.or_bessel_K.argtypes = [ctypes.c_double, ctypes.c_double]
+            L.or_bessel_K.restype = ctypes.c_double
+            L.or_ball_green.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_int, _PD, _PD]
             L.or_distance.argtypes = [ctypes.POINTER(_Domain), _PD, _PI32, _PI64, _PD]
             L.or_distance.restype = ctypes.c_double
             L.or_walk.argtypes = [ctypes.POINTER(_Domain), _PD, ctypes.c_uint64, ctypes.c_double,
@@ -179,12 +188,17 @@ class Domain:
             s.n_exp = ea.shape[0]
             s.exp_a = _ptr(ea)
             s.exp_w = _ptr(arr("exp_w", (-1,)))
+        if dom.get("source_z") is not None:
+            s.has_source = 1
+            s.source_z[:d] = list(np.asarray(dom["source_z"], float))
+            s.source_q = float(dom.get("source_q", 1.0))
         self.n_exp = int(s.n_exp)
         self.s = s
 
 
-def _opts(seed, max_steps, grad, laplace_factor, control_variate=False):
+def _opts(seed, max_steps, grad, laplace_factor, control_variate=False, plant_free_space_source_grad=False):
     o = _Options()
+    o.plant_free_space_source_grad = int(bool(plant_free_space_source_grad))
     o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     o.max_steps = int(max_steps)
     o.grad = int(bool(grad))
@@ -225,6 +239,19 @@ def dsigma_log_C(nu, R, sigma):
     return lib().or_dsigma_log_C(float(nu), float(R), float(sigma))
 
 
+def bessel_K(nu, x):
+    return lib().or_bessel_K(float(nu), float(x))
+
+
+def ball_green(d, sigma, r, R, free_space=False):
+    """(G, F): the ball's Green's function between its centre and a point at distance r, and
+    the factor F with grad_x G_B = F (y - x)/r at the centre."""
+    G, F = ctypes.c_double(), ctypes.c_double()
+    lib().or_ball_green(int(d), float(sigma), float(r), float(R), int(bool(free_space)), ctypes.byref(G),
+                        ctypes.byref(F))
+    return G.value, F.value
+
+
 def distance(dom, x):
     D = dom if isinstance(dom, Domain) else Domain(dom)
     x = np.ascontiguousarray(np.asarray(x, float))
@@ -246,12 +273,13 @@ def walk(dom, x0, walk_index, eps, sigma, seed, max_steps=10000, grad=False, lap
         "term": o.term, "jumps": o.jumps, "capped": o.capped, "outside": o.outside,
         "comp_kind": o.comp_kind, "comp_index": o.comp_index,
         "grad": np.array(o.grad[:D.d]), "dsigma": o.dsigma, "dw": np.array(o.dw[:D.n_exp]),
-        "gv0": np.array(o.gv0[:D.d]),
+        "gv0": np.array(o.gv0[:D.d]), "gsrc": np.array(o.gsrc[:D.d]),
     }
 
 
 def solve(dom, X, n_walks, eps, sigma, seed, walk_offset=0, max_steps=10000, grad=False,
-          laplace_factor=False, threads=None, per_walk=False, control_variate=False):
+          laplace_factor=False, threads=None, per_walk=False, control_variate=False,
+          plant_free_space_source_grad=False):
     """Per-query estimates. Returns a dict of numpy arrays (u, u_se, grad, grad_se,
     du_dsigma, du_dw, walk_steps, capped, outside; with per_walk also walk_term,
     walk_jumps, walk_grad, walk_dsigma). control_variate (with grad): grad and grad_se are
@@ -272,7 +300,7 @@ def solve(dom, X, n_walks, eps, sigma, seed, walk_offset=0, max_steps=10000, gra
     if per_walk:
         pw = {"walk_term": np.zeros((Q, N)), "walk_jumps": np.zeros((Q, N), np.int64),
               "walk_grad": np.zeros((Q, N, d)), "walk_dsigma": np.zeros((Q, N))}
-    opt = _opts(seed, max_steps, grad, laplace_factor, control_variate)
+    opt = _opts(seed, max_steps, grad, laplace_factor, control_variate, plant_free_space_source_grad)
     rc = lib().or_solve(
         ctypes.byref(D.s), _ptr(X), Q, N, int(walk_offset), float(eps), float(sigma), ctypes.byref(opt),
         int(threads), _ptr(out["u"]), _ptr(out["u_se"]), _ptr(out["grad"]), _ptr(out["grad_se"]),

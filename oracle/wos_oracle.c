@@ -22,6 +22,17 @@
  *       sample mean of the t_w. E[v] = 0 makes it unbiased for every N >= 2 (G times the sample
  *       covariance of t and v). Computed here by its definition, in two passes over stored
  *       per-walk values.
+ *   Impulse source (Sec. IV-A estimator with a source term; Sec. VI and VII: a unit impulse at
+ *       the goal): for Laplace(u) - sigma u = -q delta_z, each step whose ball B(x_k, R_k)
+ *       contains z adds q G_B(x_k, z) times the product of the C(R_i), i < k, where G_B is the
+ *       Green's function of the ball with zero boundary values, evaluated between its centre and
+ *       z; the first-sphere gradient adds q grad_x G_B(x_0, z). With r = |z - x|, k = sqrt(sigma),
+ *       nu = d/2 - 1 and c0 = k^nu / (2 pi)^(d/2):
+ *         G_B = c0 r^-nu [K_nu(k r) - K_nu(k R) I_nu(k r) / I_nu(k R)],
+ *         grad_x G_B = (z - x)/r c0 k r^-nu [K_nu+1(k r) - K_nu+1(k R) I_nu+1(k r) / I_nu+1(k R)],
+ *       and at sigma = 0: G_B = (r^(2-d) - R^(2-d)) / ((d-2) |S^(d-1)|) (ln(R/r)/(2 pi) for d = 2),
+ *       grad_x G_B = (z - x)/|S^(d-1)| (r^-d - R^-d). K_nu from its integral
+ *       int_0^inf exp(-x cosh t) cosh(nu t) dt (DLMF 10.32.9) by the trapezoidal rule.
  *   Closest boundary point xbar (Fig. 2): g is read at the projection of x_k on the nearest
  *       boundary component.
  *   Planner (Sec. III screened-harmonic paths; Sec. VII adaptive step):
@@ -47,6 +58,7 @@
 #include <string.h>
 
 #define OR_MAXD 16
+#define OR_PI 3.14159265358979323846
 #define OR_MAXEXP 16
 #define OR_CHUNK 256 /* walks per partial sum; fixed so results do not depend on threads */
 
@@ -75,6 +87,9 @@ typedef struct {
     int32_t n_exp;        /* >0: g(x) = sum_k w_k exp(a_k . x) on the whole boundary */
     const double *exp_w;  /* n_exp */
     const double *exp_a;  /* n_exp x d */
+    int32_t has_source;   /* 1: impulse source of strength source_q at source_z */
+    double source_z[OR_MAXD];
+    double source_q;
 } or_domain;
 
 typedef struct {
@@ -83,6 +98,7 @@ typedef struct {
     int32_t grad;           /* 1: gradient walks (the first sphere is always taken) */
     int32_t laplace_factor; /* 1: the paper's printed factor d/R0 instead of alpha(R0) */
     int32_t control_variate; /* 1 (with grad): the control-variate gradient of or_solve */
+    int32_t plant_free_space_source_grad; /* test only: drop the ball's image term in grad G_B */
 } or_options;
 
 typedef struct {
@@ -96,6 +112,7 @@ typedef struct {
     double dsigma;
     double dw[OR_MAXEXP];
     double gv0[OR_MAXD]; /* G v0 = alpha(R0)/C(R0) times the first direction, if k > 0; else 0 */
+    double gsrc[OR_MAXD]; /* source part of the gradient, q grad_x G_B(x0, z) (0 without a source) */
 } or_walk_out;
 
 /* ------------------------------------------------------------------------- */
@@ -187,6 +204,48 @@ double or_series_S(double mu, double z)
 
 /* log C_nu(z), C_nu(z) = (z/2)^nu / (Gamma(nu+1) I_nu(z)) = 1 / S_nu(z). Valid for z < ~700. */
 double or_log_C(double nu, double z) { return -log(or_series_S(nu, z)); }
+
+/* K_nu(x), x > 0: the integral int_0^inf exp(-x cosh t) cosh(nu t) dt (DLMF 10.32.9) by the
+ * trapezoidal rule. The integrand is even and analytic in the strip |Im t| < pi/2; relative to
+ * its size on the real line it grows like exp(x y^2 / 2) at height y, so the rule's relative
+ * error is about exp(-2 pi^2 / (h^2 x)): a step min(1/8, 0.6/sqrt(x)) keeps it below 1e-23.
+ * The sum stops once the terms are negligible. */
+double or_bessel_K(double nu, double x)
+{
+    const double h = x > 23.04 ? 0.6 / sqrt(x) : 0.125;
+    double sum = 0.5 * exp(-x);
+    for (int i = 1; i < 1000000; ++i) {
+        const double t = h * (double)i;
+        const double c = x * cosh(t);
+        const double term = 0.5 * (exp(nu * t - c) + exp(-nu * t - c));
+        sum += term;
+        if (c - nu * t > 50.0 && term < 1e-20 * sum) break;
+    }
+    return h * sum;
+}
+
+/* Ball Green's function (zero boundary values on the sphere of radius R) between the centre
+ * and a point at distance r, 0 < r < R, for Laplace(u) - sigma u = -delta; *F is the factor
+ * with grad_x G_B(x, y) = F (y - x) / r at the centre x. free_space: drop the image part of F
+ * (a planted mistake for the tests). */
+void or_ball_green(int d, double sigma, double r, double R, int free_space, double *G, double *F)
+{
+    const double nu = 0.5 * d - 1.0;
+    const double omega = 2.0 * pow(OR_PI, 0.5 * d) / tgamma(0.5 * d); /* |S^(d-1)| */
+    if (sigma == 0.0) {
+        *G = d == 2 ? log(R / r) / (2.0 * OR_PI) : (pow(r, 2.0 - d) - pow(R, 2.0 - d)) / ((d - 2.0) * omega);
+        *F = (pow(r, 1.0 - d) - (free_space ? 0.0 : r * pow(R, -(double)d))) / omega;
+        return;
+    }
+    const double k = sqrt(sigma);
+    const double c0 = pow(k, nu) / pow(2.0 * OR_PI, 0.5 * d);
+    /* I_mu(k r) / I_mu(k R) = (r/R)^mu S_mu(k r) / S_mu(k R) (DLMF 10.25.2) */
+    const double ratio0 = pow(r / R, nu) * or_series_S(nu, k * r) / or_series_S(nu, k * R);
+    const double ratio1 = pow(r / R, nu + 1.0) * or_series_S(nu + 1.0, k * r) / or_series_S(nu + 1.0, k * R);
+    *G = c0 * pow(r, -nu) * (or_bessel_K(nu, k * r) - or_bessel_K(nu, k * R) * ratio0);
+    *F = c0 * k * pow(r, -nu) *
+         (or_bessel_K(nu + 1.0, k * r) - (free_space ? 0.0 : or_bessel_K(nu + 1.0, k * R) * ratio1));
+}
 
 /* d/dsigma log C_nu(R sqrt(sigma)) = -(R^2 / (2d)) S_{nu+1}(z) / S_nu(z), d = 2 nu + 2. */
 double or_dsigma_log_C(double nu, double R, double sigma)
@@ -294,6 +353,7 @@ void or_walk(const or_domain *D, const double *x0, uint64_t walk, double eps, do
     const double sq = sqrt(sigma);
     double x[OR_MAXD], xbar[OR_MAXD], v[OR_MAXD], v0[OR_MAXD];
     double logw = 0.0, dsig = 0.0, R0 = 0.0, z0 = 0.0, logC0 = 0.0;
+    double src = 0.0, src0 = 0.0; /* source contributions: all steps, and step 0 alone */
     int64_t k = 0;
     int32_t kind = -1;
     int64_t index = -1;
@@ -314,7 +374,7 @@ void or_walk(const or_domain *D, const double *x0, uint64_t walk, double eps, do
             double dw[OR_MAXEXP];
             double g = boundary_g(D, kind, xbar, dw);
             double w = exp(logw);
-            out->term = g * w;
+            out->term = g * w + src;
             for (int q = 0; q < D->n_exp; ++q) out->dw[q] = w * dw[q];
             break;
         }
@@ -322,6 +382,20 @@ void or_walk(const or_domain *D, const double *x0, uint64_t walk, double eps, do
             out->capped = 1;
             out->term = 0.0;
             break;
+        }
+        if (D->has_source) {
+            /* the ball B(x_k, R) contains the source: q G_B(x_k, z) times the weight so far */
+            const double r = norm_diff(d, x, D->source_z);
+            if (r > 0.0 && r < R) {
+                double G, F;
+                or_ball_green(d, sigma, r, R, opt->plant_free_space_source_grad, &G, &F);
+                const double c = D->source_q * exp(logw) * G;
+                src += c;
+                if (k == 0) {
+                    src0 = c;
+                    for (int j = 0; j < d; ++j) out->gsrc[j] = D->source_q * F * (D->source_z[j] - x[j]) / r;
+                }
+            }
         }
         or_direction(opt->seed, walk, (uint32_t)k, d, v);
         double z = R * sq;
@@ -342,17 +416,17 @@ void or_walk(const or_domain *D, const double *x0, uint64_t walk, double eps, do
     out->jumps = k;
     out->comp_kind = kind;
     out->comp_index = index;
-    out->dsigma = out->term * dsig;
+    /* d/dsigma of the source part is not estimated: NaN marks it */
+    out->dsigma = D->has_source ? NAN : out->term * dsig;
     if (k > 0) {
         /* u^(x_1) = term / C(R0);  alpha(R0) = (d/R0) C_{nu+1}(z0);  G = alpha(R0) / C(R0) */
         double factor = opt->laplace_factor ? (double)d / R0
                                             : ((double)d / R0) / or_series_S(nu + 1.0, z0);
         double G = factor * exp(-logC0);
         for (int j = 0; j < d; ++j) out->gv0[j] = G * v0[j];
-        if (!out->capped) {
-            double u1 = out->term * exp(-logC0);
-            for (int j = 0; j < d; ++j) out->grad[j] = factor * u1 * v0[j];
-        }
+        /* u^(x_1) C(R0) = the walk's value without its step-0 source part */
+        double u1 = out->capped ? 0.0 : (out->term - src0) * exp(-logC0);
+        for (int j = 0; j < d; ++j) out->grad[j] = factor * u1 * v0[j] + out->gsrc[j];
     }
 }
 
@@ -375,6 +449,7 @@ typedef struct {
     double *walk_dsigma;
     double *cv_t;   /* control variate: Q x N walk values and Q x N x d values of G v0 */
     double *cv_gv0;
+    double *cv_gsrc; /* Q x d: the source part of the gradient (the same for every walk of a query) */
     int64_t next; /* work cursor */
     pthread_mutex_t lock;
 } solve_job;
@@ -402,6 +477,7 @@ static void run_unit(solve_job *J, int64_t unit)
         if (J->cv_t) {
             J->cv_t[flat] = o.term;
             for (int j = 0; j < d; ++j) J->cv_gv0[flat * d + j] = o.gv0[j];
+            for (int j = 0; j < d; ++j) J->cv_gsrc[q * d + j] = o.gsrc[j];
         }
         /* fields: [sum u, sum u^2, sum dsigma, grad[d], grad^2[d], dw[K]] */
         P[0] += o.term;
@@ -479,12 +555,14 @@ int or_solve(const or_domain *D, const double *X, int64_t Q, int64_t N, int64_t 
     if (cv) {
         J.cv_t = (double *)malloc(sizeof(double) * (size_t)(Q * N + 1));
         J.cv_gv0 = (double *)malloc(sizeof(double) * (size_t)(Q * N * d + 1));
+        J.cv_gsrc = (double *)calloc((size_t)(Q * d + 1), sizeof(double));
     }
-    if (!J.partial || !J.ipartial || (cv && (!J.cv_t || !J.cv_gv0))) {
+    if (!J.partial || !J.ipartial || (cv && (!J.cv_t || !J.cv_gv0 || !J.cv_gsrc))) {
         free(J.partial);
         free(J.ipartial);
         free(J.cv_t);
         free(J.cv_gv0);
+        free(J.cv_gsrc);
         return -1;
     }
     pthread_mutex_init(&J.lock, NULL);
@@ -533,7 +611,7 @@ int or_solve(const or_domain *D, const double *X, int64_t Q, int64_t N, int64_t 
                     ss += e * e;
                 }
                 const double var = ss / (double)(N - 1);
-                if (grad) grad[q * d + j] = I[2] ? NAN : sy / (double)(N - 1);
+                if (grad) grad[q * d + j] = I[2] ? NAN : sy / (double)(N - 1) + J.cv_gsrc[q * d + j];
                 if (grad_se)
                     grad_se[q * d + j] = I[2] ? NAN : ((double)N / (double)(N - 1)) * sqrt(var / (double)N);
             }
@@ -548,6 +626,7 @@ int or_solve(const or_domain *D, const double *X, int64_t Q, int64_t N, int64_t 
     free(J.ipartial);
     free(J.cv_t);
     free(J.cv_gv0);
+    free(J.cv_gsrc);
     return 0;
 }
 

@@ -412,3 +412,125 @@ def test_control_variate_exp_data_exact_and_lower_variance(oracle_mod):
     gg = a[None, :] * g[:, None]
     assert np.all(np.abs(cv["grad"] - gg) < 4.5 * cv["grad_se"] + 10 * bias[:, None])
     assert np.mean(cv["grad_se"]) < 0.5 * np.mean(plain["grad_se"])
+
+
+# --------------------------------------------------------------------------- impulse source
+# Laplace(u) - sigma u = -q delta_z, u = 0 on the boundary: each step whose ball contains z
+# adds q G_B(x_k, z) times the weight so far; the first-sphere gradient adds q grad_x G_B(x0, z).
+def _c0(d, sigma):
+    return math.sqrt(sigma) ** (d / 2 - 1) / (2 * math.pi) ** (d / 2)
+
+
+def _omega(d):
+    return 2 * math.pi ** (d / 2) / math.gamma(d / 2)
+
+
+def test_bessel_K_matches_scipy(oracle_mod):
+    worst = 0.0
+    for nu in [0, 0.5, 1, 1.5, 2, 3.5, 5, 6, 7]:
+        for x in [1e-6, 1e-3, 0.2, 1.0, 7.0, 30.0, 120.0, 400.0]:
+            a, b = oracle_mod.bessel_K(nu, x), special.kv(nu, x)
+            worst = max(worst, abs(a - b) / b)
+    assert worst < 1e-13, worst
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 7])
+def test_ball_green_function(oracle_mod, d):
+    R, sigma = 0.8, 4.0
+    k, nu = 2.0, d / 2 - 1
+    for r in [1e-3, 0.1, 0.5, 0.79]:
+        G, F = oracle_mod.ball_green(d, sigma, r, R)
+        # written with scipy's I and K (the oracle uses its own K integral and I series)
+        G_ref = _c0(d, sigma) * r ** -nu * (special.kv(nu, k * r) - special.kv(nu, k * R) * special.iv(nu, k * r)
+                                            / special.iv(nu, k * R))
+        F_ref = _c0(d, sigma) * k * r ** -nu * (special.kv(nu + 1, k * r) - special.kv(nu + 1, k * R)
+                                                * special.iv(nu + 1, k * r) / special.iv(nu + 1, k * R))
+        assert abs(G - G_ref) <= 1e-10 * abs(G_ref) + 1e-14
+        assert abs(F - F_ref) <= 1e-10 * abs(F_ref) + 1e-14
+    # zero on the sphere; unit flux out of a small sphere around the source (a unit impulse)
+    assert abs(oracle_mod.ball_green(d, sigma, R * (1 - 1e-9), R)[0]) < 1e-7
+    r, h = 1e-4, 1e-7
+    dG = (oracle_mod.ball_green(d, sigma, r + h, R)[0] - oracle_mod.ball_green(d, sigma, r - h, R)[0]) / (2 * h)
+    assert abs(-_omega(d) * r ** (d - 1) * dG - 1.0) < 1e-5
+    # sigma -> 0 is the Laplace form (closed, separate code path)
+    for r in [0.05, 0.4]:
+        G0, F0 = oracle_mod.ball_green(d, 0.0, r, R)
+        Gs, Fs = oracle_mod.ball_green(d, 1e-9, r, R)
+        assert abs(G0 - Gs) <= 1e-6 * abs(G0) and abs(F0 - Fs) <= 1e-6 * abs(F0)
+
+
+def test_ball_green_three_dimensional_closed_form(oracle_mod):
+    # d = 3: G = (e^{-kr} - e^{-kR} sinh(kr)/sinh(kR)) / (4 pi r); Laplace F = (r^-2 - r R^-3)/(4 pi)
+    R, k = 1.3, 1.7
+    for r in [0.01, 0.3, 1.0]:
+        G, _ = oracle_mod.ball_green(3, k * k, r, R)
+        want = (math.exp(-k * r) - math.exp(-k * R) * math.sinh(k * r) / math.sinh(k * R)) / (4 * math.pi * r)
+        assert abs(G - want) < 1e-12 * want
+        _, F0 = oracle_mod.ball_green(3, 0.0, r, R)
+        assert abs(F0 - (r ** -2 - r / R ** 3) / (4 * math.pi)) < 1e-12 * F0
+
+
+def _centred_source_solution(d, sigma, R, x):
+    """u = G_Omega(x, 0) for Omega = B(0, R) and its gradient (radial)."""
+    r = np.linalg.norm(x)
+    nu = d / 2 - 1
+    if sigma == 0.0:
+        u = math.log(R / r) / (2 * math.pi) if d == 2 else (r ** (2 - d) - R ** (2 - d)) / ((d - 2) * _omega(d))
+        du = -r ** (1 - d) / _omega(d)
+    else:
+        k = math.sqrt(sigma)
+        c0 = _c0(d, sigma)
+        u = c0 * r ** -nu * (special.kv(nu, k * r) - special.kv(nu, k * R) * special.iv(nu, k * r) / special.iv(nu, k * R))
+        du = -c0 * k * r ** -nu * (special.kv(nu + 1, k * r) + special.kv(nu, k * R) * special.iv(nu + 1, k * r)
+                                    / special.iv(nu, k * R))
+    return u, du * x / r
+
+
+def _source_case(oracle_mod, d, sigma, planted=False, control_variate=False):
+    R = 1.0
+    dom = {"d": d, "outer_c": np.zeros(d), "outer_r": R, "source_z": np.zeros(d), "source_q": 1.0}
+    rng = np.random.default_rng(40 + d)
+    X = []
+    for rad in [0.3, 0.6]:
+        v = rng.standard_normal(d)
+        X.append(rad * v / np.linalg.norm(v))
+    X = np.array(X)
+    res = oracle_mod.solve(dom, X, 20000, 1e-6, sigma, seed=7 + d, grad=True, control_variate=control_variate,
+                           plant_free_space_source_grad=planted)
+    ok_u, ok_g = True, True
+    for q in range(len(X)):
+        u, g = _centred_source_solution(d, sigma, R, X[q])
+        ok_u &= abs(res["u"][q] - u) < 4.5 * res["u_se"][q] + 1e-4 * abs(u)
+        ok_g &= bool(np.all(np.abs(res["grad"][q] - g) < 4.5 * res["grad_se"][q] + 1e-3 * np.abs(g).max()))
+    return ok_u, ok_g, res
+
+
+@pytest.mark.parametrize("d,sigma", [(2, 0.0), (2, 4.0), (3, 0.0), (3, 9.0)])
+def test_centred_impulse_source_in_a_ball(oracle_mod, d, sigma):
+    ok_u, ok_g, res = _source_case(oracle_mod, d, sigma)
+    assert ok_u and ok_g
+    assert np.all(np.isnan(res["du_dsigma"]))  # not estimated with a source
+    ok_u, ok_g, _ = _source_case(oracle_mod, d, sigma, control_variate=True)
+    assert ok_u and ok_g
+
+
+def test_planted_free_space_source_gradient_is_rejected(oracle_mod):
+    # dropping the ball's image term from grad_x G_B biases the gradient wherever the source is
+    # inside the first sphere
+    ok_u, ok_g, _ = _source_case(oracle_mod, 3, 9.0, planted=True)
+    assert ok_u and not ok_g
+
+
+def test_off_centre_source_kelvin_image(oracle_mod):
+    # sigma = 0, Omega = B(0, 1), source at z: u = (1/|x - z| - 1/(|z| |x - z*|)) / (4 pi), z* = z/|z|^2
+    z = np.array([0.4, 0.0, 0.0])
+    zs = z / np.dot(z, z)
+    dom = {"d": 3, "outer_c": np.zeros(3), "outer_r": 1.0, "source_z": z}
+    X = np.array([[-0.3, 0.2, 0.0], [0.6, 0.3, 0.1], [0.1, -0.5, 0.4]])
+    res = oracle_mod.solve(dom, X, 20000, 1e-6, 0.0, seed=3, grad=True)
+    for q, x in enumerate(X):
+        a, b = x - z, x - zs
+        u = (1 / np.linalg.norm(a) - 1 / (np.linalg.norm(z) * np.linalg.norm(b))) / (4 * math.pi)
+        g = (-a / np.linalg.norm(a) ** 3 + b / (np.linalg.norm(z) * np.linalg.norm(b) ** 3)) / (4 * math.pi)
+        assert abs(res["u"][q] - u) < 4.5 * res["u_se"][q] + 1e-4 * abs(u)
+        assert np.all(np.abs(res["grad"][q] - g) < 4.5 * res["grad_se"][q] + 1e-3 * np.abs(g).max())
