@@ -541,6 +541,23 @@ def secondary(W, synth):
     f = flags.cpu().numpy()
     out["planning_2d"] = {"path_ms": 1e3 * dt, "ms_per_planner_step": 1e3 * dt / w["n_steps"],
                           "reached_goal_at_step": int(np.argmax(f == 1)) if (f == 1).any() else None}
+    # the paper's two-disc environment with a unit impulse at the goal (Sec. VI): r_o = 10,
+    # k_r = 0.3, c = sigma = 1, eps = 0.01, start (-8, 0); the goal (8, 0) is this benchmark's
+    # choice (the paper shows it only in a figure). 1024 walks per planner step.
+    env = {"d": 2, "outer_c": np.zeros(2), "outer_r": 10.0, "ball_c": np.array([[0.0, 3.0], [0.0, -1.5]]),
+           "ball_r": np.array([3.0, 1.5]), "source_z": np.array([8.0, 0.0]), "source_q": 1.0}
+    dom = W.Domain(env)
+    dom.plan_path(np.array([-8.0, 0.0]), 5, 1024, 0.01, 1.0, 0.1, seed=1, control_variate=True)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    path, flags, _ = dom.plan_path(np.array([-8.0, 0.0]), 400, 1024, 0.01, 1.0, 0.1, seed=1, control_variate=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    f = flags.cpu().numpy()
+    p_end = path.cpu().numpy()[-1]
+    out["paper_environment_2d"] = {"path_ms": 1e3 * dt, "ms_per_planner_step": 1e3 * dt / 400,
+                                   "reached_goal_at_step": int(np.argmax(f == 1)) if (f == 1).any() else None,
+                                   "final_distance_to_goal": float(np.linalg.norm(p_end - env["source_z"]))}
     # differentiable d=6: forward + backward, 4096 queries x 2048 walks
     w = synth.c5()
     dom = W.Domain(w["domain"])

@@ -125,7 +125,22 @@ typedef struct {
     int32_t n_exp;              /* 0..WOS_MAX_EXP exponential data terms */
     const double *exp_w;        /* n_exp weights */
     const double *exp_a;        /* n_exp x d exponents */
+    const double *source_z;     /* d values: an impulse source at this point, or NULL for none */
+    double source_q;            /* its strength q (the paper's unit impulse at the goal: 1) */
 } wos_domain_desc;
+
+/*
+ * Impulse source (Sec. IV-A estimator with a source term; the paper's planning problems put a
+ * unit impulse at the goal, Sec. VI, VII): with source_z given, u solves
+ * Laplace(u) - sigma u = -q delta(x - source_z) in Omega, u = g on the boundary (g = 0 when the
+ * domain has neither a goal ball nor exponential data, the paper's zero Dirichlet condition).
+ * Each step whose largest empty ball B(x_k, R_k) contains the source adds q G_B(x_k, source_z)
+ * times the walk's weight so far, G_B the Green's function of that ball with zero boundary
+ * values (Yukawa potential minus its image part; logarithm / power laws at sigma = 0); the
+ * first-sphere gradient adds q grad_x G_B(x_0, source_z). du_dsigma is NaN for such domains
+ * (its source part is not estimated); du_dw is unaffected. Mixed precision runs these domains
+ * on the CUDA-core walker (ball sets) and rejects point sets.
+ */
 
 /* Per-call options. A NULL options pointer means {WOS_MIXED, 0, seed 0, offset 0, 10000}. */
 typedef struct {

@@ -633,7 +633,8 @@ int or_solve(const or_domain *D, const double *X, int64_t Q, int64_t N, int64_t 
 /* ------------------------------------------------------------------------- */
 /* Screened-harmonic path (Sec. III; Sec. VII adaptive step s = min(s_ub, d/2)). */
 /* Step i estimates grad u at x_i with N gradient walks, walk offset i N.      */
-/* flags[i]: 1 goal reached before step i (no move), 2 no signal (|grad| = 0,   */
+/* flags[i]: 1 goal reached before step i (no move; with an impulse source and no */
+/* goal ball: the source is closer than s_ub), 2 no signal (|grad| = 0,           */
 /* no move), 4 outside the domain (no move).                                  */
 /* Returns the number of points written (the path stops at the goal).         */
 /* ------------------------------------------------------------------------- */
@@ -656,6 +657,10 @@ int64_t or_plan_path(const or_domain *D, const double *x0, int64_t n_steps, int6
                 flags[i] = 1;
                 break;
             }
+        } else if (D->has_source && norm_diff(d, x, D->source_z) < s_ub) {
+            /* the goal is the impulse source: reached once it is within one nominal step */
+            flags[i] = 1;
+            break;
         }
         int32_t kind;
         int64_t index;

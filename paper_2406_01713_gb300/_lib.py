@@ -29,6 +29,7 @@ class DomainDesc(ctypes.Structure):
         ("n_balls", ctypes.c_int32), ("ball_c", _PD), ("ball_r", _PD),
         ("n_points", ctypes.c_int64), ("points", _PD),
         ("n_exp", ctypes.c_int32), ("exp_w", _PD), ("exp_a", _PD),
+        ("source_z", _PD), ("source_q", ctypes.c_double),
     ]
 
 

@@ -77,6 +77,7 @@ template <int D>
 struct MixedWalker {
     f32x2 x2[D];              // position as packed pairs (x_j, x_j)
     float logw, dsig, gfac0;  // gfac0 = alpha(R0) / C(R0); v0 is regenerated from its counter
+    float src, src0;          // impulse source: contributions so far, and the step-0 one
     int k;
     unsigned j;      // walk index within the problem
     long long q;     // query
@@ -348,7 +349,7 @@ template <int D, bool GRAD>
 __device__ __forceinline__ void add_walk(const MixedProblem &P, long long q, int outcome, int k,
                                          float term, float dsig, float gt, const float (&v0)[D],
                                          const float (&e)[kMaxExp], float gf) {
-    const int nf = acc_fields(D, P.n_exp, P.cv);
+    const int nf = acc_fields(D, P.n_exp, P.cv, P.src);
     double *acc = P.acc + q * nf;
     unsigned long long *cnt = P.counts + q * kCounters;
     atomicAdd(cnt + 0, 1ull);
@@ -416,7 +417,87 @@ __device__ __forceinline__ void start_walk(const MixedProblem &P, MixedWalker<D>
     W.logw = 0.f;
     W.dsig = 0.f;
     W.gfac0 = 0.f;
+    W.src = 0.f;
+    W.src0 = 0.f;
     W.k = 0;
+}
+
+// ---- impulse source: Green's function of the largest empty ball, FP32 -------------------
+// log K_nu(x) and log K_{nu+1}(x), x > 0, from int_0^inf exp(-x cosh t) cosh(mu t) dt
+// (DLMF 10.32.9) by the trapezoidal rule; step min(1/2, 1.1/sqrt(x)) keeps the relative error
+// near 1e-7, and the sum is scaled by the peak of exp(-x cosh t + (nu+1) t).
+__device__ __forceinline__ void log_bessel_K_pair_f32(float nu, float x, float &l0, float &l1) {
+    const float mu = nu + 1.f;
+    const float ts = asinhf(mu / x);
+    const float m = mu * ts - x * coshf(ts);
+    const float h = fminf(0.5f, 1.1f * rsqrtf(x));
+    float s0 = 0.f, s1 = 0.f;
+    for (int i = 0; i < 512; ++i) {
+        const float t = h * (float)i, c = x * coshf(t), w = i == 0 ? 0.5f : 1.f;
+        const float e1 = mu * t - c - m;
+        s1 += w * (expf(e1) + expf(-mu * t - c - m));
+        s0 += w * (expf(nu * t - c - m) + expf(-nu * t - c - m));
+        if (t > ts && e1 < -18.f) break;
+    }
+    l0 = m + logf(0.5f * h * s0);
+    l1 = m + logf(0.5f * h * s1);
+}
+
+// G = G_B between the centre of a ball of radius R and a point at distance r < R, and F with
+// grad_x G_B = F (y - x)/r at the centre (Laplace(u) - sigma u = -delta, zero values on the
+// sphere): c0 r^-nu [K_mu(kr) - K_mu(kR) I_mu(kr)/I_mu(kR)] for mu = nu (G) and nu + 1 (F,
+// times k), the I ratios from the weight table (log S_nu = -log C_nu; S_nu+1 / S_nu); tR is the
+// table entry at kR. Laplace forms at sigma = 0. Evaluated in log space.
+template <int D>
+__device__ __forceinline__ void source_green_f32(const MixedProblem &P, float r, float R, float2 tR, float &G,
+                                                 float &F) {
+    const float nu = 0.5f * (float)D - 1.f;
+    const float k = P.sqrt_sigma;
+    const float lr = logf(r), lR = logf(R);
+    if (k == 0.f) {
+        G = D == 2 ? (lR - lr) * (0.5f / CUDART_PI_F)
+                   : (expf((2.f - D) * lr) - expf((2.f - D) * lR)) * (P.src_inv_omega / (float)(D - 2));
+        F = (expf((1.f - D) * lr) - r * expf(-(float)D * lR)) * P.src_inv_omega;
+        return;
+    }
+    float ka0, ka1, kb0, kb1;
+    log_bessel_K_pair_f32(nu, k * r, ka0, ka1);
+    log_bessel_K_pair_f32(nu, k * R, kb0, kb1);
+    const float2 ta = table_lookup(P.table, k * r);
+    const float lSa0 = -ta.x, lSb0 = -tR.x;
+    const float lSa1 = lSa0 + logf(ta.y), lSb1 = lSb0 + logf(tR.y);
+    G = expf(P.src_lc0 - nu * lr + ka0) * (1.f - expf(kb0 - ka0 + nu * (lr - lR) + lSa0 - lSb0));
+    F = expf(P.src_lc0 + logf(k) - nu * lr + ka1) *
+        (1.f - expf(kb1 - ka1 + (nu + 1.f) * (lr - lR) + lSa1 - lSb1));
+}
+
+// The source term of one step (not inlined: walkers without a source keep their registers):
+// if the ball B(x_k, R) contains the source, add q G_B(x_k, z) times the weight so far; at
+// step 0 of a gradient walk also record that value and store the query's step-0 value and
+// source part of the gradient, q grad_x G_B(x_0, z) (every walk of the query writes the same).
+template <int D, bool GRAD>
+__device__ __noinline__ void source_step(const MixedProblem &P, MixedWalker<D> &W, float R, float2 t) {
+    float rr = 0.f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const float dz = P.source_z[i] - xj(W.x2, i);
+        rr = fmaf(dz, dz, rr);
+    }
+    const float r = sqrtf(rr);
+    if (!(r > 0.f && r < R)) return;
+    float G, F;
+    source_green_f32<D>(P, r, R, t, G, F);
+    const float c = P.source_q * expf(W.logw) * G;
+    W.src += c;
+    if (GRAD && W.k == 0) {
+        W.src0 = c;
+        if (P.src) {
+            double *sp = P.acc + W.q * acc_fields(D, P.n_exp, P.cv, 1) + src_field(D, P.n_exp, P.cv);
+            sp[0] = (double)c;
+#pragma unroll
+            for (int i = 0; i < D; ++i) sp[1 + i] = (double)(P.source_q * F * (P.source_z[i] - xj(W.x2, i)) / r);
+        }
+    }
 }
 
 template <int D, bool GRAD>
@@ -447,6 +528,7 @@ __device__ __forceinline__ void step_walker(const MixedLaunch &L, const MixedPro
         float v[D];
         direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + (long long)W.j), (uint32_t)W.k, v);
         const float2 t = table_lookup(P.table, R * P.sqrt_sigma);
+        if (P.has_source) source_step<D, GRAD>(P, W, R, t);
         if (GRAD && W.k == 0) {
             // alpha(R0) u^(x_1) = (d/R0) C_{nu+1}(z0) term / C_nu(z0) = (d/R0) term / ratio(z0)
             W.gfac0 = P.laplace ? ((float)D / R) * __expf(-t.x) : ((float)D / R) / t.y;
@@ -466,24 +548,28 @@ __device__ __forceinline__ void step_walker(const MixedLaunch &L, const MixedPro
     float e[kMaxExp];
 #pragma unroll
     for (int k = 0; k < kMaxExp; ++k) e[k] = 0.f;
-    if (outcome == 1) term = terminal_value<D>(P, geom, balls, W.x2, kind, idx, W.logw, e);
+    if (outcome == 1) term = terminal_value<D>(P, geom, balls, W.x2, kind, idx, W.logw, e) + W.src;
     const bool has_grad = GRAD && outcome == 1 && W.k > 0;
     const bool cv_walk = GRAD && P.cv && W.k > 0 && outcome != 3;  // capped walks count too
     float v0[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) v0[i] = 0.f;
     if constexpr (GRAD) {
-        if (has_grad && term != 0.f)
+        if (has_grad && (term != 0.f || W.src0 != 0.f))
             direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + (long long)W.j), 0u, v0);
     }
-    const float gt = has_grad ? W.gfac0 * term : 0.f;
+    // u^(x_1) C(R0): the walk's value without its step-0 source part
+    const float gt = has_grad ? W.gfac0 * (term - W.src0) : 0.f;
     add_walk<D, GRAD>(P, W.q, outcome, W.k, term, W.dsig, gt, v0, e, cv_walk ? W.gfac0 : 0.f);
     if (P.w_term != nullptr) P.w_term[W.j] = outcome == 3 ? (double)CUDART_NAN : (double)term;
     if (P.w_jumps != nullptr) P.w_jumps[W.j] = W.k;
-    if (P.w_dsigma != nullptr) P.w_dsigma[W.j] = (double)(term * W.dsig);
+    if (P.w_dsigma != nullptr) P.w_dsigma[W.j] = P.has_source ? (double)CUDART_NAN : (double)(term * W.dsig);
     if (P.w_grad != nullptr) {
+        // with a source, the per-query source part of the gradient (stored at step 0)
+        const double *sp = P.src ? P.acc + W.q * acc_fields(D, P.n_exp, P.cv, 1) + src_field(D, P.n_exp, P.cv) : nullptr;
 #pragma unroll
-        for (int i = 0; i < D; ++i) P.w_grad[(long long)W.j * D + i] = (double)(gt * v0[i]);
+        for (int i = 0; i < D; ++i)
+            P.w_grad[(long long)W.j * D + i] = (double)(gt * v0[i]) + (sp != nullptr ? sp[1 + i] : 0.0);
     }
     const unsigned nj = grab_walk(S);
     W.active = nj < end;

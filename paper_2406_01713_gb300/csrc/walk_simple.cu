@@ -19,6 +19,8 @@ struct WalkResult {
     T grad[D];
     T v0[D];   // first direction if the walk took its first sphere (control variate), else 0
     T G;       // alpha(R0)/C(R0) if the walk took its first sphere, else 0
+    T s0;      // impulse source: value added at step 0 (the same for every walk of the query)
+    T gsrc[D]; // impulse source: q grad_x G_B(x0, z), the source part of the gradient
     T dw[kMaxExp];
     int64_t jumps;
     int capped, outside;
@@ -47,6 +49,7 @@ __device__ void run_walk(const SimpleParams<T> &p, const double *xq, uint64_t wa
         v0[j] = T(0);
     }
     T logw = T(0), dsig = T(0), R0 = T(0), logC0 = T(0), S1_0 = T(1);
+    T src = T(0);  // impulse-source contributions of the steps so far
     int64_t k = 0;
     int kind = -1;
     int64_t idx = -1;
@@ -57,8 +60,9 @@ __device__ void run_walk(const SimpleParams<T> &p, const double *xq, uint64_t wa
 #pragma unroll
     for (int i = 0; i < kMaxExp; ++i) res.dw[i] = T(0);
 #pragma unroll
-    for (int j = 0; j < D; ++j) res.grad[j] = res.v0[j] = T(0);
+    for (int j = 0; j < D; ++j) res.grad[j] = res.v0[j] = res.gsrc[j] = T(0);
     res.G = T(0);
+    res.s0 = T(0);
     for (;;) {
         const T R = distance<T, D>(dm, x, kind, idx) - p.shrink;
         if (k == 0 && !(R > T(0))) {
@@ -70,7 +74,7 @@ __device__ void run_walk(const SimpleParams<T> &p, const double *xq, uint64_t wa
             T e[kMaxExp];
             const T g = boundary_value<T, D>(dm, x, kind, idx, e);
             const T w = exp(logw);
-            res.term = g * w;
+            res.term = g * w + src;
 #pragma unroll
             for (int i = 0; i < kMaxExp; ++i)
                 if (i < dm.n_exp) res.dw[i] = w * e[i];
@@ -80,6 +84,29 @@ __device__ void run_walk(const SimpleParams<T> &p, const double *xq, uint64_t wa
             res.capped = 1;
             res.term = T(0);
             break;
+        }
+        if (dm.has_source) {
+            // the ball B(x_k, R) contains the source: q G_B(x_k, z) times the weight so far
+            // (evaluated in FP64 in both precisions)
+            double rr = 0.0;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const double t = (double)dm.source_z[j] - (double)x[j];
+                rr += t * t;
+            }
+            const double r = sqrt(rr);
+            if (r > 0.0 && r < (double)R) {
+                double G, F;
+                source_green_f64(D, (double)p.sqrt_sigma, r, (double)R, G, F);
+                const T c = (T)((double)dm.source_q * exp((double)logw) * G);
+                src += c;
+                if (k == 0) {
+                    res.s0 = c;
+#pragma unroll
+                    for (int j = 0; j < D; ++j)
+                        res.gsrc[j] = (T)((double)dm.source_q * F * ((double)dm.source_z[j] - (double)x[j]) / r);
+                }
+            }
         }
         direction<D>(p.seed, walk, (uint32_t)k, v);
         const T z = R * p.sqrt_sigma;
@@ -100,7 +127,8 @@ __device__ void run_walk(const SimpleParams<T> &p, const double *xq, uint64_t wa
         ++k;
     }
     res.jumps = k;
-    res.dsig = res.term * dsig;
+    // d/dsigma of the source part is not estimated
+    res.dsig = dm.has_source ? (T)CUDART_NAN : res.term * dsig;
     if (k > 0) {
         const T factor = p.laplace ? T(D) / R0 : (T(D) / R0) / S1_0;
         if (p.cv) {
@@ -109,7 +137,8 @@ __device__ void run_walk(const SimpleParams<T> &p, const double *xq, uint64_t wa
             for (int j = 0; j < D; ++j) res.v0[j] = v0[j];
         }
         if (!res.capped) {
-            const T u1 = res.term * exp(-logC0);
+            // u^(x_1) C(R0): the walk's value without its step-0 source part
+            const T u1 = (res.term - res.s0) * exp(-logC0);
 #pragma unroll
             for (int j = 0; j < D; ++j) res.grad[j] = factor * u1 * v0[j];
         }
@@ -148,7 +177,7 @@ __global__ void __launch_bounds__(128) walk_simple_kernel(const SimpleParams<T> 
             if (p.w_jumps) p.w_jumps[j] = r.jumps;
             if (p.w_dsigma) p.w_dsigma[j] = (double)r.dsig;
             if (p.w_grad)
-                for (int i = 0; i < D; ++i) p.w_grad[j * D + i] = (double)r.grad[i];
+                for (int i = 0; i < D; ++i) p.w_grad[j * D + i] = (double)r.grad[i] + (double)r.gsrc[i];
         } else {
             r.outside = 0;
             r.capped = 0;
@@ -197,6 +226,14 @@ __global__ void __launch_bounds__(128) walk_simple_kernel(const SimpleParams<T> 
                 }
             }
             if (ok && r.G != T(0)) cvp[3 * D] = r.G;
+        }
+        if (p.src && ok && r.jumps > 0) {
+            // impulse source: step-0 value and gradient part, one per query (plain stores of
+            // the same values)
+            T *sp = acc + src_field(D, K, p.cv);
+            sp[0] = r.s0;
+#pragma unroll
+            for (int i = 0; i < D; ++i) sp[1 + i] = r.gsrc[i];
         }
         const unsigned long long c[4] = {active ? 1ull : 0ull,
                                          active ? (unsigned long long)(r.jumps + 1) : 0ull,

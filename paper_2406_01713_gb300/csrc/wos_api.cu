@@ -64,9 +64,10 @@ int device_sms() {
 // =====================================================================================
 struct wos_domain_s {
     int d = 0, has_box = 0, has_outer = 0, has_goal = 0, n_balls = 0, n_exp = 0;
+    int has_source = 0;
     int64_t n_points = 0;
-    double outer_r = 0, goal_r = 0;
-    std::vector<double> box_lo, box_hi, outer_c, goal_c, exp_w, exp_a, ball_r, ball_c, points;
+    double outer_r = 0, goal_r = 0, source_q = 0;
+    std::vector<double> box_lo, box_hi, outer_c, goal_c, exp_w, exp_a, ball_r, ball_c, points, source_z;
     double R_max = 0;     // upper bound of any distance to the boundary
     double shrink32 = 0;  // FP32 distance + jump error bound
     double slack32 = 0;   // FP32 ball-screen rounding bound
@@ -99,9 +100,11 @@ void layout_view(DomainView<T> &v, T *base, const wos_domain_s &D) {
     v.has_box = D.has_box;
     v.has_outer = D.has_outer;
     v.has_goal = D.has_goal;
+    v.has_source = D.has_source;
     v.n_points = M;
     v.outer_r = (T)D.outer_r;
     v.goal_r = (T)D.goal_r;
+    v.source_q = (T)D.source_q;
     v.box_lo = p; p += d;
     v.box_hi = p; p += d;
     v.outer_c = p; p += d;
@@ -111,10 +114,11 @@ void layout_view(DomainView<T> &v, T *base, const wos_domain_s &D) {
     v.ball_r = p; p += B;
     v.ball_c = p; p += B * d;
     v.points = p; p += M * d;
+    v.source_z = p; p += d;
 }
 
 int64_t view_size(const wos_domain_s &D) {
-    return 4LL * D.d + D.n_exp + (int64_t)D.n_exp * D.d + D.n_balls + (int64_t)D.n_balls * D.d +
+    return 5LL * D.d + D.n_exp + (int64_t)D.n_exp * D.d + D.n_balls + (int64_t)D.n_balls * D.d +
            D.n_points * D.d;
 }
 
@@ -136,6 +140,7 @@ std::vector<T> pack_view(const wos_domain_s &D) {
     put(D.ball_r, D.n_balls);
     put(D.ball_c, (size_t)D.n_balls * d);
     put(D.points, (size_t)D.n_points * d);
+    put(D.source_z, d);
     return h;
 }
 
@@ -245,7 +250,9 @@ wos_status ensure_table(wos_domain_t dom, double sigma, WeightTable *out) {
 // =====================================================================================
 struct FinalizeRec {
     int d, K, acc_f32;
-    int cv;  // gradient control variate sums present
+    int cv;          // gradient control variate sums present
+    int src;         // impulse-source fields present (gradient walks)
+    int has_source;  // impulse source: du/dsigma is not estimated (NaN)
     int64_t Q, N, q_begin;
     const void *acc;
     const unsigned long long *counts;
@@ -283,7 +290,7 @@ __global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
             R = a.recs + lo;
         }
         const int64_t q = t - R->q_begin;
-        const int d = R->d, K = R->K, nf = acc_fields(d, K, R->cv);
+        const int d = R->d, K = R->K, nf = acc_fields(d, K, R->cv, R->src);
         auto S = [&](int f) -> double {
             return R->acc_f32 ? (double)((const float *)R->acc)[q * nf + f]
                               : ((const double *)R->acc)[q * nf + f];
@@ -297,14 +304,19 @@ __global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
         const double nan = CUDART_NAN;
         if (R->u) R->u[q] = out ? nan : S(0) * inv;
         if (R->u_se) R->u_se[q] = out ? nan : se_mean(S(0), S(1), n);
-        if (R->du_dsigma) R->du_dsigma[q] = out ? nan : S(2) * inv;
+        if (R->du_dsigma) R->du_dsigma[q] = (out || R->has_source) ? nan : S(2) * inv;
         const bool cv = R->cv && n >= 2.0;
         const int cf = cv_field(d, K);
+        // impulse source: the gradient sums hold G (t - s0) v0; s0 and the source part of the
+        // gradient are one per query
+        const int sf = src_field(d, K, R->cv);
+        const double s0 = R->src ? S(sf) : 0.0;
         for (int i = 0; i < d; ++i) {
             double g = S(3 + i) * inv, se = se_mean(S(3 + i), S(3 + d + i), n);
-            if (cv)
-                cv_estimate(S(3 + i), S(3 + d + i), S(cf + i), S(cf + d + i), S(cf + 2 * d + i), S(cf + 3 * d), S(0),
-                            n, g, se);
+            if (cv)  // sum (t - s0) = sum t - n s0, sum (t - s0) v^2 = sum t v^2 - s0 sum v^2
+                cv_estimate(S(3 + i), S(3 + d + i), S(cf + i), S(cf + d + i) - s0 * S(cf + 2 * d + i),
+                            S(cf + 2 * d + i), S(cf + 3 * d), S(0) - n * s0, n, g, se);
+            if (R->src) g += S(sf + 1 + i);
             if (R->grad) R->grad[q * d + i] = out ? nan : g;
             if (R->grad_se) R->grad_se[q * d + i] = out ? nan : se;
         }
@@ -357,7 +369,7 @@ __device__ void cv_prepass_query(const MixedProblem &P, int64_t q, uint64_t seed
         }
     }
     if (lane == 0) {
-        double *cvp = P.acc + q * acc_fields(D, P.n_exp, 1) + cv_field(D, P.n_exp);
+        double *cvp = P.acc + q * acc_fields(D, P.n_exp, 1, P.src) + cv_field(D, P.n_exp);
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             cvp[i] = s1[i];
@@ -492,6 +504,16 @@ MixedProblem make_mixed_problem(wos_domain_t dom, const double *x, int64_t Q, in
     P.has_outer = dom->has_outer;
     P.has_goal = dom->has_goal;
     P.grad_mode = grad_mode;
+    P.has_source = dom->has_source;
+    P.src = grad_mode && dom->has_source;
+    if (dom->has_source) {
+        const int d = dom->d;
+        const double nu = 0.5 * d - 1.0, k = std::sqrt(sigma);
+        P.source_q = (float)dom->source_q;
+        for (int j = 0; j < d; ++j) P.source_z[j] = (float)dom->source_z[j];
+        P.src_inv_omega = (float)(std::tgamma(0.5 * d) / (2.0 * std::pow(M_PI, 0.5 * d)));
+        P.src_lc0 = k > 0.0 ? (float)(nu * std::log(k) - 0.5 * d * std::log(2.0 * M_PI)) : 0.0f;
+    }
     P.laplace = laplace;
     P.cv = grad_mode && cv;
     P.eps = (float)eps;
@@ -525,7 +547,8 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
                           double eps, double sigma, int grad_mode, const Scratch &sc,
                           const PerWalk &pw, const int *skip, cudaStream_t s) {
     const int cv = grad_mode && o.cv;
-    const int nf = acc_fields(dom->d, dom->n_exp, cv);
+    const int src = grad_mode && dom->has_source;
+    const int nf = acc_fields(dom->d, dom->n_exp, cv, src);
     if (o.precision == WOS_FP64) {
         SimpleParams<double> p{};
         p.dom = dom->v64;
@@ -541,6 +564,7 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
         p.grad_mode = grad_mode;
         p.laplace = o.laplace;
         p.cv = cv;
+        p.src = src;
         p.acc = (double *)sc.acc;
         p.counts = sc.counts;
         p.nf = nf;
@@ -567,6 +591,7 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
         p.grad_mode = grad_mode;
         p.laplace = o.laplace;
         p.cv = cv;
+        p.src = src;
         p.acc = (float *)sc.acc;
         p.counts = sc.counts;
         p.nf = nf;
@@ -586,6 +611,8 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
             return fail(WOS_ERR_UNSUPPORTED, "mixed-precision point clouds need d <= %d", kPointCloudMaxD);
         if (dom->n_balls > 0 && dom->n_points > 0)
             return fail(WOS_ERR_UNSUPPORTED, "a domain with both balls and points runs in FP64 or plain FP32");
+        if (dom->has_source)
+            return fail(WOS_ERR_UNSUPPORTED, "a point set with an impulse source runs in FP64 or plain FP32");
         MixedProblem P = make_mixed_problem(dom, x, Q, N, eps, sigma, grad_mode, o.laplace, cv, o.walk_offset, tab,
                                             (double *)sc.acc, sc.counts, pw);
         if (cv) {
@@ -678,7 +705,8 @@ wos_status run_estimator(wos_domain_t dom, const wos_options *opt, const double 
     if (stats != nullptr) WOS_CUDA(cudaMemsetAsync(stats, 0, sizeof(wos_stats), s));
     if (Q == 0) return WOS_OK;
     const int cv = grad_mode && o.cv;
-    const int nf = acc_fields(dom->d, dom->n_exp, cv);
+    const int src = grad_mode && dom->has_source;
+    const int nf = acc_fields(dom->d, dom->n_exp, cv, src);
     const size_t bytes = scratch_bytes(o.precision, Q, nf);
     void *base = nullptr;
     WOS_CUDA(cudaMallocAsync(&base, bytes, s));
@@ -700,6 +728,8 @@ wos_status run_estimator(wos_domain_t dom, const wos_options *opt, const double 
         r.K = dom->n_exp;
         r.acc_f32 = o.precision == WOS_FP32_PLAIN;
         r.cv = cv;
+        r.src = src;
+        r.has_source = dom->has_source;
         r.Q = Q;
         r.N = N;
         r.q_begin = 0;
@@ -778,6 +808,8 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
     D->n_exp = desc->n_exp;
     D->outer_r = D->has_outer ? desc->outer_r : 0.0;
     D->goal_r = D->has_goal ? desc->goal_r : 0.0;
+    D->has_source = desc->source_z != nullptr;
+    D->source_q = D->has_source ? desc->source_q : 0.0;
     auto copy = [](std::vector<double> &v, const double *p, size_t n) {
         v.assign(n, 0.0);
         if (p) std::copy(p, p + n, v.begin());
@@ -791,6 +823,7 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
     copy(D->ball_r, desc->ball_r, desc->n_balls);
     copy(D->ball_c, desc->ball_c, (size_t)desc->n_balls * d);
     copy(D->points, desc->points, (size_t)desc->n_points * d);
+    copy(D->source_z, desc->source_z, d);
     double rmax = INFINITY;
     if (D->has_box)
         for (int j = 0; j < d; ++j) rmax = std::min(rmax, 0.5 * (D->box_hi[j] - D->box_lo[j]));
@@ -856,7 +889,10 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
     }
     layout_view<double>(D->v64, D->f64, *D);
     layout_view<float>(D->v32, D->f32, *D);
-    const bool sphere_balls = D->n_points == 0 && D->n_balls >= kSphereMinBalls && d <= kPointCloudMaxD;
+    // domains with an impulse source stay on the CUDA-core walker (the sphere-set walker has no
+    // source term)
+    const bool sphere_balls =
+        D->n_points == 0 && D->n_balls >= kSphereMinBalls && d <= kPointCloudMaxD && !D->has_source;
     if ((D->n_points > 0 && d <= kPointCloudMaxD) || sphere_balls) {
         e = sphere_balls ? pointcloud_prepare(D->ball_c.data(), D->ball_r.data(), D->n_balls, d, &D->pcd)
                          : pointcloud_prepare(D->points.data(), nullptr, D->n_points, d, &D->pcd);
@@ -969,6 +1005,7 @@ struct PlanArgs {
     int acc_bytes;
     int acc_f32;
     int cv;  // control-variate gradient (sums after the du/dw fields)
+    int src;  // impulse-source fields after those
     unsigned long long *counts;
     unsigned long long *cursor;
     double *grad_row;
@@ -989,6 +1026,18 @@ __global__ void plan_pre_kernel(const __grid_constant__ PlanArgs a) {
                 s += t * t;
             }
             if (sqrt(s) - a.dom.goal_r < a.eps) {
+                skip = 1;
+                f = 1;
+                *a.done = 1;
+            }
+        } else if (a.dom.has_source) {
+            // the goal is the impulse source: reached once it is within one nominal step
+            double s = 0.0;
+            for (int j = 0; j < a.dom.d; ++j) {
+                const double t = a.x[j] - a.dom.source_z[j];
+                s += t * t;
+            }
+            if (sqrt(s) < a.s_ub) {
                 skip = 1;
                 f = 1;
                 *a.done = 1;
@@ -1022,15 +1071,18 @@ __device__ void plan_post_d(const PlanArgs &a) {
                 return a.acc_f32 ? (double)((const float *)a.acc)[f] : ((const double *)a.acc)[f];
             };
             const int cf = cv_field(D, a.dom.n_exp);
+            const int sf = src_field(D, a.dom.n_exp, a.cv);
+            const double s0 = a.src ? S(sf) : 0.0;
             double g[D];
             double gg = 0.0;
             for (int j = 0; j < D; ++j) {
                 g[j] = S(3 + j) * inv;
                 if (a.cv && a.N >= 2) {
                     double se;
-                    cv_estimate(S(3 + j), S(3 + D + j), S(cf + j), S(cf + D + j), S(cf + 2 * D + j), S(cf + 3 * D),
-                                S(0), (double)a.N, g[j], se);
+                    cv_estimate(S(3 + j), S(3 + D + j), S(cf + j), S(cf + D + j) - s0 * S(cf + 2 * D + j),
+                                S(cf + 2 * D + j), S(cf + 3 * D), S(0) - (double)a.N * s0, (double)a.N, g[j], se);
                 }
+                if (a.src) g[j] += S(sf + 1 + j);
                 gg += g[j] * g[j];
             }
             if (a.grad_row)
@@ -1066,7 +1118,7 @@ wos_status enqueue_plan_step(wos_domain_t dom, const Opts &o, double *x, int64_t
                              double sigma, double s_ub, int64_t step_idx, int *done, int *skip,
                              int32_t *flag, const Scratch &sc, double *grad_row, double *path_row,
                              cudaStream_t s) {
-    const int nf = acc_fields(dom->d, dom->n_exp, o.cv);
+    const int nf = acc_fields(dom->d, dom->n_exp, o.cv, dom->has_source);
     PlanArgs a{};
     a.dom = dom->v64;
     a.x = x;
@@ -1079,6 +1131,7 @@ wos_status enqueue_plan_step(wos_domain_t dom, const Opts &o, double *x, int64_t
     a.acc = sc.acc;
     a.acc_f32 = o.precision == WOS_FP32_PLAIN;
     a.cv = o.cv;
+    a.src = dom->has_source;
     a.acc_bytes = nf * (a.acc_f32 ? 4 : 8);
     a.counts = sc.counts;
     a.cursor = sc.cursor;
@@ -1109,7 +1162,7 @@ wos_status wos_plan_step(wos_domain_t dom, const wos_options *opt, double *x, in
         WeightTable t;
         WOS_TRY(ensure_table(dom, sigma, &t));
     }
-    const int nf = acc_fields(dom->d, dom->n_exp, o.cv);
+    const int nf = acc_fields(dom->d, dom->n_exp, o.cv, dom->has_source);
     const size_t bytes = scratch_bytes(o.precision, 1, nf) + 256;
     void *base = nullptr;
     WOS_CUDA(cudaMallocAsync(&base, bytes, s));
@@ -1140,7 +1193,7 @@ wos_status wos_plan_path(wos_domain_t dom, const wos_options *opt, const double 
         WOS_TRY(ensure_table(dom, sigma, &t));
         WOS_TRY(ensure_mixed_smem(mixed_smem_bytes(*dom)));
     }
-    const int nf = acc_fields(d, dom->n_exp, o.cv);
+    const int nf = acc_fields(d, dom->n_exp, o.cv, dom->has_source);
     const size_t bytes = scratch_bytes(o.precision, 1, nf) + 256 + sizeof(double) * d;
     void *base = nullptr;
     WOS_CUDA(cudaMalloc(&base, bytes));
@@ -1401,6 +1454,8 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
             return fail(WOS_ERR_UNSUPPORTED, "problem %d: mixed-precision point sets need d <= %d", i, kPointCloudMaxD);
         if (p.domain->n_points > 0 && p.domain->n_balls > 0)
             return fail(WOS_ERR_UNSUPPORTED, "problem %d: a domain with both balls and points", i);
+        if (p.domain->n_points > 0 && p.domain->has_source)
+            return fail(WOS_ERR_UNSUPPORTED, "problem %d: a point set with an impulse source", i);
         tensor[i] = p.domain->has_pcd && (p.domain->n_points > 0 || !b->o.cuda_core_balls);
         if (!tensor[i]) b->smem = std::max(b->smem, mixed_smem_bytes(*p.domain));
     }
@@ -1419,7 +1474,8 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     std::vector<size_t> acc_off(n), cnt_off(n);
     for (int i = 0; i < n; ++i) {
         const wos_problem &p = b->probs[i];
-        const int nf = acc_fields(p.domain->d, p.domain->n_exp, p.grad != nullptr && b->o.cv);
+        const int nf = acc_fields(p.domain->d, p.domain->n_exp, p.grad != nullptr && b->o.cv,
+                                  p.grad != nullptr && p.domain->has_source);
         acc_off[i] = acc_bytes;
         acc_bytes += align256((size_t)p.n_queries * nf * sizeof(double));
     }
@@ -1530,6 +1586,8 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         r.K = p.domain->n_exp;
         r.acc_f32 = 0;
         r.cv = mp[i].cv;
+        r.src = mp[i].src;
+        r.has_source = p.domain->has_source;
         r.Q = p.n_queries;
         r.N = p.n_walks;
         r.q_begin = q_begin;

@@ -160,23 +160,27 @@ __device__ __forceinline__ float2 table_lookup(const WeightTable &t, float z) {
 // ------------------------------------------------------------------------------------
 template <typename T>
 struct DomainView {
-    int d, n_balls, n_exp, has_box, has_outer, has_goal;
+    int d, n_balls, n_exp, has_box, has_outer, has_goal, has_source;
     int64_t n_points;
-    T outer_r, goal_r;
+    T outer_r, goal_r, source_q;
     const T *box_lo, *box_hi, *outer_c, *goal_c;  // d each
     const T *ball_c, *ball_r;                      // B x d, B
     const T *points;                               // M x d
     const T *exp_w, *exp_a;                        // K, K x d
+    const T *source_z;                             // d (impulse source; has_source)
 };
 
 // Per-query accumulator fields: [sum u, sum u^2, sum du/dsigma, sum grad (d), sum grad^2 (d),
-// sum du/dw (K)] and, with the gradient control variate, [sum v0 (d), sum t v0^2 (d),
+// sum du/dw (K)]; with the gradient control variate, [sum v0 (d), sum t v0^2 (d),
 // sum v0^2 (d), G] (v0 the first direction, t the walk's value, G = alpha(R0)/C(R0), one number
-// per query because R0 is the distance at the query); int64 counters [walks, walk_steps,
-// capped, outside] live apart.
-__host__ __device__ __forceinline__ int acc_fields(int d, int K, int cv = 0) {
-    return 3 + 2 * d + K + (cv ? 3 * d + 1 : 0);
+// per query because R0 is the distance at the query); with an impulse source in gradient walks,
+// [s0, g_src (d)]: the step-0 source value and the source part of the gradient, also one per
+// query (they depend only on the query). The gradient sums then hold G (t - s0) v0. int64
+// counters [walks, walk_steps, capped, outside] live apart.
+__host__ __device__ __forceinline__ int acc_fields(int d, int K, int cv = 0, int src = 0) {
+    return 3 + 2 * d + K + (cv ? 3 * d + 1 : 0) + (src ? d + 1 : 0);
 }
+__host__ __device__ __forceinline__ int src_field(int d, int K, int cv) { return acc_fields(d, K, cv, 0); }
 __host__ __device__ __forceinline__ int cv_field(int d, int K) { return 3 + 2 * d + K; }
 constexpr int kCounters = 4;
 

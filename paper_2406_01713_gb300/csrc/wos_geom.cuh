@@ -105,4 +105,54 @@ __device__ __forceinline__ T boundary_value(const DomainView<T> &dm, const T (&x
     return kind == kGoal ? T(1) : T(0);
 }
 
+// ---- impulse source: Green's function of the largest empty ball ------------------------
+// log K_nu(x) and log K_{nu+1}(x), x > 0, from int_0^inf exp(-x cosh t) cosh(mu t) dt
+// (DLMF 10.32.9): trapezoidal rule (even integrand, analytic in |Im t| < pi/2; step
+// min(1/8, 0.6/sqrt(x)) keeps the relative error below 1e-23) with the sum scaled by the peak
+// of exp(-x cosh t + (nu+1) t), so that no term overflows.
+__device__ inline void log_bessel_K_pair_f64(double nu, double x, double &l0, double &l1) {
+    const double mu = nu + 1.0;
+    const double ts = asinh(mu / x);
+    const double m = mu * ts - x * cosh(ts);
+    const double h = x > 23.04 ? 0.6 * rsqrt(x) : 0.125;
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = 0; i < 8000; ++i) {
+        const double t = h * (double)i, c = x * cosh(t), w = i == 0 ? 0.5 : 1.0;
+        const double e1 = mu * t - c - m;
+        s1 += w * (exp(e1) + exp(-mu * t - c - m));
+        s0 += w * (exp(nu * t - c - m) + exp(-nu * t - c - m));
+        if (t > ts && e1 < -45.0) break;
+    }
+    l0 = m + log(0.5 * h * s0);
+    l1 = m + log(0.5 * h * s1);
+}
+
+// Between the centre of a ball of radius R and a point at distance r (0 < r < R), for
+// Laplace(u) - sigma u = -delta with zero values on the sphere: G = G_B and F with
+// grad_x G_B = F (y - x)/r at the centre; k = sqrt(sigma), nu = d/2 - 1, c0 = k^nu/(2 pi)^(d/2):
+//   G = c0 r^-nu [K_nu(kr) - K_nu(kR) I_nu(kr)/I_nu(kR)],
+//   F = c0 k r^-nu [K_nu+1(kr) - K_nu+1(kR) I_nu+1(kr)/I_nu+1(kR)],
+// I ratios from the series S (I_mu(z) is proportional to z^mu S_mu(z)); at sigma = 0 the
+// Laplace forms (r^(2-d) - R^(2-d))/((d-2) omega), ln(R/r)/(2 pi) for d = 2, and
+// F = (r^(1-d) - r R^-d)/omega, omega = |S^(d-1)|. FP64.
+__device__ inline void source_green_f64(int d, double k, double r, double R, double &G, double &F) {
+    const double nu = 0.5 * d - 1.0;
+    if (k == 0.0) {
+        const double omega = 2.0 * pow(CUDART_PI, 0.5 * d) / tgamma(0.5 * d);
+        G = d == 2 ? log(R / r) / (2.0 * CUDART_PI) : (pow(r, 2.0 - d) - pow(R, 2.0 - d)) / ((d - 2.0) * omega);
+        F = (pow(r, 1.0 - d) - r * pow(R, -(double)d)) / omega;
+        return;
+    }
+    double ka0, ka1, kb0, kb1;
+    log_bessel_K_pair_f64(nu, k * r, ka0, ka1);
+    log_bessel_K_pair_f64(nu, k * R, kb0, kb1);
+    const double lc0 = nu * log(k) - 0.5 * d * log(2.0 * CUDART_PI);
+    const double lrR = log(r / R), lr = log(r);
+    const double i0 = nu * lrR + log(bessel_S<double>(nu, k * r)) - log(bessel_S<double>(nu, k * R));
+    const double i1 =
+        (nu + 1.0) * lrR + log(bessel_S<double>(nu + 1.0, k * r)) - log(bessel_S<double>(nu + 1.0, k * R));
+    G = exp(lc0 - nu * lr + ka0) * (1.0 - exp(kb0 - ka0 + i0));
+    F = exp(lc0 + log(k) - nu * lr + ka1) * (1.0 - exp(kb1 - ka1 + i1));
+}
+
 }  // namespace wos

@@ -22,6 +22,7 @@ struct SimpleParams {
     T eps, sqrt_sigma, shrink;
     int grad_mode, laplace;
     int cv;                      // gradient control variate: accumulate the 3d extra sums
+    int src;                     // impulse source in gradient walks: store its per-query fields
     T *acc;                      // Q x nf sums
     unsigned long long *counts;  // Q x kCounters
     int nf;
@@ -40,6 +41,12 @@ struct MixedProblem {
     int d, n_balls, n_exp, has_box, has_outer, has_goal;
     int grad_mode, laplace;
     int cv;        // gradient control variate: accumulate the 3d extra sums
+    int src;       // impulse source in gradient walks: store its per-query fields
+    int has_source;
+    float source_q;
+    float src_lc0;        // log(k^nu / (2 pi)^(d/2)), k = sqrt(sigma) > 0
+    float src_inv_omega;  // 1 / |S^(d-1)| (sigma = 0)
+    float source_z[kMaxD];
     float eps, sqrt_sigma;
     float shrink;  // FP32 error bound subtracted from every radius
     float slack;   // FP32 rounding bound of the ball screening test

@@ -100,6 +100,10 @@ class Domain:
             s.n_exp = ea.shape[0]
             s.exp_a = p(ea)
             s.exp_w = p(arr("exp_w", (-1,)))
+        if dom.get("source_z") is not None:  # impulse source (strength source_q, default 1)
+            s.source_z = p(arr("source_z", (d,)))
+            s.source_q = float(dom.get("source_q", 1.0))
+        self.has_source = dom.get("source_z") is not None
         self.n_exp = int(s.n_exp)
         self.n_balls = int(s.n_balls)
         self.n_points = int(s.n_points)
