@@ -43,6 +43,8 @@ constexpr int kTileN = 64;       // centres per tile = MMA N
 constexpr int kMaxStages = 6;
 constexpr int kCtasPerSm = 4;    // 4 x 128 TMEM columns; registers <= 102 per thread
 constexpr int kChunk = 32;       // candidate chunk (columns)
+// walkers whose chunk refinements a warp keeps in flight together (bounded by registers)
+__host__ __device__ constexpr int refine_group(int d) { return d > 0 ? 4 : 1; }
 constexpr int kWalkerThreads = 128;
 constexpr int kThreads = kWalkerThreads + 32;
 constexpr uint32_t kTmemCols = 2 * kTileN;
@@ -515,19 +517,31 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             auto refine = [&](int cc, bool want) {
                 const unsigned todo = __ballot_sync(0xffffffffu, want);
                 if (todo == 0u) return;
-                // lane i: sphere i of walker w's chunk, for every walker w that asks
-#pragma unroll 4
-                for (int w = 0; w < 32; ++w) {
-                    if (!((todo >> w) & 1u)) continue;
-                    const int cw = __shfl_sync(0xffffffffu, cc, w);
-                    const float *ch = SP.soa + (long long)cw * (D + 1) * kChunk;
-                    float s2 = 0.f;
+                // lane i: sphere i of walker w's chunk, refine_group(D) walkers at a time so that
+                // their chunk loads are in flight together; a walker that does not ask still
+                // names a valid chunk, and its row is not read
+                constexpr int kGroup = refine_group(D);
+#pragma unroll 1
+                for (int w0 = 0; w0 < 32; w0 += kGroup) {
+                    if (((todo >> w0) & ((1u << kGroup) - 1u)) == 0u) continue;
+                    const float *ch[kGroup];
+                    float s2[kGroup], rr[kGroup];
+#pragma unroll
+                    for (int u = 0; u < kGroup; ++u) {
+                        ch[u] = SP.soa + (long long)__shfl_sync(0xffffffffu, cc, w0 + u) * (D + 1) * kChunk + lane;
+                        rr[u] = __ldg(ch[u] + D * kChunk);
+                        s2[u] = 0.f;
+                    }
 #pragma unroll
                     for (int jj = 0; jj < D; ++jj) {
-                        const float t0 = __shfl_sync(0xffffffffu, x[jj], w) - __ldg(ch + jj * kChunk + lane);
-                        s2 = fmaf(t0, t0, s2);
+#pragma unroll
+                        for (int u = 0; u < kGroup; ++u) {
+                            const float t0 = __shfl_sync(0xffffffffu, x[jj], w0 + u) - __ldg(ch[u] + jj * kChunk);
+                            s2[u] = fmaf(t0, t0, s2[u]);
+                        }
                     }
-                    tr[w * 33 + lane] = sqrtf(s2) - __ldg(ch + D * kChunk + lane);
+#pragma unroll
+                    for (int u = 0; u < kGroup; ++u) tr[(w0 + u) * 33 + lane] = sqrtf(s2[u]) - rr[u];
                 }
                 __syncwarp();
                 // walker w scans its own row (lowest index on ties)
