@@ -43,11 +43,17 @@ constexpr int kTileN = 64;       // centres per tile = MMA N
 constexpr int kMaxStages = 6;
 constexpr int kCtasPerSm = 4;    // 4 x 128 TMEM columns; registers <= 102 per thread
 constexpr int kChunk = 32;       // candidate chunk (columns)
-// walkers whose chunk refinements a warp keeps in flight together (bounded by registers)
-__host__ __device__ constexpr int refine_group(int d) { return d > 0 ? 4 : 1; }
+constexpr int kRefineGroup = 4;  // walkers whose chunk refinements a warp keeps in flight together
+// A chunk in memory: its kChunk centres sphere-major, each padded with zeros to a multiple of
+// four coordinates (one 16-byte load per four), then its kChunk radii.
+__host__ __device__ constexpr int chunk_pitch(int d) { return (d + 3) & ~3; }
+__host__ __device__ constexpr int chunk_floats(int d) { return kChunk * (chunk_pitch(d) + 1); }
 constexpr int kWalkerThreads = 128;
 constexpr int kThreads = kWalkerThreads + 32;
 constexpr uint32_t kTmemCols = 2 * kTileN;
+// dynamic shared memory alignment: the operands use no swizzle, whose descriptors and bulk copies
+// need 16-byte addresses
+constexpr int kSmemAlign = 128;
 
 // Contraction length: 3d + 2 BF16 columns padded to 32 (d <= 10) or 48 (d = 11, 12); the
 // centre-tile ring is shorter for the wider tiles so that four CTAs still fit an SM.
@@ -61,7 +67,8 @@ struct Geo {
     static constexpr int kStages = K == 32 ? 6 : 4;  // centre-tile ring in shared memory
     static constexpr int kAhead = kStages - 2;       // tiles loaded ahead of the MMA issue point
 };
-constexpr uint32_t kTransposeBytes = 4 * 32 * 33 * 4;  // per walker warp: 32 walkers x 32 spheres (+1 pad)
+constexpr int kTrPitch = 34;  // transpose row: 32 spheres + 2 pad (8-byte aligned rows, no bank conflicts)
+constexpr uint32_t kTransposeBytes = 4 * 32 * kTrPitch * 4;  // per walker warp: 32 walkers x 32 spheres
 constexpr long long kWaitBudget = 4000000000ll;  // clock cycles (~2 s) before a wait gives up
 
 // Core-matrix layout (8 rows x 16 bytes), K-major, no swizzle: element (r, k) of a
@@ -250,12 +257,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
     constexpr int kK = G::kK;
     constexpr uint32_t kTileBytes = G::kTileBytes, kABytes = G::kABytes, kSBO = G::kSBO;
     constexpr int kStages = G::kStages, kAhead = G::kAhead;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    extern __shared__ __align__(kSmemAlign) unsigned char smem_raw[];
     __shared__ Shared S;
     __shared__ SphereProblem SP;  // the problem the CTA's walkers are on
     __shared__ float geom_s[4 * kMaxD + kMaxExp + kMaxExp * kMaxD];
     unsigned char *base =
-        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + kSmemAlign - 1) & ~(uintptr_t)(kSmemAlign - 1));
     unsigned char *A = base;
     unsigned char *Bst = base + kABytes;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -513,46 +520,71 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             //      a chunk is stored coordinate-major, so every load is one coalesced row.
             float Rp = CUDART_INF_F;
             int pbest = c1 * kChunk;
-            float *tr = reinterpret_cast<float *>(Bst + kStages * kTileBytes) + warp * 32 * 33;
+            float *tr = reinterpret_cast<float *>(Bst + kStages * kTileBytes) + warp * 32 * kTrPitch;
+            // the walkers' positions, padded like the chunk centres, in this warp's own rows of
+            // the A operand: every MMA of the step has completed, and the next step rewrites them
+            constexpr int kP = chunk_pitch(D);
+            static_assert(kChunk * kP * 4 <= 4 * kSBO, "positions fit the warp's A rows");
+            float *xs = reinterpret_cast<float *>(A + warp * 4 * kSBO);
+#pragma unroll
+            for (int i = 0; i < kP; i += 4)
+                *reinterpret_cast<float4 *>(xs + lane * kP + i) =
+                    make_float4(i < D ? x[i] : 0.f, i + 1 < D ? x[i + 1] : 0.f, i + 2 < D ? x[i + 2] : 0.f,
+                                i + 3 < D ? x[i + 3] : 0.f);
+            __syncwarp();
             auto refine = [&](int cc, bool want) {
                 const unsigned todo = __ballot_sync(0xffffffffu, want);
                 if (todo == 0u) return;
-                // lane i: sphere i of walker w's chunk, refine_group(D) walkers at a time so that
+                // lane i: sphere i of walker w's chunk, kRefineGroup walkers at a time so that
                 // their chunk loads are in flight together; a walker that does not ask still
                 // names a valid chunk, and its row is not read
-                constexpr int kGroup = refine_group(D);
 #pragma unroll 1
-                for (int w0 = 0; w0 < 32; w0 += kGroup) {
-                    if (((todo >> w0) & ((1u << kGroup) - 1u)) == 0u) continue;
-                    const float *ch[kGroup];
-                    float s2[kGroup], rr[kGroup];
+                for (int w0 = 0; w0 < 32; w0 += kRefineGroup) {
+                    if (((todo >> w0) & ((1u << kRefineGroup) - 1u)) == 0u) continue;
+                    const float4 *cen[kRefineGroup];
+                    float s2[kRefineGroup], rr[kRefineGroup];
 #pragma unroll
-                    for (int u = 0; u < kGroup; ++u) {
-                        ch[u] = SP.soa + (long long)__shfl_sync(0xffffffffu, cc, w0 + u) * (D + 1) * kChunk + lane;
-                        rr[u] = __ldg(ch[u] + D * kChunk);
+                    for (int u = 0; u < kRefineGroup; ++u) {
+                        const float *ch =
+                            SP.soa + (long long)__shfl_sync(0xffffffffu, cc, w0 + u) * chunk_floats(D);
+                        cen[u] = reinterpret_cast<const float4 *>(ch + lane * kP);
+                        rr[u] = __ldg(ch + kChunk * kP + lane);
                         s2[u] = 0.f;
                     }
 #pragma unroll
-                    for (int jj = 0; jj < D; ++jj) {
+                    for (int i4 = 0; i4 < kP / 4; ++i4) {
 #pragma unroll
-                        for (int u = 0; u < kGroup; ++u) {
-                            const float t0 = __shfl_sync(0xffffffffu, x[jj], w0 + u) - __ldg(ch[u] + jj * kChunk);
+                        for (int u = 0; u < kRefineGroup; ++u) {
+                            const float4 c = __ldg(cen[u] + i4);
+                            const float4 xv = *reinterpret_cast<const float4 *>(xs + (w0 + u) * kP + 4 * i4);
+                            // zero padding adds exact zeros: the sum is the d-term sum in order
+                            float t0 = xv.x - c.x;
+                            s2[u] = fmaf(t0, t0, s2[u]);
+                            t0 = xv.y - c.y;
+                            s2[u] = fmaf(t0, t0, s2[u]);
+                            t0 = xv.z - c.z;
+                            s2[u] = fmaf(t0, t0, s2[u]);
+                            t0 = xv.w - c.w;
                             s2[u] = fmaf(t0, t0, s2[u]);
                         }
                     }
 #pragma unroll
-                    for (int u = 0; u < kGroup; ++u) tr[(w0 + u) * 33 + lane] = sqrtf(s2[u]) - rr[u];
+                    for (int u = 0; u < kRefineGroup; ++u) tr[(w0 + u) * kTrPitch + lane] = sqrtf(s2[u]) - rr[u];
                 }
                 __syncwarp();
                 // walker w scans its own row (lowest index on ties)
                 if (want) {
-                    const float *row = tr + lane * 33;
-#pragma unroll 8
-                    for (int i = 0; i < kChunk; ++i) {
-                        const float di = row[i];
-                        if (di < Rp) {
-                            Rp = di;
-                            pbest = cc * kChunk + i;
+                    const float2 *row = reinterpret_cast<const float2 *>(tr + lane * kTrPitch);
+#pragma unroll 4
+                    for (int i = 0; i < kChunk / 2; ++i) {
+                        const float2 di = row[i];
+                        if (di.x < Rp) {
+                            Rp = di.x;
+                            pbest = cc * kChunk + 2 * i;
+                        }
+                        if (di.y < Rp) {
+                            Rp = di.y;
+                            pbest = cc * kChunk + 2 * i + 1;
                         }
                     }
                 }
@@ -633,15 +665,16 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                 for (int i = 0; i < D; ++i) xb[i] = x[i];
                 if (kind == kPoint) {
                     // closest point of the sphere (c, r): c + r (x - c)/|x - c|; c itself for a point
-                    const float *c = SP.soa + (long long)(idx / kChunk) * (D + 1) * kChunk + (idx % kChunk);
-                    const float rad = __ldg(c + D * kChunk);
+                    const float *ch = SP.soa + (long long)(idx / kChunk) * chunk_floats(D);
+                    const float *c = ch + (idx % kChunk) * chunk_pitch(D);
+                    const float rad = __ldg(ch + kChunk * chunk_pitch(D) + idx % kChunk);
                     float s = 0.f;
 #pragma unroll
-                    for (int i = 0; i < D; ++i) s = fmaf(x[i] - __ldg(c + i * kChunk), x[i] - __ldg(c + i * kChunk), s);
+                    for (int i = 0; i < D; ++i) s = fmaf(x[i] - __ldg(c + i), x[i] - __ldg(c + i), s);
                     const float len = sqrtf(s);
                     const float f = len > 0.f ? rad / len : 0.f;
 #pragma unroll
-                    for (int i = 0; i < D; ++i) xb[i] = fmaf(f, x[i] - __ldg(c + i * kChunk), __ldg(c + i * kChunk));
+                    for (int i = 0; i < D; ++i) xb[i] = fmaf(f, x[i] - __ldg(c + i), __ldg(c + i));
                 } else if (kind == kFace) {
 #pragma unroll
                     for (int i = 0; i < D; ++i)
@@ -704,7 +737,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
 template <int K>
 size_t smem_bytes_k() {
     using G = Geo<K>;
-    return std::max<size_t>(48 * 1024, 1024 + G::kABytes + (size_t)G::kStages * G::kTileBytes + kTransposeBytes);
+    return std::max<size_t>(48 * 1024, kSmemAlign + G::kABytes + (size_t)G::kStages * G::kTileBytes + kTransposeBytes);
 }
 size_t smem_bytes(int d) { return contraction_k(d) == 32 ? smem_bytes_k<32>() : smem_bytes_k<48>(); }
 
@@ -730,7 +763,7 @@ cudaError_t pointcloud_prepare(const double *pts, const double *radii, int64_t M
     const int64_t n_tiles = (M + pc::kTileN - 1) / pc::kTileN;
     const int64_t Mp = n_tiles * pc::kTileN;
     std::vector<uint16_t> hb((size_t)n_tiles * tile_bytes / 2, 0);
-    std::vector<float> hsoa((size_t)(Mp / pc::kChunk) * (d + 1) * pc::kChunk, 0.f);
+    std::vector<float> hsoa((size_t)(Mp / pc::kChunk) * pc::chunk_floats(d), 0.f);
     std::vector<float> hrhi((size_t)(Mp / pc::kChunk), 0.f);
     // balls in increasing radius (ties by index), points in input order
     std::vector<int64_t> order((size_t)M);
@@ -743,10 +776,11 @@ cudaError_t pointcloud_prepare(const double *pts, const double *radii, int64_t M
         const int64_t src = real ? order[(size_t)i] : 0;
         float p[WOS_MAX_D];
         double nn = 0.0;
-        float *chunk = hsoa.data() + (size_t)(i / pc::kChunk) * (d + 1) * pc::kChunk + (size_t)(i % pc::kChunk);
+        float *chunk = hsoa.data() + (size_t)(i / pc::kChunk) * pc::chunk_floats(d);
+        float *centre = chunk + (size_t)(i % pc::kChunk) * pc::chunk_pitch(d);
         if (real && radii != nullptr) {
             const float r32 = (float)radii[src];
-            chunk[(size_t)d * pc::kChunk] = r32;
+            chunk[(size_t)pc::kChunk * pc::chunk_pitch(d) + (size_t)(i % pc::kChunk)] = r32;
             // chunk bound rounded up: never below the FP64 radius
             float up = r32 < radii[src] ? std::nextafter(r32, 3.0e38f) : r32;
             float &cb = hrhi[(size_t)(i / pc::kChunk)];
@@ -755,7 +789,7 @@ cudaError_t pointcloud_prepare(const double *pts, const double *radii, int64_t M
         for (int j = 0; j < d; ++j) {
             // padding centres sit far outside any domain: they never win the minimum
             p[j] = real ? (float)pts[src * d + j] : 1.0e3f;
-            chunk[(size_t)j * pc::kChunk] = p[j];
+            centre[j] = p[j];
             nn += (double)p[j] * (double)p[j];
             if (real) pmax = std::max(pmax, std::fabs((double)p[j]));
         }
