@@ -127,6 +127,19 @@ struct Shared {
     SphereItem pend;
 };
 
+// A slot of the centre-tile ring and the number of completed passes over the ring (whose
+// parity is the phase a wait on that slot's barriers expects).
+struct RingPos {
+    int slot = 0;
+    uint32_t round = 0;
+    __device__ __forceinline__ void next(int n) {
+        if (++slot == n) {
+            slot = 0;
+            ++round;
+        }
+    }
+};
+
 // Bounded wait: false if the budget ran out or another thread aborted.
 __device__ __forceinline__ bool wait_bar(Shared &S, uint64_t *b, uint32_t parity, int *status) {
     if (mbar_test(b, parity)) return true;
@@ -317,7 +330,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
         // ------------------------------------------------------------------ producer
         if (lane == 0) {
             long long g_load = 0, g_mma = 0;
-            const uint32_t a_addr = su32(A);
+            // the operand descriptors, built once: a descriptor of (addr + off) is the descriptor of
+            // addr plus off / 16 while the address stays below 256 KB (its 14-bit field)
+            const uint64_t a_desc = smem_desc(su32(A), kSBO);
+            const uint64_t b_desc0 = smem_desc(su32(Bst), kSBO);
+            constexpr uint64_t kKStep = (2 * kLBO) >> 4, kStageStep = kTileBytes >> 4;
+            RingPos lp, mp;  // ring slots of the next load and of the next MMA
             bool ok = true;
             for (int step = 0; ok; ++step) {
                 if (!wait_bar(S, &S.a_ready, step & 1, L.status)) break;
@@ -327,34 +345,33 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                 const unsigned char *tiles = reinterpret_cast<const unsigned char *>(SP.tiles);
                 int t_load = 0;
                 auto issue_load = [&]() -> bool {
-                    const int s = (int)(g_load % kStages);
-                    if (g_load >= kStages &&
-                        !wait_bar(S, &S.empty[s], (uint32_t)((g_load / kStages - 1) & 1), L.status))
-                        return false;
+                    const int s = lp.slot;
+                    if (lp.round > 0 && !wait_bar(S, &S.empty[s], (lp.round - 1) & 1u, L.status)) return false;
                     mbar_expect_tx(&S.full[s], kTileBytes);
-                    bulk_load_tile(su32(Bst + s * kTileBytes), tiles + (size_t)t_load * kTileBytes, kTileBytes,
+                    bulk_load_tile(su32(Bst) + s * kTileBytes, tiles + (size_t)t_load * kTileBytes, kTileBytes,
                                    &S.full[s]);
+                    lp.next(kStages);
                     ++g_load;
                     ++t_load;
                     return true;
                 };
                 while (ok && t_load < T && g_load < g_mma + kAhead) ok = issue_load();
                 for (int t = 0; ok && t < T; ++t) {
-                    const int s = (int)(g_mma % kStages);
+                    const int s = mp.slot;
                     const int b = (int)(g_mma & 1);
-                    if (!wait_bar(S, &S.full[s], (uint32_t)((g_mma / kStages) & 1), L.status)) { ok = false; break; }
+                    if (!wait_bar(S, &S.full[s], mp.round & 1u, L.status)) { ok = false; break; }
                     if (g_mma >= 2 && !wait_bar(S, &S.tempty[b], (uint32_t)(((g_mma >> 1) - 1) & 1), L.status)) {
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t b_addr = su32(Bst + s * kTileBytes);
+                    const uint64_t b_desc = b_desc0 + (uint64_t)s * kStageStep;
 #pragma unroll
                     for (int kk = 0; kk < kK / 16; ++kk)
-                        mma_bf16(tmem + b * kTileN, smem_desc(a_addr + kk * 2 * kLBO, kSBO),
-                                 smem_desc(b_addr + kk * 2 * kLBO, kSBO), kk > 0);
+                        mma_bf16(tmem + b * kTileN, a_desc + kk * kKStep, b_desc + kk * kKStep, kk > 0);
                     mma_commit(&S.tfull[b]);
                     mma_commit(&S.empty[s]);
+                    mp.next(kStages);
                     ++g_mma;
                     while (ok && t_load < T && g_load < g_mma + kAhead) ok = issue_load();
                 }
@@ -363,8 +380,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             // load was consumed by an MMA, except after an abort
             mma_commit(&S.drain);
             wait_bar(S, &S.drain, 0, L.status);
-            for (long long g = g_mma; g < g_load; ++g)
-                wait_bar(S, &S.full[g % kStages], (uint32_t)((g / kStages) & 1), L.status);
+            for (long long g = g_mma; g < g_load; ++g) {
+                wait_bar(S, &S.full[mp.slot], mp.round & 1u, L.status);
+                mp.next(kStages);
+            }
         }
         __syncwarp();
     } else {
