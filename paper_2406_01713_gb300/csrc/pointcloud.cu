@@ -41,6 +41,7 @@ namespace pc {
 constexpr int kRows = 128;       // walkers per CTA = MMA M = TMEM lanes
 constexpr int kTileN = 64;       // centres per tile = MMA N
 constexpr int kMaxStages = 6;
+constexpr int kPairTiles = 2;  // centre tiles per bulk copy (consecutive in memory and in the ring)
 constexpr int kCtasPerSm = 4;    // 4 x 128 TMEM columns; registers <= 102 per thread
 constexpr int kChunk = 32;       // candidate chunk (columns)
 constexpr int kRefineGroup = 4;  // walkers whose chunk refinements a warp keeps in flight together
@@ -64,8 +65,11 @@ struct Geo {
     static constexpr uint32_t kTileBytes = kTileN * K * 2;
     static constexpr uint32_t kABytes = kRows * K * 2;
     static constexpr uint32_t kSBO = (K / 8) * 128;  // to the next group of 8 rows
-    static constexpr int kStages = K == 32 ? 6 : 4;  // centre-tile ring in shared memory
-    static constexpr int kAhead = kStages - 2;       // tiles loaded ahead of the MMA issue point
+    static constexpr int kStages = K == 32 ? 6 : 4;  // centre-tile ring in shared memory (tiles)
+    // the ring is filled kPairTiles tiles per bulk copy: kSlots slots, each with its own full and
+    // empty barrier
+    static constexpr int kSlots = kStages / kPairTiles;
+    static constexpr uint32_t kSlotBytes = kPairTiles * kTileBytes;
 };
 constexpr int kTrPitch = 34;  // transpose row: 32 spheres + 2 pad (8-byte aligned rows, no bank conflicts)
 constexpr uint32_t kTransposeBytes = 4 * 32 * kTrPitch * 4;  // per walker warp: 32 walkers x 32 spheres
@@ -112,8 +116,8 @@ __device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
 }
 
 struct Shared {
-    uint64_t full[kMaxStages];
-    uint64_t empty[kMaxStages];
+    uint64_t full[kMaxStages / kPairTiles];
+    uint64_t empty[kMaxStages / kPairTiles];
     uint64_t tfull[2];
     uint64_t tempty[2];
     uint64_t a_ready;
@@ -269,7 +273,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
     using G = Geo<contraction_k(D)>;
     constexpr int kK = G::kK;
     constexpr uint32_t kTileBytes = G::kTileBytes, kABytes = G::kABytes, kSBO = G::kSBO;
-    constexpr int kStages = G::kStages, kAhead = G::kAhead;
+    constexpr int kStages = G::kStages, kSlots = G::kSlots;
+    constexpr uint32_t kSlotBytes = G::kSlotBytes;
     extern __shared__ __align__(kSmemAlign) unsigned char smem_raw[];
     __shared__ Shared S;
     __shared__ SphereProblem SP;  // the problem the CTA's walkers are on
@@ -283,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
     constexpr int kGeom = 4 * D + kMaxExp + kMaxExp * D;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < kSlots; ++s) {
             mbar_init(&S.full[s], 1);
             mbar_init(&S.empty[s], 1);
         }
@@ -329,60 +334,68 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
     if (warp == 4) {
         // ------------------------------------------------------------------ producer
         if (lane == 0) {
-            long long g_load = 0, g_mma = 0;
+            long long g_mma = 0;  // tiles multiplied so far (their parity picks the accumulator buffer)
             // the operand descriptors, built once: a descriptor of (addr + off) is the descriptor of
             // addr plus off / 16 while the address stays below 256 KB (its 14-bit field)
             const uint64_t a_desc = smem_desc(su32(A), kSBO);
             const uint64_t b_desc0 = smem_desc(su32(Bst), kSBO);
             constexpr uint64_t kKStep = (2 * kLBO) >> 4, kStageStep = kTileBytes >> 4;
-            RingPos lp, mp;  // ring slots of the next load and of the next MMA
+            RingPos lp, mp;  // ring slots of the next copy and of the next MMA's tile pair
+            long long g_load = 0, g_pair = 0;  // tile pairs copied and consumed so far
             bool ok = true;
             for (int step = 0; ok; ++step) {
                 if (!wait_bar(S, &S.a_ready, step & 1, L.status)) break;
                 if (S.stop) break;
                 // the problem of this step (the walkers change it only between steps)
                 const int T = SP.n_tiles;
+                const int n_pairs = (T + kPairTiles - 1) / kPairTiles;
                 const unsigned char *tiles = reinterpret_cast<const unsigned char *>(SP.tiles);
-                int t_load = 0;
+                int p_load = 0;
+                // copies pair p_load into the next slot, once the MMAs that read the slot last
+                // have completed; a slot is refilled at most kSlots - 1 pairs ahead of the MMAs
                 auto issue_load = [&]() -> bool {
                     const int s = lp.slot;
                     if (lp.round > 0 && !wait_bar(S, &S.empty[s], (lp.round - 1) & 1u, L.status)) return false;
-                    mbar_expect_tx(&S.full[s], kTileBytes);
-                    bulk_load_tile(su32(Bst) + s * kTileBytes, tiles + (size_t)t_load * kTileBytes, kTileBytes,
+                    const int nt = T - kPairTiles * p_load < kPairTiles ? T - kPairTiles * p_load : kPairTiles;
+                    mbar_expect_tx(&S.full[s], nt * kTileBytes);
+                    bulk_load_tile(su32(Bst) + s * kSlotBytes, tiles + (size_t)p_load * kSlotBytes, nt * kTileBytes,
                                    &S.full[s]);
-                    lp.next(kStages);
+                    lp.next(kSlots);
                     ++g_load;
-                    ++t_load;
+                    ++p_load;
                     return true;
                 };
-                while (ok && t_load < T && g_load < g_mma + kAhead) ok = issue_load();
+                while (ok && p_load < n_pairs && g_load < g_pair + kSlots - 1) ok = issue_load();
                 for (int t = 0; ok && t < T; ++t) {
-                    const int s = mp.slot;
+                    const int s = mp.slot, half = t % kPairTiles;
                     const int b = (int)(g_mma & 1);
-                    if (!wait_bar(S, &S.full[s], mp.round & 1u, L.status)) { ok = false; break; }
+                    if (half == 0 && !wait_bar(S, &S.full[s], mp.round & 1u, L.status)) { ok = false; break; }
                     if (g_mma >= 2 && !wait_bar(S, &S.tempty[b], (uint32_t)(((g_mma >> 1) - 1) & 1), L.status)) {
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint64_t b_desc = b_desc0 + (uint64_t)s * kStageStep;
+                    const uint64_t b_desc = b_desc0 + (uint64_t)(s * kPairTiles + half) * kStageStep;
 #pragma unroll
                     for (int kk = 0; kk < kK / 16; ++kk)
                         mma_bf16(tmem + b * kTileN, a_desc + kk * kKStep, b_desc + kk * kKStep, kk > 0);
                     mma_commit(&S.tfull[b]);
-                    mma_commit(&S.empty[s]);
-                    mp.next(kStages);
                     ++g_mma;
-                    while (ok && t_load < T && g_load < g_mma + kAhead) ok = issue_load();
+                    if (half == kPairTiles - 1 || t == T - 1) {  // the pair's last tile: release its slot
+                        mma_commit(&S.empty[s]);
+                        mp.next(kSlots);
+                        ++g_pair;
+                        while (ok && p_load < n_pairs && g_load < g_pair + kSlots - 1) ok = issue_load();
+                    }
                 }
             }
             // drain: every issued MMA completes before the tensor memory is freed; every issued
-            // load was consumed by an MMA, except after an abort
+            // copy was consumed by an MMA, except after an abort
             mma_commit(&S.drain);
             wait_bar(S, &S.drain, 0, L.status);
-            for (long long g = g_mma; g < g_load; ++g) {
+            for (long long g = g_pair; g < g_load; ++g) {
                 wait_bar(S, &S.full[mp.slot], mp.round & 1u, L.status);
-                mp.next(kStages);
+                mp.next(kSlots);
             }
         }
         __syncwarp();
