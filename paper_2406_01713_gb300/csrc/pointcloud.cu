@@ -117,7 +117,6 @@ __device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
 
 struct Shared {
     uint64_t full[kMaxStages / kPairTiles];
-    uint64_t empty[kMaxStages / kPairTiles];
     uint64_t tfull[2];
     uint64_t tempty[2];
     uint64_t a_ready;
@@ -290,7 +289,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
     if (threadIdx.x == 0) {
         for (int s = 0; s < kSlots; ++s) {
             mbar_init(&S.full[s], 1);
-            mbar_init(&S.empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&S.tfull[b], 1);
@@ -351,11 +349,15 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                 const int n_pairs = (T + kPairTiles - 1) / kPairTiles;
                 const unsigned char *tiles = reinterpret_cast<const unsigned char *>(SP.tiles);
                 int p_load = 0;
-                // copies pair p_load into the next slot, once the MMAs that read the slot last
-                // have completed; a slot is refilled at most kSlots - 1 pairs ahead of the MMAs
+                // copies pair p_load into the next slot, kSlots - 1 pairs ahead of the MMAs. The
+                // MMAs that read the slot last (those of the pair before the one just released)
+                // have completed: at a step start every walker has read the previous step's
+                // accumulators; within a step the released pair had two tiles, and the wait on
+                // the accumulator buffer of its second tile means the walkers have read the tile
+                // two before it, the previous pair's last (an MMA completes before its
+                // accumulators are signalled, and the MMAs of one thread complete in order)
                 auto issue_load = [&]() -> bool {
                     const int s = lp.slot;
-                    if (lp.round > 0 && !wait_bar(S, &S.empty[s], (lp.round - 1) & 1u, L.status)) return false;
                     const int nt = T - kPairTiles * p_load < kPairTiles ? T - kPairTiles * p_load : kPairTiles;
                     mbar_expect_tx(&S.full[s], nt * kTileBytes);
                     bulk_load_tile(su32(Bst) + s * kSlotBytes, tiles + (size_t)p_load * kSlotBytes, nt * kTileBytes,
@@ -381,8 +383,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                         mma_bf16(tmem + b * kTileN, a_desc + kk * kKStep, b_desc + kk * kKStep, kk > 0);
                     mma_commit(&S.tfull[b]);
                     ++g_mma;
-                    if (half == kPairTiles - 1 || t == T - 1) {  // the pair's last tile: release its slot
-                        mma_commit(&S.empty[s]);
+                    if (half == kPairTiles - 1 || t == T - 1) {  // the pair's last tile: move on
                         mp.next(kSlots);
                         ++g_pair;
                         while (ok && p_load < n_pairs && g_load < g_pair + kSlots - 1) ok = issue_load();
@@ -505,12 +506,18 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             float m1 = CUDART_INF_F, m2 = CUDART_INF_F, m3 = CUDART_INF_F;
             int c1 = 0, c2 = 0;
             bool ok = true;
+            // the chunk radius bounds of the next tile, fetched a tile ahead
+            float rhi_next[kTileN / kChunk];
+#pragma unroll
+            for (int c = 0; c < kTileN / kChunk; ++c) rhi_next[c] = __ldg(SP.chunk_rhi + c);
             for (int t = 0; t < T; ++t, ++g_epi) {
                 const int b = (int)(g_epi & 1);
-                // the chunk radius bounds of this tile, fetched while the MMA result is awaited
                 float rhi[kTileN / kChunk];
 #pragma unroll
-                for (int c = 0; c < kTileN / kChunk; ++c) rhi[c] = __ldg(SP.chunk_rhi + t * (kTileN / kChunk) + c);
+                for (int c = 0; c < kTileN / kChunk; ++c) {
+                    rhi[c] = rhi_next[c];
+                    rhi_next[c] = __ldg(SP.chunk_rhi + (t + 1 < T ? t + 1 : t) * (kTileN / kChunk) + c);
+                }
                 if (!warp_wait_bar(S, &S.tfull[b], (uint32_t)((g_epi >> 1) & 1), L.status)) {
                     ok = false;
                     break;
