@@ -212,24 +212,32 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-// The 64 accumulator columns of this thread's TMEM lane, loaded and waited for in one step.
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
-    uint32_t r[64];
+static_assert(kTileN == 64, "the epilogue reads a 64-column tile as two 32-column chunks");
+
+// 32 accumulator columns of this thread's TMEM lane, loaded and waited for in one step.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
 #define R8(i) "=r"(r[i]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), "=r"(r[i + 4]), "=r"(r[i + 5]), "=r"(r[i + 6]), "=r"(r[i + 7])
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%"
-        "28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,"
-        "%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n"
+        "28,%29,%30,%31}, [%32];\n"
         "tcgen05.wait::ld.sync.aligned;\n"
-        : R8(0), R8(8), R8(16), R8(24), R8(32), R8(40), R8(48), R8(56)
+        : R8(0), R8(8), R8(16), R8(24)
         : "r"(taddr)
         : "memory");
 #undef R8
 #pragma unroll
-    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
-static_assert(kTileN == 64, "the epilogue reads a 64-column tile with one tcgen05.ld");
+
+// A lower bound of sqrt(max(s, 0)): the hardware approximation scaled down by 2^-16, far more
+// than its error.
+__device__ __forceinline__ float sqrt_below(float s) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(fmaxf(s, 0.f)));
+    return r * 0.9999847412109375f;
+}
 
 __device__ __forceinline__ float min32(const float *v) {
     float m[11];
@@ -498,7 +506,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             if (lane == 0) mbar_arrive(&S.a_ready);
 
             // ---- epilogue: best and second-best 32-column chunk by the lower bound
-            //      sqrt(min D~ + |x|^2 - delta) - r_hi, D~ = |c|^2 - 2 x.c
+            //      sqrt(min D~ + |x|^2 - delta) - r_hi, D~ = |c|^2 - 2 x.c (the square root
+            //      rounded down); one 32-column TMEM load per chunk keeps registers free
             float xx = 0.f;
 #pragma unroll
             for (int i = 0; i < D; ++i) xx = fmaf(x[i], x[i], xx);
@@ -525,20 +534,21 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 float cmin[kTileN / kChunk];
                 {
-                    float v[kTileN];
-                    tmem_ld64(trow + b * kTileN, v);
+                    float v[kChunk];
+                    tmem_ld32(trow + b * kTileN, v);
+                    cmin[0] = min32(v);
+                    tmem_ld32(trow + b * kTileN + kChunk, v);
                     // the accumulator buffer is free as soon as its columns are in registers
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&S.tempty[b]);
-#pragma unroll
-                    for (int c = 0; c < kTileN / kChunk; ++c) cmin[c] = min32(v + kChunk * c);
+                    cmin[1] = min32(v);
                 }
 #pragma unroll
                 for (int c = 0; c < kTileN / kChunk; ++c) {
                     const int id = t * (kTileN / kChunk) + c;
                     const float cs = cmin[c] + xxd;
-                    const float cm = (cs > 0.f ? sqrtf(cs) : 0.f) - rhi[c];
+                    const float cm = sqrt_below(cs) - rhi[c];
                     // best, second and third bound; select form, no divergent branches
                     const bool lt1 = cm < m1, lt2 = cm < m2;
                     m3 = lt2 ? m2 : fminf(m3, cm);
