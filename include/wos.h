@@ -85,8 +85,8 @@ typedef enum {
 #define WOS_FLAG_GRAD_CONTROL_VARIATE 2
 
 /*
- * Ball sets of at least 512 balls run, in WOS_MIXED, on the tensor-core sphere-set
- * walker (the same walker as point sets: |c|^2 - 2 x.c by tcgen05.mma, exact FP32 refinement of
+ * Ball sets of at least 192 (d <= 3), 352 (d = 4..6) or 288 (d >= 7) balls run, in WOS_MIXED,
+ * on the tensor-core sphere-set walker (the same walker as point sets: |c|^2 - 2 x.c by tcgen05.mma, exact FP32 refinement of
  * the best 32-ball chunk, a proven lower bound for the rest). This flag keeps them on the
  * CUDA-core ball screen instead (for comparisons; both are exact up to their error bounds).
  */
@@ -177,7 +177,8 @@ wos_status wos_domain_set_exp_w(wos_domain_t dom, const double *w_device, int32_
 
 /*
  * Which walker the domain's obstacles run on in WOS_MIXED: *tensor_sphere_set = 1 if they form a
- * tensor-core sphere set (a point set, or at least 512 balls), with *sphere_tiles
+ * tensor-core sphere set (a point set, or a ball set of at least 192, 352 or 288 balls for
+ * d <= 3, 4..6, >= 7), with *sphere_tiles
  * 64-sphere tiles; 0 (and 0 tiles) for the CUDA-core walker. Host outputs; either may be NULL.
  * No counterpart in the paper (introspection for schedulers and benchmarks).
  * Errors: INVALID_ARG (NULL domain).
@@ -279,7 +280,7 @@ typedef struct {
  * persistent grids to a multiple of the SM count, and records one CUDA graph: [reset,
  * control-variate prepass (with WOS_FLAG_GRAD_CONTROL_VARIATE), the CUDA-core persistent walker
  * for the problems with small ball sets, in parallel one tensor-core sphere-set walker launch
- * per dimension for the problems with tensor-core sphere sets (>= 512 balls or a point set;
+ * per dimension for the problems with tensor-core sphere sets (large ball sets or a point set;
  * WOS_FLAG_CUDA_CORE_BALLS keeps ball sets off it), finalize]. Problems may differ in d,
  * obstacle count, walk budget, sigma and eps. Precision is WOS_MIXED. The problems' domains and
  * buffers must outlive the batch. Errors: INVALID_ARG, UNSUPPORTED (a domain with both balls

@@ -82,7 +82,7 @@ struct wos_domain_s {
     std::vector<float2 *> tables;
     float2 *table = nullptr;
     double table_zmax = 0;
-    PointCloudDev pcd{};  // tensor-core operands of the sphere set (point set or >= 512 balls)
+    PointCloudDev pcd{};  // tensor-core operands of the sphere set (point set or large ball set)
     bool has_pcd = false;
     float pc_delta = 0.f;
 };
@@ -892,7 +892,7 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
     // domains with an impulse source stay on the CUDA-core walker (the sphere-set walker has no
     // source term)
     const bool sphere_balls =
-        D->n_points == 0 && D->n_balls >= kSphereMinBalls && d <= kPointCloudMaxD && !D->has_source;
+        D->n_points == 0 && D->n_balls >= sphere_min_balls(d) && d <= kPointCloudMaxD && !D->has_source;
     if ((D->n_points > 0 && d <= kPointCloudMaxD) || sphere_balls) {
         e = sphere_balls ? pointcloud_prepare(D->ball_c.data(), D->ball_r.data(), D->n_balls, d, &D->pcd)
                          : pointcloud_prepare(D->points.data(), nullptr, D->n_points, d, &D->pcd);

@@ -179,6 +179,9 @@ cudaError_t launch_pointcloud(const PointCloudDev &pcd, const MixedProblem &P, f
                               uint64_t seed, int64_t max_steps, int grad, cudaStream_t s,
                               double *radius_out = nullptr);
 constexpr int kPointCloudMaxD = 12;  // 3d + 2 BF16 columns fit a 32- or 48-wide contraction
-constexpr int kSphereMinBalls = 512; // ball sets at least this large run on the tensor cores
+// Ball sets at least this large run on the tensor cores: the measured crossover of the two
+// walkers (u and grad u, 64 queries x 16384 walks per ball set) lies near 160 balls at d = 3,
+// 330 at d = 5 and 256 for d = 8..12; the thresholds sit a little above it.
+constexpr int sphere_min_balls(int d) { return d <= 3 ? 192 : (d <= 6 ? 352 : 288); }
 
 }  // namespace wos
