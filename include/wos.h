@@ -85,7 +85,7 @@ typedef enum {
 #define WOS_FLAG_GRAD_CONTROL_VARIATE 2
 
 /*
- * Ball sets of at least 192 (d <= 3), 352 (d = 4..6) or 288 (d >= 7) balls run, in WOS_MIXED,
+ * Ball sets of at least 192 (d <= 4), 320 (d = 5, 6) or 288 (d >= 7) balls run, in WOS_MIXED,
  * on the tensor-core sphere-set walker (the same walker as point sets: |c|^2 - 2 x.c by tcgen05.mma, exact FP32 refinement of
  * the best 32-ball chunk, a proven lower bound for the rest). This flag keeps them on the
  * CUDA-core ball screen instead (for comparisons; both are exact up to their error bounds).
@@ -177,8 +177,8 @@ wos_status wos_domain_set_exp_w(wos_domain_t dom, const double *w_device, int32_
 
 /*
  * Which walker the domain's obstacles run on in WOS_MIXED: *tensor_sphere_set = 1 if they form a
- * tensor-core sphere set (a point set, or a ball set of at least 192, 352 or 288 balls for
- * d <= 3, 4..6, >= 7), with *sphere_tiles
+ * tensor-core sphere set (a point set, or a ball set of at least 192, 320 or 288 balls for
+ * d <= 4, d = 5, 6, d >= 7), with *sphere_tiles
  * 64-sphere tiles; 0 (and 0 tiles) for the CUDA-core walker. Host outputs; either may be NULL.
  * No counterpart in the paper (introspection for schedulers and benchmarks).
  * Errors: INVALID_ARG (NULL domain).

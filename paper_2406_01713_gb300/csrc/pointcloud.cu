@@ -499,7 +499,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                 }
                 continue;
             }
+            // the problem record lives in shared memory, which the waits' memory clobbers force to
+            // be re-read at every use: its fields for this step go to registers once
             const int T = SP.n_tiles;
+            const float *const soa = SP.soa;
+            const float *const chunk_rhi = SP.chunk_rhi;
             write_row<D>(A, r, x, active);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
@@ -518,14 +522,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             // the chunk radius bounds of the next tile, fetched a tile ahead
             float rhi_next[kTileN / kChunk];
 #pragma unroll
-            for (int c = 0; c < kTileN / kChunk; ++c) rhi_next[c] = __ldg(SP.chunk_rhi + c);
+            for (int c = 0; c < kTileN / kChunk; ++c) rhi_next[c] = __ldg(chunk_rhi + c);
             for (int t = 0; t < T; ++t, ++g_epi) {
                 const int b = (int)(g_epi & 1);
                 float rhi[kTileN / kChunk];
 #pragma unroll
                 for (int c = 0; c < kTileN / kChunk; ++c) {
                     rhi[c] = rhi_next[c];
-                    rhi_next[c] = __ldg(SP.chunk_rhi + (t + 1 < T ? t + 1 : t) * (kTileN / kChunk) + c);
+                    rhi_next[c] = __ldg(chunk_rhi + (t + 1 < T ? t + 1 : t) * (kTileN / kChunk) + c);
                 }
                 if (!warp_wait_bar(S, &S.tfull[b], (uint32_t)((g_epi >> 1) & 1), L.status)) {
                     ok = false;
@@ -595,7 +599,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
 #pragma unroll
                     for (int u = 0; u < kRefineGroup; ++u) {
                         const float *ch =
-                            SP.soa + (long long)__shfl_sync(0xffffffffu, cc, w0 + u) * chunk_floats(D);
+                            soa + (long long)__shfl_sync(0xffffffffu, cc, w0 + u) * chunk_floats(D);
                         cen[u] = reinterpret_cast<const float4 *>(ch + lane * kP);
                         rr[u] = __ldg(ch + kChunk * kP + lane);
                         s2[u] = 0.f;
@@ -714,7 +718,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                 for (int i = 0; i < D; ++i) xb[i] = x[i];
                 if (kind == kPoint) {
                     // closest point of the sphere (c, r): c + r (x - c)/|x - c|; c itself for a point
-                    const float *ch = SP.soa + (long long)(idx / kChunk) * chunk_floats(D);
+                    const float *ch = soa + (long long)(idx / kChunk) * chunk_floats(D);
                     const float *c = ch + (idx % kChunk) * chunk_pitch(D);
                     const float rad = __ldg(ch + kChunk * chunk_pitch(D) + idx % kChunk);
                     float s = 0.f;

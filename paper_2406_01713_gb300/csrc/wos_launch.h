@@ -181,7 +181,7 @@ cudaError_t launch_pointcloud(const PointCloudDev &pcd, const MixedProblem &P, f
 constexpr int kPointCloudMaxD = 12;  // 3d + 2 BF16 columns fit a 32- or 48-wide contraction
 // Ball sets at least this large run on the tensor cores: the measured crossover of the two
 // walkers (u and grad u, 64 queries x 16384 walks per ball set) lies near 160 balls at d = 3,
-// 330 at d = 5 and 256 for d = 8..12; the thresholds sit a little above it.
-constexpr int sphere_min_balls(int d) { return d <= 3 ? 192 : (d <= 6 ? 352 : 288); }
+// below 224 at d = 4, near 330 at d = 5, 320 at d = 6, 288 at d = 7 and 256 for d = 8..12.
+constexpr int sphere_min_balls(int d) { return d <= 4 ? 192 : (d <= 6 ? 320 : 288); }
 
 }  // namespace wos
