@@ -45,8 +45,10 @@ constexpr int kPairTiles = 2;  // centre tiles per bulk copy (consecutive in mem
 constexpr int kCtasPerSm = 4;    // 4 x 128 TMEM columns; registers <= 102 per thread
 constexpr int kChunk = 32;       // candidate chunk (columns)
 constexpr int kRefineGroup = 4;  // walkers whose chunk refinements a warp keeps in flight together
-// A chunk in memory: its kChunk centres sphere-major, each padded with zeros to a multiple of
-// four coordinates (one 16-byte load per four), then its kChunk radii.
+// A chunk in memory: its kChunk centres padded with zeros to a multiple of four coordinates and
+// stored by coordinate quads (quad q: coordinates 4q..4q+3 of sphere 0, of sphere 1, ...), so
+// that one 16-byte load per lane reads a quad of all 32 spheres in 512 contiguous bytes; then
+// its kChunk radii.
 __host__ __device__ constexpr int chunk_pitch(int d) { return (d + 3) & ~3; }
 __host__ __device__ constexpr int chunk_floats(int d) { return kChunk * (chunk_pitch(d) + 1); }
 constexpr int kWalkerThreads = 128;
@@ -600,7 +602,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                     for (int u = 0; u < kRefineGroup; ++u) {
                         const float *ch =
                             soa + (long long)__shfl_sync(0xffffffffu, cc, w0 + u) * chunk_floats(D);
-                        cen[u] = reinterpret_cast<const float4 *>(ch + lane * kP);
+                        cen[u] = reinterpret_cast<const float4 *>(ch) + lane;
                         rr[u] = __ldg(ch + kChunk * kP + lane);
                         s2[u] = 0.f;
                     }
@@ -608,7 +610,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                     for (int i4 = 0; i4 < kP / 4; ++i4) {
 #pragma unroll
                         for (int u = 0; u < kRefineGroup; ++u) {
-                            const float4 c = __ldg(cen[u] + i4);
+                            const float4 c = __ldg(cen[u] + i4 * kChunk);
                             const float4 xv = *reinterpret_cast<const float4 *>(xs + (w0 + u) * kP + 4 * i4);
                             // zero padding adds exact zeros: the sum is the d-term sum in order
                             float t0 = xv.x - c.x;
@@ -719,15 +721,18 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                 if (kind == kPoint) {
                     // closest point of the sphere (c, r): c + r (x - c)/|x - c|; c itself for a point
                     const float *ch = soa + (long long)(idx / kChunk) * chunk_floats(D);
-                    const float *c = ch + (idx % kChunk) * chunk_pitch(D);
+                    const float *c = ch + (idx % kChunk) * 4;  // coordinate i at c[(i / 4) 4 kChunk + i % 4]
                     const float rad = __ldg(ch + kChunk * chunk_pitch(D) + idx % kChunk);
+                    float cv[D];
+#pragma unroll
+                    for (int i = 0; i < D; ++i) cv[i] = __ldg(c + (i / 4) * 4 * kChunk + i % 4);
                     float s = 0.f;
 #pragma unroll
-                    for (int i = 0; i < D; ++i) s = fmaf(x[i] - __ldg(c + i), x[i] - __ldg(c + i), s);
+                    for (int i = 0; i < D; ++i) s = fmaf(x[i] - cv[i], x[i] - cv[i], s);
                     const float len = sqrtf(s);
                     const float f = len > 0.f ? rad / len : 0.f;
 #pragma unroll
-                    for (int i = 0; i < D; ++i) xb[i] = fmaf(f, x[i] - __ldg(c + i), __ldg(c + i));
+                    for (int i = 0; i < D; ++i) xb[i] = fmaf(f, x[i] - cv[i], cv[i]);
                 } else if (kind == kFace) {
 #pragma unroll
                     for (int i = 0; i < D; ++i)
@@ -830,7 +835,7 @@ cudaError_t pointcloud_prepare(const double *pts, const double *radii, int64_t M
         float p[WOS_MAX_D];
         double nn = 0.0;
         float *chunk = hsoa.data() + (size_t)(i / pc::kChunk) * pc::chunk_floats(d);
-        float *centre = chunk + (size_t)(i % pc::kChunk) * pc::chunk_pitch(d);
+        float *centre = chunk + (size_t)(i % pc::kChunk) * 4;  // coordinate j at [(j / 4) 4 kChunk + j % 4]
         if (real && radii != nullptr) {
             const float r32 = (float)radii[src];
             chunk[(size_t)pc::kChunk * pc::chunk_pitch(d) + (size_t)(i % pc::kChunk)] = r32;
@@ -842,7 +847,7 @@ cudaError_t pointcloud_prepare(const double *pts, const double *radii, int64_t M
         for (int j = 0; j < d; ++j) {
             // padding centres sit far outside any domain: they never win the minimum
             p[j] = real ? (float)pts[src * d + j] : 1.0e3f;
-            centre[j] = p[j];
+            centre[(size_t)(j / 4) * 4 * pc::kChunk + (size_t)(j % 4)] = p[j];
             nn += (double)p[j] * (double)p[j];
             if (real) pmax = std::max(pmax, std::fabs((double)p[j]));
         }

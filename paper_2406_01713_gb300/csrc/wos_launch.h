@@ -132,7 +132,7 @@ inline int max_active_mixed(int threads, size_t smem_bytes, int grad_any) {
 // chunk from above.
 struct PointCloudDev {
     void *tiles = nullptr;      // n_tiles x 4 KB BF16 tiles, already in the shared-memory layout
-    float *soa = nullptr;       // per 32-sphere chunk: 32 centres padded to 4k floats, then 32 radii
+    float *soa = nullptr;       // per 32-sphere chunk: centres by coordinate quads, then 32 radii
     float *chunk_rhi = nullptr; // largest radius of each 32-column chunk (rounded up)
     int n_tiles = 0;
     int spheres = 0;            // 1: balls with radii; 0: points
