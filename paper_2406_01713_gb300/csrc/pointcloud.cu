@@ -233,13 +233,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// A lower bound of sqrt(max(s, 0)): the hardware approximation scaled down by 2^-16, far more
-// than its error.
-__device__ __forceinline__ float sqrt_below(float s) {
+// Lower bounds of sqrt(max(s, 0)) from the hardware approximation, whose excess over the exact
+// root was measured below 2^-23.6 on every float in [2^-40, 2^40): scaled down by 2^-16 (chunk
+// bounds) or 2^-22 (refined distances, which stay within an FP32 rounding of the exact value).
+__device__ __forceinline__ float sqrt_approx(float s) {
     float r;
     asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(fmaxf(s, 0.f)));
-    return r * 0.9999847412109375f;
+    return r;
 }
+__device__ __forceinline__ float sqrt_below(float s) { return sqrt_approx(s) * 0.9999847412109375f; }
+__device__ __forceinline__ float sqrt_below_tight(float s) { return sqrt_approx(s) * 0.999999761581420898f; }
 
 __device__ __forceinline__ float min32(const float *v) {
     float m[11];
@@ -597,34 +600,37 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                 for (int w0 = 0; w0 < 32; w0 += kRefineGroup) {
                     if (((todo >> w0) & ((1u << kRefineGroup) - 1u)) == 0u) continue;
                     const float4 *cen[kRefineGroup];
-                    float s2[kRefineGroup], rr[kRefineGroup];
+                    float rr[kRefineGroup];
+                    f32x2 s01[kRefineGroup], s23[kRefineGroup];  // packed partial sums of (x - c)^2
 #pragma unroll
                     for (int u = 0; u < kRefineGroup; ++u) {
                         const float *ch =
                             soa + (long long)__shfl_sync(0xffffffffu, cc, w0 + u) * chunk_floats(D);
                         cen[u] = reinterpret_cast<const float4 *>(ch) + lane;
                         rr[u] = __ldg(ch + kChunk * kP + lane);
-                        s2[u] = 0.f;
+                        s01[u] = 0ull;
+                        s23[u] = 0ull;
                     }
+                    const f32x2 neg1 = pack2(-1.f, -1.f);
 #pragma unroll
                     for (int i4 = 0; i4 < kP / 4; ++i4) {
 #pragma unroll
                         for (int u = 0; u < kRefineGroup; ++u) {
                             const float4 c = __ldg(cen[u] + i4 * kChunk);
                             const float4 xv = *reinterpret_cast<const float4 *>(xs + (w0 + u) * kP + 4 * i4);
-                            // zero padding adds exact zeros: the sum is the d-term sum in order
-                            float t0 = xv.x - c.x;
-                            s2[u] = fmaf(t0, t0, s2[u]);
-                            t0 = xv.y - c.y;
-                            s2[u] = fmaf(t0, t0, s2[u]);
-                            t0 = xv.z - c.z;
-                            s2[u] = fmaf(t0, t0, s2[u]);
-                            t0 = xv.w - c.w;
-                            s2[u] = fmaf(t0, t0, s2[u]);
+                            // x - c exactly rounded (fma with -1), squares summed in four packed
+                            // lanes; zero padding adds exact zeros
+                            const f32x2 t01 = ffma2(pack2(c.x, c.y), neg1, pack2(xv.x, xv.y));
+                            const f32x2 t23 = ffma2(pack2(c.z, c.w), neg1, pack2(xv.z, xv.w));
+                            s01[u] = ffma2(t01, t01, s01[u]);
+                            s23[u] = ffma2(t23, t23, s23[u]);
                         }
                     }
 #pragma unroll
-                    for (int u = 0; u < kRefineGroup; ++u) tr[(w0 + u) * kTrPitch + lane] = sqrtf(s2[u]) - rr[u];
+                    for (int u = 0; u < kRefineGroup; ++u) {
+                        const float2 a = unpack2(s01[u]), b = unpack2(s23[u]);
+                        tr[(w0 + u) * kTrPitch + lane] = sqrt_below_tight((a.x + b.x) + (a.y + b.y)) - rr[u];
+                    }
                 }
                 __syncwarp();
                 // walker w scans its own row (lowest index on ties)
