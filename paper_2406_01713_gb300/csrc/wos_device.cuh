@@ -81,7 +81,11 @@ __device__ __forceinline__ void direction_f64(uint64_t seed, uint64_t walk, uint
 }
 
 // FP32 direction from the same counters: u1 = (top 24 bits + 1) 2^-24, u2 = top 24 bits 2^-24.
-// FAST selects the SFU log approximation (mixed walkers) instead of logf (plain baseline).
+// FAST (mixed walkers) takes the SFU approximations of log, square root, sine and cosine; the
+// angle 2 pi u2 is evaluated as -(cos, sin)(2 pi u2 - pi), inside the range where the SFU sine
+// and cosine are accurate, so the direction is the one of the exact sampler up to errors of
+// order 1e-7 (it is normalised after) and the walks keep the same random stream as the FP64
+// ones. Without FAST (plain baseline): logf, sqrtf and sincospif of 2 u2.
 template <int D, bool FAST>
 __device__ __forceinline__ void direction_f32(uint64_t seed, uint64_t walk, uint32_t step,
                                               float (&v)[D]) {
@@ -96,10 +100,15 @@ __device__ __forceinline__ void direction_f32(uint64_t seed, uint64_t walk, uint
             if (i < D) {
                 const float u1 = (float)((rr[2 * p] >> 8) + 1u) * kInv24;
                 const float u2 = (float)(rr[2 * p + 1] >> 8) * kInv24;
-                const float lg = FAST ? __logf(u1) : logf(u1);
-                const float rad = sqrtf(-2.0f * lg);
-                float s, c;
-                sincospif(2.0f * u2, &s, &c);
+                float rad, s, c;
+                if (FAST) {
+                    asm("sqrt.approx.f32 %0, %1;" : "=f"(rad) : "f"(-2.0f * __logf(u1)));
+                    __sincosf(fmaf(6.283185307179586f, u2, -3.141592653589793f), &s, &c);
+                    rad = -rad;
+                } else {
+                    rad = sqrtf(-2.0f * logf(u1));
+                    sincospif(2.0f * u2, &s, &c);
+                }
                 v[i] = rad * c;
                 if (i + 1 < D) v[i + 1] = rad * s;
             }
