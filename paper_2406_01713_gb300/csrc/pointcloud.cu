@@ -160,8 +160,11 @@ __device__ __forceinline__ bool wait_bar(Shared &S, uint64_t *b, uint32_t parity
     }
 }
 
-// Warp-uniform bounded wait for the walker warps: lane 0 polls, every lane gets the result.
+// Warp-uniform bounded wait for the walker warps: every lane tests the phase once (a broadcast
+// read, no divergence in the common case); if it is still open, lane 0 polls with the budget and
+// every lane gets the result.
 __device__ __forceinline__ bool warp_wait_bar(Shared &S, uint64_t *b, uint32_t parity, int *status) {
+    if (__any_sync(0xffffffffu, mbar_test(b, parity))) return true;
     int ok = 0;
     if ((threadIdx.x & 31) == 0) ok = wait_bar(S, b, parity, status) ? 1 : 0;
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
@@ -524,18 +527,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             float m1 = CUDART_INF_F, m2 = CUDART_INF_F, m3 = CUDART_INF_F;
             int c1 = 0, c2 = 0;
             bool ok = true;
-            // the chunk radius bounds of the next tile, fetched a tile ahead
-            float rhi_next[kTileN / kChunk];
-#pragma unroll
-            for (int c = 0; c < kTileN / kChunk; ++c) rhi_next[c] = __ldg(chunk_rhi + c);
+            // the chunk radius bounds of the next tile (one 8-byte load), fetched a tile ahead
+            static_assert(kTileN / kChunk == 2, "two chunk bounds per tile");
+            const float2 *const rhi2 = reinterpret_cast<const float2 *>(chunk_rhi);
+            float2 rhi_next = __ldg(rhi2);
             for (int t = 0; t < T; ++t, ++g_epi) {
                 const int b = (int)(g_epi & 1);
-                float rhi[kTileN / kChunk];
-#pragma unroll
-                for (int c = 0; c < kTileN / kChunk; ++c) {
-                    rhi[c] = rhi_next[c];
-                    rhi_next[c] = __ldg(chunk_rhi + (t + 1 < T ? t + 1 : t) * (kTileN / kChunk) + c);
-                }
+                const float rhi[kTileN / kChunk] = {rhi_next.x, rhi_next.y};
+                rhi_next = __ldg(rhi2 + (t + 1 < T ? t + 1 : t));
                 if (!warp_wait_bar(S, &S.tfull[b], (uint32_t)((g_epi >> 1) & 1), L.status)) {
                     ok = false;
                     break;
