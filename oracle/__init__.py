@@ -62,6 +62,7 @@ class _Domain(ctypes.Structure):
         ("has_source", ctypes.c_int32),
         ("source_z", ctypes.c_double * MAXD),
         ("source_q", ctypes.c_double),
+        ("proj_dims", ctypes.c_int32),
     ]
 
 
@@ -192,6 +193,7 @@ class Domain:
             s.has_source = 1
             s.source_z[:d] = list(np.asarray(dom["source_z"], float))
             s.source_q = float(dom.get("source_q", 1.0))
+        s.proj_dims = int(dom.get("proj_dims", 0))
         self.n_exp = int(s.n_exp)
         self.s = s
 

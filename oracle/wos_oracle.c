@@ -39,6 +39,11 @@
  *       x <- x + s grad/|grad|,  s = min(s_ub, 0.5 d_bound).
  *   Distance functions (Sec. VI, Eq. for d(x, dOmega); Sec. VII-A point-set distance):
  *       balls: |x - c| - r;  outer ball: r_o - |x - c_o|;  points: |x - p|;  box faces.
+ *   Extruded domains (Sec. VI, dimensionality study): with proj_dims = m < d every boundary
+ *       component is measured in the first m coordinates only (the obstacles and the outer
+ *       boundary extruded along the others, which are free and unbounded); walks, sources and
+ *       boundary data stay d-dimensional, and the closest boundary point keeps the free
+ *       coordinates of x.
  *
  * Readings where the paper is silent (random stream, ties, caps) follow the build's
  * documented contract:
@@ -90,6 +95,7 @@ typedef struct {
     int32_t has_source;   /* 1: impulse source of strength source_q at source_z */
     double source_z[OR_MAXD];
     double source_q;
+    int32_t proj_dims;    /* 0 or d: distances in all coordinates; m < d: in the first m only */
 } or_domain;
 
 typedef struct {
@@ -268,31 +274,37 @@ static double norm_diff(int d, const double *a, const double *b)
     return sqrt(s);
 }
 
+/* Coordinates the boundary components are measured in: the first m of d. */
+static int obstacle_dims(const or_domain *D)
+{
+    return D->proj_dims > 0 && D->proj_dims < D->d ? D->proj_dims : D->d;
+}
+
 double or_distance(const or_domain *D, const double *x, int32_t *kind, int64_t *index,
                    double *xbar)
 {
-    const int d = D->d;
+    const int d = D->d, m = obstacle_dims(D);
     double best = INFINITY;
     int32_t bk = -1;
     int64_t bi = -1;
     if (D->has_goal) {
-        double r = norm_diff(d, x, D->goal_c) - D->goal_r;
+        double r = norm_diff(m, x, D->goal_c) - D->goal_r;
         if (r < best) { best = r; bk = OR_KIND_GOAL; bi = 0; }
     }
     for (int32_t i = 0; i < D->n_balls; ++i) {
-        double r = norm_diff(d, x, D->ball_c + (int64_t)i * d) - D->ball_r[i];
+        double r = norm_diff(m, x, D->ball_c + (int64_t)i * d) - D->ball_r[i];
         if (r < best) { best = r; bk = OR_KIND_BALL; bi = i; }
     }
     for (int64_t i = 0; i < D->n_points; ++i) {
-        double r = norm_diff(d, x, D->points + i * d);
+        double r = norm_diff(m, x, D->points + i * d);
         if (r < best) { best = r; bk = OR_KIND_POINT; bi = i; }
     }
     if (D->has_outer) {
-        double r = D->outer_r - norm_diff(d, x, D->outer_c);
+        double r = D->outer_r - norm_diff(m, x, D->outer_c);
         if (r < best) { best = r; bk = OR_KIND_OUTER; bi = 0; }
     }
     if (D->has_box) {
-        for (int j = 0; j < d; ++j) {
+        for (int j = 0; j < m; ++j) {
             double rlo = x[j] - D->box_lo[j];
             if (rlo < best) { best = rlo; bk = OR_KIND_FACE; bi = 2 * j; }
             double rhi = D->box_hi[j] - x[j];
@@ -302,18 +314,20 @@ double or_distance(const or_domain *D, const double *x, int32_t *kind, int64_t *
     if (kind) *kind = bk;
     if (index) *index = bi;
     if (xbar) {
-        /* projection of x on the nearest component */
+        /* projection of x on the nearest component (in the first m coordinates; the others are
+           those of x) */
         const double *c = NULL;
         double rad = 0.0;
         if (bk == OR_KIND_GOAL) { c = D->goal_c; rad = D->goal_r; }
         if (bk == OR_KIND_BALL) { c = D->ball_c + bi * d; rad = D->ball_r[bi]; }
         if (bk == OR_KIND_OUTER) { c = D->outer_c; rad = D->outer_r; }
+        for (int j = m; j < d; ++j) xbar[j] = x[j];
         if (c) {
-            double len = norm_diff(d, x, c);
-            for (int j = 0; j < d; ++j)
+            double len = norm_diff(m, x, c);
+            for (int j = 0; j < m; ++j)
                 xbar[j] = len > 0.0 ? c[j] + rad * (x[j] - c[j]) / len : c[j] + (j == 0 ? rad : 0.0);
         } else if (bk == OR_KIND_POINT) {
-            for (int j = 0; j < d; ++j) xbar[j] = D->points[bi * d + j];
+            for (int j = 0; j < m; ++j) xbar[j] = D->points[bi * d + j];
         } else if (bk == OR_KIND_FACE) {
             for (int j = 0; j < d; ++j) xbar[j] = x[j];
             int j = (int)(bi / 2);
@@ -529,6 +543,7 @@ int or_solve(const or_domain *D, const double *X, int64_t Q, int64_t N, int64_t 
              int64_t *walk_jumps, double *walk_grad, double *walk_dsigma)
 {
     if (!D || !X || !opt || D->d < 1 || D->d > OR_MAXD || D->n_exp < 0 || D->n_exp > OR_MAXEXP ||
+        D->proj_dims < 0 || D->proj_dims > D->d ||
         Q < 0 || N < 1 || sigma < 0.0)
         return -1;
     const int d = D->d, K = D->n_exp;
@@ -652,7 +667,7 @@ int64_t or_plan_path(const or_domain *D, const double *x0, int64_t n_steps, int6
     for (int64_t i = 0; i < n_steps; ++i) {
         flags[i] = 0;
         if (D->has_goal) {
-            double rg = norm_diff(d, x, D->goal_c) - D->goal_r;
+            double rg = norm_diff(obstacle_dims(D), x, D->goal_c) - D->goal_r;
             if (rg < eps) {
                 flags[i] = 1;
                 break;

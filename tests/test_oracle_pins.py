@@ -13,6 +13,8 @@ never against the oracle itself.
   * derivative in sigma: closed form at the ball centre, common-random-number FD (P8)
   * derivative in w: linear, FD exact (P9); max principle (P6); SE ~ N^-1/2 (P7)
   * planner: adaptive step s = min(s_ub, d/2) and radial descent in the annulus
+  * extruded domains (Sec. VI dimensionality study): nearest-point geometry against sampled
+    cylinder surfaces, and the exp closed form with a along all or only the free coordinates
 and one planted mistake (the paper's literal d/R gradient factor at sigma > 0), which the
 off-centre ball pin must reject.
 """
@@ -534,3 +536,84 @@ def test_off_centre_source_kelvin_image(oracle_mod):
         g = (-a / np.linalg.norm(a) ** 3 + b / (np.linalg.norm(z) * np.linalg.norm(b) ** 3)) / (4 * math.pi)
         assert abs(res["u"][q] - u) < 4.5 * res["u_se"][q] + 1e-4 * abs(u)
         assert np.all(np.abs(res["grad"][q] - g) < 4.5 * res["grad_se"][q] + 1e-3 * np.abs(g).max())
+
+
+# --------------------------------------------------------------------------- extruded domains
+def _extruded_env(d, scale=1.0, k_r=0.3):
+    """The paper's two-disc environment (Sec. VI) with r_o = scale, extruded along coordinates
+    3..d: every component is measured in the first two coordinates, the others are free."""
+    r_o = scale
+    r_u = k_r * r_o
+    r_l = 0.5 * r_u
+    c = np.zeros((2, d))
+    c[0, 1], c[1, 1] = r_u, -r_l
+    return {"d": d, "outer_c": np.zeros(d), "outer_r": r_o, "ball_c": c, "ball_r": np.array([r_u, r_l]),
+            "proj_dims": 2}
+
+
+def _free_cross_section(rng, n, dom):
+    """n points of the free cross-section (first two coordinates), free coordinates in [-2, 2]."""
+    out = []
+    while len(out) < n:
+        p = rng.uniform(-dom["outer_r"], dom["outer_r"], size=2)
+        if np.linalg.norm(p) > 0.95 * dom["outer_r"]:
+            continue
+        if any(np.linalg.norm(p - c[:2]) < 1.05 * r for c, r in zip(dom["ball_c"], dom["ball_r"])):
+            continue
+        out.append(np.concatenate([p, rng.uniform(-2, 2, size=dom["d"] - 2)]))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("d", [3, 5])
+def test_extruded_distance_geometry(oracle_mod, d):
+    # a component's surface is its cross-section circle times R^(d-2): the nearest point keeps
+    # the free coordinates, lies on the boundary at distance R, and no sampled surface point is
+    # nearer (with x's free coordinates or any others)
+    dom = _extruded_env(d)
+    rng = np.random.default_rng(d)
+    t = np.linspace(0, 2 * math.pi, 721)
+    circles = [(np.zeros(2), dom["outer_r"])] + [(c[:2], r) for c, r in zip(dom["ball_c"], dom["ball_r"])]
+    for x in _free_cross_section(rng, 60, dom):
+        R, kind, idx, xbar = oracle_mod.distance(dom, x)
+        assert R > 0
+        assert abs(np.linalg.norm(x - xbar) - R) < 1e-12
+        assert np.array_equal(xbar[2:], x[2:])
+        R2, _, _, _ = oracle_mod.distance(dom, xbar)
+        assert abs(R2) < 1e-12
+        for c, r in circles:
+            ring = c[None, :] + r * np.stack([np.cos(t), np.sin(t)], 1)
+            for free in (x[2:], rng.uniform(-3, 3, size=d - 2)):
+                pts = np.concatenate([ring, np.repeat(free[None, :], len(t), 0)], 1)
+                assert np.min(np.linalg.norm(pts - x[None, :], axis=1)) >= R - 1e-12
+
+
+@pytest.mark.parametrize("d,free_only", [(3, False), (4, True)])
+def test_extruded_exp_data_exact_solution(oracle_mod, d, free_only):
+    # exp(a.x) with |a|^2 = sigma solves the PDE in all of R^d, so with g = exp(a.x) on the
+    # extruded boundary it is the solution; a along the free coordinates only tests that the
+    # nearest boundary point keeps them
+    sigma = 1.0
+    rng = np.random.default_rng(40 + d)
+    a = np.zeros(d)
+    if free_only:
+        a[2:] = rng.standard_normal(d - 2)
+    else:
+        a = rng.standard_normal(d)
+    a *= math.sqrt(sigma) / np.linalg.norm(a)
+    dom = dict(_extruded_env(d), exp_w=np.ones(1), exp_a=a[None, :])
+    X = _free_cross_section(rng, 4, dom)
+    res = oracle_mod.solve(dom, X, 6000, 1e-4, sigma, seed=5, grad=True)
+    g = np.exp(X @ a)
+    bias = 3e-4 * g
+    assert np.all(res["capped"] == 0) and np.all(res["outside"] == 0)
+    assert np.all(np.abs(res["u"] - g) < 4.5 * res["u_se"] + bias)
+    assert np.all(np.abs(res["grad"] - a[None, :] * g[:, None]) < 4.5 * res["grad_se"] + 10 * bias[:, None])
+
+
+def test_full_projection_is_the_plain_domain(oracle_mod):
+    # proj_dims = d measures every component in all coordinates: the same walks as without it
+    w = synth.c1(n_queries=4)
+    dom = dict(w["domain"])
+    a = oracle_mod.solve(dom, w["X"], 500, 1e-3, w["sigma"], w["seed"], grad=True)
+    b = oracle_mod.solve(dict(dom, proj_dims=2), w["X"], 500, 1e-3, w["sigma"], w["seed"], grad=True)
+    assert np.array_equal(a["u"], b["u"]) and np.array_equal(a["grad"], b["grad"])
