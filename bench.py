@@ -523,6 +523,64 @@ def plain_comparison(W, doms, probs, seed, mixed_steps, mixed_s, mixed_rmse, cv=
             "note": "same walk counts; plain launched per problem (256 launches)"}
 
 
+def _path_length(path, flags):
+    """Length of a planner path up to the goal (or to its end) and the step that reached it."""
+    p, f = path.cpu().numpy(), flags.cpu().numpy()
+    hit = int(np.argmax(f == 1)) if (f == 1).any() else None
+    q = p[: (hit + 1 if hit is not None else len(p))]
+    return float(np.linalg.norm(np.diff(q, axis=0), axis=1).sum()), hit
+
+
+def paper_sweeps(W, synth):
+    """The paper's evaluation studies (Sec. VI) in its two-disc environment with the unit
+    impulse at the goal, eps = 0.01, start (-8, 0, ...):
+      * dimensionality (Fig. 10): angle error of grad u against a 2^26-walk reference at the
+        start, d = 2..5 (extruded), N = 10^3..10^6 walks, and the device time per estimate;
+      * screening (Fig. 6): planner paths for c in {10, 1, 0.1} at k_r = 0.4 (10^4 walks);
+      * visibility (Fig. 7): planner paths for k_r in {0.3, 0.45, 0.6} at c = 1 (10^5 walks).
+    Paths: s_ub = 0.1, at most 400 steps; the length is measured up to the goal."""
+    import torch
+
+    eps = 0.01
+    dims = {}
+    for d in (2, 3, 4, 5):
+        dom = W.Domain(synth.paper_environment(d))
+        x = np.zeros((1, d))
+        x[0, 0] = -8.0
+        ref = dom.grad(x, 1 << 26, eps, 1.0, seed=1, control_variate=True)["grad"].cpu().numpy()[0]
+        row = {}
+        for n in (10 ** 3, 10 ** 4, 10 ** 5, 10 ** 6):
+            reps = 16 if n < 10 ** 6 else 4
+            errs, ts = [], []
+            for r in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                g = dom.grad(x, n, eps, 1.0, seed=1000 + r, control_variate=True)["grad"]
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+                g = g.cpu().numpy()[0]
+                c = float(np.dot(g, ref) / (np.linalg.norm(g) * np.linalg.norm(ref)))
+                errs.append(math.degrees(math.acos(max(-1.0, min(1.0, c)))))
+            row[str(n)] = {"angle_error_deg": float(np.mean(errs)), "ms_per_estimate": float(np.median(ts))}
+        dims[str(d)] = row
+    start = np.array([-8.0, 0.0])
+    screening = {}
+    for c in (10.0, 1.0, 0.1):
+        dom = W.Domain(synth.paper_environment(2, k_r=0.4))
+        path, flags, _ = dom.plan_path(start, 400, 10 ** 4, eps, c, 0.1, seed=3, control_variate=True)
+        length, hit = _path_length(path, flags)
+        screening[str(c)] = {"path_length": length, "reached_goal_at_step": hit}
+    visibility = {}
+    for k_r in (0.3, 0.45, 0.6):
+        dom = W.Domain(synth.paper_environment(2, k_r=k_r))
+        path, flags, _ = dom.plan_path(start, 400, 10 ** 5, eps, 1.0, 0.1, seed=3, control_variate=True)
+        length, hit = _path_length(path, flags)
+        visibility[str(k_r)] = {"path_length": length, "reached_goal_at_step": hit}
+    return {"dimensionality_angle_error": dims, "screening_k_r_0.4": screening, "visibility_c_1": visibility,
+            "note": "angle error in degrees, mean over 16 estimates (4 at 10^6 walks); goal (8, 0) assumed"}
+
+
 def secondary(W, synth):
     """Quick measurements of the other workloads (not the headline)."""
     import torch
@@ -544,8 +602,7 @@ def secondary(W, synth):
     # the paper's two-disc environment with a unit impulse at the goal (Sec. VI): r_o = 10,
     # k_r = 0.3, c = sigma = 1, eps = 0.01, start (-8, 0); the goal (8, 0) is this benchmark's
     # choice (the paper shows it only in a figure). 1024 walks per planner step.
-    env = {"d": 2, "outer_c": np.zeros(2), "outer_r": 10.0, "ball_c": np.array([[0.0, 3.0], [0.0, -1.5]]),
-           "ball_r": np.array([3.0, 1.5]), "source_z": np.array([8.0, 0.0]), "source_q": 1.0}
+    env = synth.paper_environment(2)
     dom = W.Domain(env)
     dom.plan_path(np.array([-8.0, 0.0]), 5, 1024, 0.01, 1.0, 0.1, seed=1, control_variate=True)
     torch.cuda.synchronize()
@@ -558,6 +615,7 @@ def secondary(W, synth):
     out["paper_environment_2d"] = {"path_ms": 1e3 * dt, "ms_per_planner_step": 1e3 * dt / 400,
                                    "reached_goal_at_step": int(np.argmax(f == 1)) if (f == 1).any() else None,
                                    "final_distance_to_goal": float(np.linalg.norm(p_end - env["source_z"]))}
+    out["paper_sweeps"] = paper_sweeps(W, synth)
     # differentiable d=6: forward + backward, 4096 queries x 2048 walks
     w = synth.c5()
     dom = W.Domain(w["domain"])

@@ -127,6 +127,7 @@ typedef struct {
     const double *exp_a;        /* n_exp x d exponents */
     const double *source_z;     /* d values: an impulse source at this point, or NULL for none */
     double source_q;            /* its strength q (the paper's unit impulse at the goal: 1) */
+    int32_t proj_dims;          /* 0 or d: plain domain; 1..d-1: extruded (see below) */
 } wos_domain_desc;
 
 /*
@@ -140,6 +141,17 @@ typedef struct {
  * first-sphere gradient adds q grad_x G_B(x_0, source_z). du_dsigma is NaN for such domains
  * (its source part is not estimated); du_dw is unaffected. Mixed precision runs these domains
  * on the CUDA-core walker (ball sets) and rejects point sets.
+ */
+
+/*
+ * Extruded domains (Sec. VI, dimensionality study: the obstacles and the outer boundary are
+ * extruded along the added dimensions, which are free and unbounded): with 1 <= proj_dims = m < d,
+ * every component is measured in the first m coordinates only (balls |P(x - c)| - r, goal,
+ * outer |P(x - c_o)|, box faces in coordinates 0..m-1; the box's other coordinates are ignored).
+ * Walks, directions, the impulse source and the boundary data stay d-dimensional; the closest
+ * boundary point keeps the free coordinates of x. A box or an outer ball in the first m
+ * coordinates still bounds every walk. Mixed precision runs such domains on the CUDA-core walker
+ * (ball sets) and rejects extruded point sets (UNSUPPORTED).
  */
 
 /* Per-call options. A NULL options pointer means {WOS_MIXED, 0, seed 0, offset 0, 10000}. */

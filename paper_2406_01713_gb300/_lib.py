@@ -30,6 +30,7 @@ class DomainDesc(ctypes.Structure):
         ("n_points", ctypes.c_int64), ("points", _PD),
         ("n_exp", ctypes.c_int32), ("exp_w", _PD), ("exp_a", _PD),
         ("source_z", _PD), ("source_q", ctypes.c_double),
+        ("proj_dims", ctypes.c_int32),
     ]
 
 

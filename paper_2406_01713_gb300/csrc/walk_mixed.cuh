@@ -87,8 +87,25 @@ struct MixedWalker {
 template <int D>
 __device__ __forceinline__ float xj(const f32x2 (&x2)[D], int j) { return unpack2(x2[j]).x; }
 
+// sum of term(j, s) over the coordinates the components are measured in: all D, or the first m
+// of an extruded domain (Sec. VI dimensionality study); the common case m = D takes no predicates
+template <int D, typename F>
+__device__ __forceinline__ float sum_coords(int m, F term) {
+    float s = 0.f;
+    if (m >= D) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) s = term(j, s);
+    } else {
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+            if (j < m) s = term(j, s);
+    }
+    return s;
+}
+
 // Distance to the components other than the balls. geom layout in shared memory: [0,d) box lo,
-// [d,2d) box hi, [2d,3d) goal c, [3d,4d) outer c, [4d, 4d+K) exp w, then K x d exp a.
+// [d,2d) box hi, [2d,3d) goal c, [3d,4d) outer c, [4d, 4d+K) exp w, then K x d exp a. An extruded
+// domain's box has its free-coordinate faces far away (set on the host).
 template <int D>
 __device__ __forceinline__ void other_components(const MixedProblem &P, const float *geom,
                                                  const f32x2 (&x2)[D], float &goal, float &other,
@@ -98,21 +115,17 @@ __device__ __forceinline__ void other_components(const MixedProblem &P, const fl
     okind = -1;
     oidx = -1;
     if (P.has_goal) {
-        float s = 0.f;
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
+        const float s = sum_coords<D>(P.proj, [&](int j, float a) {
             const float t = xj(x2, j) - geom[2 * D + j];
-            s = fmaf(t, t, s);
-        }
+            return fmaf(t, t, a);
+        });
         goal = sqrtf(s) - P.goal_r;
     }
     if (P.has_outer) {
-        float s = 0.f;
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
+        const float s = sum_coords<D>(P.proj, [&](int j, float a) {
             const float t = xj(x2, j) - geom[3 * D + j];
-            s = fmaf(t, t, s);
-        }
+            return fmaf(t, t, a);
+        });
         const float r = P.outer_r - sqrtf(s);
         if (r < other) { other = r; okind = kOuter; oidx = 0; }
     }
@@ -137,10 +150,10 @@ struct ScreenState {
 };
 
 template <int D>
-__device__ __forceinline__ void screen_init(ScreenState &S, const f32x2 (&x2)[D], float b0, float slack) {
-    float xx = 0.f;
-#pragma unroll
-    for (int j = 0; j < D; ++j) xx = fmaf(xj(x2, j), xj(x2, j), xx);
+__device__ __forceinline__ void screen_init(ScreenState &S, const f32x2 (&x2)[D], float b0, float slack,
+                                            int m) {
+    // |x|^2 over the measured coordinates (an extruded domain's ball records are zero in the others)
+    const float xx = sum_coords<D>(m, [&](int j, float a) { return fmaf(xj(x2, j), xj(x2, j), a); });
     S.xx = xx;
     S.b = b0;
     S.thr = fmaf(b0, b0, slack - xx);
@@ -198,7 +211,7 @@ __device__ __forceinline__ float block_min(const f32x2 &L0, const f32x2 &L1, con
 template <int D>
 __device__ __forceinline__ float screen_finish(const ScreenState &S, const ulonglong2 *B2,
                                                const f32x2 (&x2)[D], float goal, float other,
-                                               int okind, int oidx, int &kind, int &idx) {
+                                               int okind, int oidx, int m, int &kind, int &idx) {
     float best = CUDART_INF_F;
     kind = -1;
     idx = -1;
@@ -207,12 +220,10 @@ __device__ __forceinline__ float screen_finish(const ScreenState &S, const ulong
     if (S.bidx >= 0) {
         const float *Bf = reinterpret_cast<const float *>(B2 + (S.bidx / kBallBlock) * 2 * (D + 2));
         const int t = S.bidx % kBallBlock;
-        float s2 = 0.f;
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
+        const float s2 = sum_coords<D>(m, [&](int j, float a) {
             const float dj = fmaf(0.5f, Bf[kBallBlock * j + t], xj(x2, j));  // x_j - c_j
-            s2 = fmaf(dj, dj, s2);
-        }
+            return fmaf(dj, dj, a);
+        });
         bball = fminf(sqrtf(s2) + 0.5f * Bf[kBallBlock * (D + 1) + t], S.lb2);
     }
     if (bball < best) { best = bball; kind = kBall; idx = S.bidx; }
@@ -229,7 +240,7 @@ __device__ __forceinline__ float distance_mixed(const MixedProblem &P, const flo
     int okind, oidx;
     other_components<D>(P, geom, x2, goal, other, okind, oidx);
     ScreenState S;
-    screen_init<D>(S, x2, fminf(goal, other), slack);
+    screen_init<D>(S, x2, fminf(goal, other), slack, P.proj);
     const ulonglong2 *B2 = reinterpret_cast<const ulonglong2 *>(balls);
     constexpr int H = D / 2;
 #pragma unroll 1
@@ -274,7 +285,7 @@ __device__ __forceinline__ float distance_mixed(const MixedProblem &P, const flo
             screen_passing(S, Lt, Rt, slack, blk);
         }
     }
-    return screen_finish<D>(S, B2, x2, goal, other, okind, oidx, kind, idx);
+    return screen_finish<D>(S, B2, x2, goal, other, okind, oidx, P.proj, kind, idx);
 }
 
 // Closest boundary point and g there, in log space: returns g(xbar) exp(logw) and
@@ -303,17 +314,18 @@ __device__ __forceinline__ float terminal_value(const MixedProblem &P, const flo
         sphere = true;
     }
     if (sphere) {
-        float s = 0.f;
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
+        // an extruded domain projects in the measured coordinates and keeps the free ones
+        const int m = P.proj;
+        const float s = sum_coords<D>(m, [&](int j, float a) {
             const float t = xj(x2, j) - cc[j];
-            s = fmaf(t, t, s);
-        }
+            return fmaf(t, t, a);
+        });
         const float len = sqrtf(s);
         const float f = len > 0.f ? rad / len : 0.f;
 #pragma unroll
         for (int j = 0; j < D; ++j)
-            xb[j] = len > 0.f ? fmaf(f, xj(x2, j) - cc[j], cc[j]) : cc[j] + (j == 0 ? rad : 0.f);
+            xb[j] = j >= m ? xj(x2, j)
+                           : (len > 0.f ? fmaf(f, xj(x2, j) - cc[j], cc[j]) : cc[j] + (j == 0 ? rad : 0.f));
     } else {
 #pragma unroll
         for (int j = 0; j < D; ++j) xb[j] = xj(x2, j);

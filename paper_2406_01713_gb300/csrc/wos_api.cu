@@ -65,6 +65,7 @@ int device_sms() {
 struct wos_domain_s {
     int d = 0, has_box = 0, has_outer = 0, has_goal = 0, n_balls = 0, n_exp = 0;
     int has_source = 0;
+    int proj = 0;  // coordinates the components are measured in (d, or fewer when extruded)
     int64_t n_points = 0;
     double outer_r = 0, goal_r = 0, source_q = 0;
     std::vector<double> box_lo, box_hi, outer_c, goal_c, exp_w, exp_a, ball_r, ball_c, points, source_z;
@@ -101,6 +102,7 @@ void layout_view(DomainView<T> &v, T *base, const wos_domain_s &D) {
     v.has_outer = D.has_outer;
     v.has_goal = D.has_goal;
     v.has_source = D.has_source;
+    v.proj = D.proj;
     v.n_points = M;
     v.outer_r = (T)D.outer_r;
     v.goal_r = (T)D.goal_r;
@@ -152,44 +154,47 @@ int geom_floats(int d) { return 4 * d + kMaxExp + kMaxExp * d; }
 //    R (1 + (d+5) u) + u |x|. Twice the sum keeps every sphere inside the FP64 domain.
 //  * slack: the screen L = e0 + e1 b + x.m and the threshold b^2 - |x|^2 are FMA chains whose
 //    partial sums are bounded by P = |c|^2 + r^2 + 2 r b + 2 |x||c| and b^2 + |x|^2.
+//  An extruded domain measures its components in the first m = proj coordinates only, so the
+//  position bounds L, |x_j| and the centre norms are taken over those (the free coordinates are
+//  unbounded but never enter a distance); the jump term keeps the full dimension.
 void error_bounds(wos_domain_s &D) {
-    const int d = D.d;
-    double xabs = 0.0;  // bound of |x_j| inside the domain
+    const int d = D.d, m = D.proj;
+    double xabs = 0.0;  // bound of |x_j| inside the domain, j < m
     double xa_box = 0.0, xa_out = 0.0;
     if (D.has_box)
-        for (int j = 0; j < d; ++j) xa_box = std::max({xa_box, std::fabs(D.box_lo[j]), std::fabs(D.box_hi[j])});
+        for (int j = 0; j < m; ++j) xa_box = std::max({xa_box, std::fabs(D.box_lo[j]), std::fabs(D.box_hi[j])});
     if (D.has_outer)
-        for (int j = 0; j < d; ++j) xa_out = std::max(xa_out, std::fabs(D.outer_c[j]) + D.outer_r);
+        for (int j = 0; j < m; ++j) xa_out = std::max(xa_out, std::fabs(D.outer_c[j]) + D.outer_r);
     if (D.has_box && D.has_outer) xabs = std::min(xa_box, xa_out);
     else xabs = D.has_box ? xa_box : xa_out;
-    const double L = std::sqrt((double)d) * xabs;
+    const double L = std::sqrt((double)m) * xabs;
     double cmax = 0.0, rmax = 0.0, ccmax = 0.0;
     for (int i = 0; i < D.n_balls; ++i) {
         double cc = 0.0;
-        for (int j = 0; j < d; ++j) cc += D.ball_c[(size_t)i * d + j] * D.ball_c[(size_t)i * d + j];
+        for (int j = 0; j < m; ++j) cc += D.ball_c[(size_t)i * d + j] * D.ball_c[(size_t)i * d + j];
         ccmax = std::max(ccmax, cc);
         rmax = std::max(rmax, D.ball_r[i]);
     }
     for (int64_t i = 0; i < D.n_points; ++i) {
         double cc = 0.0;
-        for (int j = 0; j < d; ++j) cc += D.points[(size_t)i * d + j] * D.points[(size_t)i * d + j];
+        for (int j = 0; j < m; ++j) cc += D.points[(size_t)i * d + j] * D.points[(size_t)i * d + j];
         ccmax = std::max(ccmax, cc);
     }
     cmax = std::sqrt(ccmax);
     double cgo = 0.0;
     if (D.has_goal) {
         double cc = 0.0;
-        for (int j = 0; j < d; ++j) cc += D.goal_c[j] * D.goal_c[j];
+        for (int j = 0; j < m; ++j) cc += D.goal_c[j] * D.goal_c[j];
         cgo = std::sqrt(cc) + D.goal_r;
     }
     if (D.has_outer) {
         double cc = 0.0;
-        for (int j = 0; j < d; ++j) cc += D.outer_c[j] * D.outer_c[j];
+        for (int j = 0; j < m; ++j) cc += D.outer_c[j] * D.outer_c[j];
         cgo = std::max(cgo, std::sqrt(cc) + D.outer_r);
     }
     const double C = std::max(cmax, cgo);
     const double R = D.R_max;
-    const double dist_err = ((d + 4) / 2.0) * (L + C) + R + C + rmax + xabs;
+    const double dist_err = ((m + 4) / 2.0) * (L + C) + R + C + rmax + xabs;
     const double jump_err = (d + 5) * R + L;
     D.shrink32 = 2.0 * kU32 * (dist_err + jump_err);
     const double P = ccmax + rmax * rmax + 2.0 * rmax * R + 2.0 * L * cmax;
@@ -505,6 +510,7 @@ MixedProblem make_mixed_problem(wos_domain_t dom, const double *x, int64_t Q, in
     P.has_goal = dom->has_goal;
     P.grad_mode = grad_mode;
     P.has_source = dom->has_source;
+    P.proj = dom->proj;
     P.src = grad_mode && dom->has_source;
     if (dom->has_source) {
         const int d = dom->d;
@@ -778,6 +784,10 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
     if (d < 2 || d > WOS_MAX_D) return fail(WOS_ERR_UNSUPPORTED, "d = %d outside 2..%d", d, WOS_MAX_D);
     if (desc->n_balls < 0 || desc->n_points < 0 || desc->n_exp < 0)
         return fail(WOS_ERR_INVALID_ARG, "negative count");
+    if (desc->proj_dims < 0 || desc->proj_dims > d)
+        return fail(WOS_ERR_INVALID_ARG, "proj_dims = %d outside 0..%d", desc->proj_dims, d);
+    const int proj = desc->proj_dims > 0 ? desc->proj_dims : d;
+    if (proj < d && desc->n_points > 0) return fail(WOS_ERR_UNSUPPORTED, "extruded point sets");
     if (desc->n_exp > WOS_MAX_EXP) return fail(WOS_ERR_UNSUPPORTED, "n_exp > %d", WOS_MAX_EXP);
     if ((desc->box_lo == nullptr) != (desc->box_hi == nullptr))
         return fail(WOS_ERR_INVALID_ARG, "box_lo and box_hi must both be given");
@@ -794,7 +804,7 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
         if (!(desc->ball_r[i] > 0) || !std::isfinite(desc->ball_r[i]))
             return fail(WOS_ERR_INVALID_ARG, "ball %d radius <= 0", i);
     if (desc->box_lo != nullptr)
-        for (int j = 0; j < d; ++j)
+        for (int j = 0; j < proj; ++j)
             if (!(desc->box_hi[j] > desc->box_lo[j])) return fail(WOS_ERR_INVALID_ARG, "empty box");
 
     wos_domain_s *D = new (std::nothrow) wos_domain_s();
@@ -810,6 +820,7 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
     D->goal_r = D->has_goal ? desc->goal_r : 0.0;
     D->has_source = desc->source_z != nullptr;
     D->source_q = D->has_source ? desc->source_q : 0.0;
+    D->proj = proj;
     auto copy = [](std::vector<double> &v, const double *p, size_t n) {
         v.assign(n, 0.0);
         if (p) std::copy(p, p + n, v.begin());
@@ -824,9 +835,14 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
     copy(D->ball_c, desc->ball_c, (size_t)desc->n_balls * d);
     copy(D->points, desc->points, (size_t)desc->n_points * d);
     copy(D->source_z, desc->source_z, d);
+    // an extruded domain's box has no faces in the free coordinates: far away, never nearest
+    for (int j = proj; j < d; ++j) {
+        D->box_lo[j] = -1.0e30;
+        D->box_hi[j] = 1.0e30;
+    }
     double rmax = INFINITY;
     if (D->has_box)
-        for (int j = 0; j < d; ++j) rmax = std::min(rmax, 0.5 * (D->box_hi[j] - D->box_lo[j]));
+        for (int j = 0; j < proj; ++j) rmax = std::min(rmax, 0.5 * (D->box_hi[j] - D->box_lo[j]));
     if (D->has_outer) rmax = std::min(rmax, D->outer_r);
     D->R_max = rmax;
     error_bounds(*D);
@@ -835,7 +851,8 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
     const int64_t nv = view_size(*D);
     std::vector<double> h64 = pack_view<double>(*D);
     std::vector<float> h32 = pack_view<float>(*D);
-    // 8-ball blocks [m_0 x8]...[m_{d-1} x8][e0 x8][e1 x8], m = -2c, e0 = |c|^2 - r^2, e1 = -2r
+    // 8-ball blocks [m_0 x8]...[m_{d-1} x8][e0 x8][e1 x8], m = -2c, e0 = |c|^2 - r^2, e1 = -2r;
+    // an extruded domain has m_j = 0 in the free coordinates and |c|^2 over the first proj
     const int kB = 8;
     const int nblk = (D->n_balls + kB - 1) / kB;
     D->nblk = nblk;
@@ -846,7 +863,7 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
         if (i < D->n_balls) {
             double cc = 0.0;
             for (int j = 0; j < d; ++j) {
-                const float c = (float)D->ball_c[(size_t)i * d + j];
+                const float c = j < proj ? (float)D->ball_c[(size_t)i * d + j] : 0.0f;
                 B[kB * j + t] = -2.0f * c;
                 cc += (double)c * (double)c;
             }
@@ -891,8 +908,8 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
     layout_view<float>(D->v32, D->f32, *D);
     // domains with an impulse source stay on the CUDA-core walker (the sphere-set walker has no
     // source term)
-    const bool sphere_balls =
-        D->n_points == 0 && D->n_balls >= sphere_min_balls(d) && d <= kPointCloudMaxD && !D->has_source;
+    const bool sphere_balls = D->n_points == 0 && D->n_balls >= sphere_min_balls(d) && d <= kPointCloudMaxD &&
+                              !D->has_source && D->proj == d;
     if ((D->n_points > 0 && d <= kPointCloudMaxD) || sphere_balls) {
         e = sphere_balls ? pointcloud_prepare(D->ball_c.data(), D->ball_r.data(), D->n_balls, d, &D->pcd)
                          : pointcloud_prepare(D->points.data(), nullptr, D->n_points, d, &D->pcd);
@@ -1021,7 +1038,7 @@ __global__ void plan_pre_kernel(const __grid_constant__ PlanArgs a) {
             f = 8;
         } else if (a.dom.has_goal) {
             double s = 0.0;
-            for (int j = 0; j < a.dom.d; ++j) {
+            for (int j = 0; j < a.dom.proj; ++j) {
                 const double t = a.x[j] - a.dom.goal_c[j];
                 s += t * t;
             }

@@ -170,6 +170,7 @@ __device__ __forceinline__ float2 table_lookup(const WeightTable &t, float z) {
 template <typename T>
 struct DomainView {
     int d, n_balls, n_exp, has_box, has_outer, has_goal, has_source;
+    int proj;  // components are measured in coordinates 0..proj-1 (proj = d, or fewer: extruded)
     int64_t n_points;
     T outer_r, goal_r, source_q;
     const T *box_lo, *box_hi, *outer_c, *goal_c;  // d each

@@ -14,42 +14,48 @@ __device__ __forceinline__ T inf_of() {
     return sizeof(T) == 8 ? (T)CUDART_INF : (T)CUDART_INF_F;
 }
 
+// |x - c| over the first m coordinates (m = D, or fewer for an extruded domain)
 template <typename T, int D>
-__device__ __forceinline__ T norm_diff(const T (&x)[D], const T *c) {
+__device__ __forceinline__ T norm_diff(const T (&x)[D], const T *c, int m) {
     T s = T(0);
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        const T t = x[j] - c[j];
-        s += t * t;
+        if (j < m) {
+            const T t = x[j] - c[j];
+            s += t * t;
+        }
     }
     return sqrt(s);
 }
 
-// Distance to the boundary (minimum over components, strict '<' keeps the lowest id).
+// Distance to the boundary (minimum over components, strict '<' keeps the lowest id); an
+// extruded domain measures every component in its first dm.proj coordinates.
 template <typename T, int D>
 __device__ __forceinline__ T distance(const DomainView<T> &dm, const T (&x)[D], int &kind, int64_t &idx) {
+    const int m = dm.proj;
     T best = inf_of<T>();
     kind = -1;
     idx = -1;
     if (dm.has_goal) {
-        const T r = norm_diff<T, D>(x, dm.goal_c) - dm.goal_r;
+        const T r = norm_diff<T, D>(x, dm.goal_c, m) - dm.goal_r;
         if (r < best) { best = r; kind = kGoal; idx = 0; }
     }
     for (int i = 0; i < dm.n_balls; ++i) {
-        const T r = norm_diff<T, D>(x, dm.ball_c + (int64_t)i * D) - dm.ball_r[i];
+        const T r = norm_diff<T, D>(x, dm.ball_c + (int64_t)i * D, m) - dm.ball_r[i];
         if (r < best) { best = r; kind = kBall; idx = i; }
     }
     for (int64_t i = 0; i < dm.n_points; ++i) {
-        const T r = norm_diff<T, D>(x, dm.points + i * D);
+        const T r = norm_diff<T, D>(x, dm.points + i * D, m);
         if (r < best) { best = r; kind = kPoint; idx = i; }
     }
     if (dm.has_outer) {
-        const T r = dm.outer_r - norm_diff<T, D>(x, dm.outer_c);
+        const T r = dm.outer_r - norm_diff<T, D>(x, dm.outer_c, m);
         if (r < best) { best = r; kind = kOuter; idx = 0; }
     }
     if (dm.has_box) {
 #pragma unroll
         for (int j = 0; j < D; ++j) {
+            if (j >= m) continue;
             const T rlo = x[j] - dm.box_lo[j];
             if (rlo < best) { best = rlo; kind = kFace; idx = 2 * j; }
             const T rhi = dm.box_hi[j] - x[j];
@@ -66,17 +72,18 @@ __device__ __forceinline__ T boundary_value(const DomainView<T> &dm, const T (&x
     T xb[D];
     const T *c = nullptr;
     T rad = T(0);
+    const int m = dm.proj;  // an extruded domain projects in these and keeps the free coordinates
     if (kind == kGoal) { c = dm.goal_c; rad = dm.goal_r; }
     if (kind == kBall) { c = dm.ball_c + idx * D; rad = dm.ball_r[idx]; }
     if (kind == kOuter) { c = dm.outer_c; rad = dm.outer_r; }
     if (c != nullptr) {
-        const T len = norm_diff<T, D>(x, c);
+        const T len = norm_diff<T, D>(x, c, m);
 #pragma unroll
         for (int j = 0; j < D; ++j)
-            xb[j] = len > T(0) ? c[j] + rad * (x[j] - c[j]) / len : c[j] + (j == 0 ? rad : T(0));
+            xb[j] = j >= m ? x[j] : (len > T(0) ? c[j] + rad * (x[j] - c[j]) / len : c[j] + (j == 0 ? rad : T(0)));
     } else if (kind == kPoint) {
 #pragma unroll
-        for (int j = 0; j < D; ++j) xb[j] = dm.points[idx * D + j];
+        for (int j = 0; j < D; ++j) xb[j] = j >= m ? x[j] : dm.points[idx * D + j];
     } else {
 #pragma unroll
         for (int j = 0; j < D; ++j) xb[j] = x[j];

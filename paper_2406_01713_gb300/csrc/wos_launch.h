@@ -43,6 +43,7 @@ struct MixedProblem {
     int cv;        // gradient control variate: accumulate the 3d extra sums
     int src;       // impulse source in gradient walks: store its per-query fields
     int has_source;
+    int proj;      // components measured in coordinates 0..proj-1 (= d unless extruded)
     float source_q;
     float src_lc0;        // log(k^nu / (2 pi)^(d/2)), k = sqrt(sigma) > 0
     float src_inv_omega;  // 1 / |S^(d-1)| (sigma = 0)

@@ -12,9 +12,13 @@ generators stand in for them:
   c5  differentiable, d = 6: 64 balls, g = sum_k w_k exp(a_k.x), 8 terms, |a_k| = 2, sigma = 4
 
 Seeds: workload i (c1 = 1, ...) draws geometry from 1713 + i and walks from 2406 + i.
+  env the paper's evaluation environment (Sec. VI): outer disc r_o = 10, discs r_u = k_r r_o
+      and r_l = r_u / 2 touching at the origin, a unit impulse at the goal; for d > 2 extruded
+      along the added coordinates (free and unbounded), as in the dimensionality study
+
 A domain is a dict of numpy arrays; every key is optional except d:
   d, box_lo, box_hi, outer_c, outer_r, goal_c, goal_r, ball_c (B x d), ball_r (B),
-  points (M x d), exp_w (K), exp_a (K x d).
+  points (M x d), exp_w (K), exp_a (K x d), source_z (d), source_q, proj_dims.
 """
 import math
 
@@ -249,3 +253,22 @@ def annulus_domain(d, r_in, r_out):
     """Omega = B(0, r_out) minus B(0, r_in); g = 1 on the inner sphere (goal), 0 outside."""
     return {"d": d, "outer_c": np.zeros(d), "outer_r": float(r_out), "goal_c": np.zeros(d),
             "goal_r": float(r_in)}
+
+
+def paper_environment(d=2, k_r=0.3, goal=(8.0, 0.0), r_o=10.0):
+    """The paper's evaluation environment (Sec. VI): outer disc r_o, upper disc r_u = k_r r_o
+    centred at (0, r_u), lower disc r_l = r_u / 2 at (0, -r_l) (they touch at the origin), a
+    unit impulse at the goal. The goal point is shown only in a figure; (8, 0) mirrors the
+    paper's start (-8, 0). For d > 2 the components are measured in the first two coordinates
+    (extruded along the others)."""
+    r_u = k_r * r_o
+    r_l = 0.5 * r_u
+    c = np.zeros((2, d))
+    c[0, 1], c[1, 1] = r_u, -r_l
+    z = np.zeros(d)
+    z[:2] = goal
+    dom = {"d": d, "outer_c": np.zeros(d), "outer_r": r_o, "ball_c": c, "ball_r": np.array([r_u, r_l]),
+           "source_z": z, "source_q": 1.0}
+    if d > 2:
+        dom["proj_dims"] = 2
+    return dom

@@ -104,6 +104,8 @@ class Domain:
             s.source_z = p(arr("source_z", (d,)))
             s.source_q = float(dom.get("source_q", 1.0))
         self.has_source = dom.get("source_z") is not None
+        # extruded domain: components measured in the first proj_dims coordinates only
+        s.proj_dims = int(dom.get("proj_dims", 0))
         self.n_exp = int(s.n_exp)
         self.n_balls = int(s.n_balls)
         self.n_points = int(s.n_points)

@@ -76,6 +76,16 @@ def test_domain_create_rejects_bad_descriptions(lib):
     s.n_balls = 0
     s.n_exp = 9
     assert lib.wos_domain_create(ctypes.byref(s), ctypes.byref(h)) == 2  # too many exp terms
+    s.n_exp = 0
+    s.proj_dims = 4
+    assert lib.wos_domain_create(ctypes.byref(s), ctypes.byref(h)) == 1  # proj_dims > d
+    assert b"proj_dims" in lib.wos_last_error()
+    s.proj_dims = 2
+    pts = np.zeros((4, 3))
+    s.n_points = 4
+    s.points = pts.ctypes.data_as(P)
+    assert lib.wos_domain_create(ctypes.byref(s), ctypes.byref(h)) == 2  # extruded point set
+    assert h.value is None
 
 
 def test_calls_reject_null_handles(lib):
