@@ -3,13 +3,14 @@
 // Distance to a set of obstacle spheres: points (Sec. VII-A, d(q) = min_i |q - p_i|) or balls
 // (Sec. VI, |q - c_i| - r_i), for 128 walkers at a time. The contraction
 // D_wi = |c_i|^2 - 2 x_w . c_i runs as tcgen05.mma (BF16 inputs, FP32 accumulation in tensor
-// memory) over centre tiles that TMA streams into shared memory; the walker warps read their
-// rows back with tcgen05.ld. Per 32-column chunk, min D gives a lower bound of the chunk's
-// distances, sqrt(min D + |x|^2 - delta) - r_hi (balls are sorted by radius, so r_hi, the
-// chunk's largest radius, is close to every radius in it); each walker keeps the best and the
-// second-best chunk. The best chunk is then recomputed exactly in FP32 and every other sphere
-// is bounded from below by the second-best chunk's bound, so the radius never exceeds the true
-// distance (no sphere leaves the domain).
+// memory) over centre tiles that bulk copies (cp.async.bulk) stream into shared memory; the
+// walker warps read their rows back with tcgen05.ld. Per 32-column chunk, min D gives a lower
+// bound of the chunk's distances, sqrt(min D + |x|^2 - delta) - r_hi (balls are sorted by
+// radius, so r_hi, the chunk's largest radius, is close to every radius in it); each walker
+// keeps the best, second and third chunk bounds. The best chunk is then recomputed exactly in
+// FP32 (the second too when its bound is below that result), and every other sphere is bounded
+// from below by the next chunk's bound, so the radius never exceeds the true distance (no
+// sphere leaves the domain).
 //
 // BF16 split: x = x_h + x_l and -2p = q_h + q_l (each a BF16), |p|^2 = n_h + n_l; the walker
 // row [x_h, x_h, x_l, 1, 1] times the point row [q_h, q_l, q_h, n_h, n_l] gives
@@ -68,8 +69,9 @@ struct Geo {
     static constexpr uint32_t kABytes = kRows * K * 2;
     static constexpr uint32_t kSBO = (K / 8) * 128;  // to the next group of 8 rows
     static constexpr int kStages = K == 32 ? 6 : 4;  // centre-tile ring in shared memory (tiles)
-    // the ring is filled kPairTiles tiles per bulk copy: kSlots slots, each with its own full and
-    // empty barrier
+    // the ring is filled kPairTiles tiles per bulk copy: kSlots slots, each with its own full
+    // barrier (a slot is reused only after the MMAs that read it have completed, which the
+    // accumulator waits already establish)
     static constexpr int kSlots = kStages / kPairTiles;
     static constexpr uint32_t kSlotBytes = kPairTiles * kTileBytes;
 };
@@ -573,8 +575,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
 
             // ---- exact FP32 distances |x - c| - r of the best chunk (and of the second-best
             //      one when its bound is below that); every other sphere is bounded below by the
-            //      next chunk's bound. The warp refines one walker at a time, one sphere per lane:
-            //      a chunk is stored coordinate-major, so every load is one coalesced row.
+            //      next chunk's bound. The warp refines four asking walkers at a time, one sphere
+            //      per lane: a chunk stores its centres by coordinate quads, so every load is 512
+            //      contiguous bytes.
             float Rp = CUDART_INF_F;
             int pbest = c1 * kChunk;
             float *tr = reinterpret_cast<float *>(Bst + kStages * kTileBytes) + warp * 32 * kTrPitch;
