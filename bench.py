@@ -542,7 +542,9 @@ def paper_sweeps(W, synth):
         a figure; behind the obstacle the gradient is ~1e-10 and rare walks dominate it),
         d = 2..5 (extruded), N = 10^3..10^6 walks, and the device time per estimate;
       * screening (Fig. 6): planner paths for c in {10, 1, 0.1} at k_r = 0.4 (10^4 walks);
-      * visibility (Fig. 7): planner paths for k_r in {0.3, 0.45, 0.6} at c = 1 (10^5 walks).
+      * visibility (Fig. 7): planner paths for k_r in {0.3, 0.45, 0.6} at c = 1 (10^5 walks);
+      * multistart (Fig. 5): paths at k_r = 0.2, c = 1 (10^4 walks) from six starts at radius 8
+        (angles 90..315 degrees; the paper's starts are shown only in a figure).
     Paths: s_ub = 0.1, at most 400 steps; the length is measured up to the goal."""
     import torch
 
@@ -582,7 +584,15 @@ def paper_sweeps(W, synth):
         path, flags, _ = dom.plan_path(start, 400, 10 ** 5, eps, 1.0, 0.1, seed=3, control_variate=True)
         length, hit = _path_length(path, flags)
         visibility[str(k_r)] = {"path_length": length, "reached_goal_at_step": hit}
+    multistart = {}
+    dom = W.Domain(synth.paper_environment(2, k_r=0.2))
+    for deg in (90, 135, 180, 225, 270, 315):
+        x0 = 8.0 * np.array([math.cos(math.radians(deg)), math.sin(math.radians(deg))])
+        path, flags, _ = dom.plan_path(x0, 400, 10 ** 4, eps, 1.0, 0.1, seed=5, control_variate=True)
+        length, hit = _path_length(path, flags)
+        multistart[str(deg)] = {"path_length": length, "reached_goal_at_step": hit}
     return {"dimensionality_angle_error": dims, "screening_k_r_0.4": screening, "visibility_c_1": visibility,
+            "multistart_k_r_0.2": multistart,
             "note": "angle error in degrees, mean over 16 estimates (4 at 10^6 walks); goal (8, 0) and "
                     "angle point (2, -6) assumed; paths from (-8, 0)"}
 
