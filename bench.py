@@ -585,12 +585,15 @@ def paper_sweeps(W, synth):
         length, hit = _path_length(path, flags)
         visibility[str(k_r)] = {"path_length": length, "reached_goal_at_step": hit}
     multistart = {}
-    dom = W.Domain(synth.paper_environment(2, k_r=0.2))
-    for deg in (90, 135, 180, 225, 270, 315):
-        x0 = 8.0 * np.array([math.cos(math.radians(deg)), math.sin(math.radians(deg))])
-        path, flags, _ = dom.plan_path(x0, 400, 10 ** 4, eps, 1.0, 0.1, seed=5, control_variate=True)
-        length, hit = _path_length(path, flags)
-        multistart[str(deg)] = {"path_length": length, "reached_goal_at_step": hit}
+    try:
+        dom = W.Domain(synth.paper_environment(2, k_r=0.2))
+        for deg in (90, 135, 180, 225, 270, 315):
+            x0 = 8.0 * np.array([math.cos(math.radians(deg)), math.sin(math.radians(deg))])
+            path, flags, _ = dom.plan_path(x0, 400, 10 ** 4, eps, 1.0, 0.1, seed=5, control_variate=True)
+            length, hit = _path_length(path, flags)
+            multistart[str(deg)] = {"path_length": length, "reached_goal_at_step": hit}
+    except Exception as e:  # recorded; the studies above are kept
+        multistart = {"error": "%s: %s" % (type(e).__name__, e)}
     return {"dimensionality_angle_error": dims, "screening_k_r_0.4": screening, "visibility_c_1": visibility,
             "multistart_k_r_0.2": multistart,
             "note": "angle error in degrees, mean over 16 estimates (4 at 10^6 walks); goal (8, 0) and "
