@@ -74,6 +74,8 @@ class _Options(ctypes.Structure):
         ("laplace_factor", ctypes.c_int32),
         ("control_variate", ctypes.c_int32),
         ("plant_free_space_source_grad", ctypes.c_int32),
+        ("roulette_w", ctypes.c_double),
+        ("plant_roulette_no_reweight", ctypes.c_int32),
     ]
 
 
@@ -83,6 +85,7 @@ class _WalkOut(ctypes.Structure):
         ("jumps", ctypes.c_int64),
         ("capped", ctypes.c_int32),
         ("outside", ctypes.c_int32),
+        ("killed", ctypes.c_int32),
         ("comp_kind", ctypes.c_int32),
         ("comp_index", ctypes.c_int64),
         ("grad", ctypes.c_double * MAXD),
@@ -198,9 +201,12 @@ class Domain:
         self.s = s
 
 
-def _opts(seed, max_steps, grad, laplace_factor, control_variate=False, plant_free_space_source_grad=False):
+def _opts(seed, max_steps, grad, laplace_factor, control_variate=False, plant_free_space_source_grad=False,
+          roulette=0.0, plant_roulette_no_reweight=False):
     o = _Options()
     o.plant_free_space_source_grad = int(bool(plant_free_space_source_grad))
+    o.roulette_w = float(roulette)
+    o.plant_roulette_no_reweight = int(bool(plant_roulette_no_reweight))
     o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     o.max_steps = int(max_steps)
     o.grad = int(bool(grad))
@@ -281,11 +287,12 @@ def walk(dom, x0, walk_index, eps, sigma, seed, max_steps=10000, grad=False, lap
 
 def solve(dom, X, n_walks, eps, sigma, seed, walk_offset=0, max_steps=10000, grad=False,
           laplace_factor=False, threads=None, per_walk=False, control_variate=False,
-          plant_free_space_source_grad=False):
+          plant_free_space_source_grad=False, roulette=0.0, plant_roulette_no_reweight=False):
     """Per-query estimates. Returns a dict of numpy arrays (u, u_se, grad, grad_se,
     du_dsigma, du_dw, walk_steps, capped, outside; with per_walk also walk_term,
     walk_jumps, walk_grad, walk_dsigma). control_variate (with grad): grad and grad_se are
-    the control-variate estimate G/(N-1) sum_w (t_w - tbar) v_w and its standard error."""
+    the control-variate estimate G/(N-1) sum_w (t_w - tbar) v_w and its standard error.
+    roulette > 0: Russian roulette on walk weights below it."""
     D = dom if isinstance(dom, Domain) else Domain(dom)
     d, K = D.d, D.n_exp
     X = np.ascontiguousarray(np.asarray(X, float).reshape(-1, d))
@@ -302,7 +309,8 @@ def solve(dom, X, n_walks, eps, sigma, seed, walk_offset=0, max_steps=10000, gra
     if per_walk:
         pw = {"walk_term": np.zeros((Q, N)), "walk_jumps": np.zeros((Q, N), np.int64),
               "walk_grad": np.zeros((Q, N, d)), "walk_dsigma": np.zeros((Q, N))}
-    opt = _opts(seed, max_steps, grad, laplace_factor, control_variate, plant_free_space_source_grad)
+    opt = _opts(seed, max_steps, grad, laplace_factor, control_variate, plant_free_space_source_grad,
+                roulette, plant_roulette_no_reweight)
     rc = lib().or_solve(
         ctypes.byref(D.s), _ptr(X), Q, N, int(walk_offset), float(eps), float(sigma), ctypes.byref(opt),
         int(threads), _ptr(out["u"]), _ptr(out["u_se"]), _ptr(out["grad"]), _ptr(out["grad_se"]),

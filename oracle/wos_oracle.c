@@ -39,6 +39,14 @@
  *       x <- x + s grad/|grad|,  s = min(s_ub, 0.5 d_bound).
  *   Distance functions (Sec. VI, Eq. for d(x, dOmega); Sec. VII-A point-set distance):
  *       balls: |x - c| - r;  outer ball: r_o - |x - c_o|;  points: |x - p|;  box faces.
+ *   Russian roulette on the weight (optional; the closing discussion's "Russian roulette on C"
+ *       variance/cost trade-off, not an estimator the paper prints): before each jump k >= 1
+ *       whose weight W = prod C is below w_min, the walk survives with probability W / w_min
+ *       and then carries the weight w_min, or ends with its source contributions so far and no
+ *       boundary value. E[kept weight] = W keeps u unbiased; the pathwise du/dsigma
+ *       (term times the summed d log C / dsigma) stays unbiased because the survival
+ *       probability's sigma-derivative is the summed d log C / dsigma up to that step. The
+ *       uniform is the top 24 bits of Philox block 15 of (walk, step k), times 2^-24.
  *   Extruded domains (Sec. VI, dimensionality study): with proj_dims = m < d every boundary
  *       component is measured in the first m coordinates only (the obstacles and the outer
  *       boundary extruded along the others, which are free and unbounded); walks, sources and
@@ -105,6 +113,8 @@ typedef struct {
     int32_t laplace_factor; /* 1: the paper's printed factor d/R0 instead of alpha(R0) */
     int32_t control_variate; /* 1 (with grad): the control-variate gradient of or_solve */
     int32_t plant_free_space_source_grad; /* test only: drop the ball's image term in grad G_B */
+    double roulette_w;      /* > 0: Russian roulette when the weight falls below it */
+    int32_t plant_roulette_no_reweight; /* test only: survivors keep their weight */
 } or_options;
 
 typedef struct {
@@ -112,6 +122,7 @@ typedef struct {
     int64_t jumps; /* sphere jumps k; distance evaluations = k + 1 */
     int32_t capped;
     int32_t outside;
+    int32_t killed; /* ended by the roulette */
     int32_t comp_kind;
     int64_t comp_index;
     double grad[OR_MAXD];
@@ -396,6 +407,20 @@ void or_walk(const or_domain *D, const double *x0, uint64_t walk, double eps, do
             out->capped = 1;
             out->term = 0.0;
             break;
+        }
+        if (opt->roulette_w > 0.0 && k > 0 && exp(logw) < opt->roulette_w) {
+            const uint32_t key[2] = {(uint32_t)opt->seed, (uint32_t)(opt->seed >> 32)};
+            const uint32_t ctr[4] = {(uint32_t)walk, (uint32_t)(walk >> 32), (uint32_t)k, 15u};
+            uint32_t r[4];
+            or_philox4x32_10(key, ctr, r);
+            const double u = (double)(r[0] >> 8) * (1.0 / 16777216.0);
+            if (u < exp(logw) / opt->roulette_w) {
+                if (!opt->plant_roulette_no_reweight) logw = log(opt->roulette_w);
+            } else {
+                out->killed = 1;
+                out->term = src; /* source contributions so far, no boundary value */
+                break;
+            }
         }
         if (D->has_source) {
             /* the ball B(x_k, R) contains the source: q G_B(x_k, z) times the weight so far */

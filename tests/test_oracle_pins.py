@@ -15,6 +15,8 @@ never against the oracle itself.
   * planner: adaptive step s = min(s_ub, d/2) and radial descent in the annulus
   * extruded domains (Sec. VI dimensionality study): nearest-point geometry against sampled
     cylinder surfaces, and the exp closed form with a along all or only the free coordinates
+  * Russian roulette on the weight: the exp closed form with shorter walks, du/dsigma against
+    the plain estimator, and a planted mistake (survivors not reweighted) that must fail
 and one planted mistake (the paper's literal d/R gradient factor at sigma > 0), which the
 off-centre ball pin must reject.
 """
@@ -617,3 +619,57 @@ def test_full_projection_is_the_plain_domain(oracle_mod):
     a = oracle_mod.solve(dom, w["X"], 500, 1e-3, w["sigma"], w["seed"], grad=True)
     b = oracle_mod.solve(dict(dom, proj_dims=2), w["X"], 500, 1e-3, w["sigma"], w["seed"], grad=True)
     assert np.array_equal(a["u"], b["u"]) and np.array_equal(a["grad"], b["grad"])
+
+
+# --------------------------------------------------------------------------- Russian roulette
+def _roulette_domain(sigma=16.0):
+    """d = 3 unit ball with two ball obstacles and exp data (|a|^2 = sigma); 12 queries."""
+    rng = np.random.default_rng(4)
+    d = 3
+    a = rng.standard_normal(d)
+    a *= math.sqrt(sigma) / np.linalg.norm(a)
+    dom = {"d": d, "outer_c": np.zeros(d), "outer_r": 1.0,
+           "ball_c": np.array([[0.5, 0.0, 0.0], [-0.4, 0.3, 0.1]]), "ball_r": np.array([0.2, 0.15]),
+           "exp_w": np.ones(1), "exp_a": a[None, :]}
+    X = []
+    while len(X) < 12:
+        p = rng.uniform(-0.7, 0.7, size=d)
+        if np.linalg.norm(p) < 0.7 and all(np.linalg.norm(p - c) > r + 0.05
+                                           for c, r in zip(dom["ball_c"], dom["ball_r"])):
+            X.append(p)
+    return dom, np.array(X), a, sigma
+
+
+def test_roulette_keeps_the_exp_solution_and_shortens_walks(oracle_mod):
+    # roulette below w = 0.3 (a third of the walks' later steps have smaller weights at sigma = 16)
+    dom, X, a, sigma = _roulette_domain()
+    g = np.exp(X @ a)
+    bias = 3e-4 * g * np.linalg.norm(a)
+    plain = oracle_mod.solve(dom, X, 40000, 1e-4, sigma, 3, grad=True)
+    for cv in (False, True):
+        res = oracle_mod.solve(dom, X, 40000, 1e-4, sigma, 3, grad=True, roulette=0.3, control_variate=cv)
+        assert np.all(np.abs(res["u"] - g) < 4.5 * res["u_se"] + bias)
+        assert np.all(np.abs(res["grad"] - a[None, :] * g[:, None]) < 4.5 * res["grad_se"] + 10 * bias[:, None])
+        assert res["walk_steps"].sum() < 0.9 * plain["walk_steps"].sum()
+
+
+def test_roulette_dsigma_agrees_with_the_plain_estimator(oracle_mod):
+    # the pathwise du/dsigma (term times the summed d log C / dsigma) stays unbiased under the
+    # roulette; the plain estimator is pinned by the ball-centre closed form and the FD test
+    dom, X, _, sigma = _roulette_domain()
+    est = []
+    for roulette, seed in ((0.0, 5), (0.3, 6)):
+        r = oracle_mod.solve(dom, X, 40000, 1e-4, sigma, seed, per_walk=True, roulette=roulette)
+        w = r["walk_dsigma"]
+        est.append((w.mean(axis=1), w.std(axis=1, ddof=1) / math.sqrt(w.shape[1])))
+        assert np.allclose(est[-1][0], r["du_dsigma"], rtol=1e-9, atol=1e-12)
+    (m0, s0), (m1, s1) = est
+    assert np.all(np.abs(m0 - m1) < 4.5 * np.sqrt(s0 ** 2 + s1 ** 2))
+
+
+def test_planted_roulette_without_reweight_is_rejected(oracle_mod):
+    # survivors that keep their small weight bias u low
+    dom, X, a, sigma = _roulette_domain()
+    res = oracle_mod.solve(dom, X, 40000, 1e-4, sigma, 3, roulette=0.3, plant_roulette_no_reweight=True)
+    g = np.exp(X @ a)
+    assert np.mean(np.abs(res["u"] - g) < 4.5 * res["u_se"] + 3e-4 * g * np.linalg.norm(a)) < 0.5
