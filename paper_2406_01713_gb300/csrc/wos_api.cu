@@ -341,7 +341,9 @@ __global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
 // Control variate, outcome-independent sums: the first direction of every walk of a query,
 // regenerated from its Philox counter with the walkers' own sampler and arguments (so the
 // values are the walkers' v0 bit for bit), summed per component and squared into the query's
-// [sum v0] and [sum v0^2] fields. One warp per query; plain stores (a warp owns its query).
+// [sum v0] and [sum v0^2] fields. A batch gives each query one warp, which stores its sums; a
+// single problem with more than 4096 walks per query splits them into warps of 4096 walks that
+// add their sums atomically (a few queries with many walks would otherwise leave the GPU idle).
 struct CvPrepassArgs {
     const MixedProblem *problems;  // device array, or nullptr: problem 0 is `single`
     const FinalizeRec *recs;       // device array (q_begin per problem), or nullptr
@@ -349,14 +351,20 @@ struct CvPrepassArgs {
     int64_t total_q;
     MixedProblem single;
     uint64_t seed;
+    // single problem: each query's walks in `segments` warps of seg_walks walks (set by the
+    // launcher), whose sums are added atomically; batches: one warp per query
+    int64_t segments, seg_walks;
 };
 
+// Prepass sums of walks [w0, w1) of query q; `add`: several warps share the query (atomic
+// adds into the zeroed sums), else the warp stores them.
 template <int D>
-__device__ void cv_prepass_query(const MixedProblem &P, int64_t q, uint64_t seed, int lane) {
+__device__ void cv_prepass_query(const MixedProblem &P, int64_t q, int64_t w0, int64_t w1, bool add,
+                                 uint64_t seed, int lane) {
     double s1[D], s2[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) s1[i] = s2[i] = 0.0;
-    for (int64_t w = lane; w < P.N; w += 32) {
+    for (int64_t w = w0 + lane; w < w1; w += 32) {
         float v[D];
         direction_f32<D, true>(seed, (uint64_t)(P.walk_base + q * P.N + w), 0u, v);
 #pragma unroll
@@ -377,8 +385,13 @@ __device__ void cv_prepass_query(const MixedProblem &P, int64_t q, uint64_t seed
         double *cvp = P.acc + q * acc_fields(D, P.n_exp, 1, P.src) + cv_field(D, P.n_exp);
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            cvp[i] = s1[i];
-            cvp[2 * D + i] = s2[i];
+            if (add) {
+                atomicAdd(cvp + i, s1[i]);
+                atomicAdd(cvp + 2 * D + i, s2[i]);
+            } else {
+                cvp[i] = s1[i];
+                cvp[2 * D + i] = s2[i];
+            }
         }
     }
 }
@@ -386,9 +399,15 @@ __device__ void cv_prepass_query(const MixedProblem &P, int64_t q, uint64_t seed
 __global__ void cv_prepass_kernel(const __grid_constant__ CvPrepassArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.total_q; t += nwarps) {
+    const int64_t S = a.recs != nullptr ? 1 : a.segments;
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.total_q * S; t += nwarps) {
         const MixedProblem *P = &a.single;
-        int64_t q = t;
+        int64_t q = t / S;
+        int64_t w0 = 0, w1 = P->N;
+        if (S > 1) {
+            w0 = (t % S) * a.seg_walks;
+            w1 = w0 + a.seg_walks < P->N ? w0 + a.seg_walks : P->N;
+        }
         if (a.recs != nullptr) {
             int lo = 0, hi = a.n - 1;
             while (lo < hi) {
@@ -398,11 +417,12 @@ __global__ void cv_prepass_kernel(const __grid_constant__ CvPrepassArgs a) {
             }
             P = a.problems + lo;
             q = t - a.recs[lo].q_begin;
+            w1 = P->N;
         }
         if (!P->cv) continue;
         switch (P->d) {
 #define WOS_CASE(DD) \
-    case DD: cv_prepass_query<DD>(*P, q, a.seed, lane); break;
+    case DD: cv_prepass_query<DD>(*P, q, w0, w1, S > 1, a.seed, lane); break;
             WOS_CASE(2) WOS_CASE(3) WOS_CASE(4) WOS_CASE(5) WOS_CASE(6) WOS_CASE(7)
             WOS_CASE(8) WOS_CASE(9) WOS_CASE(10) WOS_CASE(11) WOS_CASE(12)
 #undef WOS_CASE
@@ -411,10 +431,19 @@ __global__ void cv_prepass_kernel(const __grid_constant__ CvPrepassArgs a) {
     }
 }
 
-wos_status launch_cv_prepass(const CvPrepassArgs &a, cudaStream_t s) {
-    if (a.total_q <= 0) return WOS_OK;
+wos_status launch_cv_prepass(const CvPrepassArgs &a_in, cudaStream_t s) {
+    if (a_in.total_q <= 0) return WOS_OK;
+    CvPrepassArgs a = a_in;
+    // a single problem's queries in segments of 4096 walks (128 per lane)
+    a.segments = 1;
+    a.seg_walks = a.single.N;
+    if (a.recs == nullptr && a.single.N > 4096) {
+        a.seg_walks = 4096;
+        a.segments = (a.single.N + a.seg_walks - 1) / a.seg_walks;
+    }
     const int threads = 256;
-    const int64_t blocks = std::min<int64_t>((a.total_q * 32 + threads - 1) / threads, 8192);
+    const int64_t tasks = a.total_q * (a.recs == nullptr ? a.segments : 1);
+    const int64_t blocks = std::min<int64_t>((tasks * 32 + threads - 1) / threads, 8192);
     cv_prepass_kernel<<<(unsigned)blocks, threads, 0, s>>>(a);
     WOS_CUDA(cudaGetLastError());
     return WOS_OK;
