@@ -76,6 +76,7 @@ class _Options(ctypes.Structure):
         ("plant_free_space_source_grad", ctypes.c_int32),
         ("roulette_w", ctypes.c_double),
         ("plant_roulette_no_reweight", ctypes.c_int32),
+        ("antithetic", ctypes.c_int32),
     ]
 
 
@@ -202,8 +203,9 @@ class Domain:
 
 
 def _opts(seed, max_steps, grad, laplace_factor, control_variate=False, plant_free_space_source_grad=False,
-          roulette=0.0, plant_roulette_no_reweight=False):
+          roulette=0.0, plant_roulette_no_reweight=False, antithetic=False):
     o = _Options()
+    o.antithetic = int(bool(antithetic))
     o.plant_free_space_source_grad = int(bool(plant_free_space_source_grad))
     o.roulette_w = float(roulette)
     o.plant_roulette_no_reweight = int(bool(plant_roulette_no_reweight))
@@ -270,11 +272,12 @@ def distance(dom, x):
     return r, int(kind.value), int(idx.value), xbar
 
 
-def walk(dom, x0, walk_index, eps, sigma, seed, max_steps=10000, grad=False, laplace_factor=False):
+def walk(dom, x0, walk_index, eps, sigma, seed, max_steps=10000, grad=False, laplace_factor=False,
+         antithetic=False):
     D = dom if isinstance(dom, Domain) else Domain(dom)
     x0 = np.ascontiguousarray(np.asarray(x0, float))
     o = _WalkOut()
-    opt = _opts(seed, max_steps, grad, laplace_factor)
+    opt = _opts(seed, max_steps, grad, laplace_factor, antithetic=antithetic)
     lib().or_walk(ctypes.byref(D.s), _ptr(x0), int(walk_index), float(eps), float(sigma),
                   ctypes.byref(opt), ctypes.byref(o))
     return {
@@ -287,12 +290,14 @@ def walk(dom, x0, walk_index, eps, sigma, seed, max_steps=10000, grad=False, lap
 
 def solve(dom, X, n_walks, eps, sigma, seed, walk_offset=0, max_steps=10000, grad=False,
           laplace_factor=False, threads=None, per_walk=False, control_variate=False,
-          plant_free_space_source_grad=False, roulette=0.0, plant_roulette_no_reweight=False):
+          plant_free_space_source_grad=False, roulette=0.0, plant_roulette_no_reweight=False,
+          antithetic=False):
     """Per-query estimates. Returns a dict of numpy arrays (u, u_se, grad, grad_se,
     du_dsigma, du_dw, walk_steps, capped, outside; with per_walk also walk_term,
     walk_jumps, walk_grad, walk_dsigma). control_variate (with grad): grad and grad_se are
     the control-variate estimate G/(N-1) sum_w (t_w - tbar) v_w and its standard error.
-    roulette > 0: Russian roulette on walk weights below it."""
+    roulette > 0: Russian roulette on walk weights below it. antithetic: walk pairs (2m, 2m+1)
+    with opposite first directions (n_walks and walk_offset even; not with control_variate)."""
     D = dom if isinstance(dom, Domain) else Domain(dom)
     d, K = D.d, D.n_exp
     X = np.ascontiguousarray(np.asarray(X, float).reshape(-1, d))
@@ -310,7 +315,7 @@ def solve(dom, X, n_walks, eps, sigma, seed, walk_offset=0, max_steps=10000, gra
         pw = {"walk_term": np.zeros((Q, N)), "walk_jumps": np.zeros((Q, N), np.int64),
               "walk_grad": np.zeros((Q, N, d)), "walk_dsigma": np.zeros((Q, N))}
     opt = _opts(seed, max_steps, grad, laplace_factor, control_variate, plant_free_space_source_grad,
-                roulette, plant_roulette_no_reweight)
+                roulette, plant_roulette_no_reweight, antithetic)
     rc = lib().or_solve(
         ctypes.byref(D.s), _ptr(X), Q, N, int(walk_offset), float(eps), float(sigma), ctypes.byref(opt),
         int(threads), _ptr(out["u"]), _ptr(out["u_se"]), _ptr(out["grad"]), _ptr(out["grad_se"]),

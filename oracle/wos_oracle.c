@@ -47,6 +47,11 @@
  *       (term times the summed d log C / dsigma) stays unbiased because the survival
  *       probability's sigma-derivative is the summed d log C / dsigma up to that step. The
  *       uniform is the top 24 bits of Philox block 15 of (walk, step k), times 2^-24.
+ *   Antithetic first directions (optional; the closing discussion's variance reduction): the
+ *       walks of a query pair up (2m, 2m+1 of the global index, so walk_offset and N must be
+ *       even); walk 2m+1 takes the negated first direction of walk 2m, later steps their own.
+ *       Each direction stays uniform, so every estimate is unbiased; standard errors come from
+ *       the spread of the N/2 pair means. Not combined with the control variate.
  *   Extruded domains (Sec. VI, dimensionality study): with proj_dims = m < d every boundary
  *       component is measured in the first m coordinates only (the obstacles and the outer
  *       boundary extruded along the others, which are free and unbounded); walks, sources and
@@ -115,6 +120,7 @@ typedef struct {
     int32_t plant_free_space_source_grad; /* test only: drop the ball's image term in grad G_B */
     double roulette_w;      /* > 0: Russian roulette when the weight falls below it */
     int32_t plant_roulette_no_reweight; /* test only: survivors keep their weight */
+    int32_t antithetic;     /* 1: walk 2m+1 takes the negated first direction of walk 2m */
 } or_options;
 
 typedef struct {
@@ -436,7 +442,13 @@ void or_walk(const or_domain *D, const double *x0, uint64_t walk, double eps, do
                 }
             }
         }
-        or_direction(opt->seed, walk, (uint32_t)k, d, v);
+        if (k == 0 && opt->antithetic) {
+            or_direction(opt->seed, walk & ~(uint64_t)1, 0u, d, v);
+            if (walk & 1)
+                for (int j = 0; j < d; ++j) v[j] = -v[j];
+        } else {
+            or_direction(opt->seed, walk, (uint32_t)k, d, v);
+        }
         double z = R * sq;
         double Snu = or_series_S(nu, z);
         double Snu1 = or_series_S(nu + 1.0, z);
@@ -504,6 +516,7 @@ static void run_unit(solve_job *J, int64_t unit)
     memset(P, 0, sizeof(double) * J->nfields);
     I[0] = I[1] = I[2] = 0;
     or_walk_out o;
+    double pt = 0.0, pg[OR_MAXD]; /* antithetic: the even walk of the current pair */
     for (int64_t w = w0; w < w1; ++w) {
         uint64_t walk = (uint64_t)(J->walk_offset + q * J->N + w);
         or_walk(J->D, J->X + q * d, walk, J->eps, J->sigma, J->opt, &o);
@@ -527,6 +540,21 @@ static void run_unit(solve_job *J, int64_t unit)
             P[3 + d + j] += o.grad[j] * o.grad[j];
         }
         for (int k = 0; k < K; ++k) P[3 + 2 * d + k] += o.dw[k];
+        if (J->opt->antithetic) {
+            /* squares of the pair means, after the fields above: [u, grad[d]] */
+            double *A = P + 3 + 2 * d + K;
+            if ((w & 1) == 0) {
+                pt = o.term;
+                for (int j = 0; j < d; ++j) pg[j] = o.grad[j];
+            } else {
+                const double y = 0.5 * (pt + o.term);
+                A[0] += y * y;
+                for (int j = 0; j < d; ++j) {
+                    const double g = 0.5 * (pg[j] + o.grad[j]);
+                    A[1 + j] += g * g;
+                }
+            }
+        }
         I[0] += o.jumps + 1;
         I[1] += o.capped;
         I[2] += o.outside;
@@ -569,7 +597,8 @@ int or_solve(const or_domain *D, const double *X, int64_t Q, int64_t N, int64_t 
 {
     if (!D || !X || !opt || D->d < 1 || D->d > OR_MAXD || D->n_exp < 0 || D->n_exp > OR_MAXEXP ||
         D->proj_dims < 0 || D->proj_dims > D->d ||
-        Q < 0 || N < 1 || sigma < 0.0)
+        Q < 0 || N < 1 || sigma < 0.0 ||
+        (opt->antithetic && (N % 2 != 0 || walk_offset % 2 != 0 || opt->control_variate)))
         return -1;
     const int d = D->d, K = D->n_exp;
     solve_job J;
@@ -583,7 +612,7 @@ int or_solve(const or_domain *D, const double *X, int64_t Q, int64_t N, int64_t 
     J.sigma = sigma;
     J.opt = opt;
     J.nchunks = (N + OR_CHUNK - 1) / OR_CHUNK;
-    J.nfields = 3 + 2 * d + K;
+    J.nfields = 3 + 2 * d + K + (opt->antithetic ? 1 + d : 0);
     J.walk_term = walk_term;
     J.walk_jumps = walk_jumps;
     J.walk_grad = walk_grad;
@@ -617,7 +646,7 @@ int or_solve(const or_domain *D, const double *X, int64_t Q, int64_t N, int64_t 
     pthread_mutex_destroy(&J.lock);
 
     for (int64_t q = 0; q < Q; ++q) {
-        double S[3 + 2 * OR_MAXD + OR_MAXEXP];
+        double S[3 + 2 * OR_MAXD + OR_MAXEXP + 1 + OR_MAXD];
         int64_t I[3] = {0, 0, 0};
         memset(S, 0, sizeof(S));
         for (int64_t c = 0; c < J.nchunks; ++c) {
@@ -633,6 +662,13 @@ int or_solve(const or_domain *D, const double *X, int64_t Q, int64_t N, int64_t 
         for (int j = 0; j < d; ++j) {
             if (grad) grad[q * d + j] = S[3 + j] * inv;
             if (grad_se) grad_se[q * d + j] = I[2] ? NAN : se_of(S[3 + j], S[3 + d + j], N);
+        }
+        if (opt->antithetic) {
+            /* standard errors from the N/2 pair means (their sum is half the walks' sum) */
+            const double *A = S + 3 + 2 * d + K;
+            if (u_se) u_se[q] = I[2] ? NAN : se_of(0.5 * S[0], A[0], N / 2);
+            for (int j = 0; j < d; ++j)
+                if (grad_se) grad_se[q * d + j] = I[2] ? NAN : se_of(0.5 * S[3 + j], A[1 + j], N / 2);
         }
         if (cv) {
             /* first pass: tbar; second pass: y_w = G (t_w - tbar) v_w, its sum and spread */

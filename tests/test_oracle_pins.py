@@ -17,6 +17,9 @@ never against the oracle itself.
     cylinder surfaces, and the exp closed form with a along all or only the free coordinates
   * Russian roulette on the weight: the exp closed form with shorter walks, du/dsigma against
     the plain estimator, and a planted mistake (survivors not reweighted) that must fail
+  * antithetic first directions: paired walks' first directions are exact negatives, the exp
+    closed form with a lower gradient SE, and the pair-based SE against the spread of repeated
+    estimates (a per-walk SE would be ~3.7x too large)
 and one planted mistake (the paper's literal d/R gradient factor at sigma > 0), which the
 off-centre ball pin must reject.
 """
@@ -673,3 +676,50 @@ def test_planted_roulette_without_reweight_is_rejected(oracle_mod):
     res = oracle_mod.solve(dom, X, 40000, 1e-4, sigma, 3, roulette=0.3, plant_roulette_no_reweight=True)
     g = np.exp(X @ a)
     assert np.mean(np.abs(res["u"] - g) < 4.5 * res["u_se"] + 3e-4 * g * np.linalg.norm(a)) < 0.5
+
+
+# --------------------------------------------------------------------------- antithetic pairs
+def test_antithetic_pairs_take_opposite_first_directions(oracle_mod):
+    w = synth.c1(n_queries=1)
+    dom, x = w["domain"], w["X"][0]
+    for m in (0, 5, 123):
+        a = oracle_mod.walk(dom, x, 2 * m, 1e-4, w["sigma"], 7, grad=True, antithetic=True)
+        b = oracle_mod.walk(dom, x, 2 * m + 1, 1e-4, w["sigma"], 7, grad=True, antithetic=True)
+        assert np.array_equal(a["gv0"], -b["gv0"]) and np.any(a["gv0"] != 0)
+        plain = oracle_mod.walk(dom, x, 2 * m, 1e-4, w["sigma"], 7, grad=True)
+        assert np.array_equal(a["gv0"], plain["gv0"])  # the even walk is the plain walk
+
+
+def test_antithetic_exp_solution_with_lower_gradient_se(oracle_mod):
+    w = synth.c1(n_queries=16)
+    dom = w["domain"]
+    a = dom["exp_a"][0]
+    g = np.exp(w["X"] @ a)
+    bias = 3e-4 * np.abs(g) * np.linalg.norm(a)
+    plain = oracle_mod.solve(dom, w["X"], 20000, 1e-4, w["sigma"], w["seed"], grad=True)
+    anti = oracle_mod.solve(dom, w["X"], 20000, 1e-4, w["sigma"], w["seed"], grad=True, antithetic=True)
+    assert np.all(np.abs(anti["u"] - g) < 4.5 * anti["u_se"] + bias)
+    assert np.all(np.abs(anti["grad"] - a[None, :] * g[:, None]) < 4.5 * anti["grad_se"] + 10 * bias[:, None])
+    # the pair cancels the part of the walk value even in the first direction
+    assert anti["grad_se"].mean() < 0.5 * plain["grad_se"].mean()
+
+
+def test_antithetic_se_matches_the_spread_of_estimates(oracle_mod):
+    # pair means are independent, walks of a pair are not: the SE must come from the pairs
+    w = synth.c1(n_queries=1)
+    est = np.array([[r["grad"][0, 0], r["grad_se"][0, 0]] for r in
+                    (oracle_mod.solve(w["domain"], w["X"], 2000, 1e-4, w["sigma"], 100 + s, grad=True,
+                                      antithetic=True) for s in range(60))])
+    ratio = est[:, 1].mean() / est[:, 0].std(ddof=1)
+    assert 0.7 < ratio < 1.4, ratio
+
+
+def test_antithetic_rejects_unpaired_layouts(oracle_mod):
+    w = synth.c1(n_queries=1)
+    for kw in ({"n_walks": 3}, {"walk_offset": 1}, {"control_variate": True}):
+        args = dict(n_walks=4, walk_offset=0, control_variate=False)
+        args.update(kw)
+        with pytest.raises(ValueError):
+            oracle_mod.solve(w["domain"], w["X"], args["n_walks"], 1e-4, w["sigma"], 1, grad=True,
+                             walk_offset=args["walk_offset"], control_variate=args["control_variate"],
+                             antithetic=True)
