@@ -10,6 +10,9 @@ compiles it with gcc when needed and marshals numpy arrays through ctypes.
 Domains are plain dicts (see ``paper_2406_01713_gb300.synth``):
     d, box_lo/box_hi (optional), outer_c/outer_r (optional), goal_c/goal_r (optional),
     ball_c (B x d)/ball_r (B), points (M x d), exp_w (K)/exp_a (K x d).
+  Oracle-only boundary data for the closed-form pins: poly_c (n) / poly_p (n x d int
+  exponents), g = sum_m c_m prod_j x_j^p_mj on the whole boundary; face_g (2d), a constant
+  per box face in the order lo_0, hi_0, lo_1, ...
 """
 import ctypes
 import os
@@ -63,6 +66,11 @@ class _Domain(ctypes.Structure):
         ("source_z", ctypes.c_double * MAXD),
         ("source_q", ctypes.c_double),
         ("proj_dims", ctypes.c_int32),
+        ("n_poly", ctypes.c_int32),
+        ("poly_c", ctypes.POINTER(ctypes.c_double)),
+        ("poly_p", ctypes.POINTER(ctypes.c_int32)),
+        ("has_face_g", ctypes.c_int32),
+        ("face_g", ctypes.c_double * (2 * MAXD)),
     ]
 
 
@@ -198,6 +206,18 @@ class Domain:
             s.source_z[:d] = list(np.asarray(dom["source_z"], float))
             s.source_q = float(dom.get("source_q", 1.0))
         s.proj_dims = int(dom.get("proj_dims", 0))
+        if dom.get("poly_c") is not None:
+            pc = arr("poly_c", (-1,))
+            pp = np.ascontiguousarray(np.asarray(dom["poly_p"], dtype=np.int32).reshape(-1, d))
+            if pp.shape[0] != pc.shape[0] or np.any(pp < 0):
+                raise ValueError("poly_p must be n_poly x d non-negative exponents")
+            self._keep.append(pp)
+            s.n_poly = pc.shape[0]
+            s.poly_c = _ptr(pc)
+            s.poly_p = _ptr(pp, ctypes.c_int32)
+        if dom.get("face_g") is not None:
+            s.has_face_g = 1
+            s.face_g[:2 * d] = list(np.asarray(dom["face_g"], float).reshape(2 * d))
         self.n_exp = int(s.n_exp)
         self.s = s
 

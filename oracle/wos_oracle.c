@@ -39,6 +39,10 @@
  *       x <- x + s grad/|grad|,  s = min(s_ub, 0.5 d_bound).
  *   Distance functions (Sec. VI, Eq. for d(x, dOmega); Sec. VII-A point-set distance):
  *       balls: |x - c| - r;  outer ball: r_o - |x - c_o|;  points: |x - p|;  box faces.
+ *   Boundary data g (Sec. III, u = g on the boundary): the goal indicator of the planning
+ *       field, sum_k w_k exp(a_k . x), and two forms used only by the closed-form pins: a
+ *       polynomial sum_m c_m prod_j x_j^p_mj (harmonic ones solve sigma = 0 exactly) and one
+ *       constant per box face (the unit square with g = 1 on one edge).
  *   Russian roulette on the weight (optional; the closing discussion's "Russian roulette on C"
  *       variance/cost trade-off, not an estimator the paper prints): before each jump k >= 1
  *       whose weight W = prod C is below w_min, the walk survives with probability W / w_min
@@ -109,6 +113,11 @@ typedef struct {
     double source_z[OR_MAXD];
     double source_q;
     int32_t proj_dims;    /* 0 or d: distances in all coordinates; m < d: in the first m only */
+    int32_t n_poly;       /* >0 (and n_exp = 0): g(x) = sum_m poly_c[m] prod_j x_j^poly_p[m d + j] */
+    const double *poly_c; /* n_poly coefficients */
+    const int32_t *poly_p; /* n_poly x d exponents */
+    int32_t has_face_g;   /* 1 (no exp or poly data): g = face_g[2j] on face lo_j, face_g[2j+1] on hi_j */
+    double face_g[2 * OR_MAXD];
 } or_domain;
 
 typedef struct {
@@ -356,8 +365,14 @@ double or_distance(const or_domain *D, const double *x, int32_t *kind, int64_t *
     return best;
 }
 
-/* Boundary data: sum_k w_k exp(a_k . xbar) if exp data is set, else 1 on the goal, 0 elsewhere. */
-static double boundary_g(const or_domain *D, int32_t kind, const double *xbar, double *dw)
+/* Boundary data g at the closest boundary point (Sec. III: u = g on the boundary):
+ *   exp data:        sum_k w_k exp(a_k . xbar) on the whole boundary;
+ *   polynomial data: sum_m c_m prod_j xbar_j^p_mj on the whole boundary (harmonic polynomials
+ *                    are exact solutions at sigma = 0);
+ *   face data:       a constant per box face (the unit square with g = 1 on one edge), 1 on the
+ *                    goal, 0 on other components;
+ *   otherwise:       1 on the goal, 0 elsewhere (the planning field). */
+static double boundary_g(const or_domain *D, int32_t kind, int64_t index, const double *xbar, double *dw)
 {
     if (D->n_exp > 0) {
         double g = 0.0;
@@ -370,6 +385,17 @@ static double boundary_g(const or_domain *D, int32_t kind, const double *xbar, d
         }
         return g;
     }
+    if (D->n_poly > 0) {
+        double g = 0.0;
+        for (int m = 0; m < D->n_poly; ++m) {
+            double t = D->poly_c[m];
+            for (int j = 0; j < D->d; ++j)
+                for (int e = 0; e < D->poly_p[m * D->d + j]; ++e) t *= xbar[j];
+            g += t;
+        }
+        return g;
+    }
+    if (D->has_face_g && kind == OR_KIND_FACE) return D->face_g[index];
     return kind == OR_KIND_GOAL ? 1.0 : 0.0;
 }
 
@@ -403,7 +429,7 @@ void or_walk(const or_domain *D, const double *x0, uint64_t walk, double eps, do
         int in_shell = R < eps;
         if (in_shell && !(opt->grad && k == 0)) {
             double dw[OR_MAXEXP];
-            double g = boundary_g(D, kind, xbar, dw);
+            double g = boundary_g(D, kind, index, xbar, dw);
             double w = exp(logw);
             out->term = g * w + src;
             for (int q = 0; q < D->n_exp; ++q) out->dw[q] = w * dw[q];
@@ -596,7 +622,7 @@ int or_solve(const or_domain *D, const double *X, int64_t Q, int64_t N, int64_t 
              int64_t *walk_jumps, double *walk_grad, double *walk_dsigma)
 {
     if (!D || !X || !opt || D->d < 1 || D->d > OR_MAXD || D->n_exp < 0 || D->n_exp > OR_MAXEXP ||
-        D->proj_dims < 0 || D->proj_dims > D->d ||
+        D->proj_dims < 0 || D->proj_dims > D->d || D->n_poly < 0 ||
         Q < 0 || N < 1 || sigma < 0.0 ||
         (opt->antithetic && (N % 2 != 0 || walk_offset % 2 != 0 || opt->control_variate)))
         return -1;

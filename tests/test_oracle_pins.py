@@ -20,6 +20,14 @@ never against the oracle itself.
   * antithetic first directions: paired walks' first directions are exact negatives, the exp
     closed form with a lower gradient SE, and the pair-based SE against the spread of repeated
     estimates (a per-walk SE would be ~3.7x too large)
+  * point sets (Sec. VII-A): the distance, component and closest point against numpy
+    enumeration (plain and extruded, with every other component kind present), exact ties
+    between a point and the components before and after it in the tie order, and the exp closed
+    form on a box-plus-points domain (extruded: with a along the free coordinate)
+  * sigma = 0 with harmonic polynomial data on a ball (P4): u = g, grad u = grad g
+  * the unit square with g = 1 on the top edge (P5): u and grad u against the
+    separation-of-variables series, itself checked against a Richardson-extrapolated 5-point
+    finite-difference solve on 65^2 and 129^2 grids
 and one planted mistake (the paper's literal d/R gradient factor at sigma > 0), which the
 off-centre ball pin must reject.
 """
@@ -723,3 +731,203 @@ def test_antithetic_rejects_unpaired_layouts(oracle_mod):
             oracle_mod.solve(w["domain"], w["X"], args["n_walks"], 1e-4, w["sigma"], 1, grad=True,
                              walk_offset=args["walk_offset"], control_variate=args["control_variate"],
                              antithetic=True)
+
+
+# --------------------------------------------------------------------------- point sets (Sec. VII-A)
+_ORDER = {"goal": 0, "ball": 1, "point": 2, "outer": 3, "face": 4}
+
+
+def _brute_distance(dom, x):
+    """Distance, component and closest point by enumerating every component in numpy, in the
+    tie order goal, balls, points, outer ball, box faces (lo_0, hi_0, lo_1, ...); the components
+    are measured in the first proj_dims coordinates and the closest point keeps the others."""
+    d = dom["d"]
+    m = dom.get("proj_dims", 0) or d
+    cands = []  # (distance, kind, index)
+    if dom.get("goal_r") is not None:
+        cands.append((np.linalg.norm(x[:m] - dom["goal_c"][:m]) - dom["goal_r"], 0, 0))
+    for i, (c, r) in enumerate(zip(dom.get("ball_c", []), dom.get("ball_r", []))):
+        cands.append((np.linalg.norm(x[:m] - c[:m]) - r, 1, i))
+    pts = dom.get("points")
+    if pts is not None:
+        dist = np.linalg.norm(pts[:, :m] - x[None, :m], axis=1)
+        for i in range(pts.shape[0]):
+            cands.append((dist[i], 2, i))
+    if dom.get("outer_r") is not None:
+        cands.append((dom["outer_r"] - np.linalg.norm(x[:m] - dom["outer_c"][:m]), 3, 0))
+    if dom.get("box_lo") is not None:
+        for j in range(m):
+            cands.append((x[j] - dom["box_lo"][j], 4, 2 * j))
+            cands.append((dom["box_hi"][j] - x[j], 4, 2 * j + 1))
+    best = min(range(len(cands)), key=lambda t: (cands[t][0], t))  # first of the minima
+    R, kind, idx = cands[best]
+    xbar = x.copy()
+    if kind == 2:
+        xbar[:m] = pts[idx, :m]
+    elif kind == 4:
+        xbar[idx // 2] = dom["box_lo"][idx // 2] if idx % 2 == 0 else dom["box_hi"][idx // 2]
+    else:
+        c = {0: dom.get("goal_c"), 1: None if kind != 1 else dom["ball_c"][idx], 3: dom.get("outer_c")}[kind]
+        r = {0: dom.get("goal_r"), 1: None if kind != 1 else dom["ball_r"][idx], 3: dom.get("outer_r")}[kind]
+        v = x[:m] - c[:m]
+        xbar[:m] = c[:m] + r * v / np.linalg.norm(v)
+    return R, kind, idx, xbar
+
+
+@pytest.mark.parametrize("d,m", [(2, 2), (3, 3), (7, 7), (4, 2)])
+def test_point_set_distance_brute_force(oracle_mod, d, m):
+    """The point-set branch of the distance and its closest point, in a domain that also holds
+    a goal, balls, an outer ball and a box, against numpy enumeration of every component."""
+    rng = np.random.default_rng(40 + d + m)
+    dom = {"d": d, "box_lo": -np.ones(d), "box_hi": np.ones(d), "outer_c": 0.1 * np.ones(d), "outer_r": 1.3,
+           "goal_c": rng.uniform(-0.5, 0.5, d), "goal_r": 0.05,
+           "ball_c": rng.uniform(-0.8, 0.8, (5, d)), "ball_r": rng.uniform(0.02, 0.08, 5),
+           "points": rng.uniform(-0.9, 0.9, (300, d))}
+    if m < d:
+        dom["proj_dims"] = m
+    kinds = set()
+    for x in rng.uniform(-0.95, 0.95, (400, d)):
+        R, kind, idx, xbar = oracle_mod.distance(dom, x)
+        Rb, kb, ib, xb = _brute_distance(dom, x)
+        assert abs(R - Rb) <= 1e-14 * max(1.0, abs(Rb))
+        assert (kind, idx) == (kb, ib)
+        assert np.allclose(xbar, xb, rtol=0, atol=1e-14)
+        kinds.add(kind)
+    assert 2 in kinds  # the point branch was taken
+
+
+def test_point_set_ties_go_to_the_lower_component():
+    """Exact ties (all values dyadic): a point beats the outer ball and a box face at the same
+    distance, and a ball beats a point."""
+    import oracle as oracle_mod
+
+    dom = {"d": 2, "outer_c": np.zeros(2), "outer_r": 1.0, "points": np.array([[0.5, 0.5]])}
+    R, kind, idx, xbar = oracle_mod.distance(dom, np.array([0.5, 0.0]))
+    assert (R, kind, idx) == (0.5, oracle_mod.KIND_POINT, 0) and np.array_equal(xbar, [0.5, 0.5])
+    dom = {"d": 2, "box_lo": np.zeros(2), "box_hi": np.ones(2), "points": np.array([[0.25, 0.75]])}
+    R, kind, idx, xbar = oracle_mod.distance(dom, np.array([0.25, 0.5]))
+    assert (R, kind) == (0.25, oracle_mod.KIND_POINT) and np.array_equal(xbar, [0.25, 0.75])
+    dom["ball_c"], dom["ball_r"] = np.array([[0.75, 0.5]]), np.array([0.25])
+    R, kind, idx, xbar = oracle_mod.distance(dom, np.array([0.25, 0.5]))
+    assert (R, kind) == (0.25, oracle_mod.KIND_BALL) and np.allclose(xbar, [0.5, 0.5], atol=0)
+
+
+def _ring_points(d, n, centre, radius, rng):
+    """n points on a circle in the first two coordinates (other coordinates uniform in [-1, 1])."""
+    t = 2 * math.pi * (np.arange(n) + 0.5) / n
+    p = np.zeros((n, d))
+    p[:, 0] = centre[0] + radius * np.cos(t)
+    p[:, 1] = centre[1] + radius * np.sin(t)
+    if d > 2:
+        p[:, 2:] = rng.uniform(-1, 1, (n, d - 2))
+    return p
+
+
+@pytest.mark.parametrize("d,m", [(2, 2), (3, 2)])
+def test_point_set_exp_data_exact_solution(oracle_mod, d, m):
+    """g = exp(a.x) with |a|^2 = sigma is the exact solution on a box-plus-points domain: walks
+    that end on a point read g at the point (and, extruded, at the walker's free coordinates).
+    The point ring is denser than eps, so it acts as a wall and many walks end on it."""
+    rng = np.random.default_rng(90 + d)
+    sigma = 4.0
+    a = rng.standard_normal(d)
+    if m < d:
+        a[m:] *= 3.0  # weight the free coordinate: a projection that dropped it would fail
+    a *= math.sqrt(sigma) / np.linalg.norm(a)
+    dom = {"d": d, "box_lo": np.zeros(d), "box_hi": np.ones(d),
+           "points": _ring_points(d, 600, (0.5, 0.5), 0.2, rng), "exp_w": np.ones(1), "exp_a": a[None, :]}
+    if m < d:
+        dom["proj_dims"] = m
+        dom["box_lo"][m:], dom["box_hi"][m:] = -5.0, 5.0
+    X = np.array([[0.15, 0.5], [0.5, 0.85], [0.8, 0.2], [0.5, 0.5]])
+    if d > 2:
+        X = np.hstack([X, rng.uniform(-0.5, 0.5, (4, d - 2))])
+    eps = 4e-3
+    res = oracle_mod.solve(dom, X, 20000, eps, sigma, seed=5, grad=True)
+    g = np.exp(X @ a)
+    bias = eps * np.linalg.norm(a) * g  # O(eps) shell bias
+    assert np.all(np.abs(res["u"] - g) < 4.5 * res["u_se"] + bias)
+    assert np.all(np.abs(res["grad"] - a[None, :] * g[:, None]) < 4.5 * res["grad_se"] + 10 * bias[:, None])
+    kinds = [oracle_mod.walk(dom, X[0], w, eps, sigma, 5)["comp_kind"] for w in range(400)]
+    assert np.mean(np.array(kinds) == oracle_mod.KIND_POINT) > 0.3
+
+
+# --------------------------------------------------------------------------- P4: sigma = 0, harmonic data
+@pytest.mark.parametrize("d,poly", [(2, "x1^2-x2^2"), (3, "x1^2-x2^2"), (3, "x1x2x3")])
+def test_laplace_harmonic_polynomial_on_a_ball(oracle_mod, d, poly):
+    """sigma = 0 (C = 1 exactly, gradient factor d/R0) on the unit ball with harmonic
+    polynomial data: u = g and grad u = grad g inside."""
+    if poly == "x1^2-x2^2":
+        c, p = np.array([1.0, -1.0]), np.zeros((2, d), np.int32)
+        p[0, 0], p[1, 1] = 2, 2
+        u_f = lambda x: x[0] ** 2 - x[1] ** 2
+        g_f = lambda x: np.r_[2 * x[0], -2 * x[1], np.zeros(d - 2)]
+    else:
+        c, p = np.array([1.0]), np.ones((1, d), np.int32)
+        u_f = lambda x: x[0] * x[1] * x[2]
+        g_f = lambda x: np.array([x[1] * x[2], x[0] * x[2], x[0] * x[1]])
+    dom = {"d": d, "outer_c": np.zeros(d), "outer_r": 1.0, "poly_c": c, "poly_p": p}
+    rng = np.random.default_rng(7 + d)
+    X = []
+    for rad in [0.3, 0.55, 0.8]:
+        v = rng.standard_normal(d)
+        X.append(rad * v / np.linalg.norm(v))
+    X = np.array(X)
+    res = oracle_mod.solve(dom, X, 40000, 1e-5, 0.0, seed=31 + d, grad=True)
+    for q in range(len(X)):
+        assert abs(res["u"][q] - u_f(X[q])) < 4.5 * res["u_se"][q] + 1e-4
+        assert np.all(np.abs(res["grad"][q] - g_f(X[q])) < 4.5 * res["grad_se"][q] + 1e-3)
+
+
+# --------------------------------------------------------------------------- P5: unit square, g = 1 on the top edge
+def square_series(x, y, sigma, terms=4000):
+    """u = sum_{k odd} 4/(k pi) sin(k pi x) sinh(l_k y)/sinh(l_k), l_k = sqrt(k^2 pi^2 + sigma),
+    and its gradient (separation of variables), for 0 < y < 1."""
+    k = np.arange(1, 2 * terms, 2, dtype=float)
+    lam = np.sqrt((k * math.pi) ** 2 + sigma)
+    ratio = np.exp(lam * (y - 1.0)) * (1 - np.exp(-2 * lam * y)) / (1 - np.exp(-2 * lam))  # sinh(l y)/sinh(l)
+    dratio = lam * np.exp(lam * (y - 1.0)) * (1 + np.exp(-2 * lam * y)) / (1 - np.exp(-2 * lam))
+    c = 4.0 / (k * math.pi)
+    u = np.sum(c * np.sin(k * math.pi * x) * ratio)
+    ux = np.sum(c * k * math.pi * np.cos(k * math.pi * x) * ratio)
+    uy = np.sum(c * np.sin(k * math.pi * x) * dratio)
+    return u, np.array([ux, uy])
+
+
+def square_fd(n, sigma):
+    """5-point finite differences of Laplace(u) = sigma u on an (n+1)^2 grid of the unit square,
+    u = 1 on the top edge (0.5 at its two corners), 0 on the other edges."""
+    from scipy.sparse import diags, identity, kron
+    from scipy.sparse.linalg import spsolve
+
+    h = 1.0 / n
+    m = n - 1
+    T = diags([np.ones(m - 1), -2 * np.ones(m), np.ones(m - 1)], [-1, 0, 1]) / h ** 2
+    I = identity(m)
+    A = (kron(I, T) + kron(T, I) - sigma * kron(I, I)).tocsr()  # unknowns ordered (row y, col x)
+    b = np.zeros(m * m)
+    b[(m - 1) * m:] -= 1.0 / h ** 2  # the top row's neighbours on y = 1 carry u = 1
+    U = np.zeros((n + 1, n + 1))
+    U[1:n, 1:n] = spsolve(A, b).reshape(m, m)
+    U[n, :] = 1.0
+    U[n, 0] = U[n, n] = 0.5
+    return U  # U[iy, ix]
+
+
+@pytest.mark.parametrize("sigma", [0.0, 10.0])
+def test_unit_square_top_edge_fd_and_series(oracle_mod, sigma):
+    """Unit square, g = 1 on the top edge (face hi_1) and 0 elsewhere: the oracle's u and grad u
+    against the separation-of-variables series, which is itself checked against a
+    Richardson-extrapolated 5-point finite-difference solve on 65^2 and 129^2 grids."""
+    pts = np.array([[0.5, 0.5], [0.25, 0.75], [0.75, 0.375], [0.5, 0.875], [0.125, 0.25]])
+    U64, U128 = square_fd(64, sigma), square_fd(128, sigma)
+    for x, y in pts:
+        us, _ = square_series(x, y, sigma)
+        u_rich = (4 * U128[int(round(128 * y)), int(round(128 * x))] - U64[int(round(64 * y)), int(round(64 * x))]) / 3
+        assert abs(u_rich - us) < 2e-4, (x, y, u_rich, us)
+    dom = {"d": 2, "box_lo": np.zeros(2), "box_hi": np.ones(2), "face_g": np.array([0.0, 0.0, 0.0, 1.0])}
+    res = oracle_mod.solve(dom, pts, 40000, 1e-5, sigma, seed=17, grad=True)
+    for q, (x, y) in enumerate(pts):
+        us, gs = square_series(x, y, sigma)
+        assert abs(res["u"][q] - us) < 4.5 * res["u_se"][q] + 1e-4, (q, res["u"][q], us)
+        assert np.all(np.abs(res["grad"][q] - gs) < 4.5 * res["grad_se"][q] + 1e-3), (q, res["grad"][q], gs)
