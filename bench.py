@@ -108,11 +108,31 @@ def measured_traffic(profile=TRAFFIC_PROFILE, sources=KERNEL_SOURCES):
         return None
 
 
-def alg_flops_per_step(d, n_balls):
+def alg_flops_per_step(d, n_balls, n_points=0):
     """Algorithmic FP32 flops of one walk step (one distance evaluation): the ball screen
-    costs 2d+3 flops per ball (d FMAs of x.m, the b-term FMA and the threshold add), the
-    box faces and sampling about 4d."""
-    return n_balls * (2 * d + 3) + 4 * d
+    costs 2d+3 flops per ball (d FMAs of x.m, the b-term FMA and the threshold add), a point
+    2d+1 (d FMAs and the compare), the box faces and sampling about 4d."""
+    return n_balls * (2 * d + 3) + n_points * (2 * d + 1) + 4 * d
+
+
+def contraction_k(d):
+    """Columns of the tensor-core walker's BF16-split contraction (3d + 2, padded to 32 or 48)."""
+    return 32 if 3 * d + 2 <= 32 else 48
+
+
+def domain_sizes(dom):
+    return (dom["ball_r"].size if "ball_r" in dom else 0), (dom["points"].shape[0] if "points" in dom else 0)
+
+
+FP32_LANES_PER_SM = 128
+
+
+def fp32_peak_tflops(sms, sm_mhz):
+    """FP32 FMA pipe: SMs x 128 lanes x 2 flops x SM clock."""
+    return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (nominal: the measured-peaks file holds no FP64 figure)
 
 
 # ------------------------------------------------------------------------------ clocks
@@ -310,6 +330,7 @@ def main():
 
     # accuracy: exact solution u = exp(a.x), grad u = a u on the exponential-data problems
     rmse_u, rmse_g, rmse_gn = exact_rmse(probs, batch.out)
+    calib = se_calibration(probs, batch.out)
 
     # end to end through the public API: pinned host queries in, u and grad u out, each step
     x_host = batch.x_buf.cpu().pin_memory()
@@ -340,7 +361,8 @@ def main():
                                props.multi_processor_count, sm_max, flush)
     roofline = dict(max(kernels.values(), key=lambda r: r["ms"]))
     roofline["all_kernels"] = {k: {kk: v for kk, v in r.items() if kk in ("bound", "achieved", "peak", "unit",
-                                                                           "frac", "ms", "share", "kernel")}
+                                                                           "frac", "ms", "share", "kernel",
+                                                                           "mma_achieved", "mma_frac")}
                                for k, r in kernels.items()}
     n_sphere_dims = len({p["domain"]["d"] for d, p in zip(doms, probs) if d.info()["tensor_sphere_set"]})
     launches_per_step = 1 + (0 if args.no_cv else 1) + n_sphere_dims + (1 if "cuda_core" in kernels else 0)
@@ -356,6 +378,7 @@ def main():
             "grad_evals_per_s": total_q * args.steps * world / dev_s,
             "rmse": {"u_rel": rmse_u, "grad_rel": rmse_g, "grad_rel_aggregate": rmse_gn,
                      "against": "exact solution exp(a.x) on the 128 exponential-data problems",
+                     "rmse_over_rms_se": calib,
                      "grad_estimator": "first sphere" + ("" if args.no_cv else " with control variate")},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
             "wall_s": wall}
@@ -365,10 +388,15 @@ def main():
         if not args.no_cv:
             line["without_control_variate"] = paper_estimator(W, doms, probs, replica_seed(w["seed"], rank),
                                                               tuned, ms_per_step)
+        try:
+            line["error_vs_fp64_same_stream"] = fp64_same_stream(W, doms, probs, batch.out,
+                                                                 replica_seed(w["seed"], rank), not args.no_cv)
+        except Exception as e:
+            line["error_vs_fp64_same_stream"] = {"error": "%s: %s" % (type(e).__name__, e)}
         line["vs_plain_fp32"] = plain_comparison(W, doms, probs, w["seed"], total_steps, dev_s / args.steps,
                                                  rmse_u, not args.no_cv)
         try:
-            line["secondary"] = secondary(W, synth)
+            line["secondary"] = secondary(W, synth, peaks, props.multi_processor_count, sm_max)
         except Exception as e:  # a side measurement must not cost the headline line
             line["secondary"] = {"error": "%s: %s" % (type(e).__name__, e)}
     if rank == 0:
@@ -385,12 +413,13 @@ def main():
 
 def kernel_rooflines(W, doms, probs, seed, config, cv, peaks, sms, sm_max, flush):
     """Roofline of each walker family, each timed alone with CUDA events (two launches after a
-    warm-up, L2 flushed before each) on the problems the batch gives it:
-      * CUDA-core persistent walker: FP32 ALU bound, algorithmic flops per walk-step
-        B(2d+3) + 4d, against 152 SMs x 128 lanes x 2 flops x the maximum SM clock;
-      * tensor-core sphere-set walker: bound by the tensor pipe, algorithmic flops per walk-step
-        B x 2(3d+2) (the BF16-split contraction |c|^2 - 2x.c over every sphere), against the
-        measured sustained dense BF16 peak (the launch runs for a second or more)."""
+    warm-up, L2 flushed before each) on the problems the batch gives it. Both count the
+    method's algorithmic flops per walk-step, B(2d+3) + 4d:
+      * CUDA-core persistent walker: FP32 ALU bound, against 152 SMs x 128 lanes x 2 flops x the
+        maximum SM clock;
+      * tensor-core sphere-set walker: bound by the tensor pipe, against the measured sustained
+        dense BF16 peak (the launch runs for half a second or more); the BF16-split contraction
+        it issues (2K flops per sphere) is reported beside it as mma_*."""
     import torch
 
     tens = [i for i, d in enumerate(doms) if d.info()["tensor_sphere_set"]]
@@ -426,18 +455,26 @@ def kernel_rooflines(W, doms, probs, seed, config, cv, peaks, sms, sm_max, flush
                  "traffic_note": "ncu dram__bytes_read+write per launch (profiles/walk_mixed_batched_traffic.txt); "
                                  "balls, queries and sums are L2-resident"}
         else:
-            fl = 0
+            fl, mma = 0, 0
             for s_, i in zip(steps, idx):
                 dd = probs[i]["domain"]
-                m = dd["ball_r"].size if "ball_r" in dd else dd["points"].shape[0]
-                fl += s_ * m * 2 * (3 * dd["d"] + 2)
+                nb, npnt = domain_sizes(dd)
+                fl += s_ * alg_flops_per_step(dd["d"], nb, npnt)
+                m = nb + npnt
+                mma += s_ * (-(-m // 64) * 64) * 2 * contraction_k(dd["d"])
             peak = peaks.get("bf16_tflops_sustained") or 1700.0
             r = {"bound": "tensor", "peak": peak, "peak_note": "measured sustained dense BF16 (cuBLAS), "
                  "MEASURED_PEAKS.json", "kernel": "sphere_kernel<d, true> (tensor-core sphere-set walker, one "
                  "launch per dimension)", "traffic": measured_traffic(SPHERE_TRAFFIC_PROFILE, SPHERE_SOURCES),
                  "traffic_note": "ncu dram__bytes_read+write summed over the per-dimension launches of one "
                                  "batch run (profiles/sphere_kernel_batched_traffic.txt); tiles and sums are "
-                                 "L2-resident"}
+                                 "L2-resident",
+                 "flops_note": "achieved counts the method's work, B(2d+3)+4d flops per walk-step (the same "
+                               "count as the CUDA-core walker); mma_* count the BF16-split contraction the "
+                               "tensor cores execute, 2K per sphere per walk-step (K = 3d+2 padded to 32/48, "
+                               "spheres padded to 64-column tiles)",
+                 "mma_flops_per_launch": mma, "mma_achieved": mma / (ms / 1e3) / 1e12,
+                 "mma_frac": mma / (ms / 1e3) / 1e12 / peak}
         achieved = fl / (ms / 1e3) / 1e12
         r.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / r["peak"], "ms": ms,
                   "flops_per_launch": fl, "problems": len(idx)})
@@ -600,38 +637,121 @@ def paper_sweeps(W, synth):
                     "angle point (2, -6) assumed; paths from (-8, 0)"}
 
 
-def secondary(W, synth):
-    """Quick measurements of the other workloads (not the headline)."""
+def _timed(fn):
+    """Device time (ms) of fn() with CUDA events on the current stream, synchronised on both sides."""
+    import torch
+
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), r
+
+
+def roofline_of(flops, ms, peak, bound, note):
+    achieved = flops / (ms / 1e3) / 1e12
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "flops": flops, "ms": ms, "note": note}
+
+
+def path_walk_steps(W, dom, path, flags, n_walks, eps, sigma, seed, cv=False):
+    """Walk-steps of a planner path: every step that ran walks (flag 0 or 2) is re-run at its
+    path point with its own walk offset (the same walks, so the same counts)."""
+    p, f = path.cpu().numpy(), flags.cpu().numpy()
+    total = 0
+    for i in range(len(f)):
+        if f[i] in (0, 2):
+            r = dom.grad(p[i][None, :], n_walks, eps, sigma, seed=seed, walk_offset=i * n_walks, with_stats=True,
+                         control_variate=cv)
+            total += int(r["stats"][1])
+    return total
+
+
+def fp64_same_stream(W, doms, probs, outs, seed, cv, n_pick=24):
+    """Error of the mixed-precision batch against the FP64 GPU walker on the same walks (same
+    Philox streams, walk indices and control variate): one query from each of n_pick problems,
+    half of them on the tensor-core sphere-set walker, including the problems with the most balls
+    and the most walks. Returns the largest |mixed - FP64| of u and of grad u, and the largest
+    ratio to the combined standard error."""
+    bases = np.cumsum([0] + [p["X"].shape[0] * p["n_walks"] for p in probs])
+    rng = np.random.default_rng(13)
+    tens = [i for i, d in enumerate(doms) if d.info()["tensor_sphere_set"]]
+    core = [i for i in range(len(doms)) if i not in set(tens)]
+    heavy = [max(tens, key=lambda i: probs[i]["domain"]["ball_r"].size * probs[i]["domain"]["d"]),
+             max(tens, key=lambda i: probs[i]["n_walks"])] if tens else []
+    pick = list(dict.fromkeys(heavy + list(rng.permutation(tens)[: n_pick // 2 - len(heavy)]) +
+                              list(rng.permutation(core)[: n_pick // 2])))
+    du, dg, ru, rg = 0.0, 0.0, 0.0, 0.0
+    for i in pick:
+        p, o = probs[i], outs[i]
+        q = int(rng.integers(p["X"].shape[0]))
+        r = doms[i].grad(p["X"][q:q + 1], p["n_walks"], p["eps"], p["sigma"], precision="fp64", seed=seed,
+                         walk_offset=int(bases[i]) + q * p["n_walks"], control_variate=cv)
+        u64, g64 = float(r["u"][0]), r["grad"][0].cpu().numpy()
+        se_u, se_g = float(r["u_se"][0]), r["grad_se"][0].cpu().numpy()
+        um, gm = float(o["u"][q]), o["grad"][q].cpu().numpy()
+        du = max(du, abs(um - u64))
+        dg = max(dg, float(np.max(np.abs(gm - g64))))
+        ru = max(ru, abs(um - u64) / max(se_u, 1e-300))
+        rg = max(rg, float(np.max(np.abs(gm - g64) / np.maximum(se_g, 1e-300))))
+    return {"problems": len(pick), "tensor_core_problems": sum(1 for i in pick if i in set(tens)),
+            "max_abs_u": du, "max_abs_grad": dg, "max_u_over_se": ru, "max_grad_over_se": rg,
+            "note": "one query from each problem, mixed batch output against the FP64 GPU walker on the same walks"}
+
+
+def se_calibration(probs, outs):
+    """RMSE over the reported standard error on the exponential-data problems (exact solution
+    exp(a.x)): sqrt(mean err^2) / sqrt(mean se^2), pooled over queries (u) and components (grad u).
+    About 1 when the errors are the sampling noise the standard errors state."""
+    eu, su, eg, sg = [], [], [], []
+    for p, o in zip(probs, outs):
+        if "exp_a" in p["domain"]:
+            a = p["domain"]["exp_a"][0]
+            us = np.exp(p["X"] @ a)
+            eu.append(o["u"].cpu().numpy() - us)
+            su.append(o["u_se"].cpu().numpy())
+            eg.append((o["grad"].cpu().numpy() - a[None, :] * us[:, None]).ravel())
+            sg.append(o["grad_se"].cpu().numpy().ravel())
+    rms = lambda v: float(np.sqrt(np.mean(np.concatenate(v) ** 2)))
+    return {"u": rms(eu) / rms(su), "grad": rms(eg) / rms(sg)}
+
+
+def secondary(W, synth, peaks, sms, sm_max):
+    """Measurements of the other workloads (not the headline), each with the roofline of its
+    dominant kernel: algorithmic flops per walk-step from the method (B(2d+3) + 4d for balls,
+    M(2d+1) + 4d for points) over the device time of the call (CUDA events)."""
     import torch
 
     out = {}
+    fp32 = fp32_peak_tflops(sms, sm_max)
+    bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
     # 2D planning field: 200-step graph-replayed path, 1024 walks per grad u
     w = synth.c2()
     dom = W.Domain(w["domain"])
     dom.plan_path(w["start"], 5, w["n_walks"], w["eps"], w["sigma"], w["s_ub"], seed=w["seed"])
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    path, flags, _ = dom.plan_path(w["start"], w["n_steps"], w["n_walks"], w["eps"], w["sigma"], w["s_ub"],
-                                   seed=w["seed"])
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t
+    ms, (path, flags, _) = _timed(lambda: dom.plan_path(w["start"], w["n_steps"], w["n_walks"], w["eps"],
+                                                        w["sigma"], w["s_ub"], seed=w["seed"]))
     f = flags.cpu().numpy()
-    out["planning_2d"] = {"path_ms": 1e3 * dt, "ms_per_planner_step": 1e3 * dt / w["n_steps"],
-                          "reached_goal_at_step": int(np.argmax(f == 1)) if (f == 1).any() else None}
+    ran = int(np.sum((f == 0) | (f == 2)))
+    steps = path_walk_steps(W, dom, path, flags, w["n_walks"], w["eps"], w["sigma"], w["seed"])
+    out["planning_2d"] = {"path_ms": ms, "ms_per_planner_step": ms / max(ran, 1), "planner_steps_with_walks": ran,
+                          "reached_goal_at_step": int(np.argmax(f == 1)) if (f == 1).any() else None,
+                          "grad_evals_per_s": ran / (ms / 1e3), "walk_steps_per_s": steps / (ms / 1e3),
+                          "roofline": roofline_of(steps * alg_flops_per_step(2, 33), ms, fp32, "alu",
+                                                  "latency-bound: 1024 walks per dependent step; FP32 FMA peak")}
     # the paper's two-disc environment with a unit impulse at the goal (Sec. VI): r_o = 10,
     # k_r = 0.3, c = sigma = 1, eps = 0.01, start (-8, 0); the goal (8, 0) is this benchmark's
     # choice (the paper shows it only in a figure). 1024 walks per planner step.
     env = synth.paper_environment(2)
     dom = W.Domain(env)
     dom.plan_path(np.array([-8.0, 0.0]), 5, 1024, 0.01, 1.0, 0.1, seed=1, control_variate=True)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    path, flags, _ = dom.plan_path(np.array([-8.0, 0.0]), 400, 1024, 0.01, 1.0, 0.1, seed=1, control_variate=True)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t
+    ms, (path, flags, _) = _timed(lambda: dom.plan_path(np.array([-8.0, 0.0]), 400, 1024, 0.01, 1.0, 0.1, seed=1,
+                                                        control_variate=True))
     f = flags.cpu().numpy()
     p_end = path.cpu().numpy()[-1]
-    out["paper_environment_2d"] = {"path_ms": 1e3 * dt, "ms_per_planner_step": 1e3 * dt / 400,
+    out["paper_environment_2d"] = {"path_ms": ms, "ms_per_planner_step": ms / 400,
                                    "reached_goal_at_step": int(np.argmax(f == 1)) if (f == 1).any() else None,
                                    "final_distance_to_goal": float(np.linalg.norm(p_end - env["source_z"]))}
     try:
@@ -648,46 +768,59 @@ def secondary(W, synth):
     u.sum().backward()
     torch.cuda.synchronize()
     fwd, fb = [], []
-    for _ in range(3):  # best of three: the first backward pass can include one-time host work
-        t = time.perf_counter()
-        r = dom.grad(X.detach(), w["n_walks"], w["eps"], w["sigma"], seed=w["seed"], with_stats=True)
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
+
+    def fwd_bwd():
         X.grad = None
         u = W.WoSFunction.apply(X, sig, wt, dom, w["n_walks"], w["eps"], w["seed"])
         u.sum().backward()
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
-        fwd.append(t1 - t)
-        fb.append(t2 - t1)
-    out["differentiable_6d"] = {"forward_ms": 1e3 * min(fwd), "forward_backward_ms": 1e3 * min(fb),
-                                "walk_steps_per_s": int(r["stats"][1]) / min(fwd)}
-    # point-cloud C-space, d = 7: 65536 points, tensor-core distance; 2048 of the 8192 queries
+
+    for _ in range(3):  # best of three: the first backward pass can include one-time host work
+        ms_f, r = _timed(lambda: dom.grad(X.detach(), w["n_walks"], w["eps"], w["sigma"], seed=w["seed"],
+                                          with_stats=True))
+        ms_fb, _ = _timed(fwd_bwd)
+        fwd.append(ms_f)
+        fb.append(ms_fb)
+    steps = int(r["stats"][1])
+    sub = w["X"][:256]
+    mix = dom.grad(sub, w["n_walks"], w["eps"], w["sigma"], seed=w["seed"])
+    f64 = dom.grad(sub, w["n_walks"], w["eps"], w["sigma"], seed=w["seed"], precision="fp64")
+    err = {k: float(torch.max(torch.abs(mix[k] - f64[k]))) for k in ("u", "grad", "du_dsigma", "du_dw")}
+    err["note"] = "max |mixed - FP64| on the same walks, 256 of the 4096 queries"
+    out["differentiable_6d"] = {"forward_ms": min(fwd), "forward_backward_ms": min(fb),
+                                "walk_steps_per_s": steps / (min(fwd) / 1e3),
+                                "queries_per_s": w["X"].shape[0] / (min(fwd) / 1e3),
+                                "error_vs_fp64_same_stream": err,
+                                "roofline": roofline_of(steps * alg_flops_per_step(6, 64), min(fwd), fp32, "alu",
+                                                        "CUDA-core walker (64 balls); FP32 FMA peak")}
+    # point-cloud C-space, d = 7: 65536 points, tensor-core distance, all 8192 queries x 4096 walks
     w = synth.c3()
     dom = W.Domain(w["domain"])
-    Xs = w["X"][:2048]
-    dom.solve(Xs[:128], 256, w["eps"], w["sigma"], seed=w["seed"])
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    r = dom.solve(Xs, w["n_walks"], w["eps"], w["sigma"], seed=w["seed"], with_stats=True)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t
+    M = w["domain"]["points"].shape[0]
+    dom.solve(w["X"][:128], 256, w["eps"], w["sigma"], seed=w["seed"])
+    ms, r = _timed(lambda: dom.solve(w["X"], w["n_walks"], w["eps"], w["sigma"], seed=w["seed"], with_stats=True))
     st = W.stats_dict(r["stats"])
-    out["pointcloud_7d"] = {"queries": 2048, "walks_per_query": w["n_walks"], "ms": 1e3 * dt,
-                            "walk_steps_per_s": st["walk_steps"] / dt,
-                            "point_distance_evals_per_s": st["walk_steps"] * w["domain"]["points"].shape[0] / dt,
-                            "bound_shrinks": st["shrinks"]}
+    rl = roofline_of(st["walk_steps"] * alg_flops_per_step(7, 0, M), ms, bf16, "tensor",
+                     "tensor-core sphere-set walker; measured sustained BF16 peak")
+    mma = st["walk_steps"] * M * 2 * contraction_k(7)
+    rl.update({"mma_achieved": mma / (ms / 1e3) / 1e12, "mma_frac": mma / (ms / 1e3) / 1e12 / bf16})
+    out["pointcloud_7d"] = {"queries": int(w["X"].shape[0]), "walks_per_query": w["n_walks"], "ms": ms,
+                            "walk_steps_per_s": st["walk_steps"] / (ms / 1e3),
+                            "queries_per_s": w["X"].shape[0] / (ms / 1e3),
+                            "point_distance_evals_per_s": st["walk_steps"] * M / (ms / 1e3),
+                            "bound_shrinks": st["shrinks"], "roofline": rl}
     # plain FP64 d=2 check workload
     w = synth.c1()
     dom = W.Domain(w["domain"])
     for prec in ["fp64", "mixed"]:
         dom.grad(w["X"], w["n_walks"], w["eps"], w["sigma"], precision=prec, seed=w["seed"])
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        r = dom.grad(w["X"], w["n_walks"], w["eps"], w["sigma"], precision=prec, seed=w["seed"], with_stats=True)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t
-        out["fp64_check_2d_" + prec] = {"ms": 1e3 * dt, "walk_steps_per_s": int(r["stats"][1]) / dt}
+        ms, r = _timed(lambda: dom.grad(w["X"], w["n_walks"], w["eps"], w["sigma"], precision=prec, seed=w["seed"],
+                                        with_stats=True))
+        steps = int(r["stats"][1])
+        fl = steps * alg_flops_per_step(2, 4)
+        rl = (roofline_of(fl, ms, FP64_NOMINAL_TFLOPS, "alu", "FP64 walker; nominal GB300 FP64 rate (not measured)")
+              if prec == "fp64" else roofline_of(fl, ms, fp32, "alu", "mixed CUDA-core walker; FP32 FMA peak"))
+        out["fp64_check_2d_" + prec] = {"ms": ms, "walk_steps_per_s": steps / (ms / 1e3),
+                                        "queries_per_s": w["X"].shape[0] / (ms / 1e3), "roofline": rl}
     return out
 
 

@@ -344,8 +344,10 @@ wos_status wos_set_autotune_cache(const char *cache_path);
  * for d = 12 with eight.
  * Precision: WOS_FP64 or WOS_FP32_PLAIN (the one-thread-per-walk walker); WOS_MIXED needs its
  * weight table, which is allocated, and is rejected.
- * The first call on a device looks up the device address of the array (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture. Each call clears
+ * Each call looks up the device address of the array (cudaGetSymbolAddress, which allocates
+ * nothing) with the caller's device current, so the address is never stale after a device reset.
+ * The first call on a device may load the library's device code (lazy module loading); make that
+ * first call before any stream capture. Each call clears
  * the array on its stream and then reuses it, and the array keeps the last call's contents:
  * calls whose work overlaps on the GPU (other streams, other host threads) race on it and
  * must be serialised by the caller.

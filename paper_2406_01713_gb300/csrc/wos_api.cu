@@ -1928,25 +1928,16 @@ namespace {
 // the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[WOS_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void *g_noalloc_addr[kMaxDevices] = {};
-
-// Device address of the array for the current device, looked up once per device with that
-// device current (host code cannot use the symbol itself as a device address).
+// Device address of the array for the current device. Host code cannot use the symbol itself
+// as a device address, so every call asks the runtime for it with the caller's device current:
+// the lookup allocates nothing, and no address is cached across calls (a cached one would be
+// stale after cudaDeviceReset or a new primary context).
 wos_status noalloc_scratch(void **out) {
-    int dev = 0;
-    WOS_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(WOS_ERR_UNSUPPORTED, "device %d out of range", dev);
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (g_noalloc_addr[dev] == nullptr) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || p == nullptr)
-            return fail(WOS_ERR_CUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
-        g_noalloc_addr[dev] = p;
-    }
-    *out = g_noalloc_addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr)
+        return fail(WOS_ERR_CUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+    *out = p;
     return WOS_OK;
 }
 

@@ -110,7 +110,8 @@ def test_c1_per_query(c1, c1_oracle, precision):
         assert st["walk_steps"] == int(ref["walk_steps"].sum())
     assert np.all(agree(u, se, ref["u"], ref["u_se"]))
     assert np.all(agree(g, gse, ref["grad"], ref["grad_se"]))
-    assert np.all(agree(np_(got["du_dw"])[:, 0], 0 * se, ref["du_dw"][:, 0], ref["u_se"], atol=1e-3))
+    # one term with w = 1: du/dw per walk equals the walk's value, so u's standard errors are its own
+    assert np.all(agree(np_(got["du_dw"])[:, 0], se, ref["du_dw"][:, 0], ref["u_se"]))
     # the exact solution (|a|^2 = sigma): u = exp(a.x), grad u = a u; O(eps) shell bias allowed
     a = w["domain"]["exp_a"][0]
     gx = np.exp(w["X"] @ a)
@@ -336,7 +337,7 @@ def test_batch_subsample_matches_oracle():
                            walk_offset=base, grad=True)
         base += p["X"].shape[0] * p["n_walks"]
         assert np.all(agree(np_(o["u"]), np_(o["u_se"]), ref["u"], ref["u_se"]))
-        assert np.all(agree(np_(o["grad"]), np_(o["grad_se"]), ref["grad"], ref["grad_se"], atol=1e-3))
+        assert np.all(agree(np_(o["grad"]), np_(o["grad_se"]), ref["grad"], ref["grad_se"], atol=1e-4))
 
 
 @pytest.fixture(scope="module")
@@ -388,8 +389,7 @@ def test_batch_full_size_sampled_oracle_parity(c4_full):
                            walk_offset=int(bases[i]) + q * p["n_walks"], grad=True)
         o = out[i]
         assert agree(np_(o["u"])[q], np_(o["u_se"])[q], ref["u"][0], ref["u_se"][0]), (i, q)
-        assert np.all(agree(np_(o["grad"])[q], np_(o["grad_se"])[q], ref["grad"][0], ref["grad_se"][0],
-                            atol=1e-3)), (i, q)
+        assert np.all(agree(np_(o["grad"])[q], np_(o["grad_se"])[q], ref["grad"][0], ref["grad_se"][0])), (i, q)
         picked += 1
         if picked == 40:
             break
