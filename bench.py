@@ -328,6 +328,12 @@ def main():
     dev_s, _, value = aggregate_over_ranks(sum(step_ms) / 1e3, total_steps * args.steps, world, device="cuda")
     ms_per_step = 1e3 * dev_s / args.steps
 
+    # run-to-run spread of the FP64 sums (atomics land in a different order each run)
+    u_a = batch.u_buf.clone()
+    batch.run()
+    torch.cuda.synchronize()
+    run_to_run = {"max_abs_du": float((batch.u_buf - u_a).abs().max()),
+                  "max_rel_du": float(((batch.u_buf - u_a).abs() / u_a.abs().clamp_min(1e-300)).max())}
     # accuracy: exact solution u = exp(a.x), grad u = a u on the exponential-data problems
     rmse_u, rmse_g, rmse_gn = exact_rmse(probs, batch.out)
     calib = se_calibration(probs, batch.out)
@@ -378,7 +384,7 @@ def main():
             "grad_evals_per_s": total_q * args.steps * world / dev_s,
             "rmse": {"u_rel": rmse_u, "grad_rel": rmse_g, "grad_rel_aggregate": rmse_gn,
                      "against": "exact solution exp(a.x) on the 128 exponential-data problems",
-                     "rmse_over_rms_se": calib,
+                     "rmse_over_rms_se": calib, "run_to_run": run_to_run,
                      "grad_estimator": "first sphere" + ("" if args.no_cv else " with control variate")},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
             "wall_s": wall}

@@ -34,6 +34,11 @@
  *   - A query point with no positive distance to the boundary (not in the open domain) gets
  *     NaN outputs and is counted in wos_stats.outside; the other queries still complete, and
  *     the call returns WOS_OK.
+ *   - In WOS_MIXED the per-query sums are FP64 and formed in a fixed order, so repeated calls
+ *     with the same inputs give the same outputs bit for bit. Every walk leaves a record of
+ *     rec = 4 + K (+ d for gradient walks) floats, rounded up to a multiple of four (16 to 96
+ *     bytes), in device scratch that the call allocates (Q * n_walks records), and one CTA per
+ *     query and segment of 4096 walks sums them.
  *   - Random directions: Philox4x32-10 (Salmon et al., SC'11) with key = seed and counter =
  *     (walk_lo, walk_hi, step, block). Walk w of query q has the global index
  *     walk_offset + q * n_walks + w, so results are a pure function of (seed, index, step).
@@ -79,8 +84,9 @@ typedef enum {
  *
  * Walks capped at max_steps (t_w = 0) take part with their first direction. This is a
  * variance reduction in the spirit of the paper's closing discussion (Sec. IX), not an
- * estimator the paper prints. Cost: 3d more FP64 sums per query and up to 3d more atomic
- * adds per walk. With N = 1 the plain estimate is returned. Value-only calls ignore the flag.
+ * estimator the paper prints. Cost: 3d more FP64 sums per query, and in mixed precision the
+ * first direction of every walk is kept in its record (d floats). With N = 1 the plain estimate
+ * is returned. Value-only calls ignore the flag.
  */
 #define WOS_FLAG_GRAD_CONTROL_VARIATE 2
 
@@ -289,14 +295,14 @@ typedef struct {
 
 /*
  * Builds a batch: uploads the problem table and the longest-first work queues, sizes the
- * persistent grids to a multiple of the SM count, and records one CUDA graph: [reset,
- * control-variate prepass (with WOS_FLAG_GRAD_CONTROL_VARIATE), the CUDA-core persistent walker
- * for the problems with small ball sets, in parallel one tensor-core sphere-set walker launch
- * per dimension for the problems with tensor-core sphere sets (large ball sets or a point set;
- * WOS_FLAG_CUDA_CORE_BALLS keeps ball sets off it), finalize]. Problems may differ in d,
- * obstacle count, walk budget, sigma and eps. Precision is WOS_MIXED. The problems' domains and
- * buffers must outlive the batch. Errors: INVALID_ARG, UNSUPPORTED (a domain with both balls
- * and points), OOM, CUDA.
+ * persistent grids to a multiple of the SM count, and records one CUDA graph: [reset, the
+ * CUDA-core persistent walker for the problems with small ball sets, in parallel one
+ * tensor-core sphere-set walker launch per dimension for the problems with tensor-core sphere
+ * sets (large ball sets or a point set; WOS_FLAG_CUDA_CORE_BALLS keeps ball sets off it), the
+ * per-query reduction of the walks' records, finalize]. Problems may differ in d, obstacle
+ * count, walk budget, sigma and eps. Precision is WOS_MIXED. The problems' domains and buffers
+ * must outlive the batch; the batch holds a record of 16 to 96 bytes per walk (see below).
+ * Errors: INVALID_ARG, UNSUPPORTED (a domain with both balls and points), OOM, CUDA.
  */
 wos_status wos_batch_create(const wos_problem *probs, int32_t n_problems, const wos_options *opt,
                             const wos_batch_config *cfg, wos_batch_t *out);

@@ -772,15 +772,21 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                     term = kind == kGoal ? expf(logw) : 0.f;
                 }
             }
-            const bool has_grad = GRAD && outcome == 1 && k > 0;
+            // (a value-only problem in a gradient launch has no gradient terms)
+            const bool has_grad = GRAD && P.grad_mode && outcome == 1 && k > 0;
             const bool cv_walk = GRAD && P.cv && k > 0 && outcome != 3;  // capped walks count too
             float v0[D];
 #pragma unroll
             for (int i = 0; i < D; ++i) v0[i] = 0.f;
-            if (has_grad && term != 0.f)
-                direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + j), 0u, v0);
+            // the first direction: for the gradient terms, and for every walk that took its first
+            // sphere when the control variate sums sum v0 and sum v0^2
+            const bool need_v0 = (has_grad && term != 0.f) || cv_walk;
+            if (GRAD && need_v0) direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + j), 0u, v0);
             const float gt = has_grad ? gfac0 * term : 0.f;
-            add_walk<D, GRAD>(P, q, outcome, k, term, dsig, gt, v0, e, cv_walk ? gfac0 : 0.f);
+            // control variate: G = alpha(R0)/C(R0), one number per query (every walk writes it)
+            if (cv_walk && gfac0 != 0.f)
+                P.acc[q * acc_fields(D, P.n_exp, P.cv, P.src) + cv_field(D, P.n_exp) + 3 * D] = (double)gfac0;
+            write_record<D>(P, j, outcome, k, term, dsig, gt, GRAD && need_v0, v0, e);
             if (P.w_term != nullptr) P.w_term[j] = outcome == 3 ? (double)CUDART_NAN : (double)term;
             if (P.w_jumps != nullptr) P.w_jumps[j] = k;
             if (P.w_dsigma != nullptr) P.w_dsigma[j] = (double)(term * dsig);
@@ -922,7 +928,13 @@ static cudaError_t configure_spheres() {
                                  (int)pc::smem_bytes(DD));                                                   \
     if (e == cudaSuccess)                                                                                    \
         e = cudaFuncSetAttribute(pc::sphere_kernel<DD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                 (int)pc::smem_bytes(DD));
+                                 (int)pc::smem_bytes(DD));                                                   \
+    if (e == cudaSuccess)                                                                                    \
+        e = cudaFuncSetAttribute(pc::sphere_kernel<DD, false>, cudaFuncAttributePreferredSharedMemoryCarveout, \
+                                 (int)cudaSharedmemCarveoutMaxShared);                                       \
+    if (e == cudaSuccess)                                                                                    \
+        e = cudaFuncSetAttribute(pc::sphere_kernel<DD, true>, cudaFuncAttributePreferredSharedMemoryCarveout,  \
+                                 (int)cudaSharedmemCarveoutMaxShared);
     WOS_CFG(2) WOS_CFG(3) WOS_CFG(4) WOS_CFG(5) WOS_CFG(6) WOS_CFG(7) WOS_CFG(8) WOS_CFG(9) WOS_CFG(10)
     WOS_CFG(11) WOS_CFG(12)
 #undef WOS_CFG

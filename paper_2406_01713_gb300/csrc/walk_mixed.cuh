@@ -9,9 +9,10 @@
 //     packed FP32x2 FMAs (two balls per instruction);
 //   * every lane runs walks back to back, refilling from the item's walk counter the moment
 //     its walk ends (walk lengths vary, so lanes never wait for the slowest walk of a batch);
-//   * each finished walk adds its contribution (u, u^2, du/dsigma, grad, grad^2, du/dw,
-//     counters) straight into the FP64 per-query sums in global memory, so no per-lane
-//     accumulator occupies registers between walks.
+//   * each finished walk writes a small FP32 record (value, d/dsigma, gradient factor, jumps,
+//     outcome, first direction, du/dw terms) that reduce_kernel sums per query in FP64 in a
+//     fixed order, so no per-lane accumulator occupies registers between walks and no atomic
+//     orders the sums.
 //
 // Distance to the balls (Sec. VI, |x - c| - r): a ball can only beat the current best
 // distance b if |x-c|^2 < (r+b)^2, i.e. if
@@ -355,52 +356,28 @@ __device__ __forceinline__ float terminal_value(const MixedProblem &P, const flo
     return kind == kGoal ? expf(logw) : 0.f;
 }
 
-// Adds one finished walk to the FP64 per-query sums: fields [u, u^2, du/dsigma, grad (D),
-// grad^2 (D), du/dw (K)] and counters [walks, walk-steps, capped, outside].
-template <int D, bool GRAD>
-__device__ __forceinline__ void add_walk(const MixedProblem &P, long long q, int outcome, int k,
-                                         float term, float dsig, float gt, const float (&v0)[D],
-                                         const float (&e)[kMaxExp], float gf) {
-    const int nf = acc_fields(D, P.n_exp, P.cv, P.src);
-    double *acc = P.acc + q * nf;
-    unsigned long long *cnt = P.counts + q * kCounters;
-    atomicAdd(cnt + 0, 1ull);
-    atomicAdd(cnt + 1, (unsigned long long)(k + 1));
-    if (outcome == 2) atomicAdd(cnt + 2, 1ull);
-    if (outcome == 3) {
-        atomicAdd(cnt + 3, 1ull);
-        return;
+// Writes the record of one finished walk (layout at rec_words): one 16-byte store of
+// [term, dsigma, gt, info], the first direction when the reduction needs it, and the du/dw terms
+// when the walk has a value.
+template <int D>
+__device__ __forceinline__ void write_record(const MixedProblem &P, long long j, int outcome, int k, float term,
+                                             float dsig, float gt, bool has_v0, const float (&v0)[D],
+                                             const float (&e)[kMaxExp]) {
+    if (P.rec == nullptr) return;
+    float *r = P.rec + j * P.rec_words;
+    const unsigned info = ((unsigned)k & kRecKMask) | ((unsigned)outcome << kRecOutcomeShift) | (has_v0 ? kRecHasV0 : 0u);
+    *reinterpret_cast<float4 *>(r) = make_float4(term, dsig, gt, __uint_as_float(info));
+    if (has_v0) {  // only gradient walks (grad_mode) have the v0 words
+#pragma unroll
+        for (int i = 0; i + 3 < D; i += 4) *reinterpret_cast<float4 *>(r + 4 + i) = make_float4(v0[i], v0[i + 1], v0[i + 2], v0[i + 3]);
+#pragma unroll
+        for (int i = D & ~3; i < D; ++i) r[4 + i] = v0[i];
     }
     if (term != 0.f) {
-        atomicAdd(acc + 0, (double)term);
-        atomicAdd(acc + 1, (double)term * (double)term);
-        atomicAdd(acc + 2, (double)term * (double)dsig);
-        if constexpr (GRAD) {
-            if (gt != 0.f) {
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    const double g = (double)gt * (double)v0[i];
-                    atomicAdd(acc + 3 + i, g);
-                    atomicAdd(acc + 3 + D + i, g * g);
-                }
-            }
-        }
+        float *re = r + 4 + (P.grad_mode ? D : 0);  // the layout of rec_words(d, K, grad_mode)
 #pragma unroll
         for (int kk = 0; kk < kMaxExp; ++kk)
-            if (kk < P.n_exp) atomicAdd(acc + 3 + 2 * D + kk, (double)e[kk]);
-    }
-    if constexpr (GRAD) {
-        // control variate: gf = G = alpha(R0)/C(R0) for every walk that took its first sphere
-        // (the same value for all walks of the query). sum v0 and sum v0^2 do not depend on the
-        // walk's outcome; cv_prepass_kernel forms them from the Philox stream.
-        if (gf != 0.f) {
-            double *cvp = acc + cv_field(D, P.n_exp);
-            if (term != 0.f) {
-#pragma unroll
-                for (int i = 0; i < D; ++i) atomicAdd(cvp + D + i, (double)term * (double)v0[i] * (double)v0[i]);
-            }
-            cvp[3 * D] = (double)gf;
-        }
+            if (kk < P.n_exp) re[kk] = e[kk];
     }
 }
 
@@ -561,18 +538,24 @@ __device__ __forceinline__ void step_walker(const MixedLaunch &L, const MixedPro
 #pragma unroll
     for (int k = 0; k < kMaxExp; ++k) e[k] = 0.f;
     if (outcome == 1) term = terminal_value<D>(P, geom, balls, W.x2, kind, idx, W.logw, e) + W.src;
-    const bool has_grad = GRAD && outcome == 1 && W.k > 0;
+    // (a value-only problem in a gradient launch has no gradient terms: its records carry none)
+    const bool has_grad = GRAD && P.grad_mode && outcome == 1 && W.k > 0;
     const bool cv_walk = GRAD && P.cv && W.k > 0 && outcome != 3;  // capped walks count too
     float v0[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) v0[i] = 0.f;
+    // the first direction, regenerated from its counter: for the gradient terms, and for every
+    // walk that took its first sphere when the control variate sums sum v0 and sum v0^2
+    const bool need_v0 = (has_grad && (term != 0.f || W.src0 != 0.f)) || cv_walk;
     if constexpr (GRAD) {
-        if (has_grad && (term != 0.f || W.src0 != 0.f))
-            direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + (long long)W.j), 0u, v0);
+        if (need_v0) direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + (long long)W.j), 0u, v0);
     }
     // u^(x_1) C(R0): the walk's value without its step-0 source part
     const float gt = has_grad ? W.gfac0 * (term - W.src0) : 0.f;
-    add_walk<D, GRAD>(P, W.q, outcome, W.k, term, W.dsig, gt, v0, e, cv_walk ? W.gfac0 : 0.f);
+    // control variate: G = alpha(R0)/C(R0) is one number per query (every walk writes the same)
+    if (cv_walk && W.gfac0 != 0.f)
+        P.acc[W.q * acc_fields(D, P.n_exp, P.cv, P.src) + cv_field(D, P.n_exp) + 3 * D] = (double)W.gfac0;
+    write_record<D>(P, (long long)W.j, outcome, W.k, term, W.dsig, gt, GRAD && need_v0, v0, e);
     if (P.w_term != nullptr) P.w_term[W.j] = outcome == 3 ? (double)CUDART_NAN : (double)term;
     if (P.w_jumps != nullptr) P.w_jumps[W.j] = W.k;
     if (P.w_dsigma != nullptr) P.w_dsigma[W.j] = P.has_source ? (double)CUDART_NAN : (double)(term * W.dsig);

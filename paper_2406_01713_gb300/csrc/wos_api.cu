@@ -338,114 +338,277 @@ __global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
     }
 }
 
-// Control variate, outcome-independent sums: the first direction of every walk of a query,
-// regenerated from its Philox counter with the walkers' own sampler and arguments (so the
-// values are the walkers' v0 bit for bit), summed per component and squared into the query's
-// [sum v0] and [sum v0^2] fields. A batch gives each query one warp, which stores its sums; a
-// single problem with more than 4096 walks per query splits them into warps of 4096 walks that
-// add their sums atomically (a few queries with many walks would otherwise leave the GPU idle).
-struct CvPrepassArgs {
-    const MixedProblem *problems;  // device array, or nullptr: problem 0 is `single`
-    const FinalizeRec *recs;       // device array (q_begin per problem), or nullptr
-    int n;
-    int64_t total_q;
-    MixedProblem single;
-    uint64_t seed;
-    // single problem: each query's walks in `segments` warps of seg_walks walks (set by the
-    // launcher), whose sums are added atomically; batches: one warp per query
-    int64_t segments, seg_walks;
+// =====================================================================================
+// per-query reduction of the mixed walkers' per-walk records (fixed order, FP64)
+// =====================================================================================
+// The estimates of a query are sample means over its walks (Sec. IV-A). The mixed-precision
+// walkers leave one FP32 record per walk (rec_words, wos_launch.h); one CTA sums the records of
+// a segment of at most kReduceSegment walks of one query in FP64 -- each thread its strided
+// share in walk order, then each warp's shuffle tree, then the warps in order -- and writes the
+// query's sums (one segment) or the segment's partial sums, which reduce_combine_kernel adds in
+// segment order. Every sum is formed in the same order on every run, so the outputs repeat bit
+// for bit. Sums, in the layout of the query's accumulator (acc_fields):
+//   [u, u^2, du/dsigma, grad (d), grad^2 (d), du/dw (K)] and, with the control variate,
+//   [sum v0 (d), sum t v0^2 (d), sum v0^2 (d)]; counters [walks, walk-steps, capped, outside].
+constexpr int kReduceSegment = 4096;
+constexpr int kReduceThreads = 128;
+constexpr int kReduceMaxSums = 3 + 2 * kMaxD + kMaxExp + 3 * kMaxD;
+
+__host__ __device__ inline int reduce_sums(int d, int K, int cv) { return 3 + 2 * d + K + (cv ? 3 * d : 0); }
+
+struct ReduceRec {
+    int d, K, grad, cv, nf;      // nf: accumulator fields per query (acc_fields)
+    int rw;                      // record words
+    int64_t Q, N;
+    int64_t nseg;                // segments per query
+    int64_t blk_begin;           // first reduce CTA of this problem
+    int64_t q_begin;             // first combine CTA (query) of this problem
+    const float *rec;            // Q N x rw
+    double *acc;                 // Q x nf
+    unsigned long long *counts;  // Q x kCounters
+    double *part;                // Q x nseg x (sums + kCounters) when nseg > 1
 };
 
-// Prepass sums of walks [w0, w1) of query q; `add`: several warps share the query (atomic
-// adds into the zeroed sums), else the warp stores them.
+struct ReduceArgs {
+    const ReduceRec *recs;  // device array, or nullptr: `single`
+    int n;
+    int64_t total_blocks;   // reduce: sum of Q nseg; combine: sum of Q
+    ReduceRec single;
+    const int *skip;        // nullable; nothing is done if *skip != 0
+};
+
+__device__ __forceinline__ const ReduceRec *reduce_find(const ReduceArgs &a, int64_t t, bool by_query) {
+    if (a.recs == nullptr) return &a.single;
+    int lo = 0, hi = a.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((by_query ? a.recs[mid].q_begin : a.recs[mid].blk_begin) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return a.recs + lo;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 template <int D>
-__device__ void cv_prepass_query(const MixedProblem &P, int64_t q, int64_t w0, int64_t w1, bool add,
-                                 uint64_t seed, int lane) {
-    double s1[D], s2[D];
+__device__ void reduce_segment(const ReduceRec &R, int64_t q, int64_t seg, double (*red)[kReduceMaxSums],
+                               unsigned long long (*redc)[kCounters]) {
+    const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+    double u = 0.0, u2 = 0.0, ds = 0.0, g[D], g2[D], dw[kMaxExp], sv[D], stv2[D], sv2[D];
 #pragma unroll
-    for (int i = 0; i < D; ++i) s1[i] = s2[i] = 0.0;
-    for (int64_t w = w0 + lane; w < w1; w += 32) {
-        float v[D];
-        direction_f32<D, true>(seed, (uint64_t)(P.walk_base + q * P.N + w), 0u, v);
+    for (int i = 0; i < D; ++i) g[i] = g2[i] = sv[i] = stv2[i] = sv2[i] = 0.0;
 #pragma unroll
-        for (int i = 0; i < D; ++i) {
-            s1[i] += (double)v[i];
-            s2[i] += (double)v[i] * (double)v[i];
-        }
-    }
+    for (int k = 0; k < kMaxExp; ++k) dw[k] = 0.0;
+    unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    const int64_t w0 = seg * kReduceSegment;
+    const int64_t w1 = w0 + kReduceSegment < R.N ? w0 + kReduceSegment : R.N;
+    const float *base = R.rec + (q * R.N) * R.rw;
+    const int eoff = 4 + (R.grad ? D : 0);
+    for (int64_t w = w0 + t; w < w1; w += kReduceThreads) {
+        const float *r = base + w * R.rw;
+        const float4 h = __ldg(reinterpret_cast<const float4 *>(r));
+        const unsigned info = __float_as_uint(h.w);
+        const int outcome = (int)((info >> kRecOutcomeShift) & 3u);
+        c0 += 1ull;
+        c1 += (unsigned long long)(info & kRecKMask) + 1ull;
+        c2 += outcome == 2 ? 1ull : 0ull;
+        c3 += outcome == 3 ? 1ull : 0ull;
+        if (outcome == 3) continue;
+        const double term = (double)h.x;
+        const bool has_v0 = (info & kRecHasV0) != 0u;
+        float v0[D];
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
+        for (int i = 0; i < D; ++i) v0[i] = 0.f;
+        if (has_v0) {
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            s1[i] += __shfl_xor_sync(0xffffffffu, s1[i], off);
-            s2[i] += __shfl_xor_sync(0xffffffffu, s2[i], off);
-        }
-    }
-    if (lane == 0) {
-        double *cvp = P.acc + q * acc_fields(D, P.n_exp, 1, P.src) + cv_field(D, P.n_exp);
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            if (add) {
-                atomicAdd(cvp + i, s1[i]);
-                atomicAdd(cvp + 2 * D + i, s2[i]);
-            } else {
-                cvp[i] = s1[i];
-                cvp[2 * D + i] = s2[i];
+            for (int i = 0; i + 3 < D; i += 4) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(r + 4 + i));
+                v0[i] = v.x;
+                v0[i + 1] = v.y;
+                v0[i + 2] = v.z;
+                v0[i + 3] = v.w;
             }
+#pragma unroll
+            for (int i = D & ~3; i < D; ++i) v0[i] = __ldg(r + 4 + i);
+        }
+        if (term != 0.0) {
+            u += term;
+            u2 += term * term;
+            ds += term * (double)h.y;
+            if (h.z != 0.f) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    const double gi = (double)h.z * (double)v0[i];
+                    g[i] += gi;
+                    g2[i] += gi * gi;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kMaxExp; ++k)
+                if (k < R.K) dw[k] += (double)__ldg(r + eoff + k);
+        }
+        if (R.cv && has_v0) {
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const double vi = (double)v0[i];
+                sv[i] += vi;
+                sv2[i] += vi * vi;
+                stv2[i] += term * vi * vi;
+            }
+        }
+    }
+    // the warps' shuffle trees, then the warps in order
+    int f = 0;
+    auto put = [&](double v) {
+        v = warp_sum(v);
+        if (lane == 0) red[wp][f] = v;
+        ++f;
+    };
+    put(u);
+    put(u2);
+    put(ds);
+#pragma unroll
+    for (int i = 0; i < D; ++i) put(g[i]);
+#pragma unroll
+    for (int i = 0; i < D; ++i) put(g2[i]);
+#pragma unroll
+    for (int k = 0; k < kMaxExp; ++k)
+        if (k < R.K) put(dw[k]);
+    if (R.cv) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) put(sv[i]);
+#pragma unroll
+        for (int i = 0; i < D; ++i) put(stv2[i]);
+#pragma unroll
+        for (int i = 0; i < D; ++i) put(sv2[i]);
+    }
+    c0 = warp_sum_u64(c0);
+    c1 = warp_sum_u64(c1);
+    c2 = warp_sum_u64(c2);
+    c3 = warp_sum_u64(c3);
+    if (lane == 0) {
+        redc[wp][0] = c0;
+        redc[wp][1] = c1;
+        redc[wp][2] = c2;
+        redc[wp][3] = c3;
+    }
+    __syncthreads();
+    const int nsum = f;
+    constexpr int kWarps = kReduceThreads / 32;
+    if (t < nsum + kCounters) {
+        if (t < nsum) {
+            double v = 0.0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) v += red[w][t];
+            if (R.nseg == 1) R.acc[q * R.nf + t] = v;
+            else R.part[(q * R.nseg + seg) * (nsum + kCounters) + t] = v;
+        } else {
+            unsigned long long v = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) v += redc[w][t - nsum];
+            if (R.nseg == 1) R.counts[q * kCounters + (t - nsum)] = v;
+            else
+                reinterpret_cast<unsigned long long *>(R.part)[(q * R.nseg + seg) * (nsum + kCounters) + t] = v;
         }
     }
 }
 
-__global__ void cv_prepass_kernel(const __grid_constant__ CvPrepassArgs a) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t S = a.recs != nullptr ? 1 : a.segments;
-    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.total_q * S; t += nwarps) {
-        const MixedProblem *P = &a.single;
-        int64_t q = t / S;
-        int64_t w0 = 0, w1 = P->N;
-        if (S > 1) {
-            w0 = (t % S) * a.seg_walks;
-            w1 = w0 + a.seg_walks < P->N ? w0 + a.seg_walks : P->N;
-        }
-        if (a.recs != nullptr) {
-            int lo = 0, hi = a.n - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (a.recs[mid].q_begin <= t) lo = mid;
-                else hi = mid - 1;
-            }
-            P = a.problems + lo;
-            q = t - a.recs[lo].q_begin;
-            w1 = P->N;
-        }
-        if (!P->cv) continue;
-        switch (P->d) {
+__global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const __grid_constant__ ReduceArgs a) {
+    __shared__ double red[kReduceThreads / 32][kReduceMaxSums];
+    __shared__ unsigned long long redc[kReduceThreads / 32][kCounters];
+    if (a.skip != nullptr && *a.skip != 0) return;
+    for (int64_t b = blockIdx.x; b < a.total_blocks; b += gridDim.x) {
+        const ReduceRec *R = reduce_find(a, b, false);
+        const int64_t local = b - R->blk_begin;
+        const int64_t q = local / R->nseg, seg = local % R->nseg;
+        switch (R->d) {
 #define WOS_CASE(DD) \
-    case DD: cv_prepass_query<DD>(*P, q, w0, w1, S > 1, a.seed, lane); break;
+    case DD: reduce_segment<DD>(*R, q, seg, red, redc); break;
             WOS_CASE(2) WOS_CASE(3) WOS_CASE(4) WOS_CASE(5) WOS_CASE(6) WOS_CASE(7)
             WOS_CASE(8) WOS_CASE(9) WOS_CASE(10) WOS_CASE(11) WOS_CASE(12)
 #undef WOS_CASE
             default: break;
         }
+        __syncthreads();  // red is reused by the next segment
     }
 }
 
-wos_status launch_cv_prepass(const CvPrepassArgs &a_in, cudaStream_t s) {
-    if (a_in.total_q <= 0) return WOS_OK;
-    CvPrepassArgs a = a_in;
-    // a single problem's queries in segments of 4096 walks (128 per lane)
-    a.segments = 1;
-    a.seg_walks = a.single.N;
-    if (a.recs == nullptr && a.single.N > 4096) {
-        a.seg_walks = 4096;
-        a.segments = (a.single.N + a.seg_walks - 1) / a.seg_walks;
+// Queries with several segments: the segments' partial sums added in segment order (one CTA per
+// query, one thread per sum).
+__global__ void reduce_combine_kernel(const __grid_constant__ ReduceArgs a) {
+    if (a.skip != nullptr && *a.skip != 0) return;
+    for (int64_t b = blockIdx.x; b < a.total_blocks; b += gridDim.x) {
+        const ReduceRec *R = reduce_find(a, b, true);
+        if (R->nseg <= 1) continue;
+        const int64_t q = b - R->q_begin;
+        const int nsum = reduce_sums(R->d, R->K, R->cv);
+        const int stride = nsum + kCounters;
+        const double *p = R->part + q * R->nseg * stride;
+        for (int f = threadIdx.x; f < stride; f += blockDim.x) {
+            if (f < nsum) {
+                double v = 0.0;
+                for (int64_t s = 0; s < R->nseg; ++s) v += p[s * stride + f];
+                R->acc[q * R->nf + f] = v;
+            } else {
+                const unsigned long long *pc = reinterpret_cast<const unsigned long long *>(p);
+                unsigned long long v = 0;
+                for (int64_t s = 0; s < R->nseg; ++s) v += pc[s * stride + f];
+                R->counts[q * kCounters + (f - nsum)] = v;
+            }
+        }
     }
-    const int threads = 256;
-    const int64_t tasks = a.total_q * (a.recs == nullptr ? a.segments : 1);
-    const int64_t blocks = std::min<int64_t>((tasks * 32 + threads - 1) / threads, 8192);
-    cv_prepass_kernel<<<(unsigned)blocks, threads, 0, s>>>(a);
+}
+
+// Bytes of the records and segment partials of one problem (16-byte multiples).
+size_t record_bytes(int d, int K, int grad, int64_t Q, int64_t N) {
+    return ((size_t)(Q * N) * rec_words(d, K, grad) * sizeof(float) + 255) & ~(size_t)255;
+}
+int64_t reduce_segments(int64_t N) { return (N + kReduceSegment - 1) / kReduceSegment; }
+size_t partial_bytes(int d, int K, int cv, int64_t Q, int64_t N) {
+    const int64_t nseg = reduce_segments(N);
+    if (nseg <= 1) return 0;
+    return ((size_t)(Q * nseg) * (reduce_sums(d, K, cv) + kCounters) * sizeof(double) + 255) & ~(size_t)255;
+}
+
+ReduceRec make_reduce_rec(int d, int K, int grad, int cv, int src, int64_t Q, int64_t N, const float *rec,
+                          double *acc, unsigned long long *counts, double *part) {
+    ReduceRec r{};
+    r.d = d;
+    r.K = K;
+    r.grad = grad;
+    r.cv = grad && cv;
+    r.nf = acc_fields(d, K, r.cv, grad && src);
+    r.rw = rec_words(d, K, grad);
+    r.Q = Q;
+    r.N = N;
+    r.nseg = reduce_segments(N);
+    r.rec = rec;
+    r.acc = acc;
+    r.counts = counts;
+    r.part = part;
+    return r;
+}
+
+wos_status launch_reduce(const ReduceArgs &a_in, int64_t total_queries, bool any_segmented, cudaStream_t s) {
+    if (a_in.total_blocks <= 0) return WOS_OK;
+    ReduceArgs a = a_in;
+    const unsigned grid = (unsigned)std::min<int64_t>(a.total_blocks, 1 << 20);
+    reduce_kernel<<<grid, kReduceThreads, 0, s>>>(a);
     WOS_CUDA(cudaGetLastError());
+    if (any_segmented) {
+        a.total_blocks = total_queries;
+        reduce_combine_kernel<<<(unsigned)std::min<int64_t>(total_queries, 1 << 20), 96, 0, s>>>(a);
+        WOS_CUDA(cudaGetLastError());
+    }
     return WOS_OK;
 }
 
@@ -494,6 +657,8 @@ struct Scratch {
     void *acc = nullptr;                    // Q x nf (double, or float for the plain walker)
     unsigned long long *counts = nullptr;   // Q x kCounters
     unsigned long long *cursor = nullptr;   // work-queue cursor (mixed walker)
+    float *rec = nullptr;                   // mixed walkers: Q N per-walk records
+    double *part = nullptr;                 // mixed walkers: segment partial sums (N > kReduceSegment)
 };
 
 size_t scratch_bytes(int precision, int64_t Q, int nf) {
@@ -514,6 +679,15 @@ Scratch carve_scratch(void *base, int precision, int64_t Q, int nf) {
     return s;
 }
 
+// Records and segment partials of a mixed-precision call, after the scratch of scratch_bytes.
+size_t mixed_extra_bytes(const wos_domain_s &D, int64_t Q, int64_t N, int grad_mode, int cv) {
+    return record_bytes(D.d, D.n_exp, grad_mode, Q, N) + partial_bytes(D.d, D.n_exp, grad_mode && cv, Q, N);
+}
+void carve_mixed(Scratch &sc, void *extra, const wos_domain_s &D, int64_t Q, int64_t N, int grad_mode) {
+    sc.rec = reinterpret_cast<float *>(extra);
+    sc.part = reinterpret_cast<double *>((char *)extra + record_bytes(D.d, D.n_exp, grad_mode, Q, N));
+}
+
 size_t g_mixed_smem_configured = 0;
 std::mutex g_mixed_mu;
 
@@ -529,8 +703,10 @@ wos_status ensure_mixed_smem(size_t bytes) {
 MixedProblem make_mixed_problem(wos_domain_t dom, const double *x, int64_t Q, int64_t N,
                                 double eps, double sigma, int grad_mode, int laplace, int cv,
                                 int64_t walk_base, const WeightTable &tab, double *acc,
-                                unsigned long long *counts, const PerWalk &pw) {
+                                unsigned long long *counts, const PerWalk &pw, float *rec) {
     MixedProblem P{};
+    P.rec = rec;
+    P.rec_words = rec_words(dom->d, dom->n_exp, grad_mode);
     P.d = dom->d;
     P.n_balls = dom->n_balls;
     P.n_exp = dom->n_exp;
@@ -577,7 +753,20 @@ size_t mixed_smem_bytes(const wos_domain_s &D) {
     return (size_t)((D.n_balls + 7) / 8) * (D.d + 2) * 32;
 }
 
-// Launches the walk kernel of the chosen precision for Q x N walks on zeroed scratch.
+// The per-query reduction of a single mixed-precision call (records in sc.rec).
+wos_status launch_reduce_single(wos_domain_t dom, const Opts &o, int64_t Q, int64_t N, int grad_mode,
+                                const Scratch &sc, const int *skip, cudaStream_t s) {
+    ReduceArgs ra{};
+    ra.single = make_reduce_rec(dom->d, dom->n_exp, grad_mode, o.cv, dom->has_source, Q, N, sc.rec,
+                                (double *)sc.acc, sc.counts, sc.part);
+    ra.n = 1;
+    ra.total_blocks = Q * ra.single.nseg;
+    ra.skip = skip;
+    return launch_reduce(ra, Q, ra.single.nseg > 1, s);
+}
+
+// Launches the walk kernel of the chosen precision for Q x N walks on zeroed scratch (mixed
+// precision: then the per-query reduction of its records).
 wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int64_t Q, int64_t N,
                           double eps, double sigma, int grad_mode, const Scratch &sc,
                           const PerWalk &pw, const int *skip, cudaStream_t s) {
@@ -639,6 +828,8 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
         return WOS_OK;
     }
     if (o.precision != WOS_MIXED) return fail(WOS_ERR_INVALID_ARG, "unknown precision %d", o.precision);
+    if (o.max_steps > (int64_t)kRecKMask)
+        return fail(WOS_ERR_INVALID_ARG, "max_steps must be below 2^28 in mixed precision");
     WeightTable tab;
     WOS_TRY(ensure_table(dom, sigma, &tab));
     if (dom->n_points > 0 || (dom->has_pcd && !o.cuda_core_balls)) {
@@ -649,19 +840,12 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
         if (dom->has_source)
             return fail(WOS_ERR_UNSUPPORTED, "a point set with an impulse source runs in FP64 or plain FP32");
         MixedProblem P = make_mixed_problem(dom, x, Q, N, eps, sigma, grad_mode, o.laplace, cv, o.walk_offset, tab,
-                                            (double *)sc.acc, sc.counts, pw);
-        if (cv) {
-            CvPrepassArgs pa{};
-            pa.total_q = Q;
-            pa.single = P;
-            pa.seed = o.seed;
-            WOS_TRY(launch_cv_prepass(pa, s));
-        }
+                                            (double *)sc.acc, sc.counts, pw, sc.rec);
         unsigned long long *shrinks = sc.cursor + 1;
         int *status = reinterpret_cast<int *>(sc.cursor + 2);
         WOS_CUDA(launch_pointcloud(dom->pcd, P, dom->pc_delta, sc.cursor, status, shrinks, o.seed, o.max_steps,
                                    grad_mode, s));
-        return WOS_OK;
+        return launch_reduce_single(dom, o, Q, N, grad_mode, sc, skip, s);
     }
     const int64_t total = Q * N;
     if (total > (int64_t)0x7fffffff) return fail(WOS_ERR_UNSUPPORTED, "Q * n_walks must be < 2^31");
@@ -702,16 +886,9 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
     L.max_steps = o.max_steps;
     L.skip = skip;
     L.single = make_mixed_problem(dom, x, Q, N, eps, sigma, grad_mode, o.laplace, cv, o.walk_offset,
-                                  tab, (double *)sc.acc, sc.counts, pw);
-    if (cv) {
-        CvPrepassArgs pa{};
-        pa.total_q = Q;
-        pa.single = L.single;
-        pa.seed = o.seed;
-        WOS_TRY(launch_cv_prepass(pa, s));
-    }
+                                  tab, (double *)sc.acc, sc.counts, pw, sc.rec);
     WOS_CUDA(launch_walk_mixed(L, grad_mode, grid, threads, smem, s));
-    return WOS_OK;
+    return launch_reduce_single(dom, o, Q, N, grad_mode, sc, skip, s);
 }
 
 wos_status check_common(wos_domain_t dom, const double *x, int64_t Q, int64_t N, double eps,
@@ -743,11 +920,13 @@ wos_status run_estimator(wos_domain_t dom, const wos_options *opt, const double 
     const int src = grad_mode && dom->has_source;
     const int nf = acc_fields(dom->d, dom->n_exp, cv, src);
     const size_t bytes = scratch_bytes(o.precision, Q, nf);
+    const size_t extra = o.precision == WOS_MIXED ? mixed_extra_bytes(*dom, Q, N, grad_mode, o.cv) : 0;
     void *base = nullptr;
-    WOS_CUDA(cudaMallocAsync(&base, bytes, s));
+    WOS_CUDA(cudaMallocAsync(&base, bytes + extra, s));
     Scratch sc = carve_scratch(base, o.precision, Q, nf);
+    if (o.precision == WOS_MIXED) carve_mixed(sc, (char *)base + bytes, *dom, Q, N, grad_mode);
     wos_status st = WOS_OK;
-    if (cudaMemsetAsync(base, 0, bytes, s) != cudaSuccess)
+    if (cudaMemsetAsync(base, 0, bytes, s) != cudaSuccess)  // records and partials are written in full
         st = fail(WOS_ERR_CUDA, "scratch memset failed");
     if (st == WOS_OK) st = launch_walkers(dom, o, x, Q, N, eps, sigma, grad_mode, sc, pw, nullptr, s);
     if (st == WOS_OK) {
@@ -1210,9 +1389,11 @@ wos_status wos_plan_step(wos_domain_t dom, const wos_options *opt, double *x, in
     }
     const int nf = acc_fields(dom->d, dom->n_exp, o.cv, dom->has_source);
     const size_t bytes = scratch_bytes(o.precision, 1, nf) + 256;
+    const size_t extra = o.precision == WOS_MIXED ? mixed_extra_bytes(*dom, 1, n_walks, 1, o.cv) : 0;
     void *base = nullptr;
-    WOS_CUDA(cudaMallocAsync(&base, bytes, s));
+    WOS_CUDA(cudaMallocAsync(&base, bytes + extra, s));
     Scratch sc = carve_scratch(base, o.precision, 1, nf);
+    if (o.precision == WOS_MIXED) carve_mixed(sc, (char *)base + bytes, *dom, 1, n_walks, 1);
     int *ints = reinterpret_cast<int *>((char *)base + bytes - 256);
     wos_status st = WOS_OK;
     if (cudaMemsetAsync(ints, 0, 2 * sizeof(int), s) != cudaSuccess) st = fail(WOS_ERR_CUDA, "memset");
@@ -1240,10 +1421,12 @@ wos_status wos_plan_path(wos_domain_t dom, const wos_options *opt, const double 
         WOS_TRY(ensure_mixed_smem(mixed_smem_bytes(*dom)));
     }
     const int nf = acc_fields(d, dom->n_exp, o.cv, dom->has_source);
-    const size_t bytes = scratch_bytes(o.precision, 1, nf) + 256 + sizeof(double) * d;
+    const size_t bytes = ((scratch_bytes(o.precision, 1, nf) + 256 + sizeof(double) * d) + 255) & ~(size_t)255;
+    const size_t extra = o.precision == WOS_MIXED ? mixed_extra_bytes(*dom, 1, n_walks, 1, o.cv) : 0;
     void *base = nullptr;
-    WOS_CUDA(cudaMalloc(&base, bytes));
+    WOS_CUDA(cudaMalloc(&base, bytes + extra));
     Scratch sc = carve_scratch(base, o.precision, 1, nf);
+    if (o.precision == WOS_MIXED) carve_mixed(sc, (char *)base + bytes, *dom, 1, n_walks, 1);
     int *ints = reinterpret_cast<int *>((char *)base + scratch_bytes(o.precision, 1, nf));
     double *x = reinterpret_cast<double *>((char *)ints + 256);
     wos_status st = WOS_OK;
@@ -1600,7 +1783,19 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     const size_t off_recs = off_items + align256(sizeof(MixedItem) * std::max<size_t>(1, sorted.size()));
     const size_t off_sph = off_recs + align256(sizeof(FinalizeRec) * n);
     const size_t off_sph_items = off_sph + align256(sizeof(SphereProblem) * std::max(1, n_sph));
-    const size_t off_zero = off_sph_items + align256(sizeof(SphereItem) * std::max<size_t>(1, sph_all.size()));
+    // per-walk records and segment partials of every problem, and the reduction's problem table
+    const size_t off_red = off_sph_items + align256(sizeof(SphereItem) * std::max<size_t>(1, sph_all.size()));
+    size_t off_rec = off_red + align256(sizeof(ReduceRec) * std::max(1, n));
+    std::vector<size_t> rec_off(n), part_off(n);
+    for (int i = 0; i < n; ++i) {
+        const wos_problem &p = b->probs[i];
+        const int g = p.grad != nullptr;
+        rec_off[i] = off_rec;
+        off_rec += record_bytes(p.domain->d, p.domain->n_exp, g, p.n_queries, p.n_walks);
+        part_off[i] = off_rec;
+        off_rec += partial_bytes(p.domain->d, p.domain->n_exp, g && b->o.cv, p.n_queries, p.n_walks);
+    }
+    const size_t off_zero = off_rec;
     // zeroed: accumulators | mixed cursor (8) + sphere status (8) + shrinks (8) + one cursor per
     // dimension | stats
     const size_t ctl_bytes = align256(8 * (3 + kPointCloudMaxD + 1));
@@ -1618,6 +1813,9 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     b->zero_bytes = zero_bytes;
     walk_base = b->o.walk_offset;
     q_begin = 0;
+    std::vector<ReduceRec> rr(n);
+    int64_t red_blocks = 0;
+    bool any_seg = false;
     for (int i = 0; i < n; ++i) {
         const wos_problem &p = b->probs[i];
         WeightTable tab;
@@ -1626,7 +1824,14 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         unsigned long long *cnt = (unsigned long long *)(zero + cnt_off[i]);
         mp[i] = make_mixed_problem(p.domain, p.x, p.n_queries, p.n_walks, p.eps, p.sigma,
                                    p.grad != nullptr, b->o.laplace, b->o.cv, walk_base, tab, acc, cnt,
-                                   PerWalk{});
+                                   PerWalk{}, reinterpret_cast<float *>(base + rec_off[i]));
+        rr[i] = make_reduce_rec(p.domain->d, p.domain->n_exp, p.grad != nullptr, b->o.cv, p.domain->has_source,
+                                p.n_queries, p.n_walks, reinterpret_cast<float *>(base + rec_off[i]), acc, cnt,
+                                reinterpret_cast<double *>(base + part_off[i]));
+        rr[i].blk_begin = red_blocks;
+        rr[i].q_begin = q_begin;
+        red_blocks += p.n_queries * rr[i].nseg;
+        any_seg |= rr[i].nseg > 1;
         FinalizeRec &r = fr[i];
         r.d = p.domain->d;
         r.K = p.domain->n_exp;
@@ -1654,6 +1859,12 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         WOS_CUDA(cudaMemcpy(base + off_items, sorted.data(), sizeof(MixedItem) * sorted.size(),
                             cudaMemcpyHostToDevice));
     WOS_CUDA(cudaMemcpy(base + off_recs, fr.data(), sizeof(FinalizeRec) * n, cudaMemcpyHostToDevice));
+    if (n > 0) WOS_CUDA(cudaMemcpy(base + off_red, rr.data(), sizeof(ReduceRec) * n, cudaMemcpyHostToDevice));
+    ReduceArgs ra{};
+    ra.recs = (const ReduceRec *)(base + off_red);
+    ra.n = n;
+    ra.total_blocks = red_blocks;
+    ra.skip = nullptr;
     if (n_sph > 0) {
         std::vector<SphereProblem> sp(n_sph);
         for (int k = 0; k < n_sph; ++k) {
@@ -1721,15 +1932,6 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         return fail(WOS_ERR_CUDA, "batch capture failed to start");
     }
     if (cudaMemsetAsync(zero, 0, zero_bytes, cap) != cudaSuccess) st = fail(WOS_ERR_CUDA, "memset capture");
-    if (st == WOS_OK && b->o.cv && b->grad_any) {
-        CvPrepassArgs pa{};
-        pa.problems = (const MixedProblem *)base;
-        pa.recs = fa.recs;
-        pa.n = n;
-        pa.total_q = b->total_q;
-        pa.seed = b->o.seed;
-        st = launch_cv_prepass(pa, cap);
-    }
     if (st == WOS_OK && !sph_dims.empty() && cudaEventRecord(ev.back(), cap) != cudaSuccess)
         st = fail(WOS_ERR_CUDA, "fork event capture failed");
     for (size_t k = 0; st == WOS_OK && k < sph_dims.size(); ++k) {
@@ -1755,6 +1957,7 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         st = fail(WOS_ERR_CUDA, "walk kernel capture failed");
     for (size_t k = 0; st == WOS_OK && k < sph_dims.size(); ++k)
         if (cudaStreamWaitEvent(cap, ev[k], 0) != cudaSuccess) st = fail(WOS_ERR_CUDA, "join capture failed");
+    if (st == WOS_OK) st = launch_reduce(ra, b->total_q, any_seg, cap);
     if (st == WOS_OK) st = launch_finalize(fa, cap);
     cudaError_t e = cudaStreamEndCapture(cap, &b->graph);
     cudaStreamDestroy(cap);
@@ -1794,6 +1997,7 @@ wos_status wos_batch_create(const wos_problem *probs, int32_t n_problems, const 
     const Opts o = read_opts(opt);
     if (opt != nullptr && o.precision != WOS_MIXED)
         return fail(WOS_ERR_UNSUPPORTED, "batched launches run the mixed-precision walker");
+    if (o.max_steps > (int64_t)kRecKMask) return fail(WOS_ERR_INVALID_ARG, "max_steps must be below 2^28");
     for (int i = 0; i < n_problems; ++i) {
         const wos_problem &p = probs[i];
         WOS_TRY(check_common(p.domain, p.x, p.n_queries, p.n_walks, p.eps, p.sigma));
@@ -2009,7 +2213,7 @@ extern "C" wos_status wos_debug_pointcloud_radius(wos_domain_t dom, const double
     if (st == WOS_OK) {
         // one distance evaluation per query: a walk capped at zero jumps
         MixedProblem P = make_mixed_problem(dom, x, Q, 1, 1e-30, 0.0, 0, 0, 0, 0, tab, (double *)sc.acc, sc.counts,
-                                            PerWalk{});
+                                            PerWalk{}, nullptr);
         const cudaError_t e = launch_pointcloud(dom->pcd, P, dom->pc_delta, sc.cursor,
                                                 reinterpret_cast<int *>(sc.cursor + 2), sc.cursor + 1, 0, 0, 0, s,
                                                 radius);

@@ -58,8 +58,11 @@ struct MixedProblem {
     const float *geom;            // box lo[d], box hi[d], goal c[d], outer c[d], exp w[K], exp a[K*d]
     const double *x;              // Q x d queries
     WeightTable table;
-    double *acc;                  // Q x nf FP64 sums
+    double *acc;                  // Q x nf FP64 sums (the walkers store only the per-query G and
+                                  // source fields; reduce_kernel writes the sums)
     unsigned long long *counts;   // Q x kCounters
+    float *rec;                   // Q N x rec_words per-walk records (nullable: none written)
+    int rec_words;
     double *w_term;               // per-walk outputs (nullable)
     int64_t *w_jumps;
     double *w_grad;
@@ -84,6 +87,19 @@ struct MixedLaunch {
     const int *skip;               // nullable; the kernel does nothing if *skip != 0
     MixedProblem single;
 };
+
+// Per-walk record of the mixed-precision walkers, the input of the per-query reduction
+// (reduce_kernel): rec_words floats at walk index j = q N + w,
+//   [term, dsigma, gt, info, v0 (d floats, gradient walks), e (K floats)]
+// term: the walk's value estimate; dsigma: its summed d log C / d sigma; gt: alpha(R0) u^(x1),
+// the factor of v0 in its gradient estimate (0 unless the walk reached the boundary after its
+// first sphere); info: k (jumps) | outcome << 28 (0 jumped, 1 boundary, 2 capped, 3 outside) |
+// has_v0 << 31; v0: the first direction (written when has_v0); e_k = exp(a_k . xbar) W (written
+// when term != 0). A record is 16-byte aligned.
+__host__ __device__ constexpr int rec_words(int d, int K, int grad) { return (4 + (grad ? d : 0) + K + 3) & ~3; }
+constexpr unsigned kRecKMask = 0x0fffffffu;  // jumps per walk stay below 2^28
+constexpr int kRecOutcomeShift = 28;
+constexpr unsigned kRecHasV0 = 0x80000000u;
 
 // Floats per packed ball record for dimension d.
 __host__ __device__ constexpr int ball_record_floats(int d) { return d + 2; }

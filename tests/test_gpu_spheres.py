@@ -146,3 +146,52 @@ def test_batch_mixes_tensor_and_cuda_core_problems():
         assert np.all(within(np_(o["u"]), np_(o["u_se"]), ref["u"], ref["u_se"]))
         assert np.all(within(np_(o["grad"]), np_(o["grad_se"]), ref["grad"], ref["grad_se"], atol=1e-4))
     B_.close()
+
+
+@pytest.mark.parametrize("B", [40, 2048])
+def test_per_query_sums_equal_per_walk_means(B):
+    """The per-query reduction (per-walk records summed per query in FP64, in a fixed order)
+    gives the mean of the per-walk outputs exactly up to FP64 summation order, on the CUDA-core
+    screen (40 balls) and the tensor-core sphere walker (2048 balls), alone and in a batch, with
+    few walks per query over many queries; the integer counters are exact, and repeated runs
+    agree bit for bit."""
+    d, N, Q, eps, sigma, seed = 3, 5, 300, 1e-3, 9.0, 21
+    dom, X, _ = ball_problem(d, B, sigma, 70 + B, Q)
+    D = W.Domain(dom)
+    assert D.info()["tensor_sphere_set"] == (B >= 192)
+    per = D.walks(X, N, eps, sigma, grad_mode=True, seed=seed, walk_offset=10)
+    got = D.grad(X, N, eps, sigma, seed=seed, walk_offset=10, with_stats=True)
+    st = W.stats_dict(got["stats"])
+    assert st["walks"] == Q * N and st["outside"] == 0
+    assert st["walk_steps"] == int(np_(per["jumps"]).sum()) + Q * N
+    assert np.allclose(np_(got["u"]), np_(per["term"]).mean(1), rtol=1e-12, atol=1e-15)
+    # the per-walk gradient and d/dsigma outputs are FP32 products (gt v0, term dsigma) where the
+    # sums take them in FP64: agreement to FP32 rounding of each walk's term
+    pg, pd = np_(per["grad"]), np_(per["dsigma"])
+    assert np.all(np.abs(np_(got["grad"]) - pg.mean(1)) <= 2e-7 * np.abs(pg).mean(1) + 1e-12)
+    assert np.all(np.abs(np_(got["du_dsigma"]) - pd.mean(1)) <= 2e-7 * np.abs(pd).mean(1) + 1e-12)
+    again = D.grad(X, N, eps, sigma, seed=seed, walk_offset=10, control_variate=True)
+    again2 = D.grad(X, N, eps, sigma, seed=seed, walk_offset=10, control_variate=True)
+    for k in ("u", "u_se", "grad", "grad_se", "du_dsigma"):
+        assert torch.equal(again[k], again2[k]), k
+    # a batch of both kinds, same walks (walk indices follow the problems in order)
+    dom2, X2, _ = ball_problem(d, 2048 if B < 192 else 40, sigma, 90 + B, 200)
+    D2 = W.Domain(dom2)
+    b = W.Batch([{"domain": D, "x": X, "n_walks": N, "eps": eps, "sigma": sigma, "grad": True},
+                 {"domain": D2, "x": X2, "n_walks": 3, "eps": eps, "sigma": sigma, "grad": True}], seed=seed)
+    out = b.run()
+    torch.cuda.synchronize()
+    per2 = D2.walks(X2, 3, eps, sigma, grad_mode=True, seed=seed, walk_offset=Q * N)
+    per1 = D.walks(X, N, eps, sigma, grad_mode=True, seed=seed, walk_offset=0)
+    for o, p in ((out[0], per1), (out[1], per2)):
+        assert np.allclose(np_(o["u"]), np_(p["term"]).mean(1), rtol=1e-12, atol=1e-15)
+        pg = np_(p["grad"])
+        assert np.all(np.abs(np_(o["grad"]) - pg.mean(1)) <= 2e-7 * np.abs(pg).mean(1) + 1e-12)
+        assert np.array_equal(np_(o["walk_steps"]), np_(p["jumps"]).sum(1) + p["jumps"].shape[1])
+    first = [{k: o[k].clone() for k in ("u", "u_se", "grad", "grad_se")} for o in out]
+    b.run()
+    torch.cuda.synchronize()
+    for o, f in zip(b.out, first):
+        for k in f:
+            assert torch.equal(o[k], f[k]), k
+    b.close()
