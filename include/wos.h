@@ -98,6 +98,16 @@ typedef enum {
  */
 #define WOS_FLAG_CUDA_CORE_BALLS 4
 
+/*
+ * Antithetic first directions (variance reduction of the paper's closing discussion, Sec. IX;
+ * not an estimator the paper prints): the walks pair up by global walk index (2m, 2m + 1), and
+ * walk 2m + 1 starts along the negated first direction of walk 2m (its own directions after).
+ * Every direction is still uniform, so every estimate stays unbiased; standard errors come from
+ * the spread of the N/2 pair means. Requires n_walks and walk_offset even (batches: every
+ * problem's n_walks even); not combined with WOS_FLAG_GRAD_CONTROL_VARIATE (INVALID_ARG).
+ */
+#define WOS_FLAG_ANTITHETIC 8
+
 #define WOS_MAX_D 12    /* dimensions 2..12 are supported */
 #define WOS_MAX_EXP 8   /* at most 8 exponential boundary-data terms */
 
@@ -160,13 +170,25 @@ typedef struct {
  * (ball sets) and rejects extruded point sets (UNSUPPORTED).
  */
 
-/* Per-call options. A NULL options pointer means {WOS_MIXED, 0, seed 0, offset 0, 10000}. */
+/*
+ * Per-call options. A NULL options pointer means {WOS_MIXED, 0, seed 0, offset 0, 10000, 0}.
+ *
+ * Russian roulette on the weight (roulette_w > 0; the closing discussion's roulette on C,
+ * Sec. IX; no rule is printed): before jump k >= 1 of a walk whose weight W = prod C(R_i) is
+ * below roulette_w, the walk survives with probability W / roulette_w and then carries the
+ * weight roulette_w, or ends with its impulse-source contributions so far and no boundary value
+ * (counted in wos_stats.killed). E[kept weight] = W keeps every estimate unbiased, and du/dsigma
+ * stays pathwise unbiased. The uniform is the top 24 bits of Philox block 15 of (walk, k) times
+ * 2^-24. Walks get shorter where the screening makes weights small (large sigma).
+ */
 typedef struct {
     int32_t precision;   /* wos_precision */
     int32_t flags;       /* WOS_FLAG_* */
     uint64_t seed;       /* Philox key */
     int64_t walk_offset; /* first global walk index of this call */
-    int64_t max_steps;   /* jumps per walk before it is capped (contributes 0); <= 0: 10000 */
+    int64_t max_steps;   /* jumps per walk before it is capped (contributes 0); <= 0: 10000;
+                            below 2^28 in WOS_MIXED */
+    double roulette_w;   /* > 0: Russian roulette below this weight; 0: off */
 } wos_options;
 
 /* Counters of one call, written to DEVICE memory when the stream completes (int64, exact). */
@@ -175,8 +197,8 @@ typedef struct {
     int64_t walk_steps;      /* distance evaluations (a walk with k jumps counts k + 1) */
     int64_t capped;          /* walks that hit max_steps */
     int64_t outside;         /* walks whose query was not in the open domain */
-    int64_t shrinks;         /* point-cloud steps whose radius was set by the error bound */
-    int64_t refine_overflow; /* point-cloud steps whose candidate list overflowed (bound used) */
+    int64_t shrinks;         /* tensor-core walker steps whose radius was set by a chunk bound */
+    int64_t killed;          /* walks ended by the Russian roulette (wos_options.roulette_w) */
 } wos_stats;
 
 /* ---- domain ------------------------------------------------------------------------- */

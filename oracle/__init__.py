@@ -137,7 +137,7 @@ def lib():
             L.or_solve.argtypes = [ctypes.POINTER(_Domain), _PD, ctypes.c_int64, ctypes.c_int64,
                                    ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                    ctypes.POINTER(_Options), ctypes.c_int, _PD, _PD, _PD, _PD, _PD,
-                                   _PD, _PI64, _PI64, _PI64, _PD, _PI64, _PD, _PD]
+                                   _PD, _PI64, _PI64, _PI64, _PI64, _PD, _PI64, _PD, _PD]
             L.or_solve.restype = ctypes.c_int
             L.or_plan_path.argtypes = [ctypes.POINTER(_Domain), _PD, ctypes.c_int64, ctypes.c_int64,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -293,15 +293,15 @@ def distance(dom, x):
 
 
 def walk(dom, x0, walk_index, eps, sigma, seed, max_steps=10000, grad=False, laplace_factor=False,
-         antithetic=False):
+         antithetic=False, roulette=0.0):
     D = dom if isinstance(dom, Domain) else Domain(dom)
     x0 = np.ascontiguousarray(np.asarray(x0, float))
     o = _WalkOut()
-    opt = _opts(seed, max_steps, grad, laplace_factor, antithetic=antithetic)
+    opt = _opts(seed, max_steps, grad, laplace_factor, roulette=roulette, antithetic=antithetic)
     lib().or_walk(ctypes.byref(D.s), _ptr(x0), int(walk_index), float(eps), float(sigma),
                   ctypes.byref(opt), ctypes.byref(o))
     return {
-        "term": o.term, "jumps": o.jumps, "capped": o.capped, "outside": o.outside,
+        "term": o.term, "jumps": o.jumps, "capped": o.capped, "outside": o.outside, "killed": o.killed,
         "comp_kind": o.comp_kind, "comp_index": o.comp_index,
         "grad": np.array(o.grad[:D.d]), "dsigma": o.dsigma, "dw": np.array(o.dw[:D.n_exp]),
         "gv0": np.array(o.gv0[:D.d]), "gsrc": np.array(o.gsrc[:D.d]),
@@ -313,7 +313,7 @@ def solve(dom, X, n_walks, eps, sigma, seed, walk_offset=0, max_steps=10000, gra
           plant_free_space_source_grad=False, roulette=0.0, plant_roulette_no_reweight=False,
           antithetic=False):
     """Per-query estimates. Returns a dict of numpy arrays (u, u_se, grad, grad_se,
-    du_dsigma, du_dw, walk_steps, capped, outside; with per_walk also walk_term,
+    du_dsigma, du_dw, walk_steps, capped, outside, killed; with per_walk also walk_term,
     walk_jumps, walk_grad, walk_dsigma). control_variate (with grad): grad and grad_se are
     the control-variate estimate G/(N-1) sum_w (t_w - tbar) v_w and its standard error.
     roulette > 0: Russian roulette on walk weights below it. antithetic: walk pairs (2m, 2m+1)
@@ -328,7 +328,7 @@ def solve(dom, X, n_walks, eps, sigma, seed, walk_offset=0, max_steps=10000, gra
         "u": np.zeros(Q), "u_se": np.zeros(Q), "grad": np.zeros((Q, d)), "grad_se": np.zeros((Q, d)),
         "du_dsigma": np.zeros(Q), "du_dw": np.zeros((Q, max(K, 1))),
         "walk_steps": np.zeros(Q, np.int64), "capped": np.zeros(Q, np.int64),
-        "outside": np.zeros(Q, np.int64),
+        "outside": np.zeros(Q, np.int64), "killed": np.zeros(Q, np.int64),
     }
     pw = {}
     if per_walk:
@@ -341,7 +341,7 @@ def solve(dom, X, n_walks, eps, sigma, seed, walk_offset=0, max_steps=10000, gra
         int(threads), _ptr(out["u"]), _ptr(out["u_se"]), _ptr(out["grad"]), _ptr(out["grad_se"]),
         _ptr(out["du_dsigma"]), _ptr(out["du_dw"]) if K else None,
         _ptr(out["walk_steps"], ctypes.c_int64), _ptr(out["capped"], ctypes.c_int64),
-        _ptr(out["outside"], ctypes.c_int64),
+        _ptr(out["outside"], ctypes.c_int64), _ptr(out["killed"], ctypes.c_int64),
         _ptr(pw.get("walk_term")), _ptr(pw.get("walk_jumps"), ctypes.c_int64),
         _ptr(pw.get("walk_grad")), _ptr(pw.get("walk_dsigma")))
     if rc != 0:

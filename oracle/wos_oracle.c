@@ -519,7 +519,7 @@ typedef struct {
     int64_t nchunks;   /* per query */
     int nfields;       /* doubles per chunk partial */
     double *partial;   /* Q x nchunks x nfields */
-    int64_t *ipartial; /* Q x nchunks x 3: steps, capped, outside */
+    int64_t *ipartial; /* Q x nchunks x 4: steps, capped, outside, killed */
     double *walk_term;
     int64_t *walk_jumps;
     double *walk_grad;
@@ -538,9 +538,9 @@ static void run_unit(solve_job *J, int64_t unit)
     int64_t q = unit / J->nchunks, c = unit % J->nchunks;
     int64_t w0 = c * OR_CHUNK, w1 = w0 + OR_CHUNK < J->N ? w0 + OR_CHUNK : J->N;
     double *P = J->partial + unit * J->nfields;
-    int64_t *I = J->ipartial + unit * 3;
+    int64_t *I = J->ipartial + unit * 4;
     memset(P, 0, sizeof(double) * J->nfields);
-    I[0] = I[1] = I[2] = 0;
+    I[0] = I[1] = I[2] = I[3] = 0;
     or_walk_out o;
     double pt = 0.0, pg[OR_MAXD]; /* antithetic: the even walk of the current pair */
     for (int64_t w = w0; w < w1; ++w) {
@@ -584,6 +584,7 @@ static void run_unit(solve_job *J, int64_t unit)
         I[0] += o.jumps + 1;
         I[1] += o.capped;
         I[2] += o.outside;
+        I[3] += o.killed;
     }
 }
 
@@ -611,14 +612,15 @@ static double se_of(double s, double s2, int64_t n)
 /*
  * Estimates at Q query points (X: Q x d), N walks each. Walk w of query q uses the global
  * walk index walk_offset + q N + w. Every output pointer may be NULL.
- *   u, u_se, du_dsigma, walk_steps, capped, outside: Q;  grad, grad_se: Q x d;  du_dw: Q x n_exp;
+ *   u, u_se, du_dsigma, walk_steps, capped, outside, killed: Q;  grad, grad_se: Q x d;
+ *   du_dw: Q x n_exp;
  *   walk_term, walk_jumps, walk_dsigma: Q x N;  walk_grad: Q x N x d.
  * Returns 0, or -1 on bad arguments / allocation failure.
  */
 int or_solve(const or_domain *D, const double *X, int64_t Q, int64_t N, int64_t walk_offset,
              double eps, double sigma, const or_options *opt, int nthreads, double *u,
              double *u_se, double *grad, double *grad_se, double *du_dsigma, double *du_dw,
-             int64_t *walk_steps, int64_t *capped, int64_t *outside, double *walk_term,
+             int64_t *walk_steps, int64_t *capped, int64_t *outside, int64_t *killed, double *walk_term,
              int64_t *walk_jumps, double *walk_grad, double *walk_dsigma)
 {
     if (!D || !X || !opt || D->d < 1 || D->d > OR_MAXD || D->n_exp < 0 || D->n_exp > OR_MAXEXP ||
@@ -646,7 +648,7 @@ int or_solve(const or_domain *D, const double *X, int64_t Q, int64_t N, int64_t 
     int64_t units = Q * J.nchunks;
     const int cv = opt->grad && opt->control_variate && N >= 2;
     J.partial = (double *)malloc(sizeof(double) * (size_t)(units * J.nfields + 1));
-    J.ipartial = (int64_t *)malloc(sizeof(int64_t) * (size_t)(units * 3 + 1));
+    J.ipartial = (int64_t *)malloc(sizeof(int64_t) * (size_t)(units * 4 + 1));
     if (cv) {
         J.cv_t = (double *)malloc(sizeof(double) * (size_t)(Q * N + 1));
         J.cv_gv0 = (double *)malloc(sizeof(double) * (size_t)(Q * N * d + 1));
@@ -673,13 +675,13 @@ int or_solve(const or_domain *D, const double *X, int64_t Q, int64_t N, int64_t 
 
     for (int64_t q = 0; q < Q; ++q) {
         double S[3 + 2 * OR_MAXD + OR_MAXEXP + 1 + OR_MAXD];
-        int64_t I[3] = {0, 0, 0};
+        int64_t I[4] = {0, 0, 0, 0};
         memset(S, 0, sizeof(S));
         for (int64_t c = 0; c < J.nchunks; ++c) {
             const double *P = J.partial + (q * J.nchunks + c) * J.nfields;
-            const int64_t *IP = J.ipartial + (q * J.nchunks + c) * 3;
+            const int64_t *IP = J.ipartial + (q * J.nchunks + c) * 4;
             for (int f = 0; f < J.nfields; ++f) S[f] += P[f];
-            for (int f = 0; f < 3; ++f) I[f] += IP[f];
+            for (int f = 0; f < 4; ++f) I[f] += IP[f];
         }
         double inv = 1.0 / (double)N;
         if (u) u[q] = S[0] * inv;
@@ -723,6 +725,7 @@ int or_solve(const or_domain *D, const double *X, int64_t Q, int64_t N, int64_t 
         if (walk_steps) walk_steps[q] = I[0];
         if (capped) capped[q] = I[1];
         if (outside) outside[q] = I[2];
+        if (killed) killed[q] = I[3];
     }
     free(J.partial);
     free(J.ipartial);
@@ -769,7 +772,7 @@ int64_t or_plan_path(const or_domain *D, const double *x0, int64_t n_steps, int6
         double R = or_distance(D, x, &kind, &index, xbar);
         int64_t out = 0;
         if (or_solve(D, x, 1, N, i * N, eps, sigma, &opt, nthreads, NULL, NULL, g, NULL, NULL, NULL,
-                     NULL, NULL, &out, NULL, NULL, NULL, NULL) != 0 ||
+                     NULL, NULL, &out, NULL, NULL, NULL, NULL, NULL) != 0 ||
             out > 0 || !(R > 0.0)) {
             flags[i] = 4;
             break;

@@ -11,6 +11,7 @@ WOS_FP64, WOS_FP32_PLAIN, WOS_MIXED = 0, 1, 2
 WOS_FLAG_LAPLACE_FACTOR = 1
 WOS_FLAG_GRAD_CONTROL_VARIATE = 2
 WOS_FLAG_CUDA_CORE_BALLS = 4
+WOS_FLAG_ANTITHETIC = 8
 WOS_MAX_D = 12
 WOS_MAX_EXP = 8
 
@@ -41,12 +42,13 @@ class Options(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("walk_offset", ctypes.c_int64),
         ("max_steps", ctypes.c_int64),
+        ("roulette_w", ctypes.c_double),
     ]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in
-                ("walks", "walk_steps", "capped", "outside", "shrinks", "refine_overflow")]
+                ("walks", "walk_steps", "capped", "outside", "shrinks", "killed")]
 
 
 STATS_FIELDS = [f[0] for f in Stats._fields_]

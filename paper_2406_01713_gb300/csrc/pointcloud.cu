@@ -697,16 +697,32 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             }
             if (L.radius_out != nullptr && k == 0) L.radius_out[j] = (double)best;
             const float R = best - P.shrink;
-            int outcome = 0;
+            int outcome = 0;  // 0 jump, 1 boundary reached, 2 capped, 3 query outside, 4 roulette
             if (k == 0 && !(R > 0.f))
                 outcome = 3;
             else if (R < P.eps && !(GRAD && P.grad_mode && k == 0))
                 outcome = 1;
             else if (k >= L.max_steps)
                 outcome = 2;
+            else if (P.roulette_w > 0.f && k > 0 && logw < P.log_roulette_w) {
+                // Russian roulette: survive with probability W / w_min carrying w_min
+                if (roulette_uniform(L.seed, (uint64_t)(P.walk_base + j), (uint32_t)k) < expf(logw - P.log_roulette_w))
+                    logw = P.log_roulette_w;
+                else
+                    outcome = 4;
+            }
             if (outcome == 0) {
                 float v[D];
-                direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + j), (uint32_t)k, v);
+                const uint64_t walk = (uint64_t)(P.walk_base + j);
+                if (k == 0) {
+                    direction_f32<D, true>(L.seed, first_direction_walk(walk, P.antithetic), 0u, v);
+                    if (first_direction_negated(walk, P.antithetic)) {
+#pragma unroll
+                        for (int i = 0; i < D; ++i) v[i] = -v[i];
+                    }
+                } else {
+                    direction_f32<D, true>(L.seed, walk, (uint32_t)k, v);
+                }
                 const float2 tb = table_lookup(P.table, R * P.sqrt_sigma);
                 if (GRAD && k == 0)
                     gfac0 = P.laplace ? ((float)D / R) * __expf(-tb.x) : ((float)D / R) / tb.y;
@@ -781,7 +797,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             // the first direction: for the gradient terms, and for every walk that took its first
             // sphere when the control variate sums sum v0 and sum v0^2
             const bool need_v0 = (has_grad && term != 0.f) || cv_walk;
-            if (GRAD && need_v0) direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + j), 0u, v0);
+            if (GRAD && need_v0) {
+                const uint64_t walk = (uint64_t)(P.walk_base + j);
+                direction_f32<D, true>(L.seed, first_direction_walk(walk, P.antithetic), 0u, v0);
+                if (first_direction_negated(walk, P.antithetic)) {
+#pragma unroll
+                    for (int i = 0; i < D; ++i) v0[i] = -v0[i];
+                }
+            }
             const float gt = has_grad ? gfac0 * term : 0.f;
             // control variate: G = alpha(R0)/C(R0), one number per query (every walk writes it)
             if (cv_walk && gfac0 != 0.f)

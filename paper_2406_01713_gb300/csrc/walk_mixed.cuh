@@ -506,16 +506,33 @@ template <int D, bool GRAD>
 __device__ __forceinline__ void step_walker(const MixedLaunch &L, const MixedProblem &P, MixedSmem &S,
                                             const float4 *balls, const float *geom, MixedWalker<D> &W,
                                             float R, int kind, int idx, unsigned end) {
-    int outcome = 0;  // 0 jump, 1 boundary reached, 2 capped, 3 query outside
+    int outcome = 0;  // 0 jump, 1 boundary reached, 2 capped, 3 query outside, 4 roulette
     if (W.k == 0 && !(R > 0.f))
         outcome = 3;
     else if (R < P.eps && !(GRAD && P.grad_mode && W.k == 0))
         outcome = 1;
     else if (W.k >= L.max_steps)
         outcome = 2;
+    else if (P.roulette_w > 0.f && W.k > 0 && W.logw < P.log_roulette_w) {
+        // Russian roulette: survive with probability W / w_min carrying w_min
+        if (roulette_uniform(L.seed, (uint64_t)(P.walk_base + (long long)W.j), (uint32_t)W.k) <
+            expf(W.logw - P.log_roulette_w))
+            W.logw = P.log_roulette_w;
+        else
+            outcome = 4;
+    }
     if (outcome == 0) {
         float v[D];
-        direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + (long long)W.j), (uint32_t)W.k, v);
+        const uint64_t walk = (uint64_t)(P.walk_base + (long long)W.j);
+        if (W.k == 0) {
+            direction_f32<D, true>(L.seed, first_direction_walk(walk, P.antithetic), 0u, v);
+            if (first_direction_negated(walk, P.antithetic)) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) v[i] = -v[i];
+            }
+        } else {
+            direction_f32<D, true>(L.seed, walk, (uint32_t)W.k, v);
+        }
         const float2 t = table_lookup(P.table, R * P.sqrt_sigma);
         if (P.has_source) source_step<D, GRAD>(P, W, R, t);
         if (GRAD && W.k == 0) {
@@ -538,8 +555,9 @@ __device__ __forceinline__ void step_walker(const MixedLaunch &L, const MixedPro
 #pragma unroll
     for (int k = 0; k < kMaxExp; ++k) e[k] = 0.f;
     if (outcome == 1) term = terminal_value<D>(P, geom, balls, W.x2, kind, idx, W.logw, e) + W.src;
+    if (outcome == 4) term = W.src;  // ended by the roulette: the source contributions so far
     // (a value-only problem in a gradient launch has no gradient terms: its records carry none)
-    const bool has_grad = GRAD && P.grad_mode && outcome == 1 && W.k > 0;
+    const bool has_grad = GRAD && P.grad_mode && (outcome == 1 || outcome == 4) && W.k > 0;
     const bool cv_walk = GRAD && P.cv && W.k > 0 && outcome != 3;  // capped walks count too
     float v0[D];
 #pragma unroll
@@ -548,7 +566,14 @@ __device__ __forceinline__ void step_walker(const MixedLaunch &L, const MixedPro
     // walk that took its first sphere when the control variate sums sum v0 and sum v0^2
     const bool need_v0 = (has_grad && (term != 0.f || W.src0 != 0.f)) || cv_walk;
     if constexpr (GRAD) {
-        if (need_v0) direction_f32<D, true>(L.seed, (uint64_t)(P.walk_base + (long long)W.j), 0u, v0);
+        if (need_v0) {
+            const uint64_t walk = (uint64_t)(P.walk_base + (long long)W.j);
+            direction_f32<D, true>(L.seed, first_direction_walk(walk, P.antithetic), 0u, v0);
+            if (first_direction_negated(walk, P.antithetic)) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) v0[i] = -v0[i];
+            }
+        }
     }
     // u^(x_1) C(R0): the walk's value without its step-0 source part
     const float gt = has_grad ? W.gfac0 * (term - W.src0) : 0.f;

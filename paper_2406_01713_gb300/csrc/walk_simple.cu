@@ -23,7 +23,7 @@ struct WalkResult {
     T gsrc[D]; // impulse source: q grad_x G_B(x0, z), the source part of the gradient
     T dw[kMaxExp];
     int64_t jumps;
-    int capped, outside;
+    int capped, outside, killed;
 };
 
 template <int D>
@@ -57,6 +57,7 @@ __device__ void run_walk(const SimpleParams<T> &p, const double *xq, uint64_t wa
     res.dsig = T(0);
     res.capped = 0;
     res.outside = 0;
+    res.killed = 0;
 #pragma unroll
     for (int i = 0; i < kMaxExp; ++i) res.dw[i] = T(0);
 #pragma unroll
@@ -85,6 +86,21 @@ __device__ void run_walk(const SimpleParams<T> &p, const double *xq, uint64_t wa
             res.term = T(0);
             break;
         }
+        if (p.roulette_w > 0.0 && k > 0) {
+            // Russian roulette on the weight W: survive with probability W / w_min carrying w_min,
+            // or end with the source contributions so far and no boundary value
+            const T W = exp(logw);
+            if (W < (T)p.roulette_w) {
+                const T u = (T)roulette_uniform(p.seed, walk, (uint32_t)k);
+                if (u < W / (T)p.roulette_w) {
+                    logw = log((T)p.roulette_w);
+                } else {
+                    res.killed = 1;
+                    res.term = src;
+                    break;
+                }
+            }
+        }
         if (dm.has_source) {
             // the ball B(x_k, R) contains the source: q G_B(x_k, z) times the weight so far
             // (evaluated in FP64 in both precisions)
@@ -108,7 +124,15 @@ __device__ void run_walk(const SimpleParams<T> &p, const double *xq, uint64_t wa
                 }
             }
         }
-        direction<D>(p.seed, walk, (uint32_t)k, v);
+        if (k == 0) {
+            direction<D>(p.seed, first_direction_walk(walk, p.antithetic), 0u, v);
+            if (first_direction_negated(walk, p.antithetic)) {
+#pragma unroll
+                for (int j = 0; j < D; ++j) v[j] = -v[j];
+            }
+        } else {
+            direction<D>(p.seed, walk, (uint32_t)k, v);
+        }
         const T z = R * p.sqrt_sigma;
         const T S0 = bessel_S<T>(nu, z);
         const T S1 = bessel_S<T>(nu + T(1), z);
@@ -171,6 +195,7 @@ __global__ void __launch_bounds__(128) walk_simple_kernel(const SimpleParams<T> 
         WalkResult<T, D> r;
         r.jumps = 0;
         r.term = T(0);
+        r.killed = 0;
         if (active) {
             run_walk<T, D>(p, p.x + q * D, (uint64_t)(p.walk_offset + j), r);
             if (p.w_term) p.w_term[j] = r.outside ? (double)CUDART_NAN : (double)r.term;
@@ -188,7 +213,15 @@ __global__ void __launch_bounds__(128) walk_simple_kernel(const SimpleParams<T> 
         const int seg_end = 31 - __clz(peers);
         const bool leader = (lane == __ffs(peers) - 1) && q >= 0;
         const bool ok = active && !r.outside;
-        T vals[3] = {ok ? r.term : T(0), ok ? r.term * r.term : T(0), ok ? r.dsig : T(0)};
+        // squares: of the walk's value, or with antithetic pairs (lanes 2i, 2i + 1 hold the walks
+        // 2m, 2m + 1 of one query: N and the walk offset are even) of the pair mean, on the even lane
+        auto square = [&](T v) -> T {
+            if (!p.antithetic) return v * v;
+            const T m = T(0.5) * (v + __shfl_xor_sync(0xffffffffu, v, 1));
+            return (lane & 1) ? T(0) : m * m;
+        };
+        const T t_ok = ok ? r.term : T(0);
+        T vals[3] = {t_ok, square(t_ok), ok ? r.dsig : T(0)};
         T *acc = p.acc + (q >= 0 ? q : 0) * p.nf;
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
@@ -199,7 +232,7 @@ __global__ void __launch_bounds__(128) walk_simple_kernel(const SimpleParams<T> 
         for (int i = 0; i < D; ++i) {
             const T g = ok ? r.grad[i] : T(0);
             const T s1 = segment_sum(g, lane, seg_end);
-            const T s2 = segment_sum(g * g, lane, seg_end);
+            const T s2 = segment_sum(square(g), lane, seg_end);
             if (leader) {
                 atomicAdd(acc + 3 + i, s1);
                 atomicAdd(acc + 3 + D + i, s2);
@@ -235,13 +268,14 @@ __global__ void __launch_bounds__(128) walk_simple_kernel(const SimpleParams<T> 
 #pragma unroll
             for (int i = 0; i < D; ++i) sp[1 + i] = r.gsrc[i];
         }
-        const unsigned long long c[4] = {active ? 1ull : 0ull,
-                                         active ? (unsigned long long)(r.jumps + 1) : 0ull,
-                                         (unsigned long long)(active && r.capped),
-                                         (unsigned long long)(active && r.outside)};
+        const unsigned long long c[kCounters] = {active ? 1ull : 0ull,
+                                                 active ? (unsigned long long)(r.jumps + 1) : 0ull,
+                                                 (unsigned long long)(active && r.capped),
+                                                 (unsigned long long)(active && r.outside),
+                                                 (unsigned long long)(active && r.killed)};
         unsigned long long *cnt = p.counts + (q >= 0 ? q : 0) * kCounters;
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
+        for (int f = 0; f < kCounters; ++f) {
             const unsigned long long s = segment_sum(c[f], lane, seg_end);
             if (leader) atomicAdd(cnt + f, s);
         }

@@ -255,6 +255,7 @@ wos_status ensure_table(wos_domain_t dom, double sigma, WeightTable *out) {
 // =====================================================================================
 struct FinalizeRec {
     int d, K, acc_f32;
+    int anti;        // antithetic pairs: the squared fields hold squared pair means (N/2 pairs)
     int cv;          // gradient control variate sums present
     int src;         // impulse-source fields present (gradient walks)
     int has_source;  // impulse source: du/dsigma is not estimated (NaN)
@@ -307,8 +308,11 @@ __global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
         if (t == 0 && a.stats != nullptr && a.shrinks != nullptr)
             atomicAdd(reinterpret_cast<unsigned long long *>(a.stats) + 4, *a.shrinks);
         const double nan = CUDART_NAN;
+        // standard errors: from the walks, or from the N/2 antithetic pair means (their sum is
+        // half the walks' sum)
+        const double sh = R->anti ? 0.5 : 1.0, ns = R->anti ? 0.5 * n : n;
         if (R->u) R->u[q] = out ? nan : S(0) * inv;
-        if (R->u_se) R->u_se[q] = out ? nan : se_mean(S(0), S(1), n);
+        if (R->u_se) R->u_se[q] = out ? nan : se_mean(sh * S(0), S(1), ns);
         if (R->du_dsigma) R->du_dsigma[q] = (out || R->has_source) ? nan : S(2) * inv;
         const bool cv = R->cv && n >= 2.0;
         const int cf = cv_field(d, K);
@@ -317,7 +321,7 @@ __global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
         const int sf = src_field(d, K, R->cv);
         const double s0 = R->src ? S(sf) : 0.0;
         for (int i = 0; i < d; ++i) {
-            double g = S(3 + i) * inv, se = se_mean(S(3 + i), S(3 + d + i), n);
+            double g = S(3 + i) * inv, se = se_mean(sh * S(3 + i), S(3 + d + i), ns);
             if (cv)  // sum (t - s0) = sum t - n s0, sum (t - s0) v^2 = sum t v^2 - s0 sum v^2
                 cv_estimate(S(3 + i), S(3 + d + i), S(cf + i), S(cf + d + i) - s0 * S(cf + 2 * d + i),
                             S(cf + 2 * d + i), S(cf + 3 * d), S(0) - n * s0, n, g, se);
@@ -334,6 +338,7 @@ __global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
             atomicAdd(st + 1, c[1]);
             if (c[2]) atomicAdd(st + 2, c[2]);
             if (c[3]) atomicAdd(st + 3, c[3]);
+            if (c[4]) atomicAdd(st + 5, c[4]);
         }
     }
 }
@@ -358,6 +363,7 @@ __host__ __device__ inline int reduce_sums(int d, int K, int cv) { return 3 + 2 
 
 struct ReduceRec {
     int d, K, grad, cv, nf;      // nf: accumulator fields per query (acc_fields)
+    int anti;                    // antithetic pairs: squares of pair means
     int rw;                      // record words
     int64_t Q, N;
     int64_t nseg;                // segments per query
@@ -408,21 +414,27 @@ __device__ void reduce_segment(const ReduceRec &R, int64_t q, int64_t seg, doubl
     for (int i = 0; i < D; ++i) g[i] = g2[i] = sv[i] = stv2[i] = sv2[i] = 0.0;
 #pragma unroll
     for (int k = 0; k < kMaxExp; ++k) dw[k] = 0.0;
-    unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    unsigned long long c[kCounters] = {0ull, 0ull, 0ull, 0ull, 0ull};
     const int64_t w0 = seg * kReduceSegment;
     const int64_t w1 = w0 + kReduceSegment < R.N ? w0 + kReduceSegment : R.N;
     const float *base = R.rec + (q * R.N) * R.rw;
     const int eoff = 4 + (R.grad ? D : 0);
-    for (int64_t w = w0 + t; w < w1; w += kReduceThreads) {
+    // one record: counters and plain sums; returns the walk's value and gradient terms (the
+    // squares are added by the caller: per walk, or per antithetic pair mean)
+    auto one = [&](int64_t w, double &tv, double (&gv)[D]) {
+        tv = 0.0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) gv[i] = 0.0;
         const float *r = base + w * R.rw;
         const float4 h = __ldg(reinterpret_cast<const float4 *>(r));
         const unsigned info = __float_as_uint(h.w);
-        const int outcome = (int)((info >> kRecOutcomeShift) & 3u);
-        c0 += 1ull;
-        c1 += (unsigned long long)(info & kRecKMask) + 1ull;
-        c2 += outcome == 2 ? 1ull : 0ull;
-        c3 += outcome == 3 ? 1ull : 0ull;
-        if (outcome == 3) continue;
+        const int outcome = (int)((info >> kRecOutcomeShift) & kRecOutcomeMask);
+        c[0] += 1ull;
+        c[1] += (unsigned long long)(info & kRecKMask) + 1ull;
+        c[2] += outcome == 2 ? 1ull : 0ull;
+        c[3] += outcome == 3 ? 1ull : 0ull;
+        c[4] += outcome == 4 ? 1ull : 0ull;
+        if (outcome == 3) return;
         const double term = (double)h.x;
         const bool has_v0 = (info & kRecHasV0) != 0u;
         float v0[D];
@@ -441,15 +453,14 @@ __device__ void reduce_segment(const ReduceRec &R, int64_t q, int64_t seg, doubl
             for (int i = D & ~3; i < D; ++i) v0[i] = __ldg(r + 4 + i);
         }
         if (term != 0.0) {
+            tv = term;
             u += term;
-            u2 += term * term;
             ds += term * (double)h.y;
             if (h.z != 0.f) {
 #pragma unroll
                 for (int i = 0; i < D; ++i) {
-                    const double gi = (double)h.z * (double)v0[i];
-                    g[i] += gi;
-                    g2[i] += gi * gi;
+                    gv[i] = (double)h.z * (double)v0[i];
+                    g[i] += gv[i];
                 }
             }
 #pragma unroll
@@ -463,6 +474,29 @@ __device__ void reduce_segment(const ReduceRec &R, int64_t q, int64_t seg, doubl
                 sv[i] += vi;
                 sv2[i] += vi * vi;
                 stv2[i] += term * vi * vi;
+            }
+        }
+    };
+    if (!R.anti) {
+        for (int64_t w = w0 + t; w < w1; w += kReduceThreads) {
+            double tv, gv[D];
+            one(w, tv, gv);
+            u2 += tv * tv;
+#pragma unroll
+            for (int i = 0; i < D; ++i) g2[i] += gv[i] * gv[i];
+        }
+    } else {
+        // antithetic pairs (2m, 2m + 1): the squares of the pair means (segments start even)
+        for (int64_t w = w0 + 2 * t; w + 1 < w1; w += 2 * kReduceThreads) {
+            double ta, ga[D], tb, gb[D];
+            one(w, ta, ga);
+            one(w + 1, tb, gb);
+            const double m = 0.5 * (ta + tb);
+            u2 += m * m;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const double mg = 0.5 * (ga[i] + gb[i]);
+                g2[i] += mg * mg;
             }
         }
     }
@@ -491,15 +525,10 @@ __device__ void reduce_segment(const ReduceRec &R, int64_t q, int64_t seg, doubl
 #pragma unroll
         for (int i = 0; i < D; ++i) put(sv2[i]);
     }
-    c0 = warp_sum_u64(c0);
-    c1 = warp_sum_u64(c1);
-    c2 = warp_sum_u64(c2);
-    c3 = warp_sum_u64(c3);
-    if (lane == 0) {
-        redc[wp][0] = c0;
-        redc[wp][1] = c1;
-        redc[wp][2] = c2;
-        redc[wp][3] = c3;
+#pragma unroll
+    for (int k = 0; k < kCounters; ++k) {
+        const unsigned long long v = warp_sum_u64(c[k]);
+        if (lane == 0) redc[wp][k] = v;
     }
     __syncthreads();
     const int nsum = f;
@@ -579,9 +608,10 @@ size_t partial_bytes(int d, int K, int cv, int64_t Q, int64_t N) {
     return ((size_t)(Q * nseg) * (reduce_sums(d, K, cv) + kCounters) * sizeof(double) + 255) & ~(size_t)255;
 }
 
-ReduceRec make_reduce_rec(int d, int K, int grad, int cv, int src, int64_t Q, int64_t N, const float *rec,
-                          double *acc, unsigned long long *counts, double *part) {
+ReduceRec make_reduce_rec(int d, int K, int grad, int cv, int src, int anti, int64_t Q, int64_t N,
+                          const float *rec, double *acc, unsigned long long *counts, double *part) {
     ReduceRec r{};
+    r.anti = anti;
     r.d = d;
     r.K = K;
     r.grad = grad;
@@ -628,22 +658,39 @@ struct Opts {
     int precision, laplace;
     int cv;  // gradient control variate (gradient calls only)
     int cuda_core_balls;  // keep tensor-core ball sets on the CUDA-core screen
+    int antithetic;       // walk pairs with opposite first directions
     uint64_t seed;
     int64_t walk_offset, max_steps;
+    double roulette_w;    // > 0: Russian roulette on weights below it
 };
 
 Opts read_opts(const wos_options *o) {
-    Opts r{WOS_MIXED, 0, 0, 0, 0ull, 0, 10000};
+    Opts r{WOS_MIXED, 0, 0, 0, 0, 0ull, 0, 10000, 0.0};
     if (o != nullptr) {
         r.precision = o->precision;
         r.laplace = (o->flags & WOS_FLAG_LAPLACE_FACTOR) ? 1 : 0;
         r.cv = (o->flags & WOS_FLAG_GRAD_CONTROL_VARIATE) ? 1 : 0;
         r.cuda_core_balls = (o->flags & WOS_FLAG_CUDA_CORE_BALLS) ? 1 : 0;
+        r.antithetic = (o->flags & WOS_FLAG_ANTITHETIC) ? 1 : 0;
         r.seed = o->seed;
         r.walk_offset = o->walk_offset;
         r.max_steps = o->max_steps > 0 ? o->max_steps : 10000;
+        r.roulette_w = o->roulette_w;
     }
     return r;
+}
+
+// Options that need checks against the call: the roulette threshold, and the antithetic pair
+// layout (N and the walk offset even, not with the control variate).
+wos_status check_opts(const Opts &o, int64_t N) {
+    if (!(o.roulette_w >= 0.0) || !std::isfinite(o.roulette_w))
+        return fail(WOS_ERR_INVALID_ARG, "roulette_w must be finite and >= 0");
+    if (o.antithetic) {
+        if (N % 2 != 0 || o.walk_offset % 2 != 0)
+            return fail(WOS_ERR_INVALID_ARG, "antithetic pairs need n_walks and walk_offset even");
+        if (o.cv) return fail(WOS_ERR_INVALID_ARG, "antithetic pairs are not combined with the control variate");
+    }
+    return WOS_OK;
 }
 
 struct PerWalk {
@@ -727,6 +774,9 @@ MixedProblem make_mixed_problem(wos_domain_t dom, const double *x, int64_t Q, in
     }
     P.laplace = laplace;
     P.cv = grad_mode && cv;
+    P.antithetic = 0;
+    P.roulette_w = 0.f;
+    P.log_roulette_w = 0.f;
     P.eps = (float)eps;
     P.sqrt_sigma = (float)std::sqrt(sigma);
     P.shrink = (float)dom->shrink32;
@@ -749,6 +799,13 @@ MixedProblem make_mixed_problem(wos_domain_t dom, const double *x, int64_t Q, in
     return P;
 }
 
+// The walk options every mixed-precision problem record carries: antithetic pairs, roulette.
+void apply_walk_opts(MixedProblem &P, const Opts &o) {
+    P.antithetic = o.antithetic;
+    P.roulette_w = (float)o.roulette_w;
+    P.log_roulette_w = o.roulette_w > 0.0 ? (float)std::log(o.roulette_w) : 0.f;
+}
+
 size_t mixed_smem_bytes(const wos_domain_s &D) {
     return (size_t)((D.n_balls + 7) / 8) * (D.d + 2) * 32;
 }
@@ -757,7 +814,7 @@ size_t mixed_smem_bytes(const wos_domain_s &D) {
 wos_status launch_reduce_single(wos_domain_t dom, const Opts &o, int64_t Q, int64_t N, int grad_mode,
                                 const Scratch &sc, const int *skip, cudaStream_t s) {
     ReduceArgs ra{};
-    ra.single = make_reduce_rec(dom->d, dom->n_exp, grad_mode, o.cv, dom->has_source, Q, N, sc.rec,
+    ra.single = make_reduce_rec(dom->d, dom->n_exp, grad_mode, o.cv, dom->has_source, o.antithetic, Q, N, sc.rec,
                                 (double *)sc.acc, sc.counts, sc.part);
     ra.n = 1;
     ra.total_blocks = Q * ra.single.nseg;
@@ -789,6 +846,8 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
         p.laplace = o.laplace;
         p.cv = cv;
         p.src = src;
+        p.antithetic = o.antithetic;
+        p.roulette_w = o.roulette_w;
         p.acc = (double *)sc.acc;
         p.counts = sc.counts;
         p.nf = nf;
@@ -816,6 +875,8 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
         p.laplace = o.laplace;
         p.cv = cv;
         p.src = src;
+        p.antithetic = o.antithetic;
+        p.roulette_w = o.roulette_w;
         p.acc = (float *)sc.acc;
         p.counts = sc.counts;
         p.nf = nf;
@@ -841,6 +902,7 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
             return fail(WOS_ERR_UNSUPPORTED, "a point set with an impulse source runs in FP64 or plain FP32");
         MixedProblem P = make_mixed_problem(dom, x, Q, N, eps, sigma, grad_mode, o.laplace, cv, o.walk_offset, tab,
                                             (double *)sc.acc, sc.counts, pw, sc.rec);
+        apply_walk_opts(P, o);
         unsigned long long *shrinks = sc.cursor + 1;
         int *status = reinterpret_cast<int *>(sc.cursor + 2);
         WOS_CUDA(launch_pointcloud(dom->pcd, P, dom->pc_delta, sc.cursor, status, shrinks, o.seed, o.max_steps,
@@ -887,6 +949,7 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
     L.skip = skip;
     L.single = make_mixed_problem(dom, x, Q, N, eps, sigma, grad_mode, o.laplace, cv, o.walk_offset,
                                   tab, (double *)sc.acc, sc.counts, pw, sc.rec);
+    apply_walk_opts(L.single, o);
     WOS_CUDA(launch_walk_mixed(L, grad_mode, grid, threads, smem, s));
     return launch_reduce_single(dom, o, Q, N, grad_mode, sc, skip, s);
 }
@@ -914,6 +977,11 @@ wos_status run_estimator(wos_domain_t dom, const wos_options *opt, const double 
     const Opts o = read_opts(opt);
     if (o.precision < WOS_FP64 || o.precision > WOS_MIXED)
         return fail(WOS_ERR_INVALID_ARG, "unknown precision %d", o.precision);
+    {
+        Opts oc = o;
+        if (!grad_mode) oc.cv = 0;  // value calls ignore the control variate
+        WOS_TRY(check_opts(oc, N));
+    }
     if (stats != nullptr) WOS_CUDA(cudaMemsetAsync(stats, 0, sizeof(wos_stats), s));
     if (Q == 0) return WOS_OK;
     const int cv = grad_mode && o.cv;
@@ -941,6 +1009,7 @@ wos_status run_estimator(wos_domain_t dom, const wos_options *opt, const double 
         r.d = dom->d;
         r.K = dom->n_exp;
         r.acc_f32 = o.precision == WOS_FP32_PLAIN;
+        r.anti = o.antithetic;
         r.cv = cv;
         r.src = src;
         r.has_source = dom->has_source;
@@ -1382,6 +1451,7 @@ wos_status wos_plan_step(wos_domain_t dom, const wos_options *opt, double *x, in
     WOS_TRY(check_common(dom, x, 1, n_walks, eps, sigma));
     if (flag == nullptr || !(s_ub > 0)) return fail(WOS_ERR_INVALID_ARG, "flag NULL or s_ub <= 0");
     const Opts o = read_opts(opt);
+    WOS_TRY(check_opts(o, n_walks));
     cudaStream_t s = (cudaStream_t)stream;
     if (o.precision == WOS_MIXED) {
         WeightTable t;
@@ -1411,6 +1481,7 @@ wos_status wos_plan_path(wos_domain_t dom, const wos_options *opt, const double 
     if (path == nullptr || flags == nullptr || n_steps < 0 || !(s_ub > 0))
         return fail(WOS_ERR_INVALID_ARG, "bad planner arguments");
     const Opts o = read_opts(opt);
+    WOS_TRY(check_opts(o, n_walks));
     cudaStream_t s = (cudaStream_t)stream;
     const int d = dom->d;
     WOS_CUDA(cudaMemcpyAsync(path, x0, sizeof(double) * d, cudaMemcpyDeviceToDevice, s));
@@ -1825,8 +1896,9 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         mp[i] = make_mixed_problem(p.domain, p.x, p.n_queries, p.n_walks, p.eps, p.sigma,
                                    p.grad != nullptr, b->o.laplace, b->o.cv, walk_base, tab, acc, cnt,
                                    PerWalk{}, reinterpret_cast<float *>(base + rec_off[i]));
+        apply_walk_opts(mp[i], b->o);
         rr[i] = make_reduce_rec(p.domain->d, p.domain->n_exp, p.grad != nullptr, b->o.cv, p.domain->has_source,
-                                p.n_queries, p.n_walks, reinterpret_cast<float *>(base + rec_off[i]), acc, cnt,
+                                b->o.antithetic, p.n_queries, p.n_walks, reinterpret_cast<float *>(base + rec_off[i]), acc, cnt,
                                 reinterpret_cast<double *>(base + part_off[i]));
         rr[i].blk_begin = red_blocks;
         rr[i].q_begin = q_begin;
@@ -1836,6 +1908,7 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         r.d = p.domain->d;
         r.K = p.domain->n_exp;
         r.acc_f32 = 0;
+        r.anti = b->o.antithetic;
         r.cv = mp[i].cv;
         r.src = mp[i].src;
         r.has_source = p.domain->has_source;
@@ -2007,6 +2080,9 @@ wos_status wos_batch_create(const wos_problem *probs, int32_t n_problems, const 
                         kPointCloudMaxD);
         if (p.n_queries * p.n_walks > (int64_t)0x7fffffff)
             return fail(WOS_ERR_UNSUPPORTED, "problem %d: n_queries * n_walks must be < 2^31", i);
+        Opts oc = o;
+        if (p.grad == nullptr) oc.cv = 0;
+        WOS_TRY(check_opts(oc, p.n_walks));
     }
     wos_batch_s *b = new (std::nothrow) wos_batch_s();
     if (b == nullptr) return fail(WOS_ERR_OOM, "host allocation failed");
@@ -2153,6 +2229,11 @@ extern "C" wos_status wos_solve_noalloc(wos_domain_t dom, const wos_options *opt
     WOS_TRY(check_common(dom, x, Q, n_walks, eps, sigma));
     if (Q > 0 && u == nullptr) return fail(WOS_ERR_INVALID_ARG, "u is NULL");
     const Opts o = read_opts(opt);
+    {
+        Opts oc = o;
+        oc.cv = 0;  // value walks
+        WOS_TRY(check_opts(oc, n_walks));
+    }
     if (o.precision != WOS_FP64 && o.precision != WOS_FP32_PLAIN)
         return fail(WOS_ERR_UNSUPPORTED,
                     "wos_solve_noalloc runs WOS_FP64 or WOS_FP32_PLAIN (mixed precision allocates tables)");
@@ -2181,6 +2262,7 @@ extern "C" wos_status wos_solve_noalloc(wos_domain_t dom, const wos_options *opt
     r.d = dom->d;
     r.K = dom->n_exp;
     r.acc_f32 = o.precision == WOS_FP32_PLAIN;
+    r.anti = o.antithetic;
     r.Q = Q;
     r.N = n_walks;
     r.q_begin = 0;

@@ -127,6 +127,22 @@ __device__ __forceinline__ void direction_f32(uint64_t seed, uint64_t walk, uint
     }
 }
 
+// Uniform of the Russian roulette before jump `step` of a walk: the top 24 bits of Philox block
+// 15 of (walk, step) times 2^-24 (exact in FP32 and FP64; the direction blocks are 0..2).
+__device__ __forceinline__ float roulette_uniform(uint64_t seed, uint64_t walk, uint32_t step) {
+    const uint4 r = philox_block(seed, walk, step, 15u);
+    return (float)(r.x >> 8) * 5.9604644775390625e-08f;
+}
+
+// Walk index whose step-0 stream gives a walk's first direction, and its sign: with antithetic
+// pairs, walk 2m + 1 takes the negated first direction of walk 2m.
+__device__ __forceinline__ uint64_t first_direction_walk(uint64_t walk, int antithetic) {
+    return antithetic ? (walk & ~1ull) : walk;
+}
+__device__ __forceinline__ bool first_direction_negated(uint64_t walk, int antithetic) {
+    return antithetic && (walk & 1ull);
+}
+
 // ------------------------------------------------------------------------------------
 // Screened normaliser. With S_mu(z) = Gamma(mu+1) (z/2)^-mu I_mu(z) = sum_k q^k / (k! (mu+1)_k),
 // q = z^2/4 (DLMF 10.25.2):  C_nu(z) = 1 / S_nu(z);  d/dz log C_nu = -(z/d) S_{nu+1}/S_nu;
@@ -186,13 +202,14 @@ struct DomainView {
 // per query because R0 is the distance at the query); with an impulse source in gradient walks,
 // [s0, g_src (d)]: the step-0 source value and the source part of the gradient, also one per
 // query (they depend only on the query). The gradient sums then hold G (t - s0) v0. int64
-// counters [walks, walk_steps, capped, outside] live apart.
+// counters [walks, walk_steps, capped, outside, killed] live apart. With antithetic pairs the
+// squared fields hold the sums of the squared pair means instead ([u^2] and [grad^2]).
 __host__ __device__ __forceinline__ int acc_fields(int d, int K, int cv = 0, int src = 0) {
     return 3 + 2 * d + K + (cv ? 3 * d + 1 : 0) + (src ? d + 1 : 0);
 }
 __host__ __device__ __forceinline__ int src_field(int d, int K, int cv) { return acc_fields(d, K, cv, 0); }
 __host__ __device__ __forceinline__ int cv_field(int d, int K) { return 3 + 2 * d + K; }
-constexpr int kCounters = 4;
+constexpr int kCounters = 5;
 
 // Control-variate gradient of one component from the one-pass sums of a query:
 //   A = sum G t v, A2 = sum (G t v)^2, Sv = sum v, Stv2 = sum t v^2, Sv2 = sum v^2, St = sum t,

@@ -23,6 +23,8 @@ struct SimpleParams {
     int grad_mode, laplace;
     int cv;                      // gradient control variate: accumulate the 3d extra sums
     int src;                     // impulse source in gradient walks: store its per-query fields
+    int antithetic;              // walk pairs (2m, 2m+1) with opposite first directions
+    double roulette_w;           // > 0: Russian roulette on weights below it
     T *acc;                      // Q x nf sums
     unsigned long long *counts;  // Q x kCounters
     int nf;
@@ -44,6 +46,9 @@ struct MixedProblem {
     int src;       // impulse source in gradient walks: store its per-query fields
     int has_source;
     int proj;      // components measured in coordinates 0..proj-1 (= d unless extruded)
+    int antithetic;        // walk pairs (2m, 2m+1) with opposite first directions
+    float roulette_w;      // > 0: Russian roulette on weights below it
+    float log_roulette_w;  // its logarithm (the walkers keep log weights)
     float source_q;
     float src_lc0;        // log(k^nu / (2 pi)^(d/2)), k = sqrt(sigma) > 0
     float src_inv_omega;  // 1 / |S^(d-1)| (sigma = 0)
@@ -95,10 +100,11 @@ struct MixedLaunch {
 // the factor of v0 in its gradient estimate (0 unless the walk reached the boundary after its
 // first sphere); info: k (jumps) | outcome << 28 (0 jumped, 1 boundary, 2 capped, 3 outside) |
 // has_v0 << 31; v0: the first direction (written when has_v0); e_k = exp(a_k . xbar) W (written
-// when term != 0). A record is 16-byte aligned.
+// when term != 0). Outcome 4: ended by the Russian roulette. A record is 16-byte aligned.
 __host__ __device__ constexpr int rec_words(int d, int K, int grad) { return (4 + (grad ? d : 0) + K + 3) & ~3; }
 constexpr unsigned kRecKMask = 0x0fffffffu;  // jumps per walk stay below 2^28
 constexpr int kRecOutcomeShift = 28;
+constexpr unsigned kRecOutcomeMask = 7u;
 constexpr unsigned kRecHasV0 = 0x80000000u;
 
 // Floats per packed ball record for dimension d.

@@ -27,15 +27,17 @@ def _stream():
 
 
 def _opts(precision="mixed", seed=0, walk_offset=0, max_steps=10000, laplace=False, control_variate=False,
-          cuda_core_balls=False):
+          cuda_core_balls=False, roulette=0.0, antithetic=False):
     o = _lib.Options()
     o.precision = _lib.PRECISION[precision] if isinstance(precision, str) else int(precision)
     o.flags = ((_lib.WOS_FLAG_LAPLACE_FACTOR if laplace else 0) |
                (_lib.WOS_FLAG_GRAD_CONTROL_VARIATE if control_variate else 0) |
-               (_lib.WOS_FLAG_CUDA_CORE_BALLS if cuda_core_balls else 0))
+               (_lib.WOS_FLAG_CUDA_CORE_BALLS if cuda_core_balls else 0) |
+               (_lib.WOS_FLAG_ANTITHETIC if antithetic else 0))
     o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     o.walk_offset = int(walk_offset)
     o.max_steps = int(max_steps)
+    o.roulette_w = float(roulette)
     return o
 
 
@@ -127,14 +129,16 @@ class Domain:
 
     # ----------------------------------------------------------------- estimators
     def solve(self, x, n_walks, eps, sigma, precision="mixed", seed=0, walk_offset=0,
-              max_steps=10000, laplace=False, with_stats=False, cuda_core_balls=False):
+              max_steps=10000, laplace=False, with_stats=False, cuda_core_balls=False, roulette=0.0,
+              antithetic=False):
         L = _lib.load()
         x = _dev_f64(x, self.d)
         Q = x.shape[0]
         u = torch.empty(Q, dtype=torch.float64, device=x.device)
         se = torch.empty_like(u)
         st = torch.zeros(6, dtype=torch.int64, device=x.device) if with_stats else None
-        o = _opts(precision, seed, walk_offset, max_steps, laplace, cuda_core_balls=cuda_core_balls)
+        o = _opts(precision, seed, walk_offset, max_steps, laplace, cuda_core_balls=cuda_core_balls,
+                  roulette=roulette, antithetic=antithetic)
         _lib.check(L.wos_solve(self.h, ctypes.byref(o), _ptr(x), Q, int(n_walks), float(eps),
                                float(sigma), _ptr(u), _ptr(se), _ptr(st), _stream()), "wos_solve")
         out = {"u": u, "u_se": se}
@@ -143,7 +147,8 @@ class Domain:
         return out
 
     def grad(self, x, n_walks, eps, sigma, precision="mixed", seed=0, walk_offset=0,
-             max_steps=10000, laplace=False, with_stats=False, control_variate=False, cuda_core_balls=False):
+             max_steps=10000, laplace=False, with_stats=False, control_variate=False, cuda_core_balls=False,
+             roulette=0.0, antithetic=False):
         """u, grad u (first-sphere estimator; control_variate=True subtracts the walks' mean
         value, WOS_FLAG_GRAD_CONTROL_VARIATE), their SEs, du/dsigma and du/dw per query."""
         L = _lib.load()
@@ -154,7 +159,8 @@ class Domain:
                "grad_se": torch.empty(Q, d, **f), "du_dsigma": torch.empty(Q, **f),
                "du_dw": torch.empty(Q, self.n_exp, **f) if self.n_exp else None}
         st = torch.zeros(6, dtype=torch.int64, device=x.device) if with_stats else None
-        o = _opts(precision, seed, walk_offset, max_steps, laplace, control_variate, cuda_core_balls)
+        o = _opts(precision, seed, walk_offset, max_steps, laplace, control_variate, cuda_core_balls, roulette,
+                  antithetic)
         _lib.check(L.wos_grad(self.h, ctypes.byref(o), _ptr(x), Q, int(n_walks), float(eps), float(sigma),
                               _ptr(out["u"]), _ptr(out["u_se"]), _ptr(out["grad"]), _ptr(out["grad_se"]),
                               _ptr(out["du_dsigma"]), _ptr(out["du_dw"]), _ptr(st), _stream()),
@@ -164,7 +170,8 @@ class Domain:
         return out
 
     def walks(self, x, n_walks, eps, sigma, grad_mode=False, precision="mixed", seed=0,
-              walk_offset=0, max_steps=10000, laplace=False, cuda_core_balls=False):
+              walk_offset=0, max_steps=10000, laplace=False, cuda_core_balls=False, roulette=0.0,
+              antithetic=False):
         """Per-walk terminals, jump counts, gradient estimates and d/dsigma (parity checks)."""
         L = _lib.load()
         x = _dev_f64(x, self.d)
@@ -172,7 +179,8 @@ class Domain:
         f = dict(dtype=torch.float64, device=x.device)
         out = {"term": torch.empty(Q, N, **f), "jumps": torch.empty(Q, N, dtype=torch.int64, device=x.device),
                "grad": torch.empty(Q, N, d, **f), "dsigma": torch.empty(Q, N, **f)}
-        o = _opts(precision, seed, walk_offset, max_steps, laplace, cuda_core_balls=cuda_core_balls)
+        o = _opts(precision, seed, walk_offset, max_steps, laplace, cuda_core_balls=cuda_core_balls,
+                  roulette=roulette, antithetic=antithetic)
         _lib.check(L.wos_walks(self.h, ctypes.byref(o), _ptr(x), Q, N, float(eps), float(sigma),
                                int(bool(grad_mode)), _ptr(out["term"]), _ptr(out["jumps"]),
                                _ptr(out["grad"]), _ptr(out["dsigma"]), _stream()), "wos_walks")
@@ -180,20 +188,21 @@ class Domain:
 
     # ----------------------------------------------------------------- planner
     def plan_step(self, x, n_walks, eps, sigma, s_ub, step_idx, precision="mixed", seed=0,
-                  walk_offset=0, max_steps=10000, control_variate=False):
+                  walk_offset=0, max_steps=10000, control_variate=False, roulette=0.0, antithetic=False):
         """One step in place on the device tensor x (d doubles); returns (flag, grad)."""
         L = _lib.load()
         assert x.dtype == torch.float64 and x.is_cuda and x.numel() == self.d and x.is_contiguous()
         flag = torch.zeros(1, dtype=torch.int32, device=x.device)
         g = torch.empty(self.d, dtype=torch.float64, device=x.device)
-        o = _opts(precision, seed, walk_offset, max_steps, control_variate=control_variate)
+        o = _opts(precision, seed, walk_offset, max_steps, control_variate=control_variate, roulette=roulette,
+                  antithetic=antithetic)
         _lib.check(L.wos_plan_step(self.h, ctypes.byref(o), _ptr(x), int(n_walks), float(eps), float(sigma),
                                    float(s_ub), int(step_idx), _ptr(flag), _ptr(g), _stream()),
                    "wos_plan_step")
         return flag, g
 
     def plan_path(self, x0, n_steps, n_walks, eps, sigma, s_ub, precision="mixed", seed=0,
-                  walk_offset=0, max_steps=10000, control_variate=False):
+                  walk_offset=0, max_steps=10000, control_variate=False, roulette=0.0, antithetic=False):
         """n_steps planner steps replayed as one CUDA graph: (path, flags, grads) on the device."""
         L = _lib.load()
         x0 = _dev_f64(x0).reshape(-1)
@@ -202,7 +211,8 @@ class Domain:
         path = torch.empty(n_steps + 1, d, **f)
         flags = torch.zeros(n_steps, dtype=torch.int32, device=x0.device)
         grads = torch.zeros(n_steps, d, **f)
-        o = _opts(precision, seed, walk_offset, max_steps, control_variate=control_variate)
+        o = _opts(precision, seed, walk_offset, max_steps, control_variate=control_variate, roulette=roulette,
+                  antithetic=antithetic)
         _lib.check(L.wos_plan_path(self.h, ctypes.byref(o), _ptr(x0), int(n_steps), int(n_walks), float(eps),
                                    float(sigma), float(s_ub), _ptr(path), _ptr(flags), _ptr(grads),
                                    _stream()), "wos_plan_path")
@@ -276,7 +286,8 @@ class Batch:
     self.out[i] = {u, u_se, grad, grad_se, walk_steps} are views of them.
     """
 
-    def __init__(self, problems, seed=0, max_steps=10000, config=None, control_variate=False):
+    def __init__(self, problems, seed=0, max_steps=10000, config=None, control_variate=False, roulette=0.0,
+                 antithetic=False):
         L = _lib.load()
         self.problems = problems
         f = dict(dtype=torch.float64, device="cuda")
@@ -321,7 +332,8 @@ class Batch:
             a.walk_steps = o["walk_steps"].data_ptr()
         self.n_x, self.n_q, self.n_g = ox, oq, og
         self._arr = arr
-        opts = _opts("mixed", seed, 0, max_steps, control_variate=control_variate)
+        opts = _opts("mixed", seed, 0, max_steps, control_variate=control_variate, roulette=roulette,
+                     antithetic=antithetic)
         cfg = None
         if config is not None:
             cfg = _lib.BatchConfig(int(config["threads"]), int(config["ctas_per_sm"]), int(config["item_work"]))

@@ -408,3 +408,30 @@ def test_c5_full_size_closed_form():
     assert (np.abs(u - g) <= 4.5 * se + 5e-3 * g).mean() > 0.995
     dw = np_(r["du_dw"])
     assert (np.abs(dw - E) <= 0.05 * E + 1e-3).mean() > 0.99
+
+
+def test_batch_full_size_tensor_core_queries_match_oracle(c4_full):
+    """The problems the tensor-core sphere-set walker runs in the full batch (most of the
+    headline's device time): one query from a problem of every dimension 3..12, plus the
+    problems with the largest ball set and the most walks, against the oracle on the same walk
+    indices, u and every component of grad u at 4 combined SE + 1e-4."""
+    w, doms, b, out = c4_full
+    probs = w["problems"]
+    bases = np.cumsum([0] + [p["X"].shape[0] * p["n_walks"] for p in probs])
+    tens = [i for i, d in enumerate(doms) if d.info()["tensor_sphere_set"]]
+    rng = np.random.default_rng(23)
+    pick = []
+    for d in range(3, 13):
+        of_d = [i for i in tens if probs[i]["domain"]["d"] == d]
+        assert of_d, d
+        pick.append(int(rng.choice(of_d)))
+    pick.append(max(tens, key=lambda i: probs[i]["domain"]["ball_r"].size * probs[i]["domain"]["d"]))
+    pick.append(max(tens, key=lambda i: probs[i]["n_walks"] * probs[i]["domain"]["ball_r"].size))
+    for i in dict.fromkeys(pick):
+        p, o = probs[i], out[i]
+        q = int(rng.integers(p["X"].shape[0]))
+        ref = oracle.solve(p["domain"], p["X"][q:q + 1], p["n_walks"], p["eps"], p["sigma"], w["seed"],
+                           walk_offset=int(bases[i]) + q * p["n_walks"], grad=True)
+        assert agree(np_(o["u"])[q], np_(o["u_se"])[q], ref["u"][0], ref["u_se"][0]), (i, q)
+        assert np.all(agree(np_(o["grad"])[q], np_(o["grad_se"])[q], ref["grad"][0], ref["grad_se"][0])), (i, q)
+        assert int(np_(o["walk_steps"])[q]) > 0

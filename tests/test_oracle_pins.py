@@ -678,6 +678,17 @@ def test_roulette_dsigma_agrees_with_the_plain_estimator(oracle_mod):
     assert np.all(np.abs(m0 - m1) < 4.5 * np.sqrt(s0 ** 2 + s1 ** 2))
 
 
+def test_roulette_killed_count_matches_the_walks(oracle_mod):
+    # the per-query count of walks ended by the roulette is the number of single walks that say so
+    dom, X, _, sigma = _roulette_domain()
+    res = oracle_mod.solve(dom, X[:2], 300, 1e-4, sigma, 8, grad=True, roulette=0.3)
+    for q in range(2):
+        n = sum(oracle_mod.walk(dom, X[q], q * 300 + w, 1e-4, sigma, 8, grad=True, roulette=0.3)["killed"]
+                for w in range(300))
+        assert res["killed"][q] == n > 0
+    assert oracle_mod.solve(dom, X[:2], 300, 1e-4, sigma, 8, grad=True)["killed"].sum() == 0
+
+
 def test_planted_roulette_without_reweight_is_rejected(oracle_mod):
     # survivors that keep their small weight bias u low
     dom, X, a, sigma = _roulette_domain()
