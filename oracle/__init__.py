@@ -10,6 +10,8 @@ compiles it with gcc when needed and marshals numpy arrays through ctypes.
 Domains are plain dicts (see ``paper_2406_01713_gb300.synth``):
     d, box_lo/box_hi (optional), outer_c/outer_r (optional), goal_c/goal_r (optional),
     ball_c (B x d)/ball_r (B), points (M x d), exp_w (K)/exp_a (K x d).
+  Planar arm (configuration-space domains, Sec. V): link_l (n links, joint angles q_0..q_{n-1})
+  and arm_obs (M x 2 task-space obstacle points).
   Oracle-only boundary data for the closed-form pins: poly_c (n) / poly_p (n x d int
   exponents), g = sum_m c_m prod_j x_j^p_mj on the whole boundary; face_g (2d), a constant
   per box face in the order lo_0, hi_0, lo_1, ...
@@ -27,7 +29,7 @@ _LIB = os.path.join(_HERE, "libwos_oracle.so")
 MAXD = 16
 MAXEXP = 16
 
-KIND_GOAL, KIND_BALL, KIND_POINT, KIND_OUTER, KIND_FACE = 0, 1, 2, 3, 4
+KIND_GOAL, KIND_BALL, KIND_POINT, KIND_OUTER, KIND_FACE, KIND_ARM = 0, 1, 2, 3, 4, 5
 
 
 def build(force=False):
@@ -71,6 +73,10 @@ class _Domain(ctypes.Structure):
         ("poly_p", ctypes.POINTER(ctypes.c_int32)),
         ("has_face_g", ctypes.c_int32),
         ("face_g", ctypes.c_double * (2 * MAXD)),
+        ("n_links", ctypes.c_int32),
+        ("link_l", ctypes.c_double * MAXD),
+        ("n_arm_obs", ctypes.c_int64),
+        ("arm_obs", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -120,6 +126,10 @@ def lib():
             L.or_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
             L.or_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, _PD]
             L.or_direction.argtypes = L.or_normals.argtypes
+            L.or_arm_task_distance.argtypes = [ctypes.POINTER(_Domain), _PD]
+            L.or_arm_task_distance.restype = ctypes.c_double
+            L.or_arm_lipschitz.argtypes = [ctypes.POINTER(_Domain)]
+            L.or_arm_lipschitz.restype = ctypes.c_double
             L.or_series_S.argtypes = [ctypes.c_double, ctypes.c_double]
             L.or_series_S.restype = ctypes.c_double
             L.or_log_C.argtypes = [ctypes.c_double, ctypes.c_double]
@@ -215,6 +225,15 @@ class Domain:
             s.n_poly = pc.shape[0]
             s.poly_c = _ptr(pc)
             s.poly_p = _ptr(pp, ctypes.c_int32)
+        if dom.get("link_l") is not None:
+            ll = np.asarray(dom["link_l"], float).reshape(-1)
+            if not 1 <= ll.size <= d:
+                raise ValueError("the arm needs 1..d links")
+            s.n_links = ll.size
+            s.link_l[:ll.size] = list(ll)
+            ob = arr("arm_obs", (-1, 2))
+            s.n_arm_obs = ob.shape[0]
+            s.arm_obs = _ptr(ob)
         if dom.get("face_g") is not None:
             s.has_face_g = 1
             s.face_g[:2 * d] = list(np.asarray(dom["face_g"], float).reshape(2 * d))
@@ -271,6 +290,17 @@ def dsigma_log_C(nu, R, sigma):
 
 def bessel_K(nu, x):
     return lib().or_bessel_K(float(nu), float(x))
+
+
+def arm_task_distance(dom, q):
+    D = dom if isinstance(dom, Domain) else Domain(dom)
+    q = np.ascontiguousarray(np.asarray(q, float))
+    return lib().or_arm_task_distance(ctypes.byref(D.s), _ptr(q))
+
+
+def arm_lipschitz(dom):
+    D = dom if isinstance(dom, Domain) else Domain(dom)
+    return lib().or_arm_lipschitz(ctypes.byref(D.s))
 
 
 def ball_green(d, sigma, r, R, free_space=False):

@@ -38,7 +38,10 @@
  *   Planner (Sec. III screened-harmonic paths; Sec. VII adaptive step):
  *       x <- x + s grad/|grad|,  s = min(s_ub, 0.5 d_bound).
  *   Distance functions (Sec. VI, Eq. for d(x, dOmega); Sec. VII-A point-set distance):
- *       balls: |x - c| - r;  outer ball: r_o - |x - c_o|;  points: |x - p|;  box faces.
+ *       balls: |x - c| - r;  outer ball: r_o - |x - c_o|;  points: |x - p|;  box faces;
+ *       a planar arm in configuration space (Sec. V, V-A): the safe-ball radius d_tau(q) / K,
+ *       d_tau the task-space distance between the links and obstacle points, K the Lipschitz
+ *       constant of the forward kinematics; a walk ending there reads g at its own position.
  *   Boundary data g (Sec. III, u = g on the boundary): the goal indicator of the planning
  *       field, sum_k w_k exp(a_k . x), and two forms used only by the closed-form pins: a
  *       polynomial sum_m c_m prod_j x_j^p_mj (harmonic ones solve sigma = 0 exactly) and one
@@ -66,8 +69,8 @@
  * documented contract:
  *   - sphere directions: Philox4x32-10 (Salmon et al., SC'11), key = seed, counter =
  *     (walk_lo, walk_hi, step, block); Box-Muller on consecutive output pairs;
- *   - strict eps test (R < eps); ties between components go to the lowest component id in
- *     the order [goal, balls, points, outer ball, box faces lo_0, hi_0, lo_1, ...];
+ *   - strict eps test (R < eps); ties between components go to the first in the order
+ *     [goal, balls, points, arm, outer ball, box faces lo_0, hi_0, lo_1, ...];
  *   - a walk that reaches max_steps jumps without entering the eps shell contributes 0.
  *
  * Log-Bessel: S_mu(z) = Gamma(mu+1) (z/2)^-mu I_mu(z) = sum_k (z^2/4)^k / (k! (mu+1)_k)
@@ -89,6 +92,7 @@
 #define OR_KIND_POINT 2
 #define OR_KIND_OUTER 3
 #define OR_KIND_FACE 4
+#define OR_KIND_ARM 5
 
 typedef struct {
     int32_t d;
@@ -118,6 +122,10 @@ typedef struct {
     const int32_t *poly_p; /* n_poly x d exponents */
     int32_t has_face_g;   /* 1 (no exp or poly data): g = face_g[2j] on face lo_j, face_g[2j+1] on hi_j */
     double face_g[2 * OR_MAXD];
+    int32_t n_links;      /* > 0: planar arm of n_links revolute joints, angles q_0..q_{n_links-1} */
+    double link_l[OR_MAXD]; /* link lengths */
+    int64_t n_arm_obs;    /* task-space obstacle points of the arm (planar) */
+    const double *arm_obs; /* n_arm_obs x 2 */
 } or_domain;
 
 typedef struct {
@@ -300,6 +308,43 @@ static double norm_diff(int d, const double *a, const double *b)
     return sqrt(s);
 }
 
+/* Planar arm (Sec. V-A): base at the origin, joint angles q_0..q_{n-1} accumulated along the
+ * chain, link i from the end of link i-1 along the summed angle with length l_i. d_tau(q) is the
+ * task-space distance between the links (segments) and the obstacle points. */
+double or_arm_task_distance(const or_domain *D, const double *q)
+{
+    double px = 0.0, py = 0.0, ang = 0.0, best = INFINITY;
+    for (int n = 0; n < D->n_links; ++n) {
+        ang += q[n];
+        const double ex = px + D->link_l[n] * cos(ang), ey = py + D->link_l[n] * sin(ang);
+        const double sx = ex - px, sy = ey - py, ss = sx * sx + sy * sy;
+        for (int64_t o = 0; o < D->n_arm_obs; ++o) {
+            const double ox = D->arm_obs[2 * o] - px, oy = D->arm_obs[2 * o + 1] - py;
+            double t = ss > 0.0 ? (ox * sx + oy * sy) / ss : 0.0;
+            if (t < 0.0) t = 0.0;
+            if (t > 1.0) t = 1.0;
+            const double dx = ox - t * sx, dy = oy - t * sy;
+            const double r = sqrt(dx * dx + dy * dy);
+            if (r < best) best = r;
+        }
+        px = ex;
+        py = ey;
+    }
+    return best;
+}
+
+/* Lipschitz constant of the planar chain's forward kinematics (Sec. V-A):
+ * K = sqrt(sum_n (sum_{i<=n} l_i)^2). */
+double or_arm_lipschitz(const or_domain *D)
+{
+    double reach = 0.0, k2 = 0.0;
+    for (int n = 0; n < D->n_links; ++n) {
+        reach += D->link_l[n];
+        k2 += reach * reach;
+    }
+    return sqrt(k2);
+}
+
 /* Coordinates the boundary components are measured in: the first m of d. */
 static int obstacle_dims(const or_domain *D)
 {
@@ -324,6 +369,11 @@ double or_distance(const or_domain *D, const double *x, int32_t *kind, int64_t *
     for (int64_t i = 0; i < D->n_points; ++i) {
         double r = norm_diff(m, x, D->points + i * d);
         if (r < best) { best = r; bk = OR_KIND_POINT; bi = i; }
+    }
+    if (D->n_links > 0) {
+        /* the safe-ball radius d_tau / K underestimates the C-space distance (Sec. V, Eq. safe_ball) */
+        double r = or_arm_task_distance(D, x) / or_arm_lipschitz(D);
+        if (r < best) { best = r; bk = OR_KIND_ARM; bi = 0; }
     }
     if (D->has_outer) {
         double r = D->outer_r - norm_diff(m, x, D->outer_c);
@@ -354,6 +404,10 @@ double or_distance(const or_domain *D, const double *x, int32_t *kind, int64_t *
                 xbar[j] = len > 0.0 ? c[j] + rad * (x[j] - c[j]) / len : c[j] + (j == 0 ? rad : 0.0);
         } else if (bk == OR_KIND_POINT) {
             for (int j = 0; j < m; ++j) xbar[j] = D->points[bi * d + j];
+        } else if (bk == OR_KIND_ARM) {
+            /* the arm's boundary point is not known (the distance is only bounded below): the walk
+               ends where it is and reads g there */
+            for (int j = 0; j < d; ++j) xbar[j] = x[j];
         } else if (bk == OR_KIND_FACE) {
             for (int j = 0; j < d; ++j) xbar[j] = x[j];
             int j = (int)(bi / 2);

@@ -272,3 +272,56 @@ def paper_environment(d=2, k_r=0.3, goal=(8.0, 0.0), r_o=10.0):
     if d > 2:
         dom["proj_dims"] = 2
     return dom
+
+
+# ----------------------------------------------------------------------------- RR arm
+RR_TABLE_I = {"q_ub": (1.5 * math.pi, math.pi), "q_start": (0.785, 0.800), "q_goal": (2.042, 0.200),
+              "x_obs": (0.0, 1.3), "n_col": 200, "n_walks": 10 ** 5, "s_ub": 0.1, "c": (0.0, 5.0), "eps": 0.02}
+
+
+def rr_collision_points(link_l=(1.0, 1.0), x_obs=RR_TABLE_I["x_obs"], n=RR_TABLE_I["n_col"]):
+    """Configurations of a planar two-link arm whose second link touches the task-space point
+    x_obs (closed-form inverse kinematics): the elbow lies on the circle of radius l1 at distance
+    <= l2 from x_obs, and link 2 points from the elbow at x_obs. The curve is sampled at n points
+    equidistant in arc length (angles wrapped to [-pi, pi) for joint 2)."""
+    l1, l2 = link_l
+    o = np.asarray(x_obs, float)
+    ro = float(np.linalg.norm(o))
+    # |o - e|^2 = ro^2 + l1^2 - 2 l1 (o . e) <= l2^2 with e = l1 (cos q1, sin q1)
+    c = (ro ** 2 + l1 ** 2 - l2 ** 2) / (2.0 * l1 * ro)
+    if not -1.0 <= c <= 1.0:
+        raise ValueError("the point is not reachable by the second link only")
+    base = math.atan2(o[1], o[0])
+    half = math.acos(c)
+    q1 = np.linspace(base - half, base + half, 200001)
+
+    def pts(q1):
+        e = l1 * np.stack([np.cos(q1), np.sin(q1)], 1)
+        v = o[None, :] - e
+        q2 = (np.arctan2(v[:, 1], v[:, 0]) - q1 + math.pi) % (2.0 * math.pi) - math.pi
+        return np.stack([q1, q2], 1)
+
+    p = pts(q1)
+    s = np.concatenate([[0.0], np.cumsum(np.linalg.norm(np.diff(p, axis=0), axis=1))])
+    return pts(np.interp(np.linspace(0.0, s[-1], n), s, q1))
+
+
+def rr_arm(c=0.0, method="lipschitz", link_l=(1.0, 1.0), q_lb=(0.0, -math.pi)):
+    """The RR validation environment (Sec. VII, Table I): joint limits q_lb..q_ub, the unit impulse
+    at q_goal, zero boundary values, a task-space point obstacle at x_obs. The link lengths
+    (l1 = l2 = 1) and the lower joint limits are this build's reading: the paper shows them only
+    in a figure. method "lipschitz": the arm component (d_tau / K, Sec. V-A); "ik": the 200
+    collision configurations from closed-form IK as a point set (Sec. VII-A)."""
+    t = RR_TABLE_I
+    dom = {"d": 2, "box_lo": np.asarray(q_lb, float), "box_hi": np.asarray(t["q_ub"], float),
+           "source_z": np.asarray(t["q_goal"], float), "source_q": 1.0}
+    if method == "lipschitz":
+        dom["link_l"] = np.asarray(link_l, float)
+        dom["arm_obs"] = np.asarray(t["x_obs"], float)[None, :]
+    elif method == "ik":
+        dom["points"] = rr_collision_points(link_l)
+    else:
+        raise ValueError(method)
+    return {"name": "rr_" + method, "domain": dom, "start": np.asarray(t["q_start"], float),
+            "goal": np.asarray(t["q_goal"], float), "n_walks": t["n_walks"], "eps": t["eps"], "sigma": float(c),
+            "s_ub": t["s_ub"], "seed": walk_seed(6)}

@@ -942,3 +942,110 @@ def test_unit_square_top_edge_fd_and_series(oracle_mod, sigma):
         us, gs = square_series(x, y, sigma)
         assert abs(res["u"][q] - us) < 4.5 * res["u_se"][q] + 1e-4, (q, res["u"][q], us)
         assert np.all(np.abs(res["grad"][q] - gs) < 4.5 * res["grad_se"][q] + 1e-3), (q, res["grad"][q], gs)
+
+
+# --------------------------------------------------------------------------- planar arm (Sec. V, V-A, VII)
+def _chain_points(link_l, q, per_link=4001):
+    """Points along the links of a planar chain (base at the origin), densely sampled."""
+    pts, p, ang = [], np.zeros(2), 0.0
+    for l, qi in zip(link_l, q):
+        ang += qi
+        e = p + l * np.array([math.cos(ang), math.sin(ang)])
+        t = np.linspace(0.0, 1.0, per_link)[:, None]
+        pts.append(p[None, :] + t * (e - p)[None, :])
+        p = e
+    return np.concatenate(pts)
+
+
+def _arm_domain(link_l, obs):
+    n = len(link_l)
+    return {"d": n, "box_lo": -math.pi * np.ones(n), "box_hi": math.pi * np.ones(n),
+            "link_l": np.asarray(link_l, float), "arm_obs": np.asarray(obs, float)}
+
+
+@pytest.mark.parametrize("link_l", [(1.0, 1.0), (0.7, 1.3, 0.5), (0.4, 0.3, 0.6, 0.2)])
+def test_arm_task_distance_brute_force(oracle_mod, link_l):
+    rng = np.random.default_rng(len(link_l))
+    obs = rng.uniform(-1.5, 1.5, (6, 2))
+    dom = _arm_domain(link_l, obs)
+    for q in rng.uniform(-math.pi, math.pi, (50, len(link_l))):
+        pts = _chain_points(link_l, q)
+        brute = np.min(np.linalg.norm(pts[:, None, :] - obs[None, :, :], axis=2))
+        got = oracle_mod.arm_task_distance(dom, q)
+        assert got <= brute + 1e-12 and brute - got <= max(link_l) / 4000 + 1e-12
+
+
+@pytest.mark.parametrize("link_l", [(1.0, 1.0), (0.7, 1.3, 0.5)])
+def test_arm_lipschitz_constant_bounds_the_kinematics(oracle_mod, link_l):
+    """K = sqrt(sum_n (sum_{i<=n} l_i)^2) bounds the spectral norm of the Jacobian of every
+    point of the chain (finite differences), and is reached by the stretched chain when all
+    links are equal."""
+    n = len(link_l)
+    K = oracle_mod.arm_lipschitz(_arm_domain(link_l, [[5.0, 5.0]]))
+    assert abs(K - math.sqrt(sum(sum(link_l[:i + 1]) ** 2 for i in range(n)))) < 1e-14
+    rng = np.random.default_rng(n + 10)
+    h = 1e-6
+    worst = 0.0
+    for q in list(rng.uniform(-math.pi, math.pi, (40, n))) + [np.zeros(n)]:
+        base = _chain_points(link_l, q, per_link=9)
+        J = np.stack([(_chain_points(link_l, q + h * np.eye(n)[j], per_link=9) - base) / h for j in range(n)], axis=2)
+        sv = np.linalg.norm(J, ord=2, axis=(1, 2))
+        worst = max(worst, float(sv.max()))
+        assert np.all(sv <= K * (1 + 1e-5))
+    if len(set(link_l)) == 1:
+        assert worst > K * (1 - 1e-5)  # tight for equal links (the stretched chain's tip)
+
+
+def test_arm_safe_ball_is_collision_free(oracle_mod):
+    """Eq. safe_ball: every configuration inside B(q, d_tau(q) / K) keeps the arm off the
+    obstacles; the oracle's C-space distance of the arm component is that radius."""
+    rng = np.random.default_rng(3)
+    link_l, obs = (0.7, 1.3, 0.5), rng.uniform(-1.5, 1.5, (5, 2))
+    dom = _arm_domain(link_l, obs)
+    K = oracle_mod.arm_lipschitz(dom)
+    checked = 0
+    for q in rng.uniform(-2.5, 2.5, (60, 3)):
+        dt = oracle_mod.arm_task_distance(dom, q)
+        R, kind, _, xbar = oracle_mod.distance(dom, q)
+        if kind != oracle_mod.KIND_ARM:
+            continue
+        assert abs(R - dt / K) < 1e-15 and np.array_equal(xbar, q)
+        v = rng.standard_normal((300, 3))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        y = q[None, :] + (R * rng.uniform(0, 1, (300, 1)) ** (1 / 3)) * v
+        assert all(oracle_mod.arm_task_distance(dom, yy) > 0.0 for yy in y)
+        checked += 1
+    assert checked > 20
+
+
+def test_arm_domain_exp_data_exact_solution(oracle_mod):
+    """g = exp(a.q) with |a|^2 = sigma is the exact solution on the RR configuration space; a walk
+    ending in the arm's shell reads g at its own position, so only the box faces add an O(eps)
+    shell bias."""
+    w = synth.rr_arm(0.0)
+    dom = dict(w["domain"])
+    dom.pop("source_z")
+    sigma = 4.0
+    a = np.array([1.2, -1.6])
+    dom.update({"exp_w": np.ones(1), "exp_a": a[None, :]})
+    X = np.array([w["start"], w["goal"], [1.2, 1.0], [2.6, -0.5]])
+    eps = 1e-3
+    res = oracle_mod.solve(dom, X, 20000, eps, sigma, seed=7, grad=True)
+    g = np.exp(X @ a)
+    bias = 3 * eps * np.linalg.norm(a) * g
+    assert np.all(np.abs(res["u"] - g) < 4.5 * res["u_se"] + bias)
+    assert np.all(np.abs(res["grad"] - a[None, :] * g[:, None]) < 4.5 * res["grad_se"] + 10 * bias[:, None])
+
+
+def test_rr_ik_collision_points_match_the_printed_spacing(oracle_mod):
+    """Sec. VII-A: the 200 collision configurations of the RR arm (closed-form IK) touch the
+    obstacle, and consecutive ones are 0.017..0.0235 apart, the range the paper prints (it
+    supports the link lengths l1 = l2 = 1 read from the figure)."""
+    w = synth.rr_arm(0.0, method="lipschitz")
+    p = synth.rr_collision_points()
+    assert p.shape == (200, 2)
+    assert max(oracle_mod.arm_task_distance(w["domain"], q) for q in p) < 1e-12
+    gap = np.linalg.norm(np.diff(p, axis=0), axis=1)
+    assert gap.min() >= 0.017 and gap.max() <= 0.0235
+    # every IK configuration lies in the joint box of Table I
+    assert np.all(p >= w["domain"]["box_lo"]) and np.all(p <= w["domain"]["box_hi"])
