@@ -49,7 +49,8 @@ def parse():
     p.add_argument("--scale-walks", type=float, default=1.0,
                    help="scale of the walk counts (below 1: the small profiling case)")
     p.add_argument("--launch", default=None,
-                   help="explicit launch shape threads,ctas_per_sm,item_work (skips the autotuner)")
+                   help="explicit launch shape threads,ctas_per_sm,item_work[,sphere_ctas_per_sm,sphere_item_walks] "
+                        "(skips the autotuner)")
     return p.parse_args()
 
 
@@ -281,8 +282,10 @@ def main():
         "SMALL CASE (profiling): first %d problems of [%s], walks x %g" % (args.problems, WORKLOAD, args.scale_walks))
     launch = None
     if args.launch:
-        th, ct, iw = (int(v) for v in args.launch.split(","))
-        launch = {"threads": th, "ctas_per_sm": ct, "item_work": iw}
+        v = [int(t) for t in args.launch.split(",")]
+        launch = {"threads": v[0], "ctas_per_sm": v[1], "item_work": v[2]}
+        if len(v) == 5:
+            launch.update({"sphere_ctas_per_sm": v[3], "sphere_item_walks": v[4]})
         args.no_autotune = True
     batch = W.Batch([{"domain": d, "x": p["X"], "n_walks": p["n_walks"], "eps": p["eps"], "sigma": p["sigma"],
                       "grad": True} for d, p in zip(doms, probs)], seed=replica_seed(w["seed"], rank),
@@ -399,6 +402,10 @@ def main():
                                                                  replica_seed(w["seed"], rank), not args.no_cv)
         except Exception as e:
             line["error_vs_fp64_same_stream"] = {"error": "%s: %s" % (type(e).__name__, e)}
+        try:
+            line["variance_reduction"] = variance_reduction(W, synth, doms, probs, replica_seed(w["seed"], rank))
+        except Exception as e:
+            line["variance_reduction"] = {"error": "%s: %s" % (type(e).__name__, e)}
         line["vs_plain_fp32"] = plain_comparison(W, doms, probs, w["seed"], total_steps, dev_s / args.steps,
                                                  rmse_u, not args.no_cv)
         try:
@@ -629,12 +636,25 @@ def paper_sweeps(W, synth):
         visibility[str(k_r)] = {"path_length": length, "reached_goal_at_step": hit}
     multistart = {}
     try:
+        # the six paths as one batched graph (wos_plan_paths), and one at a time for comparison
         dom = W.Domain(synth.paper_environment(2, k_r=0.2))
-        for deg in (90, 135, 180, 225, 270, 315):
-            x0 = 8.0 * np.array([math.cos(math.radians(deg)), math.sin(math.radians(deg))])
-            path, flags, _ = dom.plan_path(x0, 400, 10 ** 4, eps, 1.0, 0.1, seed=5, control_variate=True)
+        degs = (90, 135, 180, 225, 270, 315)
+        items = [{"domain": dom, "x0": 8.0 * np.array([math.cos(math.radians(g)), math.sin(math.radians(g))]),
+                  "n_walks": 10 ** 4, "eps": eps, "sigma": 1.0, "s_ub": 0.1} for g in degs]
+        ms_batch, res = _timed(lambda: W.plan_paths(items, 400, seed=5, control_variate=True))
+        same = True
+
+        def singles():
+            return [dom.plan_path(it["x0"], 400, 10 ** 4, eps, 1.0, 0.1, seed=5, control_variate=True) for it in items]
+
+        ms_single, one = _timed(singles)
+        for g, (path, flags, _), (p1, f1, _) in zip(degs, res, one):
             length, hit = _path_length(path, flags)
-            multistart[str(deg)] = {"path_length": length, "reached_goal_at_step": hit}
+            multistart[str(g)] = {"path_length": length, "reached_goal_at_step": hit}
+            same &= bool(torch.equal(path, p1)) and bool(torch.equal(flags, f1))
+        multistart["batched_ms"] = ms_batch
+        multistart["one_at_a_time_ms"] = ms_single
+        multistart["batched_equals_one_at_a_time"] = same
     except Exception as e:  # recorded; the studies above are kept
         multistart = {"error": "%s: %s" % (type(e).__name__, e)}
     return {"dimensionality_angle_error": dims, "screening_k_r_0.4": screening, "visibility_c_1": visibility,
@@ -722,6 +742,59 @@ def se_calibration(probs, outs):
             sg.append(o["grad_se"].cpu().numpy().ravel())
     rms = lambda v: float(np.sqrt(np.mean(np.concatenate(v) ** 2)))
     return {"u": rms(eu) / rms(su), "grad": rms(eg) / rms(sg)}
+
+
+def variance_reduction(W, synth, doms, probs, seed):
+    """RMSE per walk-step of the gradient estimators on the batched workload (same walks, same
+    launch shape) and on the d = 2 check workload: the paper's first-sphere estimator, the control
+    variate, antithetic first directions, Russian roulette below weight 0.1, and roulette with
+    antithetic pairs. RMSE against the exact solution (exp data); work = walk-steps; efficiency =
+    (RMSE^2 x walk-steps) of the plain estimator over that of the option (higher is better)."""
+    import torch
+
+    variants = {"plain": {}, "control_variate": {"control_variate": True}, "antithetic": {"antithetic": True},
+                "roulette_0.1": {"roulette": 0.1}, "roulette_0.1_antithetic": {"roulette": 0.1, "antithetic": True}}
+    out = {}
+    # batched workload
+    rows = {}
+    for name, kw in variants.items():
+        b = W.Batch([{"domain": d, "x": p["X"], "n_walks": p["n_walks"] + (p["n_walks"] & 1), "eps": p["eps"],
+                      "sigma": p["sigma"], "grad": True} for d, p in zip(doms, probs)], seed=seed, **kw)
+        ms, _ = _timed(b.run)
+        st = W.stats_dict(b.stats)
+        ru, rg, rgn = exact_rmse(probs, b.out)
+        rows[name] = {"rmse_u_rel": ru, "rmse_grad_rel_aggregate": rgn, "walk_steps": st["walk_steps"],
+                      "killed": st["killed"], "ms": ms}
+        b.close()
+    for name, r in rows.items():
+        p0 = rows["plain"]
+        r["efficiency_u"] = (p0["rmse_u_rel"] ** 2 * p0["walk_steps"]) / (r["rmse_u_rel"] ** 2 * r["walk_steps"])
+        r["efficiency_grad"] = ((p0["rmse_grad_rel_aggregate"] ** 2 * p0["walk_steps"]) /
+                                (r["rmse_grad_rel_aggregate"] ** 2 * r["walk_steps"]))
+    out["batched_uneven"] = rows
+    # d = 2 check workload (mixed precision, 64 queries x 10^4 walks)
+    w = synth.c1()
+    dom = W.Domain(w["domain"])
+    a = w["domain"]["exp_a"][0]
+    ex = np.exp(w["X"] @ a)
+    rows = {}
+    for name, kw in variants.items():
+        r = dom.grad(w["X"], w["n_walks"], w["eps"], w["sigma"], seed=w["seed"], with_stats=True, **kw)
+        u, g = r["u"].cpu().numpy(), r["grad"].cpu().numpy()
+        st = W.stats_dict(r["stats"])
+        eg = np.linalg.norm(g - a[None, :] * ex[:, None], axis=1)
+        rows[name] = {"rmse_u_rel": float(np.sqrt(np.mean(((u - ex) / ex) ** 2))),
+                      "rmse_grad_rel_aggregate": float(np.sqrt(np.sum(eg ** 2) / np.sum((np.linalg.norm(a) * ex) ** 2))),
+                      "walk_steps": st["walk_steps"], "killed": st["killed"]}
+    for name, r in rows.items():
+        p0 = rows["plain"]
+        r["efficiency_u"] = (p0["rmse_u_rel"] ** 2 * p0["walk_steps"]) / (r["rmse_u_rel"] ** 2 * r["walk_steps"])
+        r["efficiency_grad"] = ((p0["rmse_grad_rel_aggregate"] ** 2 * p0["walk_steps"]) /
+                                (r["rmse_grad_rel_aggregate"] ** 2 * r["walk_steps"]))
+    out["check_2d"] = rows
+    out["note"] = ("efficiency = plain RMSE^2 x walk-steps / option's (higher is better); batched workload with "
+                   "odd walk counts rounded up to even for the antithetic pairs (all variants)")
+    return out
 
 
 def secondary(W, synth, peaks, sms, sm_max):

@@ -279,6 +279,32 @@ wos_status wos_plan_path(wos_domain_t dom, const wos_options *opt, const double 
                          int64_t n_steps, int64_t n_walks, double eps, double sigma, double s_ub,
                          double *path, int32_t *flags, double *grads, void *stream);
 
+/*
+ * Many planner paths in one CUDA graph (the paper's multistart paths, Sec. VI Fig. 5; paths of
+ * uneven d and domains): step i of every path is one batched launch -- each path's gradient
+ * walks are one problem of the persistent walkers' work queues, as in wos_batch_create -- then
+ * every path's step update on the device. A path that reaches its goal runs no more walks.
+ * Path p is the path wos_plan_path gives for the same domain, options and arguments: the same
+ * walks (walk offset opt->walk_offset + i n_walks at step i), the same per-query sums (formed in
+ * the same fixed order) and so the same points, flags and gradients. WOS_MIXED only; domains
+ * with a point set and an impulse source are UNSUPPORTED (as in batches). Synchronous (it
+ * records and replays the graph, then waits for the stream).
+ */
+typedef struct {
+    wos_domain_t domain;
+    const double *x0;   /* d device doubles: the start */
+    int64_t n_walks;    /* gradient walks per step */
+    double eps;
+    double sigma;
+    double s_ub;        /* the step bound of Sec. VII, s = min(s_ub, d_bound / 2) */
+    double *path;       /* (n_steps + 1) x d device doubles (row 0 = x0) */
+    int32_t *flags;     /* n_steps device int32 (as wos_plan_step; 8 after the goal) */
+    double *grads;      /* n_steps x d device doubles or NULL */
+} wos_path_problem;
+
+wos_status wos_plan_paths(const wos_path_problem *paths, int32_t n_paths, int64_t n_steps,
+                          const wos_options *opt, void *stream);
+
 /* ---- backward of u(x; sigma, w) (autograd) --------------------------------------------- */
 
 /*
@@ -307,12 +333,15 @@ typedef struct {
     int64_t *walk_steps; /* n_queries device int64 or NULL: distance evaluations per query */
 } wos_problem;
 
-/* Launch shape of the persistent kernel. A NULL config means "autotuned": the cached best for
+/* Launch shapes of the persistent kernels. A NULL config means "autotuned": the cached best for
  * this device and problem mix if any, else the built-in default. */
 typedef struct {
-    int32_t threads;         /* threads per CTA: 32..768, multiple of 32 */
-    int32_t ctas_per_sm;     /* resident CTAs per SM requested (1..8) */
-    int64_t item_work;       /* target work per queue item, in ball-dimension units */
+    int32_t threads;            /* CUDA-core walker: threads per CTA, 32..768, multiple of 32 */
+    int32_t ctas_per_sm;        /* CUDA-core walker: resident CTAs per SM requested (1..8) */
+    int64_t item_work;          /* CUDA-core walker: target work per queue item (ball-dimension units) */
+    int32_t sphere_ctas_per_sm; /* tensor-core walker: CTAs per SM in its persistent grids (1..4) */
+    int32_t reserved;           /* 0 */
+    int64_t sphere_item_walks;  /* tensor-core walker: walks per queue item (128..2^20, multiple of 128) */
 } wos_batch_config;
 
 /*
@@ -343,10 +372,12 @@ wos_status wos_solve_batch(const wos_problem *probs, int32_t n_problems, const w
                            wos_stats *stats, void *stream);
 
 /*
- * Autotuner: times each candidate launch shape on this batch (CUDA events, after a warm-up
- * run), keeps the fastest in the batch, and appends it to the text cache file cache_path (may
- * be NULL) keyed by device name and problem-mix signature, so later wos_batch_create calls with
- * a NULL config reuse it. best (host) may be NULL. Synchronous.
+ * Autotuner: times candidate launch shapes on this batch (CUDA events, one run each after a
+ * warm-up run) in two rounds -- the CUDA-core walker's shapes (threads, CTAs per SM, item work),
+ * then, with the best of those, the tensor-core walker's (CTAs per SM in {4, 3, 2}, walks per
+ * item in {2048, 4096, 8192}) -- keeps the fastest in the batch, and appends it to the text cache
+ * file cache_path (may be NULL) keyed by device name and problem-mix signature, so later
+ * wos_batch_create calls with a NULL config reuse it. best (host) may be NULL. Synchronous.
  */
 wos_status wos_batch_autotune(wos_batch_t batch, const char *cache_path, wos_batch_config *best);
 

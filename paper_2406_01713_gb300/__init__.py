@@ -17,7 +17,7 @@ def build(force=False, verbose=False):
 
 
 def __getattr__(name):
-    if name in ("Domain", "Batch", "WoSFunction", "backward", "set_autotune_cache", "stats_dict"):
+    if name in ("Domain", "Batch", "WoSFunction", "backward", "set_autotune_cache", "stats_dict", "plan_paths"):
         from . import wos
 
         return getattr(wos, name)

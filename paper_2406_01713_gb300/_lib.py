@@ -67,9 +67,22 @@ class Problem(ctypes.Structure):
     ]
 
 
+class PathProblem(ctypes.Structure):
+    _fields_ = [
+        ("domain", _VP),
+        ("x0", _VP),
+        ("n_walks", ctypes.c_int64),
+        ("eps", ctypes.c_double),
+        ("sigma", ctypes.c_double),
+        ("s_ub", ctypes.c_double),
+        ("path", _VP), ("flags", _VP), ("grads", _VP),
+    ]
+
+
 class BatchConfig(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("item_work", ctypes.c_int64)]
+                ("item_work", ctypes.c_int64), ("sphere_ctas_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("sphere_item_walks", ctypes.c_int64)]
 
 
 # name -> (restype, argtypes); every entry point declared in include/wos.h
@@ -91,6 +104,7 @@ SIGNATURES = {
     "wos_plan_path": (ctypes.c_int, [_VP, ctypes.POINTER(Options), _VP, ctypes.c_int64, ctypes.c_int64,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP, _VP, _VP,
                                      _VP]),
+    "wos_plan_paths": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int64, _VP, _VP]),
     "wos_backward": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                     _VP, _VP, _VP, _VP]),
     "wos_batch_create": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_int32, ctypes.POINTER(Options),

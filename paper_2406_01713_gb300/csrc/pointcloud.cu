@@ -187,6 +187,9 @@ __device__ __forceinline__ bool next_item(const SphereLaunch &L, SphereItem &it)
     if (i >= (unsigned long long)L.n_items) return false;
     if (L.items != nullptr) {
         it = L.items[i];
+        // a planner path that has reached its goal runs no walks
+        const int *dn = L.problems != nullptr ? L.problems[it.problem].P.done : nullptr;
+        if (dn != nullptr && *(volatile const int *)dn != 0) it.j1 = it.j0;
     } else {
         const int64_t total = L.single.P.Q * L.single.P.N;
         it.problem = 0;
@@ -713,23 +716,19 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             }
             if (outcome == 0) {
                 float v[D];
+                // antithetic pairs: the first direction of walk 2m + 1 is the negated one of walk 2m
                 const uint64_t walk = (uint64_t)(P.walk_base + j);
-                if (k == 0) {
-                    direction_f32<D, true>(L.seed, first_direction_walk(walk, P.antithetic), 0u, v);
-                    if (first_direction_negated(walk, P.antithetic)) {
-#pragma unroll
-                        for (int i = 0; i < D; ++i) v[i] = -v[i];
-                    }
-                } else {
-                    direction_f32<D, true>(L.seed, walk, (uint32_t)k, v);
-                }
+                const bool first = k == 0;
+                direction_f32<D, true>(L.seed, first ? first_direction_walk(walk, P.antithetic) : walk, (uint32_t)k, v);
+                const float sgn = first && first_direction_negated(walk, P.antithetic) ? -1.f : 1.f;
                 const float2 tb = table_lookup(P.table, R * P.sqrt_sigma);
                 if (GRAD && k == 0)
                     gfac0 = P.laplace ? ((float)D / R) * __expf(-tb.x) : ((float)D / R) / tb.y;
                 logw += tb.x;
                 dsig = fmaf(-(R * R) * inv2d, tb.y, dsig);
+                const float Rs = sgn * R;
 #pragma unroll
-                for (int i = 0; i < D; ++i) x[i] = fmaf(R, v[i], x[i]);
+                for (int i = 0; i < D; ++i) x[i] = fmaf(Rs, v[i], x[i]);
                 ++k;
                 continue;
             }
@@ -800,10 +799,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             if (GRAD && need_v0) {
                 const uint64_t walk = (uint64_t)(P.walk_base + j);
                 direction_f32<D, true>(L.seed, first_direction_walk(walk, P.antithetic), 0u, v0);
-                if (first_direction_negated(walk, P.antithetic)) {
+                const float sgn = first_direction_negated(walk, P.antithetic) ? -1.f : 1.f;
 #pragma unroll
-                    for (int i = 0; i < D; ++i) v0[i] = -v0[i];
-                }
+                for (int i = 0; i < D; ++i) v0[i] *= sgn;
             }
             const float gt = has_grad ? gfac0 * term : 0.f;
             // control variate: G = alpha(R0)/C(R0), one number per query (every walk writes it)

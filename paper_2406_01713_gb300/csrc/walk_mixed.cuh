@@ -523,16 +523,11 @@ __device__ __forceinline__ void step_walker(const MixedLaunch &L, const MixedPro
     }
     if (outcome == 0) {
         float v[D];
+        // antithetic pairs: the first direction of walk 2m + 1 is the negated one of walk 2m
         const uint64_t walk = (uint64_t)(P.walk_base + (long long)W.j);
-        if (W.k == 0) {
-            direction_f32<D, true>(L.seed, first_direction_walk(walk, P.antithetic), 0u, v);
-            if (first_direction_negated(walk, P.antithetic)) {
-#pragma unroll
-                for (int i = 0; i < D; ++i) v[i] = -v[i];
-            }
-        } else {
-            direction_f32<D, true>(L.seed, walk, (uint32_t)W.k, v);
-        }
+        const bool first = W.k == 0;
+        direction_f32<D, true>(L.seed, first ? first_direction_walk(walk, P.antithetic) : walk, (uint32_t)W.k, v);
+        const float sgn = first && first_direction_negated(walk, P.antithetic) ? -1.f : 1.f;
         const float2 t = table_lookup(P.table, R * P.sqrt_sigma);
         if (P.has_source) source_step<D, GRAD>(P, W, R, t);
         if (GRAD && W.k == 0) {
@@ -541,9 +536,10 @@ __device__ __forceinline__ void step_walker(const MixedLaunch &L, const MixedPro
         }
         W.logw += t.x;
         W.dsig = fmaf(-(R * R) * (1.0f / (2.0f * (float)D)), t.y, W.dsig);
+        const float Rs = sgn * R;
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            const float xn = fmaf(R, v[i], xj(W.x2, i));
+            const float xn = fmaf(Rs, v[i], xj(W.x2, i));
             W.x2[i] = pack2(xn, xn);
         }
         ++W.k;
@@ -569,10 +565,9 @@ __device__ __forceinline__ void step_walker(const MixedLaunch &L, const MixedPro
         if (need_v0) {
             const uint64_t walk = (uint64_t)(P.walk_base + (long long)W.j);
             direction_f32<D, true>(L.seed, first_direction_walk(walk, P.antithetic), 0u, v0);
-            if (first_direction_negated(walk, P.antithetic)) {
+            const float sgn = first_direction_negated(walk, P.antithetic) ? -1.f : 1.f;
 #pragma unroll
-                for (int i = 0; i < D; ++i) v0[i] = -v0[i];
-            }
+            for (int i = 0; i < D; ++i) v0[i] *= sgn;
         }
     }
     // u^(x_1) C(R0): the walk's value without its step-0 source part
@@ -634,6 +629,9 @@ __global__ void __launch_bounds__(MAXT, 1) walk_mixed_kernel(const __grid_consta
                     S.item_problem = I.problem;
                     S.next_walk = (unsigned)I.j0;
                     S.end_walk = (unsigned)I.j1;
+                    // a planner path that has reached its goal runs no walks
+                    const int *dn = L.problems != nullptr ? L.problems[I.problem].done : nullptr;
+                    if (dn != nullptr && *(volatile const int *)dn != 0) S.end_walk = S.next_walk;
                 } else {
                     const long long j0 = it * L.walks_per_item;
                     const long long j1 = j0 + L.walks_per_item;

@@ -1306,8 +1306,10 @@ struct PlanArgs {
     double *path_row;
 };
 
-__global__ void plan_pre_kernel(const __grid_constant__ PlanArgs a) {
-    if (threadIdx.x == 0) {
+// The goal test of a planner step (one thread): a path that has reached its goal skips the step
+// (flag 1 at the step that finds it, 8 after).
+__device__ void plan_pre_decide(const PlanArgs &a) {
+    {
         int skip = 0;
         int32_t f = 0;
         if (*a.done) {
@@ -1339,6 +1341,12 @@ __global__ void plan_pre_kernel(const __grid_constant__ PlanArgs a) {
         }
         *a.skip = skip;
         *a.flag = f;
+    }
+}
+
+__global__ void plan_pre_kernel(const __grid_constant__ PlanArgs a) {
+    if (threadIdx.x == 0) {
+        plan_pre_decide(a);
         *a.cursor = 0ull;
     }
     __syncthreads();
@@ -1404,6 +1412,53 @@ __global__ void plan_post_kernel(const __grid_constant__ PlanArgs a) {
         WOS_CASE(8) WOS_CASE(9) WOS_CASE(10) WOS_CASE(11) WOS_CASE(12)
 #undef WOS_CASE
         default: break;
+    }
+}
+
+// ---- many planner paths in one batch: per-path records of the step kernels ----------------
+struct PathRec {
+    PlanArgs a;                 // flag/grad_row/path_row hold the bases of the path's outputs
+    int32_t *flags;             // n_steps
+    double *grads;              // n_steps x d or nullptr
+    double *path;               // (n_steps + 1) x d
+    int64_t walk_offset;        // global walk index of walk 0 at step 0
+    int64_t *walk_base_mixed;   // the walk base of the path's record in the batch's problem table
+    int64_t *walk_base_sphere;  // ... and in the tensor-core problem table (nullptr if none)
+};
+
+// Step `step` of every path, before its walks: the goal test, and the walk offset of the step
+// (walk_offset + step N, the walks wos_plan_path draws) in the problem tables. One block per path.
+__global__ void paths_pre_kernel(const PathRec *recs, int n, int64_t step) {
+    for (int p = blockIdx.x; p < n; p += gridDim.x) {
+        if (threadIdx.x != 0) continue;
+        const PathRec &R = recs[p];
+        PlanArgs a = R.a;
+        a.flag = R.flags + step;
+        plan_pre_decide(a);
+        const int64_t wb = R.walk_offset + step * a.N;
+        *R.walk_base_mixed = wb;
+        if (R.walk_base_sphere != nullptr) *R.walk_base_sphere = wb;
+    }
+}
+
+// Step `step` of every path, after the reduction of its walks: grad u and the move.
+__global__ void paths_post_kernel(const PathRec *recs, int n, int64_t step) {
+    for (int p = blockIdx.x; p < n; p += gridDim.x) {
+        if (threadIdx.x != 0) continue;
+        const PathRec &R = recs[p];
+        PlanArgs a = R.a;
+        const int d = a.dom.d;
+        a.flag = R.flags + step;
+        a.grad_row = R.grads != nullptr ? R.grads + step * d : nullptr;
+        a.path_row = R.path + (step + 1) * d;
+        switch (d) {
+#define WOS_CASE(DD) \
+    case DD: plan_post_d<DD>(a); break;
+            WOS_CASE(2) WOS_CASE(3) WOS_CASE(4) WOS_CASE(5) WOS_CASE(6) WOS_CASE(7)
+            WOS_CASE(8) WOS_CASE(9) WOS_CASE(10) WOS_CASE(11) WOS_CASE(12)
+#undef WOS_CASE
+            default: break;
+        }
     }
 }
 
@@ -1649,6 +1704,7 @@ extern "C" wos_status wos_debug_weight_table(int32_t d, double z_max, int32_t n,
 // =====================================================================================
 struct wos_batch_s {
     std::vector<wos_problem> probs;
+    std::vector<const int *> done;  // per problem: nonzero -> no walks (finished planner paths)
     Opts o{};
     wos_batch_config cfg{};
     int grad_any = 0;
@@ -1656,9 +1712,23 @@ struct wos_batch_s {
     int grid = 0;
     int64_t n_items = 0, total_q = 0;
     int64_t n_sphere_items = 0;  // items of the tensor-core sphere-set launches
-    void *dev = nullptr;       // problems | items | finalize records | zeroed region
+    void *dev = nullptr;       // problems | items | finalize records | records | zeroed region
     size_t zero_off = 0, zero_bytes = 0;
+    size_t off_sph = 0;        // the tensor-core problem table in dev
+    std::vector<int> sph_index;  // batch problem -> tensor-core problem (-1: CUDA-core walker)
+    std::vector<double *> acc_ptr;                // per problem: its accumulators
+    std::vector<unsigned long long *> cnt_ptr;    // ... and counters
+    int min_walks_per_lane = 8;  // CUDA-core items hold at least this many walks per lane
     wos_stats *d_stats = nullptr;
+    // one run: [memset zeroed region] [tensor-core launches per dimension | CUDA-core walker]
+    // [reduction] [finalize]
+    MixedLaunch L{};
+    std::vector<SphereLaunch> sph;
+    std::vector<int> sph_grid, sph_dims;
+    ReduceArgs ra{};
+    bool any_seg = false;
+    FinalizeArgs fa{};
+    bool no_graph = false;     // planner paths capture their own graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::string signature;
@@ -1708,16 +1778,18 @@ bool cache_lookup(const std::string &path, const std::string &sig, wos_batch_con
     FILE *f = fopen(path.c_str(), "r");
     if (!f) return false;
     char line[512], key[256];
-    int th, ct;
-    long long iw;
+    int th, ct, sct;
+    long long iw, siw;
     double ms;
     bool found = false;
     while (fgets(line, sizeof(line), f) != nullptr) {
         if (line[0] == '#') continue;  // candidate timings
-        if (sscanf(line, "%255s %d %d %lld %lf", key, &th, &ct, &iw, &ms) == 5 && sig == key) {
+        if (sscanf(line, "%255s %d %d %lld %d %lld %lf", key, &th, &ct, &iw, &sct, &siw, &ms) == 7 && sig == key) {
             cfg->threads = th;  // the last entry for a signature wins
             cfg->ctas_per_sm = ct;
             cfg->item_work = iw;
+            cfg->sphere_ctas_per_sm = sct;
+            cfg->sphere_item_walks = siw;
             found = true;
         }
     }
@@ -1734,6 +1806,49 @@ void free_batch_device(wos_batch_s *b) {
     b->dev = nullptr;
 }
 
+// Side streams and events of a capture: one branch per tensor-core launch.
+struct CaptureSide {
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> ev;  // one per branch, then the fork event
+    wos_status init(size_t n) {
+        side.assign(n, nullptr);
+        ev.assign(n + 1, nullptr);
+        for (size_t k = 0; k < n; ++k)
+            if (cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking) != cudaSuccess)
+                return fail(WOS_ERR_CUDA, "stream creation failed");
+        for (size_t k = 0; k < ev.size(); ++k)
+            if (cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) != cudaSuccess)
+                return fail(WOS_ERR_CUDA, "event creation failed");
+        return WOS_OK;
+    }
+    ~CaptureSide() {
+        for (cudaStream_t x : side)
+            if (x) cudaStreamDestroy(x);
+        for (cudaEvent_t x : ev)
+            if (x) cudaEventDestroy(x);
+    }
+};
+
+// Enqueues one run of the batch's walkers and reduction (no finalize) on a capturing stream:
+// zero the accumulators and queue cursors, fork the tensor-core launches onto the side streams,
+// run the CUDA-core walker, join, reduce.
+wos_status enqueue_batch_core(wos_batch_s *b, cudaStream_t cap, CaptureSide &cs) {
+    char *zero = (char *)b->dev + b->zero_off;
+    if (cudaMemsetAsync(zero, 0, b->zero_bytes, cap) != cudaSuccess) return fail(WOS_ERR_CUDA, "memset capture");
+    const size_t ns = b->sph.size();
+    if (ns > 0 && cudaEventRecord(cs.ev.back(), cap) != cudaSuccess) return fail(WOS_ERR_CUDA, "fork event capture");
+    for (size_t k = 0; k < ns; ++k)
+        if (cudaStreamWaitEvent(cs.side[k], cs.ev.back(), 0) != cudaSuccess ||
+            launch_spheres(b->sph[k], b->sph_dims[k], b->grad_any, b->sph_grid[k], cs.side[k]) != cudaSuccess ||
+            cudaEventRecord(cs.ev[k], cs.side[k]) != cudaSuccess)
+            return fail(WOS_ERR_CUDA, "sphere-set kernel capture failed");
+    if (b->n_items > 0 && launch_walk_mixed(b->L, b->grad_any, b->grid, b->cfg.threads, b->smem, cap) != cudaSuccess)
+        return fail(WOS_ERR_CUDA, "walk kernel capture failed");
+    for (size_t k = 0; k < ns; ++k)
+        if (cudaStreamWaitEvent(cap, cs.ev[k], 0) != cudaSuccess) return fail(WOS_ERR_CUDA, "join capture failed");
+    return launch_reduce(b->ra, b->total_q, b->any_seg, cap);
+}
+
 wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     free_batch_device(b);
     wos_batch_config cfg = cfg_in;
@@ -1741,6 +1856,10 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         return fail(WOS_ERR_INVALID_ARG, "threads must be a multiple of 32 in 32..768");
     if (cfg.ctas_per_sm < 1 || cfg.ctas_per_sm > 8) return fail(WOS_ERR_INVALID_ARG, "ctas_per_sm in 1..8");
     if (cfg.item_work < 1) return fail(WOS_ERR_INVALID_ARG, "item_work must be positive");
+    if (cfg.sphere_ctas_per_sm < 1 || cfg.sphere_ctas_per_sm > sphere_ctas_per_sm())
+        return fail(WOS_ERR_INVALID_ARG, "sphere_ctas_per_sm in 1..%d", sphere_ctas_per_sm());
+    if (cfg.sphere_item_walks < 128 || cfg.sphere_item_walks > (1 << 20) || cfg.sphere_item_walks % 128)
+        return fail(WOS_ERR_INVALID_ARG, "sphere_item_walks: a multiple of 128 in 128..2^20");
     const int n = (int)b->probs.size();
     b->grad_any = 0;
     b->smem = 16;
@@ -1796,7 +1915,7 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         const wos_problem &p = b->probs[i];
         const double c = step_cost(*p.domain);
         int64_t wpi = (int64_t)((double)cfg.item_work / c);
-        wpi = std::max<int64_t>(8 * (int64_t)cfg.threads, std::min<int64_t>(1 << 20, wpi));
+        wpi = std::max<int64_t>((int64_t)b->min_walks_per_lane * cfg.threads, std::min<int64_t>(1 << 20, wpi));
         prob_wpi[i] = (wpi + 31) / 32 * 32;
         prob_cost[i] = c * (double)(p.n_queries * p.n_walks);
         walk_base += p.n_queries * p.n_walks;
@@ -1821,10 +1940,10 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     }
     b->n_items = (int64_t)sorted.size();
     b->total_q = q_begin;
-    // sphere-set items: one queue per dimension, problems by decreasing cost, 32 walks per
-    // walker slot per item (a CTA continues into the next item of the same problem without a
-    // pause, so items only matter for the balance at the end)
-    const int64_t kSphereItemWalks = 128 * 32;
+    // sphere-set items: one queue per dimension, problems by decreasing cost, sphere_item_walks
+    // walks per item (a CTA continues into the next item of the same problem without a pause, so
+    // items only matter for the balance at the end)
+    const int64_t kSphereItemWalks = cfg.sphere_item_walks;
     std::vector<int> sph_index(n, -1);
     std::vector<int> sph_problem;  // sphere problem -> batch problem
     std::vector<std::vector<SphereItem>> sph_items(kPointCloudMaxD + 1);
@@ -1887,16 +2006,21 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     std::vector<ReduceRec> rr(n);
     int64_t red_blocks = 0;
     bool any_seg = false;
+    b->acc_ptr.assign(n, nullptr);
+    b->cnt_ptr.assign(n, nullptr);
     for (int i = 0; i < n; ++i) {
         const wos_problem &p = b->probs[i];
         WeightTable tab;
         WOS_TRY(ensure_table(p.domain, p.sigma, &tab));
         double *acc = (double *)(zero + acc_off[i]);
         unsigned long long *cnt = (unsigned long long *)(zero + cnt_off[i]);
+        b->acc_ptr[i] = acc;
+        b->cnt_ptr[i] = cnt;
         mp[i] = make_mixed_problem(p.domain, p.x, p.n_queries, p.n_walks, p.eps, p.sigma,
                                    p.grad != nullptr, b->o.laplace, b->o.cv, walk_base, tab, acc, cnt,
                                    PerWalk{}, reinterpret_cast<float *>(base + rec_off[i]));
         apply_walk_opts(mp[i], b->o);
+        mp[i].done = i < (int)b->done.size() ? b->done[i] : nullptr;
         rr[i] = make_reduce_rec(p.domain->d, p.domain->n_exp, p.grad != nullptr, b->o.cv, p.domain->has_source,
                                 b->o.antithetic, p.n_queries, p.n_walks, reinterpret_cast<float *>(base + rec_off[i]), acc, cnt,
                                 reinterpret_cast<double *>(base + part_off[i]));
@@ -1955,7 +2079,10 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
                             cudaMemcpyHostToDevice));
     }
 
-    MixedLaunch L{};
+    b->off_sph = off_sph;
+    b->sph_index = sph_index;
+    MixedLaunch &L = b->L;
+    L = MixedLaunch{};
     L.problems = (const MixedProblem *)base;
     L.items = (const MixedItem *)(base + off_items);
     L.n_items = b->n_items;
@@ -1964,51 +2091,23 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     L.max_steps = b->o.max_steps;
     L.skip = nullptr;
     b->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * cfg.ctas_per_sm, b->n_items));
-    FinalizeArgs fa{};
+    b->ra = ra;
+    b->any_seg = any_seg;
+    FinalizeArgs &fa = b->fa;
+    fa = FinalizeArgs{};
     fa.recs = (const FinalizeRec *)(base + off_recs);
     fa.n = n;
     fa.total_q = b->total_q;
     fa.stats = b->d_stats;
     fa.status = n_sph > 0 ? sph_status : nullptr;
     fa.shrinks = n_sph > 0 ? sph_shrinks : nullptr;
-
-    // one sphere-set launch per dimension, each on its own stream so that their CTAs and the
-    // CUDA-core walker's share the GPU as each queue drains
-    std::vector<int> sph_dims;
-    for (int dd = 0; dd <= kPointCloudMaxD; ++dd)
-        if (sph_off[dd + 1] > sph_off[dd]) sph_dims.push_back(dd);
-    std::vector<cudaStream_t> side(sph_dims.size(), nullptr);
-    std::vector<cudaEvent_t> ev(sph_dims.size() + 1, nullptr);
-    auto cleanup = [&]() {
-        for (cudaStream_t x : side)
-            if (x) cudaStreamDestroy(x);
-        for (cudaEvent_t x : ev)
-            if (x) cudaEventDestroy(x);
-    };
-    for (size_t k = 0; k < side.size(); ++k)
-        if (cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking) != cudaSuccess) {
-            cleanup();
-            return fail(WOS_ERR_CUDA, "stream creation failed");
-        }
-    for (size_t k = 0; k < ev.size(); ++k)
-        if (cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) != cudaSuccess) {
-            cleanup();
-            return fail(WOS_ERR_CUDA, "event creation failed");
-        }
-
-    cudaStream_t cap = nullptr;
-    WOS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    wos_status st = WOS_OK;
-    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        cudaStreamDestroy(cap);
-        cleanup();
-        return fail(WOS_ERR_CUDA, "batch capture failed to start");
-    }
-    if (cudaMemsetAsync(zero, 0, zero_bytes, cap) != cudaSuccess) st = fail(WOS_ERR_CUDA, "memset capture");
-    if (st == WOS_OK && !sph_dims.empty() && cudaEventRecord(ev.back(), cap) != cudaSuccess)
-        st = fail(WOS_ERR_CUDA, "fork event capture failed");
-    for (size_t k = 0; st == WOS_OK && k < sph_dims.size(); ++k) {
-        const int dd = sph_dims[k];
+    // one sphere-set launch per dimension (run on their own streams so that their CTAs and the
+    // CUDA-core walker's share the GPU as each queue drains)
+    b->sph.clear();
+    b->sph_grid.clear();
+    b->sph_dims.clear();
+    for (int dd = 0; dd <= kPointCloudMaxD; ++dd) {
+        if (sph_off[dd + 1] <= sph_off[dd]) continue;
         SphereLaunch SL;
         memset(&SL, 0, sizeof(SL));
         SL.problems = (const SphereProblem *)(base + off_sph);
@@ -2019,22 +2118,23 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         SL.shrinks = sph_shrinks;
         SL.seed = b->o.seed;
         SL.max_steps = b->o.max_steps;
-        const int grid = (int)std::min<int64_t>((int64_t)sphere_ctas_per_sm() * sms, SL.n_items);
-        if (cudaStreamWaitEvent(side[k], ev.back(), 0) != cudaSuccess ||
-            launch_spheres(SL, dd, b->grad_any, grid, side[k]) != cudaSuccess ||
-            cudaEventRecord(ev[k], side[k]) != cudaSuccess)
-            st = fail(WOS_ERR_CUDA, "sphere-set kernel capture failed");
+        b->sph.push_back(SL);
+        b->sph_grid.push_back((int)std::min<int64_t>((int64_t)cfg.sphere_ctas_per_sm * sms, SL.n_items));
+        b->sph_dims.push_back(dd);
     }
-    if (st == WOS_OK && b->n_items > 0 &&
-        launch_walk_mixed(L, b->grad_any, b->grid, cfg.threads, b->smem, cap) != cudaSuccess)
-        st = fail(WOS_ERR_CUDA, "walk kernel capture failed");
-    for (size_t k = 0; st == WOS_OK && k < sph_dims.size(); ++k)
-        if (cudaStreamWaitEvent(cap, ev[k], 0) != cudaSuccess) st = fail(WOS_ERR_CUDA, "join capture failed");
-    if (st == WOS_OK) st = launch_reduce(ra, b->total_q, any_seg, cap);
-    if (st == WOS_OK) st = launch_finalize(fa, cap);
+    if (b->no_graph) return WOS_OK;
+    CaptureSide side;
+    WOS_TRY(side.init(b->sph.size()));
+    cudaStream_t cap = nullptr;
+    WOS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaStreamDestroy(cap);
+        return fail(WOS_ERR_CUDA, "batch capture failed to start");
+    }
+    wos_status st = enqueue_batch_core(b, cap, side);
+    if (st == WOS_OK) st = launch_finalize(b->fa, cap);
     cudaError_t e = cudaStreamEndCapture(cap, &b->graph);
     cudaStreamDestroy(cap);
-    cleanup();
     if (st != WOS_OK) return st;
     if (e != cudaSuccess) return fail(WOS_ERR_CUDA, "batch capture failed: %s", cudaGetErrorString(e));
     WOS_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
@@ -2044,10 +2144,12 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
 wos_batch_config default_batch_config() {
     // the autotuner's choice for the 256-problem batched workload on GB300 (858 ms per run
     // against 963 ms for 512 threads and item_work 2^26)
-    wos_batch_config c;
+    wos_batch_config c{};
     c.threads = 768;
     c.ctas_per_sm = 1;
     c.item_work = (int64_t)1 << 24;
+    c.sphere_ctas_per_sm = sphere_ctas_per_sm();
+    c.sphere_item_walks = 4096;
     return c;
 }
 
@@ -2143,10 +2245,6 @@ wos_status wos_solve_batch(const wos_problem *probs, int32_t n_problems, const w
 wos_status wos_batch_autotune(wos_batch_t b, const char *cache_path, wos_batch_config *best) {
     if (b == nullptr) return fail(WOS_ERR_INVALID_ARG, "batch is NULL");
     const wos_batch_config start = b->cfg;
-    std::vector<wos_batch_config> cands;
-    for (int th : {512, 768})
-        for (int64_t iw : {(int64_t)1 << 24, (int64_t)1 << 26}) cands.push_back(wos_batch_config{th, 1, iw});
-    cands.push_back(wos_batch_config{256, 2, (int64_t)1 << 26});
     cudaStream_t s;
     WOS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     cudaEvent_t e0, e1;
@@ -2155,20 +2253,20 @@ wos_status wos_batch_autotune(wos_batch_t b, const char *cache_path, wos_batch_c
     double best_ms = 1e300;
     wos_batch_config best_cfg = start;
     std::vector<std::pair<wos_batch_config, float>> timed;
-    std::vector<std::pair<int, int>> seen;  // (threads, effective ctas) x item_work dedup
-    for (const wos_batch_config &c : cands) {
-        if (batch_build(b, c) != WOS_OK) continue;
-        bool dup = false;
-        for (auto &pr : seen)
-            if (pr.first == b->cfg.threads * 4096 + b->cfg.ctas_per_sm &&
-                pr.second == (int)(b->cfg.item_work >> 20))
-                dup = true;
-        if (dup) continue;
-        seen.push_back({b->cfg.threads * 4096 + b->cfg.ctas_per_sm, (int)(b->cfg.item_work >> 20)});
+    auto same = [](const wos_batch_config &a, const wos_batch_config &c) {
+        return a.threads == c.threads && a.ctas_per_sm == c.ctas_per_sm && a.item_work == c.item_work &&
+               a.sphere_ctas_per_sm == c.sphere_ctas_per_sm && a.sphere_item_walks == c.sphere_item_walks;
+    };
+    // one timed run of a candidate (batch_build clamps CTAs per SM to what fits: candidates that
+    // end up equal to one already timed are skipped)
+    auto run = [&](const wos_batch_config &c) -> bool {
+        if (batch_build(b, c) != WOS_OK) return true;
+        for (auto &t : timed)
+            if (same(t.first, b->cfg)) return true;
         cudaEventRecord(e0, s);
         cudaGraphLaunch(b->exec, s);
         cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) return false;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         timed.push_back({b->cfg, ms});
@@ -2176,6 +2274,34 @@ wos_status wos_batch_autotune(wos_batch_t b, const char *cache_path, wos_batch_c
             best_ms = ms;
             best_cfg = b->cfg;
         }
+        return true;
+    };
+    bool ok = true;
+    // round 1: the CUDA-core walker's shapes, the tensor-core walker at its default
+    {
+        wos_batch_config c = default_batch_config();
+        for (int th : {512, 768})
+            for (int64_t iw : {(int64_t)1 << 24, (int64_t)1 << 26}) {
+                c.threads = th;
+                c.ctas_per_sm = 1;
+                c.item_work = iw;
+                if (ok) ok = run(c);
+            }
+        c.threads = 256;
+        c.ctas_per_sm = 2;
+        c.item_work = (int64_t)1 << 26;
+        if (ok) ok = run(c);
+    }
+    // round 2: the tensor-core walker's shapes with the best CUDA-core shape
+    if (ok && b->n_sphere_items > 0) {
+        wos_batch_config c = best_cfg;
+        for (int sct : {4, 3, 2})
+            for (int64_t siw : {(int64_t)2048, (int64_t)4096, (int64_t)8192}) {
+                if (sct > sphere_ctas_per_sm()) continue;
+                c.sphere_ctas_per_sm = sct;
+                c.sphere_item_walks = siw;
+                if (ok) ok = run(c);
+            }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -2187,14 +2313,171 @@ wos_status wos_batch_autotune(wos_batch_t b, const char *cache_path, wos_batch_c
         FILE *f = fopen(cache_path, "a");
         if (f) {
             for (const auto &t : timed)
-                fprintf(f, "# %s %d %d %lld %.4f\n", b->signature.c_str(), t.first.threads,
-                        t.first.ctas_per_sm, (long long)t.first.item_work, t.second);
-            fprintf(f, "%s %d %d %lld %.4f\n", b->signature.c_str(), b->cfg.threads, b->cfg.ctas_per_sm,
-                    (long long)b->cfg.item_work, best_ms);
+                fprintf(f, "# %s %d %d %lld %d %lld %.4f\n", b->signature.c_str(), t.first.threads,
+                        t.first.ctas_per_sm, (long long)t.first.item_work, t.first.sphere_ctas_per_sm,
+                        (long long)t.first.sphere_item_walks, t.second);
+            fprintf(f, "%s %d %d %lld %d %lld %.4f\n", b->signature.c_str(), b->cfg.threads, b->cfg.ctas_per_sm,
+                    (long long)b->cfg.item_work, b->cfg.sphere_ctas_per_sm, (long long)b->cfg.sphere_item_walks,
+                    best_ms);
             fclose(f);
         }
     }
     return WOS_OK;
+}
+
+wos_status wos_plan_paths(const wos_path_problem *paths, int32_t n_paths, int64_t n_steps,
+                          const wos_options *opt, void *stream) {
+    if (n_paths < 0 || n_steps < 0 || (n_paths > 0 && paths == nullptr))
+        return fail(WOS_ERR_INVALID_ARG, "bad path array or n_steps");
+    const Opts o = read_opts(opt);
+    if (opt != nullptr && o.precision != WOS_MIXED)
+        return fail(WOS_ERR_UNSUPPORTED, "wos_plan_paths runs the mixed-precision walkers");
+    if (o.max_steps > (int64_t)kRecKMask) return fail(WOS_ERR_INVALID_ARG, "max_steps must be below 2^28");
+    for (int i = 0; i < n_paths; ++i) {
+        const wos_path_problem &p = paths[i];
+        WOS_TRY(check_common(p.domain, p.x0, 1, p.n_walks, p.eps, p.sigma));
+        if (p.path == nullptr || p.flags == nullptr || !(p.s_ub > 0))
+            return fail(WOS_ERR_INVALID_ARG, "path %d: path/flags NULL or s_ub <= 0", i);
+        WOS_TRY(check_opts(o, p.n_walks));
+        if (p.domain->n_points > 0 && (!p.domain->has_pcd || p.domain->has_source || p.domain->n_balls > 0))
+            return fail(WOS_ERR_UNSUPPORTED, "path %d: this point-set domain runs in FP64 or plain FP32", i);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < n_paths; ++i)
+        WOS_CUDA(cudaMemcpyAsync(paths[i].path, paths[i].x0, sizeof(double) * paths[i].domain->d,
+                                 cudaMemcpyDeviceToDevice, s));
+    if (n_paths == 0 || n_steps == 0) return WOS_OK;
+    // scratch: current points | u | grad u | [done, skip] per path | path records
+    int64_t xs = 0;
+    for (int i = 0; i < n_paths; ++i) xs += paths[i].domain->d;
+    const size_t off_u = align256(sizeof(double) * xs), off_g = off_u + align256(sizeof(double) * n_paths);
+    const size_t off_i = off_g + align256(sizeof(double) * xs);
+    const size_t off_r = off_i + align256(sizeof(int) * 2 * n_paths);
+    const size_t bytes = off_r + sizeof(PathRec) * n_paths;
+    char *scr = nullptr;
+    WOS_CUDA(cudaMalloc(&scr, bytes));
+    double *xc = (double *)scr, *uc = (double *)(scr + off_u), *gc = (double *)(scr + off_g);
+    int *ints = (int *)(scr + off_i);
+    wos_batch_s *b = new (std::nothrow) wos_batch_s();
+    if (b == nullptr) {
+        cudaFree(scr);
+        return fail(WOS_ERR_OOM, "host allocation failed");
+    }
+    wos_status st = WOS_OK;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    do {
+        if (cudaMemsetAsync(ints, 0, sizeof(int) * 2 * n_paths, s) != cudaSuccess) {
+            st = fail(WOS_ERR_CUDA, "memset failed");
+            break;
+        }
+        int64_t ox = 0;
+        for (int i = 0; i < n_paths; ++i) {
+            const wos_path_problem &p = paths[i];
+            const int d = p.domain->d;
+            if (cudaMemcpyAsync(xc + ox, p.x0, sizeof(double) * d, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+                st = fail(WOS_ERR_CUDA, "copy failed");
+                break;
+            }
+            wos_problem q{};
+            q.domain = p.domain;
+            q.x = xc + ox;
+            q.n_queries = 1;
+            q.n_walks = p.n_walks;
+            q.eps = p.eps;
+            q.sigma = p.sigma;
+            q.u = uc + i;
+            q.grad = gc + ox;
+            b->probs.push_back(q);
+            b->done.push_back(ints + 2 * i);
+            ox += d;
+        }
+        if (st != WOS_OK) break;
+        b->o = o;
+        b->no_graph = true;
+        b->min_walks_per_lane = 1;  // planner steps are latency-bound: one walk per lane
+        b->signature = batch_signature(b->probs);
+        wos_batch_config c = default_batch_config();
+        c.threads = 128;
+        c.ctas_per_sm = 4;
+        c.item_work = 1;
+        st = batch_build(b, c);
+        if (st != WOS_OK) break;
+        std::vector<PathRec> recs(n_paths);
+        ox = 0;
+        for (int i = 0; i < n_paths; ++i) {
+            const wos_path_problem &p = paths[i];
+            PathRec &R = recs[i];
+            PlanArgs &a = R.a;
+            a = PlanArgs{};
+            a.dom = p.domain->v64;
+            a.x = xc + ox;
+            a.eps = p.eps;
+            a.s_ub = p.s_ub;
+            a.N = p.n_walks;
+            a.done = ints + 2 * i;
+            a.skip = ints + 2 * i + 1;
+            a.acc = b->acc_ptr[i];
+            a.acc_f32 = 0;
+            a.cv = o.cv;
+            a.src = p.domain->has_source;
+            a.counts = b->cnt_ptr[i];
+            R.flags = p.flags;
+            R.grads = p.grads;
+            R.path = p.path;
+            R.walk_offset = o.walk_offset;
+            R.walk_base_mixed = &(reinterpret_cast<MixedProblem *>(b->dev) + i)->walk_base;
+            R.walk_base_sphere = b->sph_index[i] >= 0
+                                     ? &(reinterpret_cast<SphereProblem *>((char *)b->dev + b->off_sph) +
+                                         b->sph_index[i])->P.walk_base
+                                     : nullptr;
+            ox += p.domain->d;
+        }
+        PathRec *recs_dev = (PathRec *)(scr + off_r);
+        if (cudaMemcpyAsync(recs_dev, recs.data(), sizeof(PathRec) * n_paths, cudaMemcpyHostToDevice, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            st = fail(WOS_ERR_CUDA, "path setup failed");
+            break;
+        }
+        CaptureSide cs;
+        st = cs.init(b->sph.size());
+        if (st != WOS_OK) break;
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            st = fail(WOS_ERR_CUDA, "graph capture failed to start");
+            break;
+        }
+        const unsigned g = (unsigned)std::min(n_paths, 4096);
+        for (int64_t i = 0; i < n_steps && st == WOS_OK; ++i) {
+            paths_pre_kernel<<<g, 32, 0, cap>>>(recs_dev, n_paths, i);
+            if (cudaGetLastError() != cudaSuccess) st = fail(WOS_ERR_CUDA, "pre kernel capture failed");
+            if (st == WOS_OK) st = enqueue_batch_core(b, cap, cs);
+            if (st == WOS_OK) {
+                paths_post_kernel<<<g, 32, 0, cap>>>(recs_dev, n_paths, i);
+                if (cudaGetLastError() != cudaSuccess) st = fail(WOS_ERR_CUDA, "post kernel capture failed");
+            }
+        }
+        cudaError_t e = cudaStreamEndCapture(cap, &graph);
+        if (st != WOS_OK) break;
+        if (e != cudaSuccess) {
+            st = fail(WOS_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+            break;
+        }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = fail(WOS_ERR_CUDA, "paths graph failed: %s", cudaGetErrorString(e));
+    } while (0);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    cudaStreamSynchronize(s);
+    free_batch_device(b);
+    delete b;
+    cudaFree(scr);
+    return st;
 }
 
 }  // extern "C"

@@ -68,6 +68,7 @@ struct MixedProblem {
     unsigned long long *counts;   // Q x kCounters
     float *rec;                   // Q N x rec_words per-walk records (nullable: none written)
     int rec_words;
+    const int *done;              // nullable; nonzero: the problem runs no walks (a finished path)
     double *w_term;               // per-walk outputs (nullable)
     int64_t *w_jumps;
     double *w_grad;

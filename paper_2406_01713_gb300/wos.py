@@ -249,6 +249,39 @@ def backward(gout, grad, du_dsigma=None, du_dw=None):
     return gx, gs[0], gw[:K]
 
 
+def plan_paths(paths, n_steps, seed=0, walk_offset=0, max_steps=10000, control_variate=False, roulette=0.0,
+               antithetic=False):
+    """Many planner paths in one CUDA graph (wos_plan_paths): paths is a list of dicts
+    {domain: Domain, x0, n_walks, eps, sigma, s_ub}; returns [(path, flags, grads)] on the device,
+    each equal to Domain.plan_path with the same arguments (mixed precision)."""
+    L = _lib.load()
+    arr = (_lib.PathProblem * len(paths))()
+    out = []
+    for i, p in enumerate(paths):
+        dom = p["domain"]
+        d = dom.d
+        x0 = _dev_f64(p["x0"]).reshape(-1)
+        f = dict(dtype=torch.float64, device=x0.device)
+        path = torch.empty(n_steps + 1, d, **f)
+        flags = torch.zeros(n_steps, dtype=torch.int32, device=x0.device)
+        grads = torch.zeros(n_steps, d, **f)
+        out.append((path, flags, grads, x0))
+        a = arr[i]
+        a.domain = dom.h
+        a.x0 = x0.data_ptr()
+        a.n_walks = int(p["n_walks"])
+        a.eps = float(p["eps"])
+        a.sigma = float(p["sigma"])
+        a.s_ub = float(p["s_ub"])
+        a.path = path.data_ptr()
+        a.flags = flags.data_ptr()
+        a.grads = grads.data_ptr()
+    o = _opts("mixed", seed, walk_offset, max_steps, control_variate=control_variate, roulette=roulette,
+              antithetic=antithetic)
+    _lib.check(L.wos_plan_paths(arr, len(paths), int(n_steps), ctypes.byref(o), _stream()), "wos_plan_paths")
+    return [(p, f, g) for p, f, g, _ in out]
+
+
 class WoSFunction(torch.autograd.Function):
     """u(x; sigma, w) by Walk on Spheres with a hand-written backward.
 
@@ -336,7 +369,9 @@ class Batch:
                      antithetic=antithetic)
         cfg = None
         if config is not None:
-            cfg = _lib.BatchConfig(int(config["threads"]), int(config["ctas_per_sm"]), int(config["item_work"]))
+            cfg = _lib.BatchConfig(int(config["threads"]), int(config["ctas_per_sm"]), int(config["item_work"]),
+                                   int(config.get("sphere_ctas_per_sm", 4)), 0,
+                                   int(config.get("sphere_item_walks", 4096)))
         h = _VP()
         _lib.check(L.wos_batch_create(arr, len(problems), ctypes.byref(opts),
                                       ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(h)),
@@ -355,13 +390,15 @@ class Batch:
         best = _lib.BatchConfig()
         _lib.check(L.wos_batch_autotune(self.h, cache_path.encode() if cache_path else None,
                                         ctypes.byref(best)), "wos_batch_autotune")
-        return {"threads": best.threads, "ctas_per_sm": best.ctas_per_sm, "item_work": best.item_work}
+        return {"threads": best.threads, "ctas_per_sm": best.ctas_per_sm, "item_work": best.item_work,
+                "sphere_ctas_per_sm": best.sphere_ctas_per_sm, "sphere_item_walks": best.sphere_item_walks}
 
     def config(self):
         L = _lib.load()
         c = _lib.BatchConfig()
         _lib.check(L.wos_batch_get_config(self.h, ctypes.byref(c)), "wos_batch_get_config")
-        return {"threads": c.threads, "ctas_per_sm": c.ctas_per_sm, "item_work": c.item_work}
+        return {"threads": c.threads, "ctas_per_sm": c.ctas_per_sm, "item_work": c.item_work,
+                "sphere_ctas_per_sm": c.sphere_ctas_per_sm, "sphere_item_walks": c.sphere_item_walks}
 
     def close(self):
         if getattr(self, "h", None):

@@ -195,3 +195,33 @@ def test_per_query_sums_equal_per_walk_means(B):
         for k in f:
             assert torch.equal(o[k], f[k]), k
     b.close()
+
+
+def test_autotuner_covers_both_walkers_and_results_do_not_depend_on_the_shape(tmp_path):
+    """The autotuner times the CUDA-core walker's shapes and then the tensor-core walker's (CTAs
+    per SM, walks per item) and caches the best; every launch shape gives the same outputs bit for
+    bit (walks are a function of their indices, the per-query sums are formed in a fixed order)."""
+    probs = []
+    for i, (d, B) in enumerate([(3, 40), (4, 600), (7, 900), (10, 500)]):
+        dom, X, _ = ball_problem(d, B, 6.0, 300 + i, 8)
+        probs.append((W.Domain(dom), X))
+    items = [{"domain": D, "x": X, "n_walks": 1024, "eps": 1e-3, "sigma": 6.0, "grad": True} for D, X in probs]
+    b = W.Batch(items, seed=4, control_variate=True)
+    b.run()
+    torch.cuda.synchronize()
+    ref = [{k: o[k].clone() for k in ("u", "u_se", "grad", "grad_se", "walk_steps")} for o in b.out]
+    cache = tmp_path / "tune.txt"
+    best = b.autotune(str(cache))
+    lines = [l.split() for l in open(cache) if l.startswith("#")]
+    assert len({(int(l[5]), int(l[6])) for l in lines}) >= 4  # sphere CTAs per SM x walks per item
+    assert best["sphere_ctas_per_sm"] in (2, 3, 4) and best["sphere_item_walks"] in (2048, 4096, 8192)
+    for cfg in (best, {"threads": 256, "ctas_per_sm": 2, "item_work": 1 << 22, "sphere_ctas_per_sm": 2,
+                       "sphere_item_walks": 256}):
+        b2 = W.Batch(items, seed=4, control_variate=True, config=cfg)
+        b2.run()
+        torch.cuda.synchronize()
+        for o, r in zip(b2.out, ref):
+            for k in r:
+                assert torch.equal(o[k], r[k]), (cfg, k)
+        b2.close()
+    b.close()
