@@ -144,7 +144,25 @@ typedef struct {
     const double *source_z;     /* d values: an impulse source at this point, or NULL for none */
     double source_q;            /* its strength q (the paper's unit impulse at the goal: 1) */
     int32_t proj_dims;          /* 0 or d: plain domain; 1..d-1: extruded (see below) */
+    int32_t n_links;            /* 0, or 1..d: a planar arm in configuration space (see below) */
+    const double *link_l;       /* n_links link lengths, > 0 */
+    int64_t n_arm_obs;          /* >= 1 with an arm: task-space obstacle points */
+    const double *arm_obs;      /* n_arm_obs x 2, row major */
 } wos_domain_desc;
+
+/*
+ * Planar arm in configuration space (Sec. V, V-A; the RR validation of Sec. VII): the first
+ * n_links coordinates are the joint angles of a planar chain with its base at the origin (link i
+ * along the sum of the angles 0..i, length link_l[i]). The arm's collisions with the task-space
+ * obstacle points are a boundary component known only implicitly; its distance is the safe-ball
+ * radius d_tau(q) / K (Eq. safe_ball), d_tau the task-space distance between the links and the
+ * points and K = sqrt(sum_n (sum_{i<=n} l_i)^2) the Lipschitz constant of the forward
+ * kinematics -- a lower bound of the configuration-space distance, so every sphere stays
+ * collision-free. A walk ending in its eps-shell reads g at its own position (the nearest
+ * boundary point is not known). Component order: goal, balls, points, arm, outer ball, faces.
+ * Mixed precision runs such domains on the CUDA-core walker with at most 32 obstacle points
+ * (UNSUPPORTED beyond, and with a point set).
+ */
 
 /*
  * Impulse source (Sec. IV-A estimator with a source term; the paper's planning problems put a

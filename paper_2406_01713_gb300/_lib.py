@@ -32,6 +32,8 @@ class DomainDesc(ctypes.Structure):
         ("n_exp", ctypes.c_int32), ("exp_w", _PD), ("exp_a", _PD),
         ("source_z", _PD), ("source_q", ctypes.c_double),
         ("proj_dims", ctypes.c_int32),
+        ("n_links", ctypes.c_int32), ("link_l", _PD),
+        ("n_arm_obs", ctypes.c_int64), ("arm_obs", _PD),
     ]
 
 

@@ -38,7 +38,7 @@
 namespace wos {
 
 struct MixedSmem {
-    float geom[4 * kMaxD + kMaxExp + kMaxExp * kMaxD];
+    float geom[geom_count(kMaxD)];
     int problem;
     int item_problem;
     unsigned next_walk;
@@ -121,6 +121,30 @@ __device__ __forceinline__ void other_components(const MixedProblem &P, const fl
             return fmaf(t, t, a);
         });
         goal = sqrtf(s) - P.goal_r;
+    }
+    if (P.n_links > 0) {
+        // planar arm (Sec. V-A): the safe-ball radius d_tau / K, accurate sine and cosine (the
+        // host adds the FP32 error of this evaluation to the jump's shrink)
+        const float *ll = geom + geom_link(D), *ob = geom + geom_arm_obs(D);
+        float px = 0.f, py = 0.f, ang = 0.f, dt = CUDART_INF_F;
+#pragma unroll
+        for (int n = 0; n < D; ++n) {
+            if (n >= P.n_links) break;
+            ang += xj(x2, n);
+            float sn, cs;
+            sincosf(ang, &sn, &cs);
+            const float sx = ll[n] * cs, sy = ll[n] * sn, ss = fmaf(sx, sx, sy * sy);
+            for (int o = 0; o < P.n_arm_obs; ++o) {
+                const float ox = ob[2 * o] - px, oy = ob[2 * o + 1] - py;
+                const float t = fminf(fmaxf(fmaf(ox, sx, oy * sy) / ss, 0.f), 1.f);
+                const float dx = fmaf(-t, sx, ox), dy = fmaf(-t, sy, oy);
+                dt = fminf(dt, sqrtf(fmaf(dx, dx, dy * dy)));
+            }
+            px += sx;
+            py += sy;
+        }
+        const float r = dt * P.arm_inv_K;
+        if (r < other) { other = r; okind = kArm; oidx = 0; }
     }
     if (P.has_outer) {
         const float s = sum_coords<D>(P.proj, [&](int j, float a) {
@@ -651,7 +675,7 @@ __global__ void __launch_bounds__(MAXT, 1) walk_mixed_kernel(const __grid_consta
             const int nfl = ((src->n_balls + kBallBlock - 1) / kBallBlock) * 2 * (d + 2);
             const float4 *bsrc = reinterpret_cast<const float4 *>(src->balls);
             for (int i = threadIdx.x; i < nfl; i += blockDim.x) smem_balls[i] = __ldg(bsrc + i);
-            const int ng = 4 * d + kMaxExp + kMaxExp * d;
+            const int ng = geom_count(d);
             for (int i = threadIdx.x; i < ng; i += blockDim.x) S.geom[i] = __ldg(src->geom + i);
             __syncthreads();
             if (threadIdx.x == 0) S.problem = pi;

@@ -66,6 +66,10 @@ struct wos_domain_s {
     int d = 0, has_box = 0, has_outer = 0, has_goal = 0, n_balls = 0, n_exp = 0;
     int has_source = 0;
     int proj = 0;  // coordinates the components are measured in (d, or fewer when extruded)
+    int n_links = 0;        // planar arm: joints 0..n_links-1 (0: none)
+    int64_t n_arm_obs = 0;  // its task-space obstacle points
+    double arm_K = 0;       // Lipschitz constant of its kinematics
+    std::vector<double> link_l, arm_obs;
     int64_t n_points = 0;
     double outer_r = 0, goal_r = 0, source_q = 0;
     std::vector<double> box_lo, box_hi, outer_c, goal_c, exp_w, exp_a, ball_r, ball_c, points, source_z;
@@ -117,11 +121,16 @@ void layout_view(DomainView<T> &v, T *base, const wos_domain_s &D) {
     v.ball_c = p; p += B * d;
     v.points = p; p += M * d;
     v.source_z = p; p += d;
+    v.n_links = D.n_links;
+    v.n_arm_obs = D.n_arm_obs;
+    v.arm_inv_K = D.n_links > 0 ? (T)(1.0 / D.arm_K) : T(0);
+    v.link_l = p; p += D.n_links;
+    v.arm_obs = p; p += 2 * D.n_arm_obs;
 }
 
 int64_t view_size(const wos_domain_s &D) {
     return 5LL * D.d + D.n_exp + (int64_t)D.n_exp * D.d + D.n_balls + (int64_t)D.n_balls * D.d +
-           D.n_points * D.d;
+           D.n_points * D.d + D.n_links + 2 * D.n_arm_obs;
 }
 
 template <typename T>
@@ -143,10 +152,12 @@ std::vector<T> pack_view(const wos_domain_s &D) {
     put(D.ball_c, (size_t)D.n_balls * d);
     put(D.points, (size_t)D.n_points * d);
     put(D.source_z, d);
+    put(D.link_l, D.n_links);
+    put(D.arm_obs, 2 * D.n_arm_obs);
     return h;
 }
 
-int geom_floats(int d) { return 4 * d + kMaxExp + kMaxExp * d; }
+int geom_floats(int d) { return geom_count(d); }
 
 // Error bounds of the FP32 walkers (rounding unit u = 2^-24):
 //  * shrink: distance |x-c| - r evaluated in FP32 is within u((d+4)/2 (|x|+|c|) + R + |c| + r)
@@ -194,7 +205,22 @@ void error_bounds(wos_domain_s &D) {
     }
     const double C = std::max(cmax, cgo);
     const double R = D.R_max;
-    const double dist_err = ((m + 4) / 2.0) * (L + C) + R + C + rmax + xabs;
+    double dist_err = ((m + 4) / 2.0) * (L + C) + R + C + rmax + xabs;
+    if (D.n_links > 0) {
+        // the arm's safe-ball radius in FP32: the joint angles summed (n u sum |q|), accurate sine
+        // and cosine (2 u), the link end points (n u reach), the projection on each link and its
+        // square root (10 u (|obstacle| + reach)), divided by K
+        const int n = D.n_links;
+        double reach = 0.0, omax = 0.0, qsum = 0.0;
+        for (int i = 0; i < n; ++i) {
+            reach += D.link_l[i];
+            qsum += xabs;
+        }
+        for (int64_t o = 0; o < D.n_arm_obs; ++o)
+            omax = std::max(omax, std::hypot(D.arm_obs[2 * o], D.arm_obs[2 * o + 1]));
+        const double arm = reach * (n * qsum + 2.0 + n) + 10.0 * (omax + reach);
+        dist_err = std::max(dist_err, arm / D.arm_K);
+    }
     const double jump_err = (d + 5) * R + L;
     D.shrink32 = 2.0 * kU32 * (dist_err + jump_err);
     const double P = ccmax + rmax * rmax + 2.0 * rmax * R + 2.0 * L * cmax;
@@ -763,6 +789,9 @@ MixedProblem make_mixed_problem(wos_domain_t dom, const double *x, int64_t Q, in
     P.grad_mode = grad_mode;
     P.has_source = dom->has_source;
     P.proj = dom->proj;
+    P.n_links = dom->n_links;
+    P.n_arm_obs = (int)std::min<int64_t>(dom->n_arm_obs, kMaxArmObs);
+    P.arm_inv_K = dom->n_links > 0 ? (float)(1.0 / dom->arm_K) : 0.f;
     P.src = grad_mode && dom->has_source;
     if (dom->has_source) {
         const int d = dom->d;
@@ -891,6 +920,9 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
     if (o.precision != WOS_MIXED) return fail(WOS_ERR_INVALID_ARG, "unknown precision %d", o.precision);
     if (o.max_steps > (int64_t)kRecKMask)
         return fail(WOS_ERR_INVALID_ARG, "max_steps must be below 2^28 in mixed precision");
+    if (dom->n_links > 0 && (dom->n_points > 0 || dom->n_arm_obs > kMaxArmObs))
+        return fail(WOS_ERR_UNSUPPORTED, "mixed precision runs an arm with at most %d obstacle points and no point set",
+                    kMaxArmObs);
     WeightTable tab;
     WOS_TRY(ensure_table(dom, sigma, &tab));
     if (dom->n_points > 0 || (dom->has_pcd && !o.cuda_core_balls)) {
@@ -1083,6 +1115,16 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
     if (desc->box_lo != nullptr)
         for (int j = 0; j < proj; ++j)
             if (!(desc->box_hi[j] > desc->box_lo[j])) return fail(WOS_ERR_INVALID_ARG, "empty box");
+    if (desc->n_links < 0 || desc->n_links > d)
+        return fail(WOS_ERR_INVALID_ARG, "n_links = %d outside 0..d", desc->n_links);
+    if (desc->n_links > 0) {
+        if (desc->link_l == nullptr || desc->arm_obs == nullptr || desc->n_arm_obs < 1)
+            return fail(WOS_ERR_INVALID_ARG, "an arm needs link lengths and at least one obstacle point");
+        for (int i = 0; i < desc->n_links; ++i)
+            if (!(desc->link_l[i] > 0) || !std::isfinite(desc->link_l[i]))
+                return fail(WOS_ERR_INVALID_ARG, "link %d length <= 0", i);
+        if (proj < d) return fail(WOS_ERR_UNSUPPORTED, "an arm in an extruded domain");
+    }
 
     wos_domain_s *D = new (std::nothrow) wos_domain_s();
     if (D == nullptr) return fail(WOS_ERR_OOM, "host allocation failed");
@@ -1112,6 +1154,18 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
     copy(D->ball_c, desc->ball_c, (size_t)desc->n_balls * d);
     copy(D->points, desc->points, (size_t)desc->n_points * d);
     copy(D->source_z, desc->source_z, d);
+    D->n_links = desc->n_links;
+    D->n_arm_obs = desc->n_links > 0 ? desc->n_arm_obs : 0;
+    copy(D->link_l, desc->link_l, D->n_links);
+    copy(D->arm_obs, desc->arm_obs, (size_t)(2 * D->n_arm_obs));
+    if (D->n_links > 0) {
+        double reach = 0.0, k2 = 0.0;  // K = sqrt(sum_n (sum_{i<=n} l_i)^2), Sec. V-A
+        for (int i = 0; i < D->n_links; ++i) {
+            reach += D->link_l[i];
+            k2 += reach * reach;
+        }
+        D->arm_K = std::sqrt(k2);
+    }
     // an extruded domain's box has no faces in the free coordinates: far away, never nearest
     for (int j = proj; j < d; ++j) {
         D->box_lo[j] = -1.0e30;
@@ -1165,6 +1219,11 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
         hg[4 * d + k] = (float)D->exp_w[k];
         for (int j = 0; j < d; ++j) hg[4 * d + kMaxExp + k * d + j] = (float)D->exp_a[(size_t)k * d + j];
     }
+    for (int i = 0; i < D->n_links; ++i) hg[geom_link(d) + i] = (float)D->link_l[i];
+    for (int64_t o = 0; o < std::min<int64_t>(D->n_arm_obs, kMaxArmObs); ++o) {
+        hg[geom_arm_obs(d) + 2 * o] = (float)D->arm_obs[2 * o];
+        hg[geom_arm_obs(d) + 2 * o + 1] = (float)D->arm_obs[2 * o + 1];
+    }
     cudaError_t e = cudaMalloc(&D->f64, sizeof(double) * (size_t)nv);
     if (e == cudaSuccess) e = cudaMalloc(&D->f32, sizeof(float) * (size_t)nv);
     if (e == cudaSuccess) e = cudaMalloc(&D->balls_mixed, sizeof(float) * hb.size());
@@ -1186,7 +1245,7 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
     // domains with an impulse source stay on the CUDA-core walker (the sphere-set walker has no
     // source term)
     const bool sphere_balls = D->n_points == 0 && D->n_balls >= sphere_min_balls(d) && d <= kPointCloudMaxD &&
-                              !D->has_source && D->proj == d;
+                              !D->has_source && D->proj == d && D->n_links == 0;
     if ((D->n_points > 0 && d <= kPointCloudMaxD) || sphere_balls) {
         e = sphere_balls ? pointcloud_prepare(D->ball_c.data(), D->ball_r.data(), D->n_balls, d, &D->pcd)
                          : pointcloud_prepare(D->points.data(), nullptr, D->n_points, d, &D->pcd);
@@ -1873,6 +1932,9 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
             return fail(WOS_ERR_UNSUPPORTED, "problem %d: mixed-precision point sets need d <= %d", i, kPointCloudMaxD);
         if (p.domain->n_points > 0 && p.domain->n_balls > 0)
             return fail(WOS_ERR_UNSUPPORTED, "problem %d: a domain with both balls and points", i);
+        if (p.domain->n_links > 0 && (p.domain->n_points > 0 || p.domain->n_arm_obs > kMaxArmObs))
+            return fail(WOS_ERR_UNSUPPORTED, "problem %d: an arm with a point set or over %d obstacle points", i,
+                        kMaxArmObs);
         if (p.domain->n_points > 0 && p.domain->has_source)
             return fail(WOS_ERR_UNSUPPORTED, "problem %d: a point set with an impulse source", i);
         tensor[i] = p.domain->has_pcd && (p.domain->n_points > 0 || !b->o.cuda_core_balls);

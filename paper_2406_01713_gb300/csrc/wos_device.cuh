@@ -15,9 +15,10 @@ constexpr int kMaxD = WOS_MAX_D;
 constexpr int kMaxExp = WOS_MAX_EXP;
 constexpr int kTableNodes = 8192;  // weight-table nodes per dimension (linear interpolation)
 
-// Component kinds, in the tie-break order of the distance query:
-// goal, balls, points, outer ball, box faces (lo_0, hi_0, lo_1, ...).
-enum Kind : int { kGoal = 0, kBall = 1, kPoint = 2, kOuter = 3, kFace = 4 };
+// Component kinds. Tie-break order of the distance query: goal, balls, points, arm, outer ball,
+// box faces (lo_0, hi_0, lo_1, ...).
+enum Kind : int { kGoal = 0, kBall = 1, kPoint = 2, kOuter = 3, kFace = 4, kArm = 5 };
+constexpr int kMaxArmObs = 32;  // task-space obstacle points of an arm in the mixed walker
 
 // ------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32 -> 64-bit
@@ -194,6 +195,11 @@ struct DomainView {
     const T *points;                               // M x d
     const T *exp_w, *exp_a;                        // K, K x d
     const T *source_z;                             // d (impulse source; has_source)
+    int n_links;                                   // planar arm: joints 0..n_links-1 (0: none)
+    int64_t n_arm_obs;
+    T arm_inv_K;                                   // 1 / Lipschitz constant of the kinematics
+    const T *link_l;                               // n_links
+    const T *arm_obs;                              // n_arm_obs x 2 (task space)
 };
 
 // Per-query accumulator fields: [sum u, sum u^2, sum du/dsigma, sum grad (d), sum grad^2 (d),

@@ -28,8 +28,42 @@ __device__ __forceinline__ T norm_diff(const T (&x)[D], const T *c, int m) {
     return sqrt(s);
 }
 
-// Distance to the boundary (minimum over components, strict '<' keeps the lowest id); an
-// extruded domain measures every component in its first dm.proj coordinates.
+template <typename T>
+__device__ __forceinline__ void sincos_t(T a, T *s, T *c) {
+    if constexpr (sizeof(T) == 8) sincos(a, s, c);
+    else sincosf(a, s, c);
+}
+
+// Planar arm (Sec. V-A): joint angles x_0..x_{n-1} summed along the chain, base at the origin;
+// d_tau = the smallest task-space distance between a link (segment) and an obstacle point. The
+// returned safe-ball radius d_tau / K underestimates the configuration-space distance.
+template <typename T, int D>
+__device__ __forceinline__ T arm_distance(const DomainView<T> &dm, const T (&x)[D]) {
+    T px = T(0), py = T(0), ang = T(0), best = inf_of<T>();
+#pragma unroll
+    for (int n = 0; n < D; ++n) {
+        if (n >= dm.n_links) break;
+        ang += x[n];
+        T sn, cs;
+        sincos_t<T>(ang, &sn, &cs);
+        const T sx = dm.link_l[n] * cs, sy = dm.link_l[n] * sn, ss = sx * sx + sy * sy;
+        for (int64_t o = 0; o < dm.n_arm_obs; ++o) {
+            const T ox = dm.arm_obs[2 * o] - px, oy = dm.arm_obs[2 * o + 1] - py;
+            T t = ss > T(0) ? (ox * sx + oy * sy) / ss : T(0);
+            t = t < T(0) ? T(0) : (t > T(1) ? T(1) : t);
+            const T dx = ox - t * sx, dy = oy - t * sy;
+            const T r = sqrt(dx * dx + dy * dy);
+            if (r < best) best = r;
+        }
+        px += sx;
+        py += sy;
+    }
+    return best * dm.arm_inv_K;
+}
+
+// Distance to the boundary (minimum over components, strict '<' keeps the first in the order
+// goal, balls, points, arm, outer ball, faces); an extruded domain measures every component in
+// its first dm.proj coordinates.
 template <typename T, int D>
 __device__ __forceinline__ T distance(const DomainView<T> &dm, const T (&x)[D], int &kind, int64_t &idx) {
     const int m = dm.proj;
@@ -48,6 +82,10 @@ __device__ __forceinline__ T distance(const DomainView<T> &dm, const T (&x)[D], 
         const T r = norm_diff<T, D>(x, dm.points + i * D, m);
         if (r < best) { best = r; kind = kPoint; idx = i; }
     }
+    if (dm.n_links > 0) {
+        const T r = arm_distance<T, D>(dm, x);
+        if (r < best) { best = r; kind = kArm; idx = 0; }
+    }
     if (dm.has_outer) {
         const T r = dm.outer_r - norm_diff<T, D>(x, dm.outer_c, m);
         if (r < best) { best = r; kind = kOuter; idx = 0; }
@@ -65,7 +103,8 @@ __device__ __forceinline__ T distance(const DomainView<T> &dm, const T (&x)[D], 
     return best;
 }
 
-// g at the closest boundary point xbar (Fig. 2); e[k] = exp(a_k . xbar) for exp data.
+// g at the closest boundary point xbar (Fig. 2; an arm's walk reads g at its own position);
+// e[k] = exp(a_k . xbar) for exp data.
 template <typename T, int D>
 __device__ __forceinline__ T boundary_value(const DomainView<T> &dm, const T (&x)[D], int kind, int64_t idx,
                             T (&e)[kMaxExp]) {

@@ -46,6 +46,8 @@ struct MixedProblem {
     int src;       // impulse source in gradient walks: store its per-query fields
     int has_source;
     int proj;      // components measured in coordinates 0..proj-1 (= d unless extruded)
+    int n_links, n_arm_obs;  // planar arm (geom holds the link lengths and obstacle points)
+    float arm_inv_K;         // 1 / Lipschitz constant of its kinematics
     int antithetic;        // walk pairs (2m, 2m+1) with opposite first directions
     float roulette_w;      // > 0: Russian roulette on weights below it
     float log_roulette_w;  // its logarithm (the walkers keep log weights)
@@ -60,7 +62,7 @@ struct MixedProblem {
     int64_t Q, N;
     int64_t walk_base;            // global walk index of walk 0 of query 0
     const float *balls;           // packed ball records (see walk_mixed.cu)
-    const float *geom;            // box lo[d], box hi[d], goal c[d], outer c[d], exp w[K], exp a[K*d]
+    const float *geom;            // geom_count(d) floats, see geom_count
     const double *x;              // Q x d queries
     WeightTable table;
     double *acc;                  // Q x nf FP64 sums (the walkers store only the per-query G and
@@ -107,6 +109,13 @@ constexpr unsigned kRecKMask = 0x0fffffffu;  // jumps per walk stay below 2^28
 constexpr int kRecOutcomeShift = 28;
 constexpr unsigned kRecOutcomeMask = 7u;
 constexpr unsigned kRecHasV0 = 0x80000000u;
+
+// Domain geometry of the mixed walkers in shared memory: box lo [d], box hi [d], goal c [d],
+// outer c [d], exp w [kMaxExp], exp a [kMaxExp x d], arm link lengths [d], arm obstacle points
+// [kMaxArmObs x 2].
+__host__ __device__ constexpr int geom_count(int d) { return 4 * d + kMaxExp + kMaxExp * d + d + 2 * kMaxArmObs; }
+__host__ __device__ constexpr int geom_link(int d) { return 4 * d + kMaxExp + kMaxExp * d; }
+__host__ __device__ constexpr int geom_arm_obs(int d) { return 5 * d + kMaxExp + kMaxExp * d; }
 
 // Floats per packed ball record for dimension d.
 __host__ __device__ constexpr int ball_record_floats(int d) { return d + 2; }

@@ -108,6 +108,13 @@ class Domain:
         self.has_source = dom.get("source_z") is not None
         # extruded domain: components measured in the first proj_dims coordinates only
         s.proj_dims = int(dom.get("proj_dims", 0))
+        if dom.get("link_l") is not None:  # planar arm in configuration space (Sec. V-A)
+            ll = arr("link_l", (-1,))
+            s.n_links = ll.shape[0]
+            s.link_l = p(ll)
+            ob = arr("arm_obs", (-1, 2))
+            s.n_arm_obs = ob.shape[0]
+            s.arm_obs = p(ob)
         self.n_exp = int(s.n_exp)
         self.n_balls = int(s.n_balls)
         self.n_points = int(s.n_points)
