@@ -797,6 +797,28 @@ def variance_reduction(W, synth, doms, probs, seed):
     return out
 
 
+def rr_validation(W, synth):
+    """The RR validation (Sec. VII, Table I): paths from q_start toward the unit impulse at q_goal
+    with 10^5 walks per step, s = min(0.1, d_bound/2), eps = 0.02, for c = 0 and 5, with the
+    Lipschitz arm distance (Sec. V-A; CUDA-core walker) and with the 200 closed-form IK collision
+    configurations (a point set: tensor-core walker), mixed precision. Path lengths in joint
+    space (the paper's 4.5 for c = 0 and 3.8 for c = 5 come from its own link lengths and joint
+    limits, shown only in figures)."""
+    out = {}
+    for method, precision in (("lipschitz", "mixed"), ("ik", "mixed")):
+        for c in synth.RR_TABLE_I["c"]:
+            w = synth.rr_arm(c, method=method)
+            dom = W.Domain(w["domain"])
+            ms, (path, flags, _) = _timed(lambda: dom.plan_path(w["start"], 300, w["n_walks"], w["eps"], w["sigma"],
+                                                                w["s_ub"], precision=precision, seed=w["seed"]))
+            length, hit = _path_length(path, flags)
+            f = flags.cpu().numpy()
+            out["%s_c%g" % (method, c)] = {"path_length": length, "reached_goal_at_step": hit, "ms": ms,
+                                           "precision": precision, "no_signal_steps": int((f == 2).sum())}
+    out["note"] = "joint-space path lengths; link lengths 1, 1 and joint limits [0, -pi]..[3pi/2, pi] read from the figures"
+    return out
+
+
 def secondary(W, synth, peaks, sms, sm_max):
     """Measurements of the other workloads (not the headline), each with the roofline of its
     dominant kernel: algorithmic flops per walk-step from the method (B(2d+3) + 4d for balls,
@@ -837,6 +859,10 @@ def secondary(W, synth, peaks, sms, sm_max):
         out["paper_sweeps"] = paper_sweeps(W, synth)
     except Exception as e:  # recorded, so that the other side measurements are kept
         out["paper_sweeps"] = {"error": "%s: %s" % (type(e).__name__, e)}
+    try:
+        out["rr_validation"] = rr_validation(W, synth)
+    except Exception as e:
+        out["rr_validation"] = {"error": "%s: %s" % (type(e).__name__, e)}
     # differentiable d=6: forward + backward, 4096 queries x 2048 walks
     w = synth.c5()
     dom = W.Domain(w["domain"])

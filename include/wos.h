@@ -173,8 +173,8 @@ typedef struct {
  * times the walk's weight so far, G_B the Green's function of that ball with zero boundary
  * values (Yukawa potential minus its image part; logarithm / power laws at sigma = 0); the
  * first-sphere gradient adds q grad_x G_B(x_0, source_z). du_dsigma is NaN for such domains
- * (its source part is not estimated); du_dw is unaffected. Mixed precision runs these domains
- * on the CUDA-core walker (ball sets) and rejects point sets.
+ * (its source part is not estimated); du_dw is unaffected. Every walker has the source term
+ * (the tensor-core sphere-set walker too: point sets and large ball sets).
  */
 
 /*
@@ -304,8 +304,7 @@ wos_status wos_plan_path(wos_domain_t dom, const wos_options *opt, const double 
  * every path's step update on the device. A path that reaches its goal runs no more walks.
  * Path p is the path wos_plan_path gives for the same domain, options and arguments: the same
  * walks (walk offset opt->walk_offset + i n_walks at step i), the same per-query sums (formed in
- * the same fixed order) and so the same points, flags and gradients. WOS_MIXED only; domains
- * with a point set and an impulse source are UNSUPPORTED (as in batches). Synchronous (it
+ * the same fixed order) and so the same points, flags and gradients. WOS_MIXED only. Synchronous (it
  * records and replays the graph, then waits for the stream).
  */
 typedef struct {

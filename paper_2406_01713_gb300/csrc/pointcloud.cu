@@ -288,6 +288,29 @@ __device__ __forceinline__ void write_row(unsigned char *A, int r, const float (
     }
 }
 
+// Impulse source (Sec. IV-A source term) in the ball B(x_k, R) of a walker at distance r from
+// the source: returns q G_B(x_k, z) times the weight so far; at step 0 of a gradient walk it also
+// stores the query's step-0 value and the source part of its gradient, q grad_x G_B(x_0, z)
+// (x_0 is the query point; every walk of the query writes the same). Not inlined, scalar
+// arguments: walkers without a source keep their registers, and the position never needs local
+// memory.
+template <int D>
+__device__ __noinline__ float sphere_source(const MixedProblem &P, long long q, int k, float r, float R, float2 tR,
+                                            float logw) {
+    float G, F;
+    source_green_f32<D>(P, r, R, tR, G, F);
+    const float c = P.source_q * expf(logw) * G;
+    if (k == 0 && P.src) {
+        double *sp = P.acc + q * acc_fields(D, P.n_exp, P.cv, 1) + src_field(D, P.n_exp, P.cv);
+        sp[0] = (double)c;
+        for (int i = 0; i < D; ++i) {
+            const float x0 = (float)P.x[q * D + i];
+            sp[1 + i] = (double)(P.source_q * F * (P.source_z[i] - x0) / r);
+        }
+    }
+    return c;
+}
+
 template <int D, bool GRAD>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __grid_constant__ SphereLaunch L) {
     using G = Geo<contraction_k(D)>;
@@ -430,6 +453,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
 #pragma unroll
         for (int i = 0; i < D; ++i) x[i] = 0.f;
         float logw = 0.f, dsig = 0.f, gfac0 = 0.f;
+        float src = 0.f, src0 = 0.f;  // impulse source: contributions so far, and the step-0 one
         int k = 0;
         long long j = -1, q = 0;
         bool active = false;
@@ -452,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                         q = j / P.N;
 #pragma unroll
                         for (int i = 0; i < D; ++i) x[i] = (float)__ldg(P.x + q * D + i);
-                        logw = dsig = gfac0 = 0.f;
+                        logw = dsig = gfac0 = src = src0 = 0.f;
                         k = 0;
                     }
                 }
@@ -722,6 +746,20 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                 direction_f32<D, true>(L.seed, first ? first_direction_walk(walk, P.antithetic) : walk, (uint32_t)k, v);
                 const float sgn = first && first_direction_negated(walk, P.antithetic) ? -1.f : 1.f;
                 const float2 tb = table_lookup(P.table, R * P.sqrt_sigma);
+                if (P.has_source) {
+                    // the ball B(x_k, R) contains the source: q G_B(x_k, z) times the weight so far; at
+                    // step 0 of a gradient walk also the query's step-0 value and the source part of
+                    // the gradient, q grad_x G_B(x_0, z) (every walk of the query writes the same)
+                    float rr = 0.f;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) rr = fmaf(P.source_z[i] - x[i], P.source_z[i] - x[i], rr);
+                    const float rz = sqrtf(rr);
+                    if (rz > 0.f && rz < R) {
+                        const float c = sphere_source<D>(P, q, k, rz, R, tb, logw);
+                        src += c;
+                        if (k == 0) src0 = c;
+                    }
+                }
                 if (GRAD && k == 0)
                     gfac0 = P.laplace ? ((float)D / R) * __expf(-tb.x) : ((float)D / R) / tb.y;
                 logw += tb.x;
@@ -786,16 +824,18 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                 } else {
                     term = kind == kGoal ? expf(logw) : 0.f;
                 }
+                term += src;
             }
+            if (outcome == 4) term = src;  // ended by the roulette: the source contributions so far
             // (a value-only problem in a gradient launch has no gradient terms)
-            const bool has_grad = GRAD && P.grad_mode && outcome == 1 && k > 0;
+            const bool has_grad = GRAD && P.grad_mode && (outcome == 1 || outcome == 4) && k > 0;
             const bool cv_walk = GRAD && P.cv && k > 0 && outcome != 3;  // capped walks count too
             float v0[D];
 #pragma unroll
             for (int i = 0; i < D; ++i) v0[i] = 0.f;
             // the first direction: for the gradient terms, and for every walk that took its first
             // sphere when the control variate sums sum v0 and sum v0^2
-            const bool need_v0 = (has_grad && term != 0.f) || cv_walk;
+            const bool need_v0 = (has_grad && (term != 0.f || src0 != 0.f)) || cv_walk;
             if (GRAD && need_v0) {
                 const uint64_t walk = (uint64_t)(P.walk_base + j);
                 direction_f32<D, true>(L.seed, first_direction_walk(walk, P.antithetic), 0u, v0);
@@ -803,17 +843,21 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
 #pragma unroll
                 for (int i = 0; i < D; ++i) v0[i] *= sgn;
             }
-            const float gt = has_grad ? gfac0 * term : 0.f;
+            // u^(x_1) C(R0): the walk's value without its step-0 source part
+            const float gt = has_grad ? gfac0 * (term - src0) : 0.f;
             // control variate: G = alpha(R0)/C(R0), one number per query (every walk writes it)
             if (cv_walk && gfac0 != 0.f)
                 P.acc[q * acc_fields(D, P.n_exp, P.cv, P.src) + cv_field(D, P.n_exp) + 3 * D] = (double)gfac0;
             write_record<D>(P, j, outcome, k, term, dsig, gt, GRAD && need_v0, v0, e);
             if (P.w_term != nullptr) P.w_term[j] = outcome == 3 ? (double)CUDART_NAN : (double)term;
             if (P.w_jumps != nullptr) P.w_jumps[j] = k;
-            if (P.w_dsigma != nullptr) P.w_dsigma[j] = (double)(term * dsig);
-            if (P.w_grad != nullptr)
+            if (P.w_dsigma != nullptr) P.w_dsigma[j] = P.has_source ? (double)CUDART_NAN : (double)(term * dsig);
+            if (P.w_grad != nullptr) {
+                // with a source, the per-query source part of the gradient (stored at step 0)
+                const double *sp = P.src ? P.acc + q * acc_fields(D, P.n_exp, P.cv, 1) + src_field(D, P.n_exp, P.cv) : nullptr;
 #pragma unroll
-                for (int i = 0; i < D; ++i) P.w_grad[j * D + i] = (double)(gt * v0[i]);
+                for (int i = 0; i < D; ++i) P.w_grad[j * D + i] = (double)(gt * v0[i]) + (sp != nullptr ? sp[1 + i] : 0.0);
+            }
             active = false;
         }
     }

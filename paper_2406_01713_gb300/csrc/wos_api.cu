@@ -930,8 +930,6 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
             return fail(WOS_ERR_UNSUPPORTED, "mixed-precision point clouds need d <= %d", kPointCloudMaxD);
         if (dom->n_balls > 0 && dom->n_points > 0)
             return fail(WOS_ERR_UNSUPPORTED, "a domain with both balls and points runs in FP64 or plain FP32");
-        if (dom->has_source)
-            return fail(WOS_ERR_UNSUPPORTED, "a point set with an impulse source runs in FP64 or plain FP32");
         MixedProblem P = make_mixed_problem(dom, x, Q, N, eps, sigma, grad_mode, o.laplace, cv, o.walk_offset, tab,
                                             (double *)sc.acc, sc.counts, pw, sc.rec);
         apply_walk_opts(P, o);
@@ -1242,10 +1240,9 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
     }
     layout_view<double>(D->v64, D->f64, *D);
     layout_view<float>(D->v32, D->f32, *D);
-    // domains with an impulse source stay on the CUDA-core walker (the sphere-set walker has no
-    // source term)
+    // large ball sets run on the tensor-core sphere-set walker (not extruded domains or arms)
     const bool sphere_balls = D->n_points == 0 && D->n_balls >= sphere_min_balls(d) && d <= kPointCloudMaxD &&
-                              !D->has_source && D->proj == d && D->n_links == 0;
+                              D->proj == d && D->n_links == 0;
     if ((D->n_points > 0 && d <= kPointCloudMaxD) || sphere_balls) {
         e = sphere_balls ? pointcloud_prepare(D->ball_c.data(), D->ball_r.data(), D->n_balls, d, &D->pcd)
                          : pointcloud_prepare(D->points.data(), nullptr, D->n_points, d, &D->pcd);
@@ -1935,8 +1932,6 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         if (p.domain->n_links > 0 && (p.domain->n_points > 0 || p.domain->n_arm_obs > kMaxArmObs))
             return fail(WOS_ERR_UNSUPPORTED, "problem %d: an arm with a point set or over %d obstacle points", i,
                         kMaxArmObs);
-        if (p.domain->n_points > 0 && p.domain->has_source)
-            return fail(WOS_ERR_UNSUPPORTED, "problem %d: a point set with an impulse source", i);
         tensor[i] = p.domain->has_pcd && (p.domain->n_points > 0 || !b->o.cuda_core_balls);
         if (!tensor[i]) b->smem = std::max(b->smem, mixed_smem_bytes(*p.domain));
     }
@@ -2401,7 +2396,7 @@ wos_status wos_plan_paths(const wos_path_problem *paths, int32_t n_paths, int64_
         if (p.path == nullptr || p.flags == nullptr || !(p.s_ub > 0))
             return fail(WOS_ERR_INVALID_ARG, "path %d: path/flags NULL or s_ub <= 0", i);
         WOS_TRY(check_opts(o, p.n_walks));
-        if (p.domain->n_points > 0 && (!p.domain->has_pcd || p.domain->has_source || p.domain->n_balls > 0))
+        if (p.domain->n_points > 0 && (!p.domain->has_pcd || p.domain->n_balls > 0))
             return fail(WOS_ERR_UNSUPPORTED, "path %d: this point-set domain runs in FP64 or plain FP32", i);
     }
     cudaStream_t s = (cudaStream_t)stream;

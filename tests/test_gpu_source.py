@@ -159,3 +159,41 @@ def test_planner_reaches_the_source_goal():
     assert np.all(np.linalg.norm(p, axis=1) < 10.0)
     for c, r in zip(dom["ball_c"], dom["ball_r"]):
         assert np.all(np.linalg.norm(p - c[None, :], axis=1) > r)
+
+
+@pytest.mark.parametrize("kind", ["points", "balls"])
+@pytest.mark.parametrize("cv", [False, True])
+def test_tensor_core_walker_with_a_source(kind, cv):
+    """The impulse source on the tensor-core sphere-set walker (mixed precision): a point set
+    (Sec. VII-A) and a large ball set, against the oracle on the same walks; the per-walk records
+    carry the source part of the gradient."""
+    rng = np.random.default_rng(31)
+    d = 3
+    z = np.array([0.7, 0.5, 0.5])
+    if kind == "points":
+        t = rng.uniform(0, 2 * np.pi, 800)
+        p = np.stack([0.3 + 0.15 * np.cos(t), 0.5 + 0.15 * np.sin(t), rng.uniform(0.1, 0.9, 800)], 1)
+        dom = {"d": d, "box_lo": np.zeros(d), "box_hi": np.ones(d), "points": p, "source_z": z, "source_q": 1.0}
+        X = np.array([[0.6, 0.3, 0.4], [0.5, 0.7, 0.6], [0.85, 0.5, 0.2], [0.3, 0.5, 0.5]])
+    else:
+        c = rng.uniform(0.0, 1.0, (600, d))
+        r = np.exp(rng.uniform(np.log(0.004), np.log(0.02), 600))
+        keep = np.linalg.norm(c - z[None, :], axis=1) > r + 0.05
+        dom = {"d": d, "box_lo": np.zeros(d), "box_hi": np.ones(d), "ball_c": c[keep], "ball_r": r[keep],
+               "source_z": z, "source_q": 1.0}
+        X = synth._free_points(rng, 6, np.zeros(d), np.ones(d), c[keep], r[keep], 0.02,
+                               extra=lambda x: np.linalg.norm(x - z[None, :], axis=1) > 0.1)
+    D = W.Domain(dom)
+    assert D.info()["tensor_sphere_set"]
+    sigma, N = 4.0, 8000
+    ref = oracle.solve(dom, X, N, 2e-3, sigma, 13, grad=True, control_variate=cv)
+    got = D.grad(X, N, 2e-3, sigma, seed=13, control_variate=cv)
+    assert np.all(within(np_(got["u"]), np_(got["u_se"]), ref["u"], ref["u_se"]))
+    assert np.all(within(np_(got["grad"]), np_(got["grad_se"]), ref["grad"], ref["grad_se"]))
+    assert np.all(np.isnan(np_(got["du_dsigma"])))
+    if not cv:
+        per = D.walks(X[:2], 512, 2e-3, sigma, grad_mode=True, seed=13)
+        ro = oracle.solve(dom, X[:2], 512, 2e-3, sigma, 13, grad=True, per_walk=True)
+        # the per-walk gradients include the (deterministic) source part q grad_x G_B(x0, z)
+        assert np.allclose(np_(per["grad"]).mean(1), ro["walk_grad"].mean(1),
+                           atol=4 * ro["grad_se"].max() + 1e-4)
