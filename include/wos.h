@@ -160,8 +160,8 @@ typedef struct {
  * kinematics -- a lower bound of the configuration-space distance, so every sphere stays
  * collision-free. A walk ending in its eps-shell reads g at its own position (the nearest
  * boundary point is not known). Component order: goal, balls, points, arm, outer ball, faces.
- * Mixed precision runs such domains on the CUDA-core walker with at most 32 obstacle points
- * (UNSUPPORTED beyond, and with a point set).
+ * Mixed precision runs such domains on the CUDA-core walker for d <= 8 with at most 32
+ * obstacle points (UNSUPPORTED beyond, and with a point set); FP64 and plain FP32 take any.
  */
 
 /*

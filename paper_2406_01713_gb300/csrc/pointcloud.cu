@@ -311,7 +311,9 @@ __device__ __noinline__ float sphere_source(const MixedProblem &P, long long q, 
     return c;
 }
 
-template <int D, bool GRAD>
+// SRC: the launch holds a problem with an impulse source (the variant without keeps the walkers'
+// registers free of the source state).
+template <int D, bool GRAD, bool SRC>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __grid_constant__ SphereLaunch L) {
     using G = Geo<contraction_k(D)>;
     constexpr int kK = G::kK;
@@ -746,7 +748,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                 direction_f32<D, true>(L.seed, first ? first_direction_walk(walk, P.antithetic) : walk, (uint32_t)k, v);
                 const float sgn = first && first_direction_negated(walk, P.antithetic) ? -1.f : 1.f;
                 const float2 tb = table_lookup(P.table, R * P.sqrt_sigma);
-                if (P.has_source) {
+                if (SRC && P.has_source) {
                     // the ball B(x_k, R) contains the source: q G_B(x_k, z) times the weight so far; at
                     // step 0 of a gradient walk also the query's step-0 value and the source part of
                     // the gradient, q grad_x G_B(x_0, z) (every walk of the query writes the same)
@@ -824,18 +826,19 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                 } else {
                     term = kind == kGoal ? expf(logw) : 0.f;
                 }
-                term += src;
+                if (SRC) term += src;
             }
-            if (outcome == 4) term = src;  // ended by the roulette: the source contributions so far
+            if (outcome == 4) term = SRC ? src : 0.f;  // ended by the roulette: the source contributions so far
             // (a value-only problem in a gradient launch has no gradient terms)
-            const bool has_grad = GRAD && P.grad_mode && (outcome == 1 || outcome == 4) && k > 0;
+            // (a walk ended by the roulette has a value only from the source)
+            const bool has_grad = GRAD && P.grad_mode && (outcome == 1 || (SRC && outcome == 4)) && k > 0;
             const bool cv_walk = GRAD && P.cv && k > 0 && outcome != 3;  // capped walks count too
             float v0[D];
 #pragma unroll
             for (int i = 0; i < D; ++i) v0[i] = 0.f;
             // the first direction: for the gradient terms, and for every walk that took its first
             // sphere when the control variate sums sum v0 and sum v0^2
-            const bool need_v0 = (has_grad && (term != 0.f || src0 != 0.f)) || cv_walk;
+            const bool need_v0 = (has_grad && (term != 0.f || (SRC && src0 != 0.f))) || cv_walk;
             if (GRAD && need_v0) {
                 const uint64_t walk = (uint64_t)(P.walk_base + j);
                 direction_f32<D, true>(L.seed, first_direction_walk(walk, P.antithetic), 0u, v0);
@@ -844,19 +847,24 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                 for (int i = 0; i < D; ++i) v0[i] *= sgn;
             }
             // u^(x_1) C(R0): the walk's value without its step-0 source part
-            const float gt = has_grad ? gfac0 * (term - src0) : 0.f;
+            const float gt = has_grad ? gfac0 * (SRC ? term - src0 : term) : 0.f;
             // control variate: G = alpha(R0)/C(R0), one number per query (every walk writes it)
             if (cv_walk && gfac0 != 0.f)
                 P.acc[q * acc_fields(D, P.n_exp, P.cv, P.src) + cv_field(D, P.n_exp) + 3 * D] = (double)gfac0;
             write_record<D>(P, j, outcome, k, term, dsig, gt, GRAD && need_v0, v0, e);
             if (P.w_term != nullptr) P.w_term[j] = outcome == 3 ? (double)CUDART_NAN : (double)term;
             if (P.w_jumps != nullptr) P.w_jumps[j] = k;
-            if (P.w_dsigma != nullptr) P.w_dsigma[j] = P.has_source ? (double)CUDART_NAN : (double)(term * dsig);
+            if (P.w_dsigma != nullptr)
+                P.w_dsigma[j] = (SRC && P.has_source) ? (double)CUDART_NAN : (double)(term * dsig);
             if (P.w_grad != nullptr) {
                 // with a source, the per-query source part of the gradient (stored at step 0)
-                const double *sp = P.src ? P.acc + q * acc_fields(D, P.n_exp, P.cv, 1) + src_field(D, P.n_exp, P.cv) : nullptr;
+                const double *sp = (SRC && P.src) ? P.acc + q * acc_fields(D, P.n_exp, P.cv, 1) + src_field(D, P.n_exp, P.cv)
+                                                  : nullptr;
 #pragma unroll
-                for (int i = 0; i < D; ++i) P.w_grad[j * D + i] = (double)(gt * v0[i]) + (sp != nullptr ? sp[1 + i] : 0.0);
+                for (int i = 0; i < D; ++i) {
+                    const double g = (double)(gt * v0[i]);
+                    P.w_grad[j * D + i] = sp != nullptr ? g + sp[1 + i] : g;
+                }
             }
             active = false;
         }
@@ -985,21 +993,23 @@ float pointcloud_delta(int d, double xabs, double pmax) {
     return (float)(2.0 * bound + 1e-6);
 }
 
+template <int D, bool GRAD, bool SRC>
+static cudaError_t configure_sphere_kernel() {
+    cudaError_t e = cudaFuncSetAttribute(pc::sphere_kernel<D, GRAD, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pc::smem_bytes(D));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(pc::sphere_kernel<D, GRAD, SRC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
 static cudaError_t configure_spheres() {
     cudaError_t e = cudaSuccess;
-#define WOS_CFG(DD)                                                                                          \
-    if (e == cudaSuccess)                                                                                    \
-        e = cudaFuncSetAttribute(pc::sphere_kernel<DD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)pc::smem_bytes(DD));                                                   \
-    if (e == cudaSuccess)                                                                                    \
-        e = cudaFuncSetAttribute(pc::sphere_kernel<DD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                 (int)pc::smem_bytes(DD));                                                   \
-    if (e == cudaSuccess)                                                                                    \
-        e = cudaFuncSetAttribute(pc::sphere_kernel<DD, false>, cudaFuncAttributePreferredSharedMemoryCarveout, \
-                                 (int)cudaSharedmemCarveoutMaxShared);                                       \
-    if (e == cudaSuccess)                                                                                    \
-        e = cudaFuncSetAttribute(pc::sphere_kernel<DD, true>, cudaFuncAttributePreferredSharedMemoryCarveout,  \
-                                 (int)cudaSharedmemCarveoutMaxShared);
+#define WOS_CFG(DD)                                                             \
+    if (e == cudaSuccess) e = configure_sphere_kernel<DD, false, false>();      \
+    if (e == cudaSuccess) e = configure_sphere_kernel<DD, true, false>();       \
+    if (e == cudaSuccess) e = configure_sphere_kernel<DD, false, true>();       \
+    if (e == cudaSuccess) e = configure_sphere_kernel<DD, true, true>();
     WOS_CFG(2) WOS_CFG(3) WOS_CFG(4) WOS_CFG(5) WOS_CFG(6) WOS_CFG(7) WOS_CFG(8) WOS_CFG(9) WOS_CFG(10)
     WOS_CFG(11) WOS_CFG(12)
 #undef WOS_CFG
@@ -1008,7 +1018,7 @@ static cudaError_t configure_spheres() {
 
 int sphere_ctas_per_sm() { return pc::kCtasPerSm; }
 
-cudaError_t launch_spheres(const SphereLaunch &L, int d, int grad, int grid, cudaStream_t s) {
+cudaError_t launch_spheres(const SphereLaunch &L, int d, int grad, int src, int grid, cudaStream_t s) {
     // the attribute is per device: remember which devices are configured
     static std::mutex mu;
     static std::vector<int> configured;
@@ -1027,16 +1037,18 @@ cudaError_t launch_spheres(const SphereLaunch &L, int d, int grad, int grid, cud
     }
     if (grid < 1) return cudaSuccess;
     switch (d) {
-#define WOS_CASE(DD)                                                               \
-    case DD:                                                                       \
-        if (grad)                                                                  \
-            pc::sphere_kernel<DD, true><<<grid, pc::kThreads, smem, s>>>(L);       \
-        else                                                                       \
-            pc::sphere_kernel<DD, false><<<grid, pc::kThreads, smem, s>>>(L);      \
+#define WOS_LAUNCH(DD, G, S) pc::sphere_kernel<DD, G, S><<<grid, pc::kThreads, smem, s>>>(L)
+#define WOS_CASE(DD)                                                                   \
+    case DD:                                                                           \
+        if (grad)                                                                      \
+            src ? WOS_LAUNCH(DD, true, true) : WOS_LAUNCH(DD, true, false);            \
+        else                                                                           \
+            src ? WOS_LAUNCH(DD, false, true) : WOS_LAUNCH(DD, false, false);          \
         break;
         WOS_CASE(2) WOS_CASE(3) WOS_CASE(4) WOS_CASE(5) WOS_CASE(6) WOS_CASE(7) WOS_CASE(8) WOS_CASE(9)
         WOS_CASE(10) WOS_CASE(11) WOS_CASE(12)
 #undef WOS_CASE
+#undef WOS_LAUNCH
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -1073,7 +1085,7 @@ cudaError_t launch_pointcloud(const PointCloudDev &pcd, const MixedProblem &P, f
     L.walks_per_item = wpi;
     L.n_items = (total + wpi - 1) / wpi;
     const int grid = (int)std::min<int64_t>(slots, L.n_items);
-    return launch_spheres(L, P.d, grad, grid, s);
+    return launch_spheres(L, P.d, grad, P.has_source, grid, s);
 }
 
 }  // namespace wos

@@ -104,10 +104,38 @@ __device__ __forceinline__ float sum_coords(int m, F term) {
     return s;
 }
 
+// Planar arm (Sec. V-A): the safe-ball radius d_tau / K for the joint angles x_0..x_{n-1},
+// d_tau the task-space distance between the links and the obstacle points. Sine and cosine of
+// the summed angle as sincospi of angle / pi (exact range reduction, no large-argument path);
+// the host adds the FP32 error of this evaluation to the jump's shrink. Only the walker
+// instantiations for domains with an arm contain it.
+template <int D>
+__device__ __forceinline__ float arm_distance_f32(const MixedProblem &P, const float *geom, const f32x2 (&x2)[D]) {
+    const float *ll = geom + geom_link(D), *ob = geom + geom_arm_obs(D);
+    float px = 0.f, py = 0.f, ang = 0.f, dt = CUDART_INF_F;
+#pragma unroll
+    for (int n = 0; n < D; ++n) {
+        if (n >= P.n_links) break;
+        ang += xj(x2, n);
+        float sn, cs;
+        sincospif(ang * 0.318309886183790672f, &sn, &cs);
+        const float sx = ll[n] * cs, sy = ll[n] * sn, ss = fmaf(sx, sx, sy * sy);
+        for (int o = 0; o < P.n_arm_obs; ++o) {
+            const float ox = ob[2 * o] - px, oy = ob[2 * o + 1] - py;
+            const float t = fminf(fmaxf(fmaf(ox, sx, oy * sy) / ss, 0.f), 1.f);
+            const float dx = fmaf(-t, sx, ox), dy = fmaf(-t, sy, oy);
+            dt = fminf(dt, sqrtf(fmaf(dx, dx, dy * dy)));
+        }
+        px += sx;
+        py += sy;
+    }
+    return dt * P.arm_inv_K;
+}
+
 // Distance to the components other than the balls. geom layout in shared memory: [0,d) box lo,
 // [d,2d) box hi, [2d,3d) goal c, [3d,4d) outer c, [4d, 4d+K) exp w, then K x d exp a. An extruded
 // domain's box has its free-coordinate faces far away (set on the host).
-template <int D>
+template <int D, bool ARM>
 __device__ __forceinline__ void other_components(const MixedProblem &P, const float *geom,
                                                  const f32x2 (&x2)[D], float &goal, float &other,
                                                  int &okind, int &oidx) {
@@ -122,28 +150,8 @@ __device__ __forceinline__ void other_components(const MixedProblem &P, const fl
         });
         goal = sqrtf(s) - P.goal_r;
     }
-    if (P.n_links > 0) {
-        // planar arm (Sec. V-A): the safe-ball radius d_tau / K, accurate sine and cosine (the
-        // host adds the FP32 error of this evaluation to the jump's shrink)
-        const float *ll = geom + geom_link(D), *ob = geom + geom_arm_obs(D);
-        float px = 0.f, py = 0.f, ang = 0.f, dt = CUDART_INF_F;
-#pragma unroll
-        for (int n = 0; n < D; ++n) {
-            if (n >= P.n_links) break;
-            ang += xj(x2, n);
-            float sn, cs;
-            sincosf(ang, &sn, &cs);
-            const float sx = ll[n] * cs, sy = ll[n] * sn, ss = fmaf(sx, sx, sy * sy);
-            for (int o = 0; o < P.n_arm_obs; ++o) {
-                const float ox = ob[2 * o] - px, oy = ob[2 * o + 1] - py;
-                const float t = fminf(fmaxf(fmaf(ox, sx, oy * sy) / ss, 0.f), 1.f);
-                const float dx = fmaf(-t, sx, ox), dy = fmaf(-t, sy, oy);
-                dt = fminf(dt, sqrtf(fmaf(dx, dx, dy * dy)));
-            }
-            px += sx;
-            py += sy;
-        }
-        const float r = dt * P.arm_inv_K;
+    if constexpr (ARM) {
+        const float r = arm_distance_f32<D>(P, geom, x2);
         if (r < other) { other = r; okind = kArm; oidx = 0; }
     }
     if (P.has_outer) {
@@ -256,14 +264,14 @@ __device__ __forceinline__ float screen_finish(const ScreenState &S, const ulong
     return best;
 }
 
-template <int D>
+template <int D, bool ARM>
 __device__ __forceinline__ float distance_mixed(const MixedProblem &P, const float *geom,
                                                 const float4 *balls, int nblk,
                                                 const f32x2 (&x2)[D], float slack, int &kind,
                                                 int &idx) {
     float goal, other;
     int okind, oidx;
-    other_components<D>(P, geom, x2, goal, other, okind, oidx);
+    other_components<D, ARM>(P, geom, x2, goal, other, okind, oidx);
     ScreenState S;
     screen_init<D>(S, x2, fminf(goal, other), slack, P.proj);
     const ulonglong2 *B2 = reinterpret_cast<const ulonglong2 *>(balls);
@@ -617,7 +625,7 @@ __device__ __forceinline__ void step_walker(const MixedLaunch &L, const MixedPro
 
 // Not inlined: each dimension gets its own register allocation instead of the maximum over
 // all eleven specialisations of the kernel. One walker per thread.
-template <int D, bool GRAD>
+template <int D, bool GRAD, bool ARM>
 __device__ __noinline__ void run_item(const MixedLaunch &L, const MixedProblem &P, MixedSmem &S,
                                       const float4 *balls) {
     const int nblk = (P.n_balls + kBallBlock - 1) / kBallBlock;
@@ -628,7 +636,7 @@ __device__ __noinline__ void run_item(const MixedLaunch &L, const MixedProblem &
     while (__any_sync(0xffffffffu, W.active)) {
         if (!W.active) continue;
         int kind, idx;
-        const float R = distance_mixed<D>(P, geom, balls, nblk, W.x2, P.slack, kind, idx) - P.shrink;
+        const float R = distance_mixed<D, ARM>(P, geom, balls, nblk, W.x2, P.slack, kind, idx) - P.shrink;
         step_walker<D, GRAD>(L, P, S, balls, geom, W, R, kind, idx, end);
     }
 }
@@ -682,7 +690,12 @@ __global__ void __launch_bounds__(MAXT, 1) walk_mixed_kernel(const __grid_consta
         }
         switch (SP.d) {
 #define WOS_CASE(DD) \
-    case DD: run_item<DD, GRAD>(L, SP, S, smem_balls); break;
+    case DD:                                                                       \
+        if (DD <= kMaxArmLinksMixed && SP.n_links > 0)                                 \
+            run_item<DD, GRAD, (DD <= kMaxArmLinksMixed)>(L, SP, S, smem_balls);       \
+        else                                                                           \
+            run_item<DD, GRAD, false>(L, SP, S, smem_balls);                           \
+        break;
             WOS_CASE(2) WOS_CASE(3) WOS_CASE(4) WOS_CASE(5) WOS_CASE(6) WOS_CASE(7)
             WOS_CASE(8) WOS_CASE(9) WOS_CASE(10) WOS_CASE(11) WOS_CASE(12)
 #undef WOS_CASE

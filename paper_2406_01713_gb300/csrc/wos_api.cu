@@ -207,9 +207,10 @@ void error_bounds(wos_domain_s &D) {
     const double R = D.R_max;
     double dist_err = ((m + 4) / 2.0) * (L + C) + R + C + rmax + xabs;
     if (D.n_links > 0) {
-        // the arm's safe-ball radius in FP32: the joint angles summed (n u sum |q|), accurate sine
-        // and cosine (2 u), the link end points (n u reach), the projection on each link and its
-        // square root (10 u (|obstacle| + reach)), divided by K
+        // the arm's safe-ball radius in FP32: the joint angles summed (n u sum |q|), sine and
+        // cosine of angle / pi (the division: u |angle|; sincospi: 2 u), the link end points
+        // (n u reach), the projection on each link and its square root (10 u (|obstacle| + reach)),
+        // divided by K
         const int n = D.n_links;
         double reach = 0.0, omax = 0.0, qsum = 0.0;
         for (int i = 0; i < n; ++i) {
@@ -218,7 +219,7 @@ void error_bounds(wos_domain_s &D) {
         }
         for (int64_t o = 0; o < D.n_arm_obs; ++o)
             omax = std::max(omax, std::hypot(D.arm_obs[2 * o], D.arm_obs[2 * o + 1]));
-        const double arm = reach * (n * qsum + 2.0 + n) + 10.0 * (omax + reach);
+        const double arm = reach * ((n + 1) * qsum + 2.0 + n) + 10.0 * (omax + reach);
         dist_err = std::max(dist_err, arm / D.arm_K);
     }
     const double jump_err = (d + 5) * R + L;
@@ -920,9 +921,10 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
     if (o.precision != WOS_MIXED) return fail(WOS_ERR_INVALID_ARG, "unknown precision %d", o.precision);
     if (o.max_steps > (int64_t)kRecKMask)
         return fail(WOS_ERR_INVALID_ARG, "max_steps must be below 2^28 in mixed precision");
-    if (dom->n_links > 0 && (dom->n_points > 0 || dom->n_arm_obs > kMaxArmObs))
-        return fail(WOS_ERR_UNSUPPORTED, "mixed precision runs an arm with at most %d obstacle points and no point set",
-                    kMaxArmObs);
+    if (dom->n_links > 0 && (dom->n_points > 0 || dom->n_arm_obs > kMaxArmObs || dom->d > kMaxArmLinksMixed))
+        return fail(WOS_ERR_UNSUPPORTED,
+                    "mixed precision runs an arm in d <= %d with at most %d obstacle points, and no point set",
+                    kMaxArmLinksMixed, kMaxArmObs);
     WeightTable tab;
     WOS_TRY(ensure_table(dom, sigma, &tab));
     if (dom->n_points > 0 || (dom->has_pcd && !o.cuda_core_balls)) {
@@ -1780,7 +1782,7 @@ struct wos_batch_s {
     // [reduction] [finalize]
     MixedLaunch L{};
     std::vector<SphereLaunch> sph;
-    std::vector<int> sph_grid, sph_dims;
+    std::vector<int> sph_grid, sph_dims, sph_src;
     ReduceArgs ra{};
     bool any_seg = false;
     FinalizeArgs fa{};
@@ -1895,7 +1897,8 @@ wos_status enqueue_batch_core(wos_batch_s *b, cudaStream_t cap, CaptureSide &cs)
     if (ns > 0 && cudaEventRecord(cs.ev.back(), cap) != cudaSuccess) return fail(WOS_ERR_CUDA, "fork event capture");
     for (size_t k = 0; k < ns; ++k)
         if (cudaStreamWaitEvent(cs.side[k], cs.ev.back(), 0) != cudaSuccess ||
-            launch_spheres(b->sph[k], b->sph_dims[k], b->grad_any, b->sph_grid[k], cs.side[k]) != cudaSuccess ||
+            launch_spheres(b->sph[k], b->sph_dims[k], b->grad_any, b->sph_src[k], b->sph_grid[k], cs.side[k]) !=
+                cudaSuccess ||
             cudaEventRecord(cs.ev[k], cs.side[k]) != cudaSuccess)
             return fail(WOS_ERR_CUDA, "sphere-set kernel capture failed");
     if (b->n_items > 0 && launch_walk_mixed(b->L, b->grad_any, b->grid, b->cfg.threads, b->smem, cap) != cudaSuccess)
@@ -1929,7 +1932,8 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
             return fail(WOS_ERR_UNSUPPORTED, "problem %d: mixed-precision point sets need d <= %d", i, kPointCloudMaxD);
         if (p.domain->n_points > 0 && p.domain->n_balls > 0)
             return fail(WOS_ERR_UNSUPPORTED, "problem %d: a domain with both balls and points", i);
-        if (p.domain->n_links > 0 && (p.domain->n_points > 0 || p.domain->n_arm_obs > kMaxArmObs))
+        if (p.domain->n_links > 0 &&
+            (p.domain->n_points > 0 || p.domain->n_arm_obs > kMaxArmObs || p.domain->d > kMaxArmLinksMixed))
             return fail(WOS_ERR_UNSUPPORTED, "problem %d: an arm with a point set or over %d obstacle points", i,
                         kMaxArmObs);
         tensor[i] = p.domain->has_pcd && (p.domain->n_points > 0 || !b->o.cuda_core_balls);
@@ -2163,6 +2167,7 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     b->sph.clear();
     b->sph_grid.clear();
     b->sph_dims.clear();
+    b->sph_src.clear();
     for (int dd = 0; dd <= kPointCloudMaxD; ++dd) {
         if (sph_off[dd + 1] <= sph_off[dd]) continue;
         SphereLaunch SL;
@@ -2178,6 +2183,10 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         b->sph.push_back(SL);
         b->sph_grid.push_back((int)std::min<int64_t>((int64_t)cfg.sphere_ctas_per_sm * sms, SL.n_items));
         b->sph_dims.push_back(dd);
+        int src_any = 0;  // the source variant of the kernel if a problem of this dimension has one
+        for (int k : sph_problem)
+            src_any |= b->probs[k].domain->d == dd && b->probs[k].domain->has_source;
+        b->sph_src.push_back(src_any);
     }
     if (b->no_graph) return WOS_OK;
     CaptureSide side;

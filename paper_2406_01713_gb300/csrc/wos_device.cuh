@@ -18,7 +18,8 @@ constexpr int kTableNodes = 8192;  // weight-table nodes per dimension (linear i
 // Component kinds. Tie-break order of the distance query: goal, balls, points, arm, outer ball,
 // box faces (lo_0, hi_0, lo_1, ...).
 enum Kind : int { kGoal = 0, kBall = 1, kPoint = 2, kOuter = 3, kFace = 4, kArm = 5 };
-constexpr int kMaxArmObs = 32;  // task-space obstacle points of an arm in the mixed walker
+constexpr int kMaxArmObs = 32;        // task-space obstacle points of an arm in the mixed walker
+constexpr int kMaxArmLinksMixed = 8;  // the mixed walker runs arms in d <= 8
 
 // ------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32 -> 64-bit

@@ -28,10 +28,12 @@ __device__ __forceinline__ T norm_diff(const T (&x)[D], const T *c, int m) {
     return sqrt(s);
 }
 
+// sine and cosine of a summed joint angle: FP64 sincos; FP32 sincospi of a / pi (exact range
+// reduction, no large-argument path)
 template <typename T>
 __device__ __forceinline__ void sincos_t(T a, T *s, T *c) {
     if constexpr (sizeof(T) == 8) sincos(a, s, c);
-    else sincosf(a, s, c);
+    else sincospif(a * 0.318309886183790672f, s, c);
 }
 
 // Planar arm (Sec. V-A): joint angles x_0..x_{n-1} summed along the chain, base at the origin;

@@ -204,7 +204,8 @@ struct SphereLaunch {
     double *radius_out;  // nullable: distance bound at each walk's start (single problem only)
     SphereProblem single;
 };
-cudaError_t launch_spheres(const SphereLaunch &L, int d, int grad, int grid, cudaStream_t s);
+// src: a problem of the launch has an impulse source (selects the kernel variant with the source term)
+cudaError_t launch_spheres(const SphereLaunch &L, int d, int grad, int src, int grid, cudaStream_t s);
 int sphere_ctas_per_sm();
 // Single problem: implicit items, grid sized to the work.
 cudaError_t launch_pointcloud(const PointCloudDev &pcd, const MixedProblem &P, float delta,
