@@ -422,9 +422,7 @@ wos_status wos_set_autotune_cache(const char *cache_path);
  * weight table, which is allocated, and is rejected.
  * Each call looks up the device address of the array (cudaGetSymbolAddress, which allocates
  * nothing) with the caller's device current, so the address is never stale after a device reset.
- * The first call on a device may load the library's device code (lazy module loading); make that
- * first call before any stream capture. Each call clears
- * the array on its stream and then reuses it, and the array keeps the last call's contents:
+ * Each call clears the array on its stream and then reuses it, and the array keeps the last call's contents:
  * calls whose work overlaps on the GPU (other streams, other host threads) race on it and
  * must be serialised by the caller.
  * Errors: as wos_solve; INVALID_ARG if Q exceeds the limit; UNSUPPORTED for WOS_MIXED.
