@@ -552,7 +552,7 @@ def plain_comparison(W, doms, probs, seed, mixed_steps, mixed_s, mixed_rmse, cv=
     outs = []
     e0.record()
     base = 0
-    steps = torch.zeros(6, dtype=torch.int64, device="cuda")
+    steps = torch.zeros(7, dtype=torch.int64, device="cuda")
     total = 0
     for d, p in zip(doms, probs):
         r = d.grad(p["X"], p["n_walks"], p["eps"], p["sigma"], precision="fp32", seed=seed, walk_offset=base,

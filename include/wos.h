@@ -148,7 +148,21 @@ typedef struct {
     const double *link_l;       /* n_links link lengths, > 0 */
     int64_t n_arm_obs;          /* >= 1 with an arm: task-space obstacle points */
     const double *arm_obs;      /* n_arm_obs x 2, row major */
+    double sigma_max;           /* >= 0: build the WOS_MIXED weight tables for every sigma up to
+                                   this one at creation (0: each on first use; see below) */
 } wos_domain_desc;
+
+/*
+ * Weight tables (WOS_MIXED): log C_nu(z) and S_{nu+1}/S_nu(z), built in FP64 on the fixed grid
+ * z_i = i / 1024 (linear interpolation), so a walk's weights depend on z = R sqrt(sigma) alone.
+ * A domain needs the grid up to the smallest power of two 2^level >= sqrt(sigma) times its
+ * largest distance (level <= 12; UNSUPPORTED beyond); a table of a higher level serves every
+ * lower one. With sigma_max > 0, wos_domain_create builds the table for sigma_max, and no call
+ * with sigma <= sigma_max allocates or waits for one. Otherwise the first WOS_MIXED call that
+ * needs a larger table allocates it with cudaMalloc (8 KB times 2^level) and builds it on its
+ * own stream (no host wait); calls on other streams wait for that build on the device. The
+ * synchronous calls (wos_plan_path, wos_plan_paths, wos_batch_create) wait for it on the host.
+ */
 
 /*
  * Planar arm in configuration space (Sec. V, V-A; the RR validation of Sec. VII): the first
@@ -189,7 +203,7 @@ typedef struct {
  */
 
 /*
- * Per-call options. A NULL options pointer means {WOS_MIXED, 0, seed 0, offset 0, 10000, 0}.
+ * Per-call options. A NULL options pointer means {WOS_MIXED, 0, seed 0, offset 0, 10000, 0, 0}.
  *
  * Russian roulette on the weight (roulette_w > 0; the closing discussion's roulette on C,
  * Sec. IX; no rule is printed): before jump k >= 1 of a walk whose weight W = prod C(R_i) is
@@ -207,7 +221,22 @@ typedef struct {
     int64_t max_steps;   /* jumps per walk before it is capped (contributes 0); <= 0: 10000;
                             below 2^28 in WOS_MIXED */
     double roulette_w;   /* > 0: Russian roulette below this weight; 0: off */
+    int64_t wait_cycles; /* tensor-core sphere-set walker: SM clock cycles one wait of its main
+                            loop may take before the launch gives up (see below); <= 0: 4e9
+                            (~2 s) */
 } wos_options;
+
+/*
+ * Failure detection. The tensor-core sphere-set walker's threads wait on each other through
+ * shared-memory barriers (copies landed, products ready, accumulators read). Every wait is
+ * bounded: one that takes more than wait_cycles SM clock cycles sets the launch's status word,
+ * and every thread leaves through the same teardown, which first waits (up to 4e9 cycles each,
+ * whatever wait_cycles is) for the products and copies already issued and then frees the
+ * tensor memory. Such a call's outputs are NaN and wos_stats.timeouts is nonzero; the
+ * asynchronous calls report it only there, wos_plan_path and wos_plan_paths return
+ * WOS_ERR_TIMEOUT (the planner step flag is 16). The device stays usable: the next call runs
+ * normally. A small wait_cycles makes a healthy launch give up (how failures are tested).
+ */
 
 /* Counters of one call, written to DEVICE memory when the stream completes (int64, exact). */
 typedef struct {
@@ -217,6 +246,7 @@ typedef struct {
     int64_t outside;         /* walks whose query was not in the open domain */
     int64_t shrinks;         /* tensor-core walker steps whose radius was set by a chunk bound */
     int64_t killed;          /* walks ended by the Russian roulette (wos_options.roulette_w) */
+    int64_t timeouts;        /* nonzero: a tensor-core walker wait ran out (outputs NaN) */
 } wos_stats;
 
 /* ---- domain ------------------------------------------------------------------------- */
@@ -280,7 +310,8 @@ wos_status wos_walks(wos_domain_t dom, const wos_options *opt, const double *x, 
  * One planner step on the device point x (d device doubles, updated in place): if x is within
  * eps of the goal, flag = 1 and x is kept; otherwise grad u is estimated with n_walks gradient
  * walks (walk offset opt->walk_offset + step_idx * n_walks) and x <- x + s grad/|grad| with
- * s = min(s_ub, d_bound(x) / 2); flag = 2 if |grad| = 0 (x kept), 4 if x is outside.
+ * s = min(s_ub, d_bound(x) / 2); flag = 2 if |grad| = 0 (x kept), 4 if x is outside, 16 if a
+ * tensor-core walker wait ran out (x kept; the path stops).
  * flag: one device int32; grad_out: d device doubles or NULL. Errors as wos_solve.
  */
 wos_status wos_plan_step(wos_domain_t dom, const wos_options *opt, double *x, int64_t n_walks,
@@ -289,6 +320,7 @@ wos_status wos_plan_step(wos_domain_t dom, const wos_options *opt, double *x, in
 
 /*
  * n_steps planner steps from x0 (d device doubles), recorded and replayed as one CUDA graph.
+ * Synchronous (it records and replays the graph, then waits for the stream).
  * path: (n_steps + 1) x d device doubles (row 0 = x0; rows after the goal repeat the last
  * point); flags: n_steps device int32 (as wos_plan_step; 8 marks steps after the goal);
  * grads: n_steps x d device doubles or NULL. Errors as wos_solve.

@@ -34,6 +34,7 @@ class DomainDesc(ctypes.Structure):
         ("proj_dims", ctypes.c_int32),
         ("n_links", ctypes.c_int32), ("link_l", _PD),
         ("n_arm_obs", ctypes.c_int64), ("arm_obs", _PD),
+        ("sigma_max", ctypes.c_double),
     ]
 
 
@@ -45,12 +46,13 @@ class Options(ctypes.Structure):
         ("walk_offset", ctypes.c_int64),
         ("max_steps", ctypes.c_int64),
         ("roulette_w", ctypes.c_double),
+        ("wait_cycles", ctypes.c_int64),
     ]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in
-                ("walks", "walk_steps", "capped", "outside", "shrinks", "killed")]
+                ("walks", "walk_steps", "capped", "outside", "shrinks", "killed", "timeouts")]
 
 
 STATS_FIELDS = [f[0] for f in Stats._fields_]

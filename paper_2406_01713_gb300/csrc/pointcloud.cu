@@ -77,7 +77,7 @@ struct Geo {
 };
 constexpr int kTrPitch = 34;  // transpose row: 32 spheres + 2 pad (8-byte aligned rows, no bank conflicts)
 constexpr uint32_t kTransposeBytes = 4 * 32 * kTrPitch * 4;  // per walker warp: 32 walkers x 32 spheres
-constexpr long long kWaitBudget = 4000000000ll;  // clock cycles (~2 s) before a wait gives up
+constexpr long long kDrainBudget = kDefaultWaitBudget;  // teardown waits, whatever the launch's budget
 
 // Core-matrix layout (8 rows x 16 bytes), K-major, no swizzle: element (r, k) of a
 // rows x K BF16 operand sits at byte (r/8) SBO + (k/8) LBO + (r%8) 16 + (k%8) 2, SBO = (K/8) 128.
@@ -109,12 +109,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
 }
 // try_wait with a suspend-time hint (ns): a waiting thread is parked until the phase completes
 // or the hint runs out, instead of spinning on the issue slots the MMA-issuing thread needs.
-__device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
+// hint_ns: the longest the thread may be suspended inside one test (suspend-time hint)
+__device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity, uint32_t hint_ns = 20000u) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(su32(b)), "r"(parity), "r"(20000u)
+        : "r"(su32(b)), "r"(parity), "r"(hint_ns)
         : "memory");
     return ok != 0;
 }
@@ -147,17 +148,38 @@ struct RingPos {
     }
 };
 
-// Bounded wait: false if the budget ran out or another thread aborted.
-__device__ __forceinline__ bool wait_bar(Shared &S, uint64_t *b, uint32_t parity, int *status) {
-    if (mbar_test(b, parity)) return true;
+// Bounded wait of the main loop: false if the launch's budget ran out or another thread aborted.
+// Bounded wait of the main loop (budget and suspend-time hint from the launch; the hint is
+// scaled to the budget, so that a small budget is not outlasted by one test): false if the
+// budget ran out or another thread aborted.
+__device__ __noinline__ bool wait_bar_slow(Shared &S, uint64_t *b, uint32_t parity, int *status, long long budget,
+                                           uint32_t hint) {
     const long long t0 = clock64();
     for (;;) {
-        if (mbar_test(b, parity)) return true;
+        if (mbar_test(b, parity, hint)) return true;
         if (S.abort_flag) return false;
-        if (clock64() - t0 > kWaitBudget) {
+        if (clock64() - t0 > budget) {
             S.abort_flag = 1;
             atomicOr(status, 1);
             return false;
+        }
+    }
+}
+__device__ __forceinline__ bool wait_bar(Shared &S, uint64_t *b, uint32_t parity, const SphereLaunch &L) {
+    if (mbar_test(b, parity, L.wait_hint)) return true;
+    return wait_bar_slow(S, b, parity, L.status, L.wait_budget, L.wait_hint);
+}
+
+// Teardown wait for work already issued (products, copies): it does not stop at an abort, so
+// that nothing is in flight when the tensor memory is freed and the CTA exits; bounded by the
+// full budget.
+__device__ __forceinline__ void drain_wait(uint64_t *b, uint32_t parity, int *status) {
+    if (mbar_test(b, parity)) return;
+    const long long t0 = clock64();
+    while (!mbar_test(b, parity)) {
+        if (clock64() - t0 > kDrainBudget) {
+            atomicOr(status, 2);
+            return;
         }
     }
 }
@@ -165,10 +187,10 @@ __device__ __forceinline__ bool wait_bar(Shared &S, uint64_t *b, uint32_t parity
 // Warp-uniform bounded wait for the walker warps: every lane tests the phase once (a broadcast
 // read, no divergence in the common case); if it is still open, lane 0 polls with the budget and
 // every lane gets the result.
-__device__ __forceinline__ bool warp_wait_bar(Shared &S, uint64_t *b, uint32_t parity, int *status) {
+__device__ __forceinline__ bool warp_wait_bar(Shared &S, uint64_t *b, uint32_t parity, const SphereLaunch &L) {
     if (__any_sync(0xffffffffu, mbar_test(b, parity))) return true;
     int ok = 0;
-    if ((threadIdx.x & 31) == 0) ok = wait_bar(S, b, parity, status) ? 1 : 0;
+    if ((threadIdx.x & 31) == 0) ok = wait_bar(S, b, parity, L) ? 1 : 0;
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
@@ -195,6 +217,8 @@ __device__ __forceinline__ bool next_item(const SphereLaunch &L, SphereItem &it)
         it.problem = 0;
         it.j0 = (int64_t)i * L.walks_per_item;
         it.j1 = it.j0 + L.walks_per_item < total ? it.j0 + L.walks_per_item : total;
+        const int *dn = L.single.P.done;
+        if (dn != nullptr && *(volatile const int *)dn != 0) it.j1 = it.j0;
     }
     return true;
 }
@@ -388,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             long long g_load = 0, g_pair = 0;  // tile pairs copied and consumed so far
             bool ok = true;
             for (int step = 0; ok; ++step) {
-                if (!wait_bar(S, &S.a_ready, step & 1, L.status)) break;
+                if (!wait_bar(S, &S.a_ready, step & 1, L)) break;
                 if (S.stop) break;
                 // the problem of this step (the walkers change it only between steps)
                 const int T = SP.n_tiles;
@@ -417,8 +441,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                 for (int t = 0; ok && t < T; ++t) {
                     const int s = mp.slot, half = t % kPairTiles;
                     const int b = (int)(g_mma & 1);
-                    if (half == 0 && !wait_bar(S, &S.full[s], mp.round & 1u, L.status)) { ok = false; break; }
-                    if (g_mma >= 2 && !wait_bar(S, &S.tempty[b], (uint32_t)(((g_mma >> 1) - 1) & 1), L.status)) {
+                    if (half == 0 && !wait_bar(S, &S.full[s], mp.round & 1u, L)) { ok = false; break; }
+                    if (g_mma >= 2 && !wait_bar(S, &S.tempty[b], (uint32_t)(((g_mma >> 1) - 1) & 1), L)) {
                         ok = false;
                         break;
                     }
@@ -439,9 +463,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             // drain: every issued MMA completes before the tensor memory is freed; every issued
             // copy was consumed by an MMA, except after an abort
             mma_commit(&S.drain);
-            wait_bar(S, &S.drain, 0, L.status);
+            drain_wait(&S.drain, 0, L.status);
             for (long long g = g_pair; g < g_load; ++g) {
-                wait_bar(S, &S.full[mp.slot], mp.round & 1u, L.status);
+                drain_wait(&S.full[mp.slot], mp.round & 1u, L.status);
                 mp.next(kSlots);
             }
         }
@@ -566,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                 const int b = (int)(g_epi & 1);
                 const float rhi[kTileN / kChunk] = {rhi_next.x, rhi_next.y};
                 rhi_next = __ldg(rhi2 + (t + 1 < T ? t + 1 : t));
-                if (!warp_wait_bar(S, &S.tfull[b], (uint32_t)((g_epi >> 1) & 1), L.status)) {
+                if (!warp_wait_bar(S, &S.tfull[b], (uint32_t)((g_epi >> 1) & 1), L)) {
                     ok = false;
                     break;
                 }
@@ -1058,8 +1082,8 @@ cudaError_t launch_spheres(const SphereLaunch &L, int d, int grad, int src, int 
 // when there is that much work), so that the item tails stay short against the item.
 cudaError_t launch_pointcloud(const PointCloudDev &pcd, const MixedProblem &P, float delta,
                               unsigned long long *cursor, int *status, unsigned long long *shrinks,
-                              uint64_t seed, int64_t max_steps, int grad, cudaStream_t s,
-                              double *radius_out) {
+                              uint64_t seed, int64_t max_steps, long long wait_budget, int grad,
+                              cudaStream_t s, double *radius_out) {
     SphereLaunch L;
     memset(&L, 0, sizeof(L));
     L.single.P = P;
@@ -1073,6 +1097,8 @@ cudaError_t launch_pointcloud(const PointCloudDev &pcd, const MixedProblem &P, f
     L.shrinks = shrinks;
     L.seed = seed;
     L.max_steps = max_steps;
+    L.wait_budget = wait_budget > 0 ? wait_budget : kDefaultWaitBudget;
+    L.wait_hint = wait_hint_ns(L.wait_budget);
     L.radius_out = radius_out;
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);

@@ -62,6 +62,15 @@ int device_sms() {
 // =====================================================================================
 // domain
 // =====================================================================================
+// Weight table on the fixed grid z_i = i / kTableNodesPerUnit, i = 0 .. kTableNodesPerUnit 2^level,
+// covering z in [0, 2^level]. Every table of a dimension has the same nodes, so the interpolated
+// weights depend on z alone: not on sigma, and not on which tables earlier calls built.
+struct TableEntry {
+    int level = 0;
+    float2 *nodes = nullptr;
+    cudaEvent_t built = nullptr;  // recorded after an asynchronous build; null once it completed
+};
+
 struct wos_domain_s {
     int d = 0, has_box = 0, has_outer = 0, has_goal = 0, n_balls = 0, n_exp = 0;
     int has_source = 0;
@@ -84,9 +93,7 @@ struct wos_domain_s {
     float *geom_mixed = nullptr;   // box lo/hi, goal c, outer c, exp w (padded), exp a (padded)
     int nblk = 0;
     std::mutex mu;
-    std::vector<float2 *> tables;
-    float2 *table = nullptr;
-    double table_zmax = 0;
+    std::vector<TableEntry> tables;  // one per z-range level, built once
     PointCloudDev pcd{};  // tensor-core operands of the sphere set (point set or large ball set)
     bool has_pcd = false;
     float pc_delta = 0.f;
@@ -229,8 +236,8 @@ void error_bounds(wos_domain_s &D) {
 }
 
 // Table of log C_nu(z) and S_{nu+1}(z)/S_nu(z), built in FP64 on the device.
-__global__ void build_table_kernel(int d, double h, int n, float2 *out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void build_table_kernel(int d, double h, int64_t n, float2 *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double z = h * i;
     const double nu = 0.5 * d - 1.0;
@@ -249,32 +256,73 @@ __global__ void set_exp_w_kernel(const double *w, int K, double *w64, float *w32
     }
 }
 
-wos_status ensure_table(wos_domain_t dom, double sigma, WeightTable *out) {
-    const double need = dom->R_max * std::sqrt(sigma) * 1.0001 + 1e-9;
+constexpr int kTableNodesPerUnit = 1024;  // node spacing 2^-10 in z
+constexpr int kTableMaxLevel = 12;        // z up to 4096 (4M nodes, 32 MB)
+int64_t table_nodes(int level) { return ((int64_t)kTableNodesPerUnit << level) + 1; }
+
+// The smallest level whose table covers every z = R sqrt(sigma) of the domain, or -1 if none does.
+int table_level(const wos_domain_s &D, double sigma) {
+    const double need = D.R_max * std::sqrt(sigma) * 1.0001 + 1e-9;
+    for (int level = 0; level <= kTableMaxLevel; ++level)
+        if (std::ldexp(1.0, level) >= need) return level;
+    return -1;
+}
+
+// A weight table covering `level` (any built table of that level or above: they agree on their
+// common nodes). The first call that needs a larger one allocates it (cudaMalloc) and builds it
+// on stream s. With sync the call waits for the build; otherwise it records an event that later
+// calls on other streams wait for (on the device) until the build is seen complete.
+wos_status ensure_table_level(wos_domain_t dom, int level, WeightTable *out, cudaStream_t s, bool sync) {
+    if (level < 0)
+        return fail(WOS_ERR_UNSUPPORTED, "sigma too large for the weight tables: R_max sqrt(sigma) above %d",
+                    1 << kTableMaxLevel);
     std::lock_guard<std::mutex> lk(dom->mu);
-    if (dom->table == nullptr || dom->table_zmax < need) {
-        const double zmax = std::max(1.0, need * 1.25);
-        float2 *t = nullptr;
-        WOS_CUDA(cudaMalloc(&t, sizeof(float2) * kTableNodes));
-        cudaStream_t s;
-        WOS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-        const double h = zmax / (kTableNodes - 1);
-        build_table_kernel<<<(kTableNodes + 255) / 256, 256, 0, s>>>(dom->d, h, kTableNodes, t);
+    TableEntry *T = nullptr;
+    for (TableEntry &t : dom->tables)
+        if (t.level >= level && (T == nullptr || t.level > T->level)) T = &t;
+    if (T == nullptr) {
+        TableEntry t;
+        t.level = level;
+        const int64_t n = table_nodes(level);
+        WOS_CUDA(cudaMalloc(&t.nodes, sizeof(float2) * (size_t)n));
+        build_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dom->d, 1.0 / kTableNodesPerUnit, n,
+                                                                     t.nodes);
         cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        cudaStreamDestroy(s);
+        if (e == cudaSuccess) {
+            if (sync) e = cudaStreamSynchronize(s);
+            else if ((e = cudaEventCreateWithFlags(&t.built, cudaEventDisableTiming)) == cudaSuccess)
+                e = cudaEventRecord(t.built, s);
+        }
         if (e != cudaSuccess) {
-            cudaFree(t);
+            if (t.built) cudaEventDestroy(t.built);
+            cudaFree(t.nodes);
             return fail(WOS_ERR_CUDA, "weight table build failed: %s", cudaGetErrorString(e));
         }
         dom->tables.push_back(t);
-        dom->table = t;
-        dom->table_zmax = zmax;
+        T = &dom->tables.back();
+    } else if (T->built != nullptr) {
+        const cudaError_t q = cudaEventQuery(T->built);
+        if (q == cudaSuccess) {
+            cudaEventDestroy(T->built);
+            T->built = nullptr;
+        } else if (q == cudaErrorNotReady && sync) {
+            WOS_CUDA(cudaEventSynchronize(T->built));
+            cudaEventDestroy(T->built);
+            T->built = nullptr;
+        } else if (q == cudaErrorNotReady) {
+            WOS_CUDA(cudaStreamWaitEvent(s, T->built, 0));
+        } else {
+            return fail(WOS_ERR_CUDA, "weight table build failed: %s", cudaGetErrorString(q));
+        }
     }
-    out->nodes = dom->table;
-    out->n = kTableNodes;
-    out->inv_h = (float)((kTableNodes - 1) / dom->table_zmax);
+    out->nodes = T->nodes;
+    out->n = (int)table_nodes(T->level);
+    out->inv_h = (float)kTableNodesPerUnit;
     return WOS_OK;
+}
+
+wos_status ensure_table(wos_domain_t dom, double sigma, WeightTable *out, cudaStream_t s, bool sync) {
+    return ensure_table_level(dom, table_level(*dom, sigma), out, s, sync);
 }
 
 // =====================================================================================
@@ -334,6 +382,8 @@ __global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
         const bool out = c[3] > 0 || (a.status != nullptr && *a.status != 0);
         if (t == 0 && a.stats != nullptr && a.shrinks != nullptr)
             atomicAdd(reinterpret_cast<unsigned long long *>(a.stats) + 4, *a.shrinks);
+        if (t == 0 && a.stats != nullptr && a.status != nullptr && *a.status != 0)
+            reinterpret_cast<unsigned long long *>(a.stats)[6] = (unsigned long long)*a.status;
         const double nan = CUDART_NAN;
         // standard errors: from the walks, or from the N/2 antithetic pair means (their sum is
         // half the walks' sum)
@@ -689,10 +739,11 @@ struct Opts {
     uint64_t seed;
     int64_t walk_offset, max_steps;
     double roulette_w;    // > 0: Russian roulette on weights below it
+    long long wait_cycles;  // tensor-core walker: main-loop wait budget (clock cycles)
 };
 
 Opts read_opts(const wos_options *o) {
-    Opts r{WOS_MIXED, 0, 0, 0, 0, 0ull, 0, 10000, 0.0};
+    Opts r{WOS_MIXED, 0, 0, 0, 0, 0ull, 0, 10000, 0.0, kDefaultWaitBudget};
     if (o != nullptr) {
         r.precision = o->precision;
         r.laplace = (o->flags & WOS_FLAG_LAPLACE_FACTOR) ? 1 : 0;
@@ -703,6 +754,7 @@ Opts read_opts(const wos_options *o) {
         r.walk_offset = o->walk_offset;
         r.max_steps = o->max_steps > 0 ? o->max_steps : 10000;
         r.roulette_w = o->roulette_w;
+        r.wait_cycles = o->wait_cycles > 0 ? (long long)o->wait_cycles : kDefaultWaitBudget;
     }
     return r;
 }
@@ -926,7 +978,7 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
                     "mixed precision runs an arm in d <= %d with at most %d obstacle points, and no point set",
                     kMaxArmLinksMixed, kMaxArmObs);
     WeightTable tab;
-    WOS_TRY(ensure_table(dom, sigma, &tab));
+    WOS_TRY(ensure_table(dom, sigma, &tab, s, false));
     if (dom->n_points > 0 || (dom->has_pcd && !o.cuda_core_balls)) {
         if (!dom->has_pcd)
             return fail(WOS_ERR_UNSUPPORTED, "mixed-precision point clouds need d <= %d", kPointCloudMaxD);
@@ -937,8 +989,9 @@ wos_status launch_walkers(wos_domain_t dom, const Opts &o, const double *x, int6
         apply_walk_opts(P, o);
         unsigned long long *shrinks = sc.cursor + 1;
         int *status = reinterpret_cast<int *>(sc.cursor + 2);
+        P.done = skip;  // a planner step after the goal runs no walks
         WOS_CUDA(launch_pointcloud(dom->pcd, P, dom->pc_delta, sc.cursor, status, shrinks, o.seed, o.max_steps,
-                                   grad_mode, s));
+                                   o.wait_cycles, grad_mode, s));
         return launch_reduce_single(dom, o, Q, N, grad_mode, sc, skip, s);
     }
     const int64_t total = Q * N;
@@ -1093,6 +1146,8 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
     if (d < 2 || d > WOS_MAX_D) return fail(WOS_ERR_UNSUPPORTED, "d = %d outside 2..%d", d, WOS_MAX_D);
     if (desc->n_balls < 0 || desc->n_points < 0 || desc->n_exp < 0)
         return fail(WOS_ERR_INVALID_ARG, "negative count");
+    if (!(desc->sigma_max >= 0) || desc->sigma_max > 1e12)
+        return fail(WOS_ERR_INVALID_ARG, "sigma_max must be in [0, 1e12]");
     if (desc->proj_dims < 0 || desc->proj_dims > d)
         return fail(WOS_ERR_INVALID_ARG, "proj_dims = %d outside 0..%d", desc->proj_dims, d);
     const int proj = desc->proj_dims > 0 ? desc->proj_dims : d;
@@ -1261,6 +1316,15 @@ wos_status wos_domain_create(const wos_domain_desc *desc, wos_domain_t *out) {
                              std::fabs(D->outer_c[j]) + D->outer_r});
         D->pc_delta = pointcloud_delta(d, xabs, D->pcd.pmax);
     }
+    // weight tables for every sigma up to sigma_max, so that no later call builds one
+    if (desc->sigma_max > 0) {
+        WeightTable t;
+        const wos_status st = ensure_table_level(D, table_level(*D, desc->sigma_max), &t, nullptr, true);
+        if (st != WOS_OK) {
+            wos_domain_destroy(D);
+            return st;
+        }
+    }
     *out = D;
     return WOS_OK;
 }
@@ -1272,7 +1336,10 @@ wos_status wos_domain_destroy(wos_domain_t dom) {
     cudaFree(dom->f32);
     cudaFree(dom->balls_mixed);
     cudaFree(dom->geom_mixed);
-    for (float2 *t : dom->tables) cudaFree(t);
+    for (TableEntry &t : dom->tables) {
+        if (t.built) cudaEventDestroy(t.built);
+        cudaFree(t.nodes);
+    }
     if (dom->has_pcd) pointcloud_release(&dom->pcd);
     delete dom;
     return WOS_OK;
@@ -1359,9 +1426,11 @@ struct PlanArgs {
     int cv;  // control-variate gradient (sums after the du/dw fields)
     int src;  // impulse-source fields after those
     unsigned long long *counts;
-    unsigned long long *cursor;
+    unsigned long long *cursor;  // single walker launch: [item cursor, shrinks, status]; nullable
     double *grad_row;
     double *path_row;
+    const int *status;  // nullable: the tensor-core walker's status word (nonzero: it gave up)
+    int *timed_out;     // nullable: set when a step found the status word set
 };
 
 // The goal test of a planner step (one thread): a path that has reached its goal skips the step
@@ -1405,7 +1474,7 @@ __device__ void plan_pre_decide(const PlanArgs &a) {
 __global__ void plan_pre_kernel(const __grid_constant__ PlanArgs a) {
     if (threadIdx.x == 0) {
         plan_pre_decide(a);
-        *a.cursor = 0ull;
+        a.cursor[0] = a.cursor[1] = a.cursor[2] = 0ull;
     }
     __syncthreads();
     unsigned char *acc = (unsigned char *)a.acc;
@@ -1417,7 +1486,11 @@ template <int D>
 __device__ void plan_post_d(const PlanArgs &a) {
     double x[D];
     for (int j = 0; j < D; ++j) x[j] = a.x[j];
-    if (!*a.skip) {
+    if (!*a.skip && a.status != nullptr && *a.status != 0) {  // the walker gave up: stop the path
+        *a.flag = 16;
+        *a.done = 1;
+        if (a.timed_out != nullptr) *a.timed_out = 1;
+    } else if (!*a.skip) {
         int kind;
         int64_t idx;
         const double R = distance<double, D>(a.dom, x, kind, idx);
@@ -1544,6 +1617,8 @@ wos_status enqueue_plan_step(wos_domain_t dom, const Opts &o, double *x, int64_t
     a.cursor = sc.cursor;
     a.grad_row = grad_row;
     a.path_row = path_row;
+    a.status = reinterpret_cast<const int *>(sc.cursor + 2);
+    a.timed_out = done + 2;  // the planner's ints: [done, skip, timed out]
     plan_pre_kernel<<<1, 128, 0, s>>>(a);
     WOS_CUDA(cudaGetLastError());
     Opts os = o;
@@ -1568,7 +1643,7 @@ wos_status wos_plan_step(wos_domain_t dom, const wos_options *opt, double *x, in
     cudaStream_t s = (cudaStream_t)stream;
     if (o.precision == WOS_MIXED) {
         WeightTable t;
-        WOS_TRY(ensure_table(dom, sigma, &t));
+        WOS_TRY(ensure_table(dom, sigma, &t, s, false));
     }
     const int nf = acc_fields(dom->d, dom->n_exp, o.cv, dom->has_source);
     const size_t bytes = scratch_bytes(o.precision, 1, nf) + 256;
@@ -1579,7 +1654,7 @@ wos_status wos_plan_step(wos_domain_t dom, const wos_options *opt, double *x, in
     if (o.precision == WOS_MIXED) carve_mixed(sc, (char *)base + bytes, *dom, 1, n_walks, 1);
     int *ints = reinterpret_cast<int *>((char *)base + bytes - 256);
     wos_status st = WOS_OK;
-    if (cudaMemsetAsync(ints, 0, 2 * sizeof(int), s) != cudaSuccess) st = fail(WOS_ERR_CUDA, "memset");
+    if (cudaMemsetAsync(ints, 0, 3 * sizeof(int), s) != cudaSuccess) st = fail(WOS_ERR_CUDA, "memset");
     if (st == WOS_OK)
         st = enqueue_plan_step(dom, o, x, n_walks, eps, sigma, s_ub, step_idx, ints, ints + 1, flag,
                                sc, grad_out, nullptr, s);
@@ -1601,7 +1676,7 @@ wos_status wos_plan_path(wos_domain_t dom, const wos_options *opt, const double 
     if (n_steps == 0) return WOS_OK;
     if (o.precision == WOS_MIXED) {
         WeightTable t;
-        WOS_TRY(ensure_table(dom, sigma, &t));
+        WOS_TRY(ensure_table(dom, sigma, &t, s, true));
         WOS_TRY(ensure_mixed_smem(mixed_smem_bytes(*dom)));
     }
     const int nf = acc_fields(d, dom->n_exp, o.cv, dom->has_source);
@@ -1618,7 +1693,7 @@ wos_status wos_plan_path(wos_domain_t dom, const wos_options *opt, const double 
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     do {
-        if (cudaMemsetAsync(ints, 0, 2 * sizeof(int), s) != cudaSuccess ||
+        if (cudaMemsetAsync(ints, 0, 3 * sizeof(int), s) != cudaSuccess ||
             cudaMemcpyAsync(x, x0, sizeof(double) * d, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
             st = fail(WOS_ERR_CUDA, "planner setup failed");
             break;
@@ -1648,7 +1723,10 @@ wos_status wos_plan_path(wos_domain_t dom, const wos_options *opt, const double 
         }
         e = cudaGraphLaunch(exec, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        int timed_out = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&timed_out, ints + 2, sizeof(int), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) st = fail(WOS_ERR_CUDA, "planner graph failed: %s", cudaGetErrorString(e));
+        else if (timed_out) st = fail(WOS_ERR_TIMEOUT, "a tensor-core walker wait ran out of its budget");
     } while (0);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -1763,6 +1841,7 @@ extern "C" wos_status wos_debug_weight_table(int32_t d, double z_max, int32_t n,
 struct wos_batch_s {
     std::vector<wos_problem> probs;
     std::vector<const int *> done;  // per problem: nonzero -> no walks (finished planner paths)
+    int *sph_status = nullptr;      // the tensor-core launches' status word (zeroed every run)
     Opts o{};
     wos_batch_config cfg{};
     int grad_any = 0;
@@ -2057,6 +2136,7 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     char *zero = base + off_zero;
     unsigned long long *cursor = (unsigned long long *)(zero + acc_bytes);
     int *sph_status = reinterpret_cast<int *>(cursor + 1);
+    b->sph_status = sph_status;
     unsigned long long *sph_shrinks = cursor + 2;
     unsigned long long *sph_cursors = cursor + 3;  // [d]
     b->d_stats = (wos_stats *)(zero + acc_bytes + ctl_bytes);
@@ -2072,7 +2152,7 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     for (int i = 0; i < n; ++i) {
         const wos_problem &p = b->probs[i];
         WeightTable tab;
-        WOS_TRY(ensure_table(p.domain, p.sigma, &tab));
+        WOS_TRY(ensure_table(p.domain, p.sigma, &tab, nullptr, true));
         double *acc = (double *)(zero + acc_off[i]);
         unsigned long long *cnt = (unsigned long long *)(zero + cnt_off[i]);
         b->acc_ptr[i] = acc;
@@ -2180,6 +2260,8 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         SL.shrinks = sph_shrinks;
         SL.seed = b->o.seed;
         SL.max_steps = b->o.max_steps;
+        SL.wait_budget = b->o.wait_cycles > 0 ? b->o.wait_cycles : kDefaultWaitBudget;
+        SL.wait_hint = wait_hint_ns(SL.wait_budget);
         b->sph.push_back(SL);
         b->sph_grid.push_back((int)std::min<int64_t>((int64_t)cfg.sphere_ctas_per_sm * sms, SL.n_items));
         b->sph_dims.push_back(dd);
@@ -2418,7 +2500,7 @@ wos_status wos_plan_paths(const wos_path_problem *paths, int32_t n_paths, int64_
     for (int i = 0; i < n_paths; ++i) xs += paths[i].domain->d;
     const size_t off_u = align256(sizeof(double) * xs), off_g = off_u + align256(sizeof(double) * n_paths);
     const size_t off_i = off_g + align256(sizeof(double) * xs);
-    const size_t off_r = off_i + align256(sizeof(int) * 2 * n_paths);
+    const size_t off_r = off_i + align256(sizeof(int) * (2 * n_paths + 1));
     const size_t bytes = off_r + sizeof(PathRec) * n_paths;
     char *scr = nullptr;
     WOS_CUDA(cudaMalloc(&scr, bytes));
@@ -2434,7 +2516,7 @@ wos_status wos_plan_paths(const wos_path_problem *paths, int32_t n_paths, int64_
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     do {
-        if (cudaMemsetAsync(ints, 0, sizeof(int) * 2 * n_paths, s) != cudaSuccess) {
+        if (cudaMemsetAsync(ints, 0, sizeof(int) * (2 * n_paths + 1), s) != cudaSuccess) {
             st = fail(WOS_ERR_CUDA, "memset failed");
             break;
         }
@@ -2489,6 +2571,8 @@ wos_status wos_plan_paths(const wos_path_problem *paths, int32_t n_paths, int64_
             a.cv = o.cv;
             a.src = p.domain->has_source;
             a.counts = b->cnt_ptr[i];
+            a.status = b->sph_status;
+            a.timed_out = ints + 2 * n_paths;
             R.flags = p.flags;
             R.grads = p.grads;
             R.path = p.path;
@@ -2534,7 +2618,10 @@ wos_status wos_plan_paths(const wos_path_problem *paths, int32_t n_paths, int64_
         e = cudaGraphInstantiate(&exec, graph, 0);
         if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        int timed_out = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&timed_out, ints + 2 * n_paths, sizeof(int), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) st = fail(WOS_ERR_CUDA, "paths graph failed: %s", cudaGetErrorString(e));
+        else if (timed_out) st = fail(WOS_ERR_TIMEOUT, "a tensor-core walker wait ran out of its budget");
     } while (0);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -2633,7 +2720,7 @@ extern "C" wos_status wos_debug_pointcloud_radius(wos_domain_t dom, const double
     if (Q == 0) return WOS_OK;
     cudaStream_t s = (cudaStream_t)stream;
     WeightTable tab;
-    WOS_TRY(ensure_table(dom, 0.0, &tab));
+    WOS_TRY(ensure_table(dom, 0.0, &tab, s, false));
     const int nf = acc_fields(dom->d, dom->n_exp);
     const size_t bytes = scratch_bytes(WOS_MIXED, Q, nf);
     void *base = nullptr;
@@ -2646,8 +2733,8 @@ extern "C" wos_status wos_debug_pointcloud_radius(wos_domain_t dom, const double
         MixedProblem P = make_mixed_problem(dom, x, Q, 1, 1e-30, 0.0, 0, 0, 0, 0, tab, (double *)sc.acc, sc.counts,
                                             PerWalk{}, nullptr);
         const cudaError_t e = launch_pointcloud(dom->pcd, P, dom->pc_delta, sc.cursor,
-                                                reinterpret_cast<int *>(sc.cursor + 2), sc.cursor + 1, 0, 0, 0, s,
-                                                radius);
+                                                reinterpret_cast<int *>(sc.cursor + 2), sc.cursor + 1, 0, 0, 0, 0,
+                                                s, radius);
         if (e != cudaSuccess) st = fail(WOS_ERR_CUDA, "point-cloud probe failed: %s", cudaGetErrorString(e));
     }
     cudaFreeAsync(base, s);

@@ -13,7 +13,6 @@ namespace wos {
 
 constexpr int kMaxD = WOS_MAX_D;
 constexpr int kMaxExp = WOS_MAX_EXP;
-constexpr int kTableNodes = 8192;  // weight-table nodes per dimension (linear interpolation)
 
 // Component kinds. Tie-break order of the distance query: goal, balls, points, arm, outer ball,
 // box faces (lo_0, hi_0, lo_1, ...).

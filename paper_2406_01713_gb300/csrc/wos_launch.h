@@ -197,8 +197,10 @@ struct SphereLaunch {
     int64_t n_items;
     int64_t walks_per_item;           // implicit items: item i = walks [i wpi, min((i+1) wpi, Q N))
     unsigned long long *item_cursor;  // zero before the launch
-    int *status;                      // nonzero: a wait timed out
+    int *status;                      // nonzero: a wait timed out (1: main loop, 2: teardown)
     unsigned long long *shrinks;      // steps whose radius came from a chunk bound
+    long long wait_budget;            // clock cycles one main-loop wait may take
+    uint32_t wait_hint;               // suspend-time hint of its tests (ns), wait_hint_ns(budget)
     uint64_t seed;
     int64_t max_steps;
     double *radius_out;  // nullable: distance bound at each walk's start (single problem only)
@@ -210,8 +212,14 @@ int sphere_ctas_per_sm();
 // Single problem: implicit items, grid sized to the work.
 cudaError_t launch_pointcloud(const PointCloudDev &pcd, const MixedProblem &P, float delta,
                               unsigned long long *cursor, int *status, unsigned long long *shrinks,
-                              uint64_t seed, int64_t max_steps, int grad, cudaStream_t s,
-                              double *radius_out = nullptr);
+                              uint64_t seed, int64_t max_steps, long long wait_budget, int grad,
+                              cudaStream_t s, double *radius_out = nullptr);
+constexpr long long kDefaultWaitBudget = 4000000000ll;  // clock cycles (~2 s at 2 GHz)
+// Suspend-time hint of a wait's tests: at most 20 us, and about the budget for small budgets (a
+// budget in cycles read as ns at ~2 GHz), so that one test does not outlast a small budget.
+inline uint32_t wait_hint_ns(long long budget) {
+    return budget >= 40000ll ? 20000u : (budget >= 64ll ? (uint32_t)(budget / 2) : 32u);
+}
 constexpr int kPointCloudMaxD = 12;  // 3d + 2 BF16 columns fit a 32- or 48-wide contraction
 // Ball sets at least this large run on the tensor cores: the measured crossover of the two
 // walkers (u and grad u, 64 queries x 16384 walks per ball set) lies near 160 balls at d = 3,

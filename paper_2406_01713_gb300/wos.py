@@ -27,7 +27,7 @@ def _stream():
 
 
 def _opts(precision="mixed", seed=0, walk_offset=0, max_steps=10000, laplace=False, control_variate=False,
-          cuda_core_balls=False, roulette=0.0, antithetic=False):
+          cuda_core_balls=False, roulette=0.0, antithetic=False, wait_cycles=0):
     o = _lib.Options()
     o.precision = _lib.PRECISION[precision] if isinstance(precision, str) else int(precision)
     o.flags = ((_lib.WOS_FLAG_LAPLACE_FACTOR if laplace else 0) |
@@ -38,6 +38,7 @@ def _opts(precision="mixed", seed=0, walk_offset=0, max_steps=10000, laplace=Fal
     o.walk_offset = int(walk_offset)
     o.max_steps = int(max_steps)
     o.roulette_w = float(roulette)
+    o.wait_cycles = int(wait_cycles)
     return o
 
 
@@ -59,9 +60,11 @@ def stats_dict(t):
 
 
 class Domain:
-    """A domain on the device (wos_domain_create). See synth.py for the dict keys."""
+    """A domain on the device (wos_domain_create). See synth.py for the dict keys. sigma_max > 0
+    builds the mixed-precision weight tables for every sigma up to it here, so that no later
+    call allocates one."""
 
-    def __init__(self, dom):
+    def __init__(self, dom, sigma_max=None):
         L = _lib.load()
         d = int(dom["d"])
         self.d = d
@@ -115,6 +118,7 @@ class Domain:
             ob = arr("arm_obs", (-1, 2))
             s.n_arm_obs = ob.shape[0]
             s.arm_obs = p(ob)
+        s.sigma_max = float(sigma_max if sigma_max is not None else dom.get("sigma_max", 0.0))
         self.n_exp = int(s.n_exp)
         self.n_balls = int(s.n_balls)
         self.n_points = int(s.n_points)
@@ -137,15 +141,15 @@ class Domain:
     # ----------------------------------------------------------------- estimators
     def solve(self, x, n_walks, eps, sigma, precision="mixed", seed=0, walk_offset=0,
               max_steps=10000, laplace=False, with_stats=False, cuda_core_balls=False, roulette=0.0,
-              antithetic=False):
+              antithetic=False, wait_cycles=0):
         L = _lib.load()
         x = _dev_f64(x, self.d)
         Q = x.shape[0]
         u = torch.empty(Q, dtype=torch.float64, device=x.device)
         se = torch.empty_like(u)
-        st = torch.zeros(6, dtype=torch.int64, device=x.device) if with_stats else None
+        st = torch.zeros(len(_lib.STATS_FIELDS), dtype=torch.int64, device=x.device) if with_stats else None
         o = _opts(precision, seed, walk_offset, max_steps, laplace, cuda_core_balls=cuda_core_balls,
-                  roulette=roulette, antithetic=antithetic)
+                  roulette=roulette, antithetic=antithetic, wait_cycles=wait_cycles)
         _lib.check(L.wos_solve(self.h, ctypes.byref(o), _ptr(x), Q, int(n_walks), float(eps),
                                float(sigma), _ptr(u), _ptr(se), _ptr(st), _stream()), "wos_solve")
         out = {"u": u, "u_se": se}
@@ -155,7 +159,7 @@ class Domain:
 
     def grad(self, x, n_walks, eps, sigma, precision="mixed", seed=0, walk_offset=0,
              max_steps=10000, laplace=False, with_stats=False, control_variate=False, cuda_core_balls=False,
-             roulette=0.0, antithetic=False):
+             roulette=0.0, antithetic=False, wait_cycles=0):
         """u, grad u (first-sphere estimator; control_variate=True subtracts the walks' mean
         value, WOS_FLAG_GRAD_CONTROL_VARIATE), their SEs, du/dsigma and du/dw per query."""
         L = _lib.load()
@@ -165,9 +169,9 @@ class Domain:
         out = {"u": torch.empty(Q, **f), "u_se": torch.empty(Q, **f), "grad": torch.empty(Q, d, **f),
                "grad_se": torch.empty(Q, d, **f), "du_dsigma": torch.empty(Q, **f),
                "du_dw": torch.empty(Q, self.n_exp, **f) if self.n_exp else None}
-        st = torch.zeros(6, dtype=torch.int64, device=x.device) if with_stats else None
+        st = torch.zeros(len(_lib.STATS_FIELDS), dtype=torch.int64, device=x.device) if with_stats else None
         o = _opts(precision, seed, walk_offset, max_steps, laplace, control_variate, cuda_core_balls, roulette,
-                  antithetic)
+                  antithetic, wait_cycles)
         _lib.check(L.wos_grad(self.h, ctypes.byref(o), _ptr(x), Q, int(n_walks), float(eps), float(sigma),
                               _ptr(out["u"]), _ptr(out["u_se"]), _ptr(out["grad"]), _ptr(out["grad_se"]),
                               _ptr(out["du_dsigma"]), _ptr(out["du_dw"]), _ptr(st), _stream()),
@@ -178,7 +182,7 @@ class Domain:
 
     def walks(self, x, n_walks, eps, sigma, grad_mode=False, precision="mixed", seed=0,
               walk_offset=0, max_steps=10000, laplace=False, cuda_core_balls=False, roulette=0.0,
-              antithetic=False):
+              antithetic=False, wait_cycles=0):
         """Per-walk terminals, jump counts, gradient estimates and d/dsigma (parity checks)."""
         L = _lib.load()
         x = _dev_f64(x, self.d)
@@ -187,7 +191,7 @@ class Domain:
         out = {"term": torch.empty(Q, N, **f), "jumps": torch.empty(Q, N, dtype=torch.int64, device=x.device),
                "grad": torch.empty(Q, N, d, **f), "dsigma": torch.empty(Q, N, **f)}
         o = _opts(precision, seed, walk_offset, max_steps, laplace, cuda_core_balls=cuda_core_balls,
-                  roulette=roulette, antithetic=antithetic)
+                  roulette=roulette, antithetic=antithetic, wait_cycles=wait_cycles)
         _lib.check(L.wos_walks(self.h, ctypes.byref(o), _ptr(x), Q, N, float(eps), float(sigma),
                                int(bool(grad_mode)), _ptr(out["term"]), _ptr(out["jumps"]),
                                _ptr(out["grad"]), _ptr(out["dsigma"]), _stream()), "wos_walks")
@@ -195,21 +199,23 @@ class Domain:
 
     # ----------------------------------------------------------------- planner
     def plan_step(self, x, n_walks, eps, sigma, s_ub, step_idx, precision="mixed", seed=0,
-                  walk_offset=0, max_steps=10000, control_variate=False, roulette=0.0, antithetic=False):
+                  walk_offset=0, max_steps=10000, control_variate=False, roulette=0.0, antithetic=False,
+                  wait_cycles=0):
         """One step in place on the device tensor x (d doubles); returns (flag, grad)."""
         L = _lib.load()
         assert x.dtype == torch.float64 and x.is_cuda and x.numel() == self.d and x.is_contiguous()
         flag = torch.zeros(1, dtype=torch.int32, device=x.device)
         g = torch.empty(self.d, dtype=torch.float64, device=x.device)
         o = _opts(precision, seed, walk_offset, max_steps, control_variate=control_variate, roulette=roulette,
-                  antithetic=antithetic)
+                  antithetic=antithetic, wait_cycles=wait_cycles)
         _lib.check(L.wos_plan_step(self.h, ctypes.byref(o), _ptr(x), int(n_walks), float(eps), float(sigma),
                                    float(s_ub), int(step_idx), _ptr(flag), _ptr(g), _stream()),
                    "wos_plan_step")
         return flag, g
 
     def plan_path(self, x0, n_steps, n_walks, eps, sigma, s_ub, precision="mixed", seed=0,
-                  walk_offset=0, max_steps=10000, control_variate=False, roulette=0.0, antithetic=False):
+                  walk_offset=0, max_steps=10000, control_variate=False, roulette=0.0, antithetic=False,
+                  wait_cycles=0):
         """n_steps planner steps replayed as one CUDA graph: (path, flags, grads) on the device."""
         L = _lib.load()
         x0 = _dev_f64(x0).reshape(-1)
@@ -219,7 +225,7 @@ class Domain:
         flags = torch.zeros(n_steps, dtype=torch.int32, device=x0.device)
         grads = torch.zeros(n_steps, d, **f)
         o = _opts(precision, seed, walk_offset, max_steps, control_variate=control_variate, roulette=roulette,
-                  antithetic=antithetic)
+                  antithetic=antithetic, wait_cycles=wait_cycles)
         _lib.check(L.wos_plan_path(self.h, ctypes.byref(o), _ptr(x0), int(n_steps), int(n_walks), float(eps),
                                    float(sigma), float(s_ub), _ptr(path), _ptr(flags), _ptr(grads),
                                    _stream()), "wos_plan_path")
@@ -257,7 +263,7 @@ def backward(gout, grad, du_dsigma=None, du_dw=None):
 
 
 def plan_paths(paths, n_steps, seed=0, walk_offset=0, max_steps=10000, control_variate=False, roulette=0.0,
-               antithetic=False):
+               antithetic=False, wait_cycles=0):
     """Many planner paths in one CUDA graph (wos_plan_paths): paths is a list of dicts
     {domain: Domain, x0, n_walks, eps, sigma, s_ub}; returns [(path, flags, grads)] on the device,
     each equal to Domain.plan_path with the same arguments (mixed precision)."""
@@ -284,7 +290,7 @@ def plan_paths(paths, n_steps, seed=0, walk_offset=0, max_steps=10000, control_v
         a.flags = flags.data_ptr()
         a.grads = grads.data_ptr()
     o = _opts("mixed", seed, walk_offset, max_steps, control_variate=control_variate, roulette=roulette,
-              antithetic=antithetic)
+              antithetic=antithetic, wait_cycles=wait_cycles)
     _lib.check(L.wos_plan_paths(arr, len(paths), int(n_steps), ctypes.byref(o), _stream()), "wos_plan_paths")
     return [(p, f, g) for p, f, g, _ in out]
 
@@ -327,7 +333,7 @@ class Batch:
     """
 
     def __init__(self, problems, seed=0, max_steps=10000, config=None, control_variate=False, roulette=0.0,
-                 antithetic=False):
+                 antithetic=False, wait_cycles=0):
         L = _lib.load()
         self.problems = problems
         f = dict(dtype=torch.float64, device="cuda")
@@ -373,7 +379,7 @@ class Batch:
         self.n_x, self.n_q, self.n_g = ox, oq, og
         self._arr = arr
         opts = _opts("mixed", seed, 0, max_steps, control_variate=control_variate, roulette=roulette,
-                     antithetic=antithetic)
+                     antithetic=antithetic, wait_cycles=wait_cycles)
         cfg = None
         if config is not None:
             cfg = _lib.BatchConfig(int(config["threads"]), int(config["ctas_per_sm"]), int(config["item_work"]),
@@ -384,7 +390,7 @@ class Batch:
                                       ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(h)),
                    "wos_batch_create")
         self.h = h
-        self.stats = torch.zeros(6, dtype=torch.int64, device="cuda")
+        self.stats = torch.zeros(len(_lib.STATS_FIELDS), dtype=torch.int64, device="cuda")
 
     def run(self, with_stats=True):
         L = _lib.load()

@@ -30,7 +30,7 @@ def _call(fn, dom, opts, X, N, eps, sigma):
     Q = X.shape[0]
     u = torch.full((Q,), float("nan"), dtype=torch.float64, device="cuda")
     se = torch.full((Q,), float("nan"), dtype=torch.float64, device="cuda")
-    st = torch.zeros(6, dtype=torch.int64, device="cuda")
+    st = torch.zeros(len(_lib.STATS_FIELDS), dtype=torch.int64, device="cuda")
     stream = VP(torch.cuda.current_stream().cuda_stream)
     rc = fn(dom.h, ctypes.byref(opts), VP(X.data_ptr()), Q, N, eps, sigma, VP(u.data_ptr()),
             VP(se.data_ptr()), VP(st.data_ptr()), stream)
