@@ -140,6 +140,8 @@ def lib():
             L.or_bessel_K.restype = ctypes.c_double
             L.or_ball_green.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_int, _PD, _PD]
+            L.or_ball_green_dsigma.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            L.or_ball_green_dsigma.restype = ctypes.c_double
             L.or_distance.argtypes = [ctypes.POINTER(_Domain), _PD, _PI32, _PI64, _PD]
             L.or_distance.restype = ctypes.c_double
             L.or_walk.argtypes = [ctypes.POINTER(_Domain), _PD, ctypes.c_uint64, ctypes.c_double,
@@ -310,6 +312,11 @@ def ball_green(d, sigma, r, R, free_space=False):
     lib().or_ball_green(int(d), float(sigma), float(r), float(R), int(bool(free_space)), ctypes.byref(G),
                         ctypes.byref(F))
     return G.value, F.value
+
+
+def ball_green_dsigma(d, sigma, r, R):
+    """d/dsigma of the ball's Green's function between its centre and a point at distance r."""
+    return lib().or_ball_green_dsigma(int(d), float(sigma), float(r), float(R))
 
 
 def distance(dom, x):

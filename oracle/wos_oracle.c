@@ -33,6 +33,11 @@
  *       and at sigma = 0: G_B = (r^(2-d) - R^(2-d)) / ((d-2) |S^(d-1)|) (ln(R/r)/(2 pi) for d = 2),
  *       grad_x G_B = (z - x)/|S^(d-1)| (r^-d - R^-d). K_nu from its integral
  *       int_0^inf exp(-x cosh t) cosh(nu t) dt (DLMF 10.32.9) by the trapezoidal rule.
+ *       du/dsigma per walk (the walk geometry does not depend on sigma): the boundary part times
+ *       the summed d log C / d sigma, plus, for each source contribution, q times the weight so
+ *       far times (dG_B/dsigma + G_B times the d log C / d sigma of the steps before); dG_B/dsigma
+ *       from the Bessel derivative identities (sigma > 0) and from the first-order term of G_B in
+ *       sigma (sigma = 0), see or_ball_green_dsigma.
  *   Closest boundary point xbar (Fig. 2): g is read at the projection of x_k on the nearest
  *       boundary component.
  *   Planner (Sec. III screened-harmonic paths; Sec. VII adaptive step):
@@ -287,6 +292,39 @@ void or_ball_green(int d, double sigma, double r, double R, int free_space, doub
          (or_bessel_K(nu + 1.0, k * r) - (free_space ? 0.0 : or_bessel_K(nu + 1.0, k * R) * ratio1));
 }
 
+/* d/dsigma of G_B (or_ball_green) between the centre and a point at distance r, 0 < r < R.
+ * sigma > 0: with k = sqrt(sigma), c0 = k^nu / (2 pi)^(d/2) and A(k) = K_nu(kr) - K_nu(kR) Q(k),
+ * Q = I_nu(kr) / I_nu(kR), G = c0 r^-nu A, so dG/dk = (nu/k) G + c0 r^-nu A'(k), using
+ * K_nu'(x) = -K_{nu+1}(x) + (nu/x) K_nu(x) (DLMF 10.29.2) and I_nu'(x) / I_nu(x) =
+ * I_{nu+1}(x) / I_nu(x) + nu/x with I_{nu+1}(x) / I_nu(x) = x S_{nu+1}(x) / (2 (nu+1) S_nu(x))
+ * (DLMF 10.29.2, 10.25.2); dG/dsigma = (dG/dk) / (2k).
+ * sigma = 0: G = G_0 - sigma w + O(sigma^2), where w solves -Laplace(w) = G_0 in the ball with
+ * w = 0 on the sphere (differentiate Laplace(G) - sigma G = -delta in sigma); G_0 is radial,
+ * so w is the radial solution of (rho^(d-1) w')' = -rho^(d-1) G_0(rho), integrated twice. */
+double or_ball_green_dsigma(int d, double sigma, double r, double R)
+{
+    const double nu = 0.5 * d - 1.0;
+    const double omega = 2.0 * pow(OR_PI, 0.5 * d) / tgamma(0.5 * d);
+    if (sigma == 0.0) {
+        if (d == 2) return (0.25 * r * r * log(R / r) + 0.25 * (r * r - R * R)) / (2.0 * OR_PI);
+        if (d == 4) return (-0.5 * log(R / r) - r * r / (8.0 * R * R) + 0.125) / (2.0 * omega);
+        const double a = 1.0 / (2.0 * (4.0 - d)), b = 1.0 / (2.0 * d);
+        return (a * pow(r, 4.0 - d) - b * r * r * pow(R, 2.0 - d) - (a - b) * pow(R, 4.0 - d)) / ((d - 2.0) * omega);
+    }
+    const double k = sqrt(sigma);
+    const double c0 = pow(k, nu) / pow(2.0 * OR_PI, 0.5 * d);
+    const double Ka0 = or_bessel_K(nu, k * r), Ka1 = or_bessel_K(nu + 1.0, k * r);
+    const double Kb0 = or_bessel_K(nu, k * R), Kb1 = or_bessel_K(nu + 1.0, k * R);
+    const double Sa0 = or_series_S(nu, k * r), Sa1 = or_series_S(nu + 1.0, k * r);
+    const double Sb0 = or_series_S(nu, k * R), Sb1 = or_series_S(nu + 1.0, k * R);
+    const double Q = pow(r / R, nu) * Sa0 / Sb0;
+    const double A = Ka0 - Kb0 * Q;
+    const double dQ = Q * k / (2.0 * (nu + 1.0)) * (r * r * Sa1 / Sa0 - R * R * Sb1 / Sb0);
+    const double dA = -r * Ka1 + (nu / k) * Ka0 - Q * (-R * Kb1 + (nu / k) * Kb0) - Kb0 * dQ;
+    const double dGdk = c0 * pow(r, -nu) * ((nu / k) * A + dA);
+    return dGdk / (2.0 * k);
+}
+
 /* d/dsigma log C_nu(R sqrt(sigma)) = -(R^2 / (2d)) S_{nu+1}(z) / S_nu(z), d = 2 nu + 2. */
 double or_dsigma_log_C(double nu, double R, double sigma)
 {
@@ -465,6 +503,7 @@ void or_walk(const or_domain *D, const double *x0, uint64_t walk, double eps, do
     double x[OR_MAXD], xbar[OR_MAXD], v[OR_MAXD], v0[OR_MAXD];
     double logw = 0.0, dsig = 0.0, R0 = 0.0, z0 = 0.0, logC0 = 0.0;
     double src = 0.0, src0 = 0.0; /* source contributions: all steps, and step 0 alone */
+    double dsrc = 0.0;            /* d/dsigma of the source contributions */
     int64_t k = 0;
     int32_t kind = -1;
     int64_t index = -1;
@@ -516,6 +555,9 @@ void or_walk(const or_domain *D, const double *x0, uint64_t walk, double eps, do
                 or_ball_green(d, sigma, r, R, opt->plant_free_space_source_grad, &G, &F);
                 const double c = D->source_q * exp(logw) * G;
                 src += c;
+                /* its sigma derivative along the walk: the weight's (the sum of d log C / d sigma
+                 * of the steps before) and the Green's function's */
+                dsrc += D->source_q * exp(logw) * (dsig * G + or_ball_green_dsigma(d, sigma, r, R));
                 if (k == 0) {
                     src0 = c;
                     for (int j = 0; j < d; ++j) out->gsrc[j] = D->source_q * F * (D->source_z[j] - x[j]) / r;
@@ -547,8 +589,10 @@ void or_walk(const or_domain *D, const double *x0, uint64_t walk, double eps, do
     out->jumps = k;
     out->comp_kind = kind;
     out->comp_index = index;
-    /* d/dsigma of the source part is not estimated: NaN marks it */
-    out->dsigma = D->has_source ? NAN : out->term * dsig;
+    /* d/dsigma of the walk's value: its boundary part times the summed d log C / d sigma, plus
+     * the source contributions' derivatives (the walk geometry does not depend on sigma); a
+     * capped walk contributes 0 */
+    out->dsigma = out->capped ? 0.0 : (out->term - src) * dsig + dsrc;
     if (k > 0) {
         /* u^(x_1) = term / C(R0);  alpha(R0) = (d/R0) C_{nu+1}(z0);  G = alpha(R0) / C(R0) */
         double factor = opt->laplace_factor ? (double)d / R0

@@ -524,9 +524,99 @@ def _source_case(oracle_mod, d, sigma, planted=False, control_variate=False):
 def test_centred_impulse_source_in_a_ball(oracle_mod, d, sigma):
     ok_u, ok_g, res = _source_case(oracle_mod, d, sigma)
     assert ok_u and ok_g
-    assert np.all(np.isnan(res["du_dsigma"]))  # not estimated with a source
     ok_u, ok_g, _ = _source_case(oracle_mod, d, sigma, control_variate=True)
     assert ok_u and ok_g
+
+
+def _scipy_ball_green(d, sigma, r, R):
+    """G_B between the centre and distance r, written with scipy's I and K (sigma > 0)."""
+    k, nu = math.sqrt(sigma), d / 2 - 1
+    return _c0(d, sigma) * r ** -nu * (special.kv(nu, k * r) - special.kv(nu, k * R) * special.iv(nu, k * r)
+                                       / special.iv(nu, k * R))
+
+
+def test_ball_green_dsigma(oracle_mod):
+    # d = 3 closed form G = sinh(k (R - r)) / (4 pi r sinh(k R)), differentiated symbolically
+    sp = pytest.importorskip("sympy")
+    s_, r_, R_ = sp.symbols("s r R", positive=True)
+    G3 = sp.sinh(sp.sqrt(s_) * (R_ - r_)) / (4 * sp.pi * r_ * sp.sinh(sp.sqrt(s_) * R_))
+    dG3 = sp.lambdify((s_, r_, R_), sp.diff(G3, s_))
+    for sigma in (0.3, 4.0, 25.0):
+        for r in (0.05, 0.4, 0.9):
+            want = dG3(sigma, r, 1.2)
+            assert abs(oracle_mod.ball_green_dsigma(3, sigma, r, 1.2) - want) < 1e-12 * abs(want)
+    # every d: central differences of scipy's form (sigma > 0) and one-sided ones at sigma = 0
+    # against the Laplace limit (the first-order term of G_B in sigma)
+    for d in range(2, 8):
+        for r in (0.1, 0.6):
+            for sigma in (2.0, 30.0):
+                h = 1e-4 * sigma
+                fd = (_scipy_ball_green(d, sigma + h, r, 1.0) - _scipy_ball_green(d, sigma - h, r, 1.0)) / (2 * h)
+                assert abs(oracle_mod.ball_green_dsigma(d, sigma, r, 1.0) - fd) < 1e-6 * abs(fd)
+            h = 1e-4
+            fd = (-3 * oracle_mod.ball_green(d, 0.0, r, 1.0)[0] + 4 * _scipy_ball_green(d, h, r, 1.0)
+                  - _scipy_ball_green(d, 2 * h, r, 1.0)) / (2 * h)
+            assert abs(oracle_mod.ball_green_dsigma(d, 0.0, r, 1.0) - fd) < 1e-5 * abs(fd)
+
+
+def _source_exp_domain(d):
+    """Unit ball with two ball obstacles, exp data (|a|^2 = 4) on the whole boundary and an
+    impulse source: u has a boundary part and a source part."""
+    rng = np.random.default_rng(70 + d)
+    a = rng.standard_normal(d)
+    a *= 2.0 / np.linalg.norm(a)
+    c = np.zeros((2, d))
+    c[0, 0], c[1, 1] = 0.5, -0.45
+    z = np.zeros(d)
+    z[0] = -0.3
+    return {"d": d, "outer_c": np.zeros(d), "outer_r": 1.0, "ball_c": c, "ball_r": np.array([0.15, 0.1]),
+            "exp_w": np.ones(1), "exp_a": a[None, :], "source_z": z, "source_q": 0.7}
+
+
+@pytest.mark.parametrize("d,sigma", [(2, 0.0), (2, 3.0), (3, 0.0), (3, 6.0), (5, 2.0)])
+def test_source_dsigma_crn_finite_difference(oracle_mod, d, sigma):
+    # the walk geometry does not depend on sigma, so each walk's value is a smooth function of
+    # sigma and its estimated derivative must equal the difference quotient of the same walk
+    dom = _source_exp_domain(d)
+    X = np.array([[0.1] + [0.2] * (d - 1), [-0.5] + [0.0] * (d - 1)])
+    N, eps, seed = 300, 1e-4, 11
+
+    def term(s):
+        return oracle_mod.solve(dom, X, N, eps, s, seed, per_walk=True)["walk_term"]
+
+    ref = oracle_mod.solve(dom, X, N, eps, sigma, seed, per_walk=True)
+    h = 1e-5
+    if sigma == 0.0:
+        fd = (-3 * ref["walk_term"] + 4 * term(h) - term(2 * h)) / (2 * h)
+    else:
+        fd = (term(sigma + h) - term(sigma - h)) / (2 * h)
+    got = ref["walk_dsigma"]
+    assert np.all(np.isfinite(got))
+    assert np.abs(got - fd).max() <= 1e-5 * np.abs(fd).max()
+    assert np.allclose(ref["du_dsigma"], got.mean(axis=1), rtol=1e-12, atol=1e-15)
+    # the source part matters: without it the derivative is visibly different
+    nosrc = {k: v for k, v in dom.items() if k not in ("source_z", "source_q")}
+    base = oracle_mod.solve(nosrc, X, N, eps, sigma, seed)
+    assert np.abs(ref["du_dsigma"] - base["du_dsigma"]).max() > 1e-3
+
+
+@pytest.mark.parametrize("d,sigma", [(2, 4.0), (3, 0.0), (3, 9.0)])
+def test_centred_source_dsigma_closed_form(oracle_mod, d, sigma):
+    # Omega = B(0, 1), unit impulse at the centre: u = G_Omega(x, 0); du/dsigma from scipy's form
+    # by central differences (one-sided at sigma = 0, from the Laplace value)
+    dom = {"d": d, "outer_c": np.zeros(d), "outer_r": 1.0, "source_z": np.zeros(d), "source_q": 1.0}
+    X = np.array([[0.3] + [0.0] * (d - 1), [0.0, 0.6] + [0.0] * (d - 2)])
+    res = oracle_mod.solve(dom, X, 20000, 1e-6, sigma, seed=5 + d, per_walk=True)
+    se = res["walk_dsigma"].std(axis=1, ddof=1) / math.sqrt(20000)
+    for q in range(2):
+        r = float(np.linalg.norm(X[q]))
+        h = 1e-4
+        if sigma == 0.0:
+            want = (-3 * _centred_source_solution(d, 0.0, 1.0, X[q])[0] + 4 * _scipy_ball_green(d, h, r, 1.0)
+                    - _scipy_ball_green(d, 2 * h, r, 1.0)) / (2 * h)
+        else:
+            want = (_scipy_ball_green(d, sigma + h, r, 1.0) - _scipy_ball_green(d, sigma - h, r, 1.0)) / (2 * h)
+        assert abs(res["du_dsigma"][q] - want) < 4.5 * se[q] + 1e-4 * abs(want)
 
 
 def test_planted_free_space_source_gradient_is_rejected(oracle_mod):
