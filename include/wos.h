@@ -186,8 +186,11 @@ typedef struct {
  * Each step whose largest empty ball B(x_k, R_k) contains the source adds q G_B(x_k, source_z)
  * times the walk's weight so far, G_B the Green's function of that ball with zero boundary
  * values (Yukawa potential minus its image part; logarithm / power laws at sigma = 0); the
- * first-sphere gradient adds q grad_x G_B(x_0, source_z). du_dsigma is NaN for such domains
- * (its source part is not estimated); du_dw is unaffected. Every walker has the source term
+ * first-sphere gradient adds q grad_x G_B(x_0, source_z). du_dsigma differentiates each walk's
+ * value (the walk geometry does not depend on sigma): each source contribution adds q times the
+ * weight so far times dG_B/dsigma plus G_B times the d log C / d sigma of the steps before
+ * (dG_B/dsigma from the Bessel derivative identities, DLMF 10.29.2; at sigma = 0 from the
+ * first-order term of G_B in sigma); du_dw is unaffected. Every walker has the source term
  * (the tensor-core sphere-set walker too: point sets and large ball sets).
  */
 

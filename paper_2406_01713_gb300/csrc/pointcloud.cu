@@ -320,10 +320,12 @@ __device__ __forceinline__ void write_row(unsigned char *A, int r, const float (
 // memory.
 template <int D>
 __device__ __noinline__ float sphere_source(const MixedProblem &P, long long q, int k, float r, float R, float2 tR,
-                                            float logw) {
-    float G, F;
-    source_green_f32<D>(P, r, R, tR, G, F);
-    const float c = P.source_q * expf(logw) * G;
+                                            float logw, float dsig, float &dc) {
+    float G, F, dG;
+    source_green_f32<D>(P, r, R, tR, G, F, dG);
+    const float qw = P.source_q * expf(logw);
+    const float c = qw * G;
+    dc = qw * fmaf(dsig, G, dG);  // d c / d sigma: the weight's and G_B's
     if (k == 0 && P.src) {
         double *sp = P.acc + q * acc_fields(D, P.n_exp, P.cv, 1) + src_field(D, P.n_exp, P.cv);
         sp[0] = (double)c;
@@ -480,6 +482,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
         for (int i = 0; i < D; ++i) x[i] = 0.f;
         float logw = 0.f, dsig = 0.f, gfac0 = 0.f;
         float src = 0.f, src0 = 0.f;  // impulse source: contributions so far, and the step-0 one
+        float dsrc = 0.f;             // and their d / d sigma
         int k = 0;
         long long j = -1, q = 0;
         bool active = false;
@@ -502,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                         q = j / P.N;
 #pragma unroll
                         for (int i = 0; i < D; ++i) x[i] = (float)__ldg(P.x + q * D + i);
-                        logw = dsig = gfac0 = src = src0 = 0.f;
+                        logw = dsig = gfac0 = src = src0 = dsrc = 0.f;
                         k = 0;
                     }
                 }
@@ -781,8 +784,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                     for (int i = 0; i < D; ++i) rr = fmaf(P.source_z[i] - x[i], P.source_z[i] - x[i], rr);
                     const float rz = sqrtf(rr);
                     if (rz > 0.f && rz < R) {
-                        const float c = sphere_source<D>(P, q, k, rz, R, tb, logw);
+                        float dc;
+                        const float c = sphere_source<D>(P, q, k, rz, R, tb, logw, dsig, dc);
                         src += c;
+                        dsrc += dc;
                         if (k == 0) src0 = c;
                     }
                 }
@@ -875,11 +880,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             // control variate: G = alpha(R0)/C(R0), one number per query (every walk writes it)
             if (cv_walk && gfac0 != 0.f)
                 P.acc[q * acc_fields(D, P.n_exp, P.cv, P.src) + cv_field(D, P.n_exp) + 3 * D] = (double)gfac0;
-            write_record<D>(P, j, outcome, k, term, dsig, gt, GRAD && need_v0, v0, e);
+            // d term / d sigma: the boundary part times the summed d log C / d sigma, plus the
+            // source contributions' derivatives (a capped walk has value 0)
+            const float dv = SRC ? (outcome == 2 ? 0.f : fmaf(term - src, dsig, dsrc)) : term * dsig;
+            write_record<D>(P, j, outcome, k, term, dv, gt, GRAD && need_v0, v0, e);
             if (P.w_term != nullptr) P.w_term[j] = outcome == 3 ? (double)CUDART_NAN : (double)term;
             if (P.w_jumps != nullptr) P.w_jumps[j] = k;
             if (P.w_dsigma != nullptr)
-                P.w_dsigma[j] = (SRC && P.has_source) ? (double)CUDART_NAN : (double)(term * dsig);
+                P.w_dsigma[j] = outcome == 3 ? (double)CUDART_NAN : (double)dv;
             if (P.w_grad != nullptr) {
                 // with a source, the per-query source part of the gradient (stored at step 0)
                 const double *sp = (SRC && P.src) ? P.acc + q * acc_fields(D, P.n_exp, P.cv, 1) + src_field(D, P.n_exp, P.cv)

@@ -79,6 +79,7 @@ struct MixedWalker {
     f32x2 x2[D];              // position as packed pairs (x_j, x_j)
     float logw, dsig, gfac0;  // gfac0 = alpha(R0) / C(R0); v0 is regenerated from its counter
     float src, src0;          // impulse source: contributions so far, and the step-0 one
+    float dsrc;               // d/dsigma of the source contributions
     int k;
     unsigned j;      // walk index within the problem
     long long q;     // query
@@ -389,16 +390,16 @@ __device__ __forceinline__ float terminal_value(const MixedProblem &P, const flo
 }
 
 // Writes the record of one finished walk (layout at rec_words): one 16-byte store of
-// [term, dsigma, gt, info], the first direction when the reduction needs it, and the du/dw terms
-// when the walk has a value.
+// [term, dv, gt, info] (dv: d term / d sigma), the first direction when the reduction needs it,
+// and the du/dw terms when the walk has a value.
 template <int D>
 __device__ __forceinline__ void write_record(const MixedProblem &P, long long j, int outcome, int k, float term,
-                                             float dsig, float gt, bool has_v0, const float (&v0)[D],
+                                             float dv, float gt, bool has_v0, const float (&v0)[D],
                                              const float (&e)[kMaxExp]) {
     if (P.rec == nullptr) return;
     float *r = P.rec + j * P.rec_words;
     const unsigned info = ((unsigned)k & kRecKMask) | ((unsigned)outcome << kRecOutcomeShift) | (has_v0 ? kRecHasV0 : 0u);
-    *reinterpret_cast<float4 *>(r) = make_float4(term, dsig, gt, __uint_as_float(info));
+    *reinterpret_cast<float4 *>(r) = make_float4(term, dv, gt, __uint_as_float(info));
     if (has_v0) {  // only gradient walks (grad_mode) have the v0 words
 #pragma unroll
         for (int i = 0; i + 3 < D; i += 4) *reinterpret_cast<float4 *>(r + 4 + i) = make_float4(v0[i], v0[i + 1], v0[i + 2], v0[i + 3]);
@@ -440,6 +441,7 @@ __device__ __forceinline__ void start_walk(const MixedProblem &P, MixedWalker<D>
     W.gfac0 = 0.f;
     W.src = 0.f;
     W.src0 = 0.f;
+    W.dsrc = 0.f;
     W.k = 0;
 }
 
@@ -464,6 +466,49 @@ __device__ __forceinline__ void log_bessel_K_pair_f32(float nu, float x, float &
     l1 = m + logf(0.5f * h * s1);
 }
 
+// log K_{|nu-1|}(x), log K_nu(x) and log K_{nu+1}(x) by the same rule (for dG_B/dsigma).
+__device__ __forceinline__ void log_bessel_K_triple_f32(float nu, float x, float &lm, float &l0, float &l1) {
+    const float mu = nu + 1.f, mm = fabsf(nu - 1.f);
+    const float ts = asinhf(mu / x);
+    const float m = mu * ts - x * coshf(ts);
+    const float h = fminf(0.5f, 1.1f * rsqrtf(x));
+    float sm = 0.f, s0 = 0.f, s1 = 0.f;
+    for (int i = 0; i < 512; ++i) {
+        const float t = h * (float)i, c = x * coshf(t), w = i == 0 ? 0.5f : 1.f;
+        const float e1 = mu * t - c - m;
+        s1 += w * (expf(e1) + expf(-mu * t - c - m));
+        s0 += w * (expf(nu * t - c - m) + expf(-nu * t - c - m));
+        sm += w * (expf(mm * t - c - m) + expf(-mm * t - c - m));
+        if (t > ts && e1 < -18.f) break;
+    }
+    lm = m + logf(0.5f * h * sm);
+    l0 = m + logf(0.5f * h * s0);
+    l1 = m + logf(0.5f * h * s1);
+}
+
+// dG_B/dsigma between the centre and distance r, FP32 forms without cancellation.
+//   sigma = 0: minus the radial solution w1 of -Laplace(w1) = G_0 with w1 = 0 on the sphere.
+//   d = 2, kR < 0.15: -w1 + 2 sigma w2 with -Laplace(w2) = w1 (G_B = G_0 - sigma w1 + sigma^2 w2
+//     - ...), truncation below 1e-4 of the derivative's size.
+//   otherwise: dG/dsigma = c0 r^-nu K_nu(kr) / (2k) times
+//     [-r K_{nu-1}(kr)/K_nu(kr) + R X K_{nu-1}(kR)/K_nu(kR) - X k (r^2 s(kr) - R^2 s(kR))/(2(nu+1))],
+//     X = K_nu(kR) Q / K_nu(kr), Q = I_nu(kr)/I_nu(kR), s = S_{nu+1}/S_nu: the derivative of
+//     c0 r^-nu [K_nu(kr) - K_nu(kR) Q] in k with K_nu' = -K_{nu-1} - (nu/x) K_nu (DLMF 10.29.2),
+//     which is K_nu' = -K_{nu+1} + (nu/x) K_nu rewritten by the recurrence so that the 1/k terms
+//     cancel analytically; K_{nu-1} = K_{|nu-1|}.
+template <int D>
+__device__ __forceinline__ float source_green_dsigma0_f32(float inv_omega, float r, float R) {
+    if constexpr (D == 2) {
+        return (0.25f * r * r * logf(R / r) + 0.25f * (r * r - R * R)) * (0.5f / CUDART_PI_F);
+    } else if constexpr (D == 4) {
+        return (-0.5f * logf(R / r) - r * r / (8.f * R * R) + 0.125f) * (0.5f * inv_omega);
+    } else {
+        constexpr float a = 1.f / (2.f * (4.f - (float)D)), b = 1.f / (2.f * (float)D);
+        return (a * powf(r, 4.f - D) - b * r * r * powf(R, 2.f - D) - (a - b) * powf(R, 4.f - D)) *
+               (inv_omega / (float)(D - 2));
+    }
+}
+
 // G = G_B between the centre of a ball of radius R and a point at distance r < R, and F with
 // grad_x G_B = F (y - x)/r at the centre (Laplace(u) - sigma u = -delta, zero values on the
 // sphere): c0 r^-nu [K_mu(kr) - K_mu(kR) I_mu(kr)/I_mu(kR)] for mu = nu (G) and nu + 1 (F,
@@ -471,7 +516,7 @@ __device__ __forceinline__ void log_bessel_K_pair_f32(float nu, float x, float &
 // table entry at kR. Laplace forms at sigma = 0. Evaluated in log space.
 template <int D>
 __device__ __forceinline__ void source_green_f32(const MixedProblem &P, float r, float R, float2 tR, float &G,
-                                                 float &F) {
+                                                 float &F, float &dG) {
     const float nu = 0.5f * (float)D - 1.f;
     const float k = P.sqrt_sigma;
     const float lr = logf(r), lR = logf(R);
@@ -479,17 +524,32 @@ __device__ __forceinline__ void source_green_f32(const MixedProblem &P, float r,
         G = D == 2 ? (lR - lr) * (0.5f / CUDART_PI_F)
                    : (expf((2.f - D) * lr) - expf((2.f - D) * lR)) * (P.src_inv_omega / (float)(D - 2));
         F = (expf((1.f - D) * lr) - r * expf(-(float)D * lR)) * P.src_inv_omega;
+        dG = source_green_dsigma0_f32<D>(P.src_inv_omega, r, R);
         return;
     }
-    float ka0, ka1, kb0, kb1;
-    log_bessel_K_pair_f32(nu, k * r, ka0, ka1);
-    log_bessel_K_pair_f32(nu, k * R, kb0, kb1);
+    float kam, ka0, ka1, kbm, kb0, kb1;
+    log_bessel_K_triple_f32(nu, k * r, kam, ka0, ka1);
+    log_bessel_K_triple_f32(nu, k * R, kbm, kb0, kb1);
     const float2 ta = table_lookup(P.table, k * r);
     const float lSa0 = -ta.x, lSb0 = -tR.x;
     const float lSa1 = lSa0 + logf(ta.y), lSb1 = lSb0 + logf(tR.y);
-    G = expf(P.src_lc0 - nu * lr + ka0) * (1.f - expf(kb0 - ka0 + nu * (lr - lR) + lSa0 - lSb0));
+    const float P0 = expf(P.src_lc0 - nu * lr + ka0);
+    const float X = expf(kb0 - ka0 + nu * (lr - lR) + lSa0 - lSb0);
+    G = P0 * (1.f - X);
     F = expf(P.src_lc0 + logf(k) - nu * lr + ka1) *
         (1.f - expf(kb1 - ka1 + (nu + 1.f) * (lr - lR) + lSa1 - lSb1));
+    if (D == 2 && k * R < 0.15f) {
+        const float L = logf(R / r), r2 = r * r, R2 = R * R;
+        const float w1 = (0.25f * R2 - 0.25f * r2 - 0.25f * r2 * L) * (0.5f / CUDART_PI_F);
+        const float w2 = (-(R2 * r2 * (1.f / 16.f) - r2 * r2 * (6.f / 256.f) - r2 * r2 * (1.f / 64.f) * L) +
+                          R2 * R2 * (10.f / 256.f)) *
+                         (0.5f / CUDART_PI_F);
+        dG = -w1 + 2.f * (k * k) * w2;
+    } else {
+        const float br = -r * expf(kam - ka0) + R * X * expf(kbm - kb0) -
+                         X * k * (r * r * ta.y - R * R * tR.y) / (2.f * (nu + 1.f));
+        dG = P0 * br / (2.f * k);
+    }
 }
 
 // The source term of one step (not inlined: walkers without a source keep their registers):
@@ -506,10 +566,13 @@ __device__ __noinline__ void source_step(const MixedProblem &P, MixedWalker<D> &
     }
     const float r = sqrtf(rr);
     if (!(r > 0.f && r < R)) return;
-    float G, F;
-    source_green_f32<D>(P, r, R, t, G, F);
-    const float c = P.source_q * expf(W.logw) * G;
+    float G, F, dG;
+    source_green_f32<D>(P, r, R, t, G, F, dG);
+    const float qw = P.source_q * expf(W.logw);
+    const float c = qw * G;
     W.src += c;
+    // d/dsigma: the weight's (the d log C / d sigma of the steps before) and G_B's
+    W.dsrc += qw * fmaf(W.dsig, G, dG);
     if (GRAD && W.k == 0) {
         W.src0 = c;
         if (P.src) {
@@ -607,10 +670,13 @@ __device__ __forceinline__ void step_walker(const MixedLaunch &L, const MixedPro
     // control variate: G = alpha(R0)/C(R0) is one number per query (every walk writes the same)
     if (cv_walk && W.gfac0 != 0.f)
         P.acc[W.q * acc_fields(D, P.n_exp, P.cv, P.src) + cv_field(D, P.n_exp) + 3 * D] = (double)W.gfac0;
-    write_record<D>(P, (long long)W.j, outcome, W.k, term, W.dsig, gt, GRAD && need_v0, v0, e);
+    // d/dsigma of the walk's value: its boundary part times the summed d log C / d sigma, plus the
+    // source contributions' derivatives (a capped walk, value 0, has none)
+    const float dv = outcome == 2 ? 0.f : fmaf(term - W.src, W.dsig, W.dsrc);
+    write_record<D>(P, (long long)W.j, outcome, W.k, term, dv, gt, GRAD && need_v0, v0, e);
     if (P.w_term != nullptr) P.w_term[W.j] = outcome == 3 ? (double)CUDART_NAN : (double)term;
     if (P.w_jumps != nullptr) P.w_jumps[W.j] = W.k;
-    if (P.w_dsigma != nullptr) P.w_dsigma[W.j] = P.has_source ? (double)CUDART_NAN : (double)(term * W.dsig);
+    if (P.w_dsigma != nullptr) P.w_dsigma[W.j] = outcome == 3 ? (double)CUDART_NAN : (double)dv;
     if (P.w_grad != nullptr) {
         // with a source, the per-query source part of the gradient (stored at step 0)
         const double *sp = P.src ? P.acc + W.q * acc_fields(D, P.n_exp, P.cv, 1) + src_field(D, P.n_exp, P.cv) : nullptr;

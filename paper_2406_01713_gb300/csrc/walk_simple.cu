@@ -49,7 +49,8 @@ __device__ void run_walk(const SimpleParams<T> &p, const double *xq, uint64_t wa
         v0[j] = T(0);
     }
     T logw = T(0), dsig = T(0), R0 = T(0), logC0 = T(0), S1_0 = T(1);
-    T src = T(0);  // impulse-source contributions of the steps so far
+    T src = T(0);   // impulse-source contributions of the steps so far
+    T dsrc = T(0);  // their sigma derivatives
     int64_t k = 0;
     int kind = -1;
     int64_t idx = -1;
@@ -112,10 +113,13 @@ __device__ void run_walk(const SimpleParams<T> &p, const double *xq, uint64_t wa
             }
             const double r = sqrt(rr);
             if (r > 0.0 && r < (double)R) {
-                double G, F;
-                source_green_f64(D, (double)p.sqrt_sigma, r, (double)R, G, F);
-                const T c = (T)((double)dm.source_q * exp((double)logw) * G);
+                double G, F, dG;
+                source_green_f64(D, (double)p.sqrt_sigma, r, (double)R, G, F, &dG);
+                const double qw = (double)dm.source_q * exp((double)logw);
+                const T c = (T)(qw * G);
                 src += c;
+                // d/dsigma: the weight's (the d log C / d sigma of the steps before) and G_B's
+                dsrc += (T)(qw * ((double)dsig * G + dG));
                 if (k == 0) {
                     res.s0 = c;
 #pragma unroll
@@ -151,8 +155,10 @@ __device__ void run_walk(const SimpleParams<T> &p, const double *xq, uint64_t wa
         ++k;
     }
     res.jumps = k;
-    // d/dsigma of the source part is not estimated
-    res.dsig = dm.has_source ? (T)CUDART_NAN : res.term * dsig;
+    // d/dsigma of the walk's value (the walk geometry does not depend on sigma): the boundary
+    // part times the summed d log C / d sigma plus the source contributions' derivatives; a
+    // capped walk contributes 0
+    res.dsig = res.capped ? T(0) : (res.term - src) * dsig + dsrc;
     if (k > 0) {
         const T factor = p.laplace ? T(D) / R0 : (T(D) / R0) / S1_0;
         if (p.cv) {

@@ -333,7 +333,6 @@ struct FinalizeRec {
     int anti;        // antithetic pairs: the squared fields hold squared pair means (N/2 pairs)
     int cv;          // gradient control variate sums present
     int src;         // impulse-source fields present (gradient walks)
-    int has_source;  // impulse source: du/dsigma is not estimated (NaN)
     int64_t Q, N, q_begin;
     const void *acc;
     const unsigned long long *counts;
@@ -390,7 +389,7 @@ __global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
         const double sh = R->anti ? 0.5 : 1.0, ns = R->anti ? 0.5 * n : n;
         if (R->u) R->u[q] = out ? nan : S(0) * inv;
         if (R->u_se) R->u_se[q] = out ? nan : se_mean(sh * S(0), S(1), ns);
-        if (R->du_dsigma) R->du_dsigma[q] = (out || R->has_source) ? nan : S(2) * inv;
+        if (R->du_dsigma) R->du_dsigma[q] = out ? nan : S(2) * inv;
         const bool cv = R->cv && n >= 2.0;
         const int cf = cv_field(d, K);
         // impulse source: the gradient sums hold G (t - s0) v0; s0 and the source part of the
@@ -529,10 +528,10 @@ __device__ void reduce_segment(const ReduceRec &R, int64_t q, int64_t seg, doubl
 #pragma unroll
             for (int i = D & ~3; i < D; ++i) v0[i] = __ldg(r + 4 + i);
         }
+        ds += (double)h.y;  // the walk's d term / d sigma
         if (term != 0.0) {
             tv = term;
             u += term;
-            ds += term * (double)h.y;
             if (h.z != 0.f) {
 #pragma unroll
                 for (int i = 0; i < D; ++i) {
@@ -1097,7 +1096,6 @@ wos_status run_estimator(wos_domain_t dom, const wos_options *opt, const double 
         r.anti = o.antithetic;
         r.cv = cv;
         r.src = src;
-        r.has_source = dom->has_source;
         r.Q = Q;
         r.N = N;
         r.q_begin = 0;
@@ -2176,7 +2174,6 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         r.anti = b->o.antithetic;
         r.cv = mp[i].cv;
         r.src = mp[i].src;
-        r.has_source = p.domain->has_source;
         r.Q = p.n_queries;
         r.N = p.n_walks;
         r.q_begin = q_begin;

@@ -175,6 +175,16 @@ __device__ inline void log_bessel_K_pair_f64(double nu, double x, double &l0, do
     l1 = m + log(0.5 * h * s1);
 }
 
+// dG_B/dsigma at sigma = 0 between the centre of a ball of radius R and distance r: minus the
+// radial solution w of -Laplace(w) = G_0 with w = 0 on the sphere (the first-order term of G_B
+// in sigma); omega = |S^(d-1)|. FP64.
+__device__ inline double source_green_dsigma0_f64(int d, double omega, double r, double R) {
+    if (d == 2) return (0.25 * r * r * log(R / r) + 0.25 * (r * r - R * R)) / (2.0 * CUDART_PI);
+    if (d == 4) return (-0.5 * log(R / r) - r * r / (8.0 * R * R) + 0.125) / (2.0 * omega);
+    const double a = 1.0 / (2.0 * (4.0 - d)), b = 1.0 / (2.0 * d);
+    return (a * pow(r, 4.0 - d) - b * r * r * pow(R, 2.0 - d) - (a - b) * pow(R, 4.0 - d)) / ((d - 2.0) * omega);
+}
+
 // Between the centre of a ball of radius R and a point at distance r (0 < r < R), for
 // Laplace(u) - sigma u = -delta with zero values on the sphere: G = G_B and F with
 // grad_x G_B = F (y - x)/r at the centre; k = sqrt(sigma), nu = d/2 - 1, c0 = k^nu/(2 pi)^(d/2):
@@ -182,13 +192,15 @@ __device__ inline void log_bessel_K_pair_f64(double nu, double x, double &l0, do
 //   F = c0 k r^-nu [K_nu+1(kr) - K_nu+1(kR) I_nu+1(kr)/I_nu+1(kR)],
 // I ratios from the series S (I_mu(z) is proportional to z^mu S_mu(z)); at sigma = 0 the
 // Laplace forms (r^(2-d) - R^(2-d))/((d-2) omega), ln(R/r)/(2 pi) for d = 2, and
-// F = (r^(1-d) - r R^-d)/omega, omega = |S^(d-1)|. FP64.
-__device__ inline void source_green_f64(int d, double k, double r, double R, double &G, double &F) {
+// F = (r^(1-d) - r R^-d)/omega, omega = |S^(d-1)|; *dG (when given): dG_B/dsigma. FP64.
+__device__ inline void source_green_f64(int d, double k, double r, double R, double &G, double &F,
+                                        double *dG = nullptr) {
     const double nu = 0.5 * d - 1.0;
     if (k == 0.0) {
         const double omega = 2.0 * pow(CUDART_PI, 0.5 * d) / tgamma(0.5 * d);
         G = d == 2 ? log(R / r) / (2.0 * CUDART_PI) : (pow(r, 2.0 - d) - pow(R, 2.0 - d)) / ((d - 2.0) * omega);
         F = (pow(r, 1.0 - d) - r * pow(R, -(double)d)) / omega;
+        if (dG != nullptr) *dG = source_green_dsigma0_f64(d, omega, r, R);
         return;
     }
     double ka0, ka1, kb0, kb1;
@@ -196,11 +208,22 @@ __device__ inline void source_green_f64(int d, double k, double r, double R, dou
     log_bessel_K_pair_f64(nu, k * R, kb0, kb1);
     const double lc0 = nu * log(k) - 0.5 * d * log(2.0 * CUDART_PI);
     const double lrR = log(r / R), lr = log(r);
-    const double i0 = nu * lrR + log(bessel_S<double>(nu, k * r)) - log(bessel_S<double>(nu, k * R));
-    const double i1 =
-        (nu + 1.0) * lrR + log(bessel_S<double>(nu + 1.0, k * r)) - log(bessel_S<double>(nu + 1.0, k * R));
-    G = exp(lc0 - nu * lr + ka0) * (1.0 - exp(kb0 - ka0 + i0));
+    const double Sa0 = bessel_S<double>(nu, k * r), Sb0 = bessel_S<double>(nu, k * R);
+    const double Sa1 = bessel_S<double>(nu + 1.0, k * r), Sb1 = bessel_S<double>(nu + 1.0, k * R);
+    const double i0 = nu * lrR + log(Sa0) - log(Sb0);
+    const double i1 = (nu + 1.0) * lrR + log(Sa1) - log(Sb1);
+    const double X = exp(kb0 - ka0 + i0);  // K_nu(kR) Q / K_nu(kr), Q = I_nu(kr) / I_nu(kR)
+    const double P0 = exp(lc0 - nu * lr + ka0);
+    G = P0 * (1.0 - X);
     F = exp(lc0 + log(k) - nu * lr + ka1) * (1.0 - exp(kb1 - ka1 + i1));
+    if (dG != nullptr) {
+        // dG/dk = (nu/k) G + c0 r^-nu A'(k), A = K_nu(kr) - K_nu(kR) Q, with
+        // K_nu'(x) = -K_{nu+1}(x) + (nu/x) K_nu(x) and Q'/Q = k (r^2 s(kr) - R^2 s(kR)) / (2 (nu+1)),
+        // s = S_{nu+1}/S_nu (DLMF 10.29.2, 10.25.2); dG/dsigma = (dG/dk) / (2k)
+        const double br = (2.0 * nu / k) * (1.0 - X) - r * exp(ka1 - ka0) + R * X * exp(kb1 - kb0) -
+                          X * k * (r * r * Sa1 / Sa0 - R * R * Sb1 / Sb0) / (2.0 * (nu + 1.0));
+        *dG = P0 * br / (2.0 * k);
+    }
 }
 
 }  // namespace wos

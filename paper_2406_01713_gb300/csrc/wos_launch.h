@@ -98,8 +98,9 @@ struct MixedLaunch {
 
 // Per-walk record of the mixed-precision walkers, the input of the per-query reduction
 // (reduce_kernel): rec_words floats at walk index j = q N + w,
-//   [term, dsigma, gt, info, v0 (d floats, gradient walks), e (K floats)]
-// term: the walk's value estimate; dsigma: its summed d log C / d sigma; gt: alpha(R0) u^(x1),
+//   [term, dv, gt, info, v0 (d floats, gradient walks), e (K floats)]
+// term: the walk's value estimate; dv: d term / d sigma (the boundary part times the summed
+// d log C / d sigma, plus the derivatives of the source contributions); gt: alpha(R0) u^(x1),
 // the factor of v0 in its gradient estimate (0 unless the walk reached the boundary after its
 // first sphere); info: k (jumps) | outcome << 28 (0 jumped, 1 boundary, 2 capped, 3 outside) |
 // has_v0 << 31; v0: the first direction (written when has_v0); e_k = exp(a_k . xbar) W (written

@@ -8,7 +8,9 @@ walk's weight; the first-sphere gradient adds q grad_x G_B(x_0, z).
   * mixed and plain FP32: per query within 4 sqrt(se_gpu^2 + se_oracle^2) + 1e-4 (value and
     gradient, also with the control variate);
   * the centred source in a ball: the closed form u = G_Omega(|x|);
-  * du/dsigma is NaN (not estimated with a source);
+  * du/dsigma (each walk's derivative, including the source contributions'): FP64 per walk
+    within 1e-10, mixed and FP32 per query within 4 sqrt(2) standard errors of the oracle's
+    per-walk spread plus 1e-4 relative, and the centred-source closed form;
   * batches and the planner (the paper's two-disc environment) use it.
 """
 import math
@@ -66,7 +68,9 @@ def test_fp64_per_walk_parity(d, sigma):
             g, go = np_(got["grad"]), ref["walk_grad"]
             okg = np.all(np.abs(g - go) <= 1e-10 * np.maximum(1.0, np.abs(go)), axis=-1)
             assert okg.mean() >= 0.999, okg.mean()
-        assert np.all(np.isnan(np_(got["dsigma"])))
+        ds, dso = np_(got["dsigma"]), ref["walk_dsigma"]
+        okd = np.abs(ds - dso) <= 1e-10 * np.maximum(1.0, np.abs(dso))
+        assert okd.mean() >= 0.999, okd.mean()
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed", "fp32"])
@@ -74,12 +78,25 @@ def test_fp64_per_walk_parity(d, sigma):
 def test_per_query_matches_oracle(precision, cv):
     dom, X = source_domain(2, seed=8)
     sigma = 4.0
-    ref = oracle.solve(dom, X, 8000, 1e-3, sigma, 11, grad=True, control_variate=cv)
+    ref = oracle.solve(dom, X, 8000, 1e-3, sigma, 11, grad=True, control_variate=cv, per_walk=True)
     D = W.Domain(dom)
     got = D.grad(X, 8000, 1e-3, sigma, precision=precision, seed=11, control_variate=cv)
     assert np.all(within(np_(got["u"]), np_(got["u_se"]), ref["u"], ref["u_se"]))
     assert np.all(within(np_(got["grad"]), np_(got["grad_se"]), ref["grad"], ref["grad_se"], atol=1e-4))
-    assert np.all(np.isnan(np_(got["du_dsigma"])))
+    assert_dsigma(np_(got["du_dsigma"]), ref, precision)
+
+
+def assert_dsigma(got, ref, precision):
+    """du/dsigma against the oracle on the same walks: FP64 to rounding; mixed and plain FP32
+    within 4 sqrt(2) standard errors (from the oracle's per-walk values) + 1e-4 relative."""
+    want = ref["du_dsigma"]
+    assert np.all(np.isfinite(got))
+    if precision == "fp64":
+        assert np.allclose(got, want, rtol=1e-9, atol=1e-12)
+        return
+    wd = ref["walk_dsigma"]
+    se = wd.std(axis=1, ddof=1) / math.sqrt(wd.shape[1])
+    assert np.all(np.abs(got - want) <= 4 * math.sqrt(2) * se + 1e-4 * np.abs(want))
 
 
 @pytest.mark.parametrize("d,sigma", [(2, 0.0), (3, 9.0)])
@@ -104,6 +121,24 @@ def test_centred_source_closed_form(d, sigma):
         assert abs(np_(got["u"])[q] - u) <= 4.5 * np_(got["u_se"])[q] + 1e-4 * abs(u)
         g = du * x / r
         assert np.all(np.abs(np_(got["grad"])[q] - g) <= 4.5 * np_(got["grad_se"])[q] + 2e-3 * np.abs(g).max())
+    # du/dsigma = d/dsigma G_Omega(|x|): scipy's form by central differences (one-sided at
+    # sigma = 0); the standard error from the same walks' per-walk derivatives
+    per = np_(W.Domain(dom).walks(X, 32768, 1e-5, sigma, grad_mode=True, seed=1)["dsigma"])
+    se = per.std(axis=1, ddof=1) / math.sqrt(per.shape[1])
+    h = 1e-4
+    for q, x in enumerate(X):
+        r = np.linalg.norm(x)
+
+        def G(s):
+            if s == 0.0:
+                return math.log(R / r) / (2 * math.pi) if d == 2 else (r ** (2 - d) - R ** (2 - d)) / ((d - 2) * omega)
+            kk = math.sqrt(s)
+            c0 = kk ** nu / (2 * math.pi) ** (d / 2)
+            return c0 * r ** -nu * (special.kv(nu, kk * r) - special.kv(nu, kk * R) * special.iv(nu, kk * r)
+                                    / special.iv(nu, kk * R))
+
+        want = (-3 * G(0.0) + 4 * G(h) - G(2 * h)) / (2 * h) if sigma == 0.0 else (G(sigma + h) - G(sigma - h)) / (2 * h)
+        assert abs(np_(got["du_dsigma"])[q] - want) <= 4.5 * se[q] + 1e-4 * abs(want)
 
 
 def test_batch_with_a_source_problem():
@@ -186,11 +221,11 @@ def test_tensor_core_walker_with_a_source(kind, cv):
     D = W.Domain(dom)
     assert D.info()["tensor_sphere_set"]
     sigma, N = 4.0, 8000
-    ref = oracle.solve(dom, X, N, 2e-3, sigma, 13, grad=True, control_variate=cv)
+    ref = oracle.solve(dom, X, N, 2e-3, sigma, 13, grad=True, control_variate=cv, per_walk=True)
     got = D.grad(X, N, 2e-3, sigma, seed=13, control_variate=cv)
     assert np.all(within(np_(got["u"]), np_(got["u_se"]), ref["u"], ref["u_se"]))
     assert np.all(within(np_(got["grad"]), np_(got["grad_se"]), ref["grad"], ref["grad_se"]))
-    assert np.all(np.isnan(np_(got["du_dsigma"])))
+    assert_dsigma(np_(got["du_dsigma"]), ref, "mixed")
     if not cv:
         per = D.walks(X[:2], 512, 2e-3, sigma, grad_mode=True, seed=13)
         ro = oracle.solve(dom, X[:2], 512, 2e-3, sigma, 13, grad=True, per_walk=True)
