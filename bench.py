@@ -700,7 +700,9 @@ def fp64_same_stream(W, doms, probs, outs, seed, cv, n_pick=24):
     Philox streams, walk indices and control variate): one query from each of n_pick problems,
     half of them on the tensor-core sphere-set walker, including the problems with the most balls
     and the most walks. Returns the largest |mixed - FP64| of u and of grad u, and the largest
-    ratio to the combined standard error."""
+    ratio to the combined standard error; for du/dsigma and du/dw (which the batch does not
+    return) the mixed single-query call on the same walks against FP64, as the largest absolute
+    difference and the largest difference relative to the FP64 value."""
     bases = np.cumsum([0] + [p["X"].shape[0] * p["n_walks"] for p in probs])
     rng = np.random.default_rng(13)
     tens = [i for i, d in enumerate(doms) if d.info()["tensor_sphere_set"]]
@@ -710,11 +712,20 @@ def fp64_same_stream(W, doms, probs, outs, seed, cv, n_pick=24):
     pick = list(dict.fromkeys(heavy + list(rng.permutation(tens)[: n_pick // 2 - len(heavy)]) +
                               list(rng.permutation(core)[: n_pick // 2])))
     du, dg, ru, rg = 0.0, 0.0, 0.0, 0.0
+    ds_abs, ds_rel, dw_abs, dw_rel = 0.0, 0.0, 0.0, 0.0
     for i in pick:
         p, o = probs[i], outs[i]
         q = int(rng.integers(p["X"].shape[0]))
-        r = doms[i].grad(p["X"][q:q + 1], p["n_walks"], p["eps"], p["sigma"], precision="fp64", seed=seed,
-                         walk_offset=int(bases[i]) + q * p["n_walks"], control_variate=cv)
+        kw = dict(seed=seed, walk_offset=int(bases[i]) + q * p["n_walks"], control_variate=cv)
+        r = doms[i].grad(p["X"][q:q + 1], p["n_walks"], p["eps"], p["sigma"], precision="fp64", **kw)
+        m = doms[i].grad(p["X"][q:q + 1], p["n_walks"], p["eps"], p["sigma"], precision="mixed", **kw)
+        s64, sm = float(r["du_dsigma"][0]), float(m["du_dsigma"][0])
+        ds_abs = max(ds_abs, abs(sm - s64))
+        ds_rel = max(ds_rel, abs(sm - s64) / max(abs(s64), 1e-300))
+        if r["du_dw"] is not None:
+            w64, wm = r["du_dw"][0].cpu().numpy(), m["du_dw"][0].cpu().numpy()
+            dw_abs = max(dw_abs, float(np.max(np.abs(wm - w64))))
+            dw_rel = max(dw_rel, float(np.max(np.abs(wm - w64) / np.maximum(np.abs(w64), 1e-300))))
         u64, g64 = float(r["u"][0]), r["grad"][0].cpu().numpy()
         se_u, se_g = float(r["u_se"][0]), r["grad_se"][0].cpu().numpy()
         um, gm = float(o["u"][q]), o["grad"][q].cpu().numpy()
@@ -724,7 +735,10 @@ def fp64_same_stream(W, doms, probs, outs, seed, cv, n_pick=24):
         rg = max(rg, float(np.max(np.abs(gm - g64) / np.maximum(se_g, 1e-300))))
     return {"problems": len(pick), "tensor_core_problems": sum(1 for i in pick if i in set(tens)),
             "max_abs_u": du, "max_abs_grad": dg, "max_u_over_se": ru, "max_grad_over_se": rg,
-            "note": "one query from each problem, mixed batch output against the FP64 GPU walker on the same walks"}
+            "max_abs_du_dsigma": ds_abs, "max_rel_du_dsigma": ds_rel, "max_abs_du_dw": dw_abs,
+            "max_rel_du_dw": dw_rel,
+            "note": "one query from each problem: u and grad u of the mixed batch output, du/dsigma and du/dw "
+                    "of the mixed single-query call, against the FP64 GPU walker on the same walks"}
 
 
 def se_calibration(probs, outs):
