@@ -193,16 +193,18 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------ oracle sample
-def oracle_sample(problems, seed, target_seconds, cv=True):
+def oracle_sample(problems, seed, target_seconds, cv=True, threads=None):
     """The FP64 oracle on a bounded sample of the batched workload: the first `nq` queries of
     each problem (problems in a seeded shuffled order), min(N, 64) gradient walks per query,
     until about target_seconds. The oracle threads over queries, so nq = host cores keeps every
-    core busy. Returns (walk_steps, seconds, threads used, description)."""
+    core busy (threads = 1: the same queries on one core). Returns (walk_steps, seconds, threads
+    used, description)."""
     import oracle
 
     oracle.build()
-    threads = os.cpu_count() or 1
-    nq = min(threads, 64)
+    cores = os.cpu_count() or 1
+    nq = min(cores, 64)
+    threads = threads or cores
     order = np.random.default_rng(7).permutation(len(problems))
     steps = 0
     used = 0
@@ -415,8 +417,10 @@ def main():
     if rank == 0:
         if args.cpu_seconds > 0:
             steps_cpu, t_cpu, cores, desc = oracle_sample(probs, w["seed"], args.cpu_seconds, not args.no_cv)
+            s1, t1, _, _ = oracle_sample(probs, w["seed"], args.cpu_seconds / 4, not args.no_cv, threads=1)
             line["cpu_baseline"] = {"value": steps_cpu / t_cpu, "unit": "walk-steps/s", "cores": cores,
-                                    "kind": "oracle", "sample": desc}
+                                    "kind": "oracle", "sample": desc, "single_thread_value": s1 / t1,
+                                    "single_thread_note": "the same sample on one core, about a quarter of the time"}
         else:
             line["cpu_baseline"] = None
         print(json.dumps(line), flush=True)
