@@ -232,3 +232,24 @@ def test_tensor_core_walker_with_a_source(kind, cv):
         # the per-walk gradients include the (deterministic) source part q grad_x G_B(x0, z)
         assert np.allclose(np_(per["grad"]).mean(1), ro["walk_grad"].mean(1),
                            atol=4 * ro["grad_se"].max() + 1e-4)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "fp32"])
+def test_source_with_roulette_and_antithetic_pairs(precision):
+    """The impulse source together with the Russian roulette (a killed walk keeps its source
+    contributions and their sigma derivatives) and antithetic first directions."""
+    dom, X = source_domain(3, seed=12)
+    sigma, N, eps, seed, w_min = 16.0, 4000, 1e-3, 17, 0.3
+    D = W.Domain(dom)
+    ref = oracle.solve(dom, X, N, eps, sigma, seed, grad=True, roulette=w_min, antithetic=True, per_walk=True)
+    assert int(ref["killed"].sum()) > 0
+    if precision == "fp64":
+        got = D.walks(X, N, eps, sigma, grad_mode=True, precision="fp64", seed=seed, roulette=w_min, antithetic=True)
+        for k, kr in (("term", "walk_term"), ("dsigma", "walk_dsigma")):
+            a, b = np_(got[k]), ref[kr]
+            assert (np.abs(a - b) <= 1e-10 * np.maximum(1.0, np.abs(b))).mean() >= 0.999, k
+    r = D.grad(X, N, eps, sigma, precision=precision, seed=seed, roulette=w_min, antithetic=True, with_stats=True)
+    assert W.stats_dict(r["stats"])["killed"] > 0
+    assert np.all(within(np_(r["u"]), np_(r["u_se"]), ref["u"], ref["u_se"]))
+    assert np.all(within(np_(r["grad"]), np_(r["grad_se"]), ref["grad"], ref["grad_se"]))
+    assert_dsigma(np_(r["du_dsigma"]), ref, precision)
