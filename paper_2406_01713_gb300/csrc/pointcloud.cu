@@ -44,8 +44,9 @@ constexpr int kTileN = 64;       // centres per tile = MMA N
 constexpr int kMaxStages = 6;
 constexpr int kPairTiles = 2;  // centre tiles per bulk copy (consecutive in memory and in the ring)
 constexpr int kCtasPerSm = 4;    // 4 x 128 TMEM columns; registers <= 102 per thread
-constexpr int kChunk = 32;       // candidate chunk (columns)
-constexpr int kRefineGroup = 4;  // walkers whose chunk refinements a warp keeps in flight together
+constexpr int kChunk = 16;       // candidate chunk (columns)
+constexpr int kRefineGroup = 4;  // walker pairs whose chunk refinements a warp keeps in flight together
+constexpr int kChunksPerTile = kTileN / kChunk;
 // A chunk in memory: its kChunk centres padded with zeros to a multiple of four coordinates and
 // stored by coordinate quads (quad q: coordinates 4q..4q+3 of sphere 0, of sphere 1, ...), so
 // that one 16-byte load per lane reads a quad of all 32 spheres in 512 contiguous bytes; then
@@ -246,7 +247,7 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-static_assert(kTileN == 64, "the epilogue reads a 64-column tile as two 32-column chunks");
+static_assert(kTileN == 64 && kChunk == 16, "the epilogue reads a 64-column tile as two 32-column loads of two chunks each");
 
 // 32 accumulator columns of this thread's TMEM lane, loaded and waited for in one step.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
@@ -283,6 +284,12 @@ __device__ __forceinline__ float min32(const float *v) {
     m[10] = fminf(v[30], v[31]);
     const float a = fmin3(m[0], m[1], m[2]), b = fmin3(m[3], m[4], m[5]), c = fmin3(m[6], m[7], m[8]);
     return fmin3(fmin3(a, b, c), m[9], m[10]);
+}
+
+__device__ __forceinline__ float min16(const float *v) {
+    const float a = fmin3(v[0], v[1], v[2]), b = fmin3(v[3], v[4], v[5]), c = fmin3(v[6], v[7], v[8]);
+    const float e = fmin3(v[9], v[10], v[11]), f = fmin3(v[12], v[13], v[14]);
+    return fmin3(fmin3(a, b, c), fmin3(e, f, v[15]), a);
 }
 
 // Writes this walker's A row (BF16 split of x; zeros for an idle lane).
@@ -585,34 +592,36 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             float m1 = CUDART_INF_F, m2 = CUDART_INF_F, m3 = CUDART_INF_F;
             int c1 = 0, c2 = 0;
             bool ok = true;
-            // the chunk radius bounds of the next tile (one 8-byte load), fetched a tile ahead
-            static_assert(kTileN / kChunk == 2, "two chunk bounds per tile");
-            const float2 *const rhi2 = reinterpret_cast<const float2 *>(chunk_rhi);
-            float2 rhi_next = __ldg(rhi2);
+            // the chunk radius bounds of the next tile (one 16-byte load), fetched a tile ahead
+            static_assert(kChunksPerTile == 4, "four chunk bounds per tile");
+            const float4 *const rhi4 = reinterpret_cast<const float4 *>(chunk_rhi);
+            float4 rhi_next = __ldg(rhi4);
             for (int t = 0; t < T; ++t, ++g_epi) {
                 const int b = (int)(g_epi & 1);
-                const float rhi[kTileN / kChunk] = {rhi_next.x, rhi_next.y};
-                rhi_next = __ldg(rhi2 + (t + 1 < T ? t + 1 : t));
+                const float rhi[kChunksPerTile] = {rhi_next.x, rhi_next.y, rhi_next.z, rhi_next.w};
+                rhi_next = __ldg(rhi4 + (t + 1 < T ? t + 1 : t));
                 if (!warp_wait_bar(S, &S.tfull[b], (uint32_t)((g_epi >> 1) & 1), L)) {
                     ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                float cmin[kTileN / kChunk];
+                float cmin[kChunksPerTile];
                 {
-                    float v[kChunk];
+                    float v[32];
                     tmem_ld32(trow + b * kTileN, v);
-                    cmin[0] = min32(v);
-                    tmem_ld32(trow + b * kTileN + kChunk, v);
+                    cmin[0] = min16(v);
+                    cmin[1] = min16(v + 16);
+                    tmem_ld32(trow + b * kTileN + 32, v);
                     // the accumulator buffer is free as soon as its columns are in registers
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&S.tempty[b]);
-                    cmin[1] = min32(v);
+                    cmin[2] = min16(v);
+                    cmin[3] = min16(v + 16);
                 }
 #pragma unroll
-                for (int c = 0; c < kTileN / kChunk; ++c) {
-                    const int id = t * (kTileN / kChunk) + c;
+                for (int c = 0; c < kChunksPerTile; ++c) {
+                    const int id = t * kChunksPerTile + c;
                     const float cs = cmin[c] + xxd;
                     const float cm = sqrt_below(cs) - rhi[c];
                     // best, second and third bound; select form, no divergent branches
@@ -640,7 +649,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             // the walkers' positions, padded like the chunk centres, in this warp's own rows of
             // the A operand: every MMA of the step has completed, and the next step rewrites them
             constexpr int kP = chunk_pitch(D);
-            static_assert(kChunk * kP * 4 <= 4 * kSBO, "positions fit the warp's A rows");
+            static_assert(32 * kP * 4 <= 4 * kSBO, "positions fit the warp's A rows");
             float *xs = reinterpret_cast<float *>(A + warp * 4 * kSBO);
 #pragma unroll
             for (int i = 0; i < kP; i += 4)
@@ -651,21 +660,23 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             auto refine = [&](int cc, bool want) {
                 const unsigned todo = __ballot_sync(0xffffffffu, want);
                 if (todo == 0u) return;
-                // lane i: sphere i of walker w's chunk, kRefineGroup walkers at a time so that
-                // their chunk loads are in flight together; a walker that does not ask still
-                // names a valid chunk, and its row is not read
+                // lane i: sphere i % 16 of the chunk of walker w0 + 2u + i / 16, kRefineGroup walker
+                // pairs at a time so that their chunk loads are in flight together; a walker that
+                // does not ask still names a valid chunk, and its row is not read
+                constexpr int kGroupWalkers = 2 * kRefineGroup;
+                const int half = lane >> 4, sl = lane & 15;
 #pragma unroll 1
-                for (int w0 = 0; w0 < 32; w0 += kRefineGroup) {
-                    if (((todo >> w0) & ((1u << kRefineGroup) - 1u)) == 0u) continue;
+                for (int w0 = 0; w0 < 32; w0 += kGroupWalkers) {
+                    if (((todo >> w0) & ((1u << kGroupWalkers) - 1u)) == 0u) continue;
                     const float4 *cen[kRefineGroup];
                     float rr[kRefineGroup];
                     f32x2 s01[kRefineGroup], s23[kRefineGroup];  // packed partial sums of (x - c)^2
 #pragma unroll
                     for (int u = 0; u < kRefineGroup; ++u) {
-                        const float *ch =
-                            soa + (long long)__shfl_sync(0xffffffffu, cc, w0 + u) * chunk_floats(D);
-                        cen[u] = reinterpret_cast<const float4 *>(ch) + lane;
-                        rr[u] = __ldg(ch + kChunk * kP + lane);
+                        const int w = w0 + 2 * u + half;
+                        const float *ch = soa + (long long)__shfl_sync(0xffffffffu, cc, w) * chunk_floats(D);
+                        cen[u] = reinterpret_cast<const float4 *>(ch) + sl;
+                        rr[u] = __ldg(ch + kChunk * kP + sl);
                         s01[u] = 0ull;
                         s23[u] = 0ull;
                     }
@@ -675,7 +686,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
 #pragma unroll
                         for (int u = 0; u < kRefineGroup; ++u) {
                             const float4 c = __ldg(cen[u] + i4 * kChunk);
-                            const float4 xv = *reinterpret_cast<const float4 *>(xs + (w0 + u) * kP + 4 * i4);
+                            const float4 xv =
+                                *reinterpret_cast<const float4 *>(xs + (w0 + 2 * u + half) * kP + 4 * i4);
                             // x - c exactly rounded (fma with -1), squares summed in four packed
                             // lanes; zero padding adds exact zeros
                             const f32x2 t01 = ffma2(pack2(c.x, c.y), neg1, pack2(xv.x, xv.y));
@@ -687,7 +699,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
 #pragma unroll
                     for (int u = 0; u < kRefineGroup; ++u) {
                         const float2 a = unpack2(s01[u]), b = unpack2(s23[u]);
-                        tr[(w0 + u) * kTrPitch + lane] = sqrt_below_tight((a.x + b.x) + (a.y + b.y)) - rr[u];
+                        tr[(w0 + 2 * u + half) * kTrPitch + sl] = sqrt_below_tight((a.x + b.x) + (a.y + b.y)) - rr[u];
                     }
                 }
                 __syncwarp();
