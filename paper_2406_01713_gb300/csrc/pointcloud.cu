@@ -4,7 +4,7 @@
 // (Sec. VI, |q - c_i| - r_i), for 128 walkers at a time. The contraction
 // D_wi = |c_i|^2 - 2 x_w . c_i runs as tcgen05.mma (BF16 inputs, FP32 accumulation in tensor
 // memory) over centre tiles that bulk copies (cp.async.bulk) stream into shared memory; the
-// walker warps read their rows back with tcgen05.ld. Per 32-column chunk, min D gives a lower
+// walker warps read their rows back with tcgen05.ld. Per 16-column chunk, min D gives a lower
 // bound of the chunk's distances, sqrt(min D + |x|^2 - delta) - r_hi (balls are sorted by
 // radius, so r_hi, the chunk's largest radius, is close to every radius in it); each walker
 // keeps the best, second and third chunk bounds. The best chunk is then recomputed exactly in
@@ -49,8 +49,8 @@ constexpr int kRefineGroup = 4;  // walker pairs whose chunk refinements a warp 
 constexpr int kChunksPerTile = kTileN / kChunk;
 // A chunk in memory: its kChunk centres padded with zeros to a multiple of four coordinates and
 // stored by coordinate quads (quad q: coordinates 4q..4q+3 of sphere 0, of sphere 1, ...), so
-// that one 16-byte load per lane reads a quad of all 32 spheres in 512 contiguous bytes; then
-// its kChunk radii.
+// that one 16-byte load per lane reads a quad of all 16 spheres in 256 contiguous bytes (two
+// walkers' chunks per warp-wide load); then its kChunk radii.
 __host__ __device__ constexpr int chunk_pitch(int d) { return (d + 3) & ~3; }
 __host__ __device__ constexpr int chunk_floats(int d) { return kChunk * (chunk_pitch(d) + 1); }
 constexpr int kWalkerThreads = 128;
@@ -76,8 +76,8 @@ struct Geo {
     static constexpr int kSlots = kStages / kPairTiles;
     static constexpr uint32_t kSlotBytes = kPairTiles * kTileBytes;
 };
-constexpr int kTrPitch = 34;  // transpose row: 32 spheres + 2 pad (8-byte aligned rows, no bank conflicts)
-constexpr uint32_t kTransposeBytes = 4 * 32 * kTrPitch * 4;  // per walker warp: 32 walkers x 32 spheres
+constexpr int kTrPitch = 34;  // transpose row: up to 32 spheres + 2 pad (8-byte aligned rows, no bank conflicts)
+constexpr uint32_t kTransposeBytes = 4 * 32 * kTrPitch * 4;  // per walker warp: 32 walker rows
 constexpr long long kDrainBudget = kDefaultWaitBudget;  // teardown waits, whatever the launch's budget
 
 // Core-matrix layout (8 rows x 16 bytes), K-major, no swizzle: element (r, k) of a
@@ -582,9 +582,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             __syncwarp();
             if (lane == 0) mbar_arrive(&S.a_ready);
 
-            // ---- epilogue: best and second-best 32-column chunk by the lower bound
+            // ---- epilogue: best and second-best 16-column chunk by the lower bound
             //      sqrt(min D~ + |x|^2 - delta) - r_hi, D~ = |c|^2 - 2 x.c (the square root
-            //      rounded down); one 32-column TMEM load per chunk keeps registers free
+            //      rounded down); one 32-column TMEM load (two chunks) at a time keeps registers free
             float xx = 0.f;
 #pragma unroll
             for (int i = 0; i < D; ++i) xx = fmaf(x[i], x[i], xx);
