@@ -223,8 +223,9 @@ inline uint32_t wait_hint_ns(long long budget) {
 }
 constexpr int kPointCloudMaxD = 12;  // 3d + 2 BF16 columns fit a 32- or 48-wide contraction
 // Ball sets at least this large run on the tensor cores: the measured crossover of the two
-// walkers (u and grad u, 64 queries x 16384 walks per ball set) lies near 160 balls at d = 3,
-// below 224 at d = 4, near 330 at d = 5, 320 at d = 6, 288 at d = 7 and 256 for d = 8..12.
-constexpr int sphere_min_balls(int d) { return d <= 4 ? 192 : (d <= 6 ? 320 : 288); }
+// walkers (u and grad u with the control variate, 64 queries x 16384 walks per ball set; CUDA-core
+// time over tensor-core time 1.13-1.31 at 96 balls for d <= 4, 1.05-1.15 at 160 balls for d = 5..9,
+// 1.04-1.13 at 128 balls for d = 10..12).
+constexpr int sphere_min_balls(int d) { return d <= 4 ? 96 : (d <= 9 ? 160 : 128); }
 
 }  // namespace wos

@@ -19,7 +19,7 @@ from paper_2406_01713_gb300 import wos as W  # noqa: E402
 
 
 def _ball_field(d, B, seed):
-    """[-1,1]^d with B balls and a goal ball (g = 1 there): B >= 192 runs on the tensor cores."""
+    """[-1,1]^d with B balls and a goal ball (g = 1 there): B = 400 runs on the tensor cores."""
     rng = np.random.default_rng(seed)
     c = rng.uniform(-1, 1, size=(B, d))
     r = np.exp(rng.uniform(math.log(0.01), math.log(0.06), size=B))

@@ -158,7 +158,7 @@ def test_per_query_sums_equal_per_walk_means(B):
     d, N, Q, eps, sigma, seed = 3, 5, 300, 1e-3, 9.0, 21
     dom, X, _ = ball_problem(d, B, sigma, 70 + B, Q)
     D = W.Domain(dom)
-    assert D.info()["tensor_sphere_set"] == (B >= 192)
+    assert D.info()["tensor_sphere_set"] == (B >= 2048)
     per = D.walks(X, N, eps, sigma, grad_mode=True, seed=seed, walk_offset=10)
     got = D.grad(X, N, eps, sigma, seed=seed, walk_offset=10, with_stats=True)
     st = W.stats_dict(got["stats"])
@@ -175,7 +175,7 @@ def test_per_query_sums_equal_per_walk_means(B):
     for k in ("u", "u_se", "grad", "grad_se", "du_dsigma"):
         assert torch.equal(again[k], again2[k]), k
     # a batch of both kinds, same walks (walk indices follow the problems in order)
-    dom2, X2, _ = ball_problem(d, 2048 if B < 192 else 40, sigma, 90 + B, 200)
+    dom2, X2, _ = ball_problem(d, 2048 if B < 2048 else 40, sigma, 90 + B, 200)
     D2 = W.Domain(dom2)
     b = W.Batch([{"domain": D, "x": X, "n_walks": N, "eps": eps, "sigma": sigma, "grad": True},
                  {"domain": D2, "x": X2, "n_walks": 3, "eps": eps, "sigma": sigma, "grad": True}], seed=seed)

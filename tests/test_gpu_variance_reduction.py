@@ -37,7 +37,7 @@ def agree(a, se_a, b, se_b, k=4.0, atol=1e-4):
 def roulette_domain(sigma=16.0, n_balls=2, d=3, seed=4):
     """Unit ball with ball obstacles and exp data (|a|^2 = sigma): at sigma = 16 a third of the
     walks' later steps carry weights below 0.3, so the roulette acts often. With many balls
-    (n_balls >= 192) the mixed walker runs the domain on the tensor cores."""
+    (1024) the mixed walker runs the domain on the tensor cores."""
     rng = np.random.default_rng(seed)
     a = rng.standard_normal(d)
     a *= math.sqrt(sigma) / np.linalg.norm(a)
@@ -86,7 +86,7 @@ def test_roulette_per_query_against_oracle(precision, n_balls, sigma):
     # (1024 small balls end walks early: sigma = 64 makes their weights small enough for the roulette)
     dom, X, a, sigma = roulette_domain(sigma=sigma, n_balls=n_balls)
     D = W.Domain(dom)
-    assert D.info()["tensor_sphere_set"] == (n_balls >= 192)
+    assert D.info()["tensor_sphere_set"] == (n_balls >= 1024)
     N, seed = 8000, 5
     ref = oracle.solve(dom, X, N, EPS, sigma, seed, grad=True, roulette=ROULETTE_W)
     r = D.grad(X, N, EPS, sigma, precision=precision, seed=seed, roulette=ROULETTE_W, with_stats=True)
