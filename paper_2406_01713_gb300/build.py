@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(CSRC, "_build")
 LIB = os.path.join(HERE, "libwos.so")
 SOURCES = ["wos_api.cu", "walk_simple.cu", "walk_mixed_val512.cu", "walk_mixed_val768.cu",
-           "walk_mixed_grad512.cu", "walk_mixed_grad768.cu", "pointcloud.cu"]
+           "walk_mixed_grad512.cu", "walk_mixed_grad768.cu", "pointcloud.cu",
+           "pointcloud_wide.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -1859,7 +1859,7 @@ struct wos_batch_s {
     // [reduction] [finalize]
     MixedLaunch L{};
     std::vector<SphereLaunch> sph;
-    std::vector<int> sph_grid, sph_dims, sph_src;
+    std::vector<int> sph_grid, sph_dims, sph_src, sph_wide;
     ReduceArgs ra{};
     bool any_seg = false;
     FinalizeArgs fa{};
@@ -1974,7 +1974,8 @@ wos_status enqueue_batch_core(wos_batch_s *b, cudaStream_t cap, CaptureSide &cs)
     if (ns > 0 && cudaEventRecord(cs.ev.back(), cap) != cudaSuccess) return fail(WOS_ERR_CUDA, "fork event capture");
     for (size_t k = 0; k < ns; ++k)
         if (cudaStreamWaitEvent(cs.side[k], cs.ev.back(), 0) != cudaSuccess ||
-            launch_spheres(b->sph[k], b->sph_dims[k], b->grad_any, b->sph_src[k], b->sph_grid[k], cs.side[k]) !=
+            launch_spheres(b->sph[k], b->sph_dims[k], b->grad_any, b->sph_src[k], b->sph_wide[k], b->sph_grid[k],
+                           cs.side[k]) !=
                 cudaSuccess ||
             cudaEventRecord(cs.ev[k], cs.side[k]) != cudaSuccess)
             return fail(WOS_ERR_CUDA, "sphere-set kernel capture failed");
@@ -2084,7 +2085,9 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     const int64_t kSphereItemWalks = cfg.sphere_item_walks;
     std::vector<int> sph_index(n, -1);
     std::vector<int> sph_problem;  // sphere problem -> batch problem
-    std::vector<std::vector<SphereItem>> sph_items(kPointCloudMaxD + 1);
+    // one queue per (dimension, class): group kSphereQueueClasses d + sphere_queue_class(d, tiles)
+    constexpr int kSphGroups = kSphereQueueClasses * (kPointCloudMaxD + 1);
+    std::vector<std::vector<SphereItem>> sph_items(kSphGroups);
     for (int i : porder) {
         if (!tensor[i]) continue;
         sph_index[i] = (int)sph_problem.size();
@@ -2096,16 +2099,17 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
             it.problem = sph_index[i];
             it.j0 = j0;
             it.j1 = std::min(total, j0 + kSphereItemWalks);
-            sph_items[p.domain->d].push_back(it);
+            sph_items[kSphereQueueClasses * p.domain->d + sphere_queue_class(p.domain->d, p.domain->pcd.n_tiles)]
+                .push_back(it);
         }
     }
     std::vector<SphereItem> sph_all;
-    std::vector<size_t> sph_off(kPointCloudMaxD + 2, 0);
-    for (int dd = 0; dd <= kPointCloudMaxD; ++dd) {
-        sph_off[dd] = sph_all.size();
-        sph_all.insert(sph_all.end(), sph_items[dd].begin(), sph_items[dd].end());
+    std::vector<size_t> sph_off(kSphGroups + 1, 0);
+    for (int g = 0; g < kSphGroups; ++g) {
+        sph_off[g] = sph_all.size();
+        sph_all.insert(sph_all.end(), sph_items[g].begin(), sph_items[g].end());
     }
-    sph_off[kPointCloudMaxD + 1] = sph_all.size();
+    sph_off[kSphGroups] = sph_all.size();
     b->n_sphere_items = (int64_t)sph_all.size();
     const int n_sph = (int)sph_problem.size();
     const size_t off_recs = off_items + align256(sizeof(MixedItem) * std::max<size_t>(1, sorted.size()));
@@ -2125,8 +2129,8 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     }
     const size_t off_zero = off_rec;
     // zeroed: accumulators | mixed cursor (8) + sphere status (8) + shrinks (8) + one cursor per
-    // dimension | stats
-    const size_t ctl_bytes = align256(8 * (3 + kPointCloudMaxD + 1));
+    // sphere queue | stats
+    const size_t ctl_bytes = align256(8 * (3 + kSphGroups));
     const size_t zero_bytes = acc_bytes + ctl_bytes + align256(sizeof(wos_stats));
     const size_t total_bytes = off_zero + zero_bytes;
     WOS_CUDA(cudaMalloc(&b->dev, total_bytes));
@@ -2136,7 +2140,7 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     int *sph_status = reinterpret_cast<int *>(cursor + 1);
     b->sph_status = sph_status;
     unsigned long long *sph_shrinks = cursor + 2;
-    unsigned long long *sph_cursors = cursor + 3;  // [d]
+    unsigned long long *sph_cursors = cursor + 3;  // [queue group]
     b->d_stats = (wos_stats *)(zero + acc_bytes + ctl_bytes);
     b->zero_off = off_zero;
     b->zero_bytes = zero_bytes;
@@ -2239,20 +2243,22 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     fa.stats = b->d_stats;
     fa.status = n_sph > 0 ? sph_status : nullptr;
     fa.shrinks = n_sph > 0 ? sph_shrinks : nullptr;
-    // one sphere-set launch per dimension (run on their own streams so that their CTAs and the
+    // one sphere-set launch per queue (run on their own streams so that their CTAs and the
     // CUDA-core walker's share the GPU as each queue drains)
     b->sph.clear();
     b->sph_grid.clear();
     b->sph_dims.clear();
     b->sph_src.clear();
-    for (int dd = 0; dd <= kPointCloudMaxD; ++dd) {
-        if (sph_off[dd + 1] <= sph_off[dd]) continue;
+    b->sph_wide.clear();
+    for (int g = 0; g < kSphGroups; ++g) {
+        if (sph_off[g + 1] <= sph_off[g]) continue;
+        const int dd = g / kSphereQueueClasses, cls = g % kSphereQueueClasses, wide = cls == 2 ? 1 : 0;
         SphereLaunch SL;
         memset(&SL, 0, sizeof(SL));
         SL.problems = (const SphereProblem *)(base + off_sph);
-        SL.items = (const SphereItem *)(base + off_sph_items) + sph_off[dd];
-        SL.n_items = (int64_t)(sph_off[dd + 1] - sph_off[dd]);
-        SL.item_cursor = sph_cursors + dd;
+        SL.items = (const SphereItem *)(base + off_sph_items) + sph_off[g];
+        SL.n_items = (int64_t)(sph_off[g + 1] - sph_off[g]);
+        SL.item_cursor = sph_cursors + g;
         SL.status = sph_status;
         SL.shrinks = sph_shrinks;
         SL.seed = b->o.seed;
@@ -2262,9 +2268,12 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
         b->sph.push_back(SL);
         b->sph_grid.push_back((int)std::min<int64_t>((int64_t)cfg.sphere_ctas_per_sm * sms, SL.n_items));
         b->sph_dims.push_back(dd);
-        int src_any = 0;  // the source variant of the kernel if a problem of this dimension has one
-        for (int k : sph_problem)
-            src_any |= b->probs[k].domain->d == dd && b->probs[k].domain->has_source;
+        b->sph_wide.push_back(wide);
+        int src_any = 0;  // the source variant of the kernel if a problem of this queue has one
+        for (int k : sph_problem) {
+            const wos_domain_t dk = b->probs[k].domain;
+            src_any |= dk->d == dd && sphere_queue_class(dd, dk->pcd.n_tiles) == cls && dk->has_source;
+        }
         b->sph_src.push_back(src_any);
     }
     if (b->no_graph) return WOS_OK;

@@ -159,15 +159,14 @@ inline int max_active_mixed(int threads, size_t smem_bytes, int grad_any) {
                     : max_active_walk_mixed_val768(threads, smem_bytes);
 }
 
-// Point-cloud obstacles for the tensor-core walker (pointcloud.cu): BF16-split point tiles in
-// the MMA's core-matrix layout, their TMA tensor map, and padded FP32 copies for refinement.
-// Sphere set for the tensor-core walker: points (radius 0) or balls. Balls are sorted by radius
-// so that each 32-column chunk spans a narrow radius range; chunk_rhi bounds the radii of a
-// chunk from above.
+// Sphere set for the tensor-core walker (pointcloud.cu): points (radius 0) or balls, as
+// BF16-split centre tiles in the MMA's core-matrix layout and FP32 records of 16 spheres for the
+// exact pass. Balls are sorted by radius so that each record spans a narrow radius range;
+// chunk_rhi bounds the radii of a record from above.
 struct PointCloudDev {
-    void *tiles = nullptr;      // n_tiles x 4 KB BF16 tiles, already in the shared-memory layout
-    float *soa = nullptr;       // per 32-sphere chunk: centres by coordinate quads, then 32 radii
-    float *chunk_rhi = nullptr; // largest radius of each 32-column chunk (rounded up)
+    void *tiles = nullptr;      // n_tiles x 64 centres, BF16, already in the shared-memory layout
+    float *soa = nullptr;       // per 16-sphere record: centres by coordinate quads, then 16 radii
+    float *chunk_rhi = nullptr; // largest radius of each 16-sphere record (rounded up)
     int n_tiles = 0;
     int spheres = 0;            // 1: balls with radii; 0: points
     double pmax = 0.0;  // largest |coordinate| of a centre
@@ -207,8 +206,10 @@ struct SphereLaunch {
     double *radius_out;  // nullable: distance bound at each walk's start (single problem only)
     SphereProblem single;
 };
-// src: a problem of the launch has an impulse source (selects the kernel variant with the source term)
-cudaError_t launch_spheres(const SphereLaunch &L, int d, int grad, int src, int grid, cudaStream_t s);
+// src: a problem of the launch has an impulse source (selects the kernel variant with the source
+// term); wide: 32-column candidate chunks instead of 16 (sphere_wide of every set of the launch;
+// d <= kSphereWideMaxD)
+cudaError_t launch_spheres(const SphereLaunch &L, int d, int grad, int src, int wide, int grid, cudaStream_t s);
 int sphere_ctas_per_sm();
 // Single problem: implicit items, grid sized to the work.
 cudaError_t launch_pointcloud(const PointCloudDev &pcd, const MixedProblem &P, float delta,
@@ -227,5 +228,22 @@ constexpr int kPointCloudMaxD = 12;  // 3d + 2 BF16 columns fit a 32- or 48-wide
 // time over tensor-core time 1.13-1.31 at 96 balls for d <= 4, 1.05-1.15 at 160 balls for d = 5..9,
 // 1.04-1.13 at 128 balls for d = 10..12).
 constexpr int sphere_min_balls(int d) { return d <= 4 ? 96 : (d <= 9 ? 160 : 128); }
+// Sets of at least kSphereWideTiles 64-centre tiles in d <= kSphereWideMaxD take 32-column
+// candidate chunks: the per-tile bound work then outweighs the exact pass, which 16-column chunks
+// halve. The width is a property of the domain, so that a problem takes the same walks alone and
+// in a batch. Measured (u and grad u): 65536 points in d = 7, 17 % faster; 64 tiles in d = 8,
+// 10 % faster alone at full occupancy but 4 % slower in the batched step, whose launches of
+// large sets run few CTAs; 24-64 tiles in d = 12, 4-10 % slower.
+constexpr int kSphereWideTiles = 128;
+constexpr int kSphereWideMaxD = 8;
+constexpr int sphere_wide(int d, int n_tiles) { return d <= kSphereWideMaxD && n_tiles >= kSphereWideTiles ? 1 : 0; }
+// Batched sphere-set queues, per dimension: sets below kSphereLargeTiles tiles, larger 16-column
+// sets, 32-column sets (each queue one launch; measured 640.5 vs 645.5 ms per batched step against
+// one queue per dimension).
+constexpr int kSphereLargeTiles = 24;
+constexpr int kSphereQueueClasses = 3;
+constexpr int sphere_queue_class(int d, int n_tiles) {
+    return sphere_wide(d, n_tiles) ? 2 : (n_tiles >= kSphereLargeTiles ? 1 : 0);
+}
 
 }  // namespace wos

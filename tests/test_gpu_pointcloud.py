@@ -45,9 +45,9 @@ def small_cloud(n_surfaces=4, per_surface=500, d=7, exp_data=True, sigma=25.0):
     return dom, pts, rng
 
 
-def exact_radius(dom, pts, X):
-    d = X.shape[1]
-    dp = np.sqrt(((X[:, None, :] - pts[None, :, :]) ** 2).sum(-1)).min(1)
+def exact_radius(dom, pts, X, block=256):
+    dp = np.concatenate([np.sqrt(((X[i:i + block, None, :] - pts[None, :, :]) ** 2).sum(-1)).min(1)
+                         for i in range(0, X.shape[0], block)])
     box = np.minimum(X - dom["box_lo"][None, :], dom["box_hi"][None, :] - X).min(1)
     r = np.minimum(dp, box)
     if dom.get("goal_r") is not None:
@@ -65,8 +65,10 @@ def gpu_radius(dom_h, X):
     return np_(out)
 
 
-def test_radius_bound_is_safe_and_tight():
-    dom, pts, rng = small_cloud(exp_data=False)
+@pytest.mark.parametrize("n_surfaces,per_surface", [(4, 500), (16, 600)])
+def test_radius_bound_is_safe_and_tight(n_surfaces, per_surface):
+    """2000 points (32 tiles: 16-point chunks) and 9600 (150 tiles: 32-point chunks)."""
+    dom, pts, rng = small_cloud(exp_data=False, n_surfaces=n_surfaces, per_surface=per_surface)
     D = W.Domain(dom)
     d = dom["d"]
     far = rng.uniform(-0.9, 0.9, size=(3000, d))

@@ -1,5 +1,6 @@
 """Ball sets on the tensor-core sphere-set walker (|c|^2 - 2 x.c by tcgen05.mma, balls sorted by
-radius into 32-ball chunks, exact FP32 refinement of the best chunk, lower bound for the rest).
+radius into 16-ball chunks, or 32-ball ones from 128 tiles of 64 balls up in d <= 8, exact FP32
+refinement of the best chunk, lower bound for the rest).
 
 * the distance bound never exceeds the exact FP64 distance |x - c| - r (minus box) and is
   tight for most points;
@@ -44,9 +45,10 @@ def ball_problem(d, B, sigma, seed, n_queries):
     return dom, X, rng
 
 
-def exact_radius(dom, X):
+def exact_radius(dom, X, block=256):
     c, r = dom["ball_c"], dom["ball_r"]
-    db = (np.sqrt(((X[:, None, :] - c[None, :, :]) ** 2).sum(-1)) - r[None, :]).min(1)
+    db = np.concatenate([(np.sqrt(((X[i:i + block, None, :] - c[None, :, :]) ** 2).sum(-1)) - r[None, :]).min(1)
+                         for i in range(0, X.shape[0], block)])
     box = np.minimum(X - dom["box_lo"][None, :], dom["box_hi"][None, :] - X).min(1)
     return np.minimum(db, box)
 
@@ -61,8 +63,9 @@ def gpu_radius(D, X):
     return np_(out)
 
 
-@pytest.mark.parametrize("d,B", [(3, 4096), (7, 1000), (10, 600), (12, 800)])
+@pytest.mark.parametrize("d,B", [(3, 4096), (3, 8192), (7, 1000), (8, 9000), (10, 600), (12, 800), (12, 2048)])
 def test_radius_bound_is_safe_and_tight(d, B):
+    """Both chunk widths (32 columns for the 8192 and 9000 balls) and both contraction lengths."""
     dom, X, rng = ball_problem(d, B, 4.0, 11 + d, 2000)
     D = W.Domain(dom)
     # also points close to ball surfaces (outside them)
@@ -100,6 +103,34 @@ def test_walks_match_oracle_and_cuda_core_screen(d, B):
     ex = np.exp(X @ a)
     u, se = np_(tc["u"]), np_(tc["u_se"])
     assert np.all(np.abs(u - ex) <= 4.5 * se + 3e-3 * ex)
+
+
+def test_wide_chunks_match_oracle_alone_and_batched():
+    """A set of 8192 balls (128 tiles: 32-column candidate chunks) in d = 5: the walks against the
+    oracle, and the same problem in a batch beside a 16-column set takes the same walks."""
+    dom, X, _ = ball_problem(5, 8192, 9.0, 41, 8)
+    D = W.Domain(dom)
+    assert D.info()["tensor_sphere_set"] and D.info()["sphere_tiles"] == 128
+    N, eps, sigma, seed = 1024, 1e-3, 9.0, 6
+    ref = oracle.solve(dom, X, N, eps, sigma, seed, grad=True, control_variate=True)
+    got = D.grad(X, N, eps, sigma, seed=seed, with_stats=True, control_variate=True)
+    st = W.stats_dict(got["stats"])
+    assert st["walks"] == 8 * N and st["outside"] == 0
+    assert np.all(within(np_(got["u"]), np_(got["u_se"]), ref["u"], ref["u_se"]))
+    assert np.all(within(np_(got["grad"]), np_(got["grad_se"]), ref["grad"], ref["grad_se"]))
+    a = dom["exp_a"][0]
+    ex = np.exp(X @ a)
+    assert np.all(np.abs(np_(got["u"]) - ex) <= 4.5 * np_(got["u_se"]) + 3e-3 * ex)
+    dom2, X2, _ = ball_problem(5, 700, sigma, 42, 16)
+    b = W.Batch([{"domain": D, "x": X, "n_walks": N, "eps": eps, "sigma": sigma, "grad": True},
+                 {"domain": W.Domain(dom2), "x": X2, "n_walks": 256, "eps": eps, "sigma": sigma, "grad": True}],
+                seed=seed, control_variate=True)
+    out = b.run()
+    torch.cuda.synchronize()
+    assert np.array_equal(np_(out[0]["walk_steps"]).sum(), st["walk_steps"])
+    for k in ("u", "grad"):
+        assert np.allclose(np_(out[0][k]), np_(got[k]), rtol=1e-12, atol=1e-15), k
+    b.close()
 
 
 def test_large_problem_exact_solution():
