@@ -83,7 +83,7 @@ def aggregate_over_ranks(seconds, units, world, device="cpu"):
 KERNEL_SOURCES = ["paper_2406_01713_gb300/csrc/walk_mixed.cuh", "paper_2406_01713_gb300/csrc/wos_device.cuh",
                   "paper_2406_01713_gb300/csrc/wos_launch.h"]
 TRAFFIC_PROFILE = "profiles/walk_mixed_batched_traffic.txt"
-SPHERE_SOURCES = ["paper_2406_01713_gb300/csrc/pointcloud.cu"] + KERNEL_SOURCES
+SPHERE_SOURCES = ["paper_2406_01713_gb300/csrc/sphere_kernel.cuh", "paper_2406_01713_gb300/csrc/pointcloud.cu"] + KERNEL_SOURCES
 SPHERE_TRAFFIC_PROFILE = "profiles/sphere_kernel_batched_traffic.txt"
 
 
@@ -481,9 +481,9 @@ def kernel_rooflines(W, doms, probs, seed, config, cv, peaks, sms, sm_max, flush
                 mma += s_ * (-(-m // 64) * 64) * 2 * contraction_k(dd["d"])
             peak = peaks.get("bf16_tflops_sustained") or 1700.0
             r = {"bound": "tensor", "peak": peak, "peak_note": "measured sustained dense BF16 (cuBLAS), "
-                 "MEASURED_PEAKS.json", "kernel": "sphere_kernel<d, true> (tensor-core sphere-set walker, one "
-                 "launch per dimension)", "traffic": measured_traffic(SPHERE_TRAFFIC_PROFILE, SPHERE_SOURCES),
-                 "traffic_note": "ncu dram__bytes_read+write summed over the per-dimension launches of one "
+                 "MEASURED_PEAKS.json", "kernel": "sphere_kernel<d, true, false, 16|32> (tensor-core sphere-set "
+                 "walker, one launch per queue: dimension x set class)", "traffic": measured_traffic(SPHERE_TRAFFIC_PROFILE, SPHERE_SOURCES),
+                 "traffic_note": "ncu dram__bytes_read+write summed over the sphere-set launches of one "
                                  "batch run (profiles/sphere_kernel_batched_traffic.txt); tiles and sums are "
                                  "L2-resident",
                  "flops_note": "achieved counts the method's work, B(2d+3)+4d flops per walk-step (the same "
