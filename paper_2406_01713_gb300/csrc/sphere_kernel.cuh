@@ -4,8 +4,9 @@
 // (Sec. VI, |q - c_i| - r_i), for 128 walkers at a time. The contraction
 // D_wi = |c_i|^2 - 2 x_w . c_i runs as tcgen05.mma (BF16 inputs, FP32 accumulation in tensor
 // memory) over centre tiles that bulk copies (cp.async.bulk) stream into shared memory; the
-// walker warps read their rows back with tcgen05.ld. Per chunk of CH columns (16, or 32 for
-// large sets, a template parameter), min D gives a lower bound of the chunk's distances,
+// walker warps take the minimum of each 16 columns of their rows with the reducing form of the
+// tensor-memory load (tcgen05.ld.red .min). Per chunk of CH columns (16, or 32 for large sets, a
+// template parameter), min D gives a lower bound of the chunk's distances,
 // sqrt(min D + |x|^2 - delta) - r_hi (balls are sorted by radius, so r_hi, the chunk's largest
 // radius, is close to every radius in it); each walker keeps the best, second and third chunk
 // bounds. The best chunk is then recomputed exactly in FP32 (the second too when its bound is
@@ -249,23 +250,23 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-static_assert(kTileN == 64 && kChunk == 16, "the epilogue reads a 64-column tile as two 32-column loads of two records each");
+static_assert(kTileN == 64 && kChunk == 16, "the epilogue reads a 64-column tile as four 16-column minima");
 
-// 32 accumulator columns of this thread's TMEM lane, loaded and waited for in one step.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-#define R8(i) "=r"(r[i]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), "=r"(r[i + 4]), "=r"(r[i + 5]), "=r"(r[i + 6]), "=r"(r[i + 7])
+// Minima of the two 16-column groups of 32 accumulator columns of this thread's TMEM lane, taken
+// by the loads themselves (tcgen05.ld.red with .min, an sm_103a form: each load also returns the
+// minimum of the columns it loads). The columns land in scratch registers declared inside the
+// statement and are never read; both loads are waited for before it ends.
+__device__ __forceinline__ void tmem_min16x2(uint32_t taddr, float &m0, float &m1) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%"
-        "28,%29,%30,%31}, [%32];\n"
-        "tcgen05.wait::ld.sync.aligned;\n"
-        : R8(0), R8(8), R8(16), R8(24)
-        : "r"(taddr)
+        "{\n .reg .f32 t<32>;\n"
+        "tcgen05.ld.red.sync.aligned.32x32b.x16.min.f32 "
+        "{t0,t1,t2,t3,t4,t5,t6,t7,t8,t9,t10,t11,t12,t13,t14,t15}, %0, [%2];\n"
+        "tcgen05.ld.red.sync.aligned.32x32b.x16.min.f32 "
+        "{t16,t17,t18,t19,t20,t21,t22,t23,t24,t25,t26,t27,t28,t29,t30,t31}, %1, [%3];\n"
+        "tcgen05.wait::ld.sync.aligned;\n}\n"
+        : "=f"(m0), "=f"(m1)
+        : "r"(taddr), "r"(taddr + 16)
         : "memory");
-#undef R8
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // Lower bounds of sqrt(max(s, 0)) from the hardware approximation, whose excess over the exact
@@ -278,21 +279,6 @@ __device__ __forceinline__ float sqrt_approx(float s) {
 }
 __device__ __forceinline__ float sqrt_below(float s) { return sqrt_approx(s) * 0.9999847412109375f; }
 __device__ __forceinline__ float sqrt_below_tight(float s) { return sqrt_approx(s) * 0.999999761581420898f; }
-
-__device__ __forceinline__ float min32(const float *v) {
-    float m[11];
-#pragma unroll
-    for (int i = 0; i < 10; ++i) m[i] = fmin3(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
-    m[10] = fminf(v[30], v[31]);
-    const float a = fmin3(m[0], m[1], m[2]), b = fmin3(m[3], m[4], m[5]), c = fmin3(m[6], m[7], m[8]);
-    return fmin3(fmin3(a, b, c), m[9], m[10]);
-}
-
-__device__ __forceinline__ float min16(const float *v) {
-    const float a = fmin3(v[0], v[1], v[2]), b = fmin3(v[3], v[4], v[5]), c = fmin3(v[6], v[7], v[8]);
-    const float e = fmin3(v[9], v[10], v[11]), f = fmin3(v[12], v[13], v[14]);
-    return fmin3(fmin3(a, b, c), fmin3(e, f, v[15]), a);
-}
 
 // Writes this walker's A row (BF16 split of x; zeros for an idle lane).
 template <int D>
@@ -589,7 +575,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
 
             // ---- epilogue: best and second-best CH-column chunk by the lower bound
             //      sqrt(min D~ + |x|^2 - delta) - r_hi, D~ = |c|^2 - 2 x.c (the square root
-            //      rounded down); one 32-column TMEM load at a time keeps registers free
+            //      rounded down); the TMEM loads return the 16-column minima
             float xx = 0.f;
 #pragma unroll
             for (int i = 0; i < D; ++i) xx = fmaf(x[i], x[i], xx);
@@ -620,24 +606,21 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 float cmin[kChunksPerTile];
                 {
-                    float v[32];
-                    tmem_ld32(trow + b * kTileN, v);
-                    if constexpr (CH == kChunk) {
-                        cmin[0] = min16(v);
-                        cmin[1] = min16(v + 16);
-                    } else {
-                        cmin[0] = min32(v);
-                    }
-                    tmem_ld32(trow + b * kTileN + 32, v);
-                    // the accumulator buffer is free as soon as its columns are in registers
+                    float q[4];  // minima of the tile's four 16-column groups
+                    tmem_min16x2(trow + b * kTileN, q[0], q[1]);
+                    tmem_min16x2(trow + b * kTileN + 32, q[2], q[3]);
+                    // the accumulator buffer is free as soon as its minima are in registers
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&S.tempty[b]);
                     if constexpr (CH == kChunk) {
-                        cmin[2] = min16(v);
-                        cmin[3] = min16(v + 16);
+                        cmin[0] = q[0];
+                        cmin[1] = q[1];
+                        cmin[2] = q[2];
+                        cmin[3] = q[3];
                     } else {
-                        cmin[1] = min32(v);
+                        cmin[0] = fminf(q[0], q[1]);
+                        cmin[1] = fminf(q[2], q[3]);
                     }
                 }
 #pragma unroll
