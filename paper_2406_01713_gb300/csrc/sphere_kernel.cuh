@@ -269,6 +269,28 @@ __device__ __forceinline__ void tmem_min16x2(uint32_t taddr, float &m0, float &m
         : "memory");
 }
 
+// The same for two 32-column groups (the minima of 32-column chunks), one load at a time.
+__device__ __forceinline__ void tmem_min32x2(uint32_t taddr, float &m0, float &m1) {
+    asm volatile(
+        "{\n .reg .f32 t<32>;\n"
+        "tcgen05.ld.red.sync.aligned.32x32b.x32.min.f32 "
+        "{t0,t1,t2,t3,t4,t5,t6,t7,t8,t9,t10,t11,t12,t13,t14,t15,"
+        "t16,t17,t18,t19,t20,t21,t22,t23,t24,t25,t26,t27,t28,t29,t30,t31}, %0, [%1];\n"
+        "tcgen05.wait::ld.sync.aligned;\n}\n"
+        : "=f"(m0)
+        : "r"(taddr)
+        : "memory");
+    asm volatile(
+        "{\n .reg .f32 t<32>;\n"
+        "tcgen05.ld.red.sync.aligned.32x32b.x32.min.f32 "
+        "{t0,t1,t2,t3,t4,t5,t6,t7,t8,t9,t10,t11,t12,t13,t14,t15,"
+        "t16,t17,t18,t19,t20,t21,t22,t23,t24,t25,t26,t27,t28,t29,t30,t31}, %0, [%1];\n"
+        "tcgen05.wait::ld.sync.aligned;\n}\n"
+        : "=f"(m1)
+        : "r"(taddr + 32)
+        : "memory");
+}
+
 // Lower bounds of sqrt(max(s, 0)) from the hardware approximation, whose excess over the exact
 // root was measured below 2^-23.6 on every float in [2^-40, 2^40): scaled down by 2^-16 (chunk
 // bounds) or 2^-22 (refined distances, which stay within an FP32 rounding of the exact value).
@@ -606,22 +628,17 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 float cmin[kChunksPerTile];
                 {
-                    float q[4];  // minima of the tile's four 16-column groups
-                    tmem_min16x2(trow + b * kTileN, q[0], q[1]);
-                    tmem_min16x2(trow + b * kTileN + 32, q[2], q[3]);
+                    // the chunk minima (16 columns each, or 32)
+                    if constexpr (CH == kChunk) {
+                        tmem_min16x2(trow + b * kTileN, cmin[0], cmin[1]);
+                        tmem_min16x2(trow + b * kTileN + 32, cmin[2], cmin[3]);
+                    } else {
+                        tmem_min32x2(trow + b * kTileN, cmin[0], cmin[1]);
+                    }
                     // the accumulator buffer is free as soon as its minima are in registers
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&S.tempty[b]);
-                    if constexpr (CH == kChunk) {
-                        cmin[0] = q[0];
-                        cmin[1] = q[1];
-                        cmin[2] = q[2];
-                        cmin[3] = q[3];
-                    } else {
-                        cmin[0] = fminf(q[0], q[1]);
-                        cmin[1] = fminf(q[2], q[3]);
-                    }
                 }
 #pragma unroll
                 for (int c = 0; c < kChunksPerTile; ++c) {
