@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
         int k = 0;
         long long j = -1, q = 0;
         bool active = false;
-        long long g_epi = 0;
+        uint32_t g_epi = 0;  // tiles read so far (only its two low bits are used: wrapping is harmless)
         for (int step = 0;; ++step) {
             // refill idle lanes from the CTA's item (warp-aggregated claim on its counter)
             {
@@ -605,22 +605,27 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sphere_kernel(const __gr
             float m1 = CUDART_INF_F, m2 = CUDART_INF_F, m3 = CUDART_INF_F;
             int c1 = 0, c2 = 0;
             bool ok = true;
-            // the record radius bounds of the next tile (one 16-byte load), fetched a tile ahead
+            // the record radius bounds of a tile (one 16-byte load): issued before the wait for
+            // the tile's accumulators with 16-column chunks (fewer registers live across the tile
+            // loop: fewer spills at the 96-register cap), fetched a tile ahead with 32-column ones
+            // (no spill in d = 4..7 that way)
             const float4 *const rhi4 = reinterpret_cast<const float4 *>(chunk_rhi);
-            float4 rhi_next = __ldg(rhi4);
+            float4 rhi_ahead = make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (CH != kChunk) rhi_ahead = __ldg(rhi4);
             for (int t = 0; t < T; ++t, ++g_epi) {
                 const int b = (int)(g_epi & 1);
                 float rhi[kChunksPerTile];
                 if constexpr (CH == kChunk) {
-                    rhi[0] = rhi_next.x;
-                    rhi[1] = rhi_next.y;
-                    rhi[2] = rhi_next.z;
-                    rhi[3] = rhi_next.w;
+                    const float4 r4 = __ldg(rhi4 + t);
+                    rhi[0] = r4.x;
+                    rhi[1] = r4.y;
+                    rhi[2] = r4.z;
+                    rhi[3] = r4.w;
                 } else {
-                    rhi[0] = fmaxf(rhi_next.x, rhi_next.y);
-                    rhi[1] = fmaxf(rhi_next.z, rhi_next.w);
+                    rhi[0] = fmaxf(rhi_ahead.x, rhi_ahead.y);
+                    rhi[1] = fmaxf(rhi_ahead.z, rhi_ahead.w);
+                    rhi_ahead = __ldg(rhi4 + (t + 1 < T ? t + 1 : t));
                 }
-                rhi_next = __ldg(rhi4 + (t + 1 < T ? t + 1 : t));
                 if (!warp_wait_bar(S, &S.tfull[b], (uint32_t)((g_epi >> 1) & 1), L)) {
                     ok = false;
                     break;
