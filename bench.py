@@ -375,8 +375,17 @@ def main():
                                                                            "frac", "ms", "share", "kernel",
                                                                            "mma_achieved", "mma_frac")}
                                for k, r in kernels.items()}
-    n_sphere_dims = len({p["domain"]["d"] for d, p in zip(doms, probs) if d.info()["tensor_sphere_set"]})
-    launches_per_step = 1 + (0 if args.no_cv else 1) + n_sphere_dims + (1 if "cuda_core" in kernels else 0)
+    # kernels of one batch run: one sphere-set launch per queue (dimension x set class: below 24
+    # tiles, 24 or more, 32-column sets of 128+ tiles in d <= 8), the CUDA-core walker, the
+    # per-query reduction, its segment combine (queries of more than 4096 walks) and finalize
+    def queue(d, p):
+        tiles = d.info()["sphere_tiles"]
+        dd = p["domain"]["d"]
+        return dd, 2 if (dd <= 8 and tiles >= 128) else (1 if tiles >= 24 else 0)
+    n_sphere_queues = len({queue(d, p) for d, p in zip(doms, probs) if d.info()["tensor_sphere_set"]})
+    any_segments = any(p["n_walks"] > 4096 for p in probs)
+    launches_per_step = (n_sphere_queues + (1 if "cuda_core" in kernels else 0) + 1 + (1 if any_segments else 0)
+                         + 1)
 
     line = {"metric": METRIC, "value": value, "unit": "walk-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
