@@ -2431,7 +2431,7 @@ wos_status wos_batch_autotune(wos_batch_t b, const char *cache_path, wos_batch_c
         return true;
     };
     bool ok = true;
-    // round 1: the CUDA-core walker's shapes, the tensor-core walker at its default
+    // first pass: the CUDA-core walker's shapes, the tensor-core walker at its default
     {
         wos_batch_config c = default_batch_config();
         for (int th : {512, 768})
@@ -2446,7 +2446,7 @@ wos_status wos_batch_autotune(wos_batch_t b, const char *cache_path, wos_batch_c
         c.item_work = (int64_t)1 << 26;
         if (ok) ok = run(c);
     }
-    // round 2: the tensor-core walker's shapes with the best CUDA-core shape
+    // second pass: the tensor-core walker's shapes with the best CUDA-core shape
     if (ok && b->n_sphere_items > 0) {
         wos_batch_config c = best_cfg;
         for (int sct : {4, 3, 2})
