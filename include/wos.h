@@ -91,10 +91,11 @@ typedef enum {
 #define WOS_FLAG_GRAD_CONTROL_VARIATE 2
 
 /*
- * Ball sets of at least 192 (d <= 4), 320 (d = 5, 6) or 288 (d >= 7) balls run, in WOS_MIXED,
- * on the tensor-core sphere-set walker (the same walker as point sets: |c|^2 - 2 x.c by tcgen05.mma, exact FP32 refinement of
- * the best 32-ball chunk, a proven lower bound for the rest). This flag keeps them on the
- * CUDA-core ball screen instead (for comparisons; both are exact up to their error bounds).
+ * Ball sets of at least 96 (d <= 4), 160 (d = 5..9) or 128 (d = 10..12) balls run, in WOS_MIXED,
+ * on the tensor-core sphere-set walker (the same walker as point sets: |c|^2 - 2 x.c by
+ * tcgen05.mma, exact FP32 refinement of the best 16-ball chunk -- 32-ball for sets of 8192 or
+ * more in d <= 8 --, a proven lower bound for the rest). This flag keeps them on the CUDA-core
+ * ball screen instead (for comparisons; both are exact up to their error bounds).
  */
 #define WOS_FLAG_CUDA_CORE_BALLS 4
 
@@ -268,8 +269,8 @@ wos_status wos_domain_set_exp_w(wos_domain_t dom, const double *w_device, int32_
 
 /*
  * Which walker the domain's obstacles run on in WOS_MIXED: *tensor_sphere_set = 1 if they form a
- * tensor-core sphere set (a point set, or a ball set of at least 192, 320 or 288 balls for
- * d <= 4, d = 5, 6, d >= 7), with *sphere_tiles
+ * tensor-core sphere set (a point set, or a ball set of at least 96, 160 or 128 balls for
+ * d <= 4, d = 5..9, d = 10..12), with *sphere_tiles
  * 64-sphere tiles; 0 (and 0 tiles) for the CUDA-core walker. Host outputs; either may be NULL.
  * No counterpart in the paper (introspection for schedulers and benchmarks).
  * Errors: INVALID_ARG (NULL domain).
@@ -400,8 +401,8 @@ typedef struct {
  * Builds a batch: uploads the problem table and the longest-first work queues, sizes the
  * persistent grids to a multiple of the SM count, and records one CUDA graph: [reset, the
  * CUDA-core persistent walker for the problems with small ball sets, in parallel one
- * tensor-core sphere-set walker launch per dimension for the problems with tensor-core sphere
- * sets (large ball sets or a point set; WOS_FLAG_CUDA_CORE_BALLS keeps ball sets off it), the
+ * tensor-core sphere-set walker launch per dimension and set size class (below 24 tiles of 64
+ * spheres, 24 or more, 32-column sets) for the problems with tensor-core sphere sets (large ball sets or a point set; WOS_FLAG_CUDA_CORE_BALLS keeps ball sets off it), the
  * per-query reduction of the walks' records, finalize]. Problems may differ in d, obstacle
  * count, walk budget, sigma and eps. Precision is WOS_MIXED. The problems' domains and buffers
  * must outlive the batch; the batch holds a record of 16 to 96 bytes per walk (see below).
@@ -483,8 +484,8 @@ wos_status wos_debug_philox(uint64_t seed, uint64_t walk0, int64_t n, uint32_t s
                             uint32_t block, uint32_t *out, void *stream);
 
 /* Writes, for each point x[q] (Q x d device doubles), the distance bound the tensor-core
- * point-cloud walker uses there -- min over the FP32 refinement of its best 32-point candidate
- * chunk, the second-best chunk minus the BF16 error bound, and the other components -- to
+ * point-cloud walker uses there -- min over the FP32 refinement of its best candidate chunk (16
+ * or 32 points), the second-best chunk minus the BF16 error bound, and the other components -- to
  * radius[q] (device doubles). Sec. VII-A point-set distance (and Sec. VI ball distance for a
  * tensor-core ball set); for checks that the bound never exceeds the exact distance.
  * Errors: UNSUPPORTED without a tensor-core sphere set. */
