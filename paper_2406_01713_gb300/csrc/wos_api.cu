@@ -1855,7 +1855,7 @@ struct wos_batch_s {
     std::vector<unsigned long long *> cnt_ptr;    // ... and counters
     int min_walks_per_lane = 8;  // CUDA-core items hold at least this many walks per lane
     wos_stats *d_stats = nullptr;
-    // one run: [memset zeroed region] [tensor-core launches per dimension | CUDA-core walker]
+    // one run: [memset zeroed region] [tensor-core launches per queue | CUDA-core walker]
     // [reduction] [finalize]
     MixedLaunch L{};
     std::vector<SphereLaunch> sph;
@@ -2079,9 +2079,9 @@ wos_status batch_build(wos_batch_s *b, const wos_batch_config &cfg_in) {
     }
     b->n_items = (int64_t)sorted.size();
     b->total_q = q_begin;
-    // sphere-set items: one queue per dimension, problems by decreasing cost, sphere_item_walks
-    // walks per item (a CTA continues into the next item of the same problem without a pause, so
-    // items only matter for the balance at the end)
+    // sphere-set items: one queue per dimension and set class (sphere_queue_class), problems by
+    // decreasing cost, sphere_item_walks walks per item (a CTA continues into the next item of the
+    // same problem without a pause, so items only matter for the balance at the end)
     const int64_t kSphereItemWalks = cfg.sphere_item_walks;
     std::vector<int> sph_index(n, -1);
     std::vector<int> sph_problem;  // sphere problem -> batch problem
