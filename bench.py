@@ -80,6 +80,13 @@ def aggregate_over_ranks(seconds, units, world, device="cpu"):
     return float(t[0]), float(u[0]), float(u[0]) / float(t[0])
 
 
+def sphere_queue_class(d, tiles):
+    """The batch's queue class of a tensor-core sphere set (its launches are one per dimension and
+    class): 2 for 32-column sets (128 or more tiles of 64 spheres in d <= 8), 1 for 24 or more
+    tiles, 0 below."""
+    return 2 if (d <= 8 and tiles >= 128) else (1 if tiles >= 24 else 0)
+
+
 KERNEL_SOURCES = ["paper_2406_01713_gb300/csrc/walk_mixed.cuh", "paper_2406_01713_gb300/csrc/wos_device.cuh",
                   "paper_2406_01713_gb300/csrc/wos_launch.h"]
 TRAFFIC_PROFILE = "profiles/walk_mixed_batched_traffic.txt"
@@ -375,14 +382,10 @@ def main():
                                                                            "frac", "ms", "share", "kernel",
                                                                            "mma_achieved", "mma_frac")}
                                for k, r in kernels.items()}
-    # kernels of one batch run: one sphere-set launch per queue (dimension x set class: below 24
-    # tiles, 24 or more, 32-column sets of 128+ tiles in d <= 8), the CUDA-core walker, the
+    # kernels of one batch run: one sphere-set launch per queue, the CUDA-core walker, the
     # per-query reduction, its segment combine (queries of more than 4096 walks) and finalize
-    def queue(d, p):
-        tiles = d.info()["sphere_tiles"]
-        dd = p["domain"]["d"]
-        return dd, 2 if (dd <= 8 and tiles >= 128) else (1 if tiles >= 24 else 0)
-    n_sphere_queues = len({queue(d, p) for d, p in zip(doms, probs) if d.info()["tensor_sphere_set"]})
+    n_sphere_queues = len({(p["domain"]["d"], sphere_queue_class(p["domain"]["d"], d.info()["sphere_tiles"]))
+                           for d, p in zip(doms, probs) if d.info()["tensor_sphere_set"]})
     any_segments = any(p["n_walks"] > 4096 for p in probs)
     launches_per_step = (n_sphere_queues + (1 if "cuda_core" in kernels else 0) + 1 + (1 if any_segments else 0)
                          + 1)
